@@ -1,0 +1,179 @@
+/*
+ * wilson_mg.h -- C-ABI of a GB300 (sm_103a) adaptive multigrid solver for the
+ * lattice Wilson-Dirac equation D(U) psi = b (Babich et al., "Adaptive
+ * multigrid algorithm for the lattice Wilson-Dirac operator", arXiv:1005.3043).
+ *
+ * Every numerical step runs in CUDA kernels of this library.  Plain pointers
+ * and sizes only; no C++ or framework types cross this boundary.
+ *
+ * ---------------------------------------------------------------------------
+ * Layouts at the boundary (all host- and device-pointer arguments)
+ *   site index    s = x + L0*(y + L1*(z + L2*t)), mu = 0..3 is x, y, z, t
+ *   complex       two doubles (re, im)
+ *   links U       [mu 4][site][row 3][col 3] complex double
+ *   fine spinor   [site][spin 4][colour 3] complex double, DeGrand-Rossi
+ *                 (chiral) gamma basis: gamma5 = diag(1, 1, -1, -1)
+ *   null vectors  [i < Nv][site][spin][colour] complex double
+ *   coarse vector [X][2 Nv] complex double, X lexicographic over the coarse
+ *                 lattice L/B; dof a = s*Nv + i with chirality s = 0 (spins
+ *                 0,1) or 1 (spins 2,3)
+ *   coarse op     [X][d 9][a][b] complex double, (D_c y)[X] = sum_d A[X][d] y[X+d],
+ *                 d = 0 on-site, 1+2mu for X+mu, 2+2mu for X-mu
+ * Boundary conditions: periodic in x, y, z; antiperiodic in t when
+ * t_antiperiodic != 0.
+ *
+ * Ownership: the caller owns every buffer it passes; the library copies what
+ * it keeps.  The context owns all device memory it allocates and frees it in
+ * mg_destroy.  All work is issued on the stream given to mg_create; calls
+ * taking host buffers synchronise that stream before returning.
+ *
+ * Errors: every int-returning call returns MG_OK (0) or a negative
+ * mg_status; mg_last_error() gives a message.  A context is not thread-safe.
+ * ---------------------------------------------------------------------------
+ */
+#ifndef WILSON_MG_H
+#define WILSON_MG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mg_ctx mg_ctx;
+
+enum mg_status {
+    MG_OK = 0,
+    MG_ERR_INVALID_ARG = -1,   /* bad size, null pointer, L not divisible by B */
+    MG_ERR_NOT_SETUP = -2,     /* links / null vectors / coarse operator missing */
+    MG_ERR_OOM = -3,           /* device allocation failed */
+    MG_ERR_NOT_CONVERGED = -4, /* x holds the last iterate, info is filled */
+    MG_ERR_NUMERIC = -5,       /* NaN/Inf, breakdown, rank-deficient block QR */
+    MG_ERR_TIMEOUT = -6,       /* a bounded device wait gave up */
+    MG_ERR_CUDA = -7           /* a CUDA runtime call failed */
+};
+
+enum mg_precision { MG_FP64 = 0, MG_FP32 = 1 };
+
+/* Solver parameters (paper, Sec. III-IV; defaults from mg_default_params). */
+typedef struct {
+    int block[4];          /* aggregate (block) extent per direction, default 4^4 (Sec. III) */
+    int nvec;              /* N_v near-null vectors; 2 N_v coarse dof per site */
+    int setup_init_relax;  /* relaxation steps on each random vector (Sec. IV: 10) */
+    int setup_iters;       /* truncated-MG iterations per group (Sec. IV: 5) */
+    int setup_group;       /* prototypes refined together (Sec. IV: groups of 4) */
+    int smoother_steps;    /* post-smoothing steps, V(0,n) cycle (Sec. IV: 4) */
+    double omega;          /* smoother under-relaxation (Sec. III: 0.9) */
+    int gcr_restart;       /* flexible GCR restart length (Sec. III: GCR(8); default 16) */
+    double tol;            /* outer true relative residual ||b-Dx||/||b|| */
+    double coarse_tol;     /* coarse CG-on-normal-equations relative residual (Sec. IV: 1e-3) */
+    int max_outer;         /* maximum outer iterations (preconditioner applications) */
+    int max_coarse;        /* maximum coarse iterations per cycle */
+    double delta;          /* mixed precision: restart when ||r|| < delta * ||r at restart|| (0: off) */
+    int prec_inner;        /* MG_FP64 or MG_FP32: smoother, dslash, transfers, coarse solve, Krylov basis */
+    int coarse_check;      /* coarse iterations between convergence checks read by the host */
+} mg_params;
+
+typedef struct {
+    int outer_iters;       /* preconditioner applications (the paper's outer GCR count) */
+    int coarse_iters;      /* total coarse-solver iterations */
+    int fine_matvecs;      /* fine D applications, all precisions */
+    int restarts;          /* true-residual recomputations */
+    double true_rel_res;   /* ||b - D x|| / ||b|| in FP64 */
+    double solve_ms;       /* device time of the solve (CUDA events) */
+    int status;
+} mg_solve_info;
+
+/* Fill p with the defaults: block 4^4, nvec 8, relax 10, iters 3, group 4,
+ * smoother 4, omega 0.9, restart 16, tol 1e-10, coarse_tol 1e-3,
+ * max_outer 1000, max_coarse 5000, delta 0, FP64, coarse_check 16. */
+int mg_default_params(mg_params* p);
+
+/* Create a context for an L0 x L1 x L2 x L3 lattice.  dims[mu] must be a
+ * multiple of p->block[mu].  stream is a cudaStream_t (NULL: legacy default).
+ * Allocates the device buffers of the fine level; the coarse level is
+ * allocated by mg_set_null_vectors / mg_setup. */
+int mg_create(const int dims[4], int t_antiperiodic, const mg_params* p, void* stream, mg_ctx** out);
+
+/* Free every device buffer of the context.  Accepts NULL. */
+void mg_destroy(mg_ctx* ctx);
+
+/* Copy SU(3) links (host, boundary layout, 4*V*9 complex) to the device. */
+int mg_set_links(mg_ctx* ctx, const double* U);
+
+/* Bare mass m of eq. (2).  After a setup the coarse operator is shifted in
+ * place: D_c(m) = D_c(m0) + (m - m0) I, exact because P^dag P = I (eq. 4). */
+int mg_set_mass(mg_ctx* ctx, double m);
+
+/* Replace the solver parameters that do not change buffer sizes (tolerances,
+ * smoother, restart <= the value at create, precision, ...). */
+int mg_set_params(mg_ctx* ctx, const mg_params* p);
+
+/* Adaptive setup (Sec. II alpha-SA loop in the two-step form of Sec. IV) from
+ * caller-provided random starts V0 (host, Nv fine vectors): relaxation, group
+ * refinement with the truncated two-level method, block orthonormalisation
+ * (eq. 4) and the Galerkin coarse operator D_c = P^dag D P. */
+int mg_setup(mg_ctx* ctx, const double* V0);
+
+/* Use the given prototypes (host, nv == p->nvec fine vectors) as they are:
+ * block-orthonormalise them (eq. 4) and build D_c = P^dag D P. */
+int mg_set_null_vectors(mg_ctx* ctx, const double* V, int nv);
+
+/* Read back the block-orthonormal prolongator columns (host, Nv fine
+ * vectors: column (X, s, i) is vector i on the sites of X and spins of s). */
+int mg_get_prolongator(mg_ctx* ctx, double* P);
+
+/* Read back the current prototypes (host, Nv fine vectors). */
+int mg_get_null_vectors(mg_ctx* ctx, double* V);
+
+/* Read back D_c in FP64 (host, boundary coarse-operator layout). */
+int mg_get_coarse_op(mg_ctx* ctx, double* A);
+
+/* Solve D x = b by MG-preconditioned flexible GCR (Sec. III), x0 = 0.
+ * b, x: host fine spinors (FP64).  Returns MG_ERR_NOT_CONVERGED with x the
+ * last iterate when max_outer is reached. */
+int mg_solve(mg_ctx* ctx, const double* b, double* x, mg_solve_info* info);
+
+/* As mg_solve with b and x in device memory (boundary layout, FP64). */
+int mg_solve_device(mg_ctx* ctx, const double* b_dev, double* x_dev, mg_solve_info* info);
+
+/* ---- single steps of the method (host buffers, FP64 at the boundary; the
+ * ---- kernel runs in precision prec) -------------------------------------- */
+
+/* out = D in, eq. (2). */
+int mg_apply_dslash(mg_ctx* ctx, const double* in, double* out, int prec);
+
+/* r_c = P^dag r (eq. 8 with R = P^dag, chirality kept). */
+int mg_restrict(mg_ctx* ctx, const double* r, double* rc, int prec);
+
+/* e = P y_c. */
+int mg_prolong(mg_ctx* ctx, const double* yc, double* e, int prec);
+
+/* y = D_c x, or D_c^dag x = sigma3 D_c sigma3 x when dagger != 0. */
+int mg_apply_coarse(mg_ctx* ctx, const double* x, double* y, int dagger, int prec);
+
+/* nsteps MR smoothing steps on (e, r): q = D r, alpha = omega <q,r>/<q,q>,
+ * e += alpha r, r -= alpha q.  e and r are read and overwritten. */
+int mg_mr(mg_ctx* ctx, double* e, double* r, int nsteps, int prec);
+
+/* Coarse solve y = CGNR(D_c, rc) from y = 0 to ||rc - D_c y|| <= tol ||rc||
+ * or maxit iterations (tol = 0: exactly maxit). */
+int mg_coarse_solve(mg_ctx* ctx, const double* rc, double* y, double tol, int maxit, int prec,
+                    int* iters, double* final_rel);
+
+/* z = M r, one two-level V(0, smoother_steps) cycle. */
+int mg_vcycle(mg_ctx* ctx, const double* r, double* z, int prec);
+
+/* Device-resident operator application for timing: out = D in on internal
+ * buffers of the context, `reps` launches, returns the mean kernel time in
+ * ms (CUDA events on the context stream) and the bytes one launch must move
+ * at minimum (algorithmic: links + input + output, each read/written once). */
+int mg_time_dslash(mg_ctx* ctx, int prec, int reps, double* ms_per_launch, double* bytes_per_launch);
+
+const char* mg_status_string(int status);
+const char* mg_last_error(const mg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WILSON_MG_H */

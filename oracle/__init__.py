@@ -1,0 +1,257 @@
+"""CPU oracle for the adaptive multigrid Wilson-Dirac solve (arXiv:1005.3043).
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline / reference leg import this package; the product path
+never does.  It wraps ``oracle.c`` (plain FP64 C, one function per step of the
+method, each citing the paper passage it restates) through ctypes.
+
+Parity status per function (what pins it; see the tests):
+  dslash            free-field plane-wave eigenvalues, gamma5-hermiticity, gauge
+                    covariance, mass shift, dense brute force (eq. 2)
+  block_orthonormalize / restrict / prolong
+                    P^dag P = I, P V_c = V (eq. 4), gamma5 P = P sigma3,
+                    Q of numpy's QR up to phases
+  coarse_build / coarse_apply
+                    dense P^dag D P brute force, sigma3 D_c sigma3 = D_c^dag,
+                    mass shift, (I - P D_c^-1 P^dag D) P = 0 (eqs. 3, 8),
+                    nearest-neighbour sparsity, non-split singularity
+  mr                exact residual-decrease identity per step
+  cgnr              reaches the dense LU solution; CGLS orthogonality
+  gcr_solve         with M = I equals GMRES residuals; true residual <= tol
+  setup             parity unpinned as a bit pattern (iterative, nonlinear);
+                    pinned by the invariants of its outputs and by the two-grid
+                    convergence factor against random prototypes
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, ERR_ARG, ERR_NOT_CONVERGED, ERR_NUMERIC = 0, -1, -4, -5
+
+
+def build(force: bool = False) -> str:
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+               "-fcx-limited-range", "-Wall", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int * 4), ("B", ctypes.c_int * 4), ("nv", ctypes.c_int),
+                ("tap", ctypes.c_int), ("m", ctypes.c_double), ("mr_steps", ctypes.c_int),
+                ("omega", ctypes.c_double), ("coarse_tol", ctypes.c_double),
+                ("coarse_maxit", ctypes.c_int), ("gcr_restart", ctypes.c_int),
+                ("tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("use_mg", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("outer_iters", ctypes.c_int), ("coarse_iters", ctypes.c_int),
+                ("fine_matvecs", ctypes.c_int), ("restarts", ctypes.c_int),
+                ("true_rel_res", ctypes.c_double), ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+            lib.or_gamma_matrices.argtypes = [P]
+            lib.or_dslash.argtypes = [P, I, P, D, P, P]
+            lib.or_gamma5.argtypes = [I64, P, P]
+            lib.or_dot.argtypes = [I64, P, P, P]
+            lib.or_block_orthonormalize.argtypes = [P, P, I, P, P]
+            lib.or_block_orthonormalize.restype = I
+            lib.or_restrict.argtypes = [P, P, I, P, P, P]
+            lib.or_prolong.argtypes = [P, P, I, P, P, P]
+            lib.or_coarse_build.argtypes = [P, P, I, I, P, D, P, P]
+            lib.or_coarse_apply.argtypes = [P, I, P, P, P]
+            lib.or_coarse_apply_dag.argtypes = [P, I, P, P, P]
+            lib.or_mr.argtypes = [P, I, P, D, I, D, P, P]
+            lib.or_cgnr.argtypes = [P, I, P, P, P, D, I, P]
+            lib.or_cgnr.restype = I
+            lib.or_vcycle.argtypes = [P, P, P, P, P, P, P]
+            lib.or_gcr_solve.argtypes = [P, P, P, P, P, P, P]
+            lib.or_gcr_solve.restype = I
+            lib.or_setup.argtypes = [P, P, P, I, I, I, P, P]
+            lib.or_setup.restype = I
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"], "array must be C-contiguous"
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def _i4(L) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(L, dtype=np.int32).reshape(4))
+
+
+def volume(L) -> int:
+    return int(np.prod(np.asarray(L, dtype=np.int64)))
+
+
+def coarse_dims(L, B):
+    return tuple(int(l) // int(b) for l, b in zip(L, B))
+
+
+def gamma_matrices() -> np.ndarray:
+    g = np.zeros((4, 4, 4), dtype=np.complex128)
+    _load().or_gamma_matrices(_p(g))
+    return g
+
+
+def dslash(U, psi, m: float, L, tap: int = 1) -> np.ndarray:
+    """D(U) psi, eq. (2).  U (4,V,3,3), psi (V,4,3)."""
+    U, psi = _c(U), _c(psi)
+    out = np.empty_like(psi)
+    _load().or_dslash(_p(_i4(L)), int(tap), _p(U), float(m), _p(psi), _p(out))
+    return out
+
+
+def gamma5(psi) -> np.ndarray:
+    psi = _c(psi)
+    out = np.empty_like(psi)
+    _load().or_gamma5(psi.shape[0], _p(psi), _p(out))
+    return out
+
+
+def block_orthonormalize(Vecs, L, B):
+    """Returns (P, status).  Vecs (Nv,V,4,3) -> P (Nv,V,4,3)."""
+    Vecs = _c(Vecs)
+    P = np.empty_like(Vecs)
+    st = _load().or_block_orthonormalize(_p(_i4(L)), _p(_i4(B)), Vecs.shape[0], _p(Vecs), _p(P))
+    return P, st
+
+
+def restrict(P, r, L, B) -> np.ndarray:
+    P, r = _c(P), _c(r)
+    nv = P.shape[0]
+    Vc = volume(coarse_dims(L, B))
+    rc = np.empty((Vc, 2 * nv), dtype=np.complex128)
+    _load().or_restrict(_p(_i4(L)), _p(_i4(B)), nv, _p(P), _p(r), _p(rc))
+    return rc
+
+
+def prolong(P, yc, L, B) -> np.ndarray:
+    P, yc = _c(P), _c(yc)
+    nv = P.shape[0]
+    e = np.empty(P.shape[1:], dtype=np.complex128)
+    _load().or_prolong(_p(_i4(L)), _p(_i4(B)), nv, _p(P), _p(yc), _p(e))
+    return e
+
+
+def coarse_build(U, P, m: float, L, B, tap: int = 1) -> np.ndarray:
+    """A[Xc, 9, nc, nc] = P^dag D P in nearest-neighbour form."""
+    U, P = _c(U), _c(P)
+    nv = P.shape[0]
+    nc = 2 * nv
+    Vc = volume(coarse_dims(L, B))
+    A = np.empty((Vc, 9, nc, nc), dtype=np.complex128)
+    _load().or_coarse_build(_p(_i4(L)), _p(_i4(B)), nv, int(tap), _p(U), float(m), _p(P), _p(A))
+    return A
+
+
+def coarse_apply(A, x, Lc) -> np.ndarray:
+    A, x = _c(A), _c(x)
+    y = np.empty_like(x)
+    _load().or_coarse_apply(_p(_i4(Lc)), A.shape[-1], _p(A), _p(x), _p(y))
+    return y
+
+
+def coarse_apply_dag(A, x, Lc) -> np.ndarray:
+    A, x = _c(A), _c(x)
+    y = np.empty_like(x)
+    _load().or_coarse_apply_dag(_p(_i4(Lc)), A.shape[-1], _p(A), _p(x), _p(y))
+    return y
+
+
+def mr(U, e, r, m: float, L, nsteps: int, omega: float, tap: int = 1):
+    """nsteps MR steps; returns updated (e, r)."""
+    e, r = _c(e).copy(), _c(r).copy()
+    _load().or_mr(_p(_i4(L)), int(tap), _p(_c(U)), float(m), int(nsteps), float(omega), _p(e), _p(r))
+    return e, r
+
+
+def cgnr(A, rc, Lc, tol: float, maxit: int):
+    """Returns (y, iterations, final relative residual)."""
+    A, rc = _c(A), _c(rc)
+    y = np.empty_like(rc)
+    rel = ctypes.c_double(0)
+    it = _load().or_cgnr(_p(_i4(Lc)), A.shape[-1], _p(A), _p(rc), _p(y), float(tol), int(maxit),
+                         ctypes.byref(rel))
+    return y, it, rel.value
+
+
+def make_params(L, B=(4, 4, 4, 4), nv=8, m=0.0, tap=1, mr_steps=4, omega=0.9, coarse_tol=1e-3,
+                coarse_maxit=10000, gcr_restart=16, tol=1e-10, max_outer=1000, use_mg=1) -> Params:
+    p = Params()
+    for i in range(4):
+        p.L[i] = int(L[i]); p.B[i] = int(B[i])
+    p.nv, p.tap, p.m = int(nv), int(tap), float(m)
+    p.mr_steps, p.omega = int(mr_steps), float(omega)
+    p.coarse_tol, p.coarse_maxit = float(coarse_tol), int(coarse_maxit)
+    p.gcr_restart, p.tol, p.max_outer, p.use_mg = int(gcr_restart), float(tol), int(max_outer), int(use_mg)
+    return p
+
+
+def vcycle(params: Params, U, P, A, r):
+    U, P, A, r = _c(U), _c(P), _c(A), _c(r)
+    z = np.empty_like(r)
+    info = Info()
+    _load().or_vcycle(ctypes.byref(params), _p(U), _p(P), _p(A), _p(r), _p(z), ctypes.byref(info))
+    return z, info.as_dict()
+
+
+def gcr_solve(params: Params, U, P, A, b):
+    """Returns (x, info dict).  P, A may be None when params.use_mg == 0."""
+    U, b = _c(U), _c(b)
+    if P is None:
+        P = np.zeros((1, 1), dtype=np.complex128)
+        A = np.zeros((1, 1), dtype=np.complex128)
+    P, A = _c(P), _c(A)
+    x = np.empty_like(b)
+    info = Info()
+    _load().or_gcr_solve(ctypes.byref(params), _p(U), _p(P), _p(A), _p(b), _p(x), ctypes.byref(info))
+    return x, info.as_dict()
+
+
+def setup(params: Params, U, V0, init_relax: int, n_iter: int, group_size: int = 4):
+    """Adaptive setup from random starts V0 (Nv,V,4,3): init_relax relaxation steps,
+    then group refinement with n_iter truncated-MG iterations per group.
+    Returns (V, P, A, status)."""
+    U = _c(U)
+    Vv = _c(V0).copy()
+    nv = Vv.shape[0]
+    assert nv == params.nv
+    Lc = coarse_dims(list(params.L), list(params.B))
+    P = np.empty_like(Vv)
+    A = np.empty((volume(Lc), 9, 2 * nv, 2 * nv), dtype=np.complex128)
+    st = _load().or_setup(ctypes.byref(params), _p(U), _p(Vv), int(init_relax), int(n_iter),
+                         int(group_size), _p(P), _p(A))
+    return Vv, P, A, st

@@ -1,0 +1,746 @@
+/*
+ * CPU oracle for the adaptive multigrid Wilson-Dirac solver of Babich et al.,
+ * "Adaptive multigrid algorithm for the lattice Wilson-Dirac operator"
+ * (arXiv:1005.3043).  TEST INFRASTRUCTURE ONLY: it is called by tests/, by the
+ * package's smoke check and by the benchmark's CPU-baseline leg, never by the
+ * product path.  Plain, slow, FP64 (complex double), written from the paper:
+ * every function names the passage it restates.  It shares no code with the
+ * CUDA library.
+ *
+ * Conventions (the paper is silent on them; the readings are listed with the
+ * design notes):
+ *  - site = x + L0*(y + L1*(z + L2*t)); mu = 0..3 is x, y, z, t.
+ *  - spinor psi[site][spin 4][colour 3]; links U[mu][site][a][b].
+ *  - gamma matrices in the DeGrand-Rossi (chiral) basis, gamma5 = diag(1,1,-1,-1);
+ *    chirality + is spins {0,1}, chirality - is spins {2,3}.
+ *  - periodic in x,y,z; antiperiodic in t when tap != 0 (factor -1 on every hop
+ *    that crosses the t = L3-1 <-> 0 face).
+ *  - aggregates are hypercubic blocks B[4]; coarse site X = (x/B0, ...) with the
+ *    same lexicographic order; coarse dof a = s*Nv + i, s = 0 (+), 1 (-).
+ *  - coarse operator A[X][d][a][b], d = 0 on-site, d = 1+2mu for X+mu, d = 2+2mu
+ *    for X-mu:  (D_c y)[X] = sum_d A[X][d] y[X+d].
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+#define OR_API __attribute__((visibility("default")))
+
+enum { OR_OK = 0, OR_ERR_ARG = -1, OR_ERR_NUMERIC = -5, OR_ERR_NOT_CONVERGED = -4 };
+
+/* ------------------------------------------------------------------ */
+/* Dirac matrices (DeGrand-Rossi basis), gamma[mu][row][col]           */
+/* ------------------------------------------------------------------ */
+static cplx GAMMA[4][4][4];
+static int gamma_ready = 0;
+
+static void init_gamma(void) {
+    if (gamma_ready) return;
+    memset(GAMMA, 0, sizeof(GAMMA));
+    /* gamma_1 (x) */
+    GAMMA[0][0][3] = I;  GAMMA[0][1][2] = I;  GAMMA[0][2][1] = -I; GAMMA[0][3][0] = -I;
+    /* gamma_2 (y) */
+    GAMMA[1][0][3] = -1; GAMMA[1][1][2] = 1;  GAMMA[1][2][1] = 1;  GAMMA[1][3][0] = -1;
+    /* gamma_3 (z) */
+    GAMMA[2][0][2] = I;  GAMMA[2][1][3] = -I; GAMMA[2][2][0] = -I; GAMMA[2][3][1] = I;
+    /* gamma_4 (t) */
+    GAMMA[3][0][2] = 1;  GAMMA[3][1][3] = 1;  GAMMA[3][2][0] = 1;  GAMMA[3][3][1] = 1;
+    gamma_ready = 1;
+}
+
+OR_API void or_gamma_matrices(double* out /* [4][4][4] complex */) {
+    init_gamma();
+    memcpy(out, GAMMA, sizeof(GAMMA));
+}
+
+/* ------------------------------------------------------------------ */
+/* geometry                                                           */
+/* ------------------------------------------------------------------ */
+static int64_t vol(const int* L) { return (int64_t)L[0] * L[1] * L[2] * L[3]; }
+
+static void coords(const int* L, int64_t s, int c[4]) {
+    for (int m = 0; m < 4; ++m) { c[m] = (int)(s % L[m]); s /= L[m]; }
+}
+static int64_t index_of(const int* L, const int c[4]) {
+    return c[0] + (int64_t)L[0] * (c[1] + (int64_t)L[1] * (c[2] + (int64_t)L[2] * c[3]));
+}
+/* neighbour of s in direction mu, dir = +1/-1; *sign = -1 when the hop
+ * crosses the antiperiodic t face */
+static int64_t neighbour(const int* L, int tap, int64_t s, int mu, int dir, double* sign) {
+    int c[4];
+    coords(L, s, c);
+    *sign = 1.0;
+    int n = c[mu] + dir;
+    if (n == L[mu]) { n = 0; if (tap && mu == 3) *sign = -1.0; }
+    if (n < 0) { n = L[mu] - 1; if (tap && mu == 3) *sign = -1.0; }
+    c[mu] = n;
+    return index_of(L, c);
+}
+
+/* ------------------------------------------------------------------ */
+/* The 12x12 (spin x colour) blocks of eq. (2).                        */
+/*   D_{x,y} = (4+m) delta_{x,y}                                      */
+/*     - sum_mu [ (1-gamma_mu)/2 U^mu_x delta_{x+mu,y}                 */
+/*              + (1+gamma_mu)/2 U^{mu dag}_{x-mu} delta_{x-mu,y} ]     */
+/* hop_block(.., dir=+1) is the block multiplying psi(x+mu),           */
+/* hop_block(.., dir=-1) the block multiplying psi(x-mu).               */
+/* ------------------------------------------------------------------ */
+static void hop_block(const int* L, int tap, const cplx* U, int64_t x, int mu, int dir,
+                      cplx H[12][12], int64_t* y_out) {
+    init_gamma();
+    int64_t V = vol(L);
+    double sign;
+    int64_t y = neighbour(L, tap, x, mu, dir, &sign);
+    cplx W[3][3];                                     /* colour part */
+    if (dir > 0) {
+        const cplx* u = U + 9 * (mu * V + x);           /* U^mu_x */
+        for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) W[a][b] = u[3 * a + b];
+    } else {
+        const cplx* u = U + 9 * (mu * V + y);           /* U^mu_{x-mu}, daggered */
+        for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) W[a][b] = conj(u[3 * b + a]);
+    }
+    for (int al = 0; al < 4; ++al)
+        for (int be = 0; be < 4; ++be) {
+            cplx spin = (al == be ? 1.0 : 0.0) - (double)dir * GAMMA[mu][al][be];   /* 1 -/+ gamma */
+            cplx f = -0.5 * sign * spin;
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) H[3 * al + a][3 * be + b] = f * W[a][b];
+        }
+    *y_out = y;
+}
+
+/* eq. (2): out = D(U) in */
+OR_API void or_dslash(const int* L, int tap, const double* Ur, double m, const double* inr, double* outr) {
+    const cplx* U = (const cplx*)Ur;
+    const cplx* in = (const cplx*)inr;
+    cplx* out = (cplx*)outr;
+    int64_t V = vol(L);
+    init_gamma();
+#pragma omp parallel for schedule(static)
+    for (int64_t x = 0; x < V; ++x) {
+        cplx acc[12];
+        for (int k = 0; k < 12; ++k) acc[k] = (4.0 + m) * in[12 * x + k];
+        for (int mu = 0; mu < 4; ++mu)
+            for (int dir = 1; dir >= -1; dir -= 2) {
+                cplx H[12][12];
+                int64_t y;
+                hop_block(L, tap, U, x, mu, dir, H, &y);
+                for (int k = 0; k < 12; ++k) {
+                    cplx s = 0;
+                    for (int l = 0; l < 12; ++l) s += H[k][l] * in[12 * y + l];
+                    acc[k] += s;
+                }
+            }
+        for (int k = 0; k < 12; ++k) out[12 * x + k] = acc[k];
+    }
+}
+
+/* gamma5 = gamma1 gamma2 gamma3 gamma4 = diag(1,1,-1,-1) in this basis (checked in tests) */
+OR_API void or_gamma5(int64_t V, const double* inr, double* outr) {
+    const cplx* in = (const cplx*)inr;
+    cplx* out = (cplx*)outr;
+    for (int64_t x = 0; x < V; ++x)
+        for (int sp = 0; sp < 4; ++sp)
+            for (int c = 0; c < 3; ++c)
+                out[12 * x + 3 * sp + c] = (sp < 2 ? 1.0 : -1.0) * in[12 * x + 3 * sp + c];
+}
+
+/* ------------------------------------------------------------------ */
+/* vector helpers (fixed serial summation order)                       */
+/* ------------------------------------------------------------------ */
+static cplx vdot(int64_t n, const cplx* a, const cplx* b) {         /* a^dag b */
+    cplx s = 0;
+    for (int64_t i = 0; i < n; ++i) s += conj(a[i]) * b[i];
+    return s;
+}
+static double vnorm2(int64_t n, const cplx* a) {
+    double s = 0;
+    for (int64_t i = 0; i < n; ++i) s += creal(a[i]) * creal(a[i]) + cimag(a[i]) * cimag(a[i]);
+    return s;
+}
+static void vaxpy(int64_t n, cplx a, const cplx* x, cplx* y) {      /* y += a x */
+    for (int64_t i = 0; i < n; ++i) y[i] += a * x[i];
+}
+
+OR_API void or_dot(int64_t n, const double* a, const double* b, double* out2) {
+    cplx s = vdot(n, (const cplx*)a, (const cplx*)b);
+    out2[0] = creal(s); out2[1] = cimag(s);
+}
+
+/* ------------------------------------------------------------------ */
+/* aggregates (geometric blocks), Sec. "Formulating an algorithm"      */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int L[4], B[4], Lc[4];
+    int64_t V, Vc;
+    int nv, nc;
+} blocking_t;
+
+static int blocking_init(blocking_t* bk, const int* L, const int* B, int nv) {
+    for (int m = 0; m < 4; ++m) {
+        if (B[m] <= 0 || L[m] % B[m] != 0) return OR_ERR_ARG;
+        bk->L[m] = L[m]; bk->B[m] = B[m]; bk->Lc[m] = L[m] / B[m];
+    }
+    bk->V = vol(L); bk->Vc = vol(bk->Lc); bk->nv = nv; bk->nc = 2 * nv;
+    return OR_OK;
+}
+static int64_t block_of(const blocking_t* bk, int64_t x) {
+    int c[4];
+    coords(bk->L, x, c);
+    for (int m = 0; m < 4; ++m) c[m] /= bk->B[m];
+    return index_of(bk->Lc, c);
+}
+/* list of fine sites of each block, in increasing site order: sites[X*Vb + k] */
+static int64_t* block_sites(const blocking_t* bk) {
+    int64_t Vb = bk->V / bk->Vc;
+    int64_t* sites = (int64_t*)malloc(sizeof(int64_t) * bk->V);
+    int64_t* fill = (int64_t*)calloc(bk->Vc, sizeof(int64_t));
+    for (int64_t x = 0; x < bk->V; ++x) {
+        int64_t X = block_of(bk, x);
+        sites[X * Vb + fill[X]++] = x;
+    }
+    free(fill);
+    return sites;
+}
+
+/*
+ * Block orthonormalisation, eq. (4) and the chirality split of Sec. III:
+ * for every aggregate X and chirality s, the columns w_i = (v_i restricted to X
+ * and to the spins of chirality s), i = 0..Nv-1, are orthonormalised by
+ * modified Gram-Schmidt (two passes, index order).  The result is the Q of a
+ * QR factorisation with positive real diag(R), so P^dag P = I_c and
+ * P V_c = V.  Output P[i][site][spin][colour] holds column (X, s, i) on the
+ * sites of X and spins of chirality s.  Returns OR_ERR_NUMERIC when a column's
+ * norm drops below 1e-12 of its original norm (rank deficiency).
+ */
+OR_API int or_block_orthonormalize(const int* L, const int* B, int nv, const double* vr, double* Pr) {
+    blocking_t bk;
+    if (blocking_init(&bk, L, B, nv) != OR_OK || nv <= 0) return OR_ERR_ARG;
+    const cplx* v = (const cplx*)vr;
+    cplx* P = (cplx*)Pr;
+    int64_t Vb = bk.V / bk.Vc;
+    int64_t len = Vb * 6;                               /* sites x 2 spins x 3 colours */
+    int64_t* sites = block_sites(&bk);
+    int status = OR_OK;
+    cplx* W = (cplx*)malloc(sizeof(cplx) * len * nv);
+    double* orig = (double*)malloc(sizeof(double) * nv);
+    for (int64_t X = 0; X < bk.Vc; ++X)
+        for (int s = 0; s < 2; ++s) {
+            for (int i = 0; i < nv; ++i)                /* gather */
+                for (int64_t k = 0; k < Vb; ++k)
+                    for (int sp = 0; sp < 2; ++sp)
+                        for (int c = 0; c < 3; ++c)
+                            W[i * len + 6 * k + 3 * sp + c] =
+                                v[(int64_t)i * bk.V * 12 + 12 * sites[X * Vb + k] + 3 * (2 * s + sp) + c];
+            for (int i = 0; i < nv; ++i) {
+                cplx* wi = W + i * len;
+                orig[i] = sqrt(vnorm2(len, wi));
+                for (int pass = 0; pass < 2; ++pass)
+                    for (int j = 0; j < i; ++j) {
+                        cplx* qj = W + j * len;
+                        cplx c = vdot(len, qj, wi);
+                        vaxpy(len, -c, qj, wi);
+                    }
+                double n = sqrt(vnorm2(len, wi));
+                if (!(n > 1e-12 * orig[i])) { status = OR_ERR_NUMERIC; n = 1.0; }
+                for (int64_t k = 0; k < len; ++k) wi[k] /= n;
+            }
+            for (int i = 0; i < nv; ++i)                /* scatter */
+                for (int64_t k = 0; k < Vb; ++k)
+                    for (int sp = 0; sp < 2; ++sp)
+                        for (int c = 0; c < 3; ++c)
+                            P[(int64_t)i * bk.V * 12 + 12 * sites[X * Vb + k] + 3 * (2 * s + sp) + c] =
+                                W[i * len + 6 * k + 3 * sp + c];
+        }
+    free(W); free(orig); free(sites);
+    return status;
+}
+
+/* Restriction r_c = P^dag r (eq. 8 with R = P^dag, chirality kept):
+ * r_c[X][s*Nv+i] = sum over x in X, spins of chirality s, colours of conj(P_i(x)) r(x). */
+OR_API int or_restrict(const int* L, const int* B, int nv, const double* Pr, const double* rr, double* rcr) {
+    blocking_t bk;
+    if (blocking_init(&bk, L, B, nv) != OR_OK) return OR_ERR_ARG;
+    const cplx* P = (const cplx*)Pr;
+    const cplx* r = (const cplx*)rr;
+    cplx* rc = (cplx*)rcr;
+    int64_t Vb = bk.V / bk.Vc;
+    int64_t* sites = block_sites(&bk);
+#pragma omp parallel for schedule(static)
+    for (int64_t X = 0; X < bk.Vc; ++X)
+        for (int s = 0; s < 2; ++s)
+            for (int i = 0; i < nv; ++i) {
+                cplx acc = 0;
+                for (int64_t k = 0; k < Vb; ++k) {
+                    int64_t x = sites[X * Vb + k];
+                    for (int sp = 2 * s; sp < 2 * s + 2; ++sp)
+                        for (int c = 0; c < 3; ++c)
+                            acc += conj(P[(int64_t)i * bk.V * 12 + 12 * x + 3 * sp + c]) * r[12 * x + 3 * sp + c];
+                }
+                rc[X * bk.nc + s * nv + i] = acc;
+            }
+    free(sites);
+    return OR_OK;
+}
+
+/* Prolongation e = P y: e(x, spin, c) = sum_i P_i(x, spin, c) y[X(x)][s(spin)*Nv + i]. */
+OR_API int or_prolong(const int* L, const int* B, int nv, const double* Pr, const double* ycr, double* er) {
+    blocking_t bk;
+    if (blocking_init(&bk, L, B, nv) != OR_OK) return OR_ERR_ARG;
+    const cplx* P = (const cplx*)Pr;
+    const cplx* yc = (const cplx*)ycr;
+    cplx* e = (cplx*)er;
+#pragma omp parallel for schedule(static)
+    for (int64_t x = 0; x < bk.V; ++x) {
+        int64_t X = block_of(&bk, x);
+        for (int sp = 0; sp < 4; ++sp) {
+            int s = sp < 2 ? 0 : 1;
+            for (int c = 0; c < 3; ++c) {
+                cplx acc = 0;
+                for (int i = 0; i < nv; ++i)
+                    acc += P[(int64_t)i * bk.V * 12 + 12 * x + 3 * sp + c] * yc[X * bk.nc + s * nv + i];
+                e[12 * x + 3 * sp + c] = acc;
+            }
+        }
+    }
+    return OR_OK;
+}
+
+/*
+ * Galerkin coarse operator D_c = P^dag D P (Sec. II, "A_c = P^dag A P"; its
+ * nearest-neighbour form with 2Nv x 2Nv links, Sec. III):
+ *   A[X][d][a][b] = sum_{x in X} sum_y conj(P_a(x)) D^{(d)}_{x,y} P_b(y)
+ * where D^{(0)} is the diagonal term of eq. (2) plus every hop that stays
+ * inside X, and D^{(+mu)} / D^{(-mu)} are the hops that leave X through its
+ * +mu / -mu face.  Keeping the face of exit (rather than the target block)
+ * makes the 9-term sum exact even when the coarse extent is 1 or 2.
+ */
+OR_API int or_coarse_build(const int* L, const int* B, int nv, int tap, const double* Ur, double m,
+                           const double* Pr, double* Ar) {
+    blocking_t bk;
+    if (blocking_init(&bk, L, B, nv) != OR_OK) return OR_ERR_ARG;
+    const cplx* U = (const cplx*)Ur;
+    const cplx* P = (const cplx*)Pr;
+    cplx* A = (cplx*)Ar;
+    int nc = bk.nc;
+    int64_t Vb = bk.V / bk.Vc;
+    int64_t* sites = block_sites(&bk);
+    memset(A, 0, sizeof(cplx) * bk.Vc * 9 * nc * nc);
+#pragma omp parallel
+    {
+        cplx* HP = (cplx*)malloc(sizeof(cplx) * 12 * nc);
+#pragma omp for schedule(static)
+        for (int64_t X = 0; X < bk.Vc; ++X)
+            for (int64_t k = 0; k < Vb; ++k) {
+                int64_t x = sites[X * Vb + k];
+                int cx[4];
+                coords(L, x, cx);
+                for (int term = 0; term < 9; ++term) {
+                    cplx H[12][12];
+                    int64_t y;
+                    int d;
+                    if (term == 0) {
+                        memset(H, 0, sizeof(H));
+                        for (int q = 0; q < 12; ++q) H[q][q] = 4.0 + m;
+                        y = x;
+                        d = 0;
+                    } else {
+                        int mu = (term - 1) / 2, dir = (term % 2 == 1) ? 1 : -1;
+                        hop_block(L, tap, U, x, mu, dir, H, &y);
+                        int leaves = (dir > 0) ? (cx[mu] % B[mu] == B[mu] - 1) : (cx[mu] % B[mu] == 0);
+                        d = leaves ? term : 0;
+                    }
+                    /* HP[q][b] = (H P_b)(x) restricted to row q; P_b(y) is column b at site y */
+                    for (int q = 0; q < 12; ++q)
+                        for (int b = 0; b < nc; ++b) {
+                            int sb = b / nv, ib = b % nv;
+                            cplx acc = 0;
+                            for (int sp = 2 * sb; sp < 2 * sb + 2; ++sp)
+                                for (int c = 0; c < 3; ++c)
+                                    acc += H[q][3 * sp + c] * P[(int64_t)ib * bk.V * 12 + 12 * y + 3 * sp + c];
+                            HP[q * nc + b] = acc;
+                        }
+                    cplx* Ad = A + (X * 9 + d) * nc * nc;
+                    for (int a = 0; a < nc; ++a) {
+                        int sa = a / nv, ia = a % nv;
+                        for (int b = 0; b < nc; ++b) {
+                            cplx acc = 0;
+                            for (int sp = 2 * sa; sp < 2 * sa + 2; ++sp)
+                                for (int c = 0; c < 3; ++c)
+                                    acc += conj(P[(int64_t)ia * bk.V * 12 + 12 * x + 3 * sp + c]) * HP[(3 * sp + c) * nc + b];
+                            Ad[a * nc + b] += acc;
+                        }
+                    }
+                }
+            }
+        free(HP);
+    }
+    free(sites);
+    return OR_OK;
+}
+
+/* neighbour of coarse site X for stencil slot d (0 = X itself) */
+static int64_t coarse_neighbour(const int* Lc, int64_t X, int d) {
+    if (d == 0) return X;
+    int mu = (d - 1) / 2, dir = (d % 2 == 1) ? 1 : -1;
+    int c[4];
+    coords(Lc, X, c);
+    c[mu] = (c[mu] + dir + Lc[mu]) % Lc[mu];
+    return index_of(Lc, c);
+}
+
+/* y = D_c x : y[X] = sum_d A[X][d] x[X+d] */
+OR_API void or_coarse_apply(const int* Lc, int nc, const double* Ar, const double* xr, double* yr) {
+    const cplx* A = (const cplx*)Ar;
+    const cplx* x = (const cplx*)xr;
+    cplx* y = (cplx*)yr;
+    int64_t Vc = vol(Lc);
+#pragma omp parallel for schedule(static)
+    for (int64_t X = 0; X < Vc; ++X) {
+        for (int a = 0; a < nc; ++a) {
+            cplx acc = 0;
+            for (int d = 0; d < 9; ++d) {
+                int64_t Y = coarse_neighbour(Lc, X, d);
+                const cplx* Ad = A + (X * 9 + d) * nc * nc;
+                for (int b = 0; b < nc; ++b) acc += Ad[a * nc + b] * x[Y * nc + b];
+            }
+            y[X * nc + a] = acc;
+        }
+    }
+}
+
+/* sigma3 on coarse vectors: +1 on the first Nv dof of a site, -1 on the last Nv */
+static void sigma3(int64_t Vc, int nc, const cplx* x, cplx* y) {
+    for (int64_t X = 0; X < Vc; ++X)
+        for (int a = 0; a < nc; ++a) y[X * nc + a] = (a < nc / 2 ? 1.0 : -1.0) * x[X * nc + a];
+}
+
+/* y = D_c^dag x = sigma3 D_c sigma3 x, from P^dag gamma5 = sigma3 P^dag (Sec. III) */
+OR_API void or_coarse_apply_dag(const int* Lc, int nc, const double* Ar, const double* xr, double* yr) {
+    int64_t Vc = vol(Lc);
+    cplx* t = (cplx*)malloc(sizeof(cplx) * Vc * nc);
+    sigma3(Vc, nc, (const cplx*)xr, t);
+    or_coarse_apply(Lc, nc, Ar, (const double*)t, yr);
+    sigma3(Vc, nc, (const cplx*)yr, (cplx*)yr);
+    free(t);
+}
+
+/* ------------------------------------------------------------------ */
+/* solver parameters and the multigrid state                          */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int L[4];
+    int B[4];
+    int nv;
+    int tap;
+    double m;
+    int mr_steps;        /* post-smoothing steps, V(0, mr_steps) */
+    double omega;        /* under-relaxation of the smoother */
+    double coarse_tol;   /* relative residual of the coarse normal-equation CG */
+    int coarse_maxit;
+    int gcr_restart;
+    double tol;          /* outer relative true residual */
+    int max_outer;
+    int use_mg;          /* 0: unpreconditioned GCR (M = I) */
+} or_params;
+
+typedef struct {
+    int outer_iters;
+    int coarse_iters;
+    int fine_matvecs;
+    int restarts;
+    double true_rel_res;
+    int status;
+} or_info;
+
+typedef struct {
+    const or_params* p;
+    blocking_t bk;
+    const cplx* U;
+    const cplx* P;
+    const cplx* A;
+    or_info* info;
+} mg_t;
+
+static void D_apply(const mg_t* g, const cplx* in, cplx* out) {
+    or_dslash(g->p->L, g->p->tap, (const double*)g->U, g->p->m, (const double*)in, (double*)out);
+    if (g->info) g->info->fine_matvecs++;
+}
+
+/*
+ * Minimal-residual relaxation with under-relaxation omega (the smoother of
+ * Sec. III, GMRES with omega = 0.9, in its one-vector restarted form):
+ *   repeat n times: q = D r; alpha = omega <q,r>/<q,q>; e += alpha r; r -= alpha q
+ * e and r are updated in place.
+ */
+OR_API void or_mr(const int* L, int tap, const double* Ur, double m, int nsteps, double omega,
+                  double* er, double* rr) {
+    int64_t n = vol(L) * 12;
+    cplx* e = (cplx*)er;
+    cplx* r = (cplx*)rr;
+    cplx* q = (cplx*)malloc(sizeof(cplx) * n);
+    for (int k = 0; k < nsteps; ++k) {
+        or_dslash(L, tap, Ur, m, (const double*)r, (double*)q);
+        cplx qr = vdot(n, q, r);
+        double qq = vnorm2(n, q);
+        if (!(qq > 0)) break;
+        cplx alpha = omega * qr / qq;
+        vaxpy(n, alpha, r, e);
+        vaxpy(n, -alpha, q, r);
+    }
+    free(q);
+}
+
+static void mr_internal(const mg_t* g, int nsteps, cplx* e, cplx* r) {
+    int64_t n = g->bk.V * 12;
+    cplx* q = (cplx*)malloc(sizeof(cplx) * n);
+    for (int k = 0; k < nsteps; ++k) {
+        D_apply(g, r, q);
+        cplx qr = vdot(n, q, r);
+        double qq = vnorm2(n, q);
+        if (!(qq > 0)) break;
+        cplx alpha = g->p->omega * qr / qq;
+        vaxpy(n, alpha, r, e);
+        vaxpy(n, -alpha, q, r);
+    }
+    free(q);
+}
+
+/*
+ * Coarsest-grid solve: conjugate gradients on the normal equations
+ * (D_c^dag D_c y = D_c^dag r_c), CGLS form, from y = 0, stopping when the
+ * residual of the original system ||r_c - D_c y|| <= tol ||r_c|| (Sec. IV:
+ * "CG on the normal equations to a relative accuracy of 1e-3") or after maxit
+ * iterations.  tol = 0 runs exactly maxit iterations.  Returns the count.
+ */
+OR_API int or_cgnr(const int* Lc, int nc, const double* Ar, const double* rcr, double* yr,
+                   double tol, int maxit, double* final_rel) {
+    int64_t Vc = vol(Lc);
+    int64_t n = Vc * nc;
+    const cplx* rc = (const cplx*)rcr;
+    cplx* y = (cplx*)yr;
+    cplx* r = (cplx*)malloc(sizeof(cplx) * n);
+    cplx* s = (cplx*)malloc(sizeof(cplx) * n);
+    cplx* p = (cplx*)malloc(sizeof(cplx) * n);
+    cplx* q = (cplx*)malloc(sizeof(cplx) * n);
+    memset(y, 0, sizeof(cplx) * n);
+    memcpy(r, rc, sizeof(cplx) * n);
+    double rc_norm = sqrt(vnorm2(n, rc));
+    or_coarse_apply_dag(Lc, nc, Ar, (const double*)r, (double*)s);
+    memcpy(p, s, sizeof(cplx) * n);
+    double gamma = vnorm2(n, s);
+    int it = 0;
+    double rel = rc_norm > 0 ? 1.0 : 0.0;
+    if (rc_norm > 0) {
+        while (it < maxit) {
+            or_coarse_apply(Lc, nc, Ar, (const double*)p, (double*)q);
+            double qq = vnorm2(n, q);
+            if (!(qq > 0)) break;
+            double alpha = gamma / qq;
+            vaxpy(n, alpha, p, y);
+            vaxpy(n, -alpha, q, r);
+            ++it;
+            rel = sqrt(vnorm2(n, r)) / rc_norm;
+            if (rel <= tol) break;
+            or_coarse_apply_dag(Lc, nc, Ar, (const double*)r, (double*)s);
+            double gnew = vnorm2(n, s);
+            double beta = gnew / gamma;
+            gamma = gnew;
+            for (int64_t i = 0; i < n; ++i) p[i] = s[i] + beta * p[i];
+        }
+    }
+    if (final_rel) *final_rel = rel;
+    free(r); free(s); free(p); free(q);
+    return it;
+}
+
+/*
+ * Two-level V(0, n) cycle used as the preconditioner M (Sec. II-III):
+ *   r_c = P^dag r;  y = CGNR(D_c, r_c);  e = P y;  r' = r - D e;
+ *   n MR steps on (e, r');  return z = e.
+ * (Coarse-grid correction eq. (8) with R = P^dag, then post-relaxation only.)
+ */
+static void vcycle(const mg_t* g, const cplx* r_in, cplx* z) {
+    int64_t n = g->bk.V * 12, nC = g->bk.Vc * g->bk.nc;
+    const or_params* p = g->p;
+    cplx* rc = (cplx*)malloc(sizeof(cplx) * nC);
+    cplx* yc = (cplx*)malloc(sizeof(cplx) * nC);
+    cplx* r = (cplx*)malloc(sizeof(cplx) * n);
+    cplx* De = (cplx*)malloc(sizeof(cplx) * n);
+    or_restrict(p->L, p->B, p->nv, (const double*)g->P, (const double*)r_in, (double*)rc);
+    int it = or_cgnr(g->bk.Lc, g->bk.nc, (const double*)g->A, (const double*)rc, (double*)yc,
+                     p->coarse_tol, p->coarse_maxit, NULL);
+    if (g->info) g->info->coarse_iters += it;
+    or_prolong(p->L, p->B, p->nv, (const double*)g->P, (const double*)yc, (double*)z);
+    D_apply(g, z, De);
+    for (int64_t i = 0; i < n; ++i) r[i] = r_in[i] - De[i];
+    mr_internal(g, p->mr_steps, z, r);
+    free(rc); free(yc); free(r); free(De);
+}
+
+OR_API void or_vcycle(const or_params* p, const double* U, const double* P, const double* A,
+                      const double* r, double* z, or_info* info) {
+    mg_t g;
+    blocking_init(&g.bk, p->L, p->B, p->nv);
+    g.p = p; g.U = (const cplx*)U; g.P = (const cplx*)P; g.A = (const cplx*)A; g.info = info;
+    vcycle(&g, (const cplx*)r, (cplx*)z);
+}
+
+/*
+ * Flexible GCR(k) preconditioned by the multigrid cycle (Sec. III: "GCR(8)";
+ * the restart length k is a parameter).  x starts at 0.  Per iteration:
+ *   z_k = M r;  p_k = D z_k;  p_k -= sum_{j<k} <p_j,p_k> p_j (one classical
+ *   Gram-Schmidt pass);  R_kk = ||p_k||, p_k /= R_kk;  c_k = <p_k, r>;
+ *   r -= c_k p_k.
+ * At a restart (k iterations) or when ||r|| <= tol ||b||: solve R y = c
+ * (upper triangular), x += sum_k y_k z_k, r = b - D x (true residual).
+ * Converged when the true relative residual is <= tol.
+ */
+OR_API int or_gcr_solve(const or_params* p, const double* Ur, const double* Pr, const double* Ar,
+                        const double* br, double* xr, or_info* info) {
+    mg_t g;
+    if (p->use_mg) {
+        if (blocking_init(&g.bk, p->L, p->B, p->nv) != OR_OK) return OR_ERR_ARG;
+    } else {
+        memset(&g.bk, 0, sizeof(g.bk));
+        g.bk.V = vol(p->L);
+    }
+    or_info local;
+    memset(&local, 0, sizeof(local));
+    g.p = p; g.U = (const cplx*)Ur; g.P = (const cplx*)Pr; g.A = (const cplx*)Ar; g.info = &local;
+    int64_t n = g.bk.V * 12;
+    int K = p->gcr_restart;
+    const cplx* b = (const cplx*)br;
+    cplx* x = (cplx*)xr;
+    cplx* r = (cplx*)malloc(sizeof(cplx) * n);
+    cplx* Z = (cplx*)malloc(sizeof(cplx) * n * K);
+    cplx* Pk = (cplx*)malloc(sizeof(cplx) * n * K);
+    cplx* R = (cplx*)calloc((size_t)K * K, sizeof(cplx));
+    cplx* c = (cplx*)malloc(sizeof(cplx) * K);
+    cplx* yk = (cplx*)malloc(sizeof(cplx) * K);
+    cplx* t = (cplx*)malloc(sizeof(cplx) * n);
+    memset(x, 0, sizeof(cplx) * n);
+    memcpy(r, b, sizeof(cplx) * n);
+    double bnorm = sqrt(vnorm2(n, b));
+    double rel = bnorm > 0 ? 1.0 : 0.0;
+    int status = OR_ERR_NOT_CONVERGED;
+    if (bnorm == 0) status = OR_OK;
+    while (status == OR_ERR_NOT_CONVERGED && local.outer_iters < p->max_outer) {
+        int k = 0;
+        for (; k < K && local.outer_iters < p->max_outer;) {
+            cplx* zk = Z + (int64_t)k * n;
+            cplx* pk = Pk + (int64_t)k * n;
+            if (p->use_mg) vcycle(&g, r, zk);
+            else memcpy(zk, r, sizeof(cplx) * n);
+            D_apply(&g, zk, pk);
+            for (int j = 0; j < k; ++j) R[j * K + k] = vdot(n, Pk + (int64_t)j * n, pk);
+            for (int j = 0; j < k; ++j) vaxpy(n, -R[j * K + k], Pk + (int64_t)j * n, pk);
+            double nk = sqrt(vnorm2(n, pk));
+            if (!(nk > 0) || !isfinite(nk)) { status = OR_ERR_NUMERIC; break; }
+            R[k * K + k] = nk;
+            for (int64_t i = 0; i < n; ++i) pk[i] /= nk;
+            c[k] = vdot(n, pk, r);
+            vaxpy(n, -c[k], pk, r);
+            ++k;
+            local.outer_iters++;
+            if (sqrt(vnorm2(n, r)) <= p->tol * bnorm) break;
+        }
+        if (status == OR_ERR_NUMERIC) break;
+        for (int i = k - 1; i >= 0; --i) {                 /* back substitution R y = c */
+            cplx s = c[i];
+            for (int j = i + 1; j < k; ++j) s -= R[i * K + j] * yk[j];
+            yk[i] = s / R[i * K + i];
+        }
+        for (int i = 0; i < k; ++i) vaxpy(n, yk[i], Z + (int64_t)i * n, x);
+        D_apply(&g, x, t);                                  /* true residual */
+        for (int64_t i = 0; i < n; ++i) r[i] = b[i] - t[i];
+        local.restarts++;
+        rel = sqrt(vnorm2(n, r)) / bnorm;
+        if (!isfinite(rel)) { status = OR_ERR_NUMERIC; break; }
+        if (rel <= p->tol) status = OR_OK;
+    }
+    local.true_rel_res = rel;
+    local.status = status;
+    if (info) *info = local;
+    free(r); free(Z); free(Pk); free(R); free(c); free(yk); free(t);
+    return status;
+}
+
+/*
+ * Adaptive setup (Sec. II, the alpha-SA loop, in the two-step practical form
+ * of Sec. IV):
+ *  (i)   start from the given random vectors v_i (i = 0..Nv-1);
+ *  (ii)  relaxation of each on D v = 0: init_relax MR steps with the error
+ *        e = v_i and residual r = -D v_i, then normalise;
+ *  (iii) refinement by groups: the Nv prototypes are split into consecutive
+ *        groups of group_size.  One group at a time is taken out of V; the
+ *        truncated two-level method is built from the remaining prototypes
+ *        (P_t = block-orthonormalised V without the group, D_c,t = P_t^dag D P_t)
+ *        and iterated n_iter times on D x = 0 starting from each prototype of
+ *        the group, v <- (I - M_t D) v (normalised after each iteration); the
+ *        group is then put back.  Groups are processed in order, each seeing
+ *        the already refined earlier groups.
+ *  (iv)  P = block-orthonormalised V, D_c = P^dag D P.
+ * V is overwritten with the final prototypes; P and A receive the final
+ * prolongator and coarse operator.  n_iter = 0 (or group_size >= Nv) skips
+ * step (iii).
+ */
+OR_API int or_setup(const or_params* p, const double* Ur, double* Vr, int init_relax, int n_iter,
+                    int group_size, double* Pr, double* Ar) {
+    blocking_t bk;
+    if (blocking_init(&bk, p->L, p->B, p->nv) != OR_OK) return OR_ERR_ARG;
+    if (group_size <= 0 || p->nv % group_size != 0) return OR_ERR_ARG;
+    int64_t n = bk.V * 12;
+    int nv = p->nv;
+    cplx* V = (cplx*)Vr;
+    cplx* r = (cplx*)malloc(sizeof(cplx) * n);
+    cplx* z = (cplx*)malloc(sizeof(cplx) * n);
+    int st = OR_OK;
+    for (int i = 0; i < nv; ++i) {
+        cplx* v = V + (int64_t)i * n;
+        or_dslash(p->L, p->tap, Ur, p->m, (const double*)v, (double*)r);
+        for (int64_t k = 0; k < n; ++k) r[k] = -r[k];
+        or_mr(p->L, p->tap, Ur, p->m, init_relax, p->omega, (double*)v, (double*)r);
+        double nrm = sqrt(vnorm2(n, v));
+        for (int64_t k = 0; k < n; ++k) v[k] /= nrm;
+    }
+    int nt = nv - group_size;
+    if (n_iter > 0 && nt > 0) {
+        blocking_t bt;
+        blocking_init(&bt, p->L, p->B, nt);
+        or_params pt = *p;
+        pt.nv = nt;
+        cplx* Vt = (cplx*)malloc(sizeof(cplx) * n * nt);
+        cplx* Pt = (cplx*)malloc(sizeof(cplx) * n * nt);
+        cplx* At = (cplx*)malloc(sizeof(cplx) * bt.Vc * 9 * bt.nc * bt.nc);
+        for (int g0 = 0; g0 < nv && st == OR_OK; g0 += group_size) {
+            int k = 0;
+            for (int i = 0; i < nv; ++i)
+                if (i < g0 || i >= g0 + group_size) memcpy(Vt + (int64_t)(k++) * n, V + (int64_t)i * n, sizeof(cplx) * n);
+            st = or_block_orthonormalize(p->L, p->B, nt, (const double*)Vt, (double*)Pt);
+            if (st != OR_OK) break;
+            or_coarse_build(p->L, p->B, nt, p->tap, Ur, p->m, (const double*)Pt, (double*)At);
+            mg_t g;
+            g.bk = bt; g.p = &pt; g.U = (const cplx*)Ur; g.P = Pt; g.A = At; g.info = NULL;
+            for (int i = g0; i < g0 + group_size; ++i) {
+                cplx* v = V + (int64_t)i * n;
+                for (int it = 0; it < n_iter; ++it) {
+                    D_apply(&g, v, r);                  /* residual of D x = 0 at x = v is -D v */
+                    for (int64_t q = 0; q < n; ++q) r[q] = -r[q];
+                    vcycle(&g, r, z);
+                    for (int64_t q = 0; q < n; ++q) v[q] += z[q];
+                    double nrm = sqrt(vnorm2(n, v));
+                    for (int64_t q = 0; q < n; ++q) v[q] /= nrm;
+                }
+            }
+        }
+        free(Vt); free(Pt); free(At);
+    }
+    if (st == OR_OK) st = or_block_orthonormalize(p->L, p->B, nv, Vr, Pr);
+    if (st == OR_OK) or_coarse_build(p->L, p->B, nv, p->tap, Ur, p->m, Pr, Ar);
+    free(r); free(z);
+    return st;
+}

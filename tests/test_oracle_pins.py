@@ -1,0 +1,410 @@
+"""Pins of the CPU oracle to facts fixed by the paper and by mathematics.
+
+Nothing here compares the oracle with itself: each check is a closed form,
+an identity the paper states, a brute-force dense construction, or an
+independent library routine (numpy QR / LU / lstsq).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests._fields import dense_from_apply, rough_gauge
+
+RTOL64 = 1e-13
+
+
+def rel(a, b):
+    return np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-300)
+
+
+# ---------------------------------------------------------------- gamma basis
+def test_gamma_matrices_clifford_hermitian_chiral():
+    g = oracle.gamma_matrices()
+    for a in range(4):
+        assert np.allclose(g[a], g[a].conj().T, atol=0)
+        for b in range(4):
+            assert np.allclose(g[a] @ g[b] + g[b] @ g[a], 2 * np.eye(4) * (a == b), atol=0)
+    g5 = g[0] @ g[1] @ g[2] @ g[3]
+    # chiral basis: gamma5 diagonal, upper spins (0,1) chirality +1 (Sec. III split)
+    assert np.array_equal(g5, np.diag([1, 1, -1, -1]).astype(complex))
+    psi = synth.gaussian_spinor((2, 2, 2, 2), seed=3)
+    assert np.array_equal(oracle.gamma5(psi), np.einsum("ab,xbc->xac", g5, psi))
+
+
+# ---------------------------------------------------------------- eq. (2)
+def _plane_wave(L, p, u):
+    """psi(x) = exp(i p.x) u with u a 4x3 spin-colour constant."""
+    c = np.stack(np.meshgrid(*[np.arange(l) for l in L], indexing="ij"), -1)  # (L0,L1,L2,L3,4)
+    # site index = x + L0*(y + L1*(z + L2*t)) -> transpose to (t,z,y,x) order for ravel
+    phase = np.exp(1j * (c @ np.asarray(p)))
+    phase = np.transpose(phase, (3, 2, 1, 0)).reshape(-1)
+    return phase[:, None, None] * u[None]
+
+
+@pytest.mark.parametrize("L", [(4, 2, 2, 4), (2, 4, 2, 6)])
+def test_free_field_plane_waves(L):
+    """U = 1: D e^{ipx} u = [m + sum(1-cos p) + i sum gamma_mu sin p_mu] e^{ipx} u,
+    periodic in x,y,z (p = 2 pi n/L) and antiperiodic in t (p4 = (2n+1) pi/Lt)."""
+    g = oracle.gamma_matrices()
+    U = synth.unit_gauge(L)
+    m = 0.137
+    rng = np.random.default_rng(0)
+    for trial in range(6):
+        n = [rng.integers(0, l) for l in L]
+        p = [2 * np.pi * n[0] / L[0], 2 * np.pi * n[1] / L[1], 2 * np.pi * n[2] / L[2],
+             (2 * n[3] + 1) * np.pi / L[3]]
+        u = rng.standard_normal((4, 3)) + 1j * rng.standard_normal((4, 3))
+        Dp = (m + sum(1 - np.cos(q) for q in p)) * np.eye(4) + 1j * sum(g[mu] * np.sin(p[mu]) for mu in range(4))
+        psi = _plane_wave(L, p, u)
+        expect = _plane_wave(L, p, Dp @ u)
+        assert rel(oracle.dslash(U, psi, m, L), expect) < 1e-13
+
+
+def test_free_field_spectrum_closed_form():
+    """Dense eigenvalues on 4x2x2x4: m + sum(1-cos p) +- i sqrt(sum sin^2 p), 6-fold each."""
+    L = (4, 2, 2, 4)
+    V = oracle.volume(L)
+    U = synth.unit_gauge(L)
+    m = 0.1
+    D = dense_from_apply(lambda e: oracle.dslash(U, e.reshape(V, 4, 3), m, L).ravel(), V * 12)
+    ev = np.linalg.eigvals(D)
+    expect = []
+    for n0 in range(L[0]):
+        for n1 in range(L[1]):
+            for n2 in range(L[2]):
+                for n3 in range(L[3]):
+                    p = [2 * np.pi * n0 / L[0], 2 * np.pi * n1 / L[1], 2 * np.pi * n2 / L[2],
+                         (2 * n3 + 1) * np.pi / L[3]]
+                    re = m + sum(1 - np.cos(q) for q in p)
+                    im = np.sqrt(sum(np.sin(q) ** 2 for q in p))
+                    expect += [re + 1j * im] * 6 + [re - 1j * im] * 6
+    a = np.sort_complex(np.round(ev, 8))
+    b = np.sort_complex(np.round(np.array(expect), 8))
+    assert np.abs(a - b).max() < 1e-7
+
+
+def test_gamma5_hermiticity():
+    """D^dag = gamma5 D gamma5 (Sec. I): <x, g5 D g5 y> = <D x, y>."""
+    L = (4, 4, 2, 4)
+    U = rough_gauge(L)
+    m = -0.3
+    x = synth.gaussian_spinor(L, 1)
+    y = synth.gaussian_spinor(L, 2)
+    lhs = np.vdot(x, oracle.gamma5(oracle.dslash(U, oracle.gamma5(y), m, L)))
+    rhs = np.vdot(oracle.dslash(U, x, m, L), y)
+    assert abs(lhs - rhs) / abs(rhs) < RTOL64
+
+
+def test_gamma5_hermiticity_dense():
+    L = (2, 2, 2, 4)
+    V = oracle.volume(L)
+    U = rough_gauge(L)
+    D = dense_from_apply(lambda e: oracle.dslash(U, e.reshape(V, 4, 3), 0.2, L).ravel(), V * 12)
+    G5 = np.kron(np.eye(V), np.kron(np.diag([1, 1, -1, -1]), np.eye(3)))
+    assert np.abs(G5 @ D @ G5 - D.conj().T).max() < 1e-14
+    # eigenvalues come in complex-conjugate pairs (consequence of gamma5-hermiticity)
+    ev = np.linalg.eigvals(D)
+    assert np.abs(np.sort_complex(np.round(ev, 9)) - np.sort_complex(np.round(ev.conj(), 9))).max() < 1e-8
+
+
+def test_gauge_covariance():
+    """D[U^Om](Om psi) = Om D[U] psi with U^Om_mu(x) = Om(x) U_mu(x) Om(x+mu)^dag."""
+    L = (4, 2, 4, 4)
+    V = oracle.volume(L)
+    U = rough_gauge(L)
+    Om = synth.random_gauge_transform(V, seed=99)
+    idx = np.arange(V).reshape(L[3], L[2], L[1], L[0])       # idx[t,z,y,x]
+    Ug = np.empty_like(U)
+    for mu in range(4):
+        ax = 3 - mu
+        fwd = np.roll(idx, -1, axis=ax).reshape(-1)          # site of x + mu
+        Ug[mu] = Om @ U[mu] @ Om[fwd].conj().transpose(0, 2, 1)
+    psi = synth.gaussian_spinor(L, 5)
+    Opsi = np.einsum("xab,xsb->xsa", Om, psi)
+    lhs = oracle.dslash(Ug, Opsi, 0.05, L)
+    rhs = np.einsum("xab,xsb->xsa", Om, oracle.dslash(U, psi, 0.05, L))
+    assert rel(lhs, rhs) < RTOL64
+
+
+def test_mass_shift_is_identity_times_m():
+    L = (2, 4, 2, 4)
+    U = rough_gauge(L)
+    psi = synth.gaussian_spinor(L, 8)
+    d = oracle.dslash(U, psi, 0.7, L) - oracle.dslash(U, psi, 0.0, L)
+    assert rel(d, 0.7 * psi) < 1e-14
+
+
+# ---------------------------------------------------------------- eq. (4), chirality split
+def _setup_small(L=(4, 4, 4, 4), B=(2, 2, 2, 2), nv=3, seed=21):
+    U = rough_gauge(L)
+    V0 = synth.gaussian_vectors(L, nv, seed)
+    P, st = oracle.block_orthonormalize(V0, L, B)
+    assert st == 0
+    return U, V0, P
+
+
+def _dense_P(P, L, B):
+    nv = P.shape[0]
+    Vc = oracle.volume(oracle.coarse_dims(L, B))
+    n = Vc * 2 * nv
+    cols = []
+    for k in range(n):
+        e = np.zeros(n, dtype=np.complex128)
+        e[k] = 1
+        cols.append(oracle.prolong(P, e.reshape(Vc, 2 * nv), L, B).ravel())
+    return np.stack(cols, 1)
+
+
+def test_block_orthonormalisation_invariants():
+    L, B = (4, 4, 4, 4), (2, 2, 2, 2)
+    U, V0, P = _setup_small(L, B)
+    Pd = _dense_P(P, L, B)
+    nc = Pd.shape[1]
+    assert np.abs(Pd.conj().T @ Pd - np.eye(nc)).max() < 1e-13            # P^dag P = I_c
+    for i in range(V0.shape[0]):                                           # P V_c = V
+        v = V0[i].ravel()
+        assert rel(Pd @ (Pd.conj().T @ v), v) < 1e-13
+    V = oracle.volume(L)
+    G5 = np.kron(np.eye(V), np.kron(np.diag([1, 1, -1, -1]), np.eye(3)))
+    S3 = np.kron(np.eye(nc // (2 * V0.shape[0])), np.diag([1] * V0.shape[0] + [-1] * V0.shape[0]))
+    assert np.abs(G5 @ Pd - Pd @ S3).max() == 0                            # gamma5 P = P sigma3
+
+
+def test_block_orthonormalisation_matches_numpy_qr():
+    """Q of a Householder QR (numpy), with diag(R) made real positive, per aggregate
+    and chirality: the Q with positive real R-diagonal is unique."""
+    L, B = (4, 4, 2, 2), (2, 2, 2, 2)
+    nv = 4
+    V0 = synth.gaussian_vectors(L, nv, 77)
+    P, st = oracle.block_orthonormalize(V0, L, B)
+    assert st == 0
+    c = np.stack(np.meshgrid(*[np.arange(l) for l in L], indexing="ij"), -1)
+    c = np.transpose(c, (3, 2, 1, 0, 4)).reshape(-1, 4)
+    Lc = oracle.coarse_dims(L, B)
+    blk = (c // np.asarray(B)) @ np.array([1, Lc[0], Lc[0] * Lc[1], Lc[0] * Lc[1] * Lc[2]])
+    for X in range(oracle.volume(Lc)):
+        sites = np.nonzero(blk == X)[0]
+        for s in range(2):
+            W = V0[:, sites, 2 * s:2 * s + 2, :].reshape(nv, -1).T
+            Q, R = np.linalg.qr(W)
+            ph = np.diag(R) / np.abs(np.diag(R))
+            Q = Q * ph[None, :]
+            got = P[:, sites, 2 * s:2 * s + 2, :].reshape(nv, -1).T
+            assert np.abs(got - Q).max() < 1e-13
+
+
+def test_block_orthonormalisation_rank_deficient_is_numeric_error():
+    L, B = (4, 4, 2, 2), (2, 2, 2, 2)
+    V0 = synth.gaussian_vectors(L, 3, 5)
+    V0[2] = V0[0] * (0.5 - 0.25j)
+    _, st = oracle.block_orthonormalize(V0, L, B)
+    assert st == oracle.ERR_NUMERIC
+
+
+def test_restrict_prolong_adjoint_pair():
+    L, B = (4, 4, 4, 4), (2, 2, 2, 2)
+    U, V0, P = _setup_small(L, B)
+    Lc = oracle.coarse_dims(L, B)
+    r = synth.gaussian_spinor(L, 31)
+    y = synth.gaussian(oracle.volume(Lc) * 6, 32, 0).reshape(-1, 6)
+    assert abs(np.vdot(oracle.restrict(P, r, L, B), y) - np.vdot(r, oracle.prolong(P, y, L, B))) < 1e-12
+    assert rel(oracle.restrict(P, oracle.prolong(P, y, L, B), L, B), y) < 1e-14
+
+
+# ---------------------------------------------------------------- D_c = P^dag D P
+@pytest.mark.parametrize("L,B", [((4, 4, 4, 4), (2, 2, 2, 2)),      # coarse extent 2
+                                 ((4, 4, 4, 4), (4, 4, 4, 4)),      # coarse extent 1
+                                 ((4, 2, 2, 8), (2, 2, 2, 2))])     # coarse extent 4 in t
+def test_coarse_operator_equals_dense_galerkin(L, B):
+    nv = 2
+    U, V0, P = _setup_small(L, B, nv=nv, seed=41)
+    m = -0.25
+    A = oracle.coarse_build(U, P, m, L, B)
+    Lc = oracle.coarse_dims(L, B)
+    V = oracle.volume(L)
+    nC = oracle.volume(Lc) * 2 * nv
+    D = dense_from_apply(lambda e: oracle.dslash(U, e.reshape(V, 4, 3), m, L).ravel(), V * 12)
+    Pd = _dense_P(P, L, B)
+    Dc_dense = Pd.conj().T @ D @ Pd
+    Dc_apply = dense_from_apply(lambda e: oracle.coarse_apply(A, e.reshape(-1, 2 * nv), Lc).ravel(), nC)
+    assert np.abs(Dc_apply - Dc_dense).max() < 1e-13 * np.abs(Dc_dense).max()
+    # sigma3 D_c sigma3 = D_c^dag (from P^dag gamma5 = sigma3 P^dag)
+    S3 = np.kron(np.eye(oracle.volume(Lc)), np.diag([1] * nv + [-1] * nv))
+    assert np.abs(S3 @ Dc_dense @ S3 - Dc_dense.conj().T).max() < 1e-13
+    Dag = dense_from_apply(lambda e: oracle.coarse_apply_dag(A, e.reshape(-1, 2 * nv), Lc).ravel(), nC)
+    assert np.abs(Dag - Dc_dense.conj().T).max() < 1e-13
+    # coarse correction kills the coarse space: (I - P D_c^-1 P^dag D) P = 0 (eqs. 3, 8)
+    E = Pd - Pd @ np.linalg.solve(Dc_dense, Pd.conj().T @ D @ Pd)
+    assert np.abs(E).max() < 1e-11
+
+
+def test_coarse_operator_nearest_neighbour_and_mass_shift():
+    L, B = (8, 4, 4, 4), (2, 2, 2, 2)          # coarse 4x2x2x2: x-neighbours distinct
+    nv = 2
+    U, V0, P = _setup_small(L, B, nv=nv, seed=42)
+    A0 = oracle.coarse_build(U, P, 0.0, L, B)
+    A1 = oracle.coarse_build(U, P, 0.3, L, B)
+    d = A1 - A0
+    assert np.abs(d[:, 1:]).max() == 0
+    assert np.abs(d[:, 0] - 0.3 * np.eye(2 * nv)[None]).max() < 1e-14
+    # coupling of X to X+2x is zero: D_c is nearest neighbour (Sec. III)
+    Lc = oracle.coarse_dims(L, B)
+    nC = oracle.volume(Lc) * 2 * nv
+    Dc = dense_from_apply(lambda e: oracle.coarse_apply(A0, e.reshape(-1, 2 * nv), Lc).ravel(), nC)
+    blk = Dc.reshape(oracle.volume(Lc), 2 * nv, oracle.volume(Lc), 2 * nv)
+    assert np.abs(blk[0, :, 2, :]).max() == 0          # sites (0,..) and (2,..) in x
+
+
+def test_non_split_coarsening_is_singular_in_free_field():
+    """Sec. III: coarsening spins together, the free-field constant prototype gives
+    P^dag gamma5 P = 0; keeping chirality apart gives sigma3 instead."""
+    L, B = (4, 4, 4, 4), (2, 2, 2, 2)
+    V = oracle.volume(L)
+    u = np.zeros((4, 3), complex)
+    u[:, 0] = 1.0                                        # equal weight on both chiralities
+    v = np.broadcast_to(u, (V, 4, 3)).copy()
+    Lc = oracle.coarse_dims(L, B)
+    c = np.stack(np.meshgrid(*[np.arange(l) for l in L], indexing="ij"), -1)
+    c = np.transpose(c, (3, 2, 1, 0, 4)).reshape(-1, 4)
+    blk = (c // np.asarray(B)) @ np.array([1, Lc[0], Lc[0] * Lc[1], Lc[0] * Lc[1] * Lc[2]])
+    nb = oracle.volume(Lc)
+    Pns = np.zeros((V * 12, nb), complex)
+    for X in range(nb):
+        col = np.where((blk == X)[:, None, None], v, 0).ravel()
+        Pns[:, X] = col / np.linalg.norm(col)
+    g5 = oracle.gamma5(np.eye(V * 12).reshape(V * 12, V, 4, 3)[0].reshape(V, 4, 3))  # smoke
+    G5P = np.stack([oracle.gamma5(Pns[:, k].reshape(V, 4, 3)).ravel() for k in range(nb)], 1)
+    assert np.abs(Pns.conj().T @ G5P).max() < 1e-15
+    # the chirality-split prolongator from the same prototype: P^dag g5 P = sigma3
+    P, st = oracle.block_orthonormalize(v[None], L, B)
+    assert st == 0
+    Pd = _dense_P(P, L, B)
+    G5Pd = np.stack([oracle.gamma5(Pd[:, k].reshape(V, 4, 3)).ravel() for k in range(Pd.shape[1])], 1)
+    assert np.abs(Pd.conj().T @ G5Pd - np.kron(np.eye(nb), np.diag([1, -1]))).max() < 1e-14
+    del g5
+
+
+# ---------------------------------------------------------------- smoother, coarse solve, GCR
+def test_mr_step_residual_identity():
+    """One MR step with omega: ||r'||^2 = ||r||^2 - (2w - w^2)|<q,r>|^2/||q||^2, and
+    the pair (e, r) stays consistent: r - r' = D (e' - e)."""
+    L = (4, 4, 2, 4)
+    U = rough_gauge(L)
+    m, w = -0.2, 0.9
+    e = synth.gaussian_spinor(L, 1)
+    r = synth.gaussian_spinor(L, 2)
+    q = oracle.dslash(U, r, m, L)
+    e1, r1 = oracle.mr(U, e, r, m, L, 1, w)
+    pred = np.vdot(r, r).real - (2 * w - w * w) * abs(np.vdot(q, r)) ** 2 / np.vdot(q, q).real
+    assert abs(np.vdot(r1, r1).real - pred) / pred < 1e-13
+    e4, r4 = oracle.mr(U, e, r, m, L, 4, w)
+    assert rel(r - r4, oracle.dslash(U, e4 - e, m, L)) < 1e-13
+    assert np.linalg.norm(r4) < np.linalg.norm(r1) < np.linalg.norm(r)
+
+
+def test_cgnr_reaches_dense_solution():
+    L, B = (4, 4, 4, 4), (2, 2, 2, 2)
+    nv = 2
+    U, V0, P = _setup_small(L, B, nv=nv, seed=43)
+    A = oracle.coarse_build(U, P, 0.1, L, B)
+    Lc = oracle.coarse_dims(L, B)
+    nC = oracle.volume(Lc) * 2 * nv
+    Dc = dense_from_apply(lambda e: oracle.coarse_apply(A, e.reshape(-1, 2 * nv), Lc).ravel(), nC)
+    rc = synth.gaussian(nC, 3, 0).reshape(-1, 2 * nv)
+    y, it, relres = oracle.cgnr(A, rc, Lc, 1e-13, 5000)
+    assert relres <= 1e-13 and it < 5000
+    assert rel(y.ravel(), np.linalg.solve(Dc, rc.ravel())) < 1e-10
+    # tol = 1e-3 stops at the first iterate whose residual is <= 1e-3
+    y3, it3, rel3 = oracle.cgnr(A, rc, Lc, 1e-3, 5000)
+    assert rel3 <= 1e-3
+    _, _, rel_prev = oracle.cgnr(A, rc, Lc, 0.0, it3 - 1)
+    assert rel_prev > 1e-3
+    assert rel(Dc @ y3.ravel(), rc.ravel()) == pytest.approx(rel3, rel=1e-9)
+
+
+def test_gcr_without_preconditioner_equals_gmres():
+    """GCR and GMRES minimise ||b - D x|| over the same Krylov space K_k(D, b)."""
+    L = (2, 2, 2, 4)
+    V = oracle.volume(L)
+    U = rough_gauge(L)
+    m = 0.3
+    b = synth.gaussian_spinor(L, 4)
+    D = dense_from_apply(lambda e: oracle.dslash(U, e.reshape(V, 4, 3), m, L).ravel(), V * 12)
+    for k in (1, 3, 7):
+        p = oracle.make_params(L, nv=1, m=m, gcr_restart=32, tol=0.0, max_outer=k, use_mg=0)
+        x, info = oracle.gcr_solve(p, U, None, None, b)
+        assert info["outer_iters"] == k
+        K = [b.ravel()]
+        for _ in range(k - 1):
+            K.append(D @ K[-1])
+        Q, _ = np.linalg.qr(np.stack(K, 1))
+        c, *_ = np.linalg.lstsq(D @ Q, b.ravel(), rcond=None)
+        gm = np.linalg.norm(b.ravel() - D @ Q @ c)
+        assert abs(np.linalg.norm(b.ravel() - D @ x.ravel()) - gm) / gm < 1e-9
+
+
+def test_vcycle_coarse_part_is_galerkin():
+    """With no smoothing and an exact coarse solve, z = P D_c^-1 P^dag r, so the
+    restricted residual of z vanishes: P^dag (r - D z) = 0 (eq. 8)."""
+    L, B = (4, 4, 4, 4), (2, 2, 2, 2)
+    nv = 2
+    U, V0, P = _setup_small(L, B, nv=nv, seed=44)
+    m = 0.1
+    A = oracle.coarse_build(U, P, m, L, B)
+    p = oracle.make_params(L, B, nv=nv, m=m, mr_steps=0, coarse_tol=1e-14, coarse_maxit=20000)
+    r = synth.gaussian_spinor(L, 9)
+    z, info = oracle.vcycle(p, U, P, A, r)
+    res = oracle.restrict(P, r - oracle.dslash(U, z, m, L), L, B)
+    assert np.linalg.norm(res) / np.linalg.norm(oracle.restrict(P, r, L, B)) < 1e-11
+    # with smoothing the cycle still reduces the residual
+    p4 = oracle.make_params(L, B, nv=nv, m=m, mr_steps=4)
+    z4, _ = oracle.vcycle(p4, U, P, A, r)
+    assert np.linalg.norm(r - oracle.dslash(U, z4, m, L)) < np.linalg.norm(r)
+
+
+def test_mg_gcr_solve_true_residual():
+    L, B = (4, 4, 4, 8), (2, 2, 2, 4)
+    nv = 4
+    U = rough_gauge(L, sweeps=5)
+    m = -0.2
+    p = oracle.make_params(L, B, nv=nv, m=m)
+    V0 = synth.gaussian_vectors(L, nv, 51)
+    Vv, P, A, st = oracle.setup(p, U, V0, init_relax=10, n_iter=1, group_size=2)
+    assert st == 0
+    b = synth.gaussian_spinor(L, 52)
+    x, info = oracle.gcr_solve(p, U, P, A, b)
+    assert info["status"] == 0
+    true = np.linalg.norm(b - oracle.dslash(U, x, m, L)) / np.linalg.norm(b)
+    assert true <= 1e-10
+    assert info["true_rel_res"] == pytest.approx(true, rel=1e-6)
+    # the setup's P and D_c keep the invariants
+    Pd = _dense_P(P, L, B)
+    assert np.abs(Pd.conj().T @ Pd - np.eye(Pd.shape[1])).max() < 1e-12
+    # MG preconditioning beats unpreconditioned GCR on the same system
+    p0 = oracle.make_params(L, B, nv=nv, m=m, use_mg=0, max_outer=3000)
+    x0, info0 = oracle.gcr_solve(p0, U, None, None, b)
+    assert info["outer_iters"] * 3 < info0["outer_iters"]
+
+
+@pytest.mark.slow
+def test_setup_improves_outer_iterations():
+    """The adaptive setup (Sec. II, practical two-step form of Sec. IV) gives a
+    coarse space that cuts outer iterations: random prototypes > relaxed
+    prototypes > relaxed + group-refined prototypes, on the 8^4 beta = 6.0 field
+    at Re(lambda_min) = 0.01."""
+    from tests._fields import c1_workload
+    L, B, nv, U, m = c1_workload()
+    b = synth.gaussian_spinor(L, 7)
+    V0 = synth.gaussian_vectors(L, nv, 2001)
+    p = oracle.make_params(L, B, nv=nv, m=m)
+    Prand, _ = oracle.block_orthonormalize(V0, L, B)
+    _, info_rand = oracle.gcr_solve(p, U, Prand, oracle.coarse_build(U, Prand, m, L, B), b)
+    _, P0, A0, st0 = oracle.setup(p, U, V0, init_relax=10, n_iter=0, group_size=4)
+    _, P5, A5, st5 = oracle.setup(p, U, V0, init_relax=10, n_iter=5, group_size=4)
+    assert st0 == 0 and st5 == 0
+    _, info0 = oracle.gcr_solve(p, U, P0, A0, b)
+    _, info5 = oracle.gcr_solve(p, U, P5, A5, b)
+    for inf in (info_rand, info0, info5):
+        assert inf["status"] == 0 and inf["true_rel_res"] <= 1e-10
+    assert info_rand["outer_iters"] > info0["outer_iters"] > info5["outer_iters"]
