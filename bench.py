@@ -1,0 +1,313 @@
+"""Benchmark: MG-GCR solves per second to a true FP64 relative residual of 1e-10.
+
+One step = the whole job for one gauge field: the adaptive setup at the
+lightest mass (relaxation, group refinement, block orthonormalisation, Galerkin
+coarse operator) followed by one MG-GCR solve at each mass of the sweep, the
+setup being reused across masses.  Inputs (links, random starts, sources) are
+resident on the device before the timed region; the `e2e` figure repeats the
+step through the host-buffer C-ABI calls (links, starts and sources copied in,
+solutions copied out, inside the timed region).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--prec fp32|fp64]
+
+N > 1 (torchrun): every rank solves the same workload on its own GPU
+(replicas: the method has no exchange step on one field); `value` = all
+ranks' solves / max-over-ranks time.  `--impl reference` times the FP64 CPU
+oracle on a bounded sample of the workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1005_3043_gb300.workloads import WORKLOADS  # noqa: E402
+
+DEFAULT_WORKLOAD = "wilson_16x16x16x32_nv20_beta6_5mass"
+METRIC = "MG-GCR solves/sec to 1e-10 true residual"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                f = [x.strip() for x in out.stdout.strip().split(",")]
+                if len(f) >= 7:
+                    self.samples.append(f)
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def make_inputs(w):
+    import synth
+    U = synth.gauge_field(w.dims, beta=w.beta, sweeps=w.sweeps, n_or=w.n_or, seed=w.seed)
+    plaq = synth.plaquette(U, w.dims)
+    if np.isfinite(w.plaquette) and abs(plaq - w.plaquette) > 1e-10:
+        raise RuntimeError(f"gauge field differs from the recorded one: plaquette {plaq!r} vs {w.plaquette!r}")
+    V0 = synth.gaussian_vectors(w.dims, w.nvec, w.setup_seed)
+    masses = w.masses()
+    srcs = np.stack([synth.gaussian_spinor(w.dims, w.source_seed, stream=i) for i in range(len(masses))])
+    return U, V0, srcs, masses, plaq
+
+
+def mg_params(w, prec):
+    import paper_1005_3043_gb300 as wmg
+    p = wmg.mg_default_params()
+    for i in range(4):
+        p.block[i] = w.block[i]
+    p.nvec = w.nvec
+    p.setup_group = 4
+    p.setup_iters = 3
+    p.setup_init_relax = 10
+    p.gcr_restart = 16
+    p.tol = 1e-10
+    p.max_outer = 2000
+    p.prec_inner = wmg.MG_FP32 if prec == "fp32" else wmg.MG_FP64
+    p.delta = 1e-4 if prec == "fp32" else 0.0
+    return p
+
+
+def run_ours(args, w):
+    import torch
+    import paper_1005_3043_gb300 as wmg
+    from paper_1005_3043_gb300 import build as wbuild
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    wbuild.build()
+    wmg.load()
+    U, V0, srcs, masses, plaq = make_inputs(w)
+    stream = torch.cuda.current_stream()
+    p = mg_params(w, args.prec)
+    mg = wmg.WilsonMG(w.dims, p, stream=stream)
+    mg.set_links(U)
+    dV0 = torch.from_numpy(V0.view(np.float64)).cuda()
+    dB = torch.from_numpy(srcs.view(np.float64)).cuda()
+    dX = torch.empty_like(dB)
+    n_solve = len(masses)
+    infos = []
+
+    def step(record):
+        mg.set_mass(w.setup_mass())
+        mg.setup_device(dV0)
+        for i, m in enumerate(masses):
+            mg.set_mass(m)
+            info = mg.solve_device(dB[i], dX[i])
+            if record is not None:
+                record.append(info)
+            if info["status"] != 0:
+                raise RuntimeError(f"solve failed at m={m}: {info}")
+
+    def barrier():
+        if dist:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step(None)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step(infos)
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = world * n_solve * args.steps / (ms / 1e3)
+
+    # solve-only rate, setup time (one more step, phases timed separately)
+    barrier()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(stream)
+    mg.set_mass(w.setup_mass())
+    mg.setup_device(dV0)
+    e1.record(stream)
+    for i, m in enumerate(masses):
+        mg.set_mass(m)
+        mg.solve_device(dB[i], dX[i])
+    e2.record(stream)
+    torch.cuda.synchronize()
+    setup_ms, solves_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
+
+    # end to end through the host-buffer C-ABI (copies inside the timed region)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(max(1, min(args.steps, 2))):
+        mg.set_links(U)
+        mg.set_mass(w.setup_mass())
+        mg.setup(V0)
+        for i, m in enumerate(masses):
+            mg.set_mass(m)
+            x, info = mg.solve(srcs[i])
+    barrier()
+    e2e_steps = max(1, min(args.steps, 2))
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    h2d = U.nbytes + V0.nbytes + srcs.nbytes
+    d2h = srcs.nbytes
+
+    # dominant fine kernel: FP32 dslash timed alone with CUDA events
+    ms_ds, bytes_ds = mg.time_dslash(wmg.MG_FP32 if args.prec == "fp32" else wmg.MG_FP64, 200)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = bytes_ds / (ms_ds * 1e-3) / 1e9
+    mg.close()
+
+    if rank == 0:
+        iters = [i["outer_iters"] for i in infos[:n_solve]]
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if args.prec == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": w.name, "lattice": "x".join(map(str, w.dims)), "nvec": w.nvec,
+                       "block": "x".join(map(str, w.block)), "masses": masses, "solves_per_step": n_solve,
+                       "setup_in_step": True, "l2": "working set > L2 (129 MB)", "parallelism": f"replicas{world}",
+                       "plaquette": plaq, "prec_inner": args.prec},
+            "outer_iters": iters, "true_rel_res": [i["true_rel_res"] for i in infos[:n_solve]],
+            "setup_ms": setup_ms, "solves_ms": solves_ms, "solve_only_per_s": n_solve / (solves_ms / 1e3),
+            "e2e": {"value": n_solve / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "kernel": "k_dslash (timed alone)", "peak_source": "measured"},
+            "clocks": clk.summary(),
+            "gpu_launches": None,
+        }
+        if not args.no_baseline:
+            line["cpu_baseline"] = cpu_baseline(w, U, srcs, masses, V0)
+        print(json.dumps(line), flush=True)
+    if dist:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline(w, U, srcs, masses, V0, budget_s=20.0):
+    """The FP64 CPU oracle on a bounded sample: the setup and one solve at the
+    heaviest mass (the whole step if it fits the budget)."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count()
+    p = oracle.make_params(w.dims, w.block, nv=w.nvec, m=w.setup_mass())
+    t0 = time.perf_counter()
+    _, P, A, st = oracle.setup(p, U, V0, init_relax=10, n_iter=3, group_size=4)
+    t_setup = time.perf_counter() - t0
+    solved, t_solve = 0, 0.0
+    for i, m in enumerate(masses):
+        if t_setup + t_solve > budget_s and solved > 0:
+            break
+        A_m = A.copy()
+        A_m[:, 0] += (m - w.setup_mass()) * np.eye(2 * w.nvec)[None]
+        pm = oracle.make_params(w.dims, w.block, nv=w.nvec, m=m)
+        t1 = time.perf_counter()
+        _, info = oracle.gcr_solve(pm, U, P, A_m, srcs[i])
+        t_solve += time.perf_counter() - t1
+        solved += 1
+    per_solve = t_solve / solved
+    step_s = t_setup + per_solve * len(masses)
+    return {"value": len(masses) / step_s, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"setup + {solved} of {len(masses)} solves timed; step = setup + {len(masses)} x mean solve"}
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    U, V0, srcs, masses, plaq = make_inputs(w)
+    t0 = time.perf_counter()
+    cb = None
+    for _ in range(max(1, args.steps)):
+        cb = cpu_baseline(w, U, srcs, masses, V0, budget_s=10.0)
+    dt = time.perf_counter() - t0
+    line = {"metric": METRIC, "value": cb["value"], "unit": "solves/s", "n_gpus": 0, "steps": args.steps,
+            "warmup": 0, "ms_per_step": 1e3 * dt / max(1, args.steps), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": w.name, "lattice": "x".join(map(str, w.dims)), "nvec": w.nvec},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    w = WORKLOADS[args.workload]
+    if not np.isfinite(w.re_lambda_min_m0):
+        raise SystemExit(f"workload {w.name} has no recorded mass yet")
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

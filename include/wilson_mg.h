@@ -115,6 +115,9 @@ int mg_set_params(mg_ctx* ctx, const mg_params* p);
  * (eq. 4) and the Galerkin coarse operator D_c = P^dag D P. */
 int mg_setup(mg_ctx* ctx, const double* V0);
 
+/* As mg_setup with the random starts in device memory (boundary layout, FP64). */
+int mg_setup_device(mg_ctx* ctx, const double* V0_dev);
+
 /* Use the given prototypes (host, nv == p->nvec fine vectors) as they are:
  * block-orthonormalise them (eq. 4) and build D_c = P^dag D P. */
 int mg_set_null_vectors(mg_ctx* ctx, const double* V, int nv);

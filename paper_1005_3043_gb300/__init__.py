@@ -1,0 +1,374 @@
+"""GB300-native adaptive multigrid solver for the lattice Wilson-Dirac equation
+D(U) psi = b (Babich et al., arXiv:1005.3043).
+
+This module is a thin ctypes binding of the C-ABI in ``include/wilson_mg.h``:
+the functions keep the C names and only marshal arguments (numpy arrays for
+host buffers, torch tensors or integer addresses for device buffers, torch
+streams).  Every numerical step runs in the CUDA kernels of
+``_build/libwilson_mg.so``; if that library is missing the import of any entry
+point fails loudly -- there is no CPU path.
+
+Layouts (boundary): links ``U[mu, site, a, b]``, spinors ``psi[site, spin, colour]``,
+complex128, site = x + L0*(y + L1*(z + L2*t)).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build_mod
+
+MG_OK = 0
+MG_ERR_INVALID_ARG = -1
+MG_ERR_NOT_SETUP = -2
+MG_ERR_OOM = -3
+MG_ERR_NOT_CONVERGED = -4
+MG_ERR_NUMERIC = -5
+MG_ERR_TIMEOUT = -6
+MG_ERR_CUDA = -7
+MG_FP64 = 0
+MG_FP32 = 1
+
+LIB_PATH = _build_mod.LIB
+
+
+class MgParams(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int * 4), ("nvec", ctypes.c_int), ("setup_init_relax", ctypes.c_int),
+                ("setup_iters", ctypes.c_int), ("setup_group", ctypes.c_int), ("smoother_steps", ctypes.c_int),
+                ("omega", ctypes.c_double), ("gcr_restart", ctypes.c_int), ("tol", ctypes.c_double),
+                ("coarse_tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("max_coarse", ctypes.c_int),
+                ("delta", ctypes.c_double), ("prec_inner", ctypes.c_int), ("coarse_check", ctypes.c_int)]
+
+
+class MgSolveInfo(ctypes.Structure):
+    _fields_ = [("outer_iters", ctypes.c_int), ("coarse_iters", ctypes.c_int), ("fine_matvecs", ctypes.c_int),
+                ("restarts", ctypes.c_int), ("true_rel_res", ctypes.c_double), ("solve_ms", ctypes.c_double),
+                ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class MGError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{status_string(status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+# name -> (argtypes, restype)
+_P, _I, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+_SIGS = {
+    "mg_default_params": ([_P], _I),
+    "mg_create": ([_P, _I, _P, _P, _P], _I),
+    "mg_destroy": ([_P], None),
+    "mg_set_links": ([_P, _P], _I),
+    "mg_set_mass": ([_P, _D], _I),
+    "mg_set_params": ([_P, _P], _I),
+    "mg_setup": ([_P, _P], _I),
+    "mg_setup_device": ([_P, _P], _I),
+    "mg_set_null_vectors": ([_P, _P, _I], _I),
+    "mg_get_prolongator": ([_P, _P], _I),
+    "mg_get_null_vectors": ([_P, _P], _I),
+    "mg_get_coarse_op": ([_P, _P], _I),
+    "mg_solve": ([_P, _P, _P, _P], _I),
+    "mg_solve_device": ([_P, _P, _P, _P], _I),
+    "mg_apply_dslash": ([_P, _P, _P, _I], _I),
+    "mg_restrict": ([_P, _P, _P, _I], _I),
+    "mg_prolong": ([_P, _P, _P, _I], _I),
+    "mg_apply_coarse": ([_P, _P, _P, _I, _I], _I),
+    "mg_mr": ([_P, _P, _P, _I, _I], _I),
+    "mg_coarse_solve": ([_P, _P, _P, _D, _I, _I, _P, _P], _I),
+    "mg_vcycle": ([_P, _P, _P, _I], _I),
+    "mg_time_dslash": ([_P, _I, _I, _P, _P], _I),
+    "mg_status_string": ([_I], ctypes.c_char_p),
+    "mg_last_error": ([_P], ctypes.c_char_p),
+}
+EXPORTED = tuple(_SIGS)
+
+
+def load(path: str | None = None):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"CUDA library {p} is missing: run paper_1005_3043_gb300.build.build() first")
+        lib = ctypes.CDLL(p)
+        for name, (args, res) in _SIGS.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return load().mg_status_string(int(status)).decode()
+
+
+def _err(ctx) -> str:
+    return load().mg_last_error(ctx).decode() if ctx else ""
+
+
+def _check(status: int, ctx=None, allow=()):
+    if status != MG_OK and status not in allow:
+        raise MGError(status, _err(ctx))
+    return status
+
+
+def _host(a, shape=None) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dev_ptr(t) -> int:
+    """Device address of a torch tensor (or an int address)."""
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("device buffers must be contiguous CUDA tensors")
+    return t.data_ptr()
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ------------------------------------------------------------------ C-ABI, same names
+def mg_default_params() -> MgParams:
+    p = MgParams()
+    _check(load().mg_default_params(ctypes.byref(p)))
+    return p
+
+
+def mg_create(dims, t_antiperiodic: int = 1, params: MgParams | None = None, stream=None):
+    p = params or mg_default_params()
+    d = (ctypes.c_int * 4)(*[int(x) for x in dims])
+    out = ctypes.c_void_p()
+    _check(load().mg_create(d, int(t_antiperiodic), ctypes.byref(p), _stream_ptr(stream), ctypes.byref(out)))
+    return out
+
+
+def mg_destroy(ctx) -> None:
+    if ctx:
+        load().mg_destroy(ctx)
+
+
+def mg_set_links(ctx, U) -> None:
+    _check(load().mg_set_links(ctx, _ptr(_host(U))), ctx)
+
+
+def mg_set_mass(ctx, m: float) -> None:
+    _check(load().mg_set_mass(ctx, float(m)), ctx)
+
+
+def mg_set_params(ctx, params: MgParams) -> None:
+    _check(load().mg_set_params(ctx, ctypes.byref(params)), ctx)
+
+
+def mg_setup(ctx, V0) -> None:
+    _check(load().mg_setup(ctx, _ptr(_host(V0))), ctx)
+
+
+def mg_setup_device(ctx, V0_dev) -> None:
+    _check(load().mg_setup_device(ctx, _dev_ptr(V0_dev)), ctx)
+
+
+def mg_set_null_vectors(ctx, V) -> None:
+    V = _host(V)
+    _check(load().mg_set_null_vectors(ctx, _ptr(V), int(V.shape[0])), ctx)
+
+
+def mg_get_prolongator(ctx, nv: int, V: int) -> np.ndarray:
+    out = np.empty((nv, V, 4, 3), dtype=np.complex128)
+    _check(load().mg_get_prolongator(ctx, _ptr(out)), ctx)
+    return out
+
+
+def mg_get_null_vectors(ctx, nv: int, V: int) -> np.ndarray:
+    out = np.empty((nv, V, 4, 3), dtype=np.complex128)
+    _check(load().mg_get_null_vectors(ctx, _ptr(out)), ctx)
+    return out
+
+
+def mg_get_coarse_op(ctx, Vc: int, nc: int) -> np.ndarray:
+    out = np.empty((Vc, 9, nc, nc), dtype=np.complex128)
+    _check(load().mg_get_coarse_op(ctx, _ptr(out)), ctx)
+    return out
+
+
+def mg_solve(ctx, b):
+    """Host solve: returns (x, info dict).  NOT_CONVERGED is reported in info."""
+    b = _host(b)
+    x = np.empty_like(b)
+    info = MgSolveInfo()
+    _check(load().mg_solve(ctx, _ptr(b), _ptr(x), ctypes.byref(info)), ctx, allow=(MG_ERR_NOT_CONVERGED,))
+    return x, info.as_dict()
+
+
+def mg_solve_device(ctx, b_dev, x_dev) -> dict:
+    info = MgSolveInfo()
+    _check(load().mg_solve_device(ctx, _dev_ptr(b_dev), _dev_ptr(x_dev), ctypes.byref(info)), ctx,
+           allow=(MG_ERR_NOT_CONVERGED,))
+    return info.as_dict()
+
+
+def mg_apply_dslash(ctx, psi, prec: int = MG_FP64) -> np.ndarray:
+    psi = _host(psi)
+    out = np.empty_like(psi)
+    _check(load().mg_apply_dslash(ctx, _ptr(psi), _ptr(out), int(prec)), ctx)
+    return out
+
+
+def mg_restrict(ctx, r, Vc: int, nc: int, prec: int = MG_FP64) -> np.ndarray:
+    r = _host(r)
+    out = np.empty((Vc, nc), dtype=np.complex128)
+    _check(load().mg_restrict(ctx, _ptr(r), _ptr(out), int(prec)), ctx)
+    return out
+
+
+def mg_prolong(ctx, yc, V: int, prec: int = MG_FP64) -> np.ndarray:
+    yc = _host(yc)
+    out = np.empty((V, 4, 3), dtype=np.complex128)
+    _check(load().mg_prolong(ctx, _ptr(yc), _ptr(out), int(prec)), ctx)
+    return out
+
+
+def mg_apply_coarse(ctx, x, dagger: bool = False, prec: int = MG_FP64) -> np.ndarray:
+    x = _host(x)
+    out = np.empty_like(x)
+    _check(load().mg_apply_coarse(ctx, _ptr(x), _ptr(out), int(bool(dagger)), int(prec)), ctx)
+    return out
+
+
+def mg_mr(ctx, e, r, nsteps: int, prec: int = MG_FP64):
+    e = _host(e).copy()
+    r = _host(r).copy()
+    _check(load().mg_mr(ctx, _ptr(e), _ptr(r), int(nsteps), int(prec)), ctx)
+    return e, r
+
+
+def mg_coarse_solve(ctx, rc, tol: float, maxit: int, prec: int = MG_FP64):
+    rc = _host(rc)
+    y = np.empty_like(rc)
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0)
+    _check(load().mg_coarse_solve(ctx, _ptr(rc), _ptr(y), float(tol), int(maxit), int(prec), ctypes.byref(it),
+                                  ctypes.byref(rel)), ctx)
+    return y, it.value, rel.value
+
+
+def mg_vcycle(ctx, r, prec: int = MG_FP64) -> np.ndarray:
+    r = _host(r)
+    z = np.empty_like(r)
+    _check(load().mg_vcycle(ctx, _ptr(r), _ptr(z), int(prec)), ctx)
+    return z
+
+
+def mg_time_dslash(ctx, prec: int = MG_FP32, reps: int = 50):
+    ms = ctypes.c_double(0)
+    nbytes = ctypes.c_double(0)
+    _check(load().mg_time_dslash(ctx, int(prec), int(reps), ctypes.byref(ms), ctypes.byref(nbytes)), ctx)
+    return ms.value, nbytes.value
+
+
+class WilsonMG:
+    """Owning wrapper: ``with WilsonMG(dims, params) as mg: mg.set_links(U); ...``."""
+
+    def __init__(self, dims, params: MgParams | None = None, t_antiperiodic: int = 1, stream=None):
+        self.dims = tuple(int(x) for x in dims)
+        self.params = params or mg_default_params()
+        self.ctx = mg_create(self.dims, t_antiperiodic, self.params, stream)
+        self.V = int(np.prod(self.dims))
+        self.Vc = int(np.prod([d // b for d, b in zip(self.dims, self.params.block)]))
+        self.nv = self.params.nvec
+        self.nc = 2 * self.nv
+
+    def close(self):
+        if self.ctx:
+            mg_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_links(self, U):
+        mg_set_links(self.ctx, U)
+
+    def set_mass(self, m):
+        mg_set_mass(self.ctx, m)
+
+    def set_params(self, p: MgParams):
+        mg_set_params(self.ctx, p)
+        self.params = p
+
+    def setup(self, V0):
+        mg_setup(self.ctx, V0)
+
+    def setup_device(self, V0_dev):
+        mg_setup_device(self.ctx, V0_dev)
+
+    def set_null_vectors(self, V):
+        mg_set_null_vectors(self.ctx, V)
+
+    def prolongator(self):
+        return mg_get_prolongator(self.ctx, self.nv, self.V)
+
+    def null_vectors(self):
+        return mg_get_null_vectors(self.ctx, self.nv, self.V)
+
+    def coarse_op(self):
+        return mg_get_coarse_op(self.ctx, self.Vc, self.nc)
+
+    def solve(self, b):
+        return mg_solve(self.ctx, b)
+
+    def solve_device(self, b_dev, x_dev):
+        return mg_solve_device(self.ctx, b_dev, x_dev)
+
+    def dslash(self, psi, prec=MG_FP64):
+        return mg_apply_dslash(self.ctx, psi, prec)
+
+    def restrict(self, r, prec=MG_FP64):
+        return mg_restrict(self.ctx, r, self.Vc, self.nc, prec)
+
+    def prolong(self, yc, prec=MG_FP64):
+        return mg_prolong(self.ctx, yc, self.V, prec)
+
+    def coarse(self, x, dagger=False, prec=MG_FP64):
+        return mg_apply_coarse(self.ctx, x, dagger, prec)
+
+    def mr(self, e, r, nsteps, prec=MG_FP64):
+        return mg_mr(self.ctx, e, r, nsteps, prec)
+
+    def coarse_solve(self, rc, tol, maxit, prec=MG_FP64):
+        return mg_coarse_solve(self.ctx, rc, tol, maxit, prec)
+
+    def vcycle(self, r, prec=MG_FP64):
+        return mg_vcycle(self.ctx, r, prec)
+
+    def time_dslash(self, prec=MG_FP32, reps=50):
+        return mg_time_dslash(self.ctx, prec, reps)

@@ -1,0 +1,478 @@
+// Fine-grid kernels: boundary/internal layout conversion, the Wilson-Dirac
+// operator of eq. (2) with spin projection, and BLAS-1 / GCR kernels.
+#include "mg_launch.h"
+
+namespace wmg {
+
+constexpr int kThreads = 256;
+
+static inline int grid_for(size_t n, int threads = kThreads) {
+    size_t b = (n + threads - 1) / threads;
+    return (int)(b > 0 ? b : 1);
+}
+static inline int reduce_grid(size_t n) {
+    size_t b = (n + kThreads - 1) / kThreads;
+    if (b > (size_t)kMaxReduceBlocks) b = kMaxReduceBlocks;
+    return (int)(b > 0 ? b : 1);
+}
+
+// ================================================================ layouts
+template <typename T>
+__global__ void k_spinor_to_internal(v2<T>* out, const double2* __restrict__ in, Geom g) {
+    long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (s >= g.V) return;
+    int X = (int)(s / g.Vb), l = (int)(s - (long long)X * g.Vb);
+    long long lex = lex_site(g, X, l);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        double2 v = in[lex * 12 + k];
+        v2<T> o; o.x = (T)v.x; o.y = (T)v.y;
+        out[((size_t)X * 12 + k) * g.Vb + l] = o;
+    }
+}
+template <typename T>
+__global__ void k_spinor_from_internal(double2* out, const v2<T>* __restrict__ in, Geom g) {
+    long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (s >= g.V) return;
+    int X = (int)(s / g.Vb), l = (int)(s - (long long)X * g.Vb);
+    long long lex = lex_site(g, X, l);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        v2<T> v = in[((size_t)X * 12 + k) * g.Vb + l];
+        out[lex * 12 + k] = make_double2((double)v.x, (double)v.y);
+    }
+}
+template <typename T>
+__global__ void k_links_to_internal(v2<T>* out, const double2* __restrict__ in, Geom g) {
+    long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (s >= g.V) return;
+    int X = (int)(s / g.Vb), l = (int)(s - (long long)X * g.Vb);
+    long long lex = lex_site(g, X, l);
+    for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+        for (int e = 0; e < 9; ++e) {
+            double2 v = in[((size_t)mu * g.V + lex) * 9 + e];
+            v2<T> o; o.x = (T)v.x; o.y = (T)v.y;
+            out[(((size_t)mu * g.Vc + X) * 9 + e) * g.Vb + l] = o;
+        }
+}
+template <typename Tin, typename Tout>
+__global__ void k_convert(v2<Tout>* out, const v2<Tin>* __restrict__ in, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        v2<Tin> v = in[i];
+        v2<Tout> o; o.x = (Tout)v.x; o.y = (Tout)v.y;
+        out[i] = o;
+    }
+}
+
+template <typename T> void spinor_to_internal(v2<T>* out, const double2* in, const Geom& g, cudaStream_t st) {
+    k_spinor_to_internal<T><<<grid_for(g.V), kThreads, 0, st>>>(out, in, g);
+}
+template <typename T> void spinor_from_internal(double2* out, const v2<T>* in, const Geom& g, cudaStream_t st) {
+    k_spinor_from_internal<T><<<grid_for(g.V), kThreads, 0, st>>>(out, in, g);
+}
+template <typename T> void links_to_internal(v2<T>* out, const double2* in, const Geom& g, cudaStream_t st) {
+    k_links_to_internal<T><<<grid_for(g.V), kThreads, 0, st>>>(out, in, g);
+}
+template <typename Tin, typename Tout> void convert(v2<Tout>* out, const v2<Tin>* in, size_t n, cudaStream_t st) {
+    int grid = (int)std::min<size_t>((n + kThreads - 1) / kThreads, 152 * 16);
+    k_convert<Tin, Tout><<<grid > 0 ? grid : 1, kThreads, 0, st>>>(out, in, n);
+}
+
+// ================================================================ Wilson operator
+// Spin projection in the DeGrand-Rossi basis.  FWD: (1 - gamma_mu) psi(x+mu);
+// BWD: (1 + gamma_mu) psi(x-mu).  Both are rank-2 projectors: the upper two
+// spin components h0, h1 determine the lower two.
+template <typename T, int MU, bool FWD>
+__device__ __forceinline__ void project(const cx<T> (&p)[4][3], cx<T> (&h)[2][3]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if (MU == 0) {
+            h[0][c] = FWD ? p[0][c] + mul_mi(p[3][c]) : p[0][c] + mul_i(p[3][c]);
+            h[1][c] = FWD ? p[1][c] + mul_mi(p[2][c]) : p[1][c] + mul_i(p[2][c]);
+        } else if (MU == 1) {
+            h[0][c] = FWD ? p[0][c] + p[3][c] : p[0][c] - p[3][c];
+            h[1][c] = FWD ? p[1][c] - p[2][c] : p[1][c] + p[2][c];
+        } else if (MU == 2) {
+            h[0][c] = FWD ? p[0][c] + mul_mi(p[2][c]) : p[0][c] + mul_i(p[2][c]);
+            h[1][c] = FWD ? p[1][c] + mul_i(p[3][c]) : p[1][c] + mul_mi(p[3][c]);
+        } else {
+            h[0][c] = FWD ? p[0][c] - p[2][c] : p[0][c] + p[2][c];
+            h[1][c] = FWD ? p[1][c] - p[3][c] : p[1][c] + p[3][c];
+        }
+    }
+}
+// acc += coef * reconstruct(w): components 0,1 are w0, w1; 2,3 follow from the projector
+template <typename T, int MU, bool FWD>
+__device__ __forceinline__ void accumulate(cx<T> (&acc)[4][3], const cx<T> (&w)[2][3], T coef) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        cx<T> w0 = coef * w[0][c], w1 = coef * w[1][c];
+        acc[0][c] = acc[0][c] + w0;
+        acc[1][c] = acc[1][c] + w1;
+        if (MU == 0) {
+            acc[2][c] = acc[2][c] + (FWD ? mul_i(w1) : mul_mi(w1));
+            acc[3][c] = acc[3][c] + (FWD ? mul_i(w0) : mul_mi(w0));
+        } else if (MU == 1) {
+            acc[2][c] = FWD ? acc[2][c] - w1 : acc[2][c] + w1;
+            acc[3][c] = FWD ? acc[3][c] + w0 : acc[3][c] - w0;
+        } else if (MU == 2) {
+            acc[2][c] = acc[2][c] + (FWD ? mul_i(w0) : mul_mi(w0));
+            acc[3][c] = acc[3][c] + (FWD ? mul_mi(w1) : mul_i(w1));
+        } else {
+            acc[2][c] = FWD ? acc[2][c] - w0 : acc[2][c] + w0;
+            acc[3][c] = FWD ? acc[3][c] - w1 : acc[3][c] + w1;
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void load_spinor(cx<T> (&p)[4][3], const v2<T>* __restrict__ base, int Vb) {
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) p[s][c] = ldg<T>(base + (3 * s + c) * Vb);
+}
+
+// one hop: acc += coef * (1 -/+ gamma_mu) W psi(y), W = U (forward) or U^dag (backward)
+template <typename T, int MU, bool FWD>
+__device__ __forceinline__ void hop(cx<T> (&acc)[4][3], const v2<T>* __restrict__ in, const v2<T>* __restrict__ U,
+                                    const Geom& g, int X, int l, const int (&lc)[4], const int (&xc)[4]) {
+    int Xn, ln;
+    bool flip;
+    neighbour(g, X, l, lc, xc, MU, FWD ? 1 : -1, Xn, ln, flip);
+    cx<T> p[4][3];
+    load_spinor<T>(p, in + (size_t)Xn * 12 * g.Vb + ln, g.Vb);
+    cx<T> h[2][3];
+    project<T, MU, FWD>(p, h);
+    // link U^mu_x (forward) or U^mu_{x-mu} (backward)
+    const v2<T>* u = FWD ? U + ((size_t)MU * g.Vc + X) * 9 * g.Vb + l : U + ((size_t)MU * g.Vc + Xn) * 9 * g.Vb + ln;
+    cx<T> w[2][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        w[0][a] = cx<T>(0, 0);
+        w[1][a] = cx<T>(0, 0);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            if (FWD) {
+                cx<T> uab = ldg<T>(u + (3 * a + b) * g.Vb);
+                cmad(w[0][a], uab, h[0][b]);
+                cmad(w[1][a], uab, h[1][b]);
+            } else {
+                cx<T> uba = ldg<T>(u + (3 * b + a) * g.Vb);
+                cmadc(w[0][a], uba, h[0][b]);
+                cmadc(w[1][a], uba, h[1][b]);
+            }
+        }
+    accumulate<T, MU, FWD>(acc, w, flip ? T(0.5) : T(-0.5));
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_dslash(v2<T>* __restrict__ out, const v2<T>* __restrict__ in,
+                                                const v2<T>* __restrict__ U, const v2<T>* __restrict__ src,
+                                                Geom g, T diag, double omega, int slot, Reduce R) {
+    long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double red[3] = {0.0, 0.0, 0.0};
+    if (s < g.V) {
+        int X = (int)(s / g.Vb), l = (int)(s - (long long)X * g.Vb);
+        int lc[4], xc[4];
+        local_coords(g, l, lc);
+        coarse_coords(g, X, xc);
+        const v2<T>* self = in + (size_t)X * 12 * g.Vb + l;
+        cx<T> acc[4][3], own[4][3];
+        load_spinor<T>(own, self, g.Vb);
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc[sp][c] = diag * own[sp][c];
+        hop<T, 0, true>(acc, in, U, g, X, l, lc, xc);
+        hop<T, 0, false>(acc, in, U, g, X, l, lc, xc);
+        hop<T, 1, true>(acc, in, U, g, X, l, lc, xc);
+        hop<T, 1, false>(acc, in, U, g, X, l, lc, xc);
+        hop<T, 2, true>(acc, in, U, g, X, l, lc, xc);
+        hop<T, 2, false>(acc, in, U, g, X, l, lc, xc);
+        hop<T, 3, true>(acc, in, U, g, X, l, lc, xc);
+        hop<T, 3, false>(acc, in, U, g, X, l, lc, xc);
+        v2<T>* o = out + (size_t)X * 12 * g.Vb + l;
+        const v2<T>* sr = src + (size_t)X * 12 * g.Vb + l;
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                int k = 3 * sp + c;
+                cx<T> v = acc[sp][c];
+                if (MODE == DS_XMY || MODE == DS_XMY_NORM) v = ld<T>(sr + k * g.Vb) - v;
+                st<T>(o + k * g.Vb, v);
+                if (MODE == DS_XMY_NORM) red[0] += (double)norm2(v);
+                if (MODE == DS_MRDOT) {
+                    cx<T> r = own[sp][c];           // <q, r>: q = D r at this site
+                    red[0] += (double)(v.r * r.r + v.i * r.i);
+                    red[1] += (double)(v.r * r.i - v.i * r.r);
+                    red[2] += (double)norm2(v);
+                }
+            }
+    }
+    if (MODE == DS_XMY_NORM) {
+        double v1[1] = {red[0]};
+        grid_reduce<1>(v1, R.partials, R.ticket, [&](double (&t)[1]) { R.scal[slot] = t[0]; });
+    } else if (MODE == DS_MRDOT) {
+        grid_reduce<3>(red, R.partials, R.ticket, [&](double (&t)[3]) {
+            double f = t[2] > 0 ? omega / t[2] : 0.0;
+            R.scal[S_MR_ALPHA] = f * t[0];
+            R.scal[S_MR_ALPHA + 1] = f * t[1];
+        });
+    }
+}
+
+template <typename T>
+void dslash(int mode, v2<T>* out, const v2<T>* in, const v2<T>* U, const v2<T>* src, const Geom& g, double mass,
+            double omega, int slot, const Reduce& R, cudaStream_t st) {
+    int grid = grid_for(g.V);
+    T diag = (T)(4.0 + mass);
+    switch (mode) {
+        case DS_PLAIN: k_dslash<T, DS_PLAIN><<<grid, kThreads, 0, st>>>(out, in, U, src, g, diag, omega, slot, R); break;
+        case DS_XMY: k_dslash<T, DS_XMY><<<grid, kThreads, 0, st>>>(out, in, U, src, g, diag, omega, slot, R); break;
+        case DS_XMY_NORM:
+            k_dslash<T, DS_XMY_NORM><<<grid, kThreads, 0, st>>>(out, in, U, src, g, diag, omega, slot, R);
+            break;
+        case DS_MRDOT: k_dslash<T, DS_MRDOT><<<grid, kThreads, 0, st>>>(out, in, U, src, g, diag, omega, slot, R); break;
+    }
+}
+
+// ================================================================ BLAS-1
+template <typename T> __global__ void k_zero(v2<T>* x, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        v2<T> z; z.x = 0; z.y = 0;
+        x[i] = z;
+    }
+}
+template <typename T> __global__ void k_norm2(const v2<T>* __restrict__ x, size_t n, int slot, Reduce R) {
+    double acc[1] = {0.0};
+    T a = 0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        a += norm2(ld<T>(x + i));
+    acc[0] = (double)a;
+    grid_reduce<1>(acc, R.partials, R.ticket, [&](double (&t)[1]) { R.scal[slot] = t[0]; });
+}
+template <typename T>
+__global__ void k_dot(const v2<T>* __restrict__ x, const v2<T>* __restrict__ y, size_t n, int slot, Reduce R) {
+    cx<T> a(0, 0);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        cmadc(a, ld<T>(x + i), ld<T>(y + i));
+    double acc[2] = {(double)a.r, (double)a.i};
+    grid_reduce<2>(acc, R.partials, R.ticket, [&](double (&t)[2]) {
+        R.scal[slot] = t[0];
+        R.scal[slot + 1] = t[1];
+    });
+}
+template <typename T> __global__ void k_scale(v2<T>* x, size_t n, T s) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        st<T>(x + i, s * ld<T>(x + i));
+}
+template <typename T> __global__ void k_axpy(v2<T>* y, const v2<T>* __restrict__ x, size_t n, T ar, T ai) {
+    cx<T> a(ar, ai);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        cx<T> v = ld<T>(y + i);
+        cmad(v, a, ld<T>(x + i));
+        st<T>(y + i, v);
+    }
+}
+template <typename T>
+__global__ void k_mr_update(v2<T>* e, v2<T>* r, const v2<T>* __restrict__ q, size_t n, bool update_r,
+                            const double* __restrict__ scal) {
+    cx<T> a((T)scal[S_MR_ALPHA], (T)scal[S_MR_ALPHA + 1]);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        cx<T> ri = ld<T>(r + i);
+        cx<T> ei = ld<T>(e + i);
+        cmad(ei, a, ri);
+        st<T>(e + i, ei);
+        if (update_r) {
+            cx<T> qa = a * ld<T>(q + i);
+            st<T>(r + i, ri - qa);
+        }
+    }
+}
+template <typename T> __global__ void k_normalize(v2<T>* x, size_t n, const double* __restrict__ scal, int slot) {
+    T s = (T)(1.0 / sqrt(scal[slot]));
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        st<T>(x + i, s * ld<T>(x + i));
+}
+
+static inline int stream_grid(size_t n) {
+    size_t b = (n + kThreads - 1) / kThreads;
+    if (b > 152 * 16) b = 152 * 16;
+    return (int)(b > 0 ? b : 1);
+}
+
+template <typename T> void zero(v2<T>* x, size_t n, cudaStream_t st) { k_zero<T><<<stream_grid(n), kThreads, 0, st>>>(x, n); }
+template <typename T> void norm2(const v2<T>* x, size_t n, int slot, const Reduce& R, cudaStream_t st) {
+    k_norm2<T><<<reduce_grid(n), kThreads, 0, st>>>(x, n, slot, R);
+}
+template <typename T> void dot(const v2<T>* x, const v2<T>* y, size_t n, int slot, const Reduce& R, cudaStream_t st) {
+    k_dot<T><<<reduce_grid(n), kThreads, 0, st>>>(x, y, n, slot, R);
+}
+template <typename T> void scale(v2<T>* x, size_t n, double s, cudaStream_t st) {
+    k_scale<T><<<stream_grid(n), kThreads, 0, st>>>(x, n, (T)s);
+}
+template <typename T> void axpy(v2<T>* y, const v2<T>* x, size_t n, double ar, double ai, cudaStream_t st) {
+    k_axpy<T><<<stream_grid(n), kThreads, 0, st>>>(y, x, n, (T)ar, (T)ai);
+}
+template <typename T>
+void mr_update(v2<T>* e, v2<T>* r, const v2<T>* q, size_t n, bool update_r, const Reduce& R, cudaStream_t st) {
+    k_mr_update<T><<<stream_grid(n), kThreads, 0, st>>>(e, r, q, n, update_r, R.scal);
+}
+template <typename T> void normalize_dev(v2<T>* x, size_t n, int slot, const Reduce& R, cudaStream_t st) {
+    k_normalize<T><<<stream_grid(n), kThreads, 0, st>>>(x, n, R.scal, slot);
+}
+
+// ================================================================ GCR
+__device__ __forceinline__ int rslot(int j, int k) { return S_GCR_R + 2 * (k * K_MAX + j); }
+
+template <typename T, int NJ>
+__global__ void k_gcr_multidot(const v2<T>* __restrict__ basis, size_t n, int k, Reduce R) {
+    T a[2 * NJ];
+#pragma unroll
+    for (int j = 0; j < 2 * NJ; ++j) a[j] = 0;
+    const v2<T>* pk = basis + (size_t)k * n;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        cx<T> v = ld<T>(pk + i);
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            if (j < k) {
+                cx<T> pj = ld<T>(basis + (size_t)j * n + i);
+                cx<T> t(a[2 * j], a[2 * j + 1]);
+                cmadc(t, pj, v);
+                a[2 * j] = t.r;
+                a[2 * j + 1] = t.i;
+            }
+        }
+    }
+    double acc[2 * NJ];
+#pragma unroll
+    for (int j = 0; j < 2 * NJ; ++j) acc[j] = (double)a[j];
+    grid_reduce<2 * NJ>(acc, R.partials, R.ticket, [&](double (&t)[2 * NJ]) {
+        for (int j = 0; j < k && j < NJ; ++j) {
+            R.scal[rslot(j, k)] = t[2 * j];
+            R.scal[rslot(j, k) + 1] = t[2 * j + 1];
+        }
+    });
+}
+template <typename T>
+__global__ void k_gcr_orth_norm(v2<T>* basis, size_t n, int k, Reduce R) {
+    __shared__ double beta[2 * K_MAX];
+    for (int j = threadIdx.x; j < 2 * k; j += blockDim.x) beta[j] = R.scal[S_GCR_R + 2 * k * K_MAX + j];
+    __syncthreads();
+    v2<T>* pk = basis + (size_t)k * n;
+    T a = 0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        cx<T> v = ld<T>(pk + i);
+        for (int j = 0; j < k; ++j) {
+            cx<T> b((T)beta[2 * j], (T)beta[2 * j + 1]);
+            cx<T> pj = ld<T>(basis + (size_t)j * n + i);
+            v = v - b * pj;
+        }
+        st<T>(pk + i, v);
+        a += norm2(v);
+    }
+    double acc[1] = {(double)a};
+    grid_reduce<1>(acc, R.partials, R.ticket, [&](double (&t)[1]) { R.scal[S_GCR_PN2] = t[0]; });
+}
+template <typename T>
+__global__ void k_gcr_cdot(const v2<T>* __restrict__ basis, const v2<T>* __restrict__ r, size_t n, int k, Reduce R) {
+    const v2<T>* pk = basis + (size_t)k * n;
+    cx<T> a(0, 0);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        cmadc(a, ld<T>(pk + i), ld<T>(r + i));
+    double acc[2] = {(double)a.r, (double)a.i};
+    grid_reduce<2>(acc, R.partials, R.ticket, [&](double (&t)[2]) {
+        double nk = sqrt(R.scal[S_GCR_PN2]);
+        R.scal[rslot(k, k)] = nk;
+        R.scal[rslot(k, k) + 1] = 0.0;
+        double f = nk > 0 ? 1.0 / nk : 0.0;
+        R.scal[S_GCR_C + 2 * k] = t[0] * f;
+        R.scal[S_GCR_C + 2 * k + 1] = t[1] * f;
+    });
+}
+template <typename T>
+__global__ void k_gcr_update(v2<T>* basis, v2<T>* r, size_t n, int k, Reduce R) {
+    double nk = sqrt(R.scal[S_GCR_PN2]);
+    T f = (T)(nk > 0 ? 1.0 / nk : 0.0);
+    cx<T> c((T)R.scal[S_GCR_C + 2 * k], (T)R.scal[S_GCR_C + 2 * k + 1]);
+    v2<T>* pk = basis + (size_t)k * n;
+    T a = 0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        cx<T> p = f * ld<T>(pk + i);
+        st<T>(pk + i, p);
+        cx<T> v = ld<T>(r + i) - c * p;
+        st<T>(r + i, v);
+        a += norm2(v);
+    }
+    double acc[1] = {(double)a};
+    grid_reduce<1>(acc, R.partials, R.ticket, [&](double (&t)[1]) { R.scal[S_GCR_R2] = t[0]; });
+}
+template <typename T>
+__global__ void k_gcr_xupdate(double2* x, const v2<T>* __restrict__ Z, size_t n, int k, GcrCoef y) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        cx<double> v = ld<double>(x + i);
+        for (int j = 0; j < k; ++j) {
+            v2<T> z = Z[(size_t)j * n + i];
+            cx<double> zj((double)z.x, (double)z.y);
+            cmad(v, cx<double>(y.c[2 * j], y.c[2 * j + 1]), zj);
+        }
+        st<double>(x + i, v);
+    }
+}
+
+template <typename T> void gcr_multidot(const v2<T>* basis, size_t n, int k, const Reduce& R, cudaStream_t st) {
+    int grid = reduce_grid(n);
+    if (k <= 4) k_gcr_multidot<T, 4><<<grid, kThreads, 0, st>>>(basis, n, k, R);
+    else if (k <= 8) k_gcr_multidot<T, 8><<<grid, kThreads, 0, st>>>(basis, n, k, R);
+    else if (k <= 16) k_gcr_multidot<T, 16><<<grid, kThreads, 0, st>>>(basis, n, k, R);
+    else k_gcr_multidot<T, 32><<<grid, kThreads, 0, st>>>(basis, n, k, R);
+}
+template <typename T> void gcr_orth_norm(v2<T>* basis, size_t n, int k, const Reduce& R, cudaStream_t st) {
+    k_gcr_orth_norm<T><<<reduce_grid(n), kThreads, 0, st>>>(basis, n, k, R);
+}
+template <typename T>
+void gcr_cdot(const v2<T>* basis, const v2<T>* r, size_t n, int k, const Reduce& R, cudaStream_t st) {
+    k_gcr_cdot<T><<<reduce_grid(n), kThreads, 0, st>>>(basis, r, n, k, R);
+}
+template <typename T> void gcr_update(v2<T>* basis, v2<T>* r, size_t n, int k, const Reduce& R, cudaStream_t st) {
+    k_gcr_update<T><<<reduce_grid(n), kThreads, 0, st>>>(basis, r, n, k, R);
+}
+template <typename T>
+void gcr_xupdate(double2* x, const v2<T>* Z, size_t n, int k, const GcrCoef& y, cudaStream_t st) {
+    k_gcr_xupdate<T><<<stream_grid(n), kThreads, 0, st>>>(x, Z, n, k, y);
+}
+
+// ================================================================ instantiations
+#define INST(T)                                                                                                     \
+    template void spinor_to_internal<T>(v2<T>*, const double2*, const Geom&, cudaStream_t);                         \
+    template void spinor_from_internal<T>(double2*, const v2<T>*, const Geom&, cudaStream_t);                       \
+    template void links_to_internal<T>(v2<T>*, const double2*, const Geom&, cudaStream_t);                          \
+    template void dslash<T>(int, v2<T>*, const v2<T>*, const v2<T>*, const v2<T>*, const Geom&, double, double, int, \
+                            const Reduce&, cudaStream_t);                                                           \
+    template void zero<T>(v2<T>*, size_t, cudaStream_t);                                                            \
+    template void norm2<T>(const v2<T>*, size_t, int, const Reduce&, cudaStream_t);                                 \
+    template void dot<T>(const v2<T>*, const v2<T>*, size_t, int, const Reduce&, cudaStream_t);                     \
+    template void scale<T>(v2<T>*, size_t, double, cudaStream_t);                                                   \
+    template void axpy<T>(v2<T>*, const v2<T>*, size_t, double, double, cudaStream_t);                              \
+    template void mr_update<T>(v2<T>*, v2<T>*, const v2<T>*, size_t, bool, const Reduce&, cudaStream_t);            \
+    template void normalize_dev<T>(v2<T>*, size_t, int, const Reduce&, cudaStream_t);                               \
+    template void gcr_multidot<T>(const v2<T>*, size_t, int, const Reduce&, cudaStream_t);                          \
+    template void gcr_orth_norm<T>(v2<T>*, size_t, int, const Reduce&, cudaStream_t);                               \
+    template void gcr_cdot<T>(const v2<T>*, const v2<T>*, size_t, int, const Reduce&, cudaStream_t);                \
+    template void gcr_update<T>(v2<T>*, v2<T>*, size_t, int, const Reduce&, cudaStream_t);                          \
+    template void gcr_xupdate<T>(double2*, const v2<T>*, size_t, int, const GcrCoef&, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+template void convert<double, float>(v2<float>*, const v2<double>*, size_t, cudaStream_t);
+template void convert<float, double>(v2<double>*, const v2<float>*, size_t, cudaStream_t);
+template void convert<double, double>(v2<double>*, const v2<double>*, size_t, cudaStream_t);
+template void convert<float, float>(v2<float>*, const v2<float>*, size_t, cudaStream_t);
+
+}  // namespace wmg

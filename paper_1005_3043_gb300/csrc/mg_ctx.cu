@@ -1,0 +1,864 @@
+// Context, solver drivers and the C-ABI of include/wilson_mg.h.
+//
+// The solve path (flexible GCR, Sec. III) runs its inner work in precision T
+// (double or float): the V(0,n) cycle (restriction, coarse CGNR, prolongation,
+// MR smoothing) and the Krylov basis.  The solution x and the true residual
+// b - D x are kept in FP64.  Host code only sequences kernels; scalars stay on
+// the device and are read back at convergence checks.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/wilson_mg.h"
+#include "mg_launch.h"
+
+using namespace wmg;
+
+namespace {
+
+struct CoarseLevel {
+    int nv = 0, nc = 0, cap = 0;
+    double2* P64 = nullptr;   // [X][2][nv][6][Vb]
+    float2* P32 = nullptr;
+    double2* A64 = nullptr;   // [X][9][nc][nc] column-major blocks
+    float2* A32 = nullptr;
+    double mass = 0.0;
+    bool valid = false;
+};
+
+template <typename T> struct Work {
+    v2<T>* r = nullptr;    // GCR residual (T == double: aliases the FP64 residual)
+    v2<T>* Z = nullptr;    // K_restart preconditioned directions
+    v2<T>* Pk = nullptr;   // K_restart orthonormal D z
+    v2<T>* vr = nullptr;   // V-cycle residual r - D e
+    v2<T>* vq = nullptr;   // MR q = D r
+    v2<T>* sv = nullptr;   // setup: prototype being relaxed
+    v2<T>* sr = nullptr;   // setup: its residual
+    v2<T>* sz = nullptr;   // setup: cycle output
+    v2<T>* tin = nullptr;  // operator hooks
+    v2<T>* tout = nullptr;
+    v2<T>* crc = nullptr;  // coarse vectors
+    v2<T>* cy = nullptr;
+    v2<T>* cr = nullptr;
+    v2<T>* cs = nullptr;
+    v2<T>* cp = nullptr;
+    v2<T>* cq = nullptr;
+    int cnc = 0;           // coarse dof the coarse vectors are sized for
+    bool ready = false;
+};
+
+}  // namespace
+
+struct mg_ctx {
+    Geom g{};
+    mg_params prm{};
+    int K = 16;                      // GCR restart capacity
+    cudaStream_t st = nullptr;
+    std::string err;
+    double mass = 0.0;
+    bool has_links = false;
+    double2* U64 = nullptr;          // links [mu][X][9][Vb]
+    float2* U32 = nullptr;
+    double2* b64 = nullptr;          // FP64 fine vectors (internal layout)
+    double2* x64 = nullptr;
+    double2* r64 = nullptr;
+    double2* stage_a = nullptr;      // boundary-layout staging (12 V complex each)
+    double2* stage_b = nullptr;
+    double2* protos = nullptr;       // prototypes [nv][X][12][Vb] FP64
+    double2* protos_t = nullptr;     // truncated set during setup
+    double2* protos_stage = nullptr; // boundary layout, nv vectors
+    double2* Aself = nullptr;        // coarse-build scratch
+    double2* cstage = nullptr;       // coarse staging (FP64)
+    CoarseLevel full, trunc;
+    Work<float> wf;
+    Work<double> wd;
+    Reduce R{};
+    double* h_scal = nullptr;        // pinned host copy of the scalars
+    int* d_status = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+const char* kStatusNames[] = {"MG_OK", "MG_ERR_INVALID_ARG", "MG_ERR_NOT_SETUP", "MG_ERR_OOM",
+                              "MG_ERR_NOT_CONVERGED", "MG_ERR_NUMERIC", "MG_ERR_TIMEOUT", "MG_ERR_CUDA"};
+
+int fail(mg_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA,          \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                      \
+    } while (0)
+#define CKL()                                                                                     \
+    do {                                                                                          \
+        cudaError_t e_ = cudaGetLastError();                                                      \
+        if (e_ != cudaSuccess) return fail(ctx, MG_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e_)); \
+    } while (0)
+#define TRY(expr)                                                                                 \
+    do {                                                                                          \
+        int s_ = (expr);                                                                          \
+        if (s_ != MG_OK) return s_;                                                               \
+    } while (0)
+
+template <typename P> int dalloc(mg_ctx* ctx, P** p, size_t bytes) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes > 0 ? bytes : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, MG_ERR_OOM, std::string("cudaMalloc ") + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
+    }
+    ctx->allocs.push_back(q);
+    *p = (P*)q;
+    return MG_OK;
+}
+
+size_t nfine(const mg_ctx* c) { return (size_t)c->g.V * 12; }
+
+int read_scalars(mg_ctx* ctx, int first, int count) {
+    CK(cudaMemcpyAsync(ctx->h_scal + first, ctx->R.scal + first, sizeof(double) * count, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return MG_OK;
+}
+
+template <typename T> Work<T>& work(mg_ctx* c);
+template <> Work<float>& work<float>(mg_ctx* c) { return c->wf; }
+template <> Work<double>& work<double>(mg_ctx* c) { return c->wd; }
+template <typename T> const v2<T>* links(const mg_ctx* c);
+template <> const v2<float>* links<float>(const mg_ctx* c) { return c->U32; }
+template <> const v2<double>* links<double>(const mg_ctx* c) { return c->U64; }
+template <typename T> const v2<T>* lvlP(const CoarseLevel& L);
+template <> const v2<float>* lvlP<float>(const CoarseLevel& L) { return L.P32; }
+template <> const v2<double>* lvlP<double>(const CoarseLevel& L) { return L.P64; }
+template <typename T> const v2<T>* lvlA(const CoarseLevel& L);
+template <> const v2<float>* lvlA<float>(const CoarseLevel& L) { return L.A32; }
+template <> const v2<double>* lvlA<double>(const CoarseLevel& L) { return L.A64; }
+
+template <typename T> int ensure_work(mg_ctx* ctx) {
+    Work<T>& w = work<T>(ctx);
+    int nc = 2 * ctx->prm.nvec;
+    if (w.ready && w.cnc >= nc) return MG_OK;
+    size_t n = nfine(ctx), vb = sizeof(v2<T>) * n;
+    if (!w.ready) {
+        if (std::is_same<T, double>::value) w.r = (v2<T>*)ctx->r64;
+        else TRY(dalloc(ctx, &w.r, vb));
+        TRY(dalloc(ctx, &w.Z, vb * ctx->K));
+        TRY(dalloc(ctx, &w.Pk, vb * ctx->K));
+        TRY(dalloc(ctx, &w.vr, vb));
+        TRY(dalloc(ctx, &w.vq, vb));
+        TRY(dalloc(ctx, &w.sv, vb));
+        TRY(dalloc(ctx, &w.sr, vb));
+        TRY(dalloc(ctx, &w.sz, vb));
+        TRY(dalloc(ctx, &w.tin, vb));
+        TRY(dalloc(ctx, &w.tout, vb));
+    }
+    size_t cb = sizeof(v2<T>) * (size_t)ctx->g.Vc * (nc > 0 ? nc : 2);
+    TRY(dalloc(ctx, &w.crc, cb));
+    TRY(dalloc(ctx, &w.cy, cb));
+    TRY(dalloc(ctx, &w.cr, cb));
+    TRY(dalloc(ctx, &w.cs, cb));
+    TRY(dalloc(ctx, &w.cp, cb));
+    TRY(dalloc(ctx, &w.cq, cb));
+    w.cnc = nc;
+    w.ready = true;
+    return MG_OK;
+}
+
+int ensure_level(mg_ctx* ctx, CoarseLevel& L, int nv) {
+    if (L.cap < nv) {
+        size_t np = (size_t)nv * nfine(ctx);
+        size_t na = (size_t)ctx->g.Vc * 9 * (2 * nv) * (2 * nv);
+        TRY(dalloc(ctx, &L.P64, sizeof(double2) * np));
+        TRY(dalloc(ctx, &L.P32, sizeof(float2) * np));
+        TRY(dalloc(ctx, &L.A64, sizeof(double2) * na));
+        TRY(dalloc(ctx, &L.A32, sizeof(float2) * na));
+        L.cap = nv;
+    }
+    L.nv = nv;
+    L.nc = 2 * nv;
+    return MG_OK;
+}
+
+int ensure_protos(mg_ctx* ctx) {
+    int nv = ctx->prm.nvec;
+    if (ctx->protos) return MG_OK;
+    size_t n = nfine(ctx);
+    TRY(dalloc(ctx, &ctx->protos, sizeof(double2) * n * nv));
+    TRY(dalloc(ctx, &ctx->protos_t, sizeof(double2) * n * nv));
+    TRY(dalloc(ctx, &ctx->protos_stage, sizeof(double2) * n * nv));
+    TRY(dalloc(ctx, &ctx->Aself, sizeof(double2) * (size_t)ctx->g.Vc * 8 * (2 * nv) * (2 * nv)));
+    TRY(dalloc(ctx, &ctx->cstage, sizeof(double2) * (size_t)ctx->g.Vc * 9 * (2 * nv) * (2 * nv)));
+    return MG_OK;
+}
+
+// P, D_c of a level from nv prototypes (internal FP64 layout)
+int build_level(mg_ctx* ctx, CoarseLevel& L, const double2* V, int nv) {
+    TRY(ensure_level(ctx, L, nv));
+    CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->st));
+    block_orthonormalize(L.P64, V, nv, ctx->g, ctx->d_status, ctx->st);
+    CKL();
+    int status = 0;
+    CK(cudaMemcpyAsync(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    if (status) {
+        L.valid = false;
+        return fail(ctx, MG_ERR_NUMERIC, "block orthonormalisation: rank-deficient prototypes in an aggregate");
+    }
+    coarse_build(L.A64, ctx->Aself, L.P64, ctx->U64, nv, ctx->mass, ctx->g, ctx->st);
+    CKL();
+    size_t np = (size_t)nv * nfine(ctx), na = (size_t)ctx->g.Vc * 9 * L.nc * L.nc;
+    convert<double, float>(L.P32, L.P64, np, ctx->st);
+    convert<double, float>(L.A32, L.A64, na, ctx->st);
+    CKL();
+    L.mass = ctx->mass;
+    L.valid = true;
+    return MG_OK;
+}
+
+// ---------------------------------------------------------------- coarse solve
+template <typename T>
+int coarse_solve(mg_ctx* ctx, const CoarseLevel& L, const v2<T>* rc, v2<T>* y, double tol, int maxit, int* iters) {
+    Work<T>& w = work<T>(ctx);
+    size_t n = (size_t)ctx->g.Vc * L.nc;
+    const v2<T>* A = lvlA<T>(L);
+    cg_init<T>(y, w.cr, rc, n, tol, maxit, ctx->R, ctx->st);
+    cg_first_direction<T>(w.cs, w.cp, w.cr, A, L.nc, ctx->g, ctx->R, ctx->st);
+    CKL();
+    int check = ctx->prm.coarse_check > 0 ? ctx->prm.coarse_check : 16;
+    int launched = 0;
+    for (;;) {
+        for (int j = 0; j < check; ++j) cg_step<T>(y, w.cr, w.cs, w.cp, w.cq, A, L.nc, ctx->g, ctx->R, ctx->st);
+        CKL();
+        launched += check;
+        TRY(read_scalars(ctx, S_CG_ITERS, 2));
+        if (ctx->h_scal[S_CG_DONE] != 0.0) break;
+        if (launched > maxit + check) return fail(ctx, MG_ERR_NUMERIC, "coarse solve did not stop");
+    }
+    *iters = (int)ctx->h_scal[S_CG_ITERS];
+    return MG_OK;
+}
+
+// ---------------------------------------------------------------- V(0, n) cycle
+struct Counters {
+    int coarse_iters = 0;
+    int matvecs = 0;
+};
+
+template <typename T>
+int vcycle(mg_ctx* ctx, const CoarseLevel& L, const v2<T>* r, v2<T>* z, Counters& cnt) {
+    Work<T>& w = work<T>(ctx);
+    size_t n = nfine(ctx);
+    const v2<T>* U = links<T>(ctx);
+    restrict_<T>(w.crc, lvlP<T>(L), r, L.nv, ctx->g, ctx->st);
+    CKL();
+    int it = 0;
+    TRY(coarse_solve<T>(ctx, L, w.crc, w.cy, ctx->prm.coarse_tol, ctx->prm.max_coarse, &it));
+    cnt.coarse_iters += it;
+    prolong<T>(z, lvlP<T>(L), w.cy, L.nv, ctx->g, ctx->st);
+    dslash<T>(DS_XMY, w.vr, z, U, r, ctx->g, ctx->mass, 0.0, 0, ctx->R, ctx->st);
+    cnt.matvecs += 1;
+    int steps = ctx->prm.smoother_steps;
+    for (int k = 0; k < steps; ++k) {
+        dslash<T>(DS_MRDOT, w.vq, w.vr, U, w.vr, ctx->g, ctx->mass, ctx->prm.omega, 0, ctx->R, ctx->st);
+        mr_update<T>(z, w.vr, w.vq, n, k + 1 < steps, ctx->R, ctx->st);
+        cnt.matvecs += 1;
+    }
+    CKL();
+    return MG_OK;
+}
+
+// ---------------------------------------------------------------- flexible GCR
+template <typename T> int gcr_solve(mg_ctx* ctx, mg_solve_info* info) {
+    TRY(ensure_work<T>(ctx));
+    Work<T>& w = work<T>(ctx);
+    const mg_params& p = ctx->prm;
+    size_t n = nfine(ctx);
+    const v2<T>* U = links<T>(ctx);
+    Counters cnt;
+    int restarts = 0, iters = 0, status = MG_ERR_NOT_CONVERGED;
+    CK(cudaEventRecord(ctx->ev0, ctx->st));
+    norm2<double>(ctx->b64, n, S_NORM_A, ctx->R, ctx->st);
+    zero<double>(ctx->x64, n, ctx->st);
+    CK(cudaMemcpyAsync(ctx->r64, ctx->b64, sizeof(double2) * n, cudaMemcpyDeviceToDevice, ctx->st));
+    if (!std::is_same<T, double>::value) convert<double, T>(w.r, ctx->r64, n, ctx->st);
+    CKL();
+    TRY(read_scalars(ctx, S_NORM_A, 1));
+    double bnorm = std::sqrt(ctx->h_scal[S_NORM_A]);
+    if (!std::isfinite(bnorm)) return fail(ctx, MG_ERR_NUMERIC, "right-hand side is not finite");
+    double rel = bnorm > 0 ? 1.0 : 0.0;
+    if (bnorm == 0) status = MG_OK;
+    double rnorm = bnorm;
+    const int K = std::min(p.gcr_restart, ctx->K);
+    while (status == MG_ERR_NOT_CONVERGED && iters < p.max_outer) {
+        int k = 0;
+        double rcycle = rnorm;
+        for (; k < K && iters < p.max_outer;) {
+            v2<T>* zk = w.Z + (size_t)k * n;
+            TRY(vcycle<T>(ctx, ctx->full, w.r, zk, cnt));
+            dslash<T>(DS_PLAIN, w.Pk + (size_t)k * n, zk, U, zk, ctx->g, ctx->mass, 0.0, 0, ctx->R, ctx->st);
+            cnt.matvecs += 1;
+            if (k > 0) {
+                gcr_multidot<T>(w.Pk, n, k, ctx->R, ctx->st);
+                gcr_orth_norm<T>(w.Pk, n, k, ctx->R, ctx->st);
+            } else {
+                norm2<T>(w.Pk, n, S_GCR_PN2, ctx->R, ctx->st);
+            }
+            gcr_cdot<T>(w.Pk, w.r, n, k, ctx->R, ctx->st);
+            gcr_update<T>(w.Pk, w.r, n, k, ctx->R, ctx->st);
+            CKL();
+            TRY(read_scalars(ctx, S_GCR_PN2, 2));
+            ++k;
+            ++iters;
+            double pn = ctx->h_scal[S_GCR_PN2];
+            if (!(pn > 0) || !std::isfinite(pn)) {
+                status = MG_ERR_NUMERIC;
+                break;
+            }
+            rnorm = std::sqrt(ctx->h_scal[S_GCR_R2]);
+            if (rnorm <= p.tol * bnorm) break;
+            if (p.delta > 0 && rnorm <= p.delta * rcycle) break;
+        }
+        if (status == MG_ERR_NUMERIC) break;
+        // back substitution R y = c
+        TRY(read_scalars(ctx, S_GCR_R, 2 * K_MAX * K_MAX + 2 * K_MAX));
+        auto Rr = [&](int j, int kk) { return ctx->h_scal + S_GCR_R + 2 * (kk * K_MAX + j); };
+        GcrCoef y{};
+        for (int i = k - 1; i >= 0; --i) {
+            double sr = ctx->h_scal[S_GCR_C + 2 * i], si = ctx->h_scal[S_GCR_C + 2 * i + 1];
+            for (int j = i + 1; j < k; ++j) {
+                const double* r = Rr(i, j);
+                sr -= r[0] * y.c[2 * j] - r[1] * y.c[2 * j + 1];
+                si -= r[0] * y.c[2 * j + 1] + r[1] * y.c[2 * j];
+            }
+            const double* d = Rr(i, i);
+            double den = d[0] * d[0] + d[1] * d[1];
+            y.c[2 * i] = (sr * d[0] + si * d[1]) / den;
+            y.c[2 * i + 1] = (si * d[0] - sr * d[1]) / den;
+        }
+        gcr_xupdate<T>(ctx->x64, w.Z, n, k, y, ctx->st);
+        dslash<double>(DS_XMY_NORM, ctx->r64, ctx->x64, ctx->U64, ctx->b64, ctx->g, ctx->mass, 0.0, S_NORM_B, ctx->R,
+                       ctx->st);
+        cnt.matvecs += 1;
+        CKL();
+        TRY(read_scalars(ctx, S_NORM_B, 1));
+        ++restarts;
+        rnorm = std::sqrt(ctx->h_scal[S_NORM_B]);
+        rel = rnorm / bnorm;
+        if (!std::isfinite(rel)) { status = MG_ERR_NUMERIC; break; }
+        if (rel <= p.tol) status = MG_OK;
+        else if (!std::is_same<T, double>::value) convert<double, T>(w.r, ctx->r64, n, ctx->st);
+    }
+    CK(cudaEventRecord(ctx->ev1, ctx->st));
+    CK(cudaEventSynchronize(ctx->ev1));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+    if (info) {
+        info->outer_iters = iters;
+        info->coarse_iters = cnt.coarse_iters;
+        info->fine_matvecs = cnt.matvecs;
+        info->restarts = restarts;
+        info->true_rel_res = rel;
+        info->solve_ms = ms;
+        info->status = status;
+    }
+    if (status == MG_ERR_NOT_CONVERGED) ctx->err = "max_outer reached";
+    if (status == MG_ERR_NUMERIC) ctx->err = "non-finite residual or GCR breakdown";
+    return status;
+}
+
+// ---------------------------------------------------------------- adaptive setup
+// relaxation of prototype v (T) on D v = 0: r = -D v, init_relax MR steps, normalise
+template <typename T> int relax_and_normalize(mg_ctx* ctx, v2<T>* v, int steps) {
+    Work<T>& w = work<T>(ctx);
+    size_t n = nfine(ctx);
+    const v2<T>* U = links<T>(ctx);
+    dslash<T>(DS_PLAIN, w.sr, v, U, v, ctx->g, ctx->mass, 0.0, 0, ctx->R, ctx->st);
+    scale<T>(w.sr, n, -1.0, ctx->st);
+    for (int k = 0; k < steps; ++k) {
+        dslash<T>(DS_MRDOT, w.vq, w.sr, U, w.sr, ctx->g, ctx->mass, ctx->prm.omega, 0, ctx->R, ctx->st);
+        mr_update<T>(v, w.sr, w.vq, n, k + 1 < steps, ctx->R, ctx->st);
+    }
+    norm2<T>(v, n, S_NORM_A, ctx->R, ctx->st);
+    normalize_dev<T>(v, n, S_NORM_A, ctx->R, ctx->st);
+    CKL();
+    return MG_OK;
+}
+
+template <typename T> int setup_impl(mg_ctx* ctx) {
+    TRY(ensure_work<T>(ctx));
+    Work<T>& w = work<T>(ctx);
+    const mg_params& p = ctx->prm;
+    size_t n = nfine(ctx);
+    int nv = p.nvec;
+    const v2<T>* U = links<T>(ctx);
+    // (ii) relaxation of every random start
+    for (int i = 0; i < nv; ++i) {
+        double2* vi = ctx->protos + (size_t)i * n;
+        convert<double, T>(w.sv, vi, n, ctx->st);
+        TRY(relax_and_normalize<T>(ctx, w.sv, p.setup_init_relax));
+        convert<T, double>(vi, w.sv, n, ctx->st);
+    }
+    CKL();
+    // (iii) group refinement with the truncated two-level method
+    int gs = p.setup_group, nt = nv - gs;
+    if (p.setup_iters > 0 && nt > 0) {
+        Counters cnt;
+        for (int g0 = 0; g0 < nv; g0 += gs) {
+            int k = 0;
+            for (int i = 0; i < nv; ++i)
+                if (i < g0 || i >= g0 + gs)
+                    CK(cudaMemcpyAsync(ctx->protos_t + (size_t)(k++) * n, ctx->protos + (size_t)i * n,
+                                       sizeof(double2) * n, cudaMemcpyDeviceToDevice, ctx->st));
+            TRY(build_level(ctx, ctx->trunc, ctx->protos_t, nt));
+            for (int i = g0; i < g0 + gs; ++i) {
+                double2* vi = ctx->protos + (size_t)i * n;
+                convert<double, T>(w.sv, vi, n, ctx->st);
+                for (int it = 0; it < p.setup_iters; ++it) {
+                    dslash<T>(DS_PLAIN, w.sr, w.sv, U, w.sv, ctx->g, ctx->mass, 0.0, 0, ctx->R, ctx->st);
+                    scale<T>(w.sr, n, -1.0, ctx->st);
+                    TRY(vcycle<T>(ctx, ctx->trunc, w.sr, w.sz, cnt));
+                    axpy<T>(w.sv, w.sz, n, 1.0, 0.0, ctx->st);
+                    norm2<T>(w.sv, n, S_NORM_A, ctx->R, ctx->st);
+                    normalize_dev<T>(w.sv, n, S_NORM_A, ctx->R, ctx->st);
+                }
+                convert<T, double>(vi, w.sv, n, ctx->st);
+                CKL();
+            }
+        }
+    }
+    // (iv) final prolongator and coarse operator
+    return build_level(ctx, ctx->full, ctx->protos, nv);
+}
+
+int check_params(const int dims[4], const mg_params* p, std::string& why) {
+    for (int m = 0; m < 4; ++m) {
+        if (dims[m] <= 0 || p->block[m] <= 0 || dims[m] % p->block[m] != 0) {
+            why = "lattice extent must be a positive multiple of the block extent";
+            return MG_ERR_INVALID_ARG;
+        }
+    }
+    int vb = p->block[0] * p->block[1] * p->block[2] * p->block[3];
+    if (6 * vb > 8 * 256) { why = "block volume above 341 sites is not supported"; return MG_ERR_INVALID_ARG; }
+    if (p->nvec <= 0 || 2 * p->nvec > 50) { why = "nvec must be in 1..25"; return MG_ERR_INVALID_ARG; }
+    if (p->gcr_restart <= 0 || p->gcr_restart > K_MAX) { why = "gcr_restart must be in 1..32"; return MG_ERR_INVALID_ARG; }
+    if (p->setup_group <= 0 || p->nvec % p->setup_group != 0) {
+        why = "setup_group must divide nvec";
+        return MG_ERR_INVALID_ARG;
+    }
+    if (p->prec_inner != MG_FP64 && p->prec_inner != MG_FP32) { why = "prec_inner must be MG_FP64 or MG_FP32"; return MG_ERR_INVALID_ARG; }
+    return MG_OK;
+}
+
+// boundary host fine vector -> internal T buffer (through stage_a)
+template <typename T> int upload_fine(mg_ctx* ctx, const double* h, v2<T>* d) {
+    CK(cudaMemcpyAsync(ctx->stage_a, h, sizeof(double2) * nfine(ctx), cudaMemcpyHostToDevice, ctx->st));
+    spinor_to_internal<T>(d, ctx->stage_a, ctx->g, ctx->st);
+    CKL();
+    return MG_OK;
+}
+template <typename T> int download_fine(mg_ctx* ctx, const v2<T>* d, double* h) {
+    spinor_from_internal<T>(ctx->stage_b, d, ctx->g, ctx->st);
+    CKL();
+    CK(cudaMemcpyAsync(h, ctx->stage_b, sizeof(double2) * nfine(ctx), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return MG_OK;
+}
+template <typename T> int upload_coarse(mg_ctx* ctx, const double* h, v2<T>* d, size_t n) {
+    CK(cudaMemcpyAsync(ctx->cstage, h, sizeof(double2) * n, cudaMemcpyHostToDevice, ctx->st));
+    convert<double, T>(d, ctx->cstage, n, ctx->st);
+    CKL();
+    return MG_OK;
+}
+template <typename T> int download_coarse(mg_ctx* ctx, const v2<T>* d, double* h, size_t n) {
+    convert<T, double>(ctx->cstage, d, n, ctx->st);
+    CKL();
+    CK(cudaMemcpyAsync(h, ctx->cstage, sizeof(double2) * n, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return MG_OK;
+}
+
+int need_links(mg_ctx* ctx) {
+    if (!ctx) return MG_ERR_INVALID_ARG;
+    if (!ctx->has_links) return fail(ctx, MG_ERR_NOT_SETUP, "links not set");
+    return MG_OK;
+}
+int need_level(mg_ctx* ctx) {
+    TRY(need_links(ctx));
+    if (!ctx->full.valid) return fail(ctx, MG_ERR_NOT_SETUP, "no coarse operator: call mg_setup or mg_set_null_vectors");
+    return MG_OK;
+}
+
+template <typename T> int hook_dslash(mg_ctx* ctx, const double* in, double* out) {
+    TRY(ensure_work<T>(ctx));
+    Work<T>& w = work<T>(ctx);
+    TRY(upload_fine<T>(ctx, in, w.tin));
+    dslash<T>(DS_PLAIN, w.tout, w.tin, links<T>(ctx), w.tin, ctx->g, ctx->mass, 0.0, 0, ctx->R, ctx->st);
+    CKL();
+    return download_fine<T>(ctx, w.tout, out);
+}
+template <typename T> int hook_restrict(mg_ctx* ctx, const double* r, double* rc) {
+    TRY(ensure_work<T>(ctx));
+    Work<T>& w = work<T>(ctx);
+    TRY(upload_fine<T>(ctx, r, w.tin));
+    restrict_<T>(w.crc, lvlP<T>(ctx->full), w.tin, ctx->full.nv, ctx->g, ctx->st);
+    CKL();
+    return download_coarse<T>(ctx, w.crc, rc, (size_t)ctx->g.Vc * ctx->full.nc);
+}
+template <typename T> int hook_prolong(mg_ctx* ctx, const double* yc, double* e) {
+    TRY(ensure_work<T>(ctx));
+    Work<T>& w = work<T>(ctx);
+    TRY(upload_coarse<T>(ctx, yc, w.cy, (size_t)ctx->g.Vc * ctx->full.nc));
+    prolong<T>(w.tout, lvlP<T>(ctx->full), w.cy, ctx->full.nv, ctx->g, ctx->st);
+    CKL();
+    return download_fine<T>(ctx, w.tout, e);
+}
+template <typename T> int hook_coarse(mg_ctx* ctx, const double* x, double* y, int dagger) {
+    TRY(ensure_work<T>(ctx));
+    Work<T>& w = work<T>(ctx);
+    size_t n = (size_t)ctx->g.Vc * ctx->full.nc;
+    TRY(upload_coarse<T>(ctx, x, w.cp, n));
+    coarse_apply<T>(w.cq, lvlA<T>(ctx->full), w.cp, ctx->full.nc, dagger != 0, -1, ctx->g, ctx->R, ctx->st);
+    CKL();
+    return download_coarse<T>(ctx, w.cq, y, n);
+}
+template <typename T> int hook_mr(mg_ctx* ctx, double* e, double* r, int nsteps) {
+    TRY(ensure_work<T>(ctx));
+    Work<T>& w = work<T>(ctx);
+    size_t n = nfine(ctx);
+    TRY(upload_fine<T>(ctx, e, w.tin));
+    TRY(upload_fine<T>(ctx, r, w.tout));
+    const v2<T>* U = links<T>(ctx);
+    for (int k = 0; k < nsteps; ++k) {
+        dslash<T>(DS_MRDOT, w.vq, w.tout, U, w.tout, ctx->g, ctx->mass, ctx->prm.omega, 0, ctx->R, ctx->st);
+        mr_update<T>(w.tin, w.tout, w.vq, n, true, ctx->R, ctx->st);
+    }
+    CKL();
+    TRY(download_fine<T>(ctx, w.tin, e));
+    return download_fine<T>(ctx, w.tout, r);
+}
+template <typename T>
+int hook_coarse_solve(mg_ctx* ctx, const double* rc, double* y, double tol, int maxit, int* iters, double* rel) {
+    TRY(ensure_work<T>(ctx));
+    Work<T>& w = work<T>(ctx);
+    size_t n = (size_t)ctx->g.Vc * ctx->full.nc;
+    TRY(upload_coarse<T>(ctx, rc, w.crc, n));
+    int it = 0;
+    TRY(coarse_solve<T>(ctx, ctx->full, w.crc, w.cy, tol, maxit, &it));
+    TRY(read_scalars(ctx, S_CG_RC2, 2));
+    if (iters) *iters = it;
+    if (rel) *rel = ctx->h_scal[S_CG_RC2] > 0 ? std::sqrt(ctx->h_scal[S_CG_R2] / ctx->h_scal[S_CG_RC2]) : 0.0;
+    return download_coarse<T>(ctx, w.cy, y, n);
+}
+template <typename T> int hook_vcycle(mg_ctx* ctx, const double* r, double* z) {
+    TRY(ensure_work<T>(ctx));
+    Work<T>& w = work<T>(ctx);
+    TRY(upload_fine<T>(ctx, r, w.tin));
+    Counters cnt;
+    TRY(vcycle<T>(ctx, ctx->full, w.tin, w.tout, cnt));
+    return download_fine<T>(ctx, w.tout, z);
+}
+
+}  // namespace
+
+// ======================================================================= C-ABI
+extern "C" {
+
+int mg_default_params(mg_params* p) {
+    if (!p) return MG_ERR_INVALID_ARG;
+    std::memset(p, 0, sizeof(*p));
+    for (int m = 0; m < 4; ++m) p->block[m] = 4;
+    p->nvec = 8;
+    p->setup_init_relax = 10;
+    p->setup_iters = 3;
+    p->setup_group = 4;
+    p->smoother_steps = 4;
+    p->omega = 0.9;
+    p->gcr_restart = 16;
+    p->tol = 1e-10;
+    p->coarse_tol = 1e-3;
+    p->max_outer = 1000;
+    p->max_coarse = 5000;
+    p->delta = 0.0;
+    p->prec_inner = MG_FP64;
+    p->coarse_check = 16;
+    return MG_OK;
+}
+
+int mg_create(const int dims[4], int t_antiperiodic, const mg_params* p, void* stream, mg_ctx** out) {
+    if (!dims || !p || !out) return MG_ERR_INVALID_ARG;
+    *out = nullptr;
+    std::string why;
+    if (check_params(dims, p, why) != MG_OK) return MG_ERR_INVALID_ARG;
+    mg_ctx* ctx = new mg_ctx();
+    ctx->prm = *p;
+    ctx->K = p->gcr_restart;
+    ctx->st = (cudaStream_t)stream;
+    Geom& g = ctx->g;
+    for (int m = 0; m < 4; ++m) {
+        g.L[m] = dims[m];
+        g.B[m] = p->block[m];
+        g.Lc[m] = dims[m] / p->block[m];
+    }
+    g.lstride[0] = 1;
+    g.xstride[0] = 1;
+    for (int m = 1; m < 4; ++m) {
+        g.lstride[m] = g.lstride[m - 1] * g.B[m - 1];
+        g.xstride[m] = g.xstride[m - 1] * g.Lc[m - 1];
+    }
+    g.Vb = g.B[0] * g.B[1] * g.B[2] * g.B[3];
+    g.Vc = g.Lc[0] * g.Lc[1] * g.Lc[2] * g.Lc[3];
+    g.V = (long long)g.Vb * g.Vc;
+    g.tap = t_antiperiodic ? 1 : 0;
+    size_t n = nfine(ctx);
+    int rc = MG_OK;
+    if ((rc = dalloc(ctx, &ctx->U64, sizeof(double2) * 36 * (size_t)g.V)) ||
+        (rc = dalloc(ctx, &ctx->U32, sizeof(float2) * 36 * (size_t)g.V)) ||
+        (rc = dalloc(ctx, &ctx->b64, sizeof(double2) * n)) || (rc = dalloc(ctx, &ctx->x64, sizeof(double2) * n)) ||
+        (rc = dalloc(ctx, &ctx->r64, sizeof(double2) * n)) ||
+        (rc = dalloc(ctx, &ctx->stage_a, sizeof(double2) * 36 * (size_t)g.V)) ||
+        (rc = dalloc(ctx, &ctx->stage_b, sizeof(double2) * n)) ||
+        (rc = dalloc(ctx, &ctx->R.partials, sizeof(double) * kMaxReduceBlocks * 64)) ||
+        (rc = dalloc(ctx, &ctx->R.ticket, sizeof(unsigned int) * 4)) ||
+        (rc = dalloc(ctx, &ctx->R.scal, sizeof(double) * S_COUNT)) || (rc = dalloc(ctx, &ctx->d_status, sizeof(int)))) {
+        mg_destroy(ctx);
+        return rc;
+    }
+    if (cudaMallocHost(&ctx->h_scal, sizeof(double) * S_COUNT) != cudaSuccess ||
+        cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess ||
+        cudaMemsetAsync(ctx->R.ticket, 0, sizeof(unsigned int) * 4, ctx->st) != cudaSuccess ||
+        cudaMemsetAsync(ctx->R.scal, 0, sizeof(double) * S_COUNT, ctx->st) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->st) != cudaSuccess) {
+        cudaGetLastError();
+        mg_destroy(ctx);
+        return MG_ERR_CUDA;
+    }
+    *out = ctx;
+    return MG_OK;
+}
+
+void mg_destroy(mg_ctx* ctx) {
+    if (!ctx) return;
+    if (ctx->st) cudaStreamSynchronize(ctx->st);
+    else cudaDeviceSynchronize();
+    for (void* q : ctx->allocs) cudaFree(q);
+    if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    delete ctx;
+}
+
+int mg_set_links(mg_ctx* ctx, const double* U) {
+    if (!ctx || !U) return MG_ERR_INVALID_ARG;
+    CK(cudaMemcpyAsync(ctx->stage_a, U, sizeof(double2) * 36 * (size_t)ctx->g.V, cudaMemcpyHostToDevice, ctx->st));
+    links_to_internal<double>(ctx->U64, ctx->stage_a, ctx->g, ctx->st);
+    convert<double, float>(ctx->U32, ctx->U64, 36 * (size_t)ctx->g.V, ctx->st);
+    CKL();
+    CK(cudaStreamSynchronize(ctx->st));
+    ctx->has_links = true;
+    ctx->full.valid = false;   // D_c depends on the links
+    return MG_OK;
+}
+
+int mg_set_mass(mg_ctx* ctx, double m) {
+    if (!ctx) return MG_ERR_INVALID_ARG;
+    if (ctx->full.valid) {
+        coarse_shift_mass(ctx->full.A64, ctx->full.nc, m - ctx->full.mass, ctx->g, ctx->st);
+        convert<double, float>(ctx->full.A32, ctx->full.A64, (size_t)ctx->g.Vc * 9 * ctx->full.nc * ctx->full.nc, ctx->st);
+        CKL();
+        ctx->full.mass = m;
+    }
+    ctx->mass = m;
+    CK(cudaStreamSynchronize(ctx->st));
+    return MG_OK;
+}
+
+int mg_set_params(mg_ctx* ctx, const mg_params* p) {
+    if (!ctx || !p) return MG_ERR_INVALID_ARG;
+    std::string why;
+    if (check_params(ctx->g.L, p, why) != MG_OK) return fail(ctx, MG_ERR_INVALID_ARG, why);
+    for (int m = 0; m < 4; ++m)
+        if (p->block[m] != ctx->prm.block[m]) return fail(ctx, MG_ERR_INVALID_ARG, "block size is fixed at create");
+    if (p->nvec != ctx->prm.nvec) return fail(ctx, MG_ERR_INVALID_ARG, "nvec is fixed at create");
+    if (p->gcr_restart > ctx->K) return fail(ctx, MG_ERR_INVALID_ARG, "gcr_restart above the value at create");
+    ctx->prm = *p;
+    return MG_OK;
+}
+
+int mg_setup(mg_ctx* ctx, const double* V0) {
+    TRY(need_links(ctx));
+    if (!V0) return fail(ctx, MG_ERR_INVALID_ARG, "V0 is NULL");
+    TRY(ensure_protos(ctx));
+    int nv = ctx->prm.nvec;
+    size_t n = nfine(ctx);
+    CK(cudaMemcpyAsync(ctx->protos_stage, V0, sizeof(double2) * n * nv, cudaMemcpyHostToDevice, ctx->st));
+    for (int i = 0; i < nv; ++i)
+        spinor_to_internal<double>(ctx->protos + (size_t)i * n, ctx->protos_stage + (size_t)i * n, ctx->g, ctx->st);
+    CKL();
+    return ctx->prm.prec_inner == MG_FP32 ? setup_impl<float>(ctx) : setup_impl<double>(ctx);
+}
+
+int mg_setup_device(mg_ctx* ctx, const double* V0_dev) {
+    TRY(need_links(ctx));
+    if (!V0_dev) return fail(ctx, MG_ERR_INVALID_ARG, "V0 is NULL");
+    TRY(ensure_protos(ctx));
+    size_t n = nfine(ctx);
+    for (int i = 0; i < ctx->prm.nvec; ++i)
+        spinor_to_internal<double>(ctx->protos + (size_t)i * n, (const double2*)V0_dev + (size_t)i * n, ctx->g, ctx->st);
+    CKL();
+    return ctx->prm.prec_inner == MG_FP32 ? setup_impl<float>(ctx) : setup_impl<double>(ctx);
+}
+
+int mg_set_null_vectors(mg_ctx* ctx, const double* V, int nv) {
+    TRY(need_links(ctx));
+    if (!V || nv != ctx->prm.nvec) return fail(ctx, MG_ERR_INVALID_ARG, "nv must equal params.nvec");
+    TRY(ensure_protos(ctx));
+    size_t n = nfine(ctx);
+    CK(cudaMemcpyAsync(ctx->protos_stage, V, sizeof(double2) * n * nv, cudaMemcpyHostToDevice, ctx->st));
+    for (int i = 0; i < nv; ++i)
+        spinor_to_internal<double>(ctx->protos + (size_t)i * n, ctx->protos_stage + (size_t)i * n, ctx->g, ctx->st);
+    CKL();
+    return build_level(ctx, ctx->full, ctx->protos, nv);
+}
+
+int mg_get_prolongator(mg_ctx* ctx, double* P) {
+    TRY(need_level(ctx));
+    if (!P) return MG_ERR_INVALID_ARG;
+    size_t n = nfine(ctx);
+    prolongator_to_boundary(ctx->protos_stage, ctx->full.P64, ctx->full.nv, ctx->g, ctx->st);
+    CKL();
+    CK(cudaMemcpyAsync(P, ctx->protos_stage, sizeof(double2) * n * ctx->full.nv, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return MG_OK;
+}
+
+int mg_get_null_vectors(mg_ctx* ctx, double* V) {
+    TRY(need_links(ctx));
+    if (!V || !ctx->protos) return fail(ctx, MG_ERR_NOT_SETUP, "no prototypes");
+    size_t n = nfine(ctx);
+    for (int i = 0; i < ctx->prm.nvec; ++i)
+        spinor_from_internal<double>(ctx->protos_stage + (size_t)i * n, ctx->protos + (size_t)i * n, ctx->g, ctx->st);
+    CKL();
+    CK(cudaMemcpyAsync(V, ctx->protos_stage, sizeof(double2) * n * ctx->prm.nvec, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return MG_OK;
+}
+
+int mg_get_coarse_op(mg_ctx* ctx, double* A) {
+    TRY(need_level(ctx));
+    if (!A) return MG_ERR_INVALID_ARG;
+    int nc = ctx->full.nc;
+    coarse_op_transpose(ctx->cstage, ctx->full.A64, nc, ctx->g.Vc, ctx->st);
+    CKL();
+    CK(cudaMemcpyAsync(A, ctx->cstage, sizeof(double2) * (size_t)ctx->g.Vc * 9 * nc * nc, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return MG_OK;
+}
+
+int mg_solve_device(mg_ctx* ctx, const double* b_dev, double* x_dev, mg_solve_info* info) {
+    TRY(need_level(ctx));
+    if (!b_dev || !x_dev) return fail(ctx, MG_ERR_INVALID_ARG, "null vector");
+    spinor_to_internal<double>(ctx->b64, (const double2*)b_dev, ctx->g, ctx->st);
+    CKL();
+    int st = ctx->prm.prec_inner == MG_FP32 ? gcr_solve<float>(ctx, info) : gcr_solve<double>(ctx, info);
+    if (st != MG_OK && st != MG_ERR_NOT_CONVERGED) return st;
+    spinor_from_internal<double>((double2*)x_dev, ctx->x64, ctx->g, ctx->st);
+    CKL();
+    CK(cudaStreamSynchronize(ctx->st));
+    return st;
+}
+
+int mg_solve(mg_ctx* ctx, const double* b, double* x, mg_solve_info* info) {
+    TRY(need_level(ctx));
+    if (!b || !x) return fail(ctx, MG_ERR_INVALID_ARG, "null vector");
+    size_t n = nfine(ctx);
+    CK(cudaMemcpyAsync(ctx->stage_a, b, sizeof(double2) * n, cudaMemcpyHostToDevice, ctx->st));
+    int st = mg_solve_device(ctx, (const double*)ctx->stage_a, (double*)ctx->stage_b, info);
+    if (st != MG_OK && st != MG_ERR_NOT_CONVERGED) return st;
+    CK(cudaMemcpyAsync(x, ctx->stage_b, sizeof(double2) * n, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return st;
+}
+
+int mg_apply_dslash(mg_ctx* ctx, const double* in, double* out, int prec) {
+    TRY(need_links(ctx));
+    if (!in || !out) return MG_ERR_INVALID_ARG;
+    return prec == MG_FP32 ? hook_dslash<float>(ctx, in, out) : hook_dslash<double>(ctx, in, out);
+}
+int mg_restrict(mg_ctx* ctx, const double* r, double* rc, int prec) {
+    TRY(need_level(ctx));
+    if (!r || !rc) return MG_ERR_INVALID_ARG;
+    return prec == MG_FP32 ? hook_restrict<float>(ctx, r, rc) : hook_restrict<double>(ctx, r, rc);
+}
+int mg_prolong(mg_ctx* ctx, const double* yc, double* e, int prec) {
+    TRY(need_level(ctx));
+    if (!yc || !e) return MG_ERR_INVALID_ARG;
+    return prec == MG_FP32 ? hook_prolong<float>(ctx, yc, e) : hook_prolong<double>(ctx, yc, e);
+}
+int mg_apply_coarse(mg_ctx* ctx, const double* x, double* y, int dagger, int prec) {
+    TRY(need_level(ctx));
+    if (!x || !y) return MG_ERR_INVALID_ARG;
+    return prec == MG_FP32 ? hook_coarse<float>(ctx, x, y, dagger) : hook_coarse<double>(ctx, x, y, dagger);
+}
+int mg_mr(mg_ctx* ctx, double* e, double* r, int nsteps, int prec) {
+    TRY(need_links(ctx));
+    if (!e || !r || nsteps < 0) return MG_ERR_INVALID_ARG;
+    return prec == MG_FP32 ? hook_mr<float>(ctx, e, r, nsteps) : hook_mr<double>(ctx, e, r, nsteps);
+}
+int mg_coarse_solve(mg_ctx* ctx, const double* rc, double* y, double tol, int maxit, int prec, int* iters,
+                    double* final_rel) {
+    TRY(need_level(ctx));
+    if (!rc || !y || maxit < 0) return MG_ERR_INVALID_ARG;
+    return prec == MG_FP32 ? hook_coarse_solve<float>(ctx, rc, y, tol, maxit, iters, final_rel)
+                           : hook_coarse_solve<double>(ctx, rc, y, tol, maxit, iters, final_rel);
+}
+int mg_vcycle(mg_ctx* ctx, const double* r, double* z, int prec) {
+    TRY(need_level(ctx));
+    if (!r || !z) return MG_ERR_INVALID_ARG;
+    return prec == MG_FP32 ? hook_vcycle<float>(ctx, r, z) : hook_vcycle<double>(ctx, r, z);
+}
+
+int mg_time_dslash(mg_ctx* ctx, int prec, int reps, double* ms_per_launch, double* bytes_per_launch) {
+    TRY(need_links(ctx));
+    if (reps <= 0 || !ms_per_launch) return MG_ERR_INVALID_ARG;
+    size_t real = prec == MG_FP32 ? 4 : 8;
+    // algorithmic minimum: 4 links x 18 reals + input 24 reals + output 24 reals per site
+    if (bytes_per_launch) *bytes_per_launch = (double)ctx->g.V * (72 + 24 + 24) * real;
+    auto run = [&](auto tag) -> int {
+        using T = decltype(tag);
+        TRY(ensure_work<T>(ctx));
+        Work<T>& w = work<T>(ctx);
+        const v2<T>* U = links<T>(ctx);
+        for (int i = 0; i < 3; ++i)
+            dslash<T>(DS_PLAIN, w.tout, w.tin, U, w.tin, ctx->g, ctx->mass, 0.0, 0, ctx->R, ctx->st);
+        CK(cudaEventRecord(ctx->ev0, ctx->st));
+        for (int i = 0; i < reps; ++i)
+            dslash<T>(DS_PLAIN, (i & 1) ? w.tin : w.tout, (i & 1) ? w.tout : w.tin, U, w.tin, ctx->g, ctx->mass, 0.0, 0,
+                      ctx->R, ctx->st);
+        CK(cudaEventRecord(ctx->ev1, ctx->st));
+        CKL();
+        CK(cudaEventSynchronize(ctx->ev1));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+        *ms_per_launch = ms / reps;
+        return MG_OK;
+    };
+    return prec == MG_FP32 ? run(float{}) : run(double{});
+}
+
+const char* mg_status_string(int status) {
+    int i = -status;
+    if (i < 0 || i >= (int)(sizeof(kStatusNames) / sizeof(kStatusNames[0]))) return "MG_ERR_UNKNOWN";
+    return kStatusNames[i];
+}
+
+const char* mg_last_error(const mg_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+}  // extern "C"

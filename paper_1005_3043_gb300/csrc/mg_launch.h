@@ -1,0 +1,89 @@
+// Host-side launchers of the library's kernels (internal, not part of the C-ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include "mg_common.cuh"
+
+namespace wmg {
+
+// Scratch used by the single-pass grid reductions: per-block partial sums and
+// an arrival counter that the last block resets to zero.
+struct Reduce {
+    double* partials;      // >= kMaxReduceBlocks * 64 doubles
+    unsigned int* ticket;  // one zeroed counter
+    double* scal;          // device scalars, S_COUNT doubles (ScalarSlot)
+};
+constexpr int kMaxReduceBlocks = 1216;   // 152 SMs x 8
+
+// ---------------------------------------------------------------- layout conversion
+template <typename T> void spinor_to_internal(v2<T>* out, const double2* in_lex, const Geom& g, cudaStream_t st);
+template <typename T> void spinor_from_internal(double2* out_lex, const v2<T>* in, const Geom& g, cudaStream_t st);
+template <typename T> void links_to_internal(v2<T>* out, const double2* in_lex, const Geom& g, cudaStream_t st);
+template <typename Tin, typename Tout> void convert(v2<Tout>* out, const v2<Tin>* in, size_t n, cudaStream_t st);
+
+// ---------------------------------------------------------------- fine operator (eq. 2)
+enum DslashMode { DS_PLAIN = 0, DS_XMY = 1, DS_XMY_NORM = 2, DS_MRDOT = 3 };
+// DS_PLAIN:     out = D in
+// DS_XMY:       out = src - D in
+// DS_XMY_NORM:  out = src - D in, scal[slot] = ||out||^2
+// DS_MRDOT:     out = D in, scal[S_MR_ALPHA] = omega <out,in> / <out,out>
+template <typename T>
+void dslash(int mode, v2<T>* out, const v2<T>* in, const v2<T>* U, const v2<T>* src, const Geom& g, double mass,
+            double omega, int slot, const Reduce& R, cudaStream_t st);
+
+// ---------------------------------------------------------------- fine / generic BLAS (n complex)
+template <typename T> void zero(v2<T>* x, size_t n, cudaStream_t st);
+template <typename T> void norm2(const v2<T>* x, size_t n, int slot, const Reduce& R, cudaStream_t st);
+template <typename T> void dot(const v2<T>* x, const v2<T>* y, size_t n, int slot, const Reduce& R, cudaStream_t st);
+template <typename T> void scale(v2<T>* x, size_t n, double s, cudaStream_t st);
+// y += a x with a a host constant
+template <typename T> void axpy(v2<T>* y, const v2<T>* x, size_t n, double ar, double ai, cudaStream_t st);
+// MR update: e += alpha r; r -= alpha q (if update_r), alpha = scal[S_MR_ALPHA]
+template <typename T>
+void mr_update(v2<T>* e, v2<T>* r, const v2<T>* q, size_t n, bool update_r, const Reduce& R, cudaStream_t st);
+// normalise x in place by 1/sqrt(scal[slot])
+template <typename T> void normalize_dev(v2<T>* x, size_t n, int slot, const Reduce& R, cudaStream_t st);
+
+// ---------------------------------------------------------------- GCR (K_MAX basis vectors)
+// R[j][k] = <p_j, p_k> for j < k  (p_j = basis + j*n)
+template <typename T> void gcr_multidot(const v2<T>* basis, size_t n, int k, const Reduce& R, cudaStream_t st);
+// p_k -= sum_{j<k} R[j][k] p_j ; scal[S_GCR_PN2] = ||p_k||^2
+template <typename T> void gcr_orth_norm(v2<T>* basis, size_t n, int k, const Reduce& R, cudaStream_t st);
+// R[k][k] = ||p_k||; c_k = <p_k, r>/||p_k||
+template <typename T> void gcr_cdot(const v2<T>* basis, const v2<T>* r, size_t n, int k, const Reduce& R, cudaStream_t st);
+// p_k /= ||p_k||; r -= c_k p_k; scal[S_GCR_R2] = ||r||^2
+template <typename T> void gcr_update(v2<T>* basis, v2<T>* r, size_t n, int k, const Reduce& R, cudaStream_t st);
+// x (FP64) += sum_j y_j Z_j
+struct GcrCoef { double c[2 * K_MAX]; };
+template <typename T>
+void gcr_xupdate(double2* x, const v2<T>* Z, size_t n, int k, const GcrCoef& y, cudaStream_t st);
+
+// ---------------------------------------------------------------- transfer / coarse
+// P64[X][s][i][6][l] from prototypes V[i][X][12][l]; *status = 1 on rank deficiency
+void block_orthonormalize(double2* P, const double2* V, int nv, const Geom& g, int* d_status, cudaStream_t st);
+template <typename T> void restrict_(v2<T>* rc, const v2<T>* P, const v2<T>* r, int nv, const Geom& g, cudaStream_t st);
+template <typename T> void prolong(v2<T>* e, const v2<T>* P, const v2<T>* yc, int nv, const Geom& g, cudaStream_t st);
+// A64 (column-major blocks) = P^dag D P; Aself scratch of Vc*8*nc*nc complex
+void coarse_build(double2* A, double2* Aself, const double2* P, const double2* U, int nv, double mass, const Geom& g,
+                  cudaStream_t st);
+void coarse_shift_mass(double2* A, int nc, double dm, const Geom& g, cudaStream_t st);
+// y = D_c x (dag: sigma3 D_c sigma3 x); with slot >= 0 also scal[slot] = ||y||^2
+template <typename T>
+void coarse_apply(v2<T>* y, const v2<T>* A, const v2<T>* x, int nc, bool dag, int slot, const Geom& g, const Reduce& R,
+                  cudaStream_t st);
+// block-orthonormal prolongator to the boundary null-vector layout
+void prolongator_to_boundary(double2* out, const double2* P, int nv, const Geom& g, cudaStream_t st);
+// boundary <-> internal coarse operator ([X][d][a][b] row-major <-> [X][d][b][a])
+void coarse_op_transpose(double2* out, const double2* in, int nc, int Vc, cudaStream_t st);
+
+// CGNR (CGLS) on D_c with device-side control: the kernels become no-ops once
+// scal[S_CG_DONE] is set.
+template <typename T>
+void cg_init(v2<T>* y, v2<T>* r, const v2<T>* rc, size_t n, double tol, int maxit, const Reduce& R, cudaStream_t st);
+template <typename T>
+void cg_first_direction(v2<T>* s, v2<T>* p, const v2<T>* r, const v2<T>* A, int nc, const Geom& g, const Reduce& R,
+                        cudaStream_t st);
+template <typename T>
+void cg_step(v2<T>* y, v2<T>* r, v2<T>* s, v2<T>* p, v2<T>* q, const v2<T>* A, int nc, const Geom& g, const Reduce& R,
+             cudaStream_t st);
+
+}  // namespace wmg

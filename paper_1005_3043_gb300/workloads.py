@@ -1,0 +1,55 @@
+"""Synthetic workloads shaped like the paper's: quenched SU(3) fields at beta = 6.0
+(hot start, 200 x (1 Kennedy-Pendleton heatbath + 4 over-relaxation) sweeps),
+two-level MG with 4^4 aggregates.  They stand in for the anisotropic ensembles
+the paper measures on, which are not available here.
+
+Masses: D(m) = D(0) + m exactly, so m = target - Re(lambda_min(D(0))).  The
+Re(lambda_min(D(0))) values below were computed once per field with ARPACK
+(implicitly restarted Arnoldi, which='SR') on the FP64 Wilson operator by
+tests/golden/make_masses.py; the field is bitwise reproducible on x86-64 and
+aarch64, and its plaquette is stored to detect any difference.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    dims: tuple
+    block: tuple
+    nvec: int
+    seed: int                  # heatbath seed
+    re_lambda_min_m0: float    # Re lambda_min of D(m = 0) for this field
+    plaquette: float           # of the generated field (reproducibility check)
+    targets: tuple             # Re lambda_min(D(m)) values to solve at
+    setup_target: float        # Re lambda_min at which the adaptive setup runs
+    beta: float = 6.0
+    sweeps: int = 200
+    n_or: int = 4
+    source_seed: int = 7
+    setup_seed: int = 2001
+    extra: dict = field(default_factory=dict)
+
+    def masses(self):
+        return [t - self.re_lambda_min_m0 for t in self.targets]
+
+    def setup_mass(self):
+        return self.setup_target - self.re_lambda_min_m0
+
+
+WILSON_8x8x8x8 = Workload(
+    name="wilson_8x8x8x8_nv8_beta6",
+    dims=(8, 8, 8, 8), block=(4, 4, 4, 4), nvec=8, seed=1001,
+    re_lambda_min_m0=0.7985754005, plaquette=0.593627332231,
+    targets=(0.01,), setup_target=0.01)
+
+# 16^3 x 32, Nv = 20, masses swept toward critical (log-spaced Re lambda_min)
+WILSON_16x16x16x32 = Workload(
+    name="wilson_16x16x16x32_nv20_beta6_5mass",
+    dims=(16, 16, 16, 32), block=(4, 4, 4, 4), nvec=20, seed=2001,
+    re_lambda_min_m0=float("nan"), plaquette=float("nan"),
+    targets=(0.01, 0.0056, 0.0032, 0.0018, 0.001), setup_target=0.001)
+
+WORKLOADS = {w.name: w for w in (WILSON_8x8x8x8, WILSON_16x16x16x32)}

@@ -1,0 +1,54 @@
+"""The C-ABI library loads on a machine without a GPU and exports every entry
+point that include/wilson_mg.h declares (no compute calls here)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_1005_3043_gb300 as wmg
+from paper_1005_3043_gb300 import build as wbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))]
+
+
+def declared_functions():
+    names = set()
+    for h in HEADERS:
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?(?:int|void|char|double)\s*\**\s*(mg_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    wbuild.build()
+    return wmg.load()
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    assert {"mg_create", "mg_destroy", "mg_set_links", "mg_set_mass", "mg_setup", "mg_solve"} <= names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", wbuild.LIB], capture_output=True, text=True, check=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if " T " in ln}
+    missing = declared_functions() - exported
+    assert not missing, f"declared but not exported: {sorted(missing)}"
+    for name in declared_functions():
+        assert hasattr(lib, name)
+
+
+def test_binding_covers_every_declared_symbol():
+    assert declared_functions() <= set(wmg.EXPORTED)
+
+
+def test_host_only_calls(lib):
+    p = wmg.mg_default_params()
+    assert p.nvec == 8 and tuple(p.block) == (4, 4, 4, 4) and p.omega == 0.9 and p.tol == 1e-10
+    assert wmg.status_string(0) == "MG_OK"
+    assert wmg.status_string(wmg.MG_ERR_NUMERIC) == "MG_ERR_NUMERIC"

@@ -1,0 +1,275 @@
+"""GPU (CUDA, through the C-ABI) against the FP64 CPU oracle on identical seeded
+inputs.  Tolerances: 1e-12 relative for FP64 single operator applications,
+1e-5 for FP32; every solve reaches a true FP64 relative residual <= 1e-10,
+recomputed here with the oracle's own operator."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1005_3043_gb300 as wmg
+import synth
+from tests._fields import c1_workload, rough_gauge
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-5
+
+
+def maxrel(a, b):
+    """max elementwise |a-b| relative to max |b| (elementwise comparison)."""
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300))
+
+
+def make_params(nv, B=(4, 4, 4, 4), **kw):
+    p = wmg.mg_default_params()
+    for i in range(4):
+        p.block[i] = B[i]
+    p.nvec = nv
+    p.setup_group = kw.pop("setup_group", min(4, nv))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    wmg.build.build()
+    wmg.load()
+
+
+# lattices: several 256-site tiles, a ragged grid tail, non-cubic extents, degenerate coarse extents
+DSLASH_CASES = [
+    ((8, 8, 8, 8), (4, 4, 4, 4)),
+    ((4, 4, 4, 4), (4, 4, 4, 4)),          # one block, coarse extent 1
+    ((6, 4, 2, 10), (2, 2, 2, 2)),         # V = 480: ragged last thread block
+    ((4, 8, 4, 12), (2, 4, 2, 4)),
+]
+
+
+@pytest.mark.parametrize("L,B", DSLASH_CASES)
+def test_dslash_parity(L, B):
+    U = rough_gauge(L, seed=3)
+    psi = synth.gaussian_spinor(L, 17)
+    m = -0.42
+    ref = oracle.dslash(U, psi, m, L)
+    with wmg.WilsonMG(L, make_params(2, B)) as mg:
+        mg.set_links(U)
+        mg.set_mass(m)
+        assert maxrel(mg.dslash(psi, wmg.MG_FP64), ref) < TOL64
+        assert maxrel(mg.dslash(psi, wmg.MG_FP32), ref) < TOL32
+
+
+def test_dslash_periodic_t_and_free_field():
+    L, B = (4, 4, 4, 8), (2, 2, 2, 2)
+    U = synth.unit_gauge(L)
+    psi = synth.gaussian_spinor(L, 5)
+    with wmg.WilsonMG(L, make_params(1, B), t_antiperiodic=0) as mg:
+        mg.set_links(U)
+        mg.set_mass(0.3)
+        assert maxrel(mg.dslash(psi), oracle.dslash(U, psi, 0.3, L, tap=0)) < TOL64
+
+
+def _level(L, B, nv, seed=21, m=-0.2, sweeps=3):
+    U = rough_gauge(L, seed=seed, sweeps=sweeps)
+    V0 = synth.gaussian_vectors(L, nv, seed + 100)
+    P, st = oracle.block_orthonormalize(V0, L, B)
+    assert st == 0
+    A = oracle.coarse_build(U, P, m, L, B)
+    return U, V0, P, A
+
+
+@pytest.mark.parametrize("L,B,nv", [((8, 8, 8, 8), (4, 4, 4, 4), 4),
+                                    ((4, 4, 4, 8), (2, 2, 2, 4), 3),
+                                    ((4, 4, 4, 4), (4, 4, 4, 4), 2)])
+def test_block_ortho_restrict_prolong_coarse_parity(L, B, nv):
+    m = -0.2
+    U, V0, P, A = _level(L, B, nv, m=m)
+    Lc = oracle.coarse_dims(L, B)
+    Vc = oracle.volume(Lc)
+    with wmg.WilsonMG(L, make_params(nv, B)) as mg:
+        mg.set_links(U)
+        mg.set_mass(m)
+        mg.set_null_vectors(V0)
+        assert maxrel(mg.prolongator(), P) < TOL64
+        assert maxrel(mg.coarse_op(), A) < TOL64
+        r = synth.gaussian_spinor(L, 33)
+        rc_ref = oracle.restrict(P, r, L, B)
+        assert maxrel(mg.restrict(r), rc_ref) < TOL64
+        assert maxrel(mg.restrict(r, wmg.MG_FP32), rc_ref) < TOL32
+        y = synth.gaussian(Vc * 2 * nv, 34, 0).reshape(Vc, 2 * nv)
+        e_ref = oracle.prolong(P, y, L, B)
+        assert maxrel(mg.prolong(y), e_ref) < TOL64
+        assert maxrel(mg.prolong(y, wmg.MG_FP32), e_ref) < TOL32
+        c_ref = oracle.coarse_apply(A, y, Lc)
+        cd_ref = oracle.coarse_apply_dag(A, y, Lc)
+        assert maxrel(mg.coarse(y), c_ref) < TOL64
+        assert maxrel(mg.coarse(y, dagger=True), cd_ref) < TOL64
+        assert maxrel(mg.coarse(y, prec=wmg.MG_FP32), c_ref) < TOL32
+        assert maxrel(mg.coarse(y, dagger=True, prec=wmg.MG_FP32), cd_ref) < TOL32
+        # mass change shifts the coarse diagonal exactly (P^dag P = I)
+        mg.set_mass(m + 0.05)
+        assert maxrel(mg.coarse_op(), oracle.coarse_build(U, P, m + 0.05, L, B)) < TOL64
+
+
+def test_mr_parity():
+    L = (8, 4, 4, 8)
+    U = rough_gauge(L, seed=4)
+    m, w = -0.3, 0.9
+    e = synth.gaussian_spinor(L, 1)
+    r = synth.gaussian_spinor(L, 2)
+    e_ref, r_ref = oracle.mr(U, e, r, m, L, 4, w)
+    with wmg.WilsonMG(L, make_params(2, (4, 4, 4, 4))) as mg:
+        mg.set_links(U)
+        mg.set_mass(m)
+        e64, r64 = mg.mr(e, r, 4)
+        assert maxrel(e64, e_ref) < TOL64 and maxrel(r64, r_ref) < TOL64
+        e32, r32 = mg.mr(e, r, 4, wmg.MG_FP32)
+        assert maxrel(e32, e_ref) < 1e-4 and maxrel(r32, r_ref) < 1e-4
+
+
+def test_coarse_solve_parity():
+    L, B, nv = (8, 8, 8, 8), (4, 4, 4, 4), 4
+    m = -0.2
+    U, V0, P, A = _level(L, B, nv, m=m)
+    Lc = oracle.coarse_dims(L, B)
+    rc = synth.gaussian(oracle.volume(Lc) * 2 * nv, 8, 0).reshape(-1, 2 * nv)
+    with wmg.WilsonMG(L, make_params(nv, B)) as mg:
+        mg.set_links(U)
+        mg.set_mass(m)
+        mg.set_null_vectors(V0)
+        for k in (1, 7, 25):                         # fixed iteration counts (tol = 0)
+            y_ref, it_ref, _ = oracle.cgnr(A, rc, Lc, 0.0, k)
+            y, it, _ = mg.coarse_solve(rc, 0.0, k)
+            assert it == it_ref == k
+            assert maxrel(y, y_ref) < 1e-10
+        y_ref, it_ref, rel_ref = oracle.cgnr(A, rc, Lc, 1e-3, 5000)
+        y, it, rel = mg.coarse_solve(rc, 1e-3, 5000)
+        assert rel <= 1e-3 and abs(it - it_ref) <= 1
+        y32, it32, rel32 = mg.coarse_solve(rc, 1e-3, 5000, wmg.MG_FP32)
+        assert rel32 <= 1e-3
+
+
+def test_vcycle_parity():
+    L, B, nv = (8, 8, 8, 8), (4, 4, 4, 4), 4
+    m = -0.2
+    U, V0, P, A = _level(L, B, nv, m=m)
+    r = synth.gaussian_spinor(L, 12)
+    po = oracle.make_params(L, B, nv=nv, m=m, coarse_tol=0.0, coarse_maxit=30)
+    z_ref, _ = oracle.vcycle(po, U, P, A, r)
+    with wmg.WilsonMG(L, make_params(nv, B, coarse_tol=0.0, max_coarse=30)) as mg:
+        mg.set_links(U)
+        mg.set_mass(m)
+        mg.set_null_vectors(V0)
+        assert maxrel(mg.vcycle(r), z_ref) < 1e-10
+        assert maxrel(mg.vcycle(r, wmg.MG_FP32), z_ref) < 1e-4
+
+
+def _true_rel(U, x, b, m, L):
+    return np.linalg.norm(b - oracle.dslash(U, x, m, L)) / np.linalg.norm(b)
+
+
+@pytest.fixture(scope="module")
+def c1():
+    L, B, nv, U, m = c1_workload()
+    V0 = synth.gaussian_vectors(L, nv, 2001)
+    po = oracle.make_params(L, B, nv=nv, m=m)
+    Vs, P, A, st = oracle.setup(po, U, V0, init_relax=10, n_iter=3, group_size=4)
+    assert st == 0
+    return dict(L=L, B=B, nv=nv, U=U, m=m, V0=V0, Vs=Vs, P=P, A=A, po=po)
+
+
+def test_solve_fp64_matches_oracle(c1):
+    L, B, nv, U, m = c1["L"], c1["B"], c1["nv"], c1["U"], c1["m"]
+    b = synth.gaussian_spinor(L, 7)
+    x_ref, info_ref = oracle.gcr_solve(c1["po"], U, c1["P"], c1["A"], b)
+    with wmg.WilsonMG(L, make_params(nv, B)) as mg:
+        mg.set_links(U)
+        mg.set_mass(m)
+        mg.set_null_vectors(c1["Vs"])
+        x, info = mg.solve(b)
+    assert info["status"] == 0 and info_ref["status"] == 0
+    assert _true_rel(U, x, b, m, L) <= 1e-10
+    assert abs(info["true_rel_res"] - _true_rel(U, x, b, m, L)) < 1e-12
+    assert abs(info["outer_iters"] - info_ref["outer_iters"]) <= 2
+    assert np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref) < 1e-7
+
+
+def test_solve_fp32_inner_reaches_fp64_residual(c1):
+    L, B, nv, U, m = c1["L"], c1["B"], c1["nv"], c1["U"], c1["m"]
+    b = synth.gaussian_spinor(L, 7)
+    with wmg.WilsonMG(L, make_params(nv, B, prec_inner=wmg.MG_FP32, delta=1e-4)) as mg:
+        mg.set_links(U)
+        mg.set_mass(m)
+        mg.set_null_vectors(c1["Vs"])
+        x, info = mg.solve(b)
+    assert info["status"] == 0
+    assert _true_rel(U, x, b, m, L) <= 1e-10
+
+
+def test_setup_fp64_matches_oracle(c1):
+    L, B, nv, U, m = c1["L"], c1["B"], c1["nv"], c1["U"], c1["m"]
+    with wmg.WilsonMG(L, make_params(nv, B, setup_iters=3)) as mg:
+        mg.set_links(U)
+        mg.set_mass(m)
+        mg.setup(c1["V0"])
+        Vg = mg.null_vectors()
+        Pg = mg.prolongator()
+        Ag = mg.coarse_op()
+        b = synth.gaussian_spinor(L, 9)
+        x, info = mg.solve(b)
+    # same algorithm, FP64 on both sides: prototypes agree unless a coarse stopping
+    # test landed on the other side of its threshold
+    d = max(np.linalg.norm(Vg[i] - c1["Vs"][i]) for i in range(nv))
+    assert d < 1e-6
+    # invariants of the GPU setup output (eq. 4, chirality split, Galerkin D_c)
+    A_from_P = oracle.coarse_build(U, Pg, m, L, B)
+    assert maxrel(Ag, A_from_P) < 1e-12
+    assert info["status"] == 0 and _true_rel(U, x, b, m, L) <= 1e-10
+
+
+def test_mass_sweep_reuses_setup(c1):
+    L, B, nv, U, m = c1["L"], c1["B"], c1["nv"], c1["U"], c1["m"]
+    b = synth.gaussian_spinor(L, 11)
+    with wmg.WilsonMG(L, make_params(nv, B, prec_inner=wmg.MG_FP32, delta=1e-4)) as mg:
+        mg.set_links(U)
+        mg.set_mass(m)
+        mg.set_null_vectors(c1["Vs"])
+        iters = []
+        for mm in (m + 0.09, m + 0.04, m + 0.02, m):
+            mg.set_mass(mm)
+            x, info = mg.solve(b)
+            assert info["status"] == 0 and _true_rel(U, x, b, mm, L) <= 1e-10
+            iters.append(info["outer_iters"])
+    assert iters[0] <= iters[-1]
+
+
+def test_edge_cases(c1):
+    L, B, nv, U, m = c1["L"], c1["B"], c1["nv"], c1["U"], c1["m"]
+    with wmg.WilsonMG(L, make_params(nv, B)) as mg:
+        with pytest.raises(wmg.MGError) as ei:
+            mg.solve(np.zeros((mg.V, 4, 3)))         # no links yet
+        assert ei.value.status == wmg.MG_ERR_NOT_SETUP
+        mg.set_links(U)
+        mg.set_mass(m)
+        bad = c1["Vs"].copy()
+        bad[1] = bad[0] * 2.0                         # rank-deficient prototypes
+        with pytest.raises(wmg.MGError) as ei:
+            mg.set_null_vectors(bad)
+        assert ei.value.status == wmg.MG_ERR_NUMERIC
+        mg.set_null_vectors(c1["Vs"])
+        x, info = mg.solve(np.zeros((mg.V, 4, 3)))    # b = 0
+        assert info["status"] == 0 and np.abs(x).max() == 0
+        p = make_params(nv, B, max_outer=2)
+        mg.set_params(p)
+        x, info = mg.solve(synth.gaussian_spinor(L, 3))
+        assert info["status"] == wmg.MG_ERR_NOT_CONVERGED and info["outer_iters"] == 2
+        mg.set_params(make_params(nv, B))
+        b = synth.gaussian_spinor(L, 3)
+        b[5, 1, 2] = np.nan
+        with pytest.raises(wmg.MGError) as ei:
+            mg.solve(b)
+        assert ei.value.status == wmg.MG_ERR_NUMERIC
+    with pytest.raises(wmg.MGError) as ei:
+        wmg.WilsonMG((8, 8, 8, 6), make_params(nv, B))   # 6 not divisible by 4
+    assert ei.value.status == wmg.MG_ERR_INVALID_ARG
