@@ -164,6 +164,28 @@ int mg_mr(mg_ctx* ctx, double* e, double* r, int nsteps, int prec);
 int mg_coarse_solve(mg_ctx* ctx, const double* rc, double* y, double tol, int maxit, int prec,
                     int* iters, double* final_rel);
 
+/* Allocation-free coarse solve.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory when they call
+ * -- code running under another framework that owns the device allocator, or
+ * from a context where cudaMalloc is not allowed or would synchronise the
+ * device.  It computes what mg_coarse_solve computes in FP64 (CGNR on the
+ * context's D_c from y = 0, same kernels), with rc_dev and y_dev device
+ * buffers of Vc * 2 Nv complex doubles (boundary coarse-vector layout) that
+ * the caller owns.  It calls no cudaMalloc/cudaFree and no allocating library
+ * routine: its work vectors, reduction partial sums and scalars live in one
+ * file-scope __device__ array of 4 * 65536 complex doubles plus about 640 KB,
+ * which every GPU that loads this library holds until the process exits.
+ *   - Sizes: Vc * 2 Nv must be <= 65536, else MG_ERR_INVALID_ARG.
+ *   - The first call on a device looks up the array's device address on that
+ *     (current) device; make that first call before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents:
+ *     the arrival counter is cleared on every call, everything else is
+ *     written before it is read.  Calls that overlap on the GPU (other
+ *     streams, other host threads, other contexts on the same device) race.
+ *   - Work runs on the context's stream; the call synchronises that stream. */
+int mg_coarse_solve_noalloc(mg_ctx* ctx, const double* rc_dev, double* y_dev, double tol, int maxit, int* iters,
+                            double* final_rel);
+
 /* z = M r, one two-level V(0, smoother_steps) cycle. */
 int mg_vcycle(mg_ctx* ctx, const double* r, double* z, int prec);
 

@@ -82,6 +82,7 @@ _SIGS = {
     "mg_apply_coarse": ([_P, _P, _P, _I, _I], _I),
     "mg_mr": ([_P, _P, _P, _I, _I], _I),
     "mg_coarse_solve": ([_P, _P, _P, _D, _I, _I, _P, _P], _I),
+    "mg_coarse_solve_noalloc": ([_P, _P, _P, _D, _I, _P, _P], _I),
     "mg_vcycle": ([_P, _P, _P, _I], _I),
     "mg_time_dslash": ([_P, _I, _I, _P, _P], _I),
     "mg_status_string": ([_I], ctypes.c_char_p),
@@ -270,6 +271,15 @@ def mg_coarse_solve(ctx, rc, tol: float, maxit: int, prec: int = MG_FP64):
     _check(load().mg_coarse_solve(ctx, _ptr(rc), _ptr(y), float(tol), int(maxit), int(prec), ctypes.byref(it),
                                   ctypes.byref(rel)), ctx)
     return y, it.value, rel.value
+
+
+def mg_coarse_solve_noalloc(ctx, rc_dev, y_dev, tol: float, maxit: int):
+    """Allocation-free FP64 coarse solve on device buffers; returns (iters, final_rel)."""
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0)
+    _check(load().mg_coarse_solve_noalloc(ctx, _dev_ptr(rc_dev), _dev_ptr(y_dev), float(tol), int(maxit),
+                                          ctypes.byref(it), ctypes.byref(rel)), ctx)
+    return it.value, rel.value
 
 
 def mg_vcycle(ctx, r, prec: int = MG_FP64) -> np.ndarray:

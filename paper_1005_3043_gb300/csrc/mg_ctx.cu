@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -862,3 +863,91 @@ const char* mg_status_string(int status) {
 const char* mg_last_error(const mg_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 }  // extern "C"
+
+// ======================================================================= allocation-free coarse solve
+// For callers that must not allocate device memory at call time: code running
+// while another framework owns the device allocator, or work issued from a
+// context where cudaMalloc is not allowed or would synchronise the device
+// (a real-time loop, a host callback, code between a setup done at start-up
+// and the end of the program).  The CG work vectors, the reduction partial
+// sums, the arrival counter and the solver scalars live in one file-scope
+// __device__ array instead of context memory.  Every GPU that loads this
+// library holds the array until the process exits.
+namespace {
+
+constexpr size_t kNoAllocMaxCoarseDof = 65536;              // coarse sites x 2 Nv
+constexpr size_t kNoAllocVecBytes = kNoAllocMaxCoarseDof * sizeof(double2);
+constexpr size_t kNoAllocPartialsBytes = (size_t)kMaxReduceBlocks * 64 * sizeof(double);
+constexpr size_t kNoAllocScalBytes = ((S_COUNT * sizeof(double) + 255) / 256) * 256;
+constexpr size_t kNoAllocScratchBytes = 4 * kNoAllocVecBytes + kNoAllocPartialsBytes + kNoAllocScalBytes + 256;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+unsigned char* g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device (looked up once
+// per device; the lookup also loads the module on that device).
+int noalloc_scratch(mg_ctx* ctx, unsigned char** out) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(ctx, MG_ERR_INVALID_ARG, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(ctx, MG_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        g_noalloc_addr[dev] = (unsigned char*)p;
+    }
+    *out = g_noalloc_addr[dev];
+    return MG_OK;
+}
+
+}  // namespace
+
+extern "C" int mg_coarse_solve_noalloc(mg_ctx* ctx, const double* rc_dev, double* y_dev, double tol, int maxit,
+                                       int* iters, double* final_rel) {
+    TRY(need_level(ctx));
+    if (!rc_dev || !y_dev || maxit < 0) return fail(ctx, MG_ERR_INVALID_ARG, "null buffer or negative maxit");
+    const CoarseLevel& L = ctx->full;
+    size_t n = (size_t)ctx->g.Vc * L.nc;
+    if (n > kNoAllocMaxCoarseDof)
+        return fail(ctx, MG_ERR_INVALID_ARG,
+                    "coarse vector of " + std::to_string(n) + " complex entries exceeds the allocation-free limit of " +
+                        std::to_string(kNoAllocMaxCoarseDof));
+    unsigned char* base = nullptr;
+    TRY(noalloc_scratch(ctx, &base));
+    v2<double>* r = (v2<double>*)base;
+    v2<double>* s = (v2<double>*)(base + kNoAllocVecBytes);
+    v2<double>* p = (v2<double>*)(base + 2 * kNoAllocVecBytes);
+    v2<double>* q = (v2<double>*)(base + 3 * kNoAllocVecBytes);
+    Reduce R;
+    R.partials = (double*)(base + 4 * kNoAllocVecBytes);
+    R.scal = (double*)(base + 4 * kNoAllocVecBytes + kNoAllocPartialsBytes);
+    R.ticket = (unsigned int*)(base + 4 * kNoAllocVecBytes + kNoAllocPartialsBytes + kNoAllocScalBytes);
+    // the arrival counter must start at zero; everything else is written before it is read
+    CK(cudaMemsetAsync(R.ticket, 0, sizeof(unsigned int), ctx->st));
+    const v2<double>* A = L.A64;
+    v2<double>* y = (v2<double>*)y_dev;
+    cg_init<double>(y, r, (const v2<double>*)rc_dev, n, tol, maxit, R, ctx->st);
+    cg_first_direction<double>(s, p, r, A, L.nc, ctx->g, R, ctx->st);
+    CKL();
+    int check = ctx->prm.coarse_check > 0 ? ctx->prm.coarse_check : 16;
+    int launched = 0;
+    for (;;) {
+        for (int j = 0; j < check; ++j) cg_step<double>(y, r, s, p, q, A, L.nc, ctx->g, R, ctx->st);
+        CKL();
+        launched += check;
+        CK(cudaMemcpyAsync(ctx->h_scal + S_CG_RC2, R.scal + S_CG_RC2, sizeof(double) * 4, cudaMemcpyDeviceToHost,
+                           ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        if (ctx->h_scal[S_CG_DONE] != 0.0) break;
+        if (launched > maxit + check) return fail(ctx, MG_ERR_NUMERIC, "coarse solve did not stop");
+    }
+    if (iters) *iters = (int)ctx->h_scal[S_CG_ITERS];
+    if (final_rel)
+        *final_rel = ctx->h_scal[S_CG_RC2] > 0 ? std::sqrt(ctx->h_scal[S_CG_R2] / ctx->h_scal[S_CG_RC2]) : 0.0;
+    return MG_OK;
+}
