@@ -195,6 +195,32 @@ int mg_vcycle(mg_ctx* ctx, const double* r, double* z, int prec);
  * at minimum (algorithmic: links + input + output, each read/written once). */
 int mg_time_dslash(mg_ctx* ctx, int prec, int reps, double* ms_per_launch, double* bytes_per_launch);
 
+/* Kernel classes for the launch timer below. */
+enum mg_kernel_class {
+    MG_K_DSLASH = 0,       /* fine Wilson operator, all variants and precisions */
+    MG_K_COARSE_SOLVE = 1, /* persistent CGNR on D_c (whole coarse solve per launch) */
+    MG_K_RESTRICT = 2,
+    MG_K_PROLONG = 3,
+    MG_K_BLOCK_ORTHO = 4,
+    MG_K_COARSE_BUILD = 5,
+    MG_K_KRYLOV = 6,       /* GCR orthogonalisation, updates, norms, MR updates */
+    MG_K_TRUE_RESIDUAL = 7,/* FP64 b - D x at GCR restarts */
+    MG_K_NCLASSES = 8
+};
+
+/* Launch timer: while enabled, every launch of a tracked kernel class is
+ * bracketed by CUDA events on the context stream (negligible device cost).
+ * mg_profile_read synchronises the stream and returns, per class, the summed
+ * device time (ms) and the launch count since the last read (then resets);
+ * ms and launches point to MG_K_NCLASSES entries.  *coarse_iters receives
+ * the coarse CG iterations run since the last read (profiling on or off). */
+int mg_profile_enable(mg_ctx* ctx, int on);
+int mg_profile_read(mg_ctx* ctx, double* ms, int* launches, double* coarse_iters);
+
+/* Number of kernel launches this library has issued in the process so far
+ * (all contexts); the difference over a region counts its launches. */
+long long mg_kernel_launches(void);
+
 const char* mg_status_string(int status);
 const char* mg_last_error(const mg_ctx* ctx);
 

@@ -85,6 +85,9 @@ _SIGS = {
     "mg_coarse_solve_noalloc": ([_P, _P, _P, _D, _I, _P, _P], _I),
     "mg_vcycle": ([_P, _P, _P, _I], _I),
     "mg_time_dslash": ([_P, _I, _I, _P, _P], _I),
+    "mg_profile_enable": ([_P, _I], _I),
+    "mg_profile_read": ([_P, _P, _P, _P], _I),
+    "mg_kernel_launches": ([], ctypes.c_longlong),
     "mg_status_string": ([_I], ctypes.c_char_p),
     "mg_last_error": ([_P], ctypes.c_char_p),
 }
@@ -296,6 +299,28 @@ def mg_time_dslash(ctx, prec: int = MG_FP32, reps: int = 50):
     return ms.value, nbytes.value
 
 
+KERNEL_CLASSES = ("dslash", "coarse_solve", "restrict", "prolong", "block_ortho", "coarse_build", "krylov",
+                  "true_residual")
+
+
+def mg_kernel_launches() -> int:
+    return int(load().mg_kernel_launches())
+
+
+def mg_profile_enable(ctx, on: bool = True) -> None:
+    _check(load().mg_profile_enable(ctx, int(bool(on))), ctx)
+
+
+def mg_profile_read(ctx):
+    """({class: (total ms, launches)}, coarse CG iterations) since the last read."""
+    n = len(KERNEL_CLASSES)
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_int * n)()
+    cit = ctypes.c_double(0)
+    _check(load().mg_profile_read(ctx, ms, cnt, ctypes.byref(cit)), ctx)
+    return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_CLASSES)}, cit.value
+
+
 class WilsonMG:
     """Owning wrapper: ``with WilsonMG(dims, params) as mg: mg.set_links(U); ...``."""
 
@@ -379,6 +404,12 @@ class WilsonMG:
 
     def vcycle(self, r, prec=MG_FP64):
         return mg_vcycle(self.ctx, r, prec)
+
+    def profile_enable(self, on=True):
+        mg_profile_enable(self.ctx, on)
+
+    def profile_read(self):
+        return mg_profile_read(self.ctx)
 
     def time_dslash(self, prec=MG_FP32, reps=50):
         return mg_time_dslash(self.ctx, prec, reps)

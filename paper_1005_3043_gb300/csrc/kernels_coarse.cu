@@ -97,6 +97,7 @@ __global__ void __launch_bounds__(256) k_block_ortho(double2* __restrict__ P, co
 }
 
 void block_orthonormalize(double2* P, const double2* V, int nv, const Geom& g, int* d_status, cudaStream_t st) {
+    note_launch();
     k_block_ortho<<<2 * g.Vc, kThreads, 0, st>>>(P, V, nv, g, d_status);
 }
 
@@ -148,10 +149,12 @@ __global__ void __launch_bounds__(256) k_prolong(v2<T>* __restrict__ e, const v2
 
 template <typename T> void restrict_(v2<T>* rc, const v2<T>* P, const v2<T>* r, int nv, const Geom& g, cudaStream_t st) {
     size_t sm = sizeof(v2<T>) * 6 * g.Vb;
+    note_launch();
     k_restrict<T><<<2 * g.Vc, kThreads, sm, st>>>(rc, P, r, nv, g);
 }
 template <typename T> void prolong(v2<T>* e, const v2<T>* P, const v2<T>* yc, int nv, const Geom& g, cudaStream_t st) {
     long long total = g.V * 12;
+    note_launch();
     k_prolong<T><<<(int)((total + kThreads - 1) / kThreads), kThreads, 0, st>>>(e, P, yc, nv, g);
 }
 
@@ -164,11 +167,11 @@ template <typename T> void prolong(v2<T>* e, const v2<T>* P, const v2<T>* yc, in
 // to Aself[X][h] (summed later with the diagonal (4+m)).  FP64 throughout.
 constexpr int kBuildChunk = 8;
 
-template <int MU, bool FWD>
-__device__ __forceinline__ void hop_column(const cx<double> (&p)[4][3], const double2* __restrict__ u, int Vb,
-                                           double coef, cx<double> (&out)[4][3]) {
+template <typename TC, int MU, bool FWD>
+__device__ __forceinline__ void hop_column(const cx<TC> (&p)[4][3], const v2<TC>* __restrict__ u, int Vb, TC coef,
+                                           cx<TC> (&out)[4][3]) {
     // spin projection (same convention as the fine operator)
-    cx<double> h[2][3];
+    cx<TC> h[2][3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         if (MU == 0) {
@@ -185,19 +188,19 @@ __device__ __forceinline__ void hop_column(const cx<double> (&p)[4][3], const do
             h[1][c] = FWD ? p[1][c] - p[3][c] : p[1][c] + p[3][c];
         }
     }
-    cx<double> w[2][3];
+    cx<TC> w[2][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        w[0][a] = cx<double>(0, 0);
-        w[1][a] = cx<double>(0, 0);
+        w[0][a] = cx<TC>(0, 0);
+        w[1][a] = cx<TC>(0, 0);
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
             if (FWD) {
-                cx<double> uab = ld<double>(u + (3 * a + b) * Vb);
+                cx<TC> uab = ld<TC>(u + (3 * a + b) * Vb);
                 cmad(w[0][a], uab, h[0][b]);
                 cmad(w[1][a], uab, h[1][b]);
             } else {
-                cx<double> uba = ld<double>(u + (3 * b + a) * Vb);
+                cx<TC> uba = ld<TC>(u + (3 * b + a) * Vb);
                 cmadc(w[0][a], uba, h[0][b]);
                 cmadc(w[1][a], uba, h[1][b]);
             }
@@ -205,20 +208,22 @@ __device__ __forceinline__ void hop_column(const cx<double> (&p)[4][3], const do
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        cx<double> w0 = coef * w[0][c], w1 = coef * w[1][c];
+        cx<TC> w0 = coef * w[0][c], w1 = coef * w[1][c];
         out[0][c] = w0;
         out[1][c] = w1;
         if (MU == 0) { out[2][c] = FWD ? mul_i(w1) : mul_mi(w1); out[3][c] = FWD ? mul_i(w0) : mul_mi(w0); }
-        else if (MU == 1) { out[2][c] = FWD ? cx<double>(-w1.r, -w1.i) : w1; out[3][c] = FWD ? w0 : cx<double>(-w0.r, -w0.i); }
+        else if (MU == 1) { out[2][c] = FWD ? cx<TC>(-w1.r, -w1.i) : w1; out[3][c] = FWD ? w0 : cx<TC>(-w0.r, -w0.i); }
         else if (MU == 2) { out[2][c] = FWD ? mul_i(w0) : mul_mi(w0); out[3][c] = FWD ? mul_mi(w1) : mul_i(w1); }
-        else { out[2][c] = FWD ? cx<double>(-w0.r, -w0.i) : w0; out[3][c] = FWD ? cx<double>(-w1.r, -w1.i) : w1; }
+        else { out[2][c] = FWD ? cx<TC>(-w0.r, -w0.i) : w0; out[3][c] = FWD ? cx<TC>(-w1.r, -w1.i) : w1; }
     }
 }
 
-template <int MU, bool FWD>
-__device__ void build_hop(double2* __restrict__ A, double2* __restrict__ Aself, const double2* __restrict__ P,
-                          const double2* __restrict__ U, int nv, const Geom& g, int X, int h, double2* Wsh,
-                          double2* Psh, unsigned char* leaves) {
+// TC: precision of the products (double, or float with FP64 accumulation of
+// the per-chunk sums).
+template <typename TC, int MU, bool FWD>
+__device__ void build_hop(double2* __restrict__ A, double2* __restrict__ Aself, const v2<TC>* __restrict__ P,
+                          const v2<TC>* __restrict__ U, int nv, const Geom& g, int X, int h, v2<TC>* Wsh,
+                          v2<TC>* Psh, unsigned char* leaves) {
     const int nc = 2 * nv, len = 6 * g.Vb;
     const int npair = nc * nc;
     constexpr int kMaxPairs = 10;                      // nc <= 50 with 256 threads
@@ -238,24 +243,24 @@ __device__ void build_hop(double2* __restrict__ A, double2* __restrict__ Aself, 
             int Xn, ln;
             bool flip;
             neighbour(g, X, l, lc, xcX, MU, FWD ? 1 : -1, Xn, ln, flip);
-            if (b == 0) leaves[xi] = (Xn != X || (FWD ? lc[MU] == g.B[MU] - 1 : lc[MU] == 0)) ? 1 : 0;
+            if (b == 0) leaves[xi] = (FWD ? lc[MU] == g.B[MU] - 1 : lc[MU] == 0) ? 1 : 0;
             int sb = b / nv, ib = b - sb * nv;
-            cx<double> p[4][3];
-            const double2* col = P + (((size_t)Xn * 2 + sb) * nv + ib) * len;
+            cx<TC> p[4][3];
+            const v2<TC>* col = P + (((size_t)Xn * 2 + sb) * nv + ib) * len;
 #pragma unroll
             for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     int s_sp = sp >> 1;
-                    p[sp][c] = (s_sp == sb) ? ld<double>(col + ((sp & 1) * 3 + c) * g.Vb + ln) : cx<double>(0, 0);
+                    p[sp][c] = (s_sp == sb) ? ld<TC>(col + ((sp & 1) * 3 + c) * g.Vb + ln) : cx<TC>(0, 0);
                 }
-            const double2* u = FWD ? U + ((size_t)MU * g.Vc + X) * 9 * g.Vb + l : U + ((size_t)MU * g.Vc + Xn) * 9 * g.Vb + ln;
-            cx<double> o[4][3];
-            hop_column<MU, FWD>(p, u, g.Vb, flip ? 0.5 : -0.5, o);
+            const v2<TC>* u = FWD ? U + ((size_t)MU * g.Vc + X) * 9 * g.Vb + l : U + ((size_t)MU * g.Vc + Xn) * 9 * g.Vb + ln;
+            cx<TC> o[4][3];
+            hop_column<TC, MU, FWD>(p, u, g.Vb, flip ? TC(0.5) : TC(-0.5), o);
 #pragma unroll
             for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) st<double>(Wsh + ((size_t)xi * nc + b) * 12 + 3 * sp + c, o[sp][c]);
+                for (int c = 0; c < 3; ++c) st<TC>(Wsh + ((size_t)xi * nc + b) * 12 + 3 * sp + c, o[sp][c]);
         }
         // P_a(x) for x in chunk: Psh[(xi*nc + a)*6 + kk]
         for (int t = threadIdx.x; t < cs * nc * 6; t += blockDim.x) {
@@ -271,15 +276,18 @@ __device__ void build_hop(double2* __restrict__ A, double2* __restrict__ Aself, 
             if (pr < npair) {
                 int a = pr / nc, b = pr - a * nc;
                 int sa = a / nv;
+                cx<TC> co(0, 0), ci(0, 0);
                 for (int xi = 0; xi < cs; ++xi) {
-                    cx<double> t(0, 0);
+                    cx<TC> t(0, 0);
 #pragma unroll
                     for (int kk = 0; kk < 6; ++kk)
-                        cmadc(t, ld<double>(Psh + ((size_t)xi * nc + a) * 6 + kk),
-                              ld<double>(Wsh + ((size_t)xi * nc + b) * 12 + 6 * sa + kk));
-                    if (leaves[xi]) acc_out[q] = acc_out[q] + t;
-                    else acc_in[q] = acc_in[q] + t;
+                        cmadc(t, ld<TC>(Psh + ((size_t)xi * nc + a) * 6 + kk),
+                              ld<TC>(Wsh + ((size_t)xi * nc + b) * 12 + 6 * sa + kk));
+                    if (leaves[xi]) co = co + t;
+                    else ci = ci + t;
                 }
+                acc_out[q] = acc_out[q] + cx<double>((double)co.r, (double)co.i);
+                acc_in[q] = acc_in[q] + cx<double>((double)ci.r, (double)ci.i);
             }
         }
         __syncthreads();
@@ -296,23 +304,24 @@ __device__ void build_hop(double2* __restrict__ A, double2* __restrict__ Aself, 
     }
 }
 
-__global__ void __launch_bounds__(256) k_coarse_hop(double2* A, double2* Aself, const double2* __restrict__ P,
-                                                    const double2* __restrict__ U, int nv, Geom g) {
+template <typename TC>
+__global__ void __launch_bounds__(256) k_coarse_hop(double2* A, double2* Aself, const v2<TC>* __restrict__ P,
+                                                    const v2<TC>* __restrict__ U, int nv, Geom g) {
     extern __shared__ unsigned char smem_raw[];
     const int nc = 2 * nv;
-    double2* Wsh = reinterpret_cast<double2*>(smem_raw);
-    double2* Psh = Wsh + (size_t)kBuildChunk * nc * 12;
+    v2<TC>* Wsh = reinterpret_cast<v2<TC>*>(smem_raw);
+    v2<TC>* Psh = Wsh + (size_t)kBuildChunk * nc * 12;
     unsigned char* leaves = reinterpret_cast<unsigned char*>(Psh + (size_t)kBuildChunk * nc * 6);
     int X = blockIdx.x >> 3, h = blockIdx.x & 7;
     switch (h) {
-        case 0: build_hop<0, true>(A, Aself, P, U, nv, g, X, h, Wsh, Psh, leaves); break;
-        case 1: build_hop<0, false>(A, Aself, P, U, nv, g, X, h, Wsh, Psh, leaves); break;
-        case 2: build_hop<1, true>(A, Aself, P, U, nv, g, X, h, Wsh, Psh, leaves); break;
-        case 3: build_hop<1, false>(A, Aself, P, U, nv, g, X, h, Wsh, Psh, leaves); break;
-        case 4: build_hop<2, true>(A, Aself, P, U, nv, g, X, h, Wsh, Psh, leaves); break;
-        case 5: build_hop<2, false>(A, Aself, P, U, nv, g, X, h, Wsh, Psh, leaves); break;
-        case 6: build_hop<3, true>(A, Aself, P, U, nv, g, X, h, Wsh, Psh, leaves); break;
-        default: build_hop<3, false>(A, Aself, P, U, nv, g, X, h, Wsh, Psh, leaves); break;
+        case 0: build_hop<TC, 0, true>(A, Aself, P, U, nv, g, X, h, Wsh, Psh, leaves); break;
+        case 1: build_hop<TC, 0, false>(A, Aself, P, U, nv, g, X, h, Wsh, Psh, leaves); break;
+        case 2: build_hop<TC, 1, true>(A, Aself, P, U, nv, g, X, h, Wsh, Psh, leaves); break;
+        case 3: build_hop<TC, 1, false>(A, Aself, P, U, nv, g, X, h, Wsh, Psh, leaves); break;
+        case 4: build_hop<TC, 2, true>(A, Aself, P, U, nv, g, X, h, Wsh, Psh, leaves); break;
+        case 5: build_hop<TC, 2, false>(A, Aself, P, U, nv, g, X, h, Wsh, Psh, leaves); break;
+        case 6: build_hop<TC, 3, true>(A, Aself, P, U, nv, g, X, h, Wsh, Psh, leaves); break;
+        default: build_hop<TC, 3, false>(A, Aself, P, U, nv, g, X, h, Wsh, Psh, leaves); break;
     }
 }
 // A[X][0] = (4+m) I + sum_h Aself[X][h] (fixed order)
@@ -328,14 +337,26 @@ __global__ void k_coarse_diag(double2* A, const double2* __restrict__ Aself, int
     st<double>(A + (size_t)X * 9 * nc * nc + r, v);
 }
 
+template <typename TC>
+void coarse_build_t(double2* A, double2* Aself, const v2<TC>* P, const v2<TC>* U, int nv, double mass, const Geom& g,
+                    cudaStream_t st) {
+    int nc = 2 * nv;
+    size_t sm = sizeof(v2<TC>) * kBuildChunk * nc * 18 + kBuildChunk + 16;
+    cudaFuncSetAttribute(k_coarse_hop<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    note_launch();
+    k_coarse_hop<TC><<<g.Vc * 8, kThreads, sm, st>>>(A, Aself, P, U, nv, g);
+    long long total = (long long)g.Vc * nc * nc;
+    note_launch();
+    k_coarse_diag<<<(int)((total + kThreads - 1) / kThreads), kThreads, 0, st>>>(A, Aself, nc, 4.0 + mass, g);
+}
+void coarse_build_f32(double2* A, double2* Aself, const float2* P, const float2* U, int nv, double mass, const Geom& g,
+                      cudaStream_t st) {
+    coarse_build_t<float>(A, Aself, P, U, nv, mass, g, st);
+}
+
 void coarse_build(double2* A, double2* Aself, const double2* P, const double2* U, int nv, double mass, const Geom& g,
                   cudaStream_t st) {
-    int nc = 2 * nv;
-    size_t sm = sizeof(double2) * kBuildChunk * nc * 18 + kBuildChunk + 16;
-    cudaFuncSetAttribute(k_coarse_hop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_coarse_hop<<<g.Vc * 8, kThreads, sm, st>>>(A, Aself, P, U, nv, g);
-    long long total = (long long)g.Vc * nc * nc;
-    k_coarse_diag<<<(int)((total + kThreads - 1) / kThreads), kThreads, 0, st>>>(A, Aself, nc, 4.0 + mass, g);
+    coarse_build_t<double>(A, Aself, P, U, nv, mass, g, st);
 }
 
 __global__ void k_coarse_shift(double2* A, int nc, double dm, int Vc) {
@@ -347,6 +368,7 @@ __global__ void k_coarse_shift(double2* A, int nc, double dm, int Vc) {
 }
 void coarse_shift_mass(double2* A, int nc, double dm, const Geom& g, cudaStream_t st) {
     long long total = (long long)g.Vc * nc;
+    note_launch();
     k_coarse_shift<<<(int)((total + kThreads - 1) / kThreads), kThreads, 0, st>>>(A, nc, dm, g.Vc);
 }
 
@@ -361,6 +383,7 @@ __global__ void k_transpose_blocks(double2* out, const double2* __restrict__ in,
 }
 void coarse_op_transpose(double2* out, const double2* in, int nc, int Vc, cudaStream_t st) {
     long long total = (long long)Vc * 9 * nc * nc;
+    note_launch();
     k_transpose_blocks<<<(int)((total + kThreads - 1) / kThreads), kThreads, 0, st>>>(out, in, nc, (long long)Vc * 9);
 }
 
@@ -419,11 +442,11 @@ void coarse_apply(v2<T>* y, const v2<T>* A, const v2<T>* x, int nc, bool dag, in
     long long total = (long long)g.Vc * nc;
     int grid = (int)((total + kThreads - 1) / kThreads);
     if (slot >= 0) {
-        if (dag) k_coarse_apply<T, true, 1><<<grid, kThreads, 0, st>>>(y, A, x, nc, g, slot, R);
-        else k_coarse_apply<T, false, 1><<<grid, kThreads, 0, st>>>(y, A, x, nc, g, slot, R);
+        if (dag) { note_launch(); k_coarse_apply<T, true, 1><<<grid, kThreads, 0, st>>>(y, A, x, nc, g, slot, R); }
+        else { note_launch(); k_coarse_apply<T, false, 1><<<grid, kThreads, 0, st>>>(y, A, x, nc, g, slot, R); }
     } else {
-        if (dag) k_coarse_apply<T, true, 0><<<grid, kThreads, 0, st>>>(y, A, x, nc, g, slot, R);
-        else k_coarse_apply<T, false, 0><<<grid, kThreads, 0, st>>>(y, A, x, nc, g, slot, R);
+        if (dag) { note_launch(); k_coarse_apply<T, true, 0><<<grid, kThreads, 0, st>>>(y, A, x, nc, g, slot, R); }
+        else { note_launch(); k_coarse_apply<T, false, 0><<<grid, kThreads, 0, st>>>(y, A, x, nc, g, slot, R); }
     }
 }
 
@@ -485,6 +508,7 @@ __global__ void k_cg_update2(v2<T>* __restrict__ p, const v2<T>* __restrict__ s,
 
 template <typename T>
 void cg_init(v2<T>* y, v2<T>* r, const v2<T>* rc, size_t n, double tol, int maxit, const Reduce& R, cudaStream_t st) {
+    note_launch();
     k_cg_start<T><<<reduce_grid(n), kThreads, 0, st>>>(y, r, rc, n, tol, maxit, R);
 }
 // s = D_c^dag r, gamma = ||s||^2, p = s
@@ -493,6 +517,7 @@ void cg_first_direction(v2<T>* s, v2<T>* p, const v2<T>* r, const v2<T>* A, int 
                         cudaStream_t st) {
     size_t n = (size_t)g.Vc * nc;
     coarse_apply<T>(s, A, r, nc, true, S_CG_GAMMA, g, R, st);
+    note_launch();
     k_cg_copy<T><<<reduce_grid(n), kThreads, 0, st>>>(p, s, n);
 }
 template <typename T>
@@ -500,9 +525,13 @@ void cg_step(v2<T>* y, v2<T>* r, v2<T>* s, v2<T>* p, v2<T>* q, const v2<T>* A, i
              cudaStream_t st) {
     size_t n = (size_t)g.Vc * nc;
     int grid = (int)((n + kThreads - 1) / kThreads);
+    note_launch();
     k_coarse_apply<T, false, 2><<<grid, kThreads, 0, st>>>(q, A, p, nc, g, -1, R);        // q = D_c p, alpha
+    note_launch();
     k_cg_update1<T><<<reduce_grid(n), kThreads, 0, st>>>(y, r, p, q, n, R);               // y, r, stop test
+    note_launch();
     k_coarse_apply<T, true, 3><<<grid, kThreads, 0, st>>>(s, A, r, nc, g, -1, R);         // s = D_c^dag r, beta
+    note_launch();
     k_cg_update2<T><<<reduce_grid(n), kThreads, 0, st>>>(p, s, n, R.scal);                // p = s + beta p
 }
 
@@ -540,6 +569,317 @@ __global__ void k_prolongator_to_boundary(double2* out, const double2* __restric
 }
 void prolongator_to_boundary(double2* out, const double2* P, int nv, const Geom& g, cudaStream_t st) {
     long long total = (long long)nv * g.V * 12;
+    note_launch();
     k_prolongator_to_boundary<<<(int)((total + 255) / 256), 256, 0, st>>>(out, P, nv, g);
 }
+}  // namespace wmg
+
+// ================================================================ persistent CGNR
+// The whole coarse solve in one cooperative launch: G co-resident CTAs loop
+// over the CGLS iterations, separated by grid barriers.  Every spin-wait is
+// bounded: after kBarrierSpinLimit polls the CTA sets *err and returns, and
+// CTAs waiting at a barrier return as soon as *err is set.  Reductions:
+// each CTA writes its partial sum, and after the barrier every CTA adds all
+// partials in the same order, so all CTAs take identical decisions.
+namespace wmg {
+
+constexpr long long kBarrierSpinLimit = 40000000LL;   // a few seconds of polls
+
+__device__ __forceinline__ bool grid_sync(unsigned int* count, unsigned int* gen, unsigned int G, int* err) {
+    __shared__ int s_fail;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        volatile unsigned int* vgen = gen;
+        volatile int* verr = err;
+        unsigned int my = *vgen;
+        __threadfence();
+        if (atomicAdd(count, 1u) == G - 1) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*vgen == my) {
+                if (*verr) { s_fail = 1; break; }
+                if (++spins > kBarrierSpinLimit) { atomicExch(err, 1); s_fail = 1; break; }
+                if (spins > 256) __nanosleep(32);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return s_fail == 0;
+}
+
+template <typename T> __device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+// CTA sum in precision T (fixed order), valid in every thread
+template <typename T> __device__ __forceinline__ T block_sum_t(T v, T* sh) {
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum_t(v);
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        T x = lane < nw ? sh[lane] : T(0);
+        x = warp_sum_t(x);
+        if (lane == 0) sh[32] = x;
+    }
+    __syncthreads();
+    T r = sh[32];
+    __syncthreads();
+    return r;
+}
+// sum of partials[c * 4 + slot] over c < G in a fixed order, broadcast to the CTA
+template <typename T> __device__ __forceinline__ T sum_partials(const double* partials, int slot, int G, T* sh) {
+    T a = 0;
+    for (int c = threadIdx.x; c < G; c += blockDim.x) a += (T)__ldcg(partials + (size_t)c * 4 + slot);
+    return block_sum_t<T>(a, sh);
+}
+template <typename T> __device__ __forceinline__ void write_partial(T v, double* partials, int slot, T* sh) {
+    T a = block_sum_t<T>(v, sh);
+    if (threadIdx.x == 0) partials[(size_t)blockIdx.x * 4 + slot] = (double)a;
+}
+
+// Coarse stencil on the aggregates of this CTA, `xpb` aggregates at a time.
+// Thread (x, d, row group) accumulates R consecutive rows a of block
+// A[X][d] (R = 2 for FP32: one 16-byte load carries rows a, a+1 of column b)
+// against in[X+d] staged in shared memory, with 8 independent loads in
+// flight; shared memory then sums the 9 directions.  DAG: sigma3 D_c sigma3.
+// Epilogue EPI:
+//   0: out = result;                          returns ||out||^2 share
+//   1: p = s + beta p, q = result + beta q;   returns ||q||^2 share   (out unused)
+//   2: p = s, q = result;                     returns ||q||^2 share
+template <typename T> struct RowsPerThread { static constexpr int value = 2; };
+
+template <typename T, int R> struct RowLoad;
+template <typename T> struct RowLoad<T, 1> {
+    static __device__ __forceinline__ void load(const v2<T>* p, cx<T> (&v)[1]) {
+        v2<T> a = __ldg(p);
+        v[0] = cx<T>(a.x, a.y);
+    }
+};
+template <> struct RowLoad<double, 2> {
+    static __device__ __forceinline__ void load(const v2<double>* p, cx<double> (&v)[2]) {
+        double2 a = __ldg(p), b = __ldg(p + 1);
+        v[0] = cx<double>(a.x, a.y);
+        v[1] = cx<double>(b.x, b.y);
+    }
+};
+template <> struct RowLoad<float, 2> {
+    static __device__ __forceinline__ void load(const v2<float>* p, cx<float> (&v)[2]) {
+        float4 a = __ldg(reinterpret_cast<const float4*>(p));
+        v[0] = cx<float>(a.x, a.y);
+        v[1] = cx<float>(a.z, a.w);
+    }
+};
+
+template <typename T, bool DAG, int EPI>
+__device__ T coarse_apply_cta(v2<T>* __restrict__ out, const v2<T>* __restrict__ A, const v2<T>* __restrict__ in,
+                                  int nc, int xpb, const Geom& g, v2<T>* xs, cx<T>* part, const v2<T>* __restrict__ sv,
+                                  v2<T>* __restrict__ p, v2<T>* __restrict__ q, T beta) {
+    constexpr int R = RowsPerThread<T>::value;
+    const int nvh = nc >> 1, nrow = 9 * nc, ngrp = nc / R, nthr = 9 * ngrp, nall = xpb * nrow;
+    T nrm = 0;
+    const int xl = threadIdx.x / nthr, rem = threadIdx.x - xl * nthr;
+    const int d = rem / ngrp, a0 = (rem - d * ngrp) * R;
+    for (int Xb = blockIdx.x * xpb; Xb < g.Vc; Xb += gridDim.x * xpb) {
+        for (int i = threadIdx.x; i < nall; i += blockDim.x) {
+            int xi = i / nrow, ri = i - xi * nrow;
+            int di = ri / nc, b = ri - di * nc;
+            int X = Xb + xi;
+            if (X < g.Vc) {
+                int Y = coarse_neighbour(g, X, di);
+                v2<T> v = in[(size_t)Y * nc + b];
+                if (DAG && b >= nvh) { v.x = -v.x; v.y = -v.y; }
+                xs[i] = v;
+            }
+        }
+        __syncthreads();
+        const int X = Xb + xl;
+        if (threadIdx.x < xpb * nthr && X < g.Vc) {
+            const v2<T>* Ad = A + ((size_t)X * 9 + d) * nc * nc + a0;
+            const v2<T>* xd = xs + xl * nrow + d * nc;
+            cx<T> acc[R][2];
+#pragma unroll
+            for (int r = 0; r < R; ++r) { acc[r][0] = cx<T>(0, 0); acc[r][1] = cx<T>(0, 0); }
+            constexpr int U = 4;   // independent 16-byte loads in flight per thread
+            for (int b0 = 0; b0 < nc; b0 += U) {
+                cx<T> av[U][R];
+#pragma unroll
+                for (int j = 0; j < U; ++j)
+                    if (b0 + j < nc) RowLoad<T, R>::load(Ad + (size_t)(b0 + j) * nc, av[j]);
+#pragma unroll
+                for (int j = 0; j < U; ++j)
+                    if (b0 + j < nc) {
+                        cx<T> xb = ld<T>(xd + b0 + j);
+#pragma unroll
+                        for (int r = 0; r < R; ++r) cmad(acc[r][j & 1], av[j][r], xb);
+                    }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) part[xl * nrow + d * nc + a0 + r] = acc[r][0] + acc[r][1];
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < xpb * nc; t += blockDim.x) {
+            int x2 = t / nc, a2 = t - x2 * nc;
+            int X2 = Xb + x2;
+            if (X2 < g.Vc) {
+                cx<T> sum = part[x2 * nrow + a2];
+#pragma unroll
+                for (int dd = 1; dd < 9; ++dd) sum = sum + part[x2 * nrow + dd * nc + a2];
+                if (DAG && a2 >= nvh) sum = cx<T>(-sum.r, -sum.i);
+                size_t o = (size_t)X2 * nc + a2;
+                if (EPI == 0) {
+                    st<T>(out + o, sum);
+                    nrm += norm2(sum);
+                } else {
+                    cx<T> pn = ld<T>(sv + o), qn = sum;
+                    if (EPI == 1) {
+                        pn = pn + beta * ld<T>(p + o);
+                        qn = qn + beta * ld<T>(q + o);
+                    }
+                    st<T>(p + o, pn);
+                    st<T>(q + o, qn);
+                    nrm += norm2(qn);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    return nrm;
+}
+
+// CGLS (CG on the normal equations, textbook form), four phases per iteration
+// separated by grid barriers:
+//   A: q = D_c p, alpha = gamma / ||q||^2
+//   B: y += alpha p, r -= alpha q, ||r||^2, stopping test
+//   C: s = D_c^dag r, gamma' = ||s||^2, beta = gamma'/gamma
+//   D: p = s + beta p
+template <typename T> struct CgnrMaxThreads { static constexpr int value = 384; };
+
+template <typename T>
+__global__ void __launch_bounds__(CgnrMaxThreads<T>::value, 2) k_cgnr_persistent(CgnrArgs<T> a) {
+    extern __shared__ unsigned char smem_raw[];
+    const int nc = a.nc, xpb = a.xpb;
+    v2<T>* xs = reinterpret_cast<v2<T>*>(smem_raw);
+    cx<T>* part = reinterpret_cast<cx<T>*>(smem_raw + sizeof(v2<T>) * 9 * nc * xpb);
+    __shared__ T shr[33];
+    const unsigned int G = gridDim.x;
+    const size_t n = (size_t)a.g.Vc * nc;
+    const size_t chunk = (n + G - 1) / G;
+    const size_t i0 = (size_t)blockIdx.x * chunk, i1 = min(n, i0 + chunk);
+    unsigned int* cnt = a.bar;
+    unsigned int* gen = a.bar + 1;
+    // y = 0, r = rc, ||rc||^2
+    T loc = 0;
+    for (size_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        v2<T> v = a.rc[i];
+        a.r[i] = v;
+        v2<T> z; z.x = 0; z.y = 0;
+        a.y[i] = z;
+        loc += v.x * v.x + v.y * v.y;
+    }
+    write_partial<T>(loc, a.partials, 0, shr);
+    if (!grid_sync(cnt, gen, G, a.err)) return;
+    const T rc2 = sum_partials<T>(a.partials, 0, G, shr);
+    int it = 0;
+    T r2 = rc2;
+    if (rc2 > T(0) && a.maxit > 0) {
+        // s = D_c^dag r, gamma = ||s||^2, p = s
+        loc = coarse_apply_cta<T, true, 0>(a.s, a.A, a.r, nc, xpb, a.g, xs, part, nullptr, nullptr, nullptr, T(0));
+        write_partial<T>(loc, a.partials, 1, shr);
+        if (!grid_sync(cnt, gen, G, a.err)) return;
+        T gamma = sum_partials<T>(a.partials, 1, G, shr);
+        for (size_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) a.p[i] = a.s[i];
+        if (!grid_sync(cnt, gen, G, a.err)) return;
+        while (it < a.maxit) {
+            loc = coarse_apply_cta<T, false, 0>(a.q, a.A, a.p, nc, xpb, a.g, xs, part, nullptr, nullptr, nullptr, T(0));
+            write_partial<T>(loc, a.partials, 0, shr);
+            if (!grid_sync(cnt, gen, G, a.err)) return;
+            T qq = sum_partials<T>(a.partials, 0, G, shr);
+            if (!(qq > T(0))) break;
+            T al = gamma / qq;
+            loc = 0;
+            for (size_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+                st<T>(a.y + i, ld<T>(a.y + i) + al * ld<T>(a.p + i));
+                cx<T> v = ld<T>(a.r + i) - al * ld<T>(a.q + i);
+                st<T>(a.r + i, v);
+                loc += norm2(v);
+            }
+            write_partial<T>(loc, a.partials, 1, shr);
+            if (!grid_sync(cnt, gen, G, a.err)) return;
+            r2 = sum_partials<T>(a.partials, 1, G, shr);
+            ++it;
+            if (r2 <= (T)a.tol2 * rc2 || it >= a.maxit) break;
+            loc = coarse_apply_cta<T, true, 0>(a.s, a.A, a.r, nc, xpb, a.g, xs, part, nullptr, nullptr, nullptr, T(0));
+            write_partial<T>(loc, a.partials, 2, shr);
+            if (!grid_sync(cnt, gen, G, a.err)) return;
+            T gnew = sum_partials<T>(a.partials, 2, G, shr);
+            T be = gnew / gamma;
+            gamma = gnew;
+            for (size_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) st<T>(a.p + i, ld<T>(a.s + i) + be * ld<T>(a.p + i));
+            if (!grid_sync(cnt, gen, G, a.err)) return;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.scal[S_CG_ITERS] = (double)it;
+        a.scal[S_CG_R2] = (double)r2;
+        a.scal[S_CG_RC2] = (double)rc2;
+        a.scal[S_CG_DONE] = 1.0;
+        a.scal[S_CG_TOTAL] += (double)it;
+    }
+}
+
+// aggregates per CTA: as many 9*nc-thread groups as fit in the thread limit
+template <typename T> int cgnr_threads_per_x(int nc) { return 9 * (nc / RowsPerThread<T>::value); }
+template <typename T> int cgnr_xpb(int nc) {
+    int x = CgnrMaxThreads<T>::value / cgnr_threads_per_x<T>(nc);
+    return x > 0 ? x : 1;
+}
+template <typename T> int cgnr_block_threads(int nc) {
+    return ((cgnr_xpb<T>(nc) * cgnr_threads_per_x<T>(nc) + 31) / 32) * 32;
+}
+template <typename T> size_t cgnr_smem(int nc) {
+    return (sizeof(v2<T>) + sizeof(cx<T>)) * 9 * (size_t)nc * cgnr_xpb<T>(nc);
+}
+
+// co-resident CTAs for this nc, then the smallest balanced grid covering all aggregates
+template <typename T> int cgnr_grid(int nc, int Vc) {
+    static int cached[2][128] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int key = nc < 128 ? nc : 127;
+    int* slot = &cached[sizeof(T) == 8 ? 1 : 0][key];
+    if (*slot == 0) {
+        int sms = 0, per = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        size_t sm = cgnr_smem<T>(nc);   // < 48 KB: no attribute needed
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cgnr_persistent<T>, cgnr_block_threads<T>(nc), sm);
+        *slot = per * sms;
+    }
+    int gmax = *slot;
+    if (gmax <= 0) return 0;
+    int xpb = cgnr_xpb<T>(nc);
+    int batches = (Vc + xpb - 1) / xpb;               // CTA-sized pieces of work
+    int rounds = (batches + gmax - 1) / gmax;         // pieces per CTA
+    return (batches + rounds - 1) / rounds;
+}
+
+template <typename T> cudaError_t cgnr_persistent(const CgnrArgs<T>& args, cudaStream_t st) {
+    int G = cgnr_grid<T>(args.nc, args.g.Vc);
+    if (G <= 0) return cudaErrorCooperativeLaunchTooLarge;
+    CgnrArgs<T> a = args;
+    a.xpb = cgnr_xpb<T>(a.nc);
+    void* params[] = {&a};
+    note_launch();
+    return cudaLaunchCooperativeKernel((const void*)k_cgnr_persistent<T>, dim3(G), dim3(cgnr_block_threads<T>(a.nc)),
+                                       params, cgnr_smem<T>(a.nc), st);
+}
+template cudaError_t cgnr_persistent<float>(const CgnrArgs<float>&, cudaStream_t);
+template cudaError_t cgnr_persistent<double>(const CgnrArgs<double>&, cudaStream_t);
+
 }  // namespace wmg

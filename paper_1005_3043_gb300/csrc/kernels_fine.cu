@@ -66,16 +66,20 @@ __global__ void k_convert(v2<Tout>* out, const v2<Tin>* __restrict__ in, size_t 
 }
 
 template <typename T> void spinor_to_internal(v2<T>* out, const double2* in, const Geom& g, cudaStream_t st) {
+    note_launch();
     k_spinor_to_internal<T><<<grid_for(g.V), kThreads, 0, st>>>(out, in, g);
 }
 template <typename T> void spinor_from_internal(double2* out, const v2<T>* in, const Geom& g, cudaStream_t st) {
+    note_launch();
     k_spinor_from_internal<T><<<grid_for(g.V), kThreads, 0, st>>>(out, in, g);
 }
 template <typename T> void links_to_internal(v2<T>* out, const double2* in, const Geom& g, cudaStream_t st) {
+    note_launch();
     k_links_to_internal<T><<<grid_for(g.V), kThreads, 0, st>>>(out, in, g);
 }
 template <typename Tin, typename Tout> void convert(v2<Tout>* out, const v2<Tin>* in, size_t n, cudaStream_t st) {
     int grid = (int)std::min<size_t>((n + kThreads - 1) / kThreads, 152 * 16);
+    note_launch();
     k_convert<Tin, Tout><<<grid > 0 ? grid : 1, kThreads, 0, st>>>(out, in, n);
 }
 
@@ -171,23 +175,22 @@ __device__ __forceinline__ void hop(cx<T> (&acc)[4][3], const v2<T>* __restrict_
 }
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256) k_dslash(v2<T>* __restrict__ out, const v2<T>* __restrict__ in,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_dslash(v2<T>* __restrict__ out, const v2<T>* __restrict__ in,
                                                 const v2<T>* __restrict__ U, const v2<T>* __restrict__ src,
                                                 Geom g, T diag, double omega, int slot, Reduce R) {
     long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    double red[3] = {0.0, 0.0, 0.0};
+    T red[3] = {0, 0, 0};   // per-site partial sums in T, promoted once for the grid reduction
     if (s < g.V) {
         int X = (int)(s / g.Vb), l = (int)(s - (long long)X * g.Vb);
         int lc[4], xc[4];
         local_coords(g, l, lc);
         coarse_coords(g, X, xc);
         const v2<T>* self = in + (size_t)X * 12 * g.Vb + l;
-        cx<T> acc[4][3], own[4][3];
-        load_spinor<T>(own, self, g.Vb);
+        cx<T> acc[4][3];
 #pragma unroll
         for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) acc[sp][c] = diag * own[sp][c];
+            for (int c = 0; c < 3; ++c) acc[sp][c] = diag * ldg<T>(self + (3 * sp + c) * g.Vb);
         hop<T, 0, true>(acc, in, U, g, X, l, lc, xc);
         hop<T, 0, false>(acc, in, U, g, X, l, lc, xc);
         hop<T, 1, true>(acc, in, U, g, X, l, lc, xc);
@@ -206,20 +209,21 @@ __global__ void __launch_bounds__(256) k_dslash(v2<T>* __restrict__ out, const v
                 cx<T> v = acc[sp][c];
                 if (MODE == DS_XMY || MODE == DS_XMY_NORM) v = ld<T>(sr + k * g.Vb) - v;
                 st<T>(o + k * g.Vb, v);
-                if (MODE == DS_XMY_NORM) red[0] += (double)norm2(v);
+                if (MODE == DS_XMY_NORM) red[0] += norm2(v);
                 if (MODE == DS_MRDOT) {
-                    cx<T> r = own[sp][c];           // <q, r>: q = D r at this site
-                    red[0] += (double)(v.r * r.r + v.i * r.i);
-                    red[1] += (double)(v.r * r.i - v.i * r.r);
-                    red[2] += (double)norm2(v);
+                    cx<T> r = ldg<T>(self + k * g.Vb);   // <q, r>: q = D r at this site (cache hit)
+                    red[0] += v.r * r.r + v.i * r.i;
+                    red[1] += v.r * r.i - v.i * r.r;
+                    red[2] += norm2(v);
                 }
             }
     }
     if (MODE == DS_XMY_NORM) {
-        double v1[1] = {red[0]};
+        double v1[1] = {(double)red[0]};
         grid_reduce<1>(v1, R.partials, R.ticket, [&](double (&t)[1]) { R.scal[slot] = t[0]; });
     } else if (MODE == DS_MRDOT) {
-        grid_reduce<3>(red, R.partials, R.ticket, [&](double (&t)[3]) {
+        double v3[3] = {(double)red[0], (double)red[1], (double)red[2]};
+        grid_reduce<3>(v3, R.partials, R.ticket, [&](double (&t)[3]) {
             double f = t[2] > 0 ? omega / t[2] : 0.0;
             R.scal[S_MR_ALPHA] = f * t[0];
             R.scal[S_MR_ALPHA + 1] = f * t[1];
@@ -233,12 +237,13 @@ void dslash(int mode, v2<T>* out, const v2<T>* in, const v2<T>* U, const v2<T>* 
     int grid = grid_for(g.V);
     T diag = (T)(4.0 + mass);
     switch (mode) {
-        case DS_PLAIN: k_dslash<T, DS_PLAIN><<<grid, kThreads, 0, st>>>(out, in, U, src, g, diag, omega, slot, R); break;
-        case DS_XMY: k_dslash<T, DS_XMY><<<grid, kThreads, 0, st>>>(out, in, U, src, g, diag, omega, slot, R); break;
+        case DS_PLAIN: { note_launch(); k_dslash<T, DS_PLAIN><<<grid, kThreads, 0, st>>>(out, in, U, src, g, diag, omega, slot, R); } break;
+        case DS_XMY: { note_launch(); k_dslash<T, DS_XMY><<<grid, kThreads, 0, st>>>(out, in, U, src, g, diag, omega, slot, R); } break;
         case DS_XMY_NORM:
+            note_launch();
             k_dslash<T, DS_XMY_NORM><<<grid, kThreads, 0, st>>>(out, in, U, src, g, diag, omega, slot, R);
             break;
-        case DS_MRDOT: k_dslash<T, DS_MRDOT><<<grid, kThreads, 0, st>>>(out, in, U, src, g, diag, omega, slot, R); break;
+        case DS_MRDOT: { note_launch(); k_dslash<T, DS_MRDOT><<<grid, kThreads, 0, st>>>(out, in, U, src, g, diag, omega, slot, R); } break;
     }
 }
 
@@ -307,24 +312,33 @@ static inline int stream_grid(size_t n) {
     return (int)(b > 0 ? b : 1);
 }
 
-template <typename T> void zero(v2<T>* x, size_t n, cudaStream_t st) { k_zero<T><<<stream_grid(n), kThreads, 0, st>>>(x, n); }
+template <typename T> void zero(v2<T>* x, size_t n, cudaStream_t st) {
+    note_launch();
+    k_zero<T><<<stream_grid(n), kThreads, 0, st>>>(x, n);
+}
 template <typename T> void norm2(const v2<T>* x, size_t n, int slot, const Reduce& R, cudaStream_t st) {
+    note_launch();
     k_norm2<T><<<reduce_grid(n), kThreads, 0, st>>>(x, n, slot, R);
 }
 template <typename T> void dot(const v2<T>* x, const v2<T>* y, size_t n, int slot, const Reduce& R, cudaStream_t st) {
+    note_launch();
     k_dot<T><<<reduce_grid(n), kThreads, 0, st>>>(x, y, n, slot, R);
 }
 template <typename T> void scale(v2<T>* x, size_t n, double s, cudaStream_t st) {
+    note_launch();
     k_scale<T><<<stream_grid(n), kThreads, 0, st>>>(x, n, (T)s);
 }
 template <typename T> void axpy(v2<T>* y, const v2<T>* x, size_t n, double ar, double ai, cudaStream_t st) {
+    note_launch();
     k_axpy<T><<<stream_grid(n), kThreads, 0, st>>>(y, x, n, (T)ar, (T)ai);
 }
 template <typename T>
 void mr_update(v2<T>* e, v2<T>* r, const v2<T>* q, size_t n, bool update_r, const Reduce& R, cudaStream_t st) {
+    note_launch();
     k_mr_update<T><<<stream_grid(n), kThreads, 0, st>>>(e, r, q, n, update_r, R.scal);
 }
 template <typename T> void normalize_dev(v2<T>* x, size_t n, int slot, const Reduce& R, cudaStream_t st) {
+    note_launch();
     k_normalize<T><<<stream_grid(n), kThreads, 0, st>>>(x, n, R.scal, slot);
 }
 
@@ -428,23 +442,27 @@ __global__ void k_gcr_xupdate(double2* x, const v2<T>* __restrict__ Z, size_t n,
 
 template <typename T> void gcr_multidot(const v2<T>* basis, size_t n, int k, const Reduce& R, cudaStream_t st) {
     int grid = reduce_grid(n);
-    if (k <= 4) k_gcr_multidot<T, 4><<<grid, kThreads, 0, st>>>(basis, n, k, R);
-    else if (k <= 8) k_gcr_multidot<T, 8><<<grid, kThreads, 0, st>>>(basis, n, k, R);
-    else if (k <= 16) k_gcr_multidot<T, 16><<<grid, kThreads, 0, st>>>(basis, n, k, R);
-    else k_gcr_multidot<T, 32><<<grid, kThreads, 0, st>>>(basis, n, k, R);
+    if (k <= 4) { note_launch(); k_gcr_multidot<T, 4><<<grid, kThreads, 0, st>>>(basis, n, k, R); }
+    else if (k <= 8) { note_launch(); k_gcr_multidot<T, 8><<<grid, kThreads, 0, st>>>(basis, n, k, R); }
+    else if (k <= 16) { note_launch(); k_gcr_multidot<T, 16><<<grid, kThreads, 0, st>>>(basis, n, k, R); }
+    else { note_launch(); k_gcr_multidot<T, 32><<<grid, kThreads, 0, st>>>(basis, n, k, R); }
 }
 template <typename T> void gcr_orth_norm(v2<T>* basis, size_t n, int k, const Reduce& R, cudaStream_t st) {
+    note_launch();
     k_gcr_orth_norm<T><<<reduce_grid(n), kThreads, 0, st>>>(basis, n, k, R);
 }
 template <typename T>
 void gcr_cdot(const v2<T>* basis, const v2<T>* r, size_t n, int k, const Reduce& R, cudaStream_t st) {
+    note_launch();
     k_gcr_cdot<T><<<reduce_grid(n), kThreads, 0, st>>>(basis, r, n, k, R);
 }
 template <typename T> void gcr_update(v2<T>* basis, v2<T>* r, size_t n, int k, const Reduce& R, cudaStream_t st) {
+    note_launch();
     k_gcr_update<T><<<reduce_grid(n), kThreads, 0, st>>>(basis, r, n, k, R);
 }
 template <typename T>
 void gcr_xupdate(double2* x, const v2<T>* Z, size_t n, int k, const GcrCoef& y, cudaStream_t st) {
+    note_launch();
     k_gcr_xupdate<T><<<stream_grid(n), kThreads, 0, st>>>(x, Z, n, k, y);
 }
 

@@ -134,6 +134,7 @@ enum ScalarSlot {
     S_CG_DONE = 14,
     S_CG_TOL2 = 15,
     S_CG_MAXIT = 16,
+    S_CG_TOTAL = 17,     // coarse iterations accumulated over a solve
     S_GCR_PN2 = 20,      // ||p_k||^2 after orthogonalisation
     S_GCR_R2 = 21,       // ||r||^2 after the update
     S_GCR_R = 64,        // R[j][k] complex, K_MAX x K_MAX (column k, row j): 2*K_MAX*K_MAX

@@ -17,6 +17,11 @@
 
 using namespace wmg;
 
+std::atomic<long long>& wmg::launch_counter() {
+    static std::atomic<long long> c{0};
+    return c;
+}
+
 namespace {
 
 struct CoarseLevel {
@@ -78,8 +83,15 @@ struct mg_ctx {
     Reduce R{};
     double* h_scal = nullptr;        // pinned host copy of the scalars
     int* d_status = nullptr;
+    unsigned int* bar = nullptr;     // persistent-kernel barrier: count, generation, error flag
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<void*> allocs;
+    // launch timer
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<int> ev_class;      // class of each (start, stop) pair
+    double coarse_mark = 0.0;       // S_CG_TOTAL at the last profile read
 };
 
 namespace {
@@ -129,6 +141,21 @@ int read_scalars(mg_ctx* ctx, int first, int count) {
     CK(cudaStreamSynchronize(ctx->st));
     return MG_OK;
 }
+
+// launch timer: a (start, stop) event pair around tracked launches
+int prof_mark(mg_ctx* ctx, int cls, bool start) {
+    if (!ctx->prof) return MG_OK;
+    if (ctx->ev_used == ctx->ev_pool.size()) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        ctx->ev_pool.push_back(e);
+    }
+    CK(cudaEventRecord(ctx->ev_pool[ctx->ev_used++], ctx->st));
+    if (start) ctx->ev_class.push_back(cls);
+    return MG_OK;
+}
+#define PROF_BEGIN(cls) TRY(prof_mark(ctx, cls, true))
+#define PROF_END(cls) TRY(prof_mark(ctx, cls, false))
 
 template <typename T> Work<T>& work(mg_ctx* c);
 template <> Work<float>& work<float>(mg_ctx* c) { return c->wf; }
@@ -204,7 +231,9 @@ int ensure_protos(mg_ctx* ctx) {
 int build_level(mg_ctx* ctx, CoarseLevel& L, const double2* V, int nv) {
     TRY(ensure_level(ctx, L, nv));
     CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->st));
+    PROF_BEGIN(MG_K_BLOCK_ORTHO);
     block_orthonormalize(L.P64, V, nv, ctx->g, ctx->d_status, ctx->st);
+    PROF_END(MG_K_BLOCK_ORTHO);
     CKL();
     int status = 0;
     CK(cudaMemcpyAsync(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
@@ -213,10 +242,15 @@ int build_level(mg_ctx* ctx, CoarseLevel& L, const double2* V, int nv) {
         L.valid = false;
         return fail(ctx, MG_ERR_NUMERIC, "block orthonormalisation: rank-deficient prototypes in an aggregate");
     }
-    coarse_build(L.A64, ctx->Aself, L.P64, ctx->U64, nv, ctx->mass, ctx->g, ctx->st);
-    CKL();
     size_t np = (size_t)nv * nfine(ctx), na = (size_t)ctx->g.Vc * 9 * L.nc * L.nc;
     convert<double, float>(L.P32, L.P64, np, ctx->st);
+    PROF_BEGIN(MG_K_COARSE_BUILD);
+    if (ctx->prm.prec_inner == MG_FP32)   // FP32 products, FP64 accumulation
+        coarse_build_f32(L.A64, ctx->Aself, L.P32, ctx->U32, nv, ctx->mass, ctx->g, ctx->st);
+    else
+        coarse_build(L.A64, ctx->Aself, L.P64, ctx->U64, nv, ctx->mass, ctx->g, ctx->st);
+    PROF_END(MG_K_COARSE_BUILD);
+    CKL();
     convert<double, float>(L.A32, L.A64, na, ctx->st);
     CKL();
     L.mass = ctx->mass;
@@ -226,24 +260,44 @@ int build_level(mg_ctx* ctx, CoarseLevel& L, const double2* V, int nv) {
 
 // ---------------------------------------------------------------- coarse solve
 template <typename T>
+CgnrArgs<T> cgnr_args(const CoarseLevel& L, const Geom& g, const v2<T>* rc, v2<T>* y, v2<T>* r, v2<T>* sv, v2<T>* p,
+                      v2<T>* q, double tol, int maxit, double* partials, unsigned int* bar, double* scal) {
+    CgnrArgs<T> a;
+    a.y = y; a.r = r; a.s = sv; a.p = p; a.q = q;
+    a.A = lvlA<T>(L); a.rc = rc; a.nc = L.nc; a.g = g;
+    a.tol2 = tol * tol; a.maxit = maxit;
+    a.partials = partials; a.bar = bar; a.scal = scal; a.err = (int*)(bar + 2);
+    return a;
+}
+
+// CGNR on D_c (one persistent cooperative launch).  With iters != nullptr the
+// call waits for the result; otherwise the count is only added to
+// scal[S_CG_TOTAL] and nothing synchronises.
+template <typename T>
 int coarse_solve(mg_ctx* ctx, const CoarseLevel& L, const v2<T>* rc, v2<T>* y, double tol, int maxit, int* iters) {
     Work<T>& w = work<T>(ctx);
-    size_t n = (size_t)ctx->g.Vc * L.nc;
-    const v2<T>* A = lvlA<T>(L);
-    cg_init<T>(y, w.cr, rc, n, tol, maxit, ctx->R, ctx->st);
-    cg_first_direction<T>(w.cs, w.cp, w.cr, A, L.nc, ctx->g, ctx->R, ctx->st);
-    CKL();
-    int check = ctx->prm.coarse_check > 0 ? ctx->prm.coarse_check : 16;
-    int launched = 0;
-    for (;;) {
-        for (int j = 0; j < check; ++j) cg_step<T>(y, w.cr, w.cs, w.cp, w.cq, A, L.nc, ctx->g, ctx->R, ctx->st);
-        CKL();
-        launched += check;
-        TRY(read_scalars(ctx, S_CG_ITERS, 2));
-        if (ctx->h_scal[S_CG_DONE] != 0.0) break;
-        if (launched > maxit + check) return fail(ctx, MG_ERR_NUMERIC, "coarse solve did not stop");
+    CgnrArgs<T> a = cgnr_args<T>(L, ctx->g, rc, y, w.cr, w.cs, w.cp, w.cq, tol, maxit, ctx->R.partials, ctx->bar,
+                                 ctx->R.scal);
+    CK(cudaMemsetAsync(ctx->bar, 0, sizeof(unsigned int) * 3, ctx->st));
+    PROF_BEGIN(MG_K_COARSE_SOLVE);
+    CK(cgnr_persistent<T>(a, ctx->st));
+    PROF_END(MG_K_COARSE_SOLVE);
+    if (iters) {
+        TRY(read_scalars(ctx, S_CG_RC2, 3));
+        unsigned int flags[3];
+        CK(cudaMemcpy(flags, ctx->bar, sizeof(flags), cudaMemcpyDeviceToHost));
+        if (flags[2]) return fail(ctx, MG_ERR_TIMEOUT, "coarse solve: a grid barrier wait gave up");
+        *iters = (int)ctx->h_scal[S_CG_ITERS];
     }
-    *iters = (int)ctx->h_scal[S_CG_ITERS];
+    return MG_OK;
+}
+
+// error flag of the persistent kernels (checked once per solve)
+int check_timeout(mg_ctx* ctx) {
+    unsigned int flags[3];
+    CK(cudaMemcpyAsync(flags, ctx->bar, sizeof(flags), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    if (flags[2]) return fail(ctx, MG_ERR_TIMEOUT, "coarse solve: a grid barrier wait gave up");
     return MG_OK;
 }
 
@@ -258,18 +312,26 @@ int vcycle(mg_ctx* ctx, const CoarseLevel& L, const v2<T>* r, v2<T>* z, Counters
     Work<T>& w = work<T>(ctx);
     size_t n = nfine(ctx);
     const v2<T>* U = links<T>(ctx);
+    PROF_BEGIN(MG_K_RESTRICT);
     restrict_<T>(w.crc, lvlP<T>(L), r, L.nv, ctx->g, ctx->st);
+    PROF_END(MG_K_RESTRICT);
     CKL();
-    int it = 0;
-    TRY(coarse_solve<T>(ctx, L, w.crc, w.cy, ctx->prm.coarse_tol, ctx->prm.max_coarse, &it));
-    cnt.coarse_iters += it;
+    TRY(coarse_solve<T>(ctx, L, w.crc, w.cy, ctx->prm.coarse_tol, ctx->prm.max_coarse, nullptr));
+    PROF_BEGIN(MG_K_PROLONG);
     prolong<T>(z, lvlP<T>(L), w.cy, L.nv, ctx->g, ctx->st);
+    PROF_END(MG_K_PROLONG);
+    PROF_BEGIN(MG_K_DSLASH);
     dslash<T>(DS_XMY, w.vr, z, U, r, ctx->g, ctx->mass, 0.0, 0, ctx->R, ctx->st);
+    PROF_END(MG_K_DSLASH);
     cnt.matvecs += 1;
     int steps = ctx->prm.smoother_steps;
     for (int k = 0; k < steps; ++k) {
+        PROF_BEGIN(MG_K_DSLASH);
         dslash<T>(DS_MRDOT, w.vq, w.vr, U, w.vr, ctx->g, ctx->mass, ctx->prm.omega, 0, ctx->R, ctx->st);
+        PROF_END(MG_K_DSLASH);
+        PROF_BEGIN(MG_K_KRYLOV);
         mr_update<T>(z, w.vr, w.vq, n, k + 1 < steps, ctx->R, ctx->st);
+        PROF_END(MG_K_KRYLOV);
         cnt.matvecs += 1;
     }
     CKL();
@@ -292,6 +354,8 @@ template <typename T> int gcr_solve(mg_ctx* ctx, mg_solve_info* info) {
     if (!std::is_same<T, double>::value) convert<double, T>(w.r, ctx->r64, n, ctx->st);
     CKL();
     TRY(read_scalars(ctx, S_NORM_A, 1));
+    TRY(read_scalars(ctx, S_CG_TOTAL, 1));
+    const double coarse_before = ctx->h_scal[S_CG_TOTAL];
     double bnorm = std::sqrt(ctx->h_scal[S_NORM_A]);
     if (!std::isfinite(bnorm)) return fail(ctx, MG_ERR_NUMERIC, "right-hand side is not finite");
     double rel = bnorm > 0 ? 1.0 : 0.0;
@@ -304,8 +368,11 @@ template <typename T> int gcr_solve(mg_ctx* ctx, mg_solve_info* info) {
         for (; k < K && iters < p.max_outer;) {
             v2<T>* zk = w.Z + (size_t)k * n;
             TRY(vcycle<T>(ctx, ctx->full, w.r, zk, cnt));
+            PROF_BEGIN(MG_K_DSLASH);
             dslash<T>(DS_PLAIN, w.Pk + (size_t)k * n, zk, U, zk, ctx->g, ctx->mass, 0.0, 0, ctx->R, ctx->st);
+            PROF_END(MG_K_DSLASH);
             cnt.matvecs += 1;
+            PROF_BEGIN(MG_K_KRYLOV);
             if (k > 0) {
                 gcr_multidot<T>(w.Pk, n, k, ctx->R, ctx->st);
                 gcr_orth_norm<T>(w.Pk, n, k, ctx->R, ctx->st);
@@ -314,6 +381,7 @@ template <typename T> int gcr_solve(mg_ctx* ctx, mg_solve_info* info) {
             }
             gcr_cdot<T>(w.Pk, w.r, n, k, ctx->R, ctx->st);
             gcr_update<T>(w.Pk, w.r, n, k, ctx->R, ctx->st);
+            PROF_END(MG_K_KRYLOV);
             CKL();
             TRY(read_scalars(ctx, S_GCR_PN2, 2));
             ++k;
@@ -344,9 +412,13 @@ template <typename T> int gcr_solve(mg_ctx* ctx, mg_solve_info* info) {
             y.c[2 * i] = (sr * d[0] + si * d[1]) / den;
             y.c[2 * i + 1] = (si * d[0] - sr * d[1]) / den;
         }
+        PROF_BEGIN(MG_K_KRYLOV);
         gcr_xupdate<T>(ctx->x64, w.Z, n, k, y, ctx->st);
+        PROF_END(MG_K_KRYLOV);
+        PROF_BEGIN(MG_K_TRUE_RESIDUAL);
         dslash<double>(DS_XMY_NORM, ctx->r64, ctx->x64, ctx->U64, ctx->b64, ctx->g, ctx->mass, 0.0, S_NORM_B, ctx->R,
                        ctx->st);
+        PROF_END(MG_K_TRUE_RESIDUAL);
         cnt.matvecs += 1;
         CKL();
         TRY(read_scalars(ctx, S_NORM_B, 1));
@@ -361,9 +433,11 @@ template <typename T> int gcr_solve(mg_ctx* ctx, mg_solve_info* info) {
     CK(cudaEventSynchronize(ctx->ev1));
     float ms = 0;
     CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+    TRY(check_timeout(ctx));
+    TRY(read_scalars(ctx, S_CG_TOTAL, 1));
     if (info) {
         info->outer_iters = iters;
-        info->coarse_iters = cnt.coarse_iters;
+        info->coarse_iters = (int)(ctx->h_scal[S_CG_TOTAL] - coarse_before);
         info->fine_matvecs = cnt.matvecs;
         info->restarts = restarts;
         info->true_rel_res = rel;
@@ -435,6 +509,7 @@ template <typename T> int setup_impl(mg_ctx* ctx) {
             }
         }
     }
+    TRY(check_timeout(ctx));
     // (iv) final prolongator and coarse operator
     return build_level(ctx, ctx->full, ctx->protos, nv);
 }
@@ -564,6 +639,7 @@ template <typename T> int hook_vcycle(mg_ctx* ctx, const double* r, double* z) {
     TRY(upload_fine<T>(ctx, r, w.tin));
     Counters cnt;
     TRY(vcycle<T>(ctx, ctx->full, w.tin, w.tout, cnt));
+    TRY(check_timeout(ctx));
     return download_fine<T>(ctx, w.tout, z);
 }
 
@@ -628,7 +704,8 @@ int mg_create(const int dims[4], int t_antiperiodic, const mg_params* p, void* s
         (rc = dalloc(ctx, &ctx->stage_b, sizeof(double2) * n)) ||
         (rc = dalloc(ctx, &ctx->R.partials, sizeof(double) * kMaxReduceBlocks * 64)) ||
         (rc = dalloc(ctx, &ctx->R.ticket, sizeof(unsigned int) * 4)) ||
-        (rc = dalloc(ctx, &ctx->R.scal, sizeof(double) * S_COUNT)) || (rc = dalloc(ctx, &ctx->d_status, sizeof(int)))) {
+        (rc = dalloc(ctx, &ctx->R.scal, sizeof(double) * S_COUNT)) || (rc = dalloc(ctx, &ctx->d_status, sizeof(int))) ||
+        (rc = dalloc(ctx, &ctx->bar, sizeof(unsigned int) * 4))) {
         mg_destroy(ctx);
         return rc;
     }
@@ -636,6 +713,7 @@ int mg_create(const int dims[4], int t_antiperiodic, const mg_params* p, void* s
         cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess ||
         cudaMemsetAsync(ctx->R.ticket, 0, sizeof(unsigned int) * 4, ctx->st) != cudaSuccess ||
         cudaMemsetAsync(ctx->R.scal, 0, sizeof(double) * S_COUNT, ctx->st) != cudaSuccess ||
+        cudaMemsetAsync(ctx->bar, 0, sizeof(unsigned int) * 4, ctx->st) != cudaSuccess ||
         cudaStreamSynchronize(ctx->st) != cudaSuccess) {
         cudaGetLastError();
         mg_destroy(ctx);
@@ -653,6 +731,7 @@ void mg_destroy(mg_ctx* ctx) {
     if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     delete ctx;
 }
 
@@ -854,6 +933,31 @@ int mg_time_dslash(mg_ctx* ctx, int prec, int reps, double* ms_per_launch, doubl
     return prec == MG_FP32 ? run(float{}) : run(double{});
 }
 
+int mg_profile_enable(mg_ctx* ctx, int on) {
+    if (!ctx) return MG_ERR_INVALID_ARG;
+    ctx->prof = on != 0;
+    return MG_OK;
+}
+
+int mg_profile_read(mg_ctx* ctx, double* ms, int* launches, double* coarse_iters) {
+    if (!ctx || !ms || !launches) return MG_ERR_INVALID_ARG;
+    for (int c = 0; c < MG_K_NCLASSES; ++c) { ms[c] = 0.0; launches[c] = 0; }
+    TRY(read_scalars(ctx, S_CG_TOTAL, 1));
+    if (coarse_iters) *coarse_iters = ctx->h_scal[S_CG_TOTAL] - ctx->coarse_mark;
+    ctx->coarse_mark = ctx->h_scal[S_CG_TOTAL];
+    for (size_t i = 0; i < ctx->ev_class.size(); ++i) {
+        float t = 0;
+        CK(cudaEventElapsedTime(&t, ctx->ev_pool[2 * i], ctx->ev_pool[2 * i + 1]));
+        ms[ctx->ev_class[i]] += t;
+        launches[ctx->ev_class[i]] += 1;
+    }
+    ctx->ev_class.clear();
+    ctx->ev_used = 0;
+    return MG_OK;
+}
+
+long long mg_kernel_launches(void) { return launch_counter().load(std::memory_order_relaxed); }
+
 const char* mg_status_string(int status) {
     int i = -status;
     if (i < 0 || i >= (int)(sizeof(kStatusNames) / sizeof(kStatusNames[0]))) return "MG_ERR_UNKNOWN";
@@ -927,25 +1031,18 @@ extern "C" int mg_coarse_solve_noalloc(mg_ctx* ctx, const double* rc_dev, double
     R.partials = (double*)(base + 4 * kNoAllocVecBytes);
     R.scal = (double*)(base + 4 * kNoAllocVecBytes + kNoAllocPartialsBytes);
     R.ticket = (unsigned int*)(base + 4 * kNoAllocVecBytes + kNoAllocPartialsBytes + kNoAllocScalBytes);
-    // the arrival counter must start at zero; everything else is written before it is read
-    CK(cudaMemsetAsync(R.ticket, 0, sizeof(unsigned int), ctx->st));
-    const v2<double>* A = L.A64;
-    v2<double>* y = (v2<double>*)y_dev;
-    cg_init<double>(y, r, (const v2<double>*)rc_dev, n, tol, maxit, R, ctx->st);
-    cg_first_direction<double>(s, p, r, A, L.nc, ctx->g, R, ctx->st);
-    CKL();
-    int check = ctx->prm.coarse_check > 0 ? ctx->prm.coarse_check : 16;
-    int launched = 0;
-    for (;;) {
-        for (int j = 0; j < check; ++j) cg_step<double>(y, r, s, p, q, A, L.nc, ctx->g, R, ctx->st);
-        CKL();
-        launched += check;
-        CK(cudaMemcpyAsync(ctx->h_scal + S_CG_RC2, R.scal + S_CG_RC2, sizeof(double) * 4, cudaMemcpyDeviceToHost,
-                           ctx->st));
-        CK(cudaStreamSynchronize(ctx->st));
-        if (ctx->h_scal[S_CG_DONE] != 0.0) break;
-        if (launched > maxit + check) return fail(ctx, MG_ERR_NUMERIC, "coarse solve did not stop");
-    }
+    // the barrier counters and the error flag must start at zero; everything
+    // else is written before it is read
+    unsigned int* bar = R.ticket;
+    CK(cudaMemsetAsync(bar, 0, sizeof(unsigned int) * 3, ctx->st));
+    CgnrArgs<double> a = cgnr_args<double>(L, ctx->g, (const v2<double>*)rc_dev, (v2<double>*)y_dev, r, s, p, q, tol,
+                                           maxit, R.partials, bar, R.scal);
+    CK(cgnr_persistent<double>(a, ctx->st));
+    CK(cudaMemcpyAsync(ctx->h_scal + S_CG_RC2, R.scal + S_CG_RC2, sizeof(double) * 3, cudaMemcpyDeviceToHost, ctx->st));
+    unsigned int flags[3];
+    CK(cudaMemcpyAsync(flags, bar, sizeof(flags), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    if (flags[2]) return fail(ctx, MG_ERR_TIMEOUT, "coarse solve: a grid barrier wait gave up");
     if (iters) *iters = (int)ctx->h_scal[S_CG_ITERS];
     if (final_rel)
         *final_rel = ctx->h_scal[S_CG_RC2] > 0 ? std::sqrt(ctx->h_scal[S_CG_R2] / ctx->h_scal[S_CG_RC2]) : 0.0;

@@ -1,9 +1,16 @@
 // Host-side launchers of the library's kernels (internal, not part of the C-ABI).
 #pragma once
 #include <cuda_runtime.h>
+
+#include <atomic>
+
 #include "mg_common.cuh"
 
 namespace wmg {
+
+// Count of kernel launches issued by this library (all contexts, all threads).
+std::atomic<long long>& launch_counter();
+inline void note_launch() { launch_counter().fetch_add(1, std::memory_order_relaxed); }
 
 // Scratch used by the single-pass grid reductions: per-block partial sums and
 // an arrival counter that the last block resets to zero.
@@ -65,6 +72,9 @@ template <typename T> void prolong(v2<T>* e, const v2<T>* P, const v2<T>* yc, in
 // A64 (column-major blocks) = P^dag D P; Aself scratch of Vc*8*nc*nc complex
 void coarse_build(double2* A, double2* Aself, const double2* P, const double2* U, int nv, double mass, const Geom& g,
                   cudaStream_t st);
+// same with FP32 products (P, U in FP32), per-chunk sums added in FP64
+void coarse_build_f32(double2* A, double2* Aself, const float2* P, const float2* U, int nv, double mass, const Geom& g,
+                      cudaStream_t st);
 void coarse_shift_mass(double2* A, int nc, double dm, const Geom& g, cudaStream_t st);
 // y = D_c x (dag: sigma3 D_c sigma3 x); with slot >= 0 also scal[slot] = ||y||^2
 template <typename T>
@@ -85,5 +95,29 @@ void cg_first_direction(v2<T>* s, v2<T>* p, const v2<T>* r, const v2<T>* A, int 
 template <typename T>
 void cg_step(v2<T>* y, v2<T>* r, v2<T>* s, v2<T>* p, v2<T>* q, const v2<T>* A, int nc, const Geom& g, const Reduce& R,
              cudaStream_t st);
+
+// Whole CGNR solve in one cooperative launch (bounded-wait grid barriers).
+// q = D_c p is carried by the recurrence q = D_c s + beta q (three barriers per iteration).
+// Writes scal[S_CG_ITERS, S_CG_R2, S_CG_RC2], adds the count to scal[S_CG_TOTAL];
+// *err = 1 if a barrier wait gave up.
+template <typename T> struct CgnrArgs {
+    v2<T>* y;
+    v2<T>* r;
+    v2<T>* s;
+    v2<T>* p;
+    v2<T>* q;
+    const v2<T>* A;
+    const v2<T>* rc;
+    int nc;
+    int xpb;               // aggregates per CTA (set by the launcher)
+    Geom g;
+    double tol2;
+    int maxit;
+    double* partials;      // >= 4 * (co-resident CTAs) doubles
+    unsigned int* bar;     // 2 zeroed counters
+    double* scal;
+    int* err;
+};
+template <typename T> cudaError_t cgnr_persistent(const CgnrArgs<T>& args, cudaStream_t st);
 
 }  // namespace wmg
