@@ -173,7 +173,7 @@ int mg_coarse_solve(mg_ctx* ctx, const double* rc, double* y, double tol, int ma
  * buffers of Vc * 2 Nv complex doubles (boundary coarse-vector layout) that
  * the caller owns.  It calls no cudaMalloc/cudaFree and no allocating library
  * routine: its work vectors, reduction partial sums and scalars live in one
- * file-scope __device__ array of 4 * 65536 complex doubles plus about 640 KB,
+ * file-scope __device__ array of 6 * 65536 complex doubles plus about 640 KB,
  * which every GPU that loads this library holds until the process exits.
  *   - Sizes: Vc * 2 Nv must be <= 65536, else MG_ERR_INVALID_ARG.
  *   - The first call on a device looks up the array's device address on that

@@ -644,24 +644,22 @@ template <typename T> __device__ __forceinline__ void write_partial(T v, double*
     if (threadIdx.x == 0) partials[(size_t)blockIdx.x * 4 + slot] = (double)a;
 }
 
-// Coarse stencil on the aggregates of this CTA, `xpb` aggregates at a time.
-// Thread (x, d, row group) accumulates R consecutive rows a of block
-// A[X][d] (R = 2 for FP32: one 16-byte load carries rows a, a+1 of column b)
-// against in[X+d] staged in shared memory, with 8 independent loads in
-// flight; shared memory then sums the 9 directions.  DAG: sigma3 D_c sigma3.
-// Epilogue EPI:
-//   0: out = result;                          returns ||out||^2 share
-//   1: p = s + beta p, q = result + beta q;   returns ||q||^2 share   (out unused)
-//   2: p = s, q = result;                     returns ||q||^2 share
+// One CG phase on the aggregates of this CTA, `xpb` at a time: stage the
+// operand on X and its 8 neighbours in shared memory, then apply the coarse
+// stencil.  Thread (x, d, row group) accumulates R consecutive rows a of block
+// A[X][d] (one 16-byte load carries rows a, a+1 of column b) with U
+// independent loads in flight; shared memory sums the 9 directions.
+// The operand is formed while staging (STAGE):
+//   ST_P: pn = s + beta * p_old   (first iteration: pn = s); own entries -> p_new
+//         output q = D_c pn;          partial sums: n0 = ||q||^2
+//   ST_R: rn = r_old - alpha * q; own entries -> r_new, y += alpha * p_cur;
+//         output s = D_c^dag rn;      partial sums: n0 = ||s||^2, n1 = ||rn||^2
+//   ST_PLAIN: operand = in;          output out = D_c(^dag) in, n0 = ||out||^2
+enum { ST_PLAIN = 0, ST_P = 1, ST_R = 2 };
+
 template <typename T> struct RowsPerThread { static constexpr int value = 2; };
 
 template <typename T, int R> struct RowLoad;
-template <typename T> struct RowLoad<T, 1> {
-    static __device__ __forceinline__ void load(const v2<T>* p, cx<T> (&v)[1]) {
-        v2<T> a = __ldg(p);
-        v[0] = cx<T>(a.x, a.y);
-    }
-};
 template <> struct RowLoad<double, 2> {
     static __device__ __forceinline__ void load(const v2<double>* p, cx<double> (&v)[2]) {
         double2 a = __ldg(p), b = __ldg(p + 1);
@@ -677,13 +675,25 @@ template <> struct RowLoad<float, 2> {
     }
 };
 
-template <typename T, bool DAG, int EPI>
-__device__ T coarse_apply_cta(v2<T>* __restrict__ out, const v2<T>* __restrict__ A, const v2<T>* __restrict__ in,
-                                  int nc, int xpb, const Geom& g, v2<T>* xs, cx<T>* part, const v2<T>* __restrict__ sv,
-                                  v2<T>* __restrict__ p, v2<T>* __restrict__ q, T beta) {
+template <typename T> struct PhaseArgs {
+    const v2<T>* in;       // ST_PLAIN operand
+    const v2<T>* s;        // ST_P: s
+    const v2<T>* p_old;    // ST_P: previous direction (ignored when first)
+    v2<T>* p_new;          // ST_P: own entries of pn; ST_R: p_cur (read)
+    const v2<T>* r_old;    // ST_R
+    const v2<T>* q;        // ST_R
+    v2<T>* r_new;          // ST_R
+    v2<T>* y;              // ST_R
+    v2<T>* out;            // result
+    T coef;                // beta (ST_P) or alpha (ST_R)
+    bool first;            // ST_P, first iteration
+};
+
+template <typename T, bool DAG, int STAGE>
+__device__ void cg_phase(const PhaseArgs<T>& ph, const v2<T>* __restrict__ A, int nc, int xpb, const Geom& g,
+                         v2<T>* xs, cx<T>* part, T& n0, T& n1) {
     constexpr int R = RowsPerThread<T>::value;
     const int nvh = nc >> 1, nrow = 9 * nc, ngrp = nc / R, nthr = 9 * ngrp, nall = xpb * nrow;
-    T nrm = 0;
     const int xl = threadIdx.x / nthr, rem = threadIdx.x - xl * nthr;
     const int d = rem / ngrp, a0 = (rem - d * ngrp) * R;
     for (int Xb = blockIdx.x * xpb; Xb < g.Vc; Xb += gridDim.x * xpb) {
@@ -693,9 +703,24 @@ __device__ T coarse_apply_cta(v2<T>* __restrict__ out, const v2<T>* __restrict__
             int X = Xb + xi;
             if (X < g.Vc) {
                 int Y = coarse_neighbour(g, X, di);
-                v2<T> v = in[(size_t)Y * nc + b];
-                if (DAG && b >= nvh) { v.x = -v.x; v.y = -v.y; }
-                xs[i] = v;
+                size_t o = (size_t)Y * nc + b;
+                cx<T> v;
+                if (STAGE == ST_PLAIN) {
+                    v = ld<T>(ph.in + o);
+                } else if (STAGE == ST_P) {
+                    v = ld<T>(ph.s + o);
+                    if (!ph.first) v = v + ph.coef * ld<T>(ph.p_old + o);
+                    if (di == 0) st<T>(ph.p_new + o, v);
+                } else {
+                    v = ld<T>(ph.r_old + o) - ph.coef * ld<T>(ph.q + o);
+                    if (di == 0) {
+                        st<T>(ph.r_new + o, v);
+                        st<T>(ph.y + o, ld<T>(ph.y + o) + ph.coef * ld<T>(ph.p_new + o));
+                        n1 += norm2(v);
+                    }
+                }
+                if (DAG && b >= nvh) v = cx<T>(-v.r, -v.i);
+                st<T>(xs + i, v);
             }
         }
         __syncthreads();
@@ -706,7 +731,7 @@ __device__ T coarse_apply_cta(v2<T>* __restrict__ out, const v2<T>* __restrict__
             cx<T> acc[R][2];
 #pragma unroll
             for (int r = 0; r < R; ++r) { acc[r][0] = cx<T>(0, 0); acc[r][1] = cx<T>(0, 0); }
-            constexpr int U = 4;   // independent 16-byte loads in flight per thread
+            constexpr int U = 4;
             for (int b0 = 0; b0 < nc; b0 += U) {
                 cx<T> av[U][R];
 #pragma unroll
@@ -732,33 +757,20 @@ __device__ T coarse_apply_cta(v2<T>* __restrict__ out, const v2<T>* __restrict__
 #pragma unroll
                 for (int dd = 1; dd < 9; ++dd) sum = sum + part[x2 * nrow + dd * nc + a2];
                 if (DAG && a2 >= nvh) sum = cx<T>(-sum.r, -sum.i);
-                size_t o = (size_t)X2 * nc + a2;
-                if (EPI == 0) {
-                    st<T>(out + o, sum);
-                    nrm += norm2(sum);
-                } else {
-                    cx<T> pn = ld<T>(sv + o), qn = sum;
-                    if (EPI == 1) {
-                        pn = pn + beta * ld<T>(p + o);
-                        qn = qn + beta * ld<T>(q + o);
-                    }
-                    st<T>(p + o, pn);
-                    st<T>(q + o, qn);
-                    nrm += norm2(qn);
-                }
+                st<T>(ph.out + (size_t)X2 * nc + a2, sum);
+                n0 += norm2(sum);
             }
         }
         __syncthreads();
     }
-    return nrm;
 }
 
-// CGLS (CG on the normal equations, textbook form), four phases per iteration
-// separated by grid barriers:
-//   A: q = D_c p, alpha = gamma / ||q||^2
-//   B: y += alpha p, r -= alpha q, ||r||^2, stopping test
-//   C: s = D_c^dag r, gamma' = ||s||^2, beta = gamma'/gamma
-//   D: p = s + beta p
+// CGLS (CG on the normal equations), the textbook recurrences
+//   q = D_c p, alpha = gamma/||q||^2, y += alpha p, r -= alpha q,
+//   s = D_c^dag r, beta = ||s||^2/gamma, p = s + beta p
+// with two grid barriers per iteration: the elementwise updates of p and r are
+// done while staging the neighbour operands of the next stencil (p and r
+// double-buffered so that no CTA overwrites what another still reads).
 template <typename T> struct CgnrMaxThreads { static constexpr int value = 384; };
 
 template <typename T>
@@ -769,60 +781,68 @@ __global__ void __launch_bounds__(CgnrMaxThreads<T>::value, 2) k_cgnr_persistent
     cx<T>* part = reinterpret_cast<cx<T>*>(smem_raw + sizeof(v2<T>) * 9 * nc * xpb);
     __shared__ T shr[33];
     const unsigned int G = gridDim.x;
-    const size_t n = (size_t)a.g.Vc * nc;
-    const size_t chunk = (n + G - 1) / G;
-    const size_t i0 = (size_t)blockIdx.x * chunk, i1 = min(n, i0 + chunk);
     unsigned int* cnt = a.bar;
     unsigned int* gen = a.bar + 1;
-    // y = 0, r = rc, ||rc||^2
+    v2<T>* rbuf[2] = {a.r, a.r1};
+    v2<T>* pbuf[2] = {a.p, a.p1};
+    // y = 0, r = rc on the aggregates of this CTA; ||rc||^2
     T loc = 0;
-    for (size_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-        v2<T> v = a.rc[i];
-        a.r[i] = v;
-        v2<T> z; z.x = 0; z.y = 0;
-        a.y[i] = z;
-        loc += v.x * v.x + v.y * v.y;
-    }
+    for (int Xb = blockIdx.x * xpb; Xb < a.g.Vc; Xb += G * xpb)
+        for (int t = threadIdx.x; t < xpb * nc; t += blockDim.x) {
+            int X = Xb + t / nc;
+            if (X < a.g.Vc) {
+                size_t o = (size_t)X * nc + (t % nc);
+                v2<T> v = a.rc[o];
+                a.r[o] = v;
+                v2<T> z; z.x = 0; z.y = 0;
+                a.y[o] = z;
+                loc += v.x * v.x + v.y * v.y;
+            }
+        }
     write_partial<T>(loc, a.partials, 0, shr);
     if (!grid_sync(cnt, gen, G, a.err)) return;
     const T rc2 = sum_partials<T>(a.partials, 0, G, shr);
     int it = 0;
     T r2 = rc2;
     if (rc2 > T(0) && a.maxit > 0) {
-        // s = D_c^dag r, gamma = ||s||^2, p = s
-        loc = coarse_apply_cta<T, true, 0>(a.s, a.A, a.r, nc, xpb, a.g, xs, part, nullptr, nullptr, nullptr, T(0));
-        write_partial<T>(loc, a.partials, 1, shr);
+        PhaseArgs<T> ph{};
+        T n0 = 0, n1 = 0;
+        // s = D_c^dag r, gamma = ||s||^2
+        ph.in = a.r;
+        ph.out = a.s;
+        cg_phase<T, true, ST_PLAIN>(ph, a.A, nc, xpb, a.g, xs, part, n0, n1);
+        write_partial<T>(n0, a.partials, 1, shr);
         if (!grid_sync(cnt, gen, G, a.err)) return;
         T gamma = sum_partials<T>(a.partials, 1, G, shr);
-        for (size_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) a.p[i] = a.s[i];
-        if (!grid_sync(cnt, gen, G, a.err)) return;
-        while (it < a.maxit) {
-            loc = coarse_apply_cta<T, false, 0>(a.q, a.A, a.p, nc, xpb, a.g, xs, part, nullptr, nullptr, nullptr, T(0));
-            write_partial<T>(loc, a.partials, 0, shr);
+        T beta = 0;
+        for (;;) {
+            const int b = it & 1;
+            // p = s + beta p; q = D_c p
+            ph = PhaseArgs<T>{};
+            ph.s = a.s; ph.p_old = pbuf[b ^ 1]; ph.p_new = pbuf[b]; ph.out = a.q;
+            ph.coef = beta; ph.first = (it == 0);
+            n0 = 0; n1 = 0;
+            cg_phase<T, false, ST_P>(ph, a.A, nc, xpb, a.g, xs, part, n0, n1);
+            write_partial<T>(n0, a.partials, 0, shr);
             if (!grid_sync(cnt, gen, G, a.err)) return;
             T qq = sum_partials<T>(a.partials, 0, G, shr);
             if (!(qq > T(0))) break;
-            T al = gamma / qq;
-            loc = 0;
-            for (size_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-                st<T>(a.y + i, ld<T>(a.y + i) + al * ld<T>(a.p + i));
-                cx<T> v = ld<T>(a.r + i) - al * ld<T>(a.q + i);
-                st<T>(a.r + i, v);
-                loc += norm2(v);
-            }
-            write_partial<T>(loc, a.partials, 1, shr);
+            T alpha = gamma / qq;
+            // y += alpha p; r -= alpha q; s = D_c^dag r
+            ph = PhaseArgs<T>{};
+            ph.r_old = rbuf[b]; ph.q = a.q; ph.r_new = rbuf[b ^ 1]; ph.y = a.y; ph.p_new = pbuf[b];
+            ph.out = a.s; ph.coef = alpha;
+            n0 = 0; n1 = 0;
+            cg_phase<T, true, ST_R>(ph, a.A, nc, xpb, a.g, xs, part, n0, n1);
+            write_partial<T>(n0, a.partials, 1, shr);
+            write_partial<T>(n1, a.partials, 2, shr);
             if (!grid_sync(cnt, gen, G, a.err)) return;
-            r2 = sum_partials<T>(a.partials, 1, G, shr);
+            T gnew = sum_partials<T>(a.partials, 1, G, shr);
+            r2 = sum_partials<T>(a.partials, 2, G, shr);
             ++it;
             if (r2 <= (T)a.tol2 * rc2 || it >= a.maxit) break;
-            loc = coarse_apply_cta<T, true, 0>(a.s, a.A, a.r, nc, xpb, a.g, xs, part, nullptr, nullptr, nullptr, T(0));
-            write_partial<T>(loc, a.partials, 2, shr);
-            if (!grid_sync(cnt, gen, G, a.err)) return;
-            T gnew = sum_partials<T>(a.partials, 2, G, shr);
-            T be = gnew / gamma;
+            beta = gnew / gamma;
             gamma = gnew;
-            for (size_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) st<T>(a.p + i, ld<T>(a.s + i) + be * ld<T>(a.p + i));
-            if (!grid_sync(cnt, gen, G, a.err)) return;
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {

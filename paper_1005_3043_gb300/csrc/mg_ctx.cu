@@ -51,6 +51,8 @@ template <typename T> struct Work {
     v2<T>* cs = nullptr;
     v2<T>* cp = nullptr;
     v2<T>* cq = nullptr;
+    v2<T>* cr1 = nullptr;  // second buffers of the coarse CG
+    v2<T>* cp1 = nullptr;
     int cnc = 0;           // coarse dof the coarse vectors are sized for
     bool ready = false;
 };
@@ -195,6 +197,8 @@ template <typename T> int ensure_work(mg_ctx* ctx) {
     TRY(dalloc(ctx, &w.cs, cb));
     TRY(dalloc(ctx, &w.cp, cb));
     TRY(dalloc(ctx, &w.cq, cb));
+    TRY(dalloc(ctx, &w.cr1, cb));
+    TRY(dalloc(ctx, &w.cp1, cb));
     w.cnc = nc;
     w.ready = true;
     return MG_OK;
@@ -260,10 +264,11 @@ int build_level(mg_ctx* ctx, CoarseLevel& L, const double2* V, int nv) {
 
 // ---------------------------------------------------------------- coarse solve
 template <typename T>
-CgnrArgs<T> cgnr_args(const CoarseLevel& L, const Geom& g, const v2<T>* rc, v2<T>* y, v2<T>* r, v2<T>* sv, v2<T>* p,
-                      v2<T>* q, double tol, int maxit, double* partials, unsigned int* bar, double* scal) {
+CgnrArgs<T> cgnr_args(const CoarseLevel& L, const Geom& g, const v2<T>* rc, v2<T>* y, v2<T>* r, v2<T>* r1, v2<T>* sv,
+                      v2<T>* p, v2<T>* p1, v2<T>* q, double tol, int maxit, double* partials, unsigned int* bar,
+                      double* scal) {
     CgnrArgs<T> a;
-    a.y = y; a.r = r; a.s = sv; a.p = p; a.q = q;
+    a.y = y; a.r = r; a.r1 = r1; a.s = sv; a.p = p; a.p1 = p1; a.q = q;
     a.A = lvlA<T>(L); a.rc = rc; a.nc = L.nc; a.g = g;
     a.tol2 = tol * tol; a.maxit = maxit;
     a.partials = partials; a.bar = bar; a.scal = scal; a.err = (int*)(bar + 2);
@@ -276,8 +281,8 @@ CgnrArgs<T> cgnr_args(const CoarseLevel& L, const Geom& g, const v2<T>* rc, v2<T
 template <typename T>
 int coarse_solve(mg_ctx* ctx, const CoarseLevel& L, const v2<T>* rc, v2<T>* y, double tol, int maxit, int* iters) {
     Work<T>& w = work<T>(ctx);
-    CgnrArgs<T> a = cgnr_args<T>(L, ctx->g, rc, y, w.cr, w.cs, w.cp, w.cq, tol, maxit, ctx->R.partials, ctx->bar,
-                                 ctx->R.scal);
+    CgnrArgs<T> a = cgnr_args<T>(L, ctx->g, rc, y, w.cr, w.cr1, w.cs, w.cp, w.cp1, w.cq, tol, maxit, ctx->R.partials,
+                                 ctx->bar, ctx->R.scal);
     CK(cudaMemsetAsync(ctx->bar, 0, sizeof(unsigned int) * 3, ctx->st));
     PROF_BEGIN(MG_K_COARSE_SOLVE);
     CK(cgnr_persistent<T>(a, ctx->st));
@@ -983,7 +988,7 @@ constexpr size_t kNoAllocMaxCoarseDof = 65536;              // coarse sites x 2 
 constexpr size_t kNoAllocVecBytes = kNoAllocMaxCoarseDof * sizeof(double2);
 constexpr size_t kNoAllocPartialsBytes = (size_t)kMaxReduceBlocks * 64 * sizeof(double);
 constexpr size_t kNoAllocScalBytes = ((S_COUNT * sizeof(double) + 255) / 256) * 256;
-constexpr size_t kNoAllocScratchBytes = 4 * kNoAllocVecBytes + kNoAllocPartialsBytes + kNoAllocScalBytes + 256;
+constexpr size_t kNoAllocScratchBytes = 6 * kNoAllocVecBytes + kNoAllocPartialsBytes + kNoAllocScalBytes + 256;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
@@ -1024,19 +1029,21 @@ extern "C" int mg_coarse_solve_noalloc(mg_ctx* ctx, const double* rc_dev, double
     unsigned char* base = nullptr;
     TRY(noalloc_scratch(ctx, &base));
     v2<double>* r = (v2<double>*)base;
-    v2<double>* s = (v2<double>*)(base + kNoAllocVecBytes);
-    v2<double>* p = (v2<double>*)(base + 2 * kNoAllocVecBytes);
-    v2<double>* q = (v2<double>*)(base + 3 * kNoAllocVecBytes);
+    v2<double>* r1 = (v2<double>*)(base + kNoAllocVecBytes);
+    v2<double>* s = (v2<double>*)(base + 2 * kNoAllocVecBytes);
+    v2<double>* p = (v2<double>*)(base + 3 * kNoAllocVecBytes);
+    v2<double>* p1 = (v2<double>*)(base + 4 * kNoAllocVecBytes);
+    v2<double>* q = (v2<double>*)(base + 5 * kNoAllocVecBytes);
     Reduce R;
-    R.partials = (double*)(base + 4 * kNoAllocVecBytes);
-    R.scal = (double*)(base + 4 * kNoAllocVecBytes + kNoAllocPartialsBytes);
-    R.ticket = (unsigned int*)(base + 4 * kNoAllocVecBytes + kNoAllocPartialsBytes + kNoAllocScalBytes);
+    R.partials = (double*)(base + 6 * kNoAllocVecBytes);
+    R.scal = (double*)(base + 6 * kNoAllocVecBytes + kNoAllocPartialsBytes);
+    R.ticket = (unsigned int*)(base + 6 * kNoAllocVecBytes + kNoAllocPartialsBytes + kNoAllocScalBytes);
     // the barrier counters and the error flag must start at zero; everything
     // else is written before it is read
     unsigned int* bar = R.ticket;
     CK(cudaMemsetAsync(bar, 0, sizeof(unsigned int) * 3, ctx->st));
-    CgnrArgs<double> a = cgnr_args<double>(L, ctx->g, (const v2<double>*)rc_dev, (v2<double>*)y_dev, r, s, p, q, tol,
-                                           maxit, R.partials, bar, R.scal);
+    CgnrArgs<double> a = cgnr_args<double>(L, ctx->g, (const v2<double>*)rc_dev, (v2<double>*)y_dev, r, r1, s, p, p1, q,
+                                           tol, maxit, R.partials, bar, R.scal);
     CK(cgnr_persistent<double>(a, ctx->st));
     CK(cudaMemcpyAsync(ctx->h_scal + S_CG_RC2, R.scal + S_CG_RC2, sizeof(double) * 3, cudaMemcpyDeviceToHost, ctx->st));
     unsigned int flags[3];

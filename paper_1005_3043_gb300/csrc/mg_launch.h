@@ -96,15 +96,16 @@ template <typename T>
 void cg_step(v2<T>* y, v2<T>* r, v2<T>* s, v2<T>* p, v2<T>* q, const v2<T>* A, int nc, const Geom& g, const Reduce& R,
              cudaStream_t st);
 
-// Whole CGNR solve in one cooperative launch (bounded-wait grid barriers).
-// q = D_c p is carried by the recurrence q = D_c s + beta q (three barriers per iteration).
+// Whole CGNR solve in one cooperative launch (bounded-wait grid barriers, two per iteration).
 // Writes scal[S_CG_ITERS, S_CG_R2, S_CG_RC2], adds the count to scal[S_CG_TOTAL];
 // *err = 1 if a barrier wait gave up.
 template <typename T> struct CgnrArgs {
     v2<T>* y;
-    v2<T>* r;
+    v2<T>* r;              // r and r1, p and p1: double buffers
+    v2<T>* r1;
     v2<T>* s;
     v2<T>* p;
+    v2<T>* p1;
     v2<T>* q;
     const v2<T>* A;
     const v2<T>* rc;
