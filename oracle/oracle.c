@@ -112,29 +112,50 @@ static void hop_block(const int* L, int tap, const cplx* U, int64_t x, int mu, i
     *y_out = y;
 }
 
-/* eq. (2): out = D(U) in */
+/* eq. (2): out = D(U) in.  Each hop applies the colour matrix (U^mu_x or
+ * U^{mu dag}_{x-mu}) to every spin component of the neighbour, then the spin
+ * matrix -(1 -/+ gamma_mu)/2 (times -1 across the antiperiodic t face). */
 OR_API void or_dslash(const int* L, int tap, const double* Ur, double m, const double* inr, double* outr) {
     const cplx* U = (const cplx*)Ur;
     const cplx* in = (const cplx*)inr;
     cplx* out = (cplx*)outr;
     int64_t V = vol(L);
     init_gamma();
+    cplx S[4][2][4][4];                       /* S[mu][fwd 0 / bwd 1] = (1 -/+ gamma_mu)/2 */
+    for (int mu = 0; mu < 4; ++mu)
+        for (int f = 0; f < 2; ++f)
+            for (int al = 0; al < 4; ++al)
+                for (int be = 0; be < 4; ++be)
+                    S[mu][f][al][be] = 0.5 * ((al == be ? 1.0 : 0.0) - (f == 0 ? 1.0 : -1.0) * GAMMA[mu][al][be]);
 #pragma omp parallel for schedule(static)
     for (int64_t x = 0; x < V; ++x) {
-        cplx acc[12];
-        for (int k = 0; k < 12; ++k) acc[k] = (4.0 + m) * in[12 * x + k];
+        cplx acc[4][3];
+        for (int al = 0; al < 4; ++al)
+            for (int a = 0; a < 3; ++a) acc[al][a] = (4.0 + m) * in[12 * x + 3 * al + a];
         for (int mu = 0; mu < 4; ++mu)
-            for (int dir = 1; dir >= -1; dir -= 2) {
-                cplx H[12][12];
-                int64_t y;
-                hop_block(L, tap, U, x, mu, dir, H, &y);
-                for (int k = 0; k < 12; ++k) {
-                    cplx s = 0;
-                    for (int l = 0; l < 12; ++l) s += H[k][l] * in[12 * y + l];
-                    acc[k] += s;
-                }
+            for (int f = 0; f < 2; ++f) {
+                double sign;
+                int64_t y = neighbour(L, tap, x, mu, f == 0 ? 1 : -1, &sign);
+                const cplx* u = U + 9 * (mu * V + (f == 0 ? x : y));
+                cplx w[4][3];                 /* colour matrix on every spin component of psi(y) */
+                for (int be = 0; be < 4; ++be)
+                    for (int a = 0; a < 3; ++a) {
+                        cplx t = 0;
+                        for (int b = 0; b < 3; ++b) {
+                            cplx uab = (f == 0) ? u[3 * a + b] : conj(u[3 * b + a]);
+                            t += uab * in[12 * y + 3 * be + b];
+                        }
+                        w[be][a] = t;
+                    }
+                for (int al = 0; al < 4; ++al)
+                    for (int a = 0; a < 3; ++a) {
+                        cplx t = 0;
+                        for (int be = 0; be < 4; ++be) t += S[mu][f][al][be] * w[be][a];
+                        acc[al][a] -= sign * t;
+                    }
             }
-        for (int k = 0; k < 12; ++k) out[12 * x + k] = acc[k];
+        for (int al = 0; al < 4; ++al)
+            for (int a = 0; a < 3; ++a) out[12 * x + 3 * al + a] = acc[al][a];
     }
 }
 

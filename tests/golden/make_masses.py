@@ -24,11 +24,19 @@ WORKLOADS = {
 }
 
 
-def re_lambda_min(L, U, ncv=60, tol=1e-9):
+def re_lambda_min(L, U, k=6, ncv=60, tol=1e-9):
     V = oracle.volume(L)
-    op = sla.LinearOperator((V * 12, V * 12), dtype=np.complex128,
-                            matvec=lambda v: oracle.dslash(U, v.reshape(V, 4, 3), 0.0, L).ravel())
-    ev = sla.eigs(op, k=6, which="SR", ncv=ncv, tol=tol, return_eigenvectors=False)
+    count = [0]
+    t0 = time.time()
+
+    def mv(v):
+        count[0] += 1
+        if count[0] % 500 == 0:
+            print(f"  {count[0]} matvecs, {time.time() - t0:.0f} s", flush=True)
+        return oracle.dslash(U, v.reshape(V, 4, 3), 0.0, L).ravel()
+
+    op = sla.LinearOperator((V * 12, V * 12), dtype=np.complex128, matvec=mv)
+    ev = sla.eigs(op, k=k, which="SR", ncv=ncv, tol=tol, return_eigenvectors=False)
     return float(np.min(ev.real)), ev
 
 
@@ -37,7 +45,8 @@ if __name__ == "__main__":
     w = WORKLOADS[name]
     U = synth.gauge_field(w["L"], beta=6.0, sweeps=200, n_or=4, seed=w["seed"])
     t = time.time()
-    lam, ev = re_lambda_min(w["L"], U)
+    big = oracle.volume(w["L"]) > 100000
+    lam, ev = re_lambda_min(w["L"], U, k=8 if big else 6, ncv=100 if big else 60, tol=1e-7 if big else 1e-9)
     out = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"{name}_mass.txt")
     with open(out, "w") as f:
         f.write(f"# {name}: L={w['L']} beta=6.0 sweeps=200 n_or=4 seed={w['seed']}\n")
