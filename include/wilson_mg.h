@@ -140,6 +140,25 @@ int mg_solve(mg_ctx* ctx, const double* b, double* x, mg_solve_info* info);
 /* As mg_solve with b and x in device memory (boundary layout, FP64). */
 int mg_solve_device(mg_ctx* ctx, const double* b_dev, double* x_dev, mg_solve_info* info);
 
+/* Solve D x_n = b_n for nrhs sources together (12 spin-colour point sources
+ * plus Gaussian sources, say): flexible GCR in lockstep over the sources, each
+ * with its own Krylov space and scalars, the fine-level steps per source and
+ * the coarse solve of all sources as one batched CGNR on an RHS panel, its
+ * stencil a dense contraction on the tensor cores (FP16 operator, FP16 hi+lo
+ * panel, FP32 accumulation), its iterations replayed from a captured CUDA
+ * graph.  b, x: nrhs consecutive host fine spinors; info: nrhs entries.
+ * Needs prec_inner == MG_FP32 and 2*nvec a multiple of 16 (<= 128),
+ * nrhs <= 256; with MG_FP64 the sources are solved one after another. */
+int mg_solve_batched(mg_ctx* ctx, const double* b, double* x, int nrhs, mg_solve_info* info);
+
+/* As mg_solve_batched with b and x in device memory (boundary layout). */
+int mg_solve_batched_device(mg_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, mg_solve_info* info);
+
+/* Coarse stencil on nrhs coarse vectors at once: y_n = D_c x_n (dagger: D_c^dag).
+ * x, y: nrhs consecutive host coarse vectors.  impl 0: tensor cores (FP16
+ * operator, as in the batched solve); impl 1: SIMT with the FP64 operator. */
+int mg_apply_coarse_batched(mg_ctx* ctx, const double* x, double* y, int nrhs, int dagger, int impl);
+
 /* ---- single steps of the method (host buffers, FP64 at the boundary; the
  * ---- kernel runs in precision prec) -------------------------------------- */
 

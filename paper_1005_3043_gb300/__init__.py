@@ -76,6 +76,9 @@ _SIGS = {
     "mg_get_coarse_op": ([_P, _P], _I),
     "mg_solve": ([_P, _P, _P, _P], _I),
     "mg_solve_device": ([_P, _P, _P, _P], _I),
+    "mg_solve_batched": ([_P, _P, _P, _I, _P], _I),
+    "mg_solve_batched_device": ([_P, _P, _P, _I, _P], _I),
+    "mg_apply_coarse_batched": ([_P, _P, _P, _I, _I, _I], _I),
     "mg_apply_dslash": ([_P, _P, _P, _I], _I),
     "mg_restrict": ([_P, _P, _P, _I], _I),
     "mg_prolong": ([_P, _P, _P, _I], _I),
@@ -231,6 +234,31 @@ def mg_solve_device(ctx, b_dev, x_dev) -> dict:
     return info.as_dict()
 
 
+def mg_solve_batched(ctx, b):
+    """b (nrhs, V, 4, 3) host -> (x, [info dicts])."""
+    b = _host(b)
+    nrhs = b.shape[0]
+    x = np.empty_like(b)
+    infos = (MgSolveInfo * nrhs)()
+    _check(load().mg_solve_batched(ctx, _ptr(b), _ptr(x), nrhs, infos), ctx, allow=(MG_ERR_NOT_CONVERGED,))
+    return x, [i.as_dict() for i in infos]
+
+
+def mg_solve_batched_device(ctx, b_dev, x_dev, nrhs: int):
+    infos = (MgSolveInfo * nrhs)()
+    _check(load().mg_solve_batched_device(ctx, _dev_ptr(b_dev), _dev_ptr(x_dev), int(nrhs), infos), ctx,
+           allow=(MG_ERR_NOT_CONVERGED,))
+    return [i.as_dict() for i in infos]
+
+
+def mg_apply_coarse_batched(ctx, x, dagger: bool = False, impl: int = 0) -> np.ndarray:
+    """x (nrhs, Vc, nc) host -> y (nrhs, Vc, nc); impl 0 tensor cores, 1 SIMT FP64."""
+    x = _host(x)
+    y = np.empty_like(x)
+    _check(load().mg_apply_coarse_batched(ctx, _ptr(x), _ptr(y), int(x.shape[0]), int(bool(dagger)), int(impl)), ctx)
+    return y
+
+
 def mg_apply_dslash(ctx, psi, prec: int = MG_FP64) -> np.ndarray:
     psi = _host(psi)
     out = np.empty_like(psi)
@@ -383,6 +411,15 @@ class WilsonMG:
 
     def solve_device(self, b_dev, x_dev):
         return mg_solve_device(self.ctx, b_dev, x_dev)
+
+    def solve_batched(self, b):
+        return mg_solve_batched(self.ctx, b)
+
+    def solve_batched_device(self, b_dev, x_dev, nrhs):
+        return mg_solve_batched_device(self.ctx, b_dev, x_dev, nrhs)
+
+    def coarse_batched(self, x, dagger=False, impl=0):
+        return mg_apply_coarse_batched(self.ctx, x, dagger, impl)
 
     def dslash(self, psi, prec=MG_FP64):
         return mg_apply_dslash(self.ctx, psi, prec)

@@ -1,0 +1,575 @@
+// Batched (multi right-hand side) coarse level: the coarse stencil applied to
+// an RHS panel on the 5th-generation tensor cores, and the per-RHS CGNR steps.
+//
+// Panel layout: xB[X][b][n] complex FP32, n < npad (RHS index fastest, npad a
+// multiple of 16).  For one aggregate X the stencil is a dense contraction
+//   y[X][a][n] = sum_d sum_b A[X][d][a][b] x[X+d][b][n],
+// written as a real GEMM through the embedding
+//   [Re y]   [Re A  -Im A] [Re x]
+//   [Im y] = [Im A   Re A] [Im x]      (M = K = 2 nc per direction d),
+// M padded to 128, K = 9 * 2nc, N = npad.  A is stored once per (X, d) in
+// FP16 in the tensor-core shared-memory layout and copied with the bulk-copy
+// engine; x is split into FP16 hi + lo parts (x = hi + lo to ~22 bits) so two
+// MMAs per K step give an FP32-accurate product against the FP16 operator.
+#include <cuda_fp16.h>
+
+#include "mg_launch.h"
+
+namespace wmg {
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait; returns false after `limit` polls
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit) {
+    for (long long i = 0; i < limit; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (i > 64) __nanosleep(40);
+    }
+    return false;
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16, one CTA
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+// 16 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor, no swizzle, K-major "core matrix" layout:
+// 8 rows x 16 bytes per core matrix; lbo = byte distance between core
+// matrices adjacent in K, sbo = between core matrices adjacent in M/N.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;   // descriptor version for this architecture
+    return d;                 // base offset 0, layout type 0 (no swizzle)
+}
+// instruction descriptor: D FP32, A/B FP16, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// half offset of element (row r, k) in a K-major core-matrix tile with K columns
+__host__ __device__ __forceinline__ int core_off(int r, int k, int K) {
+    return (((r >> 3) * (K >> 3) + (k >> 3)) << 6) + ((r & 7) << 3) + (k & 7);
+}
+
+// ---------------------------------------------------------------- operator embedding
+// Aemb[X][d]: 2nc x 2nc FP16 real embedding of A[X][d] in the core-matrix layout
+// (rows 2nc..127 of the 128-row MMA tile are zero in shared memory only).
+__global__ void k_coarse_embed(__half* Aemb, const double2* __restrict__ A, int nc, long long nblk) {
+    const int K = 2 * nc;
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long total = nblk * K * K;
+    if (idx >= total) return;
+    long long blk = idx / (K * K);
+    int rem = (int)(idx - blk * K * K);
+    int m = rem / K, k = rem - m * K;
+    int a = m % nc, b = k % nc;
+    bool imr = m >= nc, imc = k >= nc;
+    double2 v = A[blk * nc * nc + (size_t)b * nc + a];   // column-major block: A[b][a] = A_ab
+    double e = (!imr && !imc) ? v.x : (!imr && imc) ? -v.y : (imr && !imc) ? v.y : v.x;
+    Aemb[blk * K * K + core_off(m, k, K)] = __double2half(e);
+}
+
+void coarse_embed(__half* Aemb, const double2* A, int nc, int Vc, cudaStream_t st) {
+    long long nblk = (long long)Vc * 9;
+    long long total = nblk * 4 * nc * nc;
+    note_launch();
+    k_coarse_embed<<<(int)((total + 255) / 256), 256, 0, st>>>(Aemb, A, nc, nblk);
+}
+
+// ---------------------------------------------------------------- tensor-core batched stencil
+constexpr int kTcThreads = 128;
+constexpr long long kTcWaitLimit = 20000000LL;
+
+__host__ __device__ inline int tc_tmem_cols(int npad) {
+    int c = 32;
+    while (c < npad) c <<= 1;
+    return c;
+}
+__host__ __device__ inline size_t tc_smem_bytes(int nc, int npad) {
+    size_t K = 2 * nc;
+    size_t SA = 128 * K * 2, SB = (size_t)npad * K * 2;
+    return 2 * SA + 4 * SB + 64;
+}
+
+// One CTA per aggregate X.  Pipeline over the 9 directions d with two stages:
+// the bulk-copy engine brings A_emb[X][d], the CTA writes the hi/lo split of
+// x[X+d] (sigma3 applied for the adjoint), one thread issues the MMAs into the
+// TMEM accumulator (128 lanes = embedded rows, npad columns = RHS).
+__global__ void __launch_bounds__(kTcThreads, 1) k_coarse_apply_tc(TcApplyArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int nc = a.nc, npad = a.npad, K = 2 * nc, nvh = nc / 2;
+    const size_t SA = (size_t)128 * K * 2, SB = (size_t)npad * K * 2;
+    __half* As = reinterpret_cast<__half*>(smem);
+    __half* Bh = reinterpret_cast<__half*>(smem + 2 * SA);
+    __half* Bl = reinterpret_cast<__half*>(smem + 2 * SA + 2 * SB);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * SA + 4 * SB);   // [0,1]: A landed, [2,3]: MMA done
+    __shared__ uint32_t s_taddr;
+    __shared__ int s_fail;
+    __shared__ float s_nrm[4][256];
+    const int X = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t ncols = tc_tmem_cols(npad);
+    const uint32_t bytesA = (uint32_t)(K * K * 2);
+
+    if (tid == 0) {
+        s_fail = 0;
+        for (int i = 0; i < 4; ++i) mbar_init(bar + i, 1);
+        fence_mbar_init();
+    }
+    // zero the padding rows (2nc..127) of both A stages once
+    {
+        const int pad0 = (K >> 3) * (K >> 3) * 64;   // first half of row group 2nc/8
+        for (int st = 0; st < 2; ++st)
+            for (int i = pad0 + tid; i < 128 * K; i += kTcThreads) As[st * 128 * K + i] = __float2half(0.f);
+    }
+    if (warp == 0) {
+        tmem_alloc(&s_taddr, ncols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_taddr;
+    const uint32_t idesc = idesc_f16(128, npad);
+    const uint32_t lbo = 128, sbo = (uint32_t)(K >> 3) * 128;
+
+    for (int d = 0; d < 9; ++d) {
+        const int s = d & 1;
+        if (d >= 2) {
+            // the MMAs that read stage s (direction d-2) must be done before it is rewritten
+            if (!mbar_wait(bar + 2 + s, ((d - 2) >> 1) & 1, kTcWaitLimit)) s_fail = 1;
+        }
+        __syncthreads();
+        if (s_fail) break;
+        if (tid == 0) {
+            mbar_expect_tx(bar + s, bytesA);
+            bulk_copy_g2s(As + (size_t)s * 128 * K, a.Aemb + ((size_t)X * 9 + d) * K * K, bytesA, bar + s);
+        }
+        // B = x[X+d] as hi + lo FP16, rows = RHS n, K-major columns k = (re|im, b)
+        const int Y = coarse_neighbour(a.g, X, d);
+        const float2* xY = a.x + (size_t)Y * nc * npad;
+        __half* bh = Bh + (size_t)s * npad * K;
+        __half* bl = Bl + (size_t)s * npad * K;
+        for (int i = tid; i < nc * npad; i += kTcThreads) {
+            int b = i / npad, n = i - b * npad;
+            float2 v = xY[i];
+            if (a.dag && b >= nvh) { v.x = -v.x; v.y = -v.y; }
+            __half hr = __float2half_rn(v.x), hi = __float2half_rn(v.y);
+            __half lr = __float2half_rn(v.x - __half2float(hr)), li = __float2half_rn(v.y - __half2float(hi));
+            int ore = core_off(n, b, K), oim = core_off(n, b + nc, K);
+            bh[ore] = hr; bl[ore] = lr;
+            bh[oim] = hi; bl[oim] = li;
+        }
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            if (!mbar_wait(bar + s, (d >> 1) & 1, kTcWaitLimit)) {
+                s_fail = 1;
+            } else {
+                tc_fence_after();
+                const uint32_t a0 = smem_u32(As + (size_t)s * 128 * K);
+                const uint32_t bh0 = smem_u32(bh), bl0 = smem_u32(bl);
+                for (int ks = 0; ks < (K >> 4); ++ks) {
+                    uint64_t ad = smem_desc(a0 + ks * 256, lbo, sbo);
+                    mma_f16(tmem, ad, smem_desc(bh0 + ks * 256, lbo, sbo), idesc, (d > 0 || ks > 0) ? 1u : 0u);
+                    mma_f16(tmem, ad, smem_desc(bl0 + ks * 256, lbo, sbo), idesc, 1u);
+                }
+                mma_commit(bar + 2 + s);
+            }
+        }
+    }
+    __syncthreads();
+    // wait for the last commit (direction 8 on stage 0, its 5th use): covers every MMA issued
+    bool ok = (s_fail == 0);
+    if (!mbar_wait(bar + 2, 0, kTcWaitLimit)) ok = false;
+    tc_fence_after();
+    // epilogue: warp w owns TMEM lanes 32w..32w+31 = embedded rows m
+    const int m = warp * 32 + lane;
+    const bool valid_row = m < K;
+    const int arow = m % nc;
+    const bool im = m >= nc;
+    const float sgn = (a.dag && arow >= nvh) ? -1.f : 1.f;
+    float* yf = reinterpret_cast<float*>(a.y);
+    for (int c0 = 0; c0 < npad; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        if (ok && valid_row) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) yf[(((size_t)X * nc + arow) * npad + c0 + j) * 2 + (im ? 1 : 0)] = sgn * v[j];
+        }
+        if (a.norms) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                float q = (ok && valid_row) ? v[j] * v[j] : 0.f;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+                if (lane == 0) s_nrm[warp][c0 + j] = q;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (a.norms)
+        for (int n = tid; n < npad; n += kTcThreads)
+            a.norms[(size_t)X * npad + n] = s_nrm[0][n] + s_nrm[1][n] + s_nrm[2][n] + s_nrm[3][n];
+    if (!ok && tid == 0) atomicExch(a.err, 1);
+    if (warp == 0) tmem_dealloc(tmem, ncols);
+}
+
+// Dynamic shared memory of one CTA: the two pipeline stages, padded so that at
+// most 512 / ncols CTAs fit on an SM (their TMEM allocations never exceed the
+// 512 columns of an SM, so no allocation waits).
+static size_t tc_launch_smem(int nc, int npad) {
+    size_t sm = tc_smem_bytes(nc, npad);
+    size_t per_sm = 228 * 1024, cap = 512 / tc_tmem_cols(npad);
+    size_t min_sm = per_sm / (cap + 1) + 1024;
+    return sm > min_sm ? sm : min_sm;
+}
+bool coarse_apply_tc_supported(int nc, int npad) {
+    return npad % 16 == 0 && npad >= 16 && npad <= 256 && (2 * nc) % 16 == 0 && 2 * nc <= 128 &&
+           tc_launch_smem(nc, npad) + 4224 <= 227 * 1024;
+}
+cudaError_t coarse_apply_tc_prepare(int nc, int npad) {
+    if (!coarse_apply_tc_supported(nc, npad)) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(k_coarse_apply_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tc_launch_smem(nc, npad));
+}
+// launch only (coarse_apply_tc_prepare must have been called for this shape)
+cudaError_t coarse_apply_tc(const TcApplyArgs& args, cudaStream_t st) {
+    note_launch();
+    k_coarse_apply_tc<<<args.g.Vc, kTcThreads, tc_launch_smem(args.nc, args.npad), st>>>(args);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- SIMT reference of the same contraction
+// One thread per (X, a, n); reads the FP64 operator.  Used by the FP64 batched
+// path and to cross-check the tensor-core kernel.
+template <typename T>
+__global__ void k_coarse_apply_batched_simt(v2<T>* __restrict__ y, const double2* __restrict__ A,
+                                            const v2<T>* __restrict__ x, int nc, int npad, int dag, Geom g,
+                                            float* norms) {
+    int X = blockIdx.x, a = blockIdx.y;
+    int nvh = nc / 2;
+    for (int n = threadIdx.x; n < npad; n += blockDim.x) {
+        cx<double> acc(0, 0);
+        for (int d = 0; d < 9; ++d) {
+            int Y = coarse_neighbour(g, X, d);
+            const double2* Ad = A + ((size_t)X * 9 + d) * nc * nc + a;
+            for (int b = 0; b < nc; ++b) {
+                v2<T> xv = x[((size_t)Y * nc + b) * npad + n];
+                cx<double> xb((double)xv.x, (double)xv.y);
+                if (dag && b >= nvh) xb = cx<double>(-xb.r, -xb.i);
+                cmad(acc, ld<double>(Ad + (size_t)b * nc), xb);
+            }
+        }
+        if (dag && a >= nvh) acc = cx<double>(-acc.r, -acc.i);
+        v2<T> o; o.x = (T)acc.r; o.y = (T)acc.i;
+        y[((size_t)X * nc + a) * npad + n] = o;
+    }
+    (void)norms;
+}
+template <typename T>
+void coarse_apply_batched_simt(v2<T>* y, const double2* A, const v2<T>* x, int nc, int npad, bool dag, const Geom& g,
+                               cudaStream_t st) {
+    note_launch();
+    k_coarse_apply_batched_simt<T><<<dim3(g.Vc, nc), 128, 0, st>>>(y, A, x, nc, npad, dag ? 1 : 0, g, nullptr);
+}
+template void coarse_apply_batched_simt<float>(v2<float>*, const double2*, const v2<float>*, int, int, bool,
+                                               const Geom&, cudaStream_t);
+template void coarse_apply_batched_simt<double>(v2<double>*, const double2*, const v2<double>*, int, int, bool,
+                                                const Geom&, cudaStream_t);
+
+// ---------------------------------------------------------------- per-RHS CGNR steps
+// Per-RHS scalars (double, npad entries each) in BatchScal; partial sums over
+// coarse rows go to part[chunk][n].  Columns whose done flag is set are frozen.
+constexpr int kRowChunks = 152;
+
+// column sums of |v|^2 over the rows of one chunk: part[chunk][n]
+__global__ void k_bcol_norm_partial(const float2* __restrict__ v, long long rows, int npad, float* part) {
+    long long r0 = (long long)blockIdx.x * rows / gridDim.x, r1 = (long long)(blockIdx.x + 1) * rows / gridDim.x;
+    for (int n = threadIdx.x; n < npad; n += blockDim.x) {
+        float s = 0.f;
+        for (long long r = r0; r < r1; ++r) {
+            float2 a = v[r * npad + n];
+            s += a.x * a.x + a.y * a.y;
+        }
+        part[(size_t)blockIdx.x * npad + n] = s;
+    }
+}
+
+// initialise: scale_n = ||rc_n||, r = rc / scale, y = 0, done = (scale == 0 || n >= nrhs)
+__global__ void k_bcg_scale(BatchScal S, const float* part, int nchunk, int npad, int nrhs, int maxit) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= npad) return;
+    double s = 0;
+    for (int c = 0; c < nchunk; ++c) s += part[(size_t)c * npad + n];
+    double sc = sqrt(s);
+    S.scale[n] = sc;
+    S.done[n] = (n >= nrhs || !(sc > 0) || maxit <= 0) ? 1.0 : 0.0;
+    S.iters[n] = 0;
+    S.r2[n] = S.done[n] != 0 ? 0.0 : 1.0;
+}
+__global__ void k_bcg_start(float2* __restrict__ y, float2* __restrict__ r, const float2* __restrict__ rc,
+                            long long total, int npad, BatchScal S) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        int n = (int)(i % npad);
+        double sc = S.scale[n];
+        float f = sc > 0 ? (float)(1.0 / sc) : 0.f;
+        float2 v = rc[i];
+        r[i] = make_float2(v.x * f, v.y * f);
+        y[i] = make_float2(0.f, 0.f);
+    }
+}
+// gamma = ||s||^2 (first direction), p = s
+__global__ void k_bcg_gamma0(BatchScal S, const float* xpart, int nx, int npad) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= npad) return;
+    double s = 0;
+    for (int c = 0; c < nx; ++c) s += xpart[(size_t)c * npad + n];
+    S.gamma[n] = s;
+}
+// alpha = gamma / ||q||^2
+__global__ void k_bcg_alpha(BatchScal S, const float* xpart, int nx, int npad) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= npad || S.done[n] != 0) return;
+    double s = 0;
+    for (int c = 0; c < nx; ++c) s += xpart[(size_t)c * npad + n];
+    if (s > 0) S.alpha[n] = S.gamma[n] / s;
+    else { S.alpha[n] = 0; S.done[n] = 1; }
+}
+// y += alpha p, r -= alpha q (active columns)
+__global__ void k_bcg_update1(float2* __restrict__ y, float2* __restrict__ r, const float2* __restrict__ p,
+                              const float2* __restrict__ q, long long total, int npad, BatchScal S) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        int n = (int)(i % npad);
+        if (S.done[n] != 0) continue;
+        float al = (float)S.alpha[n];
+        float2 pv = p[i], qv = q[i], yv = y[i], rv = r[i];
+        y[i] = make_float2(yv.x + al * pv.x, yv.y + al * pv.y);
+        r[i] = make_float2(rv.x - al * qv.x, rv.y - al * qv.y);
+    }
+}
+// ||r||^2, iteration count, stopping test; *active = columns still running
+__global__ void k_bcg_check(BatchScal S, const float* part, int nchunk, int npad, double tol2, int maxit, int* active) {
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    for (int n = threadIdx.x; n < npad; n += blockDim.x) {
+        if (S.done[n] != 0) continue;
+        double s = 0;
+        for (int c = 0; c < nchunk; ++c) s += part[(size_t)c * npad + n];
+        S.r2[n] = s;                         // relative to ||rc_n||^2 = 1 after scaling
+        S.iters[n] += 1;
+        if (s <= tol2 || S.iters[n] >= maxit) S.done[n] = 1;
+        else atomicAdd(&cnt, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *active = cnt;
+}
+// beta = ||s||^2 / gamma, gamma = ||s||^2
+__global__ void k_bcg_beta(BatchScal S, const float* xpart, int nx, int npad) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= npad || S.done[n] != 0) return;
+    double s = 0;
+    for (int c = 0; c < nx; ++c) s += xpart[(size_t)c * npad + n];
+    S.beta[n] = S.gamma[n] > 0 ? s / S.gamma[n] : 0.0;
+    S.gamma[n] = s;
+}
+__global__ void k_bcg_update2(float2* __restrict__ p, const float2* __restrict__ s, long long total, int npad,
+                              BatchScal S, int first) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        int n = (int)(i % npad);
+        if (!first && S.done[n] != 0) continue;
+        float be = first ? 0.f : (float)S.beta[n];
+        float2 sv = s[i], pv = first ? make_float2(0.f, 0.f) : p[i];
+        p[i] = make_float2(sv.x + be * pv.x, sv.y + be * pv.y);
+    }
+}
+// y *= scale (undo the normalisation)
+__global__ void k_bcg_unscale(float2* __restrict__ y, long long total, int npad, BatchScal S) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        int n = (int)(i % npad);
+        float f = (float)S.scale[n];
+        float2 v = y[i];
+        y[i] = make_float2(v.x * f, v.y * f);
+    }
+}
+
+static inline int ew_grid(long long total) {
+    long long b = (total + 255) / 256;
+    if (b > 152 * 8) b = 152 * 8;
+    return (int)(b > 0 ? b : 1);
+}
+
+// One CGLS iteration on all columns (kernels only: capturable in a CUDA graph).
+void bcg_iteration(const BatchCg& c, cudaStream_t st) {
+    const long long total = (long long)c.g.Vc * c.nc * c.npad;
+    const int nb = (c.npad + 127) / 128;
+    TcApplyArgs ap{c.Aemb, c.p, c.q, c.nc, c.npad, 0, c.g, c.xpart, c.err};
+    coarse_apply_tc(ap, st);                                                               // q = D_c p
+    note_launch();
+    k_bcg_alpha<<<nb, 128, 0, st>>>(c.S, c.xpart, c.g.Vc, c.npad);
+    note_launch();
+    k_bcg_update1<<<ew_grid(total), 256, 0, st>>>(c.y, c.r, c.p, c.q, total, c.npad, c.S);
+    note_launch();
+    k_bcol_norm_partial<<<kRowChunks, 128, 0, st>>>(c.r, (long long)c.g.Vc * c.nc, c.npad, c.rpart);
+    note_launch();
+    k_bcg_check<<<1, 256, 0, st>>>(c.S, c.rpart, kRowChunks, c.npad, c.tol2, c.maxit, c.active);
+    TcApplyArgs as{c.Aemb, c.r, c.s, c.nc, c.npad, 1, c.g, c.xpart, c.err};
+    coarse_apply_tc(as, st);                                                               // s = D_c^dag r
+    note_launch();
+    k_bcg_beta<<<nb, 128, 0, st>>>(c.S, c.xpart, c.g.Vc, c.npad);
+    note_launch();
+    k_bcg_update2<<<ew_grid(total), 256, 0, st>>>(c.p, c.s, total, c.npad, c.S, 0);
+}
+
+// y = 0, r = rc/||rc||, s = D_c^dag r, gamma, p = s
+void bcg_start(const BatchCg& c, cudaStream_t st) {
+    const long long total = (long long)c.g.Vc * c.nc * c.npad;
+    const int nb = (c.npad + 127) / 128;
+    note_launch();
+    k_bcol_norm_partial<<<kRowChunks, 128, 0, st>>>(c.rc, (long long)c.g.Vc * c.nc, c.npad, c.rpart);
+    note_launch();
+    k_bcg_scale<<<nb, 128, 0, st>>>(c.S, c.rpart, kRowChunks, c.npad, c.nrhs, c.maxit);
+    note_launch();
+    k_bcg_start<<<ew_grid(total), 256, 0, st>>>(c.y, c.r, c.rc, total, c.npad, c.S);
+    TcApplyArgs as{c.Aemb, c.r, c.s, c.nc, c.npad, 1, c.g, c.xpart, c.err};
+    coarse_apply_tc(as, st);
+    note_launch();
+    k_bcg_gamma0<<<nb, 128, 0, st>>>(c.S, c.xpart, c.g.Vc, c.npad);
+    note_launch();
+    k_bcg_update2<<<ew_grid(total), 256, 0, st>>>(c.p, c.s, total, c.npad, c.S, 1);
+}
+
+void bcg_finish(const BatchCg& c, cudaStream_t st) {
+    const long long total = (long long)c.g.Vc * c.nc * c.npad;
+    note_launch();
+    k_bcg_unscale<<<ew_grid(total), 256, 0, st>>>(c.y, total, c.npad, c.S);
+}
+
+}  // namespace wmg
+
+namespace wmg {
+// columns n < nrhs of a panel from nrhs stacked coarse vectors in[n][row] (FP64), other columns zero
+__global__ void k_panel_pack(float2* __restrict__ out, const double2* __restrict__ in, long long rows, int nrhs, int npad) {
+    long long total = rows * npad;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        long long r = i / npad;
+        int n = (int)(i - r * npad);
+        float2 v = make_float2(0.f, 0.f);
+        if (n < nrhs) {
+            double2 d = in[(size_t)n * rows + r];
+            v = make_float2((float)d.x, (float)d.y);
+        }
+        out[i] = v;
+    }
+}
+__global__ void k_panel_unpack(double2* __restrict__ out, const float2* __restrict__ in, long long rows, int nrhs, int npad) {
+    long long total = rows * nrhs;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        long long n = i / rows, r = i - n * rows;
+        float2 v = in[r * npad + n];
+        out[i] = make_double2((double)v.x, (double)v.y);
+    }
+}
+template <typename T>
+__global__ void k_panel_pack_t(v2<T>* __restrict__ out, const double2* __restrict__ in, long long rows, int nrhs, int npad) {
+    long long total = rows * npad;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        long long r = i / npad;
+        int n = (int)(i - r * npad);
+        v2<T> v; v.x = 0; v.y = 0;
+        if (n < nrhs) { double2 d = in[(size_t)n * rows + r]; v.x = (T)d.x; v.y = (T)d.y; }
+        out[i] = v;
+    }
+}
+template <typename T>
+__global__ void k_panel_unpack_t(double2* __restrict__ out, const v2<T>* __restrict__ in, long long rows, int nrhs, int npad) {
+    long long total = rows * nrhs;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        long long n = i / rows, r = i - n * rows;
+        v2<T> v = in[r * npad + n];
+        out[i] = make_double2((double)v.x, (double)v.y);
+    }
+}
+void panel_pack(float2* out, const double2* in, long long rows, int nrhs, int npad, cudaStream_t st) {
+    note_launch();
+    k_panel_pack<<<ew_grid(rows * npad), 256, 0, st>>>(out, in, rows, nrhs, npad);
+}
+void panel_unpack(double2* out, const float2* in, long long rows, int nrhs, int npad, cudaStream_t st) {
+    note_launch();
+    k_panel_unpack<<<ew_grid(rows * nrhs), 256, 0, st>>>(out, in, rows, nrhs, npad);
+}
+void panel_pack64(double2* out, const double2* in, long long rows, int nrhs, int npad, cudaStream_t st) {
+    note_launch();
+    k_panel_pack_t<double><<<ew_grid(rows * npad), 256, 0, st>>>(out, in, rows, nrhs, npad);
+}
+void panel_unpack64(double2* out, const double2* in, long long rows, int nrhs, int npad, cudaStream_t st) {
+    note_launch();
+    k_panel_unpack_t<double><<<ew_grid(rows * nrhs), 256, 0, st>>>(out, in, rows, nrhs, npad);
+}
+}  // namespace wmg

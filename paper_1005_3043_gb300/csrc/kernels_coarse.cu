@@ -106,7 +106,7 @@ void block_orthonormalize(double2* P, const double2* V, int nv, const Geom& g, i
 // r on X (6*Vb contiguous) is staged in shared memory, warp w handles i = w, w+8, ...
 template <typename T>
 __global__ void __launch_bounds__(256) k_restrict(v2<T>* __restrict__ rc, const v2<T>* __restrict__ P,
-                                                  const v2<T>* __restrict__ r, int nv, Geom g) {
+                                                  const v2<T>* __restrict__ r, int nv, Geom g, int cstride, int coff) {
     extern __shared__ unsigned char smem_raw[];
     v2<T>* rs = reinterpret_cast<v2<T>*>(smem_raw);
     int X = blockIdx.x >> 1, s = blockIdx.x & 1;
@@ -123,14 +123,14 @@ __global__ void __launch_bounds__(256) k_restrict(v2<T>* __restrict__ rc, const 
         double ar = warp_sum((double)a.r), ai = warp_sum((double)a.i);
         if (lane == 0) {
             v2<T> o; o.x = (T)ar; o.y = (T)ai;
-            rc[(size_t)X * 2 * nv + s * nv + i] = o;
+            rc[((size_t)X * 2 * nv + s * nv + i) * cstride + coff] = o;
         }
     }
 }
 // e[X][k][l] = sum_i P[X][s(k)][i][k%6][l] y[X][s(k)*Nv + i]
 template <typename T>
 __global__ void __launch_bounds__(256) k_prolong(v2<T>* __restrict__ e, const v2<T>* __restrict__ P,
-                                                 const v2<T>* __restrict__ yc, int nv, Geom g) {
+                                                 const v2<T>* __restrict__ yc, int nv, Geom g, int cstride, int coff) {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;   // over V*12 as (X, k, l)
     long long total = g.V * 12;
     if (idx >= total) return;
@@ -141,21 +141,23 @@ __global__ void __launch_bounds__(256) k_prolong(v2<T>* __restrict__ e, const v2
     int s = k / 6, kk = k - 6 * s;
     int len = 6 * g.Vb;
     const v2<T>* p = P + (((size_t)X * 2 + s) * nv * 6 + kk) * g.Vb + l;
-    const v2<T>* y = yc + (size_t)X * 2 * nv + s * nv;
+    const v2<T>* y = yc + ((size_t)X * 2 * nv + s * nv) * cstride + coff;
     cx<T> a(0, 0);
-    for (int i = 0; i < nv; ++i) cmad(a, ldg<T>(p + (size_t)i * len), ldg<T>(y + i));
+    for (int i = 0; i < nv; ++i) cmad(a, ldg<T>(p + (size_t)i * len), ldg<T>(y + (size_t)i * cstride));
     st<T>(e + idx, a);
 }
 
-template <typename T> void restrict_(v2<T>* rc, const v2<T>* P, const v2<T>* r, int nv, const Geom& g, cudaStream_t st) {
+template <typename T>
+void restrict_(v2<T>* rc, const v2<T>* P, const v2<T>* r, int nv, const Geom& g, cudaStream_t st, int cstride, int coff) {
     size_t sm = sizeof(v2<T>) * 6 * g.Vb;
     note_launch();
-    k_restrict<T><<<2 * g.Vc, kThreads, sm, st>>>(rc, P, r, nv, g);
+    k_restrict<T><<<2 * g.Vc, kThreads, sm, st>>>(rc, P, r, nv, g, cstride, coff);
 }
-template <typename T> void prolong(v2<T>* e, const v2<T>* P, const v2<T>* yc, int nv, const Geom& g, cudaStream_t st) {
+template <typename T>
+void prolong(v2<T>* e, const v2<T>* P, const v2<T>* yc, int nv, const Geom& g, cudaStream_t st, int cstride, int coff) {
     long long total = g.V * 12;
     note_launch();
-    k_prolong<T><<<(int)((total + kThreads - 1) / kThreads), kThreads, 0, st>>>(e, P, yc, nv, g);
+    k_prolong<T><<<(int)((total + kThreads - 1) / kThreads), kThreads, 0, st>>>(e, P, yc, nv, g, cstride, coff);
 }
 
 // ================================================================ coarse operator build
@@ -536,8 +538,8 @@ void cg_step(v2<T>* y, v2<T>* r, v2<T>* s, v2<T>* p, v2<T>* q, const v2<T>* A, i
 }
 
 #define INST(T)                                                                                                     \
-    template void restrict_<T>(v2<T>*, const v2<T>*, const v2<T>*, int, const Geom&, cudaStream_t);                 \
-    template void prolong<T>(v2<T>*, const v2<T>*, const v2<T>*, int, const Geom&, cudaStream_t);                   \
+    template void restrict_<T>(v2<T>*, const v2<T>*, const v2<T>*, int, const Geom&, cudaStream_t, int, int);       \
+    template void prolong<T>(v2<T>*, const v2<T>*, const v2<T>*, int, const Geom&, cudaStream_t, int, int);         \
     template void coarse_apply<T>(v2<T>*, const v2<T>*, const v2<T>*, int, bool, int, const Geom&, const Reduce&,    \
                                   cudaStream_t);                                                                    \
     template void cg_init<T>(v2<T>*, v2<T>*, const v2<T>*, size_t, double, int, const Reduce&, cudaStream_t);       \

@@ -7,6 +7,7 @@
 // the device and are read back at convergence checks.
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -30,8 +31,32 @@ struct CoarseLevel {
     float2* P32 = nullptr;
     double2* A64 = nullptr;   // [X][9][nc][nc] column-major blocks
     float2* A32 = nullptr;
+    __half* Aemb = nullptr;   // FP16 tensor-core embedding of A64 (batched path), built on demand
+    bool emb_valid = false;
     double mass = 0.0;
     bool valid = false;
+};
+
+// Workspace of the batched (multi-RHS) solve, sized for npad panel columns.
+struct BatchWork {
+    int npad = 0, nrhs_cap = 0, K = 0, nc = 0;
+    float2 *rcB = nullptr, *yB = nullptr, *rB = nullptr, *sB = nullptr, *pB = nullptr, *qB = nullptr;
+    double* cgs = nullptr;          // 7 x npad per-RHS CG scalars
+    float* xpart = nullptr;         // Vc x npad
+    float* rpart = nullptr;         // 152 x npad
+    int* flags = nullptr;           // [0] active columns, [1] error
+    int* h_flags = nullptr;         // pinned
+    double* h_iters = nullptr;      // pinned, npad
+    float2* r32 = nullptr;          // nrhs x n
+    float2* Z = nullptr;            // nrhs x K x n
+    float2* Pk = nullptr;           // nrhs x K x n
+    double2* x64 = nullptr;         // nrhs x n (internal layout)
+    double2* b64 = nullptr;         // nrhs x n
+    double* scal = nullptr;         // nrhs x S_COUNT
+    double* h_scal = nullptr;       // pinned nrhs x S_COUNT
+    cudaStream_t cap = nullptr;     // capture stream
+    cudaGraphExec_t graph = nullptr;
+    long long graph_key[6] = {0, 0, 0, 0, 0, 0};
 };
 
 template <typename T> struct Work {
@@ -80,6 +105,7 @@ struct mg_ctx {
     double2* Aself = nullptr;        // coarse-build scratch
     double2* cstage = nullptr;       // coarse staging (FP64)
     CoarseLevel full, trunc;
+    BatchWork bw;
     Work<float> wf;
     Work<double> wd;
     Reduce R{};
@@ -134,6 +160,13 @@ template <typename P> int dalloc(mg_ctx* ctx, P** p, size_t bytes) {
     ctx->allocs.push_back(q);
     *p = (P*)q;
     return MG_OK;
+}
+
+void dfree(mg_ctx* ctx, void* q) {
+    if (!q) return;
+    for (size_t i = 0; i < ctx->allocs.size(); ++i)
+        if (ctx->allocs[i] == q) { ctx->allocs.erase(ctx->allocs.begin() + i); break; }
+    cudaFree(q);
 }
 
 size_t nfine(const mg_ctx* c) { return (size_t)c->g.V * 12; }
@@ -259,6 +292,7 @@ int build_level(mg_ctx* ctx, CoarseLevel& L, const double2* V, int nv) {
     CKL();
     L.mass = ctx->mass;
     L.valid = true;
+    L.emb_valid = false;
     return MG_OK;
 }
 
@@ -737,6 +771,11 @@ void mg_destroy(mg_ctx* ctx) {
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    if (ctx->bw.graph) cudaGraphExecDestroy(ctx->bw.graph);
+    if (ctx->bw.cap) cudaStreamDestroy(ctx->bw.cap);
+    if (ctx->bw.h_flags) cudaFreeHost(ctx->bw.h_flags);
+    if (ctx->bw.h_iters) cudaFreeHost(ctx->bw.h_iters);
+    if (ctx->bw.h_scal) cudaFreeHost(ctx->bw.h_scal);
     delete ctx;
 }
 
@@ -759,6 +798,7 @@ int mg_set_mass(mg_ctx* ctx, double m) {
         convert<double, float>(ctx->full.A32, ctx->full.A64, (size_t)ctx->g.Vc * 9 * ctx->full.nc * ctx->full.nc, ctx->st);
         CKL();
         ctx->full.mass = m;
+        ctx->full.emb_valid = false;
     }
     ctx->mass = m;
     CK(cudaStreamSynchronize(ctx->st));
@@ -1055,3 +1095,428 @@ extern "C" int mg_coarse_solve_noalloc(mg_ctx* ctx, const double* rc_dev, double
         *final_rel = ctx->h_scal[S_CG_RC2] > 0 ? std::sqrt(ctx->h_scal[S_CG_R2] / ctx->h_scal[S_CG_RC2]) : 0.0;
     return MG_OK;
 }
+
+// ======================================================================= batched right-hand sides
+// Lockstep flexible GCR over nrhs sources: the fine-level steps of each source
+// use the single-source kernels, the coarse solve of all sources runs as one
+// batched CGNR on an RHS panel (tensor-core stencil, iterations replayed from a
+// captured CUDA graph), each source keeps its own GCR scalars.
+namespace {
+
+constexpr int kBatchCheck = 8;   // coarse iterations per graph replay between host checks
+
+int round16(int n) { return ((n + 15) / 16) * 16; }
+
+int ensure_embedding(mg_ctx* ctx, CoarseLevel& L) {
+    if (L.emb_valid) return MG_OK;
+    // per (X, d) block: the (2 nc) x (2 nc) real embedding, nc = 2 nv
+    const size_t kemb = (size_t)4 * L.cap;
+    if (!L.Aemb) TRY(dalloc(ctx, &L.Aemb, sizeof(__half) * (size_t)ctx->g.Vc * 9 * kemb * kemb));
+    coarse_embed(L.Aemb, L.A64, L.nc, ctx->g.Vc, ctx->st);
+    CKL();
+    L.emb_valid = true;
+    return MG_OK;
+}
+
+int ensure_batch(mg_ctx* ctx, int nrhs) {
+    BatchWork& b = ctx->bw;
+    int npad = round16(nrhs), nc = ctx->full.nc;
+    size_t n = nfine(ctx);
+    int K = std::min(ctx->prm.gcr_restart, ctx->K);
+    if (b.npad >= npad && b.nrhs_cap >= nrhs && b.nc == nc && b.K >= K) return MG_OK;
+    if (b.npad || b.nrhs_cap) {   // grow: release the smaller workspace first
+        CK(cudaStreamSynchronize(ctx->st));
+        for (void* q : {(void*)b.rcB, (void*)b.yB, (void*)b.rB, (void*)b.sB, (void*)b.pB, (void*)b.qB, (void*)b.cgs,
+                        (void*)b.xpart, (void*)b.rpart, (void*)b.flags, (void*)b.r32, (void*)b.Z, (void*)b.Pk,
+                        (void*)b.x64, (void*)b.b64, (void*)b.scal})
+            dfree(ctx, q);
+        if (b.graph) cudaGraphExecDestroy(b.graph);
+        if (b.cap) cudaStreamDestroy(b.cap);
+        cudaFreeHost(b.h_flags);
+        cudaFreeHost(b.h_iters);
+        cudaFreeHost(b.h_scal);
+        b = BatchWork{};
+        npad = std::max(npad, round16(nrhs));
+    }
+    size_t pe = (size_t)ctx->g.Vc * nc * npad;
+    TRY(dalloc(ctx, &b.rcB, sizeof(float2) * pe));
+    TRY(dalloc(ctx, &b.yB, sizeof(float2) * pe));
+    TRY(dalloc(ctx, &b.rB, sizeof(float2) * pe));
+    TRY(dalloc(ctx, &b.sB, sizeof(float2) * pe));
+    TRY(dalloc(ctx, &b.pB, sizeof(float2) * pe));
+    TRY(dalloc(ctx, &b.qB, sizeof(float2) * pe));
+    TRY(dalloc(ctx, &b.cgs, sizeof(double) * 7 * npad));
+    TRY(dalloc(ctx, &b.xpart, sizeof(float) * (size_t)ctx->g.Vc * npad));
+    TRY(dalloc(ctx, &b.rpart, sizeof(float) * kBatchRowChunks * npad));
+    TRY(dalloc(ctx, &b.flags, sizeof(int) * 4));
+    TRY(dalloc(ctx, &b.r32, sizeof(float2) * n * nrhs));
+    TRY(dalloc(ctx, &b.Z, sizeof(float2) * n * nrhs * K));
+    TRY(dalloc(ctx, &b.Pk, sizeof(float2) * n * nrhs * K));
+    TRY(dalloc(ctx, &b.x64, sizeof(double2) * n * nrhs));
+    TRY(dalloc(ctx, &b.b64, sizeof(double2) * n * nrhs));
+    TRY(dalloc(ctx, &b.scal, sizeof(double) * S_COUNT * nrhs));
+    CK(cudaMallocHost(&b.h_flags, sizeof(int) * 4));
+    CK(cudaMallocHost(&b.h_iters, sizeof(double) * npad));
+    CK(cudaMallocHost(&b.h_scal, sizeof(double) * S_COUNT * nrhs));
+    CK(cudaStreamCreateWithFlags(&b.cap, cudaStreamNonBlocking));
+    CK(cudaMemsetAsync(b.scal, 0, sizeof(double) * S_COUNT * nrhs, ctx->st));
+    CK(cudaMemsetAsync(b.flags, 0, sizeof(int) * 4, ctx->st));
+    b.npad = npad;
+    b.nrhs_cap = nrhs;
+    b.nc = nc;
+    b.K = K;
+    return MG_OK;
+}
+
+BatchCg batch_cg(mg_ctx* ctx, double tol, int maxit, int nrhs) {
+    BatchWork& b = ctx->bw;
+    BatchCg c;
+    c.Aemb = ctx->full.Aemb;
+    c.y = b.yB; c.r = b.rB; c.s = b.sB; c.p = b.pB; c.q = b.qB; c.rc = b.rcB;
+    c.nc = ctx->full.nc; c.npad = b.npad; c.nrhs = nrhs; c.maxit = maxit;
+    c.tol2 = tol * tol;
+    c.g = ctx->g;
+    c.S.scale = b.cgs; c.S.done = b.cgs + b.npad; c.S.iters = b.cgs + 2 * b.npad; c.S.r2 = b.cgs + 3 * b.npad;
+    c.S.gamma = b.cgs + 4 * b.npad; c.S.alpha = b.cgs + 5 * b.npad; c.S.beta = b.cgs + 6 * b.npad;
+    c.xpart = b.xpart; c.rpart = b.rpart; c.active = b.flags; c.err = b.flags + 1;
+    return c;
+}
+
+// CGNR on the panel rcB -> yB for columns 0..nrhs-1 (zero columns stay zero).
+// iters_out[n] += coarse iterations of column n.
+int batched_coarse_solve(mg_ctx* ctx, int nrhs, double tol, int maxit, std::vector<double>& iters_out) {
+    BatchWork& b = ctx->bw;
+    TRY(ensure_embedding(ctx, ctx->full));
+    CK(coarse_apply_tc_prepare(ctx->full.nc, b.npad));
+    BatchCg c = batch_cg(ctx, tol, maxit, nrhs);
+    long long tolbits = 0;
+    std::memcpy(&tolbits, &c.tol2, sizeof(tolbits));
+    long long key[6] = {(long long)(size_t)c.Aemb, b.npad, nrhs, maxit, tolbits, ctx->full.nc};
+    if (!b.graph || std::memcmp(key, b.graph_key, sizeof(key)) != 0) {
+        if (b.graph) { cudaGraphExecDestroy(b.graph); b.graph = nullptr; }
+        cudaGraph_t gr;
+        CK(cudaStreamBeginCapture(b.cap, cudaStreamCaptureModeThreadLocal));
+        for (int j = 0; j < kBatchCheck; ++j) bcg_iteration(c, b.cap);
+        CK(cudaStreamEndCapture(b.cap, &gr));
+        // captured launches run only when the graph is replayed (counted there)
+        launch_counter().fetch_sub(kBatchCheck * kBcgKernelsPerIteration, std::memory_order_relaxed);
+        cudaError_t e = cudaGraphInstantiate(&b.graph, gr, 0);
+        cudaGraphDestroy(gr);
+        CK(e);
+        std::memcpy(b.graph_key, key, sizeof(key));
+    }
+    PROF_BEGIN(MG_K_COARSE_SOLVE);
+    bcg_start(c, ctx->st);
+    CKL();
+    int done_its = 0;
+    for (;;) {
+        CK(cudaGraphLaunch(b.graph, ctx->st));
+        launch_counter().fetch_add(kBatchCheck * kBcgKernelsPerIteration, std::memory_order_relaxed);
+        done_its += kBatchCheck;
+        CK(cudaMemcpyAsync(b.h_flags, b.flags, sizeof(int) * 2, cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        if (b.h_flags[1]) return fail(ctx, MG_ERR_TIMEOUT, "batched coarse stencil: a bounded wait gave up");
+        if (b.h_flags[0] == 0 || done_its >= maxit) break;
+    }
+    bcg_finish(c, ctx->st);
+    PROF_END(MG_K_COARSE_SOLVE);
+    CKL();
+    CK(cudaMemcpyAsync(b.h_iters, c.S.iters, sizeof(double) * b.npad, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    for (int n = 0; n < nrhs; ++n) iters_out[n] += b.h_iters[n];
+    return MG_OK;
+}
+
+// b64 (internal layout) -> x64 for nrhs sources, FP32 inner precision
+int solve_batched_impl(mg_ctx* ctx, int nrhs, mg_solve_info* infos) {
+    TRY(ensure_work<float>(ctx));
+    BatchWork& b = ctx->bw;
+    Work<float>& w = ctx->wf;
+    const mg_params& p = ctx->prm;
+    const CoarseLevel& L = ctx->full;
+    const size_t n = nfine(ctx);
+    const int K = b.K;
+    const v2<float>* U = ctx->U32;
+    std::vector<double> bnorm(nrhs), rnorm(nrhs), rcycle(nrhs), rel(nrhs, 1.0), coarse(nrhs, 0.0);
+    std::vector<int> iters(nrhs, 0), restarts(nrhs, 0), status(nrhs, MG_ERR_NOT_CONVERGED), kk(nrhs, 0),
+        active(nrhs, 1), cycle_end(nrhs, 0), mv(nrhs, 0);
+    auto RR = [&](int r) {
+        Reduce R = ctx->R;
+        R.scal = b.scal + (size_t)r * S_COUNT;
+        return R;
+    };
+    CK(cudaEventRecord(ctx->ev0, ctx->st));
+    for (int r = 0; r < nrhs; ++r) {
+        norm2<double>(b.b64 + r * n, n, S_NORM_A, RR(r), ctx->st);
+        zero<double>(b.x64 + r * n, n, ctx->st);
+        convert<double, float>(b.r32 + r * n, b.b64 + r * n, n, ctx->st);
+    }
+    CKL();
+    CK(cudaMemcpyAsync(b.h_scal, b.scal, sizeof(double) * S_COUNT * nrhs, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    for (int r = 0; r < nrhs; ++r) {
+        bnorm[r] = std::sqrt(b.h_scal[(size_t)r * S_COUNT + S_NORM_A]);
+        if (!std::isfinite(bnorm[r])) return fail(ctx, MG_ERR_NUMERIC, "right-hand side is not finite");
+        rnorm[r] = rcycle[r] = bnorm[r];
+        if (bnorm[r] == 0) { status[r] = MG_OK; active[r] = 0; rel[r] = 0; }
+    }
+    auto any_active = [&]() { for (int r = 0; r < nrhs; ++r) if (active[r]) return true; return false; };
+    while (any_active()) {
+        bool stepping = false;
+        for (int r = 0; r < nrhs; ++r)
+            if (active[r] && !cycle_end[r] && kk[r] < K && iters[r] < p.max_outer) stepping = true;
+        if (stepping) {
+            // restriction of every stepping source into its panel column
+            CK(cudaMemsetAsync(b.rcB, 0, sizeof(float2) * (size_t)ctx->g.Vc * L.nc * b.npad, ctx->st));
+            PROF_BEGIN(MG_K_RESTRICT);
+            for (int r = 0; r < nrhs; ++r)
+                if (active[r] && !cycle_end[r] && kk[r] < K && iters[r] < p.max_outer)
+                    restrict_<float>(b.rcB, L.P32, b.r32 + r * n, L.nv, ctx->g, ctx->st, b.npad, r);
+            PROF_END(MG_K_RESTRICT);
+            CKL();
+            TRY(batched_coarse_solve(ctx, nrhs, p.coarse_tol, p.max_coarse, coarse));
+            for (int r = 0; r < nrhs; ++r) {
+                if (!(active[r] && !cycle_end[r] && kk[r] < K && iters[r] < p.max_outer)) continue;
+                Reduce Rr = RR(r);
+                v2<float>* zk = b.Z + ((size_t)r * K + kk[r]) * n;
+                v2<float>* Pr = b.Pk + (size_t)r * K * n;
+                PROF_BEGIN(MG_K_PROLONG);
+                prolong<float>(zk, L.P32, b.yB, L.nv, ctx->g, ctx->st, b.npad, r);
+                PROF_END(MG_K_PROLONG);
+                PROF_BEGIN(MG_K_DSLASH);
+                dslash<float>(DS_XMY, w.vr, zk, U, b.r32 + r * n, ctx->g, ctx->mass, 0.0, 0, Rr, ctx->st);
+                PROF_END(MG_K_DSLASH);
+                for (int s = 0; s < p.smoother_steps; ++s) {
+                    PROF_BEGIN(MG_K_DSLASH);
+                    dslash<float>(DS_MRDOT, w.vq, w.vr, U, w.vr, ctx->g, ctx->mass, p.omega, 0, Rr, ctx->st);
+                    PROF_END(MG_K_DSLASH);
+                    PROF_BEGIN(MG_K_KRYLOV);
+                    mr_update<float>(zk, w.vr, w.vq, n, s + 1 < p.smoother_steps, Rr, ctx->st);
+                    PROF_END(MG_K_KRYLOV);
+                }
+                PROF_BEGIN(MG_K_DSLASH);
+                dslash<float>(DS_PLAIN, Pr + (size_t)kk[r] * n, zk, U, zk, ctx->g, ctx->mass, 0.0, 0, Rr, ctx->st);
+                PROF_END(MG_K_DSLASH);
+                mv[r] += 2 + p.smoother_steps;
+                PROF_BEGIN(MG_K_KRYLOV);
+                if (kk[r] > 0) {
+                    gcr_multidot<float>(Pr, n, kk[r], Rr, ctx->st);
+                    gcr_orth_norm<float>(Pr, n, kk[r], Rr, ctx->st);
+                } else {
+                    norm2<float>(Pr, n, S_GCR_PN2, Rr, ctx->st);
+                }
+                gcr_cdot<float>(Pr, b.r32 + r * n, n, kk[r], Rr, ctx->st);
+                gcr_update<float>(Pr, b.r32 + r * n, n, kk[r], Rr, ctx->st);
+                PROF_END(MG_K_KRYLOV);
+                CKL();
+            }
+            CK(cudaMemcpyAsync(b.h_scal, b.scal, sizeof(double) * S_COUNT * nrhs, cudaMemcpyDeviceToHost, ctx->st));
+            CK(cudaStreamSynchronize(ctx->st));
+            for (int r = 0; r < nrhs; ++r) {
+                if (!(active[r] && !cycle_end[r] && kk[r] < K && iters[r] < p.max_outer)) continue;
+                const double* sc = b.h_scal + (size_t)r * S_COUNT;
+                ++kk[r];
+                ++iters[r];
+                double pn = sc[S_GCR_PN2];
+                if (!(pn > 0) || !std::isfinite(pn)) { status[r] = MG_ERR_NUMERIC; active[r] = 0; continue; }
+                rnorm[r] = std::sqrt(sc[S_GCR_R2]);
+                if (rnorm[r] <= p.tol * bnorm[r] || (p.delta > 0 && rnorm[r] <= p.delta * rcycle[r]) || kk[r] >= K ||
+                    iters[r] >= p.max_outer)
+                    cycle_end[r] = 1;
+            }
+        }
+        // restart every source that closed its cycle once no source is still stepping in it
+        bool all_closed = true;
+        for (int r = 0; r < nrhs; ++r)
+            if (active[r] && !cycle_end[r] && kk[r] < K && iters[r] < p.max_outer) all_closed = false;
+        if (!all_closed) continue;
+        for (int r = 0; r < nrhs; ++r) {
+            if (!active[r]) continue;
+            const double* sc = b.h_scal + (size_t)r * S_COUNT;
+            int k = kk[r];
+            auto Rr = [&](int j, int c) { return sc + S_GCR_R + 2 * (c * K_MAX + j); };
+            GcrCoef y{};
+            for (int i = k - 1; i >= 0; --i) {
+                double sr = sc[S_GCR_C + 2 * i], si = sc[S_GCR_C + 2 * i + 1];
+                for (int j = i + 1; j < k; ++j) {
+                    const double* q = Rr(i, j);
+                    sr -= q[0] * y.c[2 * j] - q[1] * y.c[2 * j + 1];
+                    si -= q[0] * y.c[2 * j + 1] + q[1] * y.c[2 * j];
+                }
+                const double* dd = Rr(i, i);
+                double den = dd[0] * dd[0] + dd[1] * dd[1];
+                y.c[2 * i] = (sr * dd[0] + si * dd[1]) / den;
+                y.c[2 * i + 1] = (si * dd[0] - sr * dd[1]) / den;
+            }
+            Reduce R = RR(r);
+            PROF_BEGIN(MG_K_KRYLOV);
+            gcr_xupdate<float>(b.x64 + r * n, b.Z + (size_t)r * K * n, n, k, y, ctx->st);
+            PROF_END(MG_K_KRYLOV);
+            PROF_BEGIN(MG_K_TRUE_RESIDUAL);
+            dslash<double>(DS_XMY_NORM, ctx->r64, b.x64 + r * n, ctx->U64, b.b64 + r * n, ctx->g, ctx->mass, 0.0, S_NORM_B,
+                           R, ctx->st);
+            PROF_END(MG_K_TRUE_RESIDUAL);
+            convert<double, float>(b.r32 + r * n, ctx->r64, n, ctx->st);
+            mv[r] += 1;
+            CKL();
+        }
+        CK(cudaMemcpyAsync(b.h_scal, b.scal, sizeof(double) * S_COUNT * nrhs, cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        for (int r = 0; r < nrhs; ++r) {
+            if (!active[r]) continue;
+            ++restarts[r];
+            rnorm[r] = std::sqrt(b.h_scal[(size_t)r * S_COUNT + S_NORM_B]);
+            rel[r] = rnorm[r] / bnorm[r];
+            kk[r] = 0;
+            cycle_end[r] = 0;
+            rcycle[r] = rnorm[r];
+            if (!std::isfinite(rel[r])) { status[r] = MG_ERR_NUMERIC; active[r] = 0; }
+            else if (rel[r] <= p.tol) { status[r] = MG_OK; active[r] = 0; }
+            else if (iters[r] >= p.max_outer) { status[r] = MG_ERR_NOT_CONVERGED; active[r] = 0; }
+        }
+    }
+    CK(cudaEventRecord(ctx->ev1, ctx->st));
+    CK(cudaEventSynchronize(ctx->ev1));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+    int worst = MG_OK;
+    for (int r = 0; r < nrhs; ++r) {
+        if (infos) {
+            infos[r].outer_iters = iters[r];
+            infos[r].coarse_iters = (int)coarse[r];
+            infos[r].fine_matvecs = mv[r];
+            infos[r].restarts = restarts[r];
+            infos[r].true_rel_res = rel[r];
+            infos[r].solve_ms = ms;
+            infos[r].status = status[r];
+        }
+        if (status[r] == MG_ERR_NUMERIC) worst = MG_ERR_NUMERIC;
+        else if (status[r] == MG_ERR_NOT_CONVERGED && worst == MG_OK) worst = MG_ERR_NOT_CONVERGED;
+    }
+    if (worst == MG_ERR_NUMERIC) ctx->err = "non-finite residual or GCR breakdown in a batched source";
+    if (worst == MG_ERR_NOT_CONVERGED) ctx->err = "max_outer reached for a batched source";
+    return worst;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mg_solve_batched_device(mg_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, mg_solve_info* infos) {
+    TRY(need_level(ctx));
+    if (!b_dev || !x_dev || nrhs <= 0) return fail(ctx, MG_ERR_INVALID_ARG, "null buffer or nrhs <= 0");
+    size_t n = nfine(ctx);
+    if (ctx->prm.prec_inner != MG_FP32) {   // FP64 inner precision: the sources one after another
+        int worst = MG_OK;
+        for (int r = 0; r < nrhs; ++r) {
+            int st = mg_solve_device(ctx, b_dev + 2 * r * n, x_dev + 2 * r * n, infos ? infos + r : nullptr);
+            if (st != MG_OK && st != MG_ERR_NOT_CONVERGED) return st;
+            if (st != MG_OK) worst = st;
+        }
+        return worst;
+    }
+    if (nrhs > 256) return fail(ctx, MG_ERR_INVALID_ARG, "at most 256 sources per batch");
+    if (!coarse_apply_tc_supported(ctx->full.nc, round16(nrhs)))
+        return fail(ctx, MG_ERR_INVALID_ARG, "batched coarse stencil needs 2*nvec a multiple of 16 and <= 128");
+    TRY(ensure_batch(ctx, nrhs));
+    for (int r = 0; r < nrhs; ++r)
+        spinor_to_internal<double>(ctx->bw.b64 + r * n, (const double2*)b_dev + r * n, ctx->g, ctx->st);
+    CKL();
+    int st = solve_batched_impl(ctx, nrhs, infos);
+    if (st != MG_OK && st != MG_ERR_NOT_CONVERGED) return st;
+    for (int r = 0; r < nrhs; ++r)
+        spinor_from_internal<double>((double2*)x_dev + r * n, ctx->bw.x64 + r * n, ctx->g, ctx->st);
+    CKL();
+    CK(cudaStreamSynchronize(ctx->st));
+    return st;
+}
+
+int mg_solve_batched(mg_ctx* ctx, const double* b, double* x, int nrhs, mg_solve_info* infos) {
+    TRY(need_level(ctx));
+    if (!b || !x || nrhs <= 0) return fail(ctx, MG_ERR_INVALID_ARG, "null buffer or nrhs <= 0");
+    size_t n = nfine(ctx);
+    double2 *db = nullptr, *dx = nullptr;
+    TRY(dalloc(ctx, &db, sizeof(double2) * n * nrhs));
+    TRY(dalloc(ctx, &dx, sizeof(double2) * n * nrhs));
+    CK(cudaMemcpyAsync(db, b, sizeof(double2) * n * nrhs, cudaMemcpyHostToDevice, ctx->st));
+    int st = mg_solve_batched_device(ctx, (const double*)db, (double*)dx, nrhs, infos);
+    if (st == MG_OK || st == MG_ERR_NOT_CONVERGED) {
+        CK(cudaMemcpyAsync(x, dx, sizeof(double2) * n * nrhs, cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+    }
+    // release the staging buffers of this call
+    for (void* q : {(void*)db, (void*)dx}) {
+        for (size_t i = 0; i < ctx->allocs.size(); ++i)
+            if (ctx->allocs[i] == q) { ctx->allocs.erase(ctx->allocs.begin() + i); break; }
+        cudaFree(q);
+    }
+    return st;
+}
+
+int mg_apply_coarse_batched(mg_ctx* ctx, const double* x, double* y, int nrhs, int dagger, int impl) {
+    TRY(need_level(ctx));
+    if (!x || !y || nrhs <= 0 || nrhs > 256) return fail(ctx, MG_ERR_INVALID_ARG, "bad buffers or nrhs");
+    const CoarseLevel& L = ctx->full;
+    int npad = round16(nrhs);
+    long long rows = (long long)ctx->g.Vc * L.nc;
+    size_t nin = (size_t)rows * nrhs, npanel = (size_t)rows * npad;
+    double2 *hin = nullptr, *hout = nullptr, *p64a = nullptr, *p64b = nullptr;
+    float2 *pa = nullptr, *pb = nullptr;
+    // each source scaled to max |x| = 1 (the FP16 panel of the tensor-core path has
+    // no subnormal headroom), scaled back afterwards
+    std::vector<double> scale(nrhs, 1.0), xs((size_t)2 * nin);
+    for (int r = 0; r < nrhs; ++r) {
+        double mx = 0;
+        for (long long i = 0; i < 2 * rows; ++i) mx = std::max(mx, std::fabs(x[(size_t)r * 2 * rows + i]));
+        scale[r] = mx > 0 ? mx : 1.0;
+        for (long long i = 0; i < 2 * rows; ++i) xs[(size_t)r * 2 * rows + i] = x[(size_t)r * 2 * rows + i] / scale[r];
+    }
+    TRY(dalloc(ctx, &hin, sizeof(double2) * nin));
+    TRY(dalloc(ctx, &hout, sizeof(double2) * nin));
+    CK(cudaMemcpyAsync(hin, xs.data(), sizeof(double2) * nin, cudaMemcpyHostToDevice, ctx->st));
+    std::vector<void*> tmp = {hin, hout};
+    int st = MG_OK;
+    if (impl == 0) {
+        if (!coarse_apply_tc_supported(L.nc, npad)) return fail(ctx, MG_ERR_INVALID_ARG, "unsupported shape");
+        TRY(dalloc(ctx, &pa, sizeof(float2) * npanel));
+        TRY(dalloc(ctx, &pb, sizeof(float2) * npanel));
+        tmp.push_back(pa);
+        tmp.push_back(pb);
+        TRY(dalloc(ctx, &p64a, sizeof(int) * 4));   // error flag
+        tmp.push_back(p64a);
+        CK(cudaMemsetAsync(p64a, 0, sizeof(int) * 4, ctx->st));
+        TRY(ensure_embedding(ctx, ctx->full));
+        panel_pack(pa, hin, rows, nrhs, npad, ctx->st);
+        CK(coarse_apply_tc_prepare(L.nc, npad));
+        TcApplyArgs a{L.Aemb, pa, pb, L.nc, npad, dagger ? 1 : 0, ctx->g, nullptr, (int*)p64a};
+        CK(coarse_apply_tc(a, ctx->st));
+        panel_unpack(hout, pb, rows, nrhs, npad, ctx->st);
+        int err = 0;
+        CK(cudaMemcpyAsync(&err, p64a, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        if (err) st = fail(ctx, MG_ERR_TIMEOUT, "batched coarse stencil: a bounded wait gave up");
+    } else {
+        TRY(dalloc(ctx, &p64a, sizeof(double2) * npanel));
+        TRY(dalloc(ctx, &p64b, sizeof(double2) * npanel));
+        tmp.push_back(p64a);
+        tmp.push_back(p64b);
+        panel_pack64(p64a, hin, rows, nrhs, npad, ctx->st);
+        coarse_apply_batched_simt<double>(p64b, L.A64, p64a, L.nc, npad, dagger != 0, ctx->g, ctx->st);
+        panel_unpack64(hout, p64b, rows, nrhs, npad, ctx->st);
+    }
+    CKL();
+    if (st == MG_OK) {
+        CK(cudaMemcpyAsync(y, hout, sizeof(double2) * nin, cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        for (int r = 0; r < nrhs; ++r)
+            for (long long i = 0; i < 2 * rows; ++i) y[(size_t)r * 2 * rows + i] *= scale[r];
+    }
+    for (void* q : tmp) {
+        for (size_t i = 0; i < ctx->allocs.size(); ++i)
+            if (ctx->allocs[i] == q) { ctx->allocs.erase(ctx->allocs.begin() + i); break; }
+        cudaFree(q);
+    }
+    return st;
+}
+
+}  // extern "C"

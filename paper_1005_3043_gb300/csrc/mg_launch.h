@@ -1,5 +1,6 @@
 // Host-side launchers of the library's kernels (internal, not part of the C-ABI).
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -67,8 +68,14 @@ void gcr_xupdate(double2* x, const v2<T>* Z, size_t n, int k, const GcrCoef& y, 
 // ---------------------------------------------------------------- transfer / coarse
 // P64[X][s][i][6][l] from prototypes V[i][X][12][l]; *status = 1 on rank deficiency
 void block_orthonormalize(double2* P, const double2* V, int nv, const Geom& g, int* d_status, cudaStream_t st);
-template <typename T> void restrict_(v2<T>* rc, const v2<T>* P, const v2<T>* r, int nv, const Geom& g, cudaStream_t st);
-template <typename T> void prolong(v2<T>* e, const v2<T>* P, const v2<T>* yc, int nv, const Geom& g, cudaStream_t st);
+// coarse vector entry (X, a) lives at index (X*2nv + a)*cstride + coff (1, 0: plain coarse vector;
+// npad, n: column n of an RHS panel)
+template <typename T>
+void restrict_(v2<T>* rc, const v2<T>* P, const v2<T>* r, int nv, const Geom& g, cudaStream_t st, int cstride = 1,
+               int coff = 0);
+template <typename T>
+void prolong(v2<T>* e, const v2<T>* P, const v2<T>* yc, int nv, const Geom& g, cudaStream_t st, int cstride = 1,
+             int coff = 0);
 // A64 (column-major blocks) = P^dag D P; Aself scratch of Vc*8*nc*nc complex
 void coarse_build(double2* A, double2* Aself, const double2* P, const double2* U, int nv, double mass, const Geom& g,
                   cudaStream_t st);
@@ -120,5 +127,68 @@ template <typename T> struct CgnrArgs {
     int* err;
 };
 template <typename T> cudaError_t cgnr_persistent(const CgnrArgs<T>& args, cudaStream_t st);
+
+// ---------------------------------------------------------------- batched (multi-RHS) coarse level
+// Panel layout xB[X][b][n], n < npad (multiple of 16), complex FP32.
+// Aemb: per (X, d) the 2nc x 2nc real embedding of A[X][d] in FP16, tensor-core layout.
+void coarse_embed(__half* Aemb, const double2* A, int nc, int Vc, cudaStream_t st);
+struct TcApplyArgs {
+    const __half* Aemb;
+    const float2* x;
+    float2* y;
+    int nc;
+    int npad;
+    int dag;
+    Geom g;
+    float* norms;   // optional per-aggregate column sums of |y|^2: [Vc][npad]
+    int* err;       // set to 1 if a bounded wait gave up
+};
+// y = D_c x (dag: sigma3 D_c sigma3 x) for the whole panel on tcgen05 tensor cores;
+// coarse_apply_tc_prepare(nc, npad) once per shape before launching (and before any capture)
+bool coarse_apply_tc_supported(int nc, int npad);
+cudaError_t coarse_apply_tc_prepare(int nc, int npad);
+cudaError_t coarse_apply_tc(const TcApplyArgs& args, cudaStream_t st);
+// kernels launched by one bcg_iteration
+constexpr int kBcgKernelsPerIteration = 8;
+// SIMT reference of the same contraction with the FP64 operator
+template <typename T>
+void coarse_apply_batched_simt(v2<T>* y, const double2* A, const v2<T>* x, int nc, int npad, bool dag, const Geom& g,
+                               cudaStream_t st);
+
+struct BatchScal {   // per-RHS CG scalars, npad doubles each
+    double* scale;
+    double* done;
+    double* iters;
+    double* r2;
+    double* gamma;
+    double* alpha;
+    double* beta;
+};
+struct BatchCg {
+    const __half* Aemb;
+    float2* y;
+    float2* r;
+    float2* s;
+    float2* p;
+    float2* q;
+    const float2* rc;
+    int nc, npad, nrhs, maxit;
+    double tol2;
+    Geom g;
+    BatchScal S;
+    float* xpart;    // [Vc][npad]
+    float* rpart;    // [152][npad]
+    int* active;     // columns still iterating after the last check
+    int* err;
+};
+constexpr int kBatchRowChunks = 152;
+void bcg_start(const BatchCg& c, cudaStream_t st);
+void bcg_iteration(const BatchCg& c, cudaStream_t st);
+void bcg_finish(const BatchCg& c, cudaStream_t st);
+// nrhs stacked FP64 coarse vectors in[n][row] <-> panel [row][npad]
+void panel_pack(float2* out, const double2* in, long long rows, int nrhs, int npad, cudaStream_t st);
+void panel_unpack(double2* out, const float2* in, long long rows, int nrhs, int npad, cudaStream_t st);
+void panel_pack64(double2* out, const double2* in, long long rows, int nrhs, int npad, cudaStream_t st);
+void panel_unpack64(double2* out, const double2* in, long long rows, int nrhs, int npad, cudaStream_t st);
 
 }  // namespace wmg

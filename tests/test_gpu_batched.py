@@ -1,0 +1,80 @@
+"""Batched right-hand sides: the tensor-core coarse stencil on an RHS panel and
+the lockstep batched MG-GCR solve, against the FP64 CPU oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1005_3043_gb300 as wmg
+import synth
+from tests._fields import c1_workload, rough_gauge
+
+pytestmark = pytest.mark.gpu
+
+
+def maxrel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300))
+
+
+def params(nv, B=(4, 4, 4, 4), **kw):
+    p = wmg.mg_default_params()
+    for i in range(4):
+        p.block[i] = B[i]
+    p.nvec = nv
+    p.setup_group = kw.pop("setup_group", min(4, nv))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+@pytest.mark.parametrize("L,B,nv,nrhs", [((8, 8, 8, 8), (4, 4, 4, 4), 8, 5),
+                                         ((8, 8, 8, 8), (4, 4, 4, 4), 8, 16),
+                                         ((4, 4, 4, 8), (2, 2, 2, 2), 8, 33),
+                                         ((8, 8, 8, 8), (4, 4, 4, 4), 24, 12)])
+def test_batched_coarse_stencil(L, B, nv, nrhs):
+    """Tensor cores (FP16 operator, hi+lo panel, FP32 accumulation) and the FP64 SIMT
+    reference against the oracle's D_c and D_c^dag, one RHS at a time."""
+    wmg.build.build()
+    U = rough_gauge(L, seed=5)
+    m = -0.2
+    V0 = synth.gaussian_vectors(L, nv, 91)
+    P, st = oracle.block_orthonormalize(V0, L, B)
+    A = oracle.coarse_build(U, P, m, L, B)
+    Lc = oracle.coarse_dims(L, B)
+    Vc = oracle.volume(Lc)
+    x = synth.gaussian(nrhs * Vc * 2 * nv, 92, 0).reshape(nrhs, Vc, 2 * nv)
+    x[1 % nrhs] *= 1e-6                          # sources of very different scale in one panel
+    with wmg.WilsonMG(L, params(nv, B)) as mg:
+        mg.set_links(U)
+        mg.set_mass(m)
+        mg.set_null_vectors(V0)
+        for dag in (False, True):
+            ref = np.stack([(oracle.coarse_apply_dag if dag else oracle.coarse_apply)(A, x[i], Lc) for i in range(nrhs)])
+            y64 = mg.coarse_batched(x, dagger=dag, impl=1)
+            assert maxrel(y64, ref) < 1e-12
+            ytc = mg.coarse_batched(x, dagger=dag, impl=0)
+            for i in range(nrhs):                # per source, relative to its own size
+                assert maxrel(ytc[i], ref[i]) < 2e-3, (dag, i, maxrel(ytc[i], ref[i]))
+
+
+def test_batched_solve_matches_single_solves():
+    L, B, nv, U, m = c1_workload()
+    V0 = synth.gaussian_vectors(L, nv, 2001)
+    po = oracle.make_params(L, B, nv=nv, m=m)
+    _, P, A, st = oracle.setup(po, U, V0, init_relax=10, n_iter=3, group_size=4)
+    Vs = _
+    nrhs = 6
+    V = oracle.volume(L)
+    b = np.stack([synth.gaussian_spinor(L, 7, stream=i) for i in range(nrhs - 2)] +
+                 [synth.point_source(L, 0, 0, 0), synth.point_source(L, 77, 3, 2)])
+    with wmg.WilsonMG(L, params(nv, B, prec_inner=wmg.MG_FP32, delta=1e-4)) as mg:
+        mg.set_links(U)
+        mg.set_mass(m)
+        mg.set_null_vectors(Vs)
+        x, infos = mg.solve_batched(b)
+        single = [mg.solve(b[i])[1] for i in range(nrhs)]
+    for i in range(nrhs):
+        assert infos[i]["status"] == 0
+        res = np.linalg.norm(b[i] - oracle.dslash(U, x[i], m, L)) / np.linalg.norm(b[i])
+        assert res <= 1e-10, (i, res)
+        # same method per source; the FP16 coarse operator changes the preconditioner only slightly
+        assert abs(infos[i]["outer_iters"] - single[i]["outer_iters"]) <= max(3, 0.15 * single[i]["outer_iters"])
