@@ -344,29 +344,65 @@ template void coarse_apply_batched_simt<double>(v2<double>*, const double2*, con
                                                 const Geom&, cudaStream_t);
 
 // ---------------------------------------------------------------- per-RHS CGNR steps
-// Per-RHS scalars (double, npad entries each) in BatchScal; partial sums over
-// coarse rows go to part[chunk][n].  Columns whose done flag is set are frozen.
-constexpr int kRowChunks = 152;
+// Per-RHS scalars (double, npad entries each) in BatchScal.  Column sums are
+// reduced in two fixed-order stages: per-block partials part[block][n], then
+// one CTA per column adds the partials.  Columns whose done flag is set are
+// frozen.
+constexpr int kRowChunks = kBatchRowChunks;
 
-// column sums of |v|^2 over the rows of one chunk: part[chunk][n]
-__global__ void k_bcol_norm_partial(const float2* __restrict__ v, long long rows, int npad, float* part) {
-    long long r0 = (long long)blockIdx.x * rows / gridDim.x, r1 = (long long)(blockIdx.x + 1) * rows / gridDim.x;
+// rows [r0, r1) of block b of nb over `rows`; thread (rg, n), rgs row groups
+struct ColTile {
+    int n, rg, rgs;
+    long long r0, r1;
+    __device__ ColTile(int npad, long long rows) {
+        rgs = blockDim.x / npad;
+        if (rgs < 1) rgs = 1;
+        n = threadIdx.x % npad;
+        rg = threadIdx.x / npad;
+        r0 = (long long)blockIdx.x * rows / gridDim.x;
+        r1 = (long long)(blockIdx.x + 1) * rows / gridDim.x;
+    }
+    __device__ bool active() const { return rg < rgs; }
+};
+// per-column sum of v over the row groups of this block (fixed order) -> part[blockIdx][n]
+__device__ __forceinline__ void col_partial(float v, const ColTile& t, int npad, float* sh, float* part) {
+    if (t.active()) sh[t.rg * npad + t.n] = v;
+    __syncthreads();
     for (int n = threadIdx.x; n < npad; n += blockDim.x) {
         float s = 0.f;
-        for (long long r = r0; r < r1; ++r) {
-            float2 a = v[r * npad + n];
-            s += a.x * a.x + a.y * a.y;
-        }
+        for (int g = 0; g < t.rgs; ++g) s += sh[g * npad + n];
         part[(size_t)blockIdx.x * npad + n] = s;
     }
 }
+// one CTA per column: sum of part[c][n] over c < nparts, fixed order
+__device__ __forceinline__ double col_total(const float* part, int nparts, int npad) {
+    __shared__ double sh[33];
+    const int n = blockIdx.x;
+    double a = 0;
+    for (int c = threadIdx.x; c < nparts; c += blockDim.x) a += (double)part[(size_t)c * npad + n];
+    double v[1] = {a};
+    block_reduce<1>(v, (double (*)[32])sh);
+    if (threadIdx.x == 0) sh[32] = v[0];
+    __syncthreads();
+    return sh[32];
+}
 
-// initialise: scale_n = ||rc_n||, r = rc / scale, y = 0, done = (scale == 0 || n >= nrhs)
-__global__ void k_bcg_scale(BatchScal S, const float* part, int nchunk, int npad, int nrhs, int maxit) {
-    int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= npad) return;
-    double s = 0;
-    for (int c = 0; c < nchunk; ++c) s += part[(size_t)c * npad + n];
+__global__ void k_bcol_norm(const float2* __restrict__ v, long long rows, int npad, float* part) {
+    extern __shared__ float shf[];
+    ColTile t(npad, rows);
+    float s = 0.f;
+    if (t.active())
+        for (long long r = t.r0 + t.rg; r < t.r1; r += t.rgs) {
+            float2 a = v[r * npad + t.n];
+            s += a.x * a.x + a.y * a.y;
+        }
+    col_partial(s, t, npad, shf, part);
+}
+// scale_n = ||rc_n||, done = (scale == 0 || n >= nrhs)
+__global__ void k_bcg_scale(BatchScal S, const float* part, int nparts, int npad, int nrhs, int maxit) {
+    double s = col_total(part, nparts, npad);
+    if (threadIdx.x != 0) return;
+    int n = blockIdx.x;
     double sc = sqrt(s);
     S.scale[n] = sc;
     S.done[n] = (n >= nrhs || !(sc > 0) || maxit <= 0) ? 1.0 : 0.0;
@@ -384,58 +420,55 @@ __global__ void k_bcg_start(float2* __restrict__ y, float2* __restrict__ r, cons
         y[i] = make_float2(0.f, 0.f);
     }
 }
-// gamma = ||s||^2 (first direction), p = s
+// gamma = ||s||^2 (first direction)
 __global__ void k_bcg_gamma0(BatchScal S, const float* xpart, int nx, int npad) {
-    int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= npad) return;
-    double s = 0;
-    for (int c = 0; c < nx; ++c) s += xpart[(size_t)c * npad + n];
-    S.gamma[n] = s;
+    double s = col_total(xpart, nx, npad);
+    if (threadIdx.x == 0) S.gamma[blockIdx.x] = s;
 }
 // alpha = gamma / ||q||^2
 __global__ void k_bcg_alpha(BatchScal S, const float* xpart, int nx, int npad) {
-    int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= npad || S.done[n] != 0) return;
-    double s = 0;
-    for (int c = 0; c < nx; ++c) s += xpart[(size_t)c * npad + n];
+    double s = col_total(xpart, nx, npad);
+    int n = blockIdx.x;
+    if (threadIdx.x != 0 || S.done[n] != 0) return;
     if (s > 0) S.alpha[n] = S.gamma[n] / s;
     else { S.alpha[n] = 0; S.done[n] = 1; }
 }
-// y += alpha p, r -= alpha q (active columns)
+// y += alpha p, r -= alpha q (active columns), column partials of ||r||^2; zeroes *active
 __global__ void k_bcg_update1(float2* __restrict__ y, float2* __restrict__ r, const float2* __restrict__ p,
-                              const float2* __restrict__ q, long long total, int npad, BatchScal S) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-        int n = (int)(i % npad);
-        if (S.done[n] != 0) continue;
-        float al = (float)S.alpha[n];
-        float2 pv = p[i], qv = q[i], yv = y[i], rv = r[i];
-        y[i] = make_float2(yv.x + al * pv.x, yv.y + al * pv.y);
-        r[i] = make_float2(rv.x - al * qv.x, rv.y - al * qv.y);
+                              const float2* __restrict__ q, long long rows, int npad, BatchScal S, float* part,
+                              int* active) {
+    extern __shared__ float shf[];
+    if (blockIdx.x == 0 && threadIdx.x == 0) *active = 0;
+    ColTile t(npad, rows);
+    float s = 0.f;
+    if (t.active() && S.done[t.n] == 0) {
+        const float al = (float)S.alpha[t.n];
+        for (long long rr = t.r0 + t.rg; rr < t.r1; rr += t.rgs) {
+            long long i = rr * npad + t.n;
+            float2 pv = p[i], qv = q[i], yv = y[i], rv = r[i];
+            y[i] = make_float2(yv.x + al * pv.x, yv.y + al * pv.y);
+            float2 rn = make_float2(rv.x - al * qv.x, rv.y - al * qv.y);
+            r[i] = rn;
+            s += rn.x * rn.x + rn.y * rn.y;
+        }
     }
+    col_partial(s, t, npad, shf, part);
 }
-// ||r||^2, iteration count, stopping test; *active = columns still running
-__global__ void k_bcg_check(BatchScal S, const float* part, int nchunk, int npad, double tol2, int maxit, int* active) {
-    __shared__ int cnt;
-    if (threadIdx.x == 0) cnt = 0;
-    __syncthreads();
-    for (int n = threadIdx.x; n < npad; n += blockDim.x) {
-        if (S.done[n] != 0) continue;
-        double s = 0;
-        for (int c = 0; c < nchunk; ++c) s += part[(size_t)c * npad + n];
-        S.r2[n] = s;                         // relative to ||rc_n||^2 = 1 after scaling
-        S.iters[n] += 1;
-        if (s <= tol2 || S.iters[n] >= maxit) S.done[n] = 1;
-        else atomicAdd(&cnt, 1);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) *active = cnt;
+// ||r||^2, iteration count, stopping test; *active counts columns still running
+__global__ void k_bcg_check(BatchScal S, const float* part, int nparts, int npad, double tol2, int maxit, int* active) {
+    double s = col_total(part, nparts, npad);
+    int n = blockIdx.x;
+    if (threadIdx.x != 0 || S.done[n] != 0) return;
+    S.r2[n] = s;                         // relative to ||rc_n||^2 = 1 after scaling
+    S.iters[n] += 1;
+    if (s <= tol2 || S.iters[n] >= maxit) S.done[n] = 1;
+    else atomicAdd(active, 1);
 }
 // beta = ||s||^2 / gamma, gamma = ||s||^2
 __global__ void k_bcg_beta(BatchScal S, const float* xpart, int nx, int npad) {
-    int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= npad || S.done[n] != 0) return;
-    double s = 0;
-    for (int c = 0; c < nx; ++c) s += xpart[(size_t)c * npad + n];
+    double s = col_total(xpart, nx, npad);
+    int n = blockIdx.x;
+    if (threadIdx.x != 0 || S.done[n] != 0) return;
     S.beta[n] = S.gamma[n] > 0 ? s / S.gamma[n] : 0.0;
     S.gamma[n] = s;
 }
@@ -464,43 +497,47 @@ static inline int ew_grid(long long total) {
     if (b > 152 * 8) b = 152 * 8;
     return (int)(b > 0 ? b : 1);
 }
+static inline int col_threads(int npad) {
+    int rgs = 256 / npad;
+    if (rgs < 1) rgs = 1;
+    return ((rgs * npad + 31) / 32) * 32;
+}
+static inline size_t col_smem(int npad) { return sizeof(float) * (size_t)col_threads(npad) + sizeof(float) * npad; }
 
 // One CGLS iteration on all columns (kernels only: capturable in a CUDA graph).
 void bcg_iteration(const BatchCg& c, cudaStream_t st) {
-    const long long total = (long long)c.g.Vc * c.nc * c.npad;
-    const int nb = (c.npad + 127) / 128;
+    const long long rows = (long long)c.g.Vc * c.nc, total = rows * c.npad;
+    const int ct = col_threads(c.npad);
+    const size_t cs = col_smem(c.npad);
     TcApplyArgs ap{c.Aemb, c.p, c.q, c.nc, c.npad, 0, c.g, c.xpart, c.err};
     coarse_apply_tc(ap, st);                                                               // q = D_c p
     note_launch();
-    k_bcg_alpha<<<nb, 128, 0, st>>>(c.S, c.xpart, c.g.Vc, c.npad);
+    k_bcg_alpha<<<c.npad, 256, 0, st>>>(c.S, c.xpart, c.g.Vc, c.npad);
     note_launch();
-    k_bcg_update1<<<ew_grid(total), 256, 0, st>>>(c.y, c.r, c.p, c.q, total, c.npad, c.S);
+    k_bcg_update1<<<kRowChunks, ct, cs, st>>>(c.y, c.r, c.p, c.q, rows, c.npad, c.S, c.rpart, c.active);
     note_launch();
-    k_bcol_norm_partial<<<kRowChunks, 128, 0, st>>>(c.r, (long long)c.g.Vc * c.nc, c.npad, c.rpart);
-    note_launch();
-    k_bcg_check<<<1, 256, 0, st>>>(c.S, c.rpart, kRowChunks, c.npad, c.tol2, c.maxit, c.active);
+    k_bcg_check<<<c.npad, 256, 0, st>>>(c.S, c.rpart, kRowChunks, c.npad, c.tol2, c.maxit, c.active);
     TcApplyArgs as{c.Aemb, c.r, c.s, c.nc, c.npad, 1, c.g, c.xpart, c.err};
     coarse_apply_tc(as, st);                                                               // s = D_c^dag r
     note_launch();
-    k_bcg_beta<<<nb, 128, 0, st>>>(c.S, c.xpart, c.g.Vc, c.npad);
+    k_bcg_beta<<<c.npad, 256, 0, st>>>(c.S, c.xpart, c.g.Vc, c.npad);
     note_launch();
     k_bcg_update2<<<ew_grid(total), 256, 0, st>>>(c.p, c.s, total, c.npad, c.S, 0);
 }
 
 // y = 0, r = rc/||rc||, s = D_c^dag r, gamma, p = s
 void bcg_start(const BatchCg& c, cudaStream_t st) {
-    const long long total = (long long)c.g.Vc * c.nc * c.npad;
-    const int nb = (c.npad + 127) / 128;
+    const long long rows = (long long)c.g.Vc * c.nc, total = rows * c.npad;
     note_launch();
-    k_bcol_norm_partial<<<kRowChunks, 128, 0, st>>>(c.rc, (long long)c.g.Vc * c.nc, c.npad, c.rpart);
+    k_bcol_norm<<<kRowChunks, col_threads(c.npad), col_smem(c.npad), st>>>(c.rc, rows, c.npad, c.rpart);
     note_launch();
-    k_bcg_scale<<<nb, 128, 0, st>>>(c.S, c.rpart, kRowChunks, c.npad, c.nrhs, c.maxit);
+    k_bcg_scale<<<c.npad, 256, 0, st>>>(c.S, c.rpart, kRowChunks, c.npad, c.nrhs, c.maxit);
     note_launch();
     k_bcg_start<<<ew_grid(total), 256, 0, st>>>(c.y, c.r, c.rc, total, c.npad, c.S);
     TcApplyArgs as{c.Aemb, c.r, c.s, c.nc, c.npad, 1, c.g, c.xpart, c.err};
     coarse_apply_tc(as, st);
     note_launch();
-    k_bcg_gamma0<<<nb, 128, 0, st>>>(c.S, c.xpart, c.g.Vc, c.npad);
+    k_bcg_gamma0<<<c.npad, 256, 0, st>>>(c.S, c.xpart, c.g.Vc, c.npad);
     note_launch();
     k_bcg_update2<<<ew_grid(total), 256, 0, st>>>(c.p, c.s, total, c.npad, c.S, 1);
 }
@@ -514,6 +551,11 @@ void bcg_finish(const BatchCg& c, cudaStream_t st) {
 }  // namespace wmg
 
 namespace wmg {
+static inline int ew_grid2(long long total) {
+    long long b = (total + 255) / 256;
+    if (b > 152 * 8) b = 152 * 8;
+    return (int)(b > 0 ? b : 1);
+}
 // columns n < nrhs of a panel from nrhs stacked coarse vectors in[n][row] (FP64), other columns zero
 __global__ void k_panel_pack(float2* __restrict__ out, const double2* __restrict__ in, long long rows, int nrhs, int npad) {
     long long total = rows * npad;
@@ -558,18 +600,18 @@ __global__ void k_panel_unpack_t(double2* __restrict__ out, const v2<T>* __restr
 }
 void panel_pack(float2* out, const double2* in, long long rows, int nrhs, int npad, cudaStream_t st) {
     note_launch();
-    k_panel_pack<<<ew_grid(rows * npad), 256, 0, st>>>(out, in, rows, nrhs, npad);
+    k_panel_pack<<<ew_grid2(rows * npad), 256, 0, st>>>(out, in, rows, nrhs, npad);
 }
 void panel_unpack(double2* out, const float2* in, long long rows, int nrhs, int npad, cudaStream_t st) {
     note_launch();
-    k_panel_unpack<<<ew_grid(rows * nrhs), 256, 0, st>>>(out, in, rows, nrhs, npad);
+    k_panel_unpack<<<ew_grid2(rows * nrhs), 256, 0, st>>>(out, in, rows, nrhs, npad);
 }
 void panel_pack64(double2* out, const double2* in, long long rows, int nrhs, int npad, cudaStream_t st) {
     note_launch();
-    k_panel_pack_t<double><<<ew_grid(rows * npad), 256, 0, st>>>(out, in, rows, nrhs, npad);
+    k_panel_pack_t<double><<<ew_grid2(rows * npad), 256, 0, st>>>(out, in, rows, nrhs, npad);
 }
 void panel_unpack64(double2* out, const double2* in, long long rows, int nrhs, int npad, cudaStream_t st) {
     note_launch();
-    k_panel_unpack_t<double><<<ew_grid(rows * nrhs), 256, 0, st>>>(out, in, rows, nrhs, npad);
+    k_panel_unpack_t<double><<<ew_grid2(rows * nrhs), 256, 0, st>>>(out, in, rows, nrhs, npad);
 }
 }  // namespace wmg
