@@ -219,11 +219,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_dslash(v2<T>* _
             }
     }
     if (MODE == DS_XMY_NORM) {
-        double v1[1] = {(double)red[0]};
-        grid_reduce<1>(v1, R.partials, R.ticket, [&](double (&t)[1]) { R.scal[slot] = t[0]; });
+        T v1[1] = {red[0]};
+        grid_reduce<1, T>(v1, R.partials, R.ticket, [&](double (&t)[1]) { R.scal[slot] = t[0]; });
     } else if (MODE == DS_MRDOT) {
-        double v3[3] = {(double)red[0], (double)red[1], (double)red[2]};
-        grid_reduce<3>(v3, R.partials, R.ticket, [&](double (&t)[3]) {
+        T v3[3] = {red[0], red[1], red[2]};
+        grid_reduce<3, T>(v3, R.partials, R.ticket, [&](double (&t)[3]) {
             double f = t[2] > 0 ? omega / t[2] : 0.0;
             R.scal[S_MR_ALPHA] = f * t[0];
             R.scal[S_MR_ALPHA + 1] = f * t[1];
@@ -255,20 +255,19 @@ template <typename T> __global__ void k_zero(v2<T>* x, size_t n) {
     }
 }
 template <typename T> __global__ void k_norm2(const v2<T>* __restrict__ x, size_t n, int slot, Reduce R) {
-    double acc[1] = {0.0};
     T a = 0;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         a += norm2(ld<T>(x + i));
-    acc[0] = (double)a;
-    grid_reduce<1>(acc, R.partials, R.ticket, [&](double (&t)[1]) { R.scal[slot] = t[0]; });
+    T acc[1] = {a};
+    grid_reduce<1, T>(acc, R.partials, R.ticket, [&](double (&t)[1]) { R.scal[slot] = t[0]; });
 }
 template <typename T>
 __global__ void k_dot(const v2<T>* __restrict__ x, const v2<T>* __restrict__ y, size_t n, int slot, Reduce R) {
     cx<T> a(0, 0);
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         cmadc(a, ld<T>(x + i), ld<T>(y + i));
-    double acc[2] = {(double)a.r, (double)a.i};
-    grid_reduce<2>(acc, R.partials, R.ticket, [&](double (&t)[2]) {
+    T acc[2] = {a.r, a.i};
+    grid_reduce<2, T>(acc, R.partials, R.ticket, [&](double (&t)[2]) {
         R.scal[slot] = t[0];
         R.scal[slot + 1] = t[1];
     });
@@ -364,10 +363,7 @@ __global__ void k_gcr_multidot(const v2<T>* __restrict__ basis, size_t n, int k,
             }
         }
     }
-    double acc[2 * NJ];
-#pragma unroll
-    for (int j = 0; j < 2 * NJ; ++j) acc[j] = (double)a[j];
-    grid_reduce<2 * NJ>(acc, R.partials, R.ticket, [&](double (&t)[2 * NJ]) {
+    grid_reduce<2 * NJ, T>(a, R.partials, R.ticket, [&](double (&t)[2 * NJ]) {
         for (int j = 0; j < k && j < NJ; ++j) {
             R.scal[rslot(j, k)] = t[2 * j];
             R.scal[rslot(j, k) + 1] = t[2 * j + 1];
@@ -391,8 +387,8 @@ __global__ void k_gcr_orth_norm(v2<T>* basis, size_t n, int k, Reduce R) {
         st<T>(pk + i, v);
         a += norm2(v);
     }
-    double acc[1] = {(double)a};
-    grid_reduce<1>(acc, R.partials, R.ticket, [&](double (&t)[1]) { R.scal[S_GCR_PN2] = t[0]; });
+    T acc[1] = {a};
+    grid_reduce<1, T>(acc, R.partials, R.ticket, [&](double (&t)[1]) { R.scal[S_GCR_PN2] = t[0]; });
 }
 template <typename T>
 __global__ void k_gcr_cdot(const v2<T>* __restrict__ basis, const v2<T>* __restrict__ r, size_t n, int k, Reduce R) {
@@ -400,8 +396,8 @@ __global__ void k_gcr_cdot(const v2<T>* __restrict__ basis, const v2<T>* __restr
     cx<T> a(0, 0);
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         cmadc(a, ld<T>(pk + i), ld<T>(r + i));
-    double acc[2] = {(double)a.r, (double)a.i};
-    grid_reduce<2>(acc, R.partials, R.ticket, [&](double (&t)[2]) {
+    T acc[2] = {a.r, a.i};
+    grid_reduce<2, T>(acc, R.partials, R.ticket, [&](double (&t)[2]) {
         double nk = sqrt(R.scal[S_GCR_PN2]);
         R.scal[rslot(k, k)] = nk;
         R.scal[rslot(k, k) + 1] = 0.0;
@@ -424,8 +420,8 @@ __global__ void k_gcr_update(v2<T>* basis, v2<T>* r, size_t n, int k, Reduce R) 
         st<T>(r + i, v);
         a += norm2(v);
     }
-    double acc[1] = {(double)a};
-    grid_reduce<1>(acc, R.partials, R.ticket, [&](double (&t)[1]) { R.scal[S_GCR_R2] = t[0]; });
+    T acc[1] = {a};
+    grid_reduce<1, T>(acc, R.partials, R.ticket, [&](double (&t)[1]) { R.scal[S_GCR_R2] = t[0]; });
 }
 template <typename T>
 __global__ void k_gcr_xupdate(double2* x, const v2<T>* __restrict__ Z, size_t n, int k, GcrCoef y) {

@@ -172,18 +172,47 @@ __device__ __forceinline__ void block_reduce(double (&v)[N], double (*sh)[32]) {
     }
 }
 
+template <typename TA> __device__ __forceinline__ TA warp_sum_acc(TA v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+// Block-reduce N values of type TA; result valid in thread 0.
+template <int N, typename TA>
+__device__ __forceinline__ void block_reduce_acc(TA (&v)[N], TA (*sh)[32]) {
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] = warp_sum_acc(v[k]);
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) sh[k][warp] = v[k];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            TA x = lane < nw ? sh[k][lane] : TA(0);
+            v[k] = warp_sum_acc(x);
+        }
+    }
+}
+
 // Single-pass deterministic grid reduction: every block writes its partial
 // sums, the last block to arrive adds them in block order and calls
-// fin(total) on thread 0.  `partials` needs gridDim.x * N doubles, `ticket`
-// one zeroed counter (reset to 0 by the last block).
-template <int N, typename Fin>
-__device__ __forceinline__ void grid_reduce(double (&v)[N], double* partials, unsigned int* ticket, Fin fin) {
-    __shared__ double sh[N][32];
+// fin(total) on thread 0 (totals promoted to double).  TA is the accumulation
+// type inside blocks (float for the FP32 path: the FP64 pipe of this part is
+// narrow).  `partials` needs gridDim.x * N doubles, `ticket` one zeroed
+// counter (reset to 0 by the last block).
+template <int N, typename TA = double, typename Fin>
+__device__ __forceinline__ void grid_reduce(TA (&v)[N], double* partials, unsigned int* ticket, Fin fin) {
+    __shared__ TA sh[N][32];
     __shared__ bool is_last;
-    block_reduce<N>(v, sh);
+    block_reduce_acc<N, TA>(v, sh);
+    TA* part = reinterpret_cast<TA*>(partials);
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int k = 0; k < N; ++k) partials[(size_t)blockIdx.x * N + k] = v[k];
+        for (int k = 0; k < N; ++k) part[(size_t)blockIdx.x * N + k] = v[k];
         __threadfence();
         unsigned int t = atomicAdd(ticket, 1u);
         is_last = (t == gridDim.x - 1);
@@ -191,16 +220,19 @@ __device__ __forceinline__ void grid_reduce(double (&v)[N], double* partials, un
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    double acc[N];
+    TA acc[N];
 #pragma unroll
-    for (int k = 0; k < N; ++k) acc[k] = 0.0;
+    for (int k = 0; k < N; ++k) acc[k] = TA(0);
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
 #pragma unroll
-        for (int k = 0; k < N; ++k) acc[k] += __ldcg(partials + (size_t)b * N + k);
+        for (int k = 0; k < N; ++k) acc[k] += __ldcg(part + (size_t)b * N + k);
     }
-    block_reduce<N>(acc, sh);
+    block_reduce_acc<N, TA>(acc, sh);
     if (threadIdx.x == 0) {
-        fin(acc);
+        double t[N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) t[k] = (double)acc[k];
+        fin(t);
         *ticket = 0u;
     }
 }
