@@ -53,7 +53,11 @@ enum mg_status {
     MG_ERR_CUDA = -7           /* a CUDA runtime call failed */
 };
 
-enum mg_precision { MG_FP64 = 0, MG_FP32 = 1 };
+/* Inner precision of the preconditioner and Krylov basis (the solution and
+ * the true residual are always FP64).  MG_FP16: FP32 arithmetic with the
+ * coarse operator of the CGNR coarse solve stored in FP16 with one scale per
+ * (aggregate, direction) block (needs an even nvec). */
+enum mg_precision { MG_FP64 = 0, MG_FP32 = 1, MG_FP16 = 2 };
 
 /* Solver parameters (paper, Sec. III-IV; defaults from mg_default_params). */
 typedef struct {
@@ -70,7 +74,7 @@ typedef struct {
     int max_outer;         /* maximum outer iterations (preconditioner applications) */
     int max_coarse;        /* maximum coarse iterations per cycle */
     double delta;          /* mixed precision: restart when ||r|| < delta * ||r at restart|| (0: off) */
-    int prec_inner;        /* MG_FP64 or MG_FP32: smoother, dslash, transfers, coarse solve, Krylov basis */
+    int prec_inner;        /* MG_FP64, MG_FP32 or MG_FP16: smoother, dslash, transfers, coarse solve, Krylov basis */
     int coarse_check;      /* coarse iterations between convergence checks read by the host */
 } mg_params;
 

@@ -30,6 +30,7 @@ MG_ERR_TIMEOUT = -6
 MG_ERR_CUDA = -7
 MG_FP64 = 0
 MG_FP32 = 1
+MG_FP16 = 2
 
 LIB_PATH = _build_mod.LIB
 

@@ -659,7 +659,7 @@ template <typename T> __device__ __forceinline__ void write_partial(T v, double*
 //   ST_PLAIN: operand = in;          output out = D_c(^dag) in, n0 = ||out||^2
 enum { ST_PLAIN = 0, ST_P = 1, ST_R = 2 };
 
-template <typename T> struct RowsPerThread { static constexpr int value = 2; };
+template <typename T, bool H16 = false> struct RowsPerThread { static constexpr int value = H16 ? 4 : 2; };
 
 template <typename T, int R> struct RowLoad;
 template <> struct RowLoad<double, 2> {
@@ -676,6 +676,16 @@ template <> struct RowLoad<float, 2> {
         v[1] = cx<float>(a.z, a.w);
     }
 };
+// four consecutive rows of the FP16 operator in one 16-byte load
+__device__ __forceinline__ void row_load16(const __half2* p, cx<float> (&v)[4]) {
+    uint4 u = __ldg(reinterpret_cast<const uint4*>(p));
+    const __half2* h = reinterpret_cast<const __half2*>(&u);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        float2 f = __half22float2(h[r]);
+        v[r] = cx<float>(f.x, f.y);
+    }
+}
 
 template <typename T> struct PhaseArgs {
     const v2<T>* in;       // ST_PLAIN operand
@@ -691,10 +701,11 @@ template <typename T> struct PhaseArgs {
     bool first;            // ST_P, first iteration
 };
 
-template <typename T, bool DAG, int STAGE>
-__device__ void cg_phase(const PhaseArgs<T>& ph, const v2<T>* __restrict__ A, int nc, int xpb, const Geom& g,
-                         v2<T>* xs, cx<T>* part, T& n0, T& n1) {
-    constexpr int R = RowsPerThread<T>::value;
+template <typename T, bool DAG, int STAGE, bool H16>
+__device__ void cg_phase(const PhaseArgs<T>& ph, const v2<T>* __restrict__ A, const __half2* __restrict__ A16,
+                         const float* __restrict__ s16, int nc, int xpb, const Geom& g, v2<T>* xs, cx<T>* part, T& n0,
+                         T& n1) {
+    constexpr int R = RowsPerThread<T, H16>::value;
     const int nvh = nc >> 1, nrow = 9 * nc, ngrp = nc / R, nthr = 9 * ngrp, nall = xpb * nrow;
     const int xl = threadIdx.x / nthr, rem = threadIdx.x - xl * nthr;
     const int d = rem / ngrp, a0 = (rem - d * ngrp) * R;
@@ -728,27 +739,51 @@ __device__ void cg_phase(const PhaseArgs<T>& ph, const v2<T>* __restrict__ A, in
         __syncthreads();
         const int X = Xb + xl;
         if (threadIdx.x < xpb * nthr && X < g.Vc) {
-            const v2<T>* Ad = A + ((size_t)X * 9 + d) * nc * nc + a0;
             const v2<T>* xd = xs + xl * nrow + d * nc;
             cx<T> acc[R][2];
 #pragma unroll
             for (int r = 0; r < R; ++r) { acc[r][0] = cx<T>(0, 0); acc[r][1] = cx<T>(0, 0); }
             constexpr int U = 4;
-            for (int b0 = 0; b0 < nc; b0 += U) {
-                cx<T> av[U][R];
+            if constexpr (H16) {
+                const __half2* Ad = A16 + ((size_t)X * 9 + d) * nc * nc + a0;
+                for (int b0 = 0; b0 < nc; b0 += U) {
+                    uint4 raw[U];
 #pragma unroll
-                for (int j = 0; j < U; ++j)
-                    if (b0 + j < nc) RowLoad<T, R>::load(Ad + (size_t)(b0 + j) * nc, av[j]);
+                    for (int j = 0; j < U; ++j)
+                        if (b0 + j < nc) raw[j] = __ldg(reinterpret_cast<const uint4*>(Ad + (size_t)(b0 + j) * nc));
 #pragma unroll
-                for (int j = 0; j < U; ++j)
-                    if (b0 + j < nc) {
-                        cx<T> xb = ld<T>(xd + b0 + j);
+                    for (int j = 0; j < U; ++j)
+                        if (b0 + j < nc) {
+                            cx<T> xb = ld<T>(xd + b0 + j);
+                            const __half2* h = reinterpret_cast<const __half2*>(&raw[j]);
 #pragma unroll
-                        for (int r = 0; r < R; ++r) cmad(acc[r][j & 1], av[j][r], xb);
-                    }
+                            for (int r = 0; r < R; ++r) {
+                                float2 f = __half22float2(h[r]);
+                                cmad(acc[r][j & 1], cx<T>(f.x, f.y), xb);
+                            }
+                        }
+                }
+                const T sc = (T)s16[(size_t)X * 9 + d];
+#pragma unroll
+                for (int r = 0; r < R; ++r) part[xl * nrow + d * nc + a0 + r] = sc * (acc[r][0] + acc[r][1]);
+            } else {
+                const v2<T>* Ad = A + ((size_t)X * 9 + d) * nc * nc + a0;
+                for (int b0 = 0; b0 < nc; b0 += U) {
+                    cx<T> av[U][R];
+#pragma unroll
+                    for (int j = 0; j < U; ++j)
+                        if (b0 + j < nc) RowLoad<T, R>::load(Ad + (size_t)(b0 + j) * nc, av[j]);
+#pragma unroll
+                    for (int j = 0; j < U; ++j)
+                        if (b0 + j < nc) {
+                            cx<T> xb = ld<T>(xd + b0 + j);
+#pragma unroll
+                            for (int r = 0; r < R; ++r) cmad(acc[r][j & 1], av[j][r], xb);
+                        }
+                }
+#pragma unroll
+                for (int r = 0; r < R; ++r) part[xl * nrow + d * nc + a0 + r] = acc[r][0] + acc[r][1];
             }
-#pragma unroll
-            for (int r = 0; r < R; ++r) part[xl * nrow + d * nc + a0 + r] = acc[r][0] + acc[r][1];
         }
         __syncthreads();
         for (int t = threadIdx.x; t < xpb * nc; t += blockDim.x) {
@@ -775,7 +810,7 @@ __device__ void cg_phase(const PhaseArgs<T>& ph, const v2<T>* __restrict__ A, in
 // double-buffered so that no CTA overwrites what another still reads).
 template <typename T> struct CgnrMaxThreads { static constexpr int value = 384; };
 
-template <typename T>
+template <typename T, bool H16>
 __global__ void __launch_bounds__(CgnrMaxThreads<T>::value, 2) k_cgnr_persistent(CgnrArgs<T> a) {
     extern __shared__ unsigned char smem_raw[];
     const int nc = a.nc, xpb = a.xpb;
@@ -812,7 +847,7 @@ __global__ void __launch_bounds__(CgnrMaxThreads<T>::value, 2) k_cgnr_persistent
         // s = D_c^dag r, gamma = ||s||^2
         ph.in = a.r;
         ph.out = a.s;
-        cg_phase<T, true, ST_PLAIN>(ph, a.A, nc, xpb, a.g, xs, part, n0, n1);
+        cg_phase<T, true, ST_PLAIN, H16>(ph, a.A, a.A16, a.s16, nc, xpb, a.g, xs, part, n0, n1);
         write_partial<T>(n0, a.partials, 1, shr);
         if (!grid_sync(cnt, gen, G, a.err)) return;
         T gamma = sum_partials<T>(a.partials, 1, G, shr);
@@ -824,7 +859,7 @@ __global__ void __launch_bounds__(CgnrMaxThreads<T>::value, 2) k_cgnr_persistent
             ph.s = a.s; ph.p_old = pbuf[b ^ 1]; ph.p_new = pbuf[b]; ph.out = a.q;
             ph.coef = beta; ph.first = (it == 0);
             n0 = 0; n1 = 0;
-            cg_phase<T, false, ST_P>(ph, a.A, nc, xpb, a.g, xs, part, n0, n1);
+            cg_phase<T, false, ST_P, H16>(ph, a.A, a.A16, a.s16, nc, xpb, a.g, xs, part, n0, n1);
             write_partial<T>(n0, a.partials, 0, shr);
             if (!grid_sync(cnt, gen, G, a.err)) return;
             T qq = sum_partials<T>(a.partials, 0, G, shr);
@@ -835,7 +870,7 @@ __global__ void __launch_bounds__(CgnrMaxThreads<T>::value, 2) k_cgnr_persistent
             ph.r_old = rbuf[b]; ph.q = a.q; ph.r_new = rbuf[b ^ 1]; ph.y = a.y; ph.p_new = pbuf[b];
             ph.out = a.s; ph.coef = alpha;
             n0 = 0; n1 = 0;
-            cg_phase<T, true, ST_R>(ph, a.A, nc, xpb, a.g, xs, part, n0, n1);
+            cg_phase<T, true, ST_R, H16>(ph, a.A, a.A16, a.s16, nc, xpb, a.g, xs, part, n0, n1);
             write_partial<T>(n0, a.partials, 1, shr);
             write_partial<T>(n1, a.partials, 2, shr);
             if (!grid_sync(cnt, gen, G, a.err)) return;
@@ -857,51 +892,87 @@ __global__ void __launch_bounds__(CgnrMaxThreads<T>::value, 2) k_cgnr_persistent
 }
 
 // aggregates per CTA: as many 9*nc-thread groups as fit in the thread limit
-template <typename T> int cgnr_threads_per_x(int nc) { return 9 * (nc / RowsPerThread<T>::value); }
-template <typename T> int cgnr_xpb(int nc) {
-    int x = CgnrMaxThreads<T>::value / cgnr_threads_per_x<T>(nc);
+template <typename T, bool H16> int cgnr_threads_per_x(int nc) { return 9 * (nc / RowsPerThread<T, H16>::value); }
+template <typename T, bool H16> int cgnr_xpb(int nc) {
+    int x = CgnrMaxThreads<T>::value / cgnr_threads_per_x<T, H16>(nc);
     return x > 0 ? x : 1;
 }
-template <typename T> int cgnr_block_threads(int nc) {
-    return ((cgnr_xpb<T>(nc) * cgnr_threads_per_x<T>(nc) + 31) / 32) * 32;
+template <typename T, bool H16> int cgnr_block_threads(int nc) {
+    return ((cgnr_xpb<T, H16>(nc) * cgnr_threads_per_x<T, H16>(nc) + 31) / 32) * 32;
 }
-template <typename T> size_t cgnr_smem(int nc) {
-    return (sizeof(v2<T>) + sizeof(cx<T>)) * 9 * (size_t)nc * cgnr_xpb<T>(nc);
+template <typename T, bool H16> size_t cgnr_smem(int nc) {
+    return (sizeof(v2<T>) + sizeof(cx<T>)) * 9 * (size_t)nc * cgnr_xpb<T, H16>(nc);
 }
 
 // co-resident CTAs for this nc, then the smallest balanced grid covering all aggregates
-template <typename T> int cgnr_grid(int nc, int Vc) {
+template <typename T, bool H16> int cgnr_grid(int nc, int Vc) {
     static int cached[2][128] = {};
     int dev = 0;
     cudaGetDevice(&dev);
     int key = nc < 128 ? nc : 127;
-    int* slot = &cached[sizeof(T) == 8 ? 1 : 0][key];
+    int* slot = &cached[H16 ? 1 : 0][key];
     if (*slot == 0) {
         int sms = 0, per = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        size_t sm = cgnr_smem<T>(nc);   // < 48 KB: no attribute needed
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cgnr_persistent<T>, cgnr_block_threads<T>(nc), sm);
+        size_t sm = cgnr_smem<T, H16>(nc);   // < 48 KB: no attribute needed
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cgnr_persistent<T, H16>, cgnr_block_threads<T, H16>(nc), sm);
         *slot = per * sms;
     }
     int gmax = *slot;
     if (gmax <= 0) return 0;
-    int xpb = cgnr_xpb<T>(nc);
+    int xpb = cgnr_xpb<T, H16>(nc);
     int batches = (Vc + xpb - 1) / xpb;               // CTA-sized pieces of work
     int rounds = (batches + gmax - 1) / gmax;         // pieces per CTA
     return (batches + rounds - 1) / rounds;
 }
 
-template <typename T> cudaError_t cgnr_persistent(const CgnrArgs<T>& args, cudaStream_t st) {
-    int G = cgnr_grid<T>(args.nc, args.g.Vc);
+template <typename T, bool H16> cudaError_t cgnr_launch(const CgnrArgs<T>& args, cudaStream_t st) {
+    int G = cgnr_grid<T, H16>(args.nc, args.g.Vc);
     if (G <= 0) return cudaErrorCooperativeLaunchTooLarge;
     CgnrArgs<T> a = args;
-    a.xpb = cgnr_xpb<T>(a.nc);
+    a.xpb = cgnr_xpb<T, H16>(a.nc);
     void* params[] = {&a};
     note_launch();
-    return cudaLaunchCooperativeKernel((const void*)k_cgnr_persistent<T>, dim3(G), dim3(cgnr_block_threads<T>(a.nc)),
-                                       params, cgnr_smem<T>(a.nc), st);
+    return cudaLaunchCooperativeKernel((const void*)k_cgnr_persistent<T, H16>, dim3(G),
+                                       dim3(cgnr_block_threads<T, H16>(a.nc)), params, cgnr_smem<T, H16>(a.nc), st);
 }
-template cudaError_t cgnr_persistent<float>(const CgnrArgs<float>&, cudaStream_t);
-template cudaError_t cgnr_persistent<double>(const CgnrArgs<double>&, cudaStream_t);
+template <> cudaError_t cgnr_persistent<float>(const CgnrArgs<float>& a, cudaStream_t st) {
+    if (a.A16) {
+        if (a.nc % 4 != 0) return cudaErrorInvalidValue;
+        return cgnr_launch<float, true>(a, st);
+    }
+    return cgnr_launch<float, false>(a, st);
+}
+template <> cudaError_t cgnr_persistent<double>(const CgnrArgs<double>& a, cudaStream_t st) {
+    return cgnr_launch<double, false>(a, st);
+}
+
+// FP16 copy of the coarse operator with one scale per (X, d) block: A16 = A / s, s = max |Re, Im|
+__global__ void k_coarse_pack16(__half2* A16, float* s16, const double2* __restrict__ A, int nc) {
+    __shared__ double sh[33];
+    const size_t blk = blockIdx.x, nn = (size_t)nc * nc;
+    const double2* Ab = A + blk * nn;
+    double mx = 0;
+    for (size_t i = threadIdx.x; i < nn; i += blockDim.x) mx = fmax(mx, fmax(fabs(Ab[i].x), fabs(Ab[i].y)));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, sh[w]);
+        sh[32] = m > 0 ? m : 1.0;
+        s16[blk] = (float)sh[32];
+    }
+    __syncthreads();
+    const double inv = 1.0 / (double)(float)sh[32];
+    for (size_t i = threadIdx.x; i < nn; i += blockDim.x)
+        A16[blk * nn + i] = __floats2half2_rn((float)(Ab[i].x * inv), (float)(Ab[i].y * inv));
+}
+void coarse_pack16(__half2* A16, float* s16, const double2* A, int nc, int Vc, cudaStream_t st) {
+    note_launch();
+    k_coarse_pack16<<<Vc * 9, 256, 0, st>>>(A16, s16, A, nc);
+}
+
+
 
 }  // namespace wmg

@@ -33,6 +33,9 @@ struct CoarseLevel {
     float2* A32 = nullptr;
     __half* Aemb = nullptr;   // FP16 tensor-core embedding of A64 (batched path), built on demand
     bool emb_valid = false;
+    __half2* A16 = nullptr;   // FP16 copy with per-block scales s16 (FP16-storage mode), built on demand
+    float* s16 = nullptr;
+    bool a16_valid = false;
     double mass = 0.0;
     bool valid = false;
 };
@@ -120,6 +123,7 @@ struct mg_ctx {
     size_t ev_used = 0;
     std::vector<int> ev_class;      // class of each (start, stop) pair
     double coarse_mark = 0.0;       // S_CG_TOTAL at the last profile read
+    bool coarse16 = false;          // coarse CGNR reads the FP16 operator
 };
 
 namespace {
@@ -282,7 +286,7 @@ int build_level(mg_ctx* ctx, CoarseLevel& L, const double2* V, int nv) {
     size_t np = (size_t)nv * nfine(ctx), na = (size_t)ctx->g.Vc * 9 * L.nc * L.nc;
     convert<double, float>(L.P32, L.P64, np, ctx->st);
     PROF_BEGIN(MG_K_COARSE_BUILD);
-    if (ctx->prm.prec_inner == MG_FP32)   // FP32 products, FP64 accumulation
+    if (ctx->prm.prec_inner != MG_FP64)   // FP32 products, FP64 accumulation
         coarse_build_f32(L.A64, ctx->Aself, L.P32, ctx->U32, nv, ctx->mass, ctx->g, ctx->st);
     else
         coarse_build(L.A64, ctx->Aself, L.P64, ctx->U64, nv, ctx->mass, ctx->g, ctx->st);
@@ -293,17 +297,31 @@ int build_level(mg_ctx* ctx, CoarseLevel& L, const double2* V, int nv) {
     L.mass = ctx->mass;
     L.valid = true;
     L.emb_valid = false;
+    L.a16_valid = false;
     return MG_OK;
 }
 
 // ---------------------------------------------------------------- coarse solve
+int ensure_a16(mg_ctx* ctx, CoarseLevel& L) {
+    if (L.a16_valid) return MG_OK;
+    if (L.nc % 4 != 0) return fail(ctx, MG_ERR_INVALID_ARG, "FP16 coarse storage needs an even nvec");
+    if (!L.A16) {
+        TRY(dalloc(ctx, &L.A16, sizeof(__half2) * (size_t)ctx->g.Vc * 9 * (2 * L.cap) * (2 * L.cap)));
+        TRY(dalloc(ctx, &L.s16, sizeof(float) * (size_t)ctx->g.Vc * 9));
+    }
+    coarse_pack16(L.A16, L.s16, L.A64, L.nc, ctx->g.Vc, ctx->st);
+    CKL();
+    L.a16_valid = true;
+    return MG_OK;
+}
+
 template <typename T>
 CgnrArgs<T> cgnr_args(const CoarseLevel& L, const Geom& g, const v2<T>* rc, v2<T>* y, v2<T>* r, v2<T>* r1, v2<T>* sv,
                       v2<T>* p, v2<T>* p1, v2<T>* q, double tol, int maxit, double* partials, unsigned int* bar,
                       double* scal) {
     CgnrArgs<T> a;
     a.y = y; a.r = r; a.r1 = r1; a.s = sv; a.p = p; a.p1 = p1; a.q = q;
-    a.A = lvlA<T>(L); a.rc = rc; a.nc = L.nc; a.g = g;
+    a.A = lvlA<T>(L); a.A16 = nullptr; a.s16 = nullptr; a.rc = rc; a.nc = L.nc; a.g = g;
     a.tol2 = tol * tol; a.maxit = maxit;
     a.partials = partials; a.bar = bar; a.scal = scal; a.err = (int*)(bar + 2);
     return a;
@@ -317,6 +335,12 @@ int coarse_solve(mg_ctx* ctx, const CoarseLevel& L, const v2<T>* rc, v2<T>* y, d
     Work<T>& w = work<T>(ctx);
     CgnrArgs<T> a = cgnr_args<T>(L, ctx->g, rc, y, w.cr, w.cr1, w.cs, w.cp, w.cp1, w.cq, tol, maxit, ctx->R.partials,
                                  ctx->bar, ctx->R.scal);
+    if (std::is_same<T, float>::value && ctx->coarse16) {
+        CoarseLevel& Lm = const_cast<CoarseLevel&>(L);
+        TRY(ensure_a16(ctx, Lm));
+        a.A16 = Lm.A16;
+        a.s16 = Lm.s16;
+    }
     CK(cudaMemsetAsync(ctx->bar, 0, sizeof(unsigned int) * 3, ctx->st));
     PROF_BEGIN(MG_K_COARSE_SOLVE);
     CK(cgnr_persistent<T>(a, ctx->st));
@@ -568,7 +592,11 @@ int check_params(const int dims[4], const mg_params* p, std::string& why) {
         why = "setup_group must divide nvec";
         return MG_ERR_INVALID_ARG;
     }
-    if (p->prec_inner != MG_FP64 && p->prec_inner != MG_FP32) { why = "prec_inner must be MG_FP64 or MG_FP32"; return MG_ERR_INVALID_ARG; }
+    if (p->prec_inner != MG_FP64 && p->prec_inner != MG_FP32 && p->prec_inner != MG_FP16) {
+        why = "prec_inner must be MG_FP64, MG_FP32 or MG_FP16";
+        return MG_ERR_INVALID_ARG;
+    }
+    if (p->prec_inner == MG_FP16 && p->nvec % 2 != 0) { why = "MG_FP16 needs an even nvec"; return MG_ERR_INVALID_ARG; }
     return MG_OK;
 }
 
@@ -799,6 +827,7 @@ int mg_set_mass(mg_ctx* ctx, double m) {
         CKL();
         ctx->full.mass = m;
         ctx->full.emb_valid = false;
+        ctx->full.a16_valid = false;
     }
     ctx->mass = m;
     CK(cudaStreamSynchronize(ctx->st));
@@ -827,7 +856,8 @@ int mg_setup(mg_ctx* ctx, const double* V0) {
     for (int i = 0; i < nv; ++i)
         spinor_to_internal<double>(ctx->protos + (size_t)i * n, ctx->protos_stage + (size_t)i * n, ctx->g, ctx->st);
     CKL();
-    return ctx->prm.prec_inner == MG_FP32 ? setup_impl<float>(ctx) : setup_impl<double>(ctx);
+    ctx->coarse16 = ctx->prm.prec_inner == MG_FP16;
+    return ctx->prm.prec_inner != MG_FP64 ? setup_impl<float>(ctx) : setup_impl<double>(ctx);
 }
 
 int mg_setup_device(mg_ctx* ctx, const double* V0_dev) {
@@ -838,7 +868,8 @@ int mg_setup_device(mg_ctx* ctx, const double* V0_dev) {
     for (int i = 0; i < ctx->prm.nvec; ++i)
         spinor_to_internal<double>(ctx->protos + (size_t)i * n, (const double2*)V0_dev + (size_t)i * n, ctx->g, ctx->st);
     CKL();
-    return ctx->prm.prec_inner == MG_FP32 ? setup_impl<float>(ctx) : setup_impl<double>(ctx);
+    ctx->coarse16 = ctx->prm.prec_inner == MG_FP16;
+    return ctx->prm.prec_inner != MG_FP64 ? setup_impl<float>(ctx) : setup_impl<double>(ctx);
 }
 
 int mg_set_null_vectors(mg_ctx* ctx, const double* V, int nv) {
@@ -892,7 +923,8 @@ int mg_solve_device(mg_ctx* ctx, const double* b_dev, double* x_dev, mg_solve_in
     if (!b_dev || !x_dev) return fail(ctx, MG_ERR_INVALID_ARG, "null vector");
     spinor_to_internal<double>(ctx->b64, (const double2*)b_dev, ctx->g, ctx->st);
     CKL();
-    int st = ctx->prm.prec_inner == MG_FP32 ? gcr_solve<float>(ctx, info) : gcr_solve<double>(ctx, info);
+    ctx->coarse16 = ctx->prm.prec_inner == MG_FP16;
+    int st = ctx->prm.prec_inner != MG_FP64 ? gcr_solve<float>(ctx, info) : gcr_solve<double>(ctx, info);
     if (st != MG_OK && st != MG_ERR_NOT_CONVERGED) return st;
     spinor_from_internal<double>((double2*)x_dev, ctx->x64, ctx->g, ctx->st);
     CKL();
@@ -915,45 +947,52 @@ int mg_solve(mg_ctx* ctx, const double* b, double* x, mg_solve_info* info) {
 int mg_apply_dslash(mg_ctx* ctx, const double* in, double* out, int prec) {
     TRY(need_links(ctx));
     if (!in || !out) return MG_ERR_INVALID_ARG;
-    return prec == MG_FP32 ? hook_dslash<float>(ctx, in, out) : hook_dslash<double>(ctx, in, out);
+    ctx->coarse16 = prec == MG_FP16;
+    return prec != MG_FP64 ? hook_dslash<float>(ctx, in, out) : hook_dslash<double>(ctx, in, out);
 }
 int mg_restrict(mg_ctx* ctx, const double* r, double* rc, int prec) {
     TRY(need_level(ctx));
     if (!r || !rc) return MG_ERR_INVALID_ARG;
-    return prec == MG_FP32 ? hook_restrict<float>(ctx, r, rc) : hook_restrict<double>(ctx, r, rc);
+    ctx->coarse16 = prec == MG_FP16;
+    return prec != MG_FP64 ? hook_restrict<float>(ctx, r, rc) : hook_restrict<double>(ctx, r, rc);
 }
 int mg_prolong(mg_ctx* ctx, const double* yc, double* e, int prec) {
     TRY(need_level(ctx));
     if (!yc || !e) return MG_ERR_INVALID_ARG;
-    return prec == MG_FP32 ? hook_prolong<float>(ctx, yc, e) : hook_prolong<double>(ctx, yc, e);
+    ctx->coarse16 = prec == MG_FP16;
+    return prec != MG_FP64 ? hook_prolong<float>(ctx, yc, e) : hook_prolong<double>(ctx, yc, e);
 }
 int mg_apply_coarse(mg_ctx* ctx, const double* x, double* y, int dagger, int prec) {
     TRY(need_level(ctx));
     if (!x || !y) return MG_ERR_INVALID_ARG;
-    return prec == MG_FP32 ? hook_coarse<float>(ctx, x, y, dagger) : hook_coarse<double>(ctx, x, y, dagger);
+    ctx->coarse16 = prec == MG_FP16;
+    return prec != MG_FP64 ? hook_coarse<float>(ctx, x, y, dagger) : hook_coarse<double>(ctx, x, y, dagger);
 }
 int mg_mr(mg_ctx* ctx, double* e, double* r, int nsteps, int prec) {
     TRY(need_links(ctx));
     if (!e || !r || nsteps < 0) return MG_ERR_INVALID_ARG;
-    return prec == MG_FP32 ? hook_mr<float>(ctx, e, r, nsteps) : hook_mr<double>(ctx, e, r, nsteps);
+    ctx->coarse16 = prec == MG_FP16;
+    return prec != MG_FP64 ? hook_mr<float>(ctx, e, r, nsteps) : hook_mr<double>(ctx, e, r, nsteps);
 }
 int mg_coarse_solve(mg_ctx* ctx, const double* rc, double* y, double tol, int maxit, int prec, int* iters,
                     double* final_rel) {
     TRY(need_level(ctx));
     if (!rc || !y || maxit < 0) return MG_ERR_INVALID_ARG;
-    return prec == MG_FP32 ? hook_coarse_solve<float>(ctx, rc, y, tol, maxit, iters, final_rel)
+    ctx->coarse16 = prec == MG_FP16;
+    return prec != MG_FP64 ? hook_coarse_solve<float>(ctx, rc, y, tol, maxit, iters, final_rel)
                            : hook_coarse_solve<double>(ctx, rc, y, tol, maxit, iters, final_rel);
 }
 int mg_vcycle(mg_ctx* ctx, const double* r, double* z, int prec) {
     TRY(need_level(ctx));
     if (!r || !z) return MG_ERR_INVALID_ARG;
-    return prec == MG_FP32 ? hook_vcycle<float>(ctx, r, z) : hook_vcycle<double>(ctx, r, z);
+    ctx->coarse16 = prec == MG_FP16;
+    return prec != MG_FP64 ? hook_vcycle<float>(ctx, r, z) : hook_vcycle<double>(ctx, r, z);
 }
 
 int mg_time_dslash(mg_ctx* ctx, int prec, int reps, double* ms_per_launch, double* bytes_per_launch) {
     TRY(need_links(ctx));
     if (reps <= 0 || !ms_per_launch) return MG_ERR_INVALID_ARG;
-    size_t real = prec == MG_FP32 ? 4 : 8;
+    size_t real = prec != MG_FP64 ? 4 : 8;
     // algorithmic minimum: 4 links x 18 reals + input 24 reals + output 24 reals per site
     if (bytes_per_launch) *bytes_per_launch = (double)ctx->g.V * (72 + 24 + 24) * real;
     auto run = [&](auto tag) -> int {
@@ -975,7 +1014,7 @@ int mg_time_dslash(mg_ctx* ctx, int prec, int reps, double* ms_per_launch, doubl
         *ms_per_launch = ms / reps;
         return MG_OK;
     };
-    return prec == MG_FP32 ? run(float{}) : run(double{});
+    return prec != MG_FP64 ? run(float{}) : run(double{});
 }
 
 int mg_profile_enable(mg_ctx* ctx, int on) {
@@ -1406,7 +1445,7 @@ int mg_solve_batched_device(mg_ctx* ctx, const double* b_dev, double* x_dev, int
     TRY(need_level(ctx));
     if (!b_dev || !x_dev || nrhs <= 0) return fail(ctx, MG_ERR_INVALID_ARG, "null buffer or nrhs <= 0");
     size_t n = nfine(ctx);
-    if (ctx->prm.prec_inner != MG_FP32) {   // FP64 inner precision: the sources one after another
+    if (ctx->prm.prec_inner == MG_FP64) {   // FP64 inner precision: the sources one after another
         int worst = MG_OK;
         for (int r = 0; r < nrhs; ++r) {
             int st = mg_solve_device(ctx, b_dev + 2 * r * n, x_dev + 2 * r * n, infos ? infos + r : nullptr);

@@ -115,6 +115,8 @@ template <typename T> struct CgnrArgs {
     v2<T>* p1;
     v2<T>* q;
     const v2<T>* A;
+    const __half2* A16;    // optional FP16 operator (T = float): A = s16[X*9+d] * A16
+    const float* s16;
     const v2<T>* rc;
     int nc;
     int xpb;               // aggregates per CTA (set by the launcher)
@@ -127,6 +129,8 @@ template <typename T> struct CgnrArgs {
     int* err;
 };
 template <typename T> cudaError_t cgnr_persistent(const CgnrArgs<T>& args, cudaStream_t st);
+// FP16 coarse operator with a per-(X, d) block scale, for the FP16-storage mode
+void coarse_pack16(__half2* A16, float* s16, const double2* A, int nc, int Vc, cudaStream_t st);
 
 // ---------------------------------------------------------------- batched (multi-RHS) coarse level
 // Panel layout xB[X][b][n], n < npad (multiple of 16), complex FP32.

@@ -273,3 +273,25 @@ def test_edge_cases(c1):
     with pytest.raises(wmg.MGError) as ei:
         wmg.WilsonMG((8, 8, 8, 6), make_params(nv, B))   # 6 not divisible by 4
     assert ei.value.status == wmg.MG_ERR_INVALID_ARG
+
+
+def test_fp16_coarse_storage(c1):
+    """MG_FP16: FP16 coarse operator (per-block scale) in the coarse CGNR.  The coarse
+    residual against the exact D_c stays at the FP16 storage level; every solve still
+    reaches a true FP64 residual of 1e-10."""
+    L, B, nv, U, m = c1["L"], c1["B"], c1["nv"], c1["U"], c1["m"]
+    Lc = oracle.coarse_dims(L, B)
+    with wmg.WilsonMG(L, make_params(nv, B, prec_inner=wmg.MG_FP16, delta=1e-4)) as mg:
+        mg.set_links(U)
+        mg.set_mass(m)
+        mg.set_null_vectors(c1["Vs"])
+        A = mg.coarse_op()
+        rc = synth.gaussian(mg.Vc * mg.nc, 41, 0).reshape(mg.Vc, mg.nc)
+        y16, it16, rel16 = mg.coarse_solve(rc, 1e-3, 5000, wmg.MG_FP16)
+        assert rel16 <= 1e-3
+        true_rel = np.linalg.norm(rc - oracle.coarse_apply(A, y16, Lc)) / np.linalg.norm(rc)
+        assert true_rel < 1e-2, true_rel
+        b = synth.gaussian_spinor(L, 7)
+        x, info = mg.solve(b)
+    assert info["status"] == 0
+    assert _true_rel(U, x, b, m, L) <= 1e-10
