@@ -13,6 +13,9 @@
 // MMAs per K step give an FP32-accurate product against the FP16 operator.
 #include <cuda_fp16.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "mg_launch.h"
 
 namespace wmg {
@@ -156,14 +159,15 @@ __host__ __device__ inline size_t tc_smem_bytes(int nc, int npad) {
     return 2 * SA + 4 * SB + 64;
 }
 
-// One CTA per aggregate X.  Pipeline over the 9 directions d with two stages:
+// One CTA per (aggregate X, column chunk of width nw).  Pipeline over the 9
+// directions d with two stages:
 // the bulk-copy engine brings A_emb[X][d], the CTA writes the hi/lo split of
 // x[X+d] (sigma3 applied for the adjoint), one thread issues the MMAs into the
 // TMEM accumulator (128 lanes = embedded rows, npad columns = RHS).
 __global__ void __launch_bounds__(kTcThreads, 1) k_coarse_apply_tc(TcApplyArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    const int nc = a.nc, npad = a.npad, K = 2 * nc, nvh = nc / 2;
-    const size_t SA = (size_t)128 * K * 2, SB = (size_t)npad * K * 2;
+    const int nc = a.nc, npad = a.npad, nw = a.nw, n0 = blockIdx.y * nw, K = 2 * nc, nvh = nc / 2;
+    const size_t SA = (size_t)128 * K * 2, SB = (size_t)nw * K * 2;
     __half* As = reinterpret_cast<__half*>(smem);
     __half* Bh = reinterpret_cast<__half*>(smem + 2 * SA);
     __half* Bl = reinterpret_cast<__half*>(smem + 2 * SA + 2 * SB);
@@ -172,7 +176,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_coarse_apply_tc(TcApplyArgs a
     __shared__ int s_fail;
     __shared__ float s_nrm[4][256];
     const int X = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t ncols = tc_tmem_cols(npad);
+    const uint32_t ncols = tc_tmem_cols(nw);
     const uint32_t bytesA = (uint32_t)(K * K * 2);
 
     if (tid == 0) {
@@ -194,7 +198,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_coarse_apply_tc(TcApplyArgs a
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_taddr;
-    const uint32_t idesc = idesc_f16(128, npad);
+    const uint32_t idesc = idesc_f16(128, nw);
     const uint32_t lbo = 128, sbo = (uint32_t)(K >> 3) * 128;
 
     for (int d = 0; d < 9; ++d) {
@@ -211,12 +215,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_coarse_apply_tc(TcApplyArgs a
         }
         // B = x[X+d] as hi + lo FP16, rows = RHS n, K-major columns k = (re|im, b)
         const int Y = coarse_neighbour(a.g, X, d);
-        const float2* xY = a.x + (size_t)Y * nc * npad;
-        __half* bh = Bh + (size_t)s * npad * K;
-        __half* bl = Bl + (size_t)s * npad * K;
-        for (int i = tid; i < nc * npad; i += kTcThreads) {
-            int b = i / npad, n = i - b * npad;
-            float2 v = xY[i];
+        const float2* xY = a.x + (size_t)Y * nc * npad + n0;
+        __half* bh = Bh + (size_t)s * nw * K;
+        __half* bl = Bl + (size_t)s * nw * K;
+        for (int i = tid; i < nc * nw; i += kTcThreads) {
+            int b = i / nw, n = i - b * nw;
+            float2 v = xY[(size_t)b * npad + n];
             if (a.dag && b >= nvh) { v.x = -v.x; v.y = -v.y; }
             __half hr = __float2half_rn(v.x), hi = __float2half_rn(v.y);
             __half lr = __float2half_rn(v.x - __half2float(hr)), li = __float2half_rn(v.y - __half2float(hi));
@@ -254,12 +258,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_coarse_apply_tc(TcApplyArgs a
     const bool im = m >= nc;
     const float sgn = (a.dag && arow >= nvh) ? -1.f : 1.f;
     float* yf = reinterpret_cast<float*>(a.y);
-    for (int c0 = 0; c0 < npad; c0 += 16) {
+    for (int c0 = 0; c0 < nw; c0 += 16) {
         float v[16];
         tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
         if (ok && valid_row) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) yf[(((size_t)X * nc + arow) * npad + c0 + j) * 2 + (im ? 1 : 0)] = sgn * v[j];
+            for (int j = 0; j < 16; ++j)
+                yf[(((size_t)X * nc + arow) * npad + n0 + c0 + j) * 2 + (im ? 1 : 0)] = sgn * v[j];
         }
         if (a.norms) {
 #pragma unroll
@@ -274,8 +279,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_coarse_apply_tc(TcApplyArgs a
     tc_fence_before();
     __syncthreads();
     if (a.norms)
-        for (int n = tid; n < npad; n += kTcThreads)
-            a.norms[(size_t)X * npad + n] = s_nrm[0][n] + s_nrm[1][n] + s_nrm[2][n] + s_nrm[3][n];
+        for (int n = tid; n < nw; n += kTcThreads)
+            a.norms[(size_t)X * npad + n0 + n] = s_nrm[0][n] + s_nrm[1][n] + s_nrm[2][n] + s_nrm[3][n];
     if (!ok && tid == 0) atomicExch(a.err, 1);
     if (warp == 0) tmem_dealloc(tmem, ncols);
 }
@@ -283,9 +288,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_coarse_apply_tc(TcApplyArgs a
 // Dynamic shared memory of one CTA: the two pipeline stages, padded so that at
 // most 512 / ncols CTAs fit on an SM (their TMEM allocations never exceed the
 // 512 columns of an SM, so no allocation waits).
-static size_t tc_launch_smem(int nc, int npad) {
-    size_t sm = tc_smem_bytes(nc, npad);
-    size_t per_sm = 228 * 1024, cap = 512 / tc_tmem_cols(npad);
+static size_t tc_launch_smem(int nc, int nw) {
+    size_t sm = tc_smem_bytes(nc, nw);
+    size_t per_sm = 228 * 1024, cap = 512 / tc_tmem_cols(nw);
     size_t min_sm = per_sm / (cap + 1) + 1024;
     return sm > min_sm ? sm : min_sm;
 }
@@ -293,16 +298,52 @@ bool coarse_apply_tc_supported(int nc, int npad) {
     return npad % 16 == 0 && npad >= 16 && npad <= 256 && (2 * nc) % 16 == 0 && 2 * nc <= 128 &&
            tc_launch_smem(nc, npad) + 4224 <= 227 * 1024;
 }
+// attribute for the largest chunk width used with this nc (every nw <= npad fits)
 cudaError_t coarse_apply_tc_prepare(int nc, int npad) {
     if (!coarse_apply_tc_supported(nc, npad)) return cudaErrorInvalidValue;
-    return cudaFuncSetAttribute(k_coarse_apply_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)tc_launch_smem(nc, npad));
+    size_t mx = 0;
+    for (int nw = 16; nw <= npad; nw += 16) mx = std::max(mx, tc_launch_smem(nc, nw));
+    return cudaFuncSetAttribute(k_coarse_apply_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
 }
-// launch only (coarse_apply_tc_prepare must have been called for this shape)
+// launch only (coarse_apply_tc_prepare must have been called for this shape);
+// args.nw = column chunk per CTA (multiple of 16 dividing npad; 0 = npad)
 cudaError_t coarse_apply_tc(const TcApplyArgs& args, cudaStream_t st) {
+    TcApplyArgs a = args;
+    if (a.nw <= 0) a.nw = a.npad;
     note_launch();
-    k_coarse_apply_tc<<<args.g.Vc, kTcThreads, tc_launch_smem(args.nc, args.npad), st>>>(args);
+    k_coarse_apply_tc<<<dim3(a.g.Vc, a.npad / a.nw), kTcThreads, tc_launch_smem(a.nc, a.nw), st>>>(a);
     return cudaGetLastError();
+}
+
+// Chunk width for (nc, npad): every candidate (multiples of 16 dividing npad)
+// is timed with CUDA events on the given stream and the fastest is kept.
+int coarse_apply_tc_tune(const TcApplyArgs& args, cudaStream_t st) {
+    struct Entry { int nc, npad, nw; };
+    static std::vector<Entry> cache;
+    for (const Entry& e : cache)
+        if (e.nc == args.nc && e.npad == args.npad) return e.nw;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = args.npad;
+    float best_ms = 1e30f;
+    for (int nw = 16; nw <= args.npad; nw += 16) {
+        if (args.npad % nw) continue;
+        TcApplyArgs a = args;
+        a.nw = nw;
+        coarse_apply_tc(a, st);   // warm-up
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 5; ++r) coarse_apply_tc(a, st);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) { best_ms = ms; best = nw; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cache.push_back({args.nc, args.npad, best});
+    return best;
 }
 
 // ---------------------------------------------------------------- SIMT reference of the same contraction
@@ -509,7 +550,7 @@ void bcg_iteration(const BatchCg& c, cudaStream_t st) {
     const long long rows = (long long)c.g.Vc * c.nc, total = rows * c.npad;
     const int ct = col_threads(c.npad);
     const size_t cs = col_smem(c.npad);
-    TcApplyArgs ap{c.Aemb, c.p, c.q, c.nc, c.npad, 0, c.g, c.xpart, c.err};
+    TcApplyArgs ap{c.Aemb, c.p, c.q, c.nc, c.npad, c.nw, 0, c.g, c.xpart, c.err};
     coarse_apply_tc(ap, st);                                                               // q = D_c p
     note_launch();
     k_bcg_alpha<<<c.npad, 256, 0, st>>>(c.S, c.xpart, c.g.Vc, c.npad);
@@ -517,7 +558,7 @@ void bcg_iteration(const BatchCg& c, cudaStream_t st) {
     k_bcg_update1<<<kRowChunks, ct, cs, st>>>(c.y, c.r, c.p, c.q, rows, c.npad, c.S, c.rpart, c.active);
     note_launch();
     k_bcg_check<<<c.npad, 256, 0, st>>>(c.S, c.rpart, kRowChunks, c.npad, c.tol2, c.maxit, c.active);
-    TcApplyArgs as{c.Aemb, c.r, c.s, c.nc, c.npad, 1, c.g, c.xpart, c.err};
+    TcApplyArgs as{c.Aemb, c.r, c.s, c.nc, c.npad, c.nw, 1, c.g, c.xpart, c.err};
     coarse_apply_tc(as, st);                                                               // s = D_c^dag r
     note_launch();
     k_bcg_beta<<<c.npad, 256, 0, st>>>(c.S, c.xpart, c.g.Vc, c.npad);
@@ -534,7 +575,7 @@ void bcg_start(const BatchCg& c, cudaStream_t st) {
     k_bcg_scale<<<c.npad, 256, 0, st>>>(c.S, c.rpart, kRowChunks, c.npad, c.nrhs, c.maxit);
     note_launch();
     k_bcg_start<<<ew_grid(total), 256, 0, st>>>(c.y, c.r, c.rc, total, c.npad, c.S);
-    TcApplyArgs as{c.Aemb, c.r, c.s, c.nc, c.npad, 1, c.g, c.xpart, c.err};
+    TcApplyArgs as{c.Aemb, c.r, c.s, c.nc, c.npad, c.nw, 1, c.g, c.xpart, c.err};
     coarse_apply_tc(as, st);
     note_launch();
     k_bcg_gamma0<<<c.npad, 256, 0, st>>>(c.S, c.xpart, c.g.Vc, c.npad);

@@ -1212,7 +1212,7 @@ BatchCg batch_cg(mg_ctx* ctx, double tol, int maxit, int nrhs) {
     BatchCg c;
     c.Aemb = ctx->full.Aemb;
     c.y = b.yB; c.r = b.rB; c.s = b.sB; c.p = b.pB; c.q = b.qB; c.rc = b.rcB;
-    c.nc = ctx->full.nc; c.npad = b.npad; c.nrhs = nrhs; c.maxit = maxit;
+    c.nc = ctx->full.nc; c.npad = b.npad; c.nw = b.npad; c.nrhs = nrhs; c.maxit = maxit;
     c.tol2 = tol * tol;
     c.g = ctx->g;
     c.S.scale = b.cgs; c.S.done = b.cgs + b.npad; c.S.iters = b.cgs + 2 * b.npad; c.S.r2 = b.cgs + 3 * b.npad;
@@ -1228,9 +1228,14 @@ int batched_coarse_solve(mg_ctx* ctx, int nrhs, double tol, int maxit, std::vect
     TRY(ensure_embedding(ctx, ctx->full));
     CK(coarse_apply_tc_prepare(ctx->full.nc, b.npad));
     BatchCg c = batch_cg(ctx, tol, maxit, nrhs);
+    {   // tile width from the autotuner (timed on the panel buffers once per shape)
+        TcApplyArgs t{c.Aemb, c.p, c.q, c.nc, c.npad, 0, 0, c.g, nullptr, c.err};
+        c.nw = coarse_apply_tc_tune(t, ctx->st);
+        CKL();
+    }
     long long tolbits = 0;
     std::memcpy(&tolbits, &c.tol2, sizeof(tolbits));
-    long long key[6] = {(long long)(size_t)c.Aemb, b.npad, nrhs, maxit, tolbits, ctx->full.nc};
+    long long key[6] = {(long long)(size_t)c.Aemb, b.npad, nrhs, maxit, tolbits, ctx->full.nc * 1024 + c.nw};
     if (!b.graph || std::memcmp(key, b.graph_key, sizeof(key)) != 0) {
         if (b.graph) { cudaGraphExecDestroy(b.graph); b.graph = nullptr; }
         cudaGraph_t gr;
@@ -1527,7 +1532,8 @@ int mg_apply_coarse_batched(mg_ctx* ctx, const double* x, double* y, int nrhs, i
         TRY(ensure_embedding(ctx, ctx->full));
         panel_pack(pa, hin, rows, nrhs, npad, ctx->st);
         CK(coarse_apply_tc_prepare(L.nc, npad));
-        TcApplyArgs a{L.Aemb, pa, pb, L.nc, npad, dagger ? 1 : 0, ctx->g, nullptr, (int*)p64a};
+        TcApplyArgs a{L.Aemb, pa, pb, L.nc, npad, 0, dagger ? 1 : 0, ctx->g, nullptr, (int*)p64a};
+        a.nw = coarse_apply_tc_tune(a, ctx->st);
         CK(coarse_apply_tc(a, ctx->st));
         panel_unpack(hout, pb, rows, nrhs, npad, ctx->st);
         int err = 0;

@@ -142,6 +142,7 @@ struct TcApplyArgs {
     float2* y;
     int nc;
     int npad;
+    int nw;         // panel columns per CTA (multiple of 16 dividing npad; 0: all)
     int dag;
     Geom g;
     float* norms;   // optional per-aggregate column sums of |y|^2: [Vc][npad]
@@ -152,6 +153,8 @@ struct TcApplyArgs {
 bool coarse_apply_tc_supported(int nc, int npad);
 cudaError_t coarse_apply_tc_prepare(int nc, int npad);
 cudaError_t coarse_apply_tc(const TcApplyArgs& args, cudaStream_t st);
+// autotuner: fastest chunk width for args' (nc, npad), timed once and cached
+int coarse_apply_tc_tune(const TcApplyArgs& args, cudaStream_t st);
 // kernels launched by one bcg_iteration
 constexpr int kBcgKernelsPerIteration = 8;
 // SIMT reference of the same contraction with the FP64 operator
@@ -176,7 +179,7 @@ struct BatchCg {
     float2* p;
     float2* q;
     const float2* rc;
-    int nc, npad, nrhs, maxit;
+    int nc, npad, nw, nrhs, maxit;
     double tol2;
     Geom g;
     BatchScal S;
