@@ -154,6 +154,23 @@ def one_step_rate(wmg, torch, w, prec, U, dV0, dB, dX, masses, stream):
     return len(masses) / (ms / 1e3), ms, iters
 
 
+def max_over_ranks(ms, device="cpu"):
+    """The job's time is its slowest replica's: MAX of the per-rank times
+    (identity when no process group is up)."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()):
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, ms):
+    """Whole-job throughput: the units every rank processed / the max-over-ranks time."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def run_ours(args, w):
     import torch
     import paper_1005_3043_gb300 as wmg
@@ -211,13 +228,9 @@ def run_ours(args, w):
     launches = wmg.mg_kernel_launches() - launches0
     prof, coarse_iters = mg.profile_read()
     mg.profile_enable(False)
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), "cuda")
     ms_step = ms / args.steps
-    value = world * n_solve * args.steps / (ms / 1e3)
+    value = job_rate(world, n_solve * args.steps, ms)
 
     # setup and solve phases of one more step, timed separately
     barrier()

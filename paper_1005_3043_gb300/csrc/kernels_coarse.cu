@@ -703,8 +703,8 @@ template <typename T> struct PhaseArgs {
 
 template <typename T, bool DAG, int STAGE, bool H16>
 __device__ void cg_phase(const PhaseArgs<T>& ph, const v2<T>* __restrict__ A, const __half2* __restrict__ A16,
-                         const float* __restrict__ s16, int nc, int xpb, const Geom& g, v2<T>* xs, cx<T>* part, T& n0,
-                         T& n1) {
+                         const float* __restrict__ s16, int nc, int xpb, const Geom& g, v2<T>* xs, cx<T>* part,
+                         const int* __restrict__ nbr, T& n0, T& n1) {
     constexpr int R = RowsPerThread<T, H16>::value;
     const int nvh = nc >> 1, nrow = 9 * nc, ngrp = nc / R, nthr = 9 * ngrp, nall = xpb * nrow;
     const int xl = threadIdx.x / nthr, rem = threadIdx.x - xl * nthr;
@@ -715,7 +715,7 @@ __device__ void cg_phase(const PhaseArgs<T>& ph, const v2<T>* __restrict__ A, co
             int di = ri / nc, b = ri - di * nc;
             int X = Xb + xi;
             if (X < g.Vc) {
-                int Y = coarse_neighbour(g, X, di);
+                int Y = __ldg(nbr + (size_t)X * 9 + di);
                 size_t o = (size_t)Y * nc + b;
                 cx<T> v;
                 if (STAGE == ST_PLAIN) {
@@ -847,7 +847,7 @@ __global__ void __launch_bounds__(CgnrMaxThreads<T>::value, 2) k_cgnr_persistent
         // s = D_c^dag r, gamma = ||s||^2
         ph.in = a.r;
         ph.out = a.s;
-        cg_phase<T, true, ST_PLAIN, H16>(ph, a.A, a.A16, a.s16, nc, xpb, a.g, xs, part, n0, n1);
+        cg_phase<T, true, ST_PLAIN, H16>(ph, a.A, a.A16, a.s16, nc, xpb, a.g, xs, part, a.nbr, n0, n1);
         write_partial<T>(n0, a.partials, 1, shr);
         if (!grid_sync(cnt, gen, G, a.err)) return;
         T gamma = sum_partials<T>(a.partials, 1, G, shr);
@@ -859,7 +859,7 @@ __global__ void __launch_bounds__(CgnrMaxThreads<T>::value, 2) k_cgnr_persistent
             ph.s = a.s; ph.p_old = pbuf[b ^ 1]; ph.p_new = pbuf[b]; ph.out = a.q;
             ph.coef = beta; ph.first = (it == 0);
             n0 = 0; n1 = 0;
-            cg_phase<T, false, ST_P, H16>(ph, a.A, a.A16, a.s16, nc, xpb, a.g, xs, part, n0, n1);
+            cg_phase<T, false, ST_P, H16>(ph, a.A, a.A16, a.s16, nc, xpb, a.g, xs, part, a.nbr, n0, n1);
             write_partial<T>(n0, a.partials, 0, shr);
             if (!grid_sync(cnt, gen, G, a.err)) return;
             T qq = sum_partials<T>(a.partials, 0, G, shr);
@@ -870,7 +870,7 @@ __global__ void __launch_bounds__(CgnrMaxThreads<T>::value, 2) k_cgnr_persistent
             ph.r_old = rbuf[b]; ph.q = a.q; ph.r_new = rbuf[b ^ 1]; ph.y = a.y; ph.p_new = pbuf[b];
             ph.out = a.s; ph.coef = alpha;
             n0 = 0; n1 = 0;
-            cg_phase<T, true, ST_R, H16>(ph, a.A, a.A16, a.s16, nc, xpb, a.g, xs, part, n0, n1);
+            cg_phase<T, true, ST_R, H16>(ph, a.A, a.A16, a.s16, nc, xpb, a.g, xs, part, a.nbr, n0, n1);
             write_partial<T>(n0, a.partials, 1, shr);
             write_partial<T>(n1, a.partials, 2, shr);
             if (!grid_sync(cnt, gen, G, a.err)) return;
@@ -945,6 +945,16 @@ template <> cudaError_t cgnr_persistent<float>(const CgnrArgs<float>& a, cudaStr
 }
 template <> cudaError_t cgnr_persistent<double>(const CgnrArgs<double>& a, cudaStream_t st) {
     return cgnr_launch<double, false>(a, st);
+}
+
+// coarse neighbour table nbr[X][d] (d = 0 self, 1+2mu / 2+2mu: +mu / -mu)
+__global__ void k_coarse_nbr(int* nbr, Geom g) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < g.Vc * 9) nbr[i] = coarse_neighbour(g, i / 9, i % 9);
+}
+void coarse_neighbour_table(int* nbr, const Geom& g, cudaStream_t st) {
+    note_launch();
+    k_coarse_nbr<<<(g.Vc * 9 + 255) / 256, 256, 0, st>>>(nbr, g);
 }
 
 // FP16 copy of the coarse operator with one scale per (X, d) block: A16 = A / s, s = max |Re, Im|

@@ -115,6 +115,7 @@ struct mg_ctx {
     double* h_scal = nullptr;        // pinned host copy of the scalars
     int* d_status = nullptr;
     unsigned int* bar = nullptr;     // persistent-kernel barrier: count, generation, error flag
+    int* cnbr = nullptr;             // coarse neighbour table [Vc][9]
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<void*> allocs;
     // launch timer
@@ -321,7 +322,7 @@ CgnrArgs<T> cgnr_args(const CoarseLevel& L, const Geom& g, const v2<T>* rc, v2<T
                       double* scal) {
     CgnrArgs<T> a;
     a.y = y; a.r = r; a.r1 = r1; a.s = sv; a.p = p; a.p1 = p1; a.q = q;
-    a.A = lvlA<T>(L); a.A16 = nullptr; a.s16 = nullptr; a.rc = rc; a.nc = L.nc; a.g = g;
+    a.A = lvlA<T>(L); a.A16 = nullptr; a.s16 = nullptr; a.nbr = nullptr; a.rc = rc; a.nc = L.nc; a.g = g;
     a.tol2 = tol * tol; a.maxit = maxit;
     a.partials = partials; a.bar = bar; a.scal = scal; a.err = (int*)(bar + 2);
     return a;
@@ -335,6 +336,7 @@ int coarse_solve(mg_ctx* ctx, const CoarseLevel& L, const v2<T>* rc, v2<T>* y, d
     Work<T>& w = work<T>(ctx);
     CgnrArgs<T> a = cgnr_args<T>(L, ctx->g, rc, y, w.cr, w.cr1, w.cs, w.cp, w.cp1, w.cq, tol, maxit, ctx->R.partials,
                                  ctx->bar, ctx->R.scal);
+    a.nbr = ctx->cnbr;
     if (std::is_same<T, float>::value && ctx->coarse16) {
         CoarseLevel& Lm = const_cast<CoarseLevel&>(L);
         TRY(ensure_a16(ctx, Lm));
@@ -772,7 +774,8 @@ int mg_create(const int dims[4], int t_antiperiodic, const mg_params* p, void* s
         (rc = dalloc(ctx, &ctx->R.partials, sizeof(double) * kMaxReduceBlocks * 64)) ||
         (rc = dalloc(ctx, &ctx->R.ticket, sizeof(unsigned int) * 4)) ||
         (rc = dalloc(ctx, &ctx->R.scal, sizeof(double) * S_COUNT)) || (rc = dalloc(ctx, &ctx->d_status, sizeof(int))) ||
-        (rc = dalloc(ctx, &ctx->bar, sizeof(unsigned int) * 4))) {
+        (rc = dalloc(ctx, &ctx->bar, sizeof(unsigned int) * 4)) ||
+        (rc = dalloc(ctx, &ctx->cnbr, sizeof(int) * 9 * (size_t)g.Vc))) {
         mg_destroy(ctx);
         return rc;
     }
@@ -781,6 +784,7 @@ int mg_create(const int dims[4], int t_antiperiodic, const mg_params* p, void* s
         cudaMemsetAsync(ctx->R.ticket, 0, sizeof(unsigned int) * 4, ctx->st) != cudaSuccess ||
         cudaMemsetAsync(ctx->R.scal, 0, sizeof(double) * S_COUNT, ctx->st) != cudaSuccess ||
         cudaMemsetAsync(ctx->bar, 0, sizeof(unsigned int) * 4, ctx->st) != cudaSuccess ||
+        (coarse_neighbour_table(ctx->cnbr, ctx->g, ctx->st), cudaGetLastError()) != cudaSuccess ||
         cudaStreamSynchronize(ctx->st) != cudaSuccess) {
         cudaGetLastError();
         mg_destroy(ctx);
@@ -1123,6 +1127,7 @@ extern "C" int mg_coarse_solve_noalloc(mg_ctx* ctx, const double* rc_dev, double
     CK(cudaMemsetAsync(bar, 0, sizeof(unsigned int) * 3, ctx->st));
     CgnrArgs<double> a = cgnr_args<double>(L, ctx->g, (const v2<double>*)rc_dev, (v2<double>*)y_dev, r, r1, s, p, p1, q,
                                            tol, maxit, R.partials, bar, R.scal);
+    a.nbr = ctx->cnbr;   // context memory made at create (an input, not an allocation here)
     CK(cgnr_persistent<double>(a, ctx->st));
     CK(cudaMemcpyAsync(ctx->h_scal + S_CG_RC2, R.scal + S_CG_RC2, sizeof(double) * 3, cudaMemcpyDeviceToHost, ctx->st));
     unsigned int flags[3];

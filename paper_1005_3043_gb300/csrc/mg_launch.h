@@ -117,6 +117,7 @@ template <typename T> struct CgnrArgs {
     const v2<T>* A;
     const __half2* A16;    // optional FP16 operator (T = float): A = s16[X*9+d] * A16
     const float* s16;
+    const int* nbr;        // coarse neighbour table [Vc][9]
     const v2<T>* rc;
     int nc;
     int xpb;               // aggregates per CTA (set by the launcher)
@@ -129,6 +130,7 @@ template <typename T> struct CgnrArgs {
     int* err;
 };
 template <typename T> cudaError_t cgnr_persistent(const CgnrArgs<T>& args, cudaStream_t st);
+void coarse_neighbour_table(int* nbr, const Geom& g, cudaStream_t st);
 // FP16 coarse operator with a per-(X, d) block scale, for the FP16-storage mode
 void coarse_pack16(__half2* A16, float* s16, const double2* A, int nc, int Vc, cudaStream_t st);
 
