@@ -76,6 +76,9 @@ typedef struct {
     double delta;          /* mixed precision: restart when ||r|| < delta * ||r at restart|| (0: off) */
     int prec_inner;        /* MG_FP64, MG_FP32 or MG_FP16: smoother, dslash, transfers, coarse solve, Krylov basis */
     int coarse_check;      /* coarse iterations between convergence checks read by the host */
+    int coarse_kernel;     /* FP32/FP16 coarse solve: 0 operator in shared memory, resident when it
+                              fits, else streamed through a bulk-copy ring (default); 1 operator
+                              read from global memory into registers; 2 the ring forced (tests) */
 } mg_params;
 
 typedef struct {
@@ -90,7 +93,7 @@ typedef struct {
 
 /* Fill p with the defaults: block 4^4, nvec 8, relax 10, iters 3, group 4,
  * smoother 4, omega 0.9, restart 16, tol 1e-10, coarse_tol 1e-3,
- * max_outer 1000, max_coarse 5000, delta 0, FP64, coarse_check 16. */
+ * max_outer 1000, max_coarse 5000, delta 0, FP64, coarse_check 16, coarse_kernel 0. */
 int mg_default_params(mg_params* p);
 
 /* Create a context for an L0 x L1 x L2 x L3 lattice.  dims[mu] must be a

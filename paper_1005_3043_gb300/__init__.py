@@ -40,7 +40,8 @@ class MgParams(ctypes.Structure):
                 ("setup_iters", ctypes.c_int), ("setup_group", ctypes.c_int), ("smoother_steps", ctypes.c_int),
                 ("omega", ctypes.c_double), ("gcr_restart", ctypes.c_int), ("tol", ctypes.c_double),
                 ("coarse_tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("max_coarse", ctypes.c_int),
-                ("delta", ctypes.c_double), ("prec_inner", ctypes.c_int), ("coarse_check", ctypes.c_int)]
+                ("delta", ctypes.c_double), ("prec_inner", ctypes.c_int), ("coarse_check", ctypes.c_int),
+                ("coarse_kernel", ctypes.c_int)]
 
 
 class MgSolveInfo(ctypes.Structure):

@@ -1,0 +1,516 @@
+// Coarse CGNR (CGLS, Sec. IV: CG on the normal equations of D_c) in one
+// persistent cooperative launch, with the coarse operator held on chip.
+//
+// Work split.  The operator rows of every aggregate X are cut into H = nc/RU
+// chunks of RU rows; a "unit" u = X*H + h holds rows h*RU .. h*RU+RU-1 of all
+// nine blocks of X and is stored contiguously,
+//     Au[u][d 9][b nc][a RU]        (FP32 complex, or FP16 complex + su[X][d])
+// so one bulk copy moves it.  CTA c (one per SM) owns the contiguous range of
+// units [c*NU/G, (c+1)*NU/G); the owner of unit (X, h) computes output rows
+// h*RU.. of X and does the elementwise CG updates of those entries, so every
+// entry is written by exactly one CTA.
+//
+// On-chip operator.  When a CTA's units fit in shared memory they are copied
+// once per launch and stay there for all iterations ("resident"); otherwise
+// they stream through a ring of slot groups, and the copies for the next
+// phase are issued while the current one is finishing, so they land during
+// the grid barrier.  The stencil operand (the CG vector on the CTA's
+// aggregates and their 8 neighbours) is staged in shared memory per phase,
+// pre-multiplied by the FP16 block scales and with the sigma_3 sign flips of
+// D_c^dag = sigma_3 D_c sigma_3 applied.
+//
+// Iteration (textbook CGLS, two grid-wide exchanges of partial sums, which
+// also serve as the grid barriers):
+//   q = D_c p,  alpha = gamma/|q|^2,  y += alpha p,  r -= alpha q,
+//   s = D_c^dag r,  gamma' = |s|^2,  beta = gamma'/gamma,  p = s + beta p
+// with the vector updates done while staging (p and r double-buffered).
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
+#include "mg_launch.h"
+#include "mg_ptx.cuh"
+#include "mg_sync.cuh"
+
+namespace wmg {
+
+constexpr int kCglsThreads = 512;
+constexpr long long kCopyWaitLimit = 4000000LL;   // polls of a bulk-copy mbarrier before giving up
+
+// Four consecutive rows a..a+3 of one column of a unit, as complex FP32 pairs
+// (re, im).  FP32: 32 bytes; FP16: 16 bytes (the block scale is carried by
+// the staged operand).
+template <bool H16> struct UnitOp;
+template <> struct UnitOp<false> {
+    using type = float2;
+    static constexpr int bytes = 8;
+    static __device__ __forceinline__ void quad(const float2* p, float2 (&v)[4]) {
+        const float4 w0 = reinterpret_cast<const float4*>(p)[0];
+        const float4 w1 = reinterpret_cast<const float4*>(p)[1];
+        v[0] = make_float2(w0.x, w0.y);
+        v[1] = make_float2(w0.z, w0.w);
+        v[2] = make_float2(w1.x, w1.y);
+        v[3] = make_float2(w1.z, w1.w);
+    }
+};
+template <> struct UnitOp<true> {
+    using type = __half2;
+    static constexpr int bytes = 4;
+    static __device__ __forceinline__ void quad(const __half2* p, float2 (&v)[4]) {
+        const uint4 w = *reinterpret_cast<const uint4*>(p);
+        v[0] = __half22float2(*reinterpret_cast<const __half2*>(&w.x));
+        v[1] = __half22float2(*reinterpret_cast<const __half2*>(&w.y));
+        v[2] = __half22float2(*reinterpret_cast<const __half2*>(&w.z));
+        v[3] = __half22float2(*reinterpret_cast<const __half2*>(&w.w));
+    }
+};
+
+// vectors of one phase (see the staging rules in cgls_phase)
+struct CglsPhase {
+    const float2* in;      // ST_IN: operand
+    const float2* s;       // ST_P: s
+    const float2* p_old;   // ST_P: previous direction (ignored when first)
+    float2* p_new;         // ST_P: own entries of the new direction; ST_R: current direction (read)
+    const float2* r_old;   // ST_R
+    const float2* q;       // ST_R
+    float2* r_new;         // ST_R
+    float2* y;             // ST_R
+    float2* out;
+    float coef;            // beta (ST_P) or alpha (ST_R)
+    bool first;
+};
+enum { ST_IN = 0, ST_P = 1, ST_R = 2 };
+
+constexpr int kStageRegs = 4;   // staged operand entries per thread kept as precomputed offsets
+
+template <bool H16> struct CglsCta {
+    using OT = typename UnitOp<H16>::type;
+    const CglsArgs& a;
+    int nc, K, nvh, RU, H, u0, u1, nu, X0, nX;
+    int W, NG, NW;
+    bool resident;
+    uint64_t* mbar;
+    cx<float>* red;
+    cx<float>* xs;
+    unsigned char* slots;
+    int buf = 0;
+    long long gw_next = 0;     // next wave to consume (all threads)
+    long long gw_issued = 0;   // next wave to copy (thread 0)
+    bool loaded = false;       // resident copy issued
+    // staging entries of this thread (when nX * K <= kStageRegs * blockDim.x):
+    // global offset Y*nc + b, FP16 block scale, flags (1: own entry, 2: b >= nc/2)
+    bool pre = false;
+    int st_o[kStageRegs];
+    float st_s[kStageRegs];
+    int st_f[kStageRegs];
+
+    __device__ CglsCta(const CglsArgs& args, unsigned char* sm) : a(args) {
+        nc = a.nc; K = 9 * nc; nvh = nc >> 1; RU = a.sh.ru; H = nc / RU;
+        const long long NU = (long long)a.g.Vc * H, G = gridDim.x;
+        u0 = (int)(blockIdx.x * NU / G);
+        u1 = (int)((blockIdx.x + 1) * NU / G);
+        nu = u1 - u0;
+        X0 = u0 / H;
+        nX = (u1 - 1) / H - X0 + 1;
+        resident = a.sh.resident != 0;
+        NG = resident ? 1 : a.sh.groups;
+        W = resident ? nu : a.sh.wave;
+        NW = (nu + W - 1) / W;
+        mbar = reinterpret_cast<uint64_t*>(sm);
+        red = reinterpret_cast<cx<float>*>(sm + 256);
+        xs = red + (resident ? 1 : 2) * a.sh.red_n;
+        slots = sm + a.sh.slot_off;
+        pre = nX * K <= kStageRegs * (int)blockDim.x;
+        if (pre) {
+#pragma unroll
+            for (int q = 0; q < kStageRegs; ++q) {
+                const int i = threadIdx.x + q * blockDim.x;
+                st_o[q] = -1;
+                st_s[q] = 1.f;
+                st_f[q] = 0;
+                if (i < nX * K) {
+                    const int xl = i / K, kk = i - xl * K, d = kk / nc, b = kk - d * nc, X = X0 + xl;
+                    st_o[q] = __ldg(a.nbr + (size_t)X * 9 + d) * nc + b;
+                    if (H16) st_s[q] = __ldg(a.su + (size_t)X * 9 + d);
+                    st_f[q] = ((d == 0 && owned(X, b)) ? 1 : 0) | (b >= nvh ? 2 : 0);
+                }
+            }
+        }
+    }
+    __device__ bool owned(int X, int b) const {
+        long long u = (long long)X * H + b / RU;
+        return u >= u0 && u < u1;
+    }
+    __device__ size_t unit_bytes() const { return (size_t)K * RU * UnitOp<H16>::bytes; }
+    // thread 0: copy the units of wave gw into its slot group
+    __device__ void issue(long long gw) {
+        const int grp = resident ? 0 : (int)(gw % NG);
+        const int iw = resident ? 0 : (int)(gw % NW);
+        const int j0 = iw * W, n = min(W, nu - j0);
+        const uint32_t ub = (uint32_t)unit_bytes();
+        mbar_expect_tx(mbar + grp, ub * (uint32_t)n);
+        const unsigned char* src = reinterpret_cast<const unsigned char*>(a.Au) + (size_t)(u0 + j0) * ub;
+        for (int j = 0; j < n; ++j)
+            bulk_copy_g2s(slots + (size_t)(grp * W + j) * a.sh.stride, src + (size_t)j * ub, ub, mbar + grp);
+    }
+    __device__ void start() {
+        if (threadIdx.x == 0) {
+            for (int i = 0; i < NG; ++i) mbar_init(mbar + i, 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (resident) {
+                issue(0);
+            } else {
+                for (int i = 0; i < NG; ++i) issue(i);
+            }
+        }
+        gw_issued = resident ? 1 : NG;
+        loaded = true;
+    }
+    // thread 0: wait for every copy still in flight (before the CTA may exit)
+    __device__ void drain() {
+        if (threadIdx.x != 0 || !loaded) return;
+        if (resident) {
+            mbar_wait(mbar, 0, kCopyWaitLimit);
+        } else {
+            for (long long g = gw_next; g < gw_issued; ++g) mbar_wait(mbar + g % NG, (uint32_t)((g / NG) & 1), kCopyWaitLimit);
+        }
+    }
+
+    // operand entry at global offset o, formed per STAGE (see phase); own: this
+    // CTA owns the entry and performs its vector updates
+    template <int STAGE> __device__ __forceinline__ cx<float> form(const CglsPhase& ph, int o, bool own, float& n1) {
+        cx<float> v;
+        if (STAGE == ST_IN) {
+            v = ld<float>(ph.in + o);
+        } else if (STAGE == ST_P) {
+            v = ld<float>(ph.s + o);
+            if (!ph.first) v = v + ph.coef * ld<float>(ph.p_old + o);
+            if (own) st<float>(ph.p_new + o, v);
+        } else {
+            v = ld<float>(ph.r_old + o) - ph.coef * ld<float>(ph.q + o);
+            if (own) {
+                st<float>(ph.r_new + o, v);
+                st<float>(ph.y + o, ld<float>(ph.y + o) + ph.coef * ld<float>(ph.p_new + o));
+                n1 += norm2(v);
+            }
+        }
+        return v;
+    }
+
+    // One stencil application out = D_c (or D_c^dag) x on the CTA's rows, the
+    // operand x formed while staging:
+    //   ST_IN: x = in
+    //   ST_P : x = s + beta p_old (first: s); own entries -> p_new
+    //   ST_R : x = r_old - alpha q; own entries -> r_new, y += alpha p_new, n1 += |x|^2
+    // n0 accumulates |out|^2 over the CTA's rows.
+    template <int STAGE, bool DAG> __device__ void phase(const CglsPhase& ph, float& n0, float& n1) {
+        const int T = blockDim.x;
+        if (pre) {
+            cx<float> v[kStageRegs];
+#pragma unroll
+            for (int q = 0; q < kStageRegs; ++q)
+                if (st_o[q] >= 0) v[q] = form<STAGE>(ph, st_o[q], (st_f[q] & 1) != 0, n1);
+#pragma unroll
+            for (int q = 0; q < kStageRegs; ++q)
+                if (st_o[q] >= 0) {
+                    cx<float> w = v[q];
+                    if (DAG && (st_f[q] & 2)) w = cx<float>(-w.r, -w.i);
+                    if (H16) w = st_s[q] * w;
+                    xs[threadIdx.x + q * T] = w;
+                }
+        } else {
+            for (int i = threadIdx.x; i < nX * K; i += T) {
+                const int xl = i / K, kk = i - xl * K, d = kk / nc, b = kk - d * nc;
+                const int X = X0 + xl;
+                const int o = __ldg(a.nbr + (size_t)X * 9 + d) * nc + b;
+                cx<float> w = form<STAGE>(ph, o, d == 0 && owned(X, b), n1);
+                if (DAG && b >= nvh) w = cx<float>(-w.r, -w.i);
+                if (H16) w = __ldg(a.su + (size_t)X * 9 + d) * w;
+                xs[i] = w;
+            }
+        }
+        __syncthreads();
+        const float2* xs2 = reinterpret_cast<const float2*>(xs);
+        for (int iw = 0; iw < NW; ++iw) {
+            const int j0 = iw * W, n = min(W, nu - j0), rows = n * RU, quads = rows >> 2;
+            const int grp = resident ? 0 : (int)(gw_next % NG);
+            const uint32_t par = resident ? 0u : (uint32_t)((gw_next / NG) & 1);
+            if (!mbar_wait(mbar + grp, par, kCopyWaitLimit)) atomicExch(a.err, 2);
+            const unsigned char* base = slots + (size_t)(resident ? j0 : grp * W) * a.sh.stride;
+            const int KS = max(1, T / quads);
+            cx<float>* rb = red + buf * a.sh.red_n;
+            for (int t = threadIdx.x; t < quads * KS; t += T) {
+                const int ks = t / quads, qd = t - ks * quads;
+                const int r = 4 * qd, j = r / RU, ain = r - j * RU;
+                const int xl = (u0 + j0 + j) / H - X0;
+                const OT* A = reinterpret_cast<const OT*>(base + (size_t)j * a.sh.stride) + ain;
+                const float2* xv = xs2 + (size_t)xl * K;
+                // P_r = sum (Re a x_r, Im a x_i), Q_r = sum (Re a x_i, Im a x_r):
+                // Re y_r = P.x - P.y, Im y_r = Q.x + Q.y (packed FP32 FMA)
+                float2 P[4], Q[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) { P[q] = make_float2(0.f, 0.f); Q[q] = make_float2(0.f, 0.f); }
+#pragma unroll 2
+                for (int k = ks; k < K; k += KS) {
+                    const float2 x = xv[k];
+                    const float2 xw = make_float2(x.y, x.x);
+                    float2 av[4];
+                    UnitOp<H16>::quad(A + (size_t)k * RU, av);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        P[q] = __ffma2_rn(av[q], x, P[q]);
+                        Q[q] = __ffma2_rn(av[q], xw, Q[q]);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) rb[ks * rows + r + q] = cx<float>(P[q].x - P[q].y, Q[q].x + Q[q].y);
+            }
+            __syncthreads();
+            if (!resident) {
+                ++gw_next;
+                if (threadIdx.x == 0) {
+                    fence_proxy_async();
+                    issue(gw_issued);
+                    ++gw_issued;
+                }
+            }
+            for (int r = threadIdx.x; r < rows; r += T) {
+                cx<float> sum = rb[r];
+                for (int ks = 1; ks < KS; ++ks) sum = sum + rb[ks * rows + r];
+                const int j = r / RU, ain = r - j * RU, u = u0 + j0 + j, X = u / H, row = (u - X * H) * RU + ain;
+                if (DAG && row >= nvh) sum = cx<float>(-sum.r, -sum.i);
+                st<float>(ph.out + (size_t)X * nc + row, sum);
+                n0 += norm2(sum);
+            }
+            if (!resident) buf ^= 1;
+        }
+    }
+};
+
+template <bool H16> __device__ void cgls_body(const CglsArgs& a, CglsCta<H16>& c, float* shr) {
+    unsigned int e = a.epoch0;   // one epoch per exchange
+    float2* rbuf[2] = {a.r, a.r1};
+    float2* pbuf[2] = {a.p, a.p1};
+    // y = 0, r = rc on the own rows; |rc|^2
+    float one[1] = {0.f};
+    for (int i = threadIdx.x; i < c.nu * c.RU; i += blockDim.x) {
+        const int j = i / c.RU, ain = i - j * c.RU, u = c.u0 + j, X = u / c.H;
+        const size_t o = (size_t)X * c.nc + (u - X * c.H) * c.RU + ain;
+        const float2 v = a.rc[o];
+        a.r[o] = v;
+        a.y[o] = make_float2(0.f, 0.f);
+        one[0] += v.x * v.x + v.y * v.y;
+    }
+    if (!xch_allreduce<1>(one, a.xch, e++, a.err, shr)) return;
+    const float rc2 = one[0];
+    int it = 0;
+    float r2 = rc2;
+    if (rc2 > 0.f && a.maxit > 0) {
+        CglsPhase ph{};
+        float n0 = 0.f, n1 = 0.f;
+        // s = D_c^dag r, gamma = |s|^2
+        ph.in = a.r;
+        ph.out = a.s;
+        c.template phase<ST_IN, true>(ph, n0, n1);
+        one[0] = n0;
+        if (!xch_allreduce<1>(one, a.xch, e++, a.err, shr)) return;
+        float gamma = one[0];
+        float beta = 0.f;
+        for (;;) {
+            const int b = it & 1;
+            ph = CglsPhase{};
+            ph.s = a.s; ph.p_old = pbuf[b ^ 1]; ph.p_new = pbuf[b]; ph.out = a.q;
+            ph.coef = beta; ph.first = (it == 0);
+            n0 = 0.f; n1 = 0.f;
+            c.template phase<ST_P, false>(ph, n0, n1);
+            one[0] = n0;
+            if (!xch_allreduce<1>(one, a.xch, e++, a.err, shr)) return;
+            const float qq = one[0];
+            if (!(qq > 0.f)) break;
+            const float alpha = gamma / qq;
+            ph = CglsPhase{};
+            ph.r_old = rbuf[b]; ph.q = a.q; ph.r_new = rbuf[b ^ 1]; ph.y = a.y; ph.p_new = pbuf[b];
+            ph.out = a.s; ph.coef = alpha;
+            n0 = 0.f; n1 = 0.f;
+            c.template phase<ST_R, true>(ph, n0, n1);
+            float two[2] = {n0, n1};
+            if (!xch_allreduce<2>(two, a.xch, e++, a.err, shr)) return;
+            const float gnew = two[0];
+            r2 = two[1];
+            ++it;
+            if (r2 <= a.tol2 * rc2 || it >= a.maxit) break;
+            beta = gnew / gamma;
+            gamma = gnew;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.scal[S_CG_ITERS] = (double)it;
+        a.scal[S_CG_R2] = (double)r2;
+        a.scal[S_CG_RC2] = (double)rc2;
+        a.scal[S_CG_DONE] = 1.0;
+        a.scal[S_CG_TOTAL] += (double)it;
+    }
+}
+
+template <bool H16> __global__ void __launch_bounds__(kCglsThreads, 1) k_cgls_onchip(CglsArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ float shr[33];
+    CglsCta<H16> c(a, smem_raw);
+    c.start();
+    cgls_body<H16>(a, c, shr);
+    c.drain();   // no copy may still be writing shared memory when the CTA exits
+}
+
+// ---------------------------------------------------------------- operator packing
+// Au[u = X*H + h][d][b][a - h*RU] from the FP64 operator A[X][d][b][a]; for
+// FP16 one scale per (X, d) block, su = max |Re|, |Im| over the block.
+template <bool H16> __global__ void k_pack_units(void* Au, float* su, const double2* __restrict__ A, int nc, int RU) {
+    __shared__ double sh[33];
+    const size_t blk = blockIdx.x, nn = (size_t)nc * nc;
+    const int X = (int)(blk / 9), d = (int)(blk % 9), H = nc / RU;
+    const double2* Ab = A + blk * nn;
+    double inv = 1.0;
+    if (H16) {
+        double mx = 0;
+        for (size_t i = threadIdx.x; i < nn; i += blockDim.x) mx = fmax(mx, fmax(fabs(Ab[i].x), fabs(Ab[i].y)));
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double m = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, sh[w]);
+            sh[32] = m > 0 ? m : 1.0;
+            su[blk] = (float)sh[32];
+        }
+        __syncthreads();
+        inv = 1.0 / (double)(float)sh[32];
+    }
+    for (size_t i = threadIdx.x; i < nn; i += blockDim.x) {
+        const int b = (int)(i / nc), arow = (int)(i % nc), h = arow / RU, ain = arow - h * RU;
+        const size_t dst = ((((size_t)X * H + h) * 9 + d) * nc + b) * RU + ain;
+        if (H16)
+            reinterpret_cast<__half2*>(Au)[dst] = __floats2half2_rn((float)(Ab[i].x * inv), (float)(Ab[i].y * inv));
+        else
+            reinterpret_cast<float2*>(Au)[dst] = make_float2((float)Ab[i].x, (float)Ab[i].y);
+    }
+}
+void coarse_pack_units(void* Au, float* su, const double2* A, int nc, int ru, int Vc, bool h16, cudaStream_t st) {
+    note_launch();
+    if (h16)
+        k_pack_units<true><<<Vc * 9, 256, 0, st>>>(Au, su, A, nc, ru);
+    else
+        k_pack_units<false><<<Vc * 9, 256, 0, st>>>(Au, su, A, nc, ru);
+}
+
+// ---------------------------------------------------------------- shape and launch
+namespace {
+struct DevLimits {
+    int sms = 0, smem = 0;
+};
+DevLimits dev_limits() {
+    static DevLimits cached[16];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    DevLimits& l = cached[dev & 15];
+    if (l.sms == 0) {
+        cudaDeviceGetAttribute(&l.sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&l.smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    }
+    return l;
+}
+size_t round_up(size_t x, size_t m) { return (x + m - 1) / m * m; }
+}  // namespace
+
+// Pick the rows per unit RU (a divisor of nc with RU * element bytes a
+// multiple of 16, RU >= 8 when nc allows) that minimises the rows of the
+// busiest CTA among the shapes whose units all stay resident (none: false,
+// the caller uses the register-streaming kernel).  With force_stream the
+// operator is streamed through two one-unit slot groups by
+// about a third as many CTAs as units (several waves per phase, so the ring
+// wraps within every phase), whatever the size.
+bool cgls_shape(int nc, int Vc, bool h16, bool force_stream, CglsShape* out) {
+    const DevLimits lim = dev_limits();
+    if (lim.sms <= 0 || lim.smem <= 2048 || nc < 2 || (nc & 1)) return false;
+    const size_t budget = (size_t)lim.smem - 1024;   // leave room for the kernel's static shared memory
+    const int esz = h16 ? 4 : 8;
+    bool found = false;
+    long long best = 0;
+    for (int ru = nc; ru >= 2; --ru) {
+        if (nc % ru || ru % 4 || (ru * esz) % 16 || (ru < 8 && ru != nc && nc >= 8)) continue;
+        CglsShape s{};
+        const int H = nc / ru;
+        const long long NU = (long long)Vc * H;
+        const int G = (int)std::min<long long>(lim.sms, NU);
+        s.ru = ru;
+        s.grid = G;
+        s.nu_max = (int)((NU + G - 1) / G);
+        s.nx_max = std::min(Vc, (s.nu_max - 1 + H - 1) / H + 1);
+        const size_t ub = (size_t)9 * nc * ru * esz;
+        s.stride = (int)(round_up(ub, 128) + (ru * esz) % 128);
+        const int T = kCglsThreads;
+        // resident: one wave of all units, one reduction buffer of (rows x row splits) <= 4T
+        s.red_n = std::max(4 * T, s.nu_max * ru);
+        size_t off = round_up(256 + (size_t)s.red_n * 8 + (size_t)s.nx_max * 9 * nc * 8, 128);
+        long long score;
+        if (force_stream) {
+            s.grid = (int)std::min<long long>(lim.sms, (NU + 2) / 3);
+            s.nu_max = (int)((NU + s.grid - 1) / s.grid);
+            s.nx_max = std::min(Vc, (s.nu_max - 1 + H - 1) / H + 1);
+            s.resident = 0;
+            s.red_n = std::max(4 * T, ru);   // two reduction buffers (consecutive waves)
+            off = round_up(256 + 2 * (size_t)s.red_n * 8 + (size_t)s.nx_max * 9 * nc * 8, 128);
+            if (off + 2 * (size_t)s.stride > budget) continue;
+            s.groups = 2;
+            s.wave = 1;
+            s.slots = 2;
+            score = (long long)s.nu_max * ru;
+        } else if (off + (size_t)s.nu_max * s.stride <= budget) {
+            s.resident = 1;
+            s.slots = s.nu_max;
+            s.wave = s.nu_max;
+            s.groups = 1;
+            score = (long long)s.nu_max * ru;
+        } else {
+            // the operator would have to stream by waves of a few units, each with a
+            // CTA barrier and reduction: measured slower than the register-streaming
+            // kernel, so that kernel is used instead
+            continue;
+        }
+        s.slot_off = (int)off;
+        s.smem = off + (size_t)s.slots * s.stride;
+        if (!found || score < best) {
+            *out = s;
+            best = score;
+            found = true;
+        }
+    }
+    return found;
+}
+
+cudaError_t cgls_onchip(const CglsArgs& args, cudaStream_t st) {
+    const bool h16 = args.su != nullptr;
+    const void* fn = h16 ? (const void*)k_cgls_onchip<true> : (const void*)k_cgls_onchip<false>;
+    static bool attr[2] = {false, false};
+    const DevLimits lim = dev_limits();
+    if (!attr[h16]) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lim.smem - 1024);
+        if (e != cudaSuccess) return e;
+        attr[h16] = true;
+    }
+    if (args.sh.smem > (size_t)lim.smem - 1024 || args.sh.grid <= 0 || args.sh.grid > lim.sms ||
+        args.sh.grid > kXchMaxGrid || 2 * args.sh.grid > kCglsThreads)
+        return cudaErrorInvalidValue;
+    int per = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kCglsThreads, args.sh.smem);
+    if (e != cudaSuccess) return e;
+    if (per < 1) return cudaErrorCooperativeLaunchTooLarge;
+    CglsArgs a = args;
+    void* params[] = {&a};
+    note_launch();
+    return cudaLaunchCooperativeKernel(fn, dim3(a.sh.grid), dim3(kCglsThreads), params, a.sh.smem, st);
+}
+
+}  // namespace wmg

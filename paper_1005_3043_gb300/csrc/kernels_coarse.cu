@@ -3,6 +3,7 @@
 // prolongation e = P y, the Galerkin coarse operator D_c = P^dag D P and its
 // nearest-neighbour application, and the CGNR (CGLS) coarse solve steps.
 #include "mg_launch.h"
+#include "mg_sync.cuh"
 
 namespace wmg {
 
@@ -584,67 +585,6 @@ void prolongator_to_boundary(double2* out, const double2* P, int nv, const Geom&
 // each CTA writes its partial sum, and after the barrier every CTA adds all
 // partials in the same order, so all CTAs take identical decisions.
 namespace wmg {
-
-constexpr long long kBarrierSpinLimit = 40000000LL;   // a few seconds of polls
-
-__device__ __forceinline__ bool grid_sync(unsigned int* count, unsigned int* gen, unsigned int G, int* err) {
-    __shared__ int s_fail;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        s_fail = 0;
-        volatile unsigned int* vgen = gen;
-        volatile int* verr = err;
-        unsigned int my = *vgen;
-        __threadfence();
-        if (atomicAdd(count, 1u) == G - 1) {
-            atomicExch(count, 0u);
-            __threadfence();
-            atomicAdd(gen, 1u);
-        } else {
-            long long spins = 0;
-            while (*vgen == my) {
-                if (*verr) { s_fail = 1; break; }
-                if (++spins > kBarrierSpinLimit) { atomicExch(err, 1); s_fail = 1; break; }
-                if (spins > 256) __nanosleep(32);
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return s_fail == 0;
-}
-
-template <typename T> __device__ __forceinline__ T warp_sum_t(T v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-// CTA sum in precision T (fixed order), valid in every thread
-template <typename T> __device__ __forceinline__ T block_sum_t(T v, T* sh) {
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    v = warp_sum_t(v);
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
-    if (warp == 0) {
-        T x = lane < nw ? sh[lane] : T(0);
-        x = warp_sum_t(x);
-        if (lane == 0) sh[32] = x;
-    }
-    __syncthreads();
-    T r = sh[32];
-    __syncthreads();
-    return r;
-}
-// sum of partials[c * 4 + slot] over c < G in a fixed order, broadcast to the CTA
-template <typename T> __device__ __forceinline__ T sum_partials(const double* partials, int slot, int G, T* sh) {
-    T a = 0;
-    for (int c = threadIdx.x; c < G; c += blockDim.x) a += (T)__ldcg(partials + (size_t)c * 4 + slot);
-    return block_sum_t<T>(a, sh);
-}
-template <typename T> __device__ __forceinline__ void write_partial(T v, double* partials, int slot, T* sh) {
-    T a = block_sum_t<T>(v, sh);
-    if (threadIdx.x == 0) partials[(size_t)blockIdx.x * 4 + slot] = (double)a;
-}
 
 // One CG phase on the aggregates of this CTA, `xpb` at a time: stage the
 // operand on X and its 8 neighbours in shared memory, then apply the coarse

@@ -36,6 +36,11 @@ struct CoarseLevel {
     __half2* A16 = nullptr;   // FP16 copy with per-block scales s16 (FP16-storage mode), built on demand
     float* s16 = nullptr;
     bool a16_valid = false;
+    void* Au = nullptr;       // operator in CGLS units (FP32 or FP16), built on demand
+    float* su = nullptr;      // FP16 unit scales [X][d]
+    size_t au_bytes = 0;
+    bool au_valid = false, au_h16 = false, au_forced = false;
+    CglsShape au_shape{};
     double mass = 0.0;
     bool valid = false;
 };
@@ -116,6 +121,8 @@ struct mg_ctx {
     int* d_status = nullptr;
     unsigned int* bar = nullptr;     // persistent-kernel barrier: count, generation, error flag
     int* cnbr = nullptr;             // coarse neighbour table [Vc][9]
+    unsigned long long* xch = nullptr;   // exchange slots of the on-chip coarse CGLS
+    unsigned int xch_epoch = 1;          // next free epoch
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<void*> allocs;
     // launch timer
@@ -299,6 +306,7 @@ int build_level(mg_ctx* ctx, CoarseLevel& L, const double2* V, int nv) {
     L.valid = true;
     L.emb_valid = false;
     L.a16_valid = false;
+    L.au_valid = false;
     return MG_OK;
 }
 
@@ -313,6 +321,33 @@ int ensure_a16(mg_ctx* ctx, CoarseLevel& L) {
     coarse_pack16(L.A16, L.s16, L.A64, L.nc, ctx->g.Vc, ctx->st);
     CKL();
     L.a16_valid = true;
+    return MG_OK;
+}
+
+// The operator in the unit layout of the on-chip CGLS kernel; false when no
+// shape fits this device (the register-streaming kernel is used instead).
+int ensure_units(mg_ctx* ctx, CoarseLevel& L, bool h16, bool force_stream, bool* ok) {
+    *ok = false;
+    if (L.au_valid && L.au_h16 == h16 && L.au_forced == force_stream) {
+        *ok = true;
+        return MG_OK;
+    }
+    CglsShape sh{};
+    if (!cgls_shape(L.nc, ctx->g.Vc, h16, force_stream, &sh)) return MG_OK;
+    const size_t bytes = (size_t)ctx->g.Vc * 9 * L.nc * L.nc * (h16 ? 4 : 8);
+    if (L.au_bytes < bytes) {
+        if (L.Au) { dfree(ctx, L.Au); L.Au = nullptr; L.au_bytes = 0; }
+        TRY(dalloc(ctx, &L.Au, bytes));
+        L.au_bytes = bytes;
+    }
+    if (h16 && !L.su) TRY(dalloc(ctx, &L.su, sizeof(float) * (size_t)ctx->g.Vc * 9));
+    coarse_pack_units(L.Au, h16 ? L.su : nullptr, L.A64, L.nc, sh.ru, ctx->g.Vc, h16, ctx->st);
+    CKL();
+    L.au_shape = sh;
+    L.au_h16 = h16;
+    L.au_forced = force_stream;
+    L.au_valid = true;
+    *ok = true;
     return MG_OK;
 }
 
@@ -337,16 +372,43 @@ int coarse_solve(mg_ctx* ctx, const CoarseLevel& L, const v2<T>* rc, v2<T>* y, d
     CgnrArgs<T> a = cgnr_args<T>(L, ctx->g, rc, y, w.cr, w.cr1, w.cs, w.cp, w.cp1, w.cq, tol, maxit, ctx->R.partials,
                                  ctx->bar, ctx->R.scal);
     a.nbr = ctx->cnbr;
-    if (std::is_same<T, float>::value && ctx->coarse16) {
+    bool onchip = false;
+    if (std::is_same<T, float>::value && ctx->prm.coarse_kernel != 1) {
+        CoarseLevel& Lm = const_cast<CoarseLevel&>(L);
+        TRY(ensure_units(ctx, Lm, ctx->coarse16, ctx->prm.coarse_kernel == 2, &onchip));
+    }
+    if (onchip) {
+        CglsArgs c{};
+        c.Au = L.Au; c.su = ctx->coarse16 ? L.su : nullptr; c.nbr = ctx->cnbr;
+        c.rc = (const float2*)a.rc; c.y = (float2*)a.y; c.r = (float2*)a.r; c.r1 = (float2*)a.r1;
+        c.s = (float2*)a.s; c.p = (float2*)a.p; c.p1 = (float2*)a.p1; c.q = (float2*)a.q;
+        c.nc = L.nc; c.g = ctx->g; c.tol2 = (float)(tol * tol); c.maxit = maxit;
+        c.scal = ctx->R.scal; c.err = (int*)(ctx->bar + 2);
+        c.sh = L.au_shape;
+        const unsigned long long reserve = 2ull * (unsigned long long)(maxit > 0 ? maxit : 0) + 4ull;
+        if ((unsigned long long)ctx->xch_epoch + reserve >= 0xFFFFFFFFull) {   // 32-bit epochs would wrap
+            CK(cudaMemsetAsync(ctx->xch, 0, sizeof(unsigned long long) * kXchWords, ctx->st));
+            ctx->xch_epoch = 1;
+        }
+        c.xch = ctx->xch;
+        c.epoch0 = ctx->xch_epoch;
+        ctx->xch_epoch += (unsigned int)reserve;
+        CK(cudaMemsetAsync(ctx->bar, 0, sizeof(unsigned int) * 3, ctx->st));
+        PROF_BEGIN(MG_K_COARSE_SOLVE);
+        CK(cgls_onchip(c, ctx->st));
+        PROF_END(MG_K_COARSE_SOLVE);
+    } else if (std::is_same<T, float>::value && ctx->coarse16) {
         CoarseLevel& Lm = const_cast<CoarseLevel&>(L);
         TRY(ensure_a16(ctx, Lm));
         a.A16 = Lm.A16;
         a.s16 = Lm.s16;
     }
-    CK(cudaMemsetAsync(ctx->bar, 0, sizeof(unsigned int) * 3, ctx->st));
-    PROF_BEGIN(MG_K_COARSE_SOLVE);
-    CK(cgnr_persistent<T>(a, ctx->st));
-    PROF_END(MG_K_COARSE_SOLVE);
+    if (!onchip) {
+        CK(cudaMemsetAsync(ctx->bar, 0, sizeof(unsigned int) * 3, ctx->st));
+        PROF_BEGIN(MG_K_COARSE_SOLVE);
+        CK(cgnr_persistent<T>(a, ctx->st));
+        PROF_END(MG_K_COARSE_SOLVE);
+    }
     if (iters) {
         TRY(read_scalars(ctx, S_CG_RC2, 3));
         unsigned int flags[3];
@@ -599,6 +661,7 @@ int check_params(const int dims[4], const mg_params* p, std::string& why) {
         return MG_ERR_INVALID_ARG;
     }
     if (p->prec_inner == MG_FP16 && p->nvec % 2 != 0) { why = "MG_FP16 needs an even nvec"; return MG_ERR_INVALID_ARG; }
+    if (p->coarse_kernel < 0 || p->coarse_kernel > 2) { why = "coarse_kernel must be 0, 1 or 2"; return MG_ERR_INVALID_ARG; }
     return MG_OK;
 }
 
@@ -775,7 +838,8 @@ int mg_create(const int dims[4], int t_antiperiodic, const mg_params* p, void* s
         (rc = dalloc(ctx, &ctx->R.ticket, sizeof(unsigned int) * 4)) ||
         (rc = dalloc(ctx, &ctx->R.scal, sizeof(double) * S_COUNT)) || (rc = dalloc(ctx, &ctx->d_status, sizeof(int))) ||
         (rc = dalloc(ctx, &ctx->bar, sizeof(unsigned int) * 4)) ||
-        (rc = dalloc(ctx, &ctx->cnbr, sizeof(int) * 9 * (size_t)g.Vc))) {
+        (rc = dalloc(ctx, &ctx->cnbr, sizeof(int) * 9 * (size_t)g.Vc)) ||
+        (rc = dalloc(ctx, &ctx->xch, sizeof(unsigned long long) * kXchWords))) {
         mg_destroy(ctx);
         return rc;
     }
@@ -784,6 +848,7 @@ int mg_create(const int dims[4], int t_antiperiodic, const mg_params* p, void* s
         cudaMemsetAsync(ctx->R.ticket, 0, sizeof(unsigned int) * 4, ctx->st) != cudaSuccess ||
         cudaMemsetAsync(ctx->R.scal, 0, sizeof(double) * S_COUNT, ctx->st) != cudaSuccess ||
         cudaMemsetAsync(ctx->bar, 0, sizeof(unsigned int) * 4, ctx->st) != cudaSuccess ||
+        cudaMemsetAsync(ctx->xch, 0, sizeof(unsigned long long) * kXchWords, ctx->st) != cudaSuccess ||
         (coarse_neighbour_table(ctx->cnbr, ctx->g, ctx->st), cudaGetLastError()) != cudaSuccess ||
         cudaStreamSynchronize(ctx->st) != cudaSuccess) {
         cudaGetLastError();
@@ -832,6 +897,7 @@ int mg_set_mass(mg_ctx* ctx, double m) {
         ctx->full.mass = m;
         ctx->full.emb_valid = false;
         ctx->full.a16_valid = false;
+        ctx->full.au_valid = false;
     }
     ctx->mass = m;
     CK(cudaStreamSynchronize(ctx->st));

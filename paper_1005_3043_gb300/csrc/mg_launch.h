@@ -131,6 +131,45 @@ template <typename T> struct CgnrArgs {
 };
 template <typename T> cudaError_t cgnr_persistent(const CgnrArgs<T>& args, cudaStream_t st);
 void coarse_neighbour_table(int* nbr, const Geom& g, cudaStream_t st);
+
+// Coarse CGLS with the operator on chip (kernels_cgls.cu).  The operator rows
+// of each aggregate are cut into units of `ru` rows, Au[X*H + h][d][b][a].
+struct CglsShape {
+    int ru;          // operator rows per unit (divides nc)
+    int grid;        // CTAs, at most one per SM
+    int nu_max;      // units of the busiest CTA
+    int nx_max;      // aggregates the units of one CTA can touch
+    int slots;       // unit slots in shared memory
+    int wave;        // units per wave
+    int groups;      // slot groups in flight (streamed mode)
+    int resident;    // 1: every CTA keeps all its units in shared memory
+    int stride;      // bytes between slots
+    int slot_off;    // byte offset of slot 0 in dynamic shared memory
+    int red_n;       // complex entries per reduction buffer
+    size_t smem;     // dynamic shared memory per CTA
+};
+struct CglsArgs {
+    const void* Au;        // float2 or __half2 units
+    const float* su;       // FP16 block scales [X][d]; nullptr selects the FP32 operator
+    const int* nbr;        // coarse neighbour table [Vc][9]
+    const float2* rc;
+    float2 *y, *r, *r1, *s, *p, *p1, *q;
+    int nc;
+    Geom g;
+    float tol2;
+    int maxit;
+    unsigned long long* xch;   // exchange slots [2][2][grid][16] (value, epoch), kXchWords words
+    unsigned int epoch0;       // first epoch of this launch; 2 * maxit + 4 are reserved
+    double* scal;
+    int* err;                  // error flag (zeroed before the launch)
+    CglsShape sh;
+};
+constexpr int kXchMaxGrid = 256;
+constexpr size_t kXchWords = 2 * 2 * kXchMaxGrid * 16;
+bool cgls_shape(int nc, int Vc, bool h16, bool force_stream, CglsShape* out);
+// Not for graph capture: every launch takes a fresh epoch range from the host.
+void coarse_pack_units(void* Au, float* su, const double2* A, int nc, int ru, int Vc, bool h16, cudaStream_t st);
+cudaError_t cgls_onchip(const CglsArgs& args, cudaStream_t st);
 // FP16 coarse operator with a per-(X, d) block scale, for the FP16-storage mode
 void coarse_pack16(__half2* A16, float* s16, const double2* A, int nc, int Vc, cudaStream_t st);
 

@@ -1,0 +1,144 @@
+// Grid-wide synchronisation and fixed-order reductions for persistent
+// cooperative kernels (all CTAs co-resident).
+//
+// grid_sync: counter + generation barrier with a bounded spin; a CTA that
+// gives up sets the error flag, and every waiting CTA returns as soon as it
+// sees the flag, so no launch can wait forever.
+// block_sum_t / write_partial / sum_partials: per-CTA partial sums written to
+// global memory before the barrier and summed after it by every CTA in the
+// same order, so all CTAs take identical decisions from identical values.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace wmg {
+
+constexpr long long kBarrierSpinLimit = 40000000LL;   // a few seconds of polls
+
+__device__ __forceinline__ bool grid_sync(unsigned int* count, unsigned int* gen, unsigned int G, int* err) {
+    __shared__ int s_fail;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        volatile unsigned int* vgen = gen;
+        volatile int* verr = err;
+        unsigned int my = *vgen;
+        __threadfence();
+        if (atomicAdd(count, 1u) == G - 1) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*vgen == my) {
+                if (*verr) { s_fail = 1; break; }
+                if (++spins > kBarrierSpinLimit) { atomicExch(err, 1); s_fail = 1; break; }
+                if (spins > 256) __nanosleep(32);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return s_fail == 0;
+}
+
+template <typename T> __device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+// CTA sum in precision T (fixed order), valid in every thread
+template <typename T> __device__ __forceinline__ T block_sum_t(T v, T* sh) {
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum_t(v);
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        T x = lane < nw ? sh[lane] : T(0);
+        x = warp_sum_t(x);
+        if (lane == 0) sh[32] = x;
+    }
+    __syncthreads();
+    T r = sh[32];
+    __syncthreads();
+    return r;
+}
+// sum of partials[c * 4 + slot] over c < G in a fixed order, broadcast to the CTA
+template <typename T> __device__ __forceinline__ T sum_partials(const double* partials, int slot, int G, T* sh) {
+    T a = 0;
+    for (int c = threadIdx.x; c < G; c += blockDim.x) a += (T)__ldcg(partials + (size_t)c * 4 + slot);
+    return block_sum_t<T>(a, sh);
+}
+template <typename T> __device__ __forceinline__ void write_partial(T v, double* partials, int slot, T* sh) {
+    T a = block_sum_t<T>(v, sh);
+    if (threadIdx.x == 0) partials[(size_t)blockIdx.x * 4 + slot] = (double)a;
+}
+
+
+// ---------------------------------------------------------------- epoch exchange
+// All-to-all exchange of per-CTA partial sums that is also the grid barrier:
+// CTA c publishes (value, epoch) as one 8-byte word in its slot (a release at
+// GPU scope by thread 0, after a CTA barrier, so every global write the CTA made
+// before is ordered before it), and every CTA waits, one thread per slot, until
+// all G slots carry the epoch (acquire), then sums the values in CTA order.
+// Slots are double-buffered by epoch parity: a CTA can be at most one exchange
+// ahead of the slowest one, so it never overwrites a word another CTA still
+// waits for.  Epochs increase across launches (the host reserves a range per
+// launch and clears the slots when the 32-bit counter would wrap).
+constexpr long long kExchangeSpinLimit = 40000000LL;   // a few seconds of polls
+
+__device__ __forceinline__ void xch_publish(unsigned long long* slot, float v, unsigned int e) {
+    const unsigned long long w = ((unsigned long long)e << 32) | __float_as_uint(v);
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(slot), "l"(w) : "memory");
+}
+__device__ __forceinline__ unsigned long long xch_load(const unsigned long long* slot) {
+    unsigned long long w;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(slot) : "memory");
+    return w;
+}
+// bounded wait until *slot carries epoch e; false on timeout or a raised error flag
+__device__ __forceinline__ bool xch_wait(const unsigned long long* slot, unsigned int e, int* err, float& v) {
+    long long spins = 0;
+    for (;;) {
+        const unsigned long long w = xch_load(slot);
+        if ((unsigned int)(w >> 32) == e) {
+            v = __uint_as_float((unsigned int)w);
+            return true;
+        }
+        if (*(volatile int*)err) return false;
+        if (++spins > kExchangeSpinLimit) {
+            atomicExch(err, 1);
+            return false;
+        }
+        if (spins > 32) __nanosleep(20);
+    }
+}
+// Each slot sits alone in a 128-byte line (kXchPad words): every slot is polled
+// by one thread of every CTA, and slots packed into a few lines made those lines
+// a hot spot (measured: 4.2 us from the last publish to the first CTA through,
+// 2.3 us with one slot per line).
+constexpr int kXchPad = 16;
+// v[j] (this thread's share) -> the grid-wide sums, identical in every CTA.
+// slots: [parity 2][value 2][G][kXchPad]; needs NV * G <= blockDim.x.
+template <int NV>
+__device__ bool xch_allreduce(float (&v)[NV], unsigned long long* slots, unsigned int e, int* err, float* sh) {
+    static_assert(NV >= 1 && NV <= 2, "one or two values per exchange");
+    const int G = gridDim.x, t = threadIdx.x;
+    unsigned long long* base = slots + (size_t)(e & 1) * 2 * G * kXchPad;
+    float cta[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) cta[j] = block_sum_t<float>(v[j], sh);
+    if (t == 0) {
+        __threadfence();
+#pragma unroll
+        for (int j = 0; j < NV; ++j) xch_publish(base + ((size_t)j * G + blockIdx.x) * kXchPad, cta[j], e);
+    }
+    float got = 0.f;
+    bool ok = true;
+    if (t < NV * G) ok = xch_wait(base + (size_t)t * kXchPad, e, err, got);
+    if (__syncthreads_or(!ok)) return false;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) v[j] = block_sum_t<float>((t >= j * G && t < (j + 1) * G) ? got : 0.f, sh);
+    return true;
+}
+
+}  // namespace wmg

@@ -285,7 +285,7 @@ def test_fp16_coarse_storage(c1):
         mg.set_links(U)
         mg.set_mass(m)
         mg.set_null_vectors(c1["Vs"])
-        A = mg.coarse_op()
+        A = c1["A"]                                  # the oracle's D_c of the same setup
         rc = synth.gaussian(mg.Vc * mg.nc, 41, 0).reshape(mg.Vc, mg.nc)
         y16, it16, rel16 = mg.coarse_solve(rc, 1e-3, 5000, wmg.MG_FP16)
         assert rel16 <= 1e-3
