@@ -76,9 +76,11 @@ typedef struct {
     double delta;          /* mixed precision: restart when ||r|| < delta * ||r at restart|| (0: off) */
     int prec_inner;        /* MG_FP64, MG_FP32 or MG_FP16: smoother, dslash, transfers, coarse solve, Krylov basis */
     int coarse_check;      /* coarse iterations between convergence checks read by the host */
-    int coarse_kernel;     /* FP32/FP16 coarse solve: 0 operator in shared memory, resident when it
-                              fits, else streamed through a bulk-copy ring (default); 1 operator
-                              read from global memory into registers; 2 the ring forced (tests) */
+    int coarse_kernel;     /* FP32/FP16 coarse solve: 0 (default) operator held on chip for the
+                              whole solve, in tensor memory when each SM's share fits, else in
+                              shared memory, else as 1; 1 operator read from global memory into
+                              registers every iteration; 2 operator streamed through a
+                              shared-memory ring (tests); 3 shared memory only (tests) */
 } mg_params;
 
 typedef struct {

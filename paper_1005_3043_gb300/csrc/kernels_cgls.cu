@@ -44,6 +44,10 @@ template <bool H16> struct UnitOp;
 template <> struct UnitOp<false> {
     using type = float2;
     static constexpr int bytes = 8;
+    static __device__ __forceinline__ void words(const uint32_t* w, float2 (&v)[4]) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = make_float2(__uint_as_float(w[2 * q]), __uint_as_float(w[2 * q + 1]));
+    }
     static __device__ __forceinline__ void quad(const float2* p, float2 (&v)[4]) {
         const float4 w0 = reinterpret_cast<const float4*>(p)[0];
         const float4 w1 = reinterpret_cast<const float4*>(p)[1];
@@ -56,6 +60,10 @@ template <> struct UnitOp<false> {
 template <> struct UnitOp<true> {
     using type = __half2;
     static constexpr int bytes = 4;
+    static __device__ __forceinline__ void words(const uint32_t* w, float2 (&v)[4]) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = __half22float2(*reinterpret_cast<const __half2*>(w + q));
+    }
     static __device__ __forceinline__ void quad(const __half2* p, float2 (&v)[4]) {
         const uint4 w = *reinterpret_cast<const uint4*>(p);
         v[0] = __half22float2(*reinterpret_cast<const __half2*>(&w.x));
@@ -83,8 +91,11 @@ enum { ST_IN = 0, ST_P = 1, ST_R = 2 };
 
 constexpr int kStageRegs = 4;   // staged operand entries per thread kept as precomputed offsets
 
-template <bool H16> struct CglsCta {
+template <bool H16, bool TM> struct CglsCta {
     using OT = typename UnitOp<H16>::type;
+    // words of one row quad of one column: FP16 4 x half2, FP32 4 x float2
+    static constexpr int kWpq = H16 ? 4 : 8;
+    static constexpr int kQpc = 32 / kWpq;   // quads per 32-column TMEM chunk
     const CglsArgs& a;
     int nc, K, nvh, RU, H, u0, u1, nu, X0, nX;
     int W, NG, NW;
@@ -100,6 +111,11 @@ template <bool H16> struct CglsCta {
     // staging entries of this thread (when nX * K <= kStageRegs * blockDim.x):
     // global offset Y*nc + b, FP16 block scale, flags (1: own entry, 2: b >= nc/2)
     bool pre = false;
+    // TMEM-resident operator (TM): this thread's quad qd and column split ks
+    // (k = ks, ks + KS, ...), its TMEM lane/column base and the CTA-wide chunk count
+    int q_ks = 0, q_qd = 0, q_KS = 1, q_quads = 0, q_nch = 0;
+    bool q_act = false;
+    uint32_t q_taddr = 0, tm_base = 0;
     int st_o[kStageRegs];
     float st_s[kStageRegs];
     int st_f[kStageRegs];
@@ -154,6 +170,10 @@ template <bool H16> struct CglsCta {
             bulk_copy_g2s(slots + (size_t)(grp * W + j) * a.sh.stride, src + (size_t)j * ub, ub, mbar + grp);
     }
     __device__ void start() {
+        if (TM) {
+            start_tmem();
+            return;
+        }
         if (threadIdx.x == 0) {
             for (int i = 0; i < NG; ++i) mbar_init(mbar + i, 1);
             fence_mbar_init();
@@ -169,8 +189,58 @@ template <bool H16> struct CglsCta {
         gw_issued = resident ? 1 : NG;
         loaded = true;
     }
-    // thread 0: wait for every copy still in flight (before the CTA may exit)
+    // TM: allocate all 512 TMEM columns (one CTA per SM) and copy this thread's
+    // share of the operator into its lane: thread (warp w, lane l) owns lane
+    // 32 (w % 4) + l, columns 128 (w / 4) .. +127
+    __device__ void start_tmem() {
+        __shared__ uint32_t s_taddr;
+        const int warp = threadIdx.x >> 5, T = blockDim.x;
+        if (warp == 0) {
+            tmem_alloc(&s_taddr, 512);
+            tmem_relinquish();
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        const uint32_t base = s_taddr;
+        tm_base = base;
+        q_quads = (nu * RU) >> 2;
+        q_KS = max(1, T / q_quads);
+        q_act = (int)threadIdx.x < q_quads * q_KS;
+        q_ks = threadIdx.x / q_quads;
+        q_qd = threadIdx.x - q_ks * q_quads;
+        q_nch = ((K + q_KS - 1) / q_KS + kQpc - 1) / kQpc;   // chunks of the thread with ks = 0
+        q_taddr = base + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(128 * (warp >> 2));
+        const int r = 4 * q_qd, j = r / RU, ain = r - j * RU;
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(
+            reinterpret_cast<const unsigned char*>(a.Au) + (size_t)(u0 + j) * unit_bytes()) + (size_t)ain * (kWpq / 4);
+        for (int c = 0; c < q_nch; ++c) {
+            uint32_t w[32];
+#pragma unroll
+            for (int i = 0; i < kQpc; ++i) {
+                const int k = q_ks + (c * kQpc + i) * q_KS;
+                const bool ok = q_act && k < K;
+#pragma unroll
+                for (int v = 0; v < kWpq; ++v) w[i * kWpq + v] = ok ? __ldg(src + (size_t)k * RU * (kWpq / 4) + v) : 0u;
+            }
+            tmem_st32(q_taddr + 32 * c, w);
+        }
+        tmem_wait_st();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        loaded = true;
+    }
+    // thread 0: wait for every copy still in flight (before the CTA may exit);
+    // TM: release the tensor memory
     __device__ void drain() {
+        if (TM) {
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            if ((threadIdx.x >> 5) == 0) tmem_dealloc(tm_base, 512);
+            return;
+        }
         if (threadIdx.x != 0 || !loaded) return;
         if (resident) {
             mbar_wait(mbar, 0, kCopyWaitLimit);
@@ -234,6 +304,48 @@ template <bool H16> struct CglsCta {
         }
         __syncthreads();
         const float2* xs2 = reinterpret_cast<const float2*>(xs);
+        if (TM) {
+            const int rows = nu * RU;
+            const int r = 4 * q_qd, j = r / RU;
+            const float2* xv = xs2 + (size_t)((u0 + j) / H - X0) * K;
+            float2 P[4], Q[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) { P[q] = make_float2(0.f, 0.f); Q[q] = make_float2(0.f, 0.f); }
+            for (int c = 0; c < q_nch; ++c) {
+                uint32_t w[32];
+                tmem_ld32(q_taddr + 32 * c, w);
+                if (q_act) {
+#pragma unroll
+                    for (int i = 0; i < kQpc; ++i) {
+                        const int k = q_ks + (c * kQpc + i) * q_KS;
+                        if (k < K) {
+                            const float2 x = xv[k];
+                            const float2 xw = make_float2(x.y, x.x);
+                            float2 av[4];
+                            UnitOp<H16>::words(w + i * kWpq, av);
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                P[q] = __ffma2_rn(av[q], x, P[q]);
+                                Q[q] = __ffma2_rn(av[q], xw, Q[q]);
+                            }
+                        }
+                    }
+                }
+            }
+            if (q_act)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) red[q_ks * rows + r + q] = cx<float>(P[q].x - P[q].y, Q[q].x + Q[q].y);
+            __syncthreads();
+            for (int rr = threadIdx.x; rr < rows; rr += T) {
+                cx<float> sum = red[rr];
+                for (int ks = 1; ks < q_KS; ++ks) sum = sum + red[ks * rows + rr];
+                const int jj = rr / RU, ain = rr - jj * RU, u = u0 + jj, X = u / H, row = (u - X * H) * RU + ain;
+                if (DAG && row >= nvh) sum = cx<float>(-sum.r, -sum.i);
+                st<float>(ph.out + (size_t)X * nc + row, sum);
+                n0 += norm2(sum);
+            }
+            return;
+        }
         for (int iw = 0; iw < NW; ++iw) {
             const int j0 = iw * W, n = min(W, nu - j0), rows = n * RU, quads = rows >> 2;
             const int grp = resident ? 0 : (int)(gw_next % NG);
@@ -290,7 +402,7 @@ template <bool H16> struct CglsCta {
     }
 };
 
-template <bool H16> __device__ void cgls_body(const CglsArgs& a, CglsCta<H16>& c, float* shr) {
+template <bool H16, bool TM> __device__ void cgls_body(const CglsArgs& a, CglsCta<H16, TM>& c, float* shr) {
     unsigned int e = a.epoch0;   // one epoch per exchange
     float2* rbuf[2] = {a.r, a.r1};
     float2* pbuf[2] = {a.p, a.p1};
@@ -355,13 +467,13 @@ template <bool H16> __device__ void cgls_body(const CglsArgs& a, CglsCta<H16>& c
     }
 }
 
-template <bool H16> __global__ void __launch_bounds__(kCglsThreads, 1) k_cgls_onchip(CglsArgs a) {
+template <bool H16, bool TM> __global__ void __launch_bounds__(kCglsThreads, 1) k_cgls_onchip(CglsArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ float shr[33];
-    CglsCta<H16> c(a, smem_raw);
+    CglsCta<H16, TM> c(a, smem_raw);
     c.start();
-    cgls_body<H16>(a, c, shr);
-    c.drain();   // no copy may still be writing shared memory when the CTA exits
+    cgls_body<H16, TM>(a, c, shr);
+    c.drain();   // no copy may still be writing shared memory, and no TMEM stays allocated, when the CTA exits
 }
 
 // ---------------------------------------------------------------- operator packing
@@ -424,24 +536,26 @@ DevLimits dev_limits() {
 size_t round_up(size_t x, size_t m) { return (x + m - 1) / m * m; }
 }  // namespace
 
-// Pick the rows per unit RU (a divisor of nc with RU * element bytes a
-// multiple of 16, RU >= 8 when nc allows) that minimises the rows of the
-// busiest CTA among the shapes whose units all stay resident (none: false,
-// the caller uses the register-streaming kernel).  With force_stream the
-// operator is streamed through two one-unit slot groups by
-// about a third as many CTAs as units (several waves per phase, so the ring
-// wraps within every phase), whatever the size.
-bool cgls_shape(int nc, int Vc, bool h16, bool force_stream, CglsShape* out) {
+// Pick the rows per unit RU (a divisor of nc, a multiple of 4, with RU * element
+// bytes a multiple of 16, RU >= 8 when nc allows) that minimises the rows of
+// the busiest CTA.  mode CGLS_AUTO: the operator in tensor memory when every
+// thread's share fits its 128 columns, else in shared memory when a CTA's units
+// fit there (none: false, the caller uses the register-streaming kernel);
+// CGLS_SMEM: shared memory only; CGLS_STREAM: streamed through two one-unit
+// slot groups by about a third as many CTAs as units (several waves per phase,
+// so the ring wraps within every phase), whatever the size.
+bool cgls_shape(int nc, int Vc, bool h16, int mode, CglsShape* out) {
     const DevLimits lim = dev_limits();
-    if (lim.sms <= 0 || lim.smem <= 2048 || nc < 2 || (nc & 1)) return false;
+    if (lim.sms <= 0 || lim.smem <= 2048 || nc < 4 || (nc & 1)) return false;
     const size_t budget = (size_t)lim.smem - 1024;   // leave room for the kernel's static shared memory
-    const int esz = h16 ? 4 : 8;
+    const int esz = h16 ? 4 : 8, T = kCglsThreads;
+    const int qpc = h16 ? 8 : 4;                     // row quads per 32-column TMEM chunk
     bool found = false;
     long long best = 0;
-    for (int ru = nc; ru >= 2; --ru) {
+    for (int ru = nc; ru >= 4; --ru) {
         if (nc % ru || ru % 4 || (ru * esz) % 16 || (ru < 8 && ru != nc && nc >= 8)) continue;
         CglsShape s{};
-        const int H = nc / ru;
+        const int H = nc / ru, K = 9 * nc;
         const long long NU = (long long)Vc * H;
         const int G = (int)std::min<long long>(lim.sms, NU);
         s.ru = ru;
@@ -450,12 +564,14 @@ bool cgls_shape(int nc, int Vc, bool h16, bool force_stream, CglsShape* out) {
         s.nx_max = std::min(Vc, (s.nu_max - 1 + H - 1) / H + 1);
         const size_t ub = (size_t)9 * nc * ru * esz;
         s.stride = (int)(round_up(ub, 128) + (ru * esz) % 128);
-        const int T = kCglsThreads;
-        // resident: one wave of all units, one reduction buffer of (rows x row splits) <= 4T
+        // one reduction buffer of (rows x row splits) <= 4T entries
         s.red_n = std::max(4 * T, s.nu_max * ru);
         size_t off = round_up(256 + (size_t)s.red_n * 8 + (size_t)s.nx_max * 9 * nc * 8, 128);
         long long score;
-        if (force_stream) {
+        const int quads = s.nu_max * ru / 4;
+        const int ks_min = quads <= T ? T / quads : 0;
+        const int chunks = ks_min ? (((K + ks_min - 1) / ks_min) + qpc - 1) / qpc : 1 << 20;
+        if (mode == CGLS_STREAM) {
             s.grid = (int)std::min<long long>(lim.sms, (NU + 2) / 3);
             s.nu_max = (int)((NU + s.grid - 1) / s.grid);
             s.nx_max = std::min(Vc, (s.nu_max - 1 + H - 1) / H + 1);
@@ -467,12 +583,24 @@ bool cgls_shape(int nc, int Vc, bool h16, bool force_stream, CglsShape* out) {
             s.wave = 1;
             s.slots = 2;
             score = (long long)s.nu_max * ru;
+        } else if (mode == CGLS_AUTO && chunks <= 4 && off <= budget) {
+            // the operator in tensor memory; shared memory padded past half an SM so
+            // that no second CTA (and no second TMEM allocation) shares the SM
+            s.tm = 1;
+            s.tm_chunks = chunks;
+            s.resident = 1;
+            s.slots = 0;
+            s.wave = s.nu_max;
+            s.groups = 1;
+            off = std::max(off, (size_t)lim.smem / 2 + 4096);
+            if (off > budget) continue;
+            score = (long long)s.nu_max * ru;
         } else if (off + (size_t)s.nu_max * s.stride <= budget) {
             s.resident = 1;
             s.slots = s.nu_max;
             s.wave = s.nu_max;
             s.groups = 1;
-            score = (long long)s.nu_max * ru;
+            score = (long long)s.nu_max * ru + (mode == CGLS_AUTO ? (1LL << 40) : 0);   // TMEM shapes first
         } else {
             // the operator would have to stream by waves of a few units, each with a
             // CTA barrier and reduction: measured slower than the register-streaming
@@ -491,14 +619,16 @@ bool cgls_shape(int nc, int Vc, bool h16, bool force_stream, CglsShape* out) {
 }
 
 cudaError_t cgls_onchip(const CglsArgs& args, cudaStream_t st) {
-    const bool h16 = args.su != nullptr;
-    const void* fn = h16 ? (const void*)k_cgls_onchip<true> : (const void*)k_cgls_onchip<false>;
-    static bool attr[2] = {false, false};
+    const bool h16 = args.su != nullptr, tm = args.sh.tm != 0;
+    const void* fns[2][2] = {{(const void*)k_cgls_onchip<false, false>, (const void*)k_cgls_onchip<false, true>},
+                             {(const void*)k_cgls_onchip<true, false>, (const void*)k_cgls_onchip<true, true>}};
+    const void* fn = fns[h16][tm];
+    static bool attr[2][2] = {{false, false}, {false, false}};
     const DevLimits lim = dev_limits();
-    if (!attr[h16]) {
+    if (!attr[h16][tm]) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lim.smem - 1024);
         if (e != cudaSuccess) return e;
-        attr[h16] = true;
+        attr[h16][tm] = true;
     }
     if (args.sh.smem > (size_t)lim.smem - 1024 || args.sh.grid <= 0 || args.sh.grid > lim.sms ||
         args.sh.grid > kXchMaxGrid || 2 * args.sh.grid > kCglsThreads)
@@ -507,6 +637,7 @@ cudaError_t cgls_onchip(const CglsArgs& args, cudaStream_t st) {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kCglsThreads, args.sh.smem);
     if (e != cudaSuccess) return e;
     if (per < 1) return cudaErrorCooperativeLaunchTooLarge;
+    if (tm && per > 1) return cudaErrorInvalidValue;   // two CTAs on an SM would both ask for all of its TMEM
     CglsArgs a = args;
     void* params[] = {&a};
     note_launch();

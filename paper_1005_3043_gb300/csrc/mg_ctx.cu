@@ -39,7 +39,8 @@ struct CoarseLevel {
     void* Au = nullptr;       // operator in CGLS units (FP32 or FP16), built on demand
     float* su = nullptr;      // FP16 unit scales [X][d]
     size_t au_bytes = 0;
-    bool au_valid = false, au_h16 = false, au_forced = false;
+    bool au_valid = false, au_h16 = false;
+    int au_mode = 0;
     CglsShape au_shape{};
     double mass = 0.0;
     bool valid = false;
@@ -326,14 +327,14 @@ int ensure_a16(mg_ctx* ctx, CoarseLevel& L) {
 
 // The operator in the unit layout of the on-chip CGLS kernel; false when no
 // shape fits this device (the register-streaming kernel is used instead).
-int ensure_units(mg_ctx* ctx, CoarseLevel& L, bool h16, bool force_stream, bool* ok) {
+int ensure_units(mg_ctx* ctx, CoarseLevel& L, bool h16, int mode, bool* ok) {
     *ok = false;
-    if (L.au_valid && L.au_h16 == h16 && L.au_forced == force_stream) {
+    if (L.au_valid && L.au_h16 == h16 && L.au_mode == mode) {
         *ok = true;
         return MG_OK;
     }
     CglsShape sh{};
-    if (!cgls_shape(L.nc, ctx->g.Vc, h16, force_stream, &sh)) return MG_OK;
+    if (!cgls_shape(L.nc, ctx->g.Vc, h16, mode, &sh)) return MG_OK;
     const size_t bytes = (size_t)ctx->g.Vc * 9 * L.nc * L.nc * (h16 ? 4 : 8);
     if (L.au_bytes < bytes) {
         if (L.Au) { dfree(ctx, L.Au); L.Au = nullptr; L.au_bytes = 0; }
@@ -345,7 +346,7 @@ int ensure_units(mg_ctx* ctx, CoarseLevel& L, bool h16, bool force_stream, bool*
     CKL();
     L.au_shape = sh;
     L.au_h16 = h16;
-    L.au_forced = force_stream;
+    L.au_mode = mode;
     L.au_valid = true;
     *ok = true;
     return MG_OK;
@@ -375,7 +376,8 @@ int coarse_solve(mg_ctx* ctx, const CoarseLevel& L, const v2<T>* rc, v2<T>* y, d
     bool onchip = false;
     if (std::is_same<T, float>::value && ctx->prm.coarse_kernel != 1) {
         CoarseLevel& Lm = const_cast<CoarseLevel&>(L);
-        TRY(ensure_units(ctx, Lm, ctx->coarse16, ctx->prm.coarse_kernel == 2, &onchip));
+        const int mode = ctx->prm.coarse_kernel == 2 ? CGLS_STREAM : ctx->prm.coarse_kernel == 3 ? CGLS_SMEM : CGLS_AUTO;
+        TRY(ensure_units(ctx, Lm, ctx->coarse16, mode, &onchip));
     }
     if (onchip) {
         CglsArgs c{};
@@ -661,7 +663,7 @@ int check_params(const int dims[4], const mg_params* p, std::string& why) {
         return MG_ERR_INVALID_ARG;
     }
     if (p->prec_inner == MG_FP16 && p->nvec % 2 != 0) { why = "MG_FP16 needs an even nvec"; return MG_ERR_INVALID_ARG; }
-    if (p->coarse_kernel < 0 || p->coarse_kernel > 2) { why = "coarse_kernel must be 0, 1 or 2"; return MG_ERR_INVALID_ARG; }
+    if (p->coarse_kernel < 0 || p->coarse_kernel > 3) { why = "coarse_kernel must be 0, 1, 2 or 3"; return MG_ERR_INVALID_ARG; }
     return MG_OK;
 }
 

@@ -146,8 +146,11 @@ struct CglsShape {
     int stride;      // bytes between slots
     int slot_off;    // byte offset of slot 0 in dynamic shared memory
     int red_n;       // complex entries per reduction buffer
+    int tm;          // 1: the operator in tensor memory (all 512 columns of the SM)
+    int tm_chunks;   // 32-column TMEM chunks per thread
     size_t smem;     // dynamic shared memory per CTA
 };
+enum { CGLS_AUTO = 0, CGLS_STREAM = 2, CGLS_SMEM = 3 };
 struct CglsArgs {
     const void* Au;        // float2 or __half2 units
     const float* su;       // FP16 block scales [X][d]; nullptr selects the FP32 operator
@@ -166,7 +169,7 @@ struct CglsArgs {
 };
 constexpr int kXchMaxGrid = 256;
 constexpr size_t kXchWords = 2 * 2 * kXchMaxGrid * 16;
-bool cgls_shape(int nc, int Vc, bool h16, bool force_stream, CglsShape* out);
+bool cgls_shape(int nc, int Vc, bool h16, int mode, CglsShape* out);
 // Not for graph capture: every launch takes a fresh epoch range from the host.
 void coarse_pack_units(void* Au, float* su, const double2* A, int nc, int ru, int Vc, bool h16, cudaStream_t st);
 cudaError_t cgls_onchip(const CglsArgs& args, cudaStream_t st);

@@ -1,8 +1,9 @@
 """Coarse CGNR (Sec. IV: CG on the normal equations of D_c) on the GPU in FP32
 and with the FP16-stored operator, for each coarse kernel: 0 the operator held
-in shared memory (resident when it fits, else streamed through a bulk-copy
-ring), 1 the operator read from global memory into registers, 2 the ring
-forced with several waves per phase.  References are the FP64 oracle's CGLS on
+on chip for the whole solve (tensor memory at these sizes), 1 the operator
+read from global memory into registers, 2 the operator streamed through a
+shared-memory ring with several waves per phase, 3 the operator resident in
+shared memory.  References are the FP64 oracle's CGLS on
 the oracle's own D_c (FP32) or on that D_c rounded to FP16 with one scale per
 (aggregate, direction) block, the storage rule of the FP16 mode."""
 import numpy as np
@@ -15,7 +16,7 @@ from tests._fields import c1_workload
 
 pytestmark = pytest.mark.gpu
 
-KERNELS = (0, 1, 2)
+KERNELS = (0, 1, 2, 3)
 # FP32 CG iterates against FP64 after k steps on this operator (condition
 # number ~14): near FP32 rounding for the first steps (1.7e-7 at k = 1 and 7
 # for a complex64 CGLS in numpy), then growing with the loss of conjugacy
