@@ -223,6 +223,13 @@ int mg_vcycle(mg_ctx* ctx, const double* r, double* z, int prec);
  * at minimum (algorithmic: links + input + output, each read/written once). */
 int mg_time_dslash(mg_ctx* ctx, int prec, int reps, double* ms_per_launch, double* bytes_per_launch);
 
+/* As mg_time_dslash, with the L2 cache flushed before every launch: the
+ * caller's device buffer `flush` (flush_bytes, larger than the L2) is
+ * overwritten on the context stream between launches, and only the dslash
+ * launches are timed (one event pair each). */
+int mg_time_dslash_cold(mg_ctx* ctx, int prec, int reps, void* flush, size_t flush_bytes, double* ms_per_launch,
+                        double* bytes_per_launch);
+
 /* Kernel classes for the launch timer below. */
 enum mg_kernel_class {
     MG_K_DSLASH = 0,       /* fine Wilson operator, all variants and precisions */
@@ -248,6 +255,14 @@ int mg_profile_read(mg_ctx* ctx, double* ms, int* launches, double* coarse_iters
 /* Number of kernel launches this library has issued in the process so far
  * (all contexts); the difference over a region counts its launches. */
 long long mg_kernel_launches(void);
+
+/* Which coarse CGNR kernel the last coarse solve of this context ran (a
+ * diagnostic; no counterpart in the paper): MG_CK_REGISTER operator read from
+ * global memory every iteration, MG_CK_SMEM operator resident in shared
+ * memory, MG_CK_STREAM operator streamed through a shared-memory ring,
+ * MG_CK_TMEM operator resident in tensor memory; MG_CK_NONE before any. */
+enum mg_coarse_kernel_id { MG_CK_NONE = -1, MG_CK_REGISTER = 0, MG_CK_SMEM = 1, MG_CK_STREAM = 2, MG_CK_TMEM = 3 };
+int mg_coarse_kernel(mg_ctx* ctx);
 
 const char* mg_status_string(int status);
 const char* mg_last_error(const mg_ctx* ctx);

@@ -90,9 +90,11 @@ _SIGS = {
     "mg_coarse_solve_noalloc": ([_P, _P, _P, _D, _I, _P, _P], _I),
     "mg_vcycle": ([_P, _P, _P, _I], _I),
     "mg_time_dslash": ([_P, _I, _I, _P, _P], _I),
+    "mg_time_dslash_cold": ([_P, _I, _I, _P, ctypes.c_size_t, _P, _P], _I),
     "mg_profile_enable": ([_P, _I], _I),
     "mg_profile_read": ([_P, _P, _P, _P], _I),
     "mg_kernel_launches": ([], ctypes.c_longlong),
+    "mg_coarse_kernel": ([ctypes.c_void_p], ctypes.c_int),
     "mg_status_string": ([_I], ctypes.c_char_p),
     "mg_last_error": ([_P], ctypes.c_char_p),
 }
@@ -329,12 +331,31 @@ def mg_time_dslash(ctx, prec: int = MG_FP32, reps: int = 50):
     return ms.value, nbytes.value
 
 
+def mg_time_dslash_cold(ctx, flush_ptr: int, flush_bytes: int, prec: int = MG_FP32, reps: int = 20):
+    """Mean dslash time with the L2 flushed (a device buffer of flush_bytes overwritten) before each launch."""
+    ms = ctypes.c_double(0)
+    nbytes = ctypes.c_double(0)
+    _check(load().mg_time_dslash_cold(ctx, int(prec), int(reps), ctypes.c_void_p(flush_ptr), ctypes.c_size_t(flush_bytes),
+                                      ctypes.byref(ms), ctypes.byref(nbytes)), ctx)
+    return ms.value, nbytes.value
+
+
 KERNEL_CLASSES = ("dslash", "coarse_solve", "restrict", "prolong", "block_ortho", "coarse_build", "krylov",
                   "true_residual")
 
 
 def mg_kernel_launches() -> int:
     return int(load().mg_kernel_launches())
+
+
+COARSE_KERNELS = {-1: "none", 0: "k_cgnr_persistent (operator from global memory)",
+                  1: "k_cgls_onchip (operator resident in shared memory)",
+                  2: "k_cgls_onchip (operator streamed through shared memory)",
+                  3: "k_cgls_onchip (operator resident in tensor memory)"}
+
+
+def mg_coarse_kernel(ctx) -> int:
+    return int(load().mg_coarse_kernel(ctx))
 
 
 def mg_profile_enable(ctx, on: bool = True) -> None:
@@ -452,3 +473,10 @@ class WilsonMG:
 
     def time_dslash(self, prec=MG_FP32, reps=50):
         return mg_time_dslash(self.ctx, prec, reps)
+
+    def time_dslash_cold(self, flush_ptr: int, flush_bytes: int, prec=MG_FP32, reps=20):
+        return mg_time_dslash_cold(self.ctx, flush_ptr, flush_bytes, prec, reps)
+
+    def coarse_kernel(self) -> int:
+        """MG_CK_* id of the coarse CGNR kernel the last coarse solve ran."""
+        return mg_coarse_kernel(self.ctx)

@@ -124,6 +124,7 @@ struct mg_ctx {
     int* cnbr = nullptr;             // coarse neighbour table [Vc][9]
     unsigned long long* xch = nullptr;   // exchange slots of the on-chip coarse CGLS
     unsigned int xch_epoch = 1;          // next free epoch
+    int coarse_kernel_used = MG_CK_NONE;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<void*> allocs;
     // launch timer
@@ -399,6 +400,7 @@ int coarse_solve(mg_ctx* ctx, const CoarseLevel& L, const v2<T>* rc, v2<T>* y, d
         PROF_BEGIN(MG_K_COARSE_SOLVE);
         CK(cgls_onchip(c, ctx->st));
         PROF_END(MG_K_COARSE_SOLVE);
+        ctx->coarse_kernel_used = c.sh.tm ? MG_CK_TMEM : c.sh.resident ? MG_CK_SMEM : MG_CK_STREAM;
     } else if (std::is_same<T, float>::value && ctx->coarse16) {
         CoarseLevel& Lm = const_cast<CoarseLevel&>(L);
         TRY(ensure_a16(ctx, Lm));
@@ -410,6 +412,7 @@ int coarse_solve(mg_ctx* ctx, const CoarseLevel& L, const v2<T>* rc, v2<T>* y, d
         PROF_BEGIN(MG_K_COARSE_SOLVE);
         CK(cgnr_persistent<T>(a, ctx->st));
         PROF_END(MG_K_COARSE_SOLVE);
+        ctx->coarse_kernel_used = MG_CK_REGISTER;
     }
     if (iters) {
         TRY(read_scalars(ctx, S_CG_RC2, 3));
@@ -1089,6 +1092,39 @@ int mg_time_dslash(mg_ctx* ctx, int prec, int reps, double* ms_per_launch, doubl
     return prec != MG_FP64 ? run(float{}) : run(double{});
 }
 
+int mg_time_dslash_cold(mg_ctx* ctx, int prec, int reps, void* flush, size_t flush_bytes, double* ms_per_launch,
+                        double* bytes_per_launch) {
+    TRY(need_links(ctx));
+    if (reps <= 0 || !ms_per_launch || !flush || flush_bytes == 0) return MG_ERR_INVALID_ARG;
+    size_t real = prec != MG_FP64 ? 4 : 8;
+    if (bytes_per_launch) *bytes_per_launch = (double)ctx->g.V * (72 + 24 + 24) * real;
+    auto run = [&](auto tag) -> int {
+        using T = decltype(tag);
+        TRY(ensure_work<T>(ctx));
+        Work<T>& w = work<T>(ctx);
+        const v2<T>* U = links<T>(ctx);
+        for (int i = 0; i < 3; ++i)
+            dslash<T>(DS_PLAIN, w.tout, w.tin, U, w.tin, ctx->g, ctx->mass, 0.0, 0, ctx->R, ctx->st);
+        double total = 0;
+        for (int i = 0; i < reps; ++i) {
+            // overwrite a buffer larger than L2 so that links and spinors come from HBM
+            CK(cudaMemsetAsync(flush, i & 0xff, flush_bytes, ctx->st));
+            CK(cudaEventRecord(ctx->ev0, ctx->st));
+            dslash<T>(DS_PLAIN, (i & 1) ? w.tin : w.tout, (i & 1) ? w.tout : w.tin, U, w.tin, ctx->g, ctx->mass, 0.0, 0,
+                      ctx->R, ctx->st);
+            CK(cudaEventRecord(ctx->ev1, ctx->st));
+            CKL();
+            CK(cudaEventSynchronize(ctx->ev1));
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+            total += ms;
+        }
+        *ms_per_launch = total / reps;
+        return MG_OK;
+    };
+    return prec != MG_FP64 ? run(float{}) : run(double{});
+}
+
 int mg_profile_enable(mg_ctx* ctx, int on) {
     if (!ctx) return MG_ERR_INVALID_ARG;
     ctx->prof = on != 0;
@@ -1113,6 +1149,7 @@ int mg_profile_read(mg_ctx* ctx, double* ms, int* launches, double* coarse_iters
 }
 
 long long mg_kernel_launches(void) { return launch_counter().load(std::memory_order_relaxed); }
+int mg_coarse_kernel(mg_ctx* ctx) { return ctx ? ctx->coarse_kernel_used : MG_CK_NONE; }
 
 const char* mg_status_string(int status) {
     int i = -status;

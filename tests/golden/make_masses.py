@@ -46,9 +46,12 @@ if __name__ == "__main__":
     U = synth.gauge_field(w["L"], beta=6.0, sweeps=200, n_or=4, seed=w["seed"])
     t = time.time()
     big = oracle.volume(w["L"]) > 100000
-    # on large lattices the left edge of the spectrum is dense: a looser Ritz
-    # tolerance (relative 1e-4, i.e. about 1e-4 on Re lambda_min) keeps ARPACK affordable
-    lam, ev = re_lambda_min(w["L"], U, k=4 if big else 6, ncv=40 if big else 60, tol=1e-4 if big else 1e-9)
+    # on large lattices the left edge of the spectrum is dense and ARPACK
+    # stagnates when asked for several converged pairs: ask for the leftmost
+    # pair only, with a larger Krylov space and a residual tolerance of 1e-3
+    # relative (the eigenvalue error is far below the residual for the real,
+    # isolated edge modes found on the smaller lattice)
+    lam, ev = re_lambda_min(w["L"], U, k=2 if big else 6, ncv=80 if big else 60, tol=1e-3 if big else 1e-9)
     out = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"{name}_mass.txt")
     with open(out, "w") as f:
         f.write(f"# {name}: L={w['L']} beta=6.0 sweeps=200 n_or=4 seed={w['seed']}\n")
