@@ -54,9 +54,13 @@ enum mg_status {
 };
 
 /* Inner precision of the preconditioner and Krylov basis (the solution and
- * the true residual are always FP64).  MG_FP16: FP32 arithmetic with the
- * coarse operator of the CGNR coarse solve stored in FP16 with one scale per
- * (aggregate, direction) block (needs an even nvec). */
+ * the true residual are always FP64).  MG_FP16: FP32 arithmetic with FP16
+ * storage of the coarse operator of the CGNR coarse solve (one scale per
+ * (aggregate, direction) block; needs an even nvec), of the links of the
+ * smoother's Wilson operator (no scale: |U_ij| <= 1) and of the smoother's
+ * residual and D-residual spinors (one FP32 scale per site, the site's
+ * largest |re|, |im|) as selected by mg_params.smoother_fp16; the Krylov
+ * basis, restriction and prolongation stay FP32. */
 enum mg_precision { MG_FP64 = 0, MG_FP32 = 1, MG_FP16 = 2 };
 
 /* Solver parameters (paper, Sec. III-IV; defaults from mg_default_params). */
@@ -81,6 +85,9 @@ typedef struct {
                               shared memory, else as 1; 1 operator read from global memory into
                               registers every iteration; 2 operator streamed through a
                               shared-memory ring (tests); 3 shared memory only (tests) */
+    int smoother_fp16;     /* MG_FP16 only, storage of the smoother's spinors and links: 0 (default)
+                              FP16 when the FP32 smoother working set (links + 3 spinors, 576 B per
+                              site) exceeds the device L2, else FP32; 1 always FP16; 2 never */
 } mg_params;
 
 typedef struct {
@@ -95,7 +102,8 @@ typedef struct {
 
 /* Fill p with the defaults: block 4^4, nvec 8, relax 10, iters 3, group 4,
  * smoother 4, omega 0.9, restart 16, tol 1e-10, coarse_tol 1e-3,
- * max_outer 1000, max_coarse 5000, delta 0, FP64, coarse_check 16, coarse_kernel 0. */
+ * max_outer 1000, max_coarse 5000, delta 0, FP64, coarse_check 16, coarse_kernel 0,
+ * smoother_fp16 0. */
 int mg_default_params(mg_params* p);
 
 /* Create a context for an L0 x L1 x L2 x L3 lattice.  dims[mu] must be a
@@ -171,7 +179,8 @@ int mg_apply_coarse_batched(mg_ctx* ctx, const double* x, double* y, int nrhs, i
 /* ---- single steps of the method (host buffers, FP64 at the boundary; the
  * ---- kernel runs in precision prec) -------------------------------------- */
 
-/* out = D in, eq. (2). */
+/* out = D in, eq. (2).  MG_FP16: in rounded to FP16 with a per-site scale,
+ * FP16 links, out rounded likewise (the smoother's storage). */
 int mg_apply_dslash(mg_ctx* ctx, const double* in, double* out, int prec);
 
 /* r_c = P^dag r (eq. 8 with R = P^dag, chirality kept). */
@@ -184,7 +193,8 @@ int mg_prolong(mg_ctx* ctx, const double* yc, double* e, int prec);
 int mg_apply_coarse(mg_ctx* ctx, const double* x, double* y, int dagger, int prec);
 
 /* nsteps MR smoothing steps on (e, r): q = D r, alpha = omega <q,r>/<q,q>,
- * e += alpha r, r -= alpha q.  e and r are read and overwritten. */
+ * e += alpha r, r -= alpha q.  e and r are read and overwritten.  MG_FP16:
+ * r and q stored in FP16 with a per-site scale, FP16 links, e in FP32. */
 int mg_mr(mg_ctx* ctx, double* e, double* r, int nsteps, int prec);
 
 /* Coarse solve y = CGNR(D_c, rc) from y = 0 to ||rc - D_c y|| <= tol ||rc||

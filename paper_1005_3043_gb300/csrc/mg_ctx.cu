@@ -133,7 +133,11 @@ struct mg_ctx {
     size_t ev_used = 0;
     std::vector<int> ev_class;      // class of each (start, stop) pair
     double coarse_mark = 0.0;       // S_CG_TOTAL at the last profile read
-    bool coarse16 = false;          // coarse CGNR reads the FP16 operator
+    bool coarse16 = false;          // MG_FP16 mode: FP16 coarse operator and FP16 fine smoother storage
+    uint2* U16 = nullptr;           // FP16 links (built on demand from U32)
+    bool u16_valid = false;
+    uint2 *h_r = nullptr, *h_q = nullptr;     // FP16 smoother vectors r, q (+ per-site scales)
+    float *h_sr = nullptr, *h_sq = nullptr;
 };
 
 namespace {
@@ -439,6 +443,83 @@ struct Counters {
     int matvecs = 0;
 };
 
+// FP16 links and the FP16 smoother vectors (MG_FP16 mode), built on first use
+int ensure_fine16(mg_ctx* ctx) {
+    const size_t V = (size_t)ctx->g.V;
+    if (!ctx->U16) {
+        TRY(dalloc(ctx, &ctx->U16, sizeof(uint2) * 20 * V));
+        TRY(dalloc(ctx, &ctx->h_r, sizeof(uint2) * 6 * V));
+        TRY(dalloc(ctx, &ctx->h_q, sizeof(uint2) * 6 * V));
+        TRY(dalloc(ctx, &ctx->h_sr, sizeof(float) * V));
+        TRY(dalloc(ctx, &ctx->h_sq, sizeof(float) * V));
+    }
+    if (!ctx->u16_valid) {
+        links_to_half(ctx->U16, ctx->U32, ctx->g, ctx->st);
+        CKL();
+        ctx->u16_valid = true;
+    }
+    return MG_OK;
+}
+
+// MG_FP16: whether the smoother stores its spinors and links in FP16.  Its
+// dslash is limited by dependent load rounds more than by bytes, so FP16 pays
+// only when the FP32 working set would not stay in L2 (measured: 24^3x64
+// 103 -> 90 us per dslash with L2 flushed; 16^3x32, L2-resident in a solve,
+// 14.7 -> 16.4 us).
+bool smoother_fp16(mg_ctx* ctx) {
+    if (!ctx->coarse16 || ctx->prm.smoother_fp16 == 2) return false;
+    if (ctx->prm.smoother_fp16 == 1) return true;
+    int dev = 0, l2 = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+    return (double)ctx->g.V * 576.0 > (double)l2;
+}
+
+// Post-smoothing of the V(0,n) cycle (Sec. III): r_s = r - D z, then n MR steps
+// q = D r_s, alpha = omega <q,r_s>/<q,q>, z += alpha r_s, r_s -= alpha q.  In
+// MG_FP16 mode r_s and q are stored in FP16 with a per-site scale and the
+// links in FP16 (FP32 arithmetic); z stays in the path's precision.
+template <typename T>
+int smooth(mg_ctx* ctx, const v2<T>* r, v2<T>* z, const Reduce& R, Counters& cnt) {
+    Work<T>& w = work<T>(ctx);
+    const size_t n = nfine(ctx);
+    const int steps = ctx->prm.smoother_steps;
+    if (std::is_same<T, float>::value && smoother_fp16(ctx)) {
+        TRY(ensure_fine16(ctx));
+        HalfSpinor hr{ctx->h_r, ctx->h_sr}, hq{ctx->h_q, ctx->h_sq};
+        float2* zf = reinterpret_cast<float2*>(z);
+        PROF_BEGIN(MG_K_DSLASH);
+        dslash_h_xmy(hr, zf, ctx->U16, reinterpret_cast<const float2*>(r), ctx->g, ctx->mass, ctx->st);
+        PROF_END(MG_K_DSLASH);
+        cnt.matvecs += 1;
+        for (int k = 0; k < steps; ++k) {
+            PROF_BEGIN(MG_K_DSLASH);
+            dslash_h_mrdot(hq, hr, ctx->U16, ctx->g, ctx->mass, ctx->prm.omega, R, ctx->st);
+            PROF_END(MG_K_DSLASH);
+            PROF_BEGIN(MG_K_KRYLOV);
+            mr_update_h(zf, hr, hq, ctx->g, k + 1 < steps, R, ctx->st);
+            PROF_END(MG_K_KRYLOV);
+            cnt.matvecs += 1;
+        }
+        return MG_OK;
+    }
+    const v2<T>* U = links<T>(ctx);
+    PROF_BEGIN(MG_K_DSLASH);
+    dslash<T>(DS_XMY, w.vr, z, U, r, ctx->g, ctx->mass, 0.0, 0, R, ctx->st);
+    PROF_END(MG_K_DSLASH);
+    cnt.matvecs += 1;
+    for (int k = 0; k < steps; ++k) {
+        PROF_BEGIN(MG_K_DSLASH);
+        dslash<T>(DS_MRDOT, w.vq, w.vr, U, w.vr, ctx->g, ctx->mass, ctx->prm.omega, 0, R, ctx->st);
+        PROF_END(MG_K_DSLASH);
+        PROF_BEGIN(MG_K_KRYLOV);
+        mr_update<T>(z, w.vr, w.vq, n, k + 1 < steps, R, ctx->st);
+        PROF_END(MG_K_KRYLOV);
+        cnt.matvecs += 1;
+    }
+    return MG_OK;
+}
+
 template <typename T>
 int vcycle(mg_ctx* ctx, const CoarseLevel& L, const v2<T>* r, v2<T>* z, Counters& cnt) {
     Work<T>& w = work<T>(ctx);
@@ -452,20 +533,7 @@ int vcycle(mg_ctx* ctx, const CoarseLevel& L, const v2<T>* r, v2<T>* z, Counters
     PROF_BEGIN(MG_K_PROLONG);
     prolong<T>(z, lvlP<T>(L), w.cy, L.nv, ctx->g, ctx->st);
     PROF_END(MG_K_PROLONG);
-    PROF_BEGIN(MG_K_DSLASH);
-    dslash<T>(DS_XMY, w.vr, z, U, r, ctx->g, ctx->mass, 0.0, 0, ctx->R, ctx->st);
-    PROF_END(MG_K_DSLASH);
-    cnt.matvecs += 1;
-    int steps = ctx->prm.smoother_steps;
-    for (int k = 0; k < steps; ++k) {
-        PROF_BEGIN(MG_K_DSLASH);
-        dslash<T>(DS_MRDOT, w.vq, w.vr, U, w.vr, ctx->g, ctx->mass, ctx->prm.omega, 0, ctx->R, ctx->st);
-        PROF_END(MG_K_DSLASH);
-        PROF_BEGIN(MG_K_KRYLOV);
-        mr_update<T>(z, w.vr, w.vq, n, k + 1 < steps, ctx->R, ctx->st);
-        PROF_END(MG_K_KRYLOV);
-        cnt.matvecs += 1;
-    }
+    TRY(smooth<T>(ctx, r, z, ctx->R, cnt));
     CKL();
     return MG_OK;
 }
@@ -667,6 +735,7 @@ int check_params(const int dims[4], const mg_params* p, std::string& why) {
     }
     if (p->prec_inner == MG_FP16 && p->nvec % 2 != 0) { why = "MG_FP16 needs an even nvec"; return MG_ERR_INVALID_ARG; }
     if (p->coarse_kernel < 0 || p->coarse_kernel > 3) { why = "coarse_kernel must be 0, 1, 2 or 3"; return MG_ERR_INVALID_ARG; }
+    if (p->smoother_fp16 < 0 || p->smoother_fp16 > 2) { why = "smoother_fp16 must be 0, 1 or 2"; return MG_ERR_INVALID_ARG; }
     return MG_OK;
 }
 
@@ -713,7 +782,18 @@ template <typename T> int hook_dslash(mg_ctx* ctx, const double* in, double* out
     TRY(ensure_work<T>(ctx));
     Work<T>& w = work<T>(ctx);
     TRY(upload_fine<T>(ctx, in, w.tin));
-    dslash<T>(DS_PLAIN, w.tout, w.tin, links<T>(ctx), w.tin, ctx->g, ctx->mass, 0.0, 0, ctx->R, ctx->st);
+    if (std::is_same<T, float>::value && ctx->coarse16) {
+        // MG_FP16 (the hook always uses the FP16 storage, whatever smoother_fp16
+        // selects for solves): the input rounded to FP16 with its site scale, FP16 links,
+        // the output rounded likewise (then widened for the caller)
+        TRY(ensure_fine16(ctx));
+        HalfSpinor hr{ctx->h_r, ctx->h_sr}, hq{ctx->h_q, ctx->h_sq};
+        to_half(hr, reinterpret_cast<const float2*>(w.tin), ctx->g, ctx->st);
+        dslash_h_plain(hq, hr, ctx->U16, ctx->g, ctx->mass, ctx->st);
+        from_half(reinterpret_cast<float2*>(w.tout), hq, ctx->g, ctx->st);
+    } else {
+        dslash<T>(DS_PLAIN, w.tout, w.tin, links<T>(ctx), w.tin, ctx->g, ctx->mass, 0.0, 0, ctx->R, ctx->st);
+    }
     CKL();
     return download_fine<T>(ctx, w.tout, out);
 }
@@ -749,9 +829,21 @@ template <typename T> int hook_mr(mg_ctx* ctx, double* e, double* r, int nsteps)
     TRY(upload_fine<T>(ctx, e, w.tin));
     TRY(upload_fine<T>(ctx, r, w.tout));
     const v2<T>* U = links<T>(ctx);
-    for (int k = 0; k < nsteps; ++k) {
-        dslash<T>(DS_MRDOT, w.vq, w.tout, U, w.tout, ctx->g, ctx->mass, ctx->prm.omega, 0, ctx->R, ctx->st);
-        mr_update<T>(w.tin, w.tout, w.vq, n, true, ctx->R, ctx->st);
+    if (std::is_same<T, float>::value && ctx->coarse16) {
+        // MG_FP16 (always FP16 storage here): r and q in FP16, e in FP32
+        TRY(ensure_fine16(ctx));
+        HalfSpinor hr{ctx->h_r, ctx->h_sr}, hq{ctx->h_q, ctx->h_sq};
+        to_half(hr, reinterpret_cast<const float2*>(w.tout), ctx->g, ctx->st);
+        for (int k = 0; k < nsteps; ++k) {
+            dslash_h_mrdot(hq, hr, ctx->U16, ctx->g, ctx->mass, ctx->prm.omega, ctx->R, ctx->st);
+            mr_update_h(reinterpret_cast<float2*>(w.tin), hr, hq, ctx->g, true, ctx->R, ctx->st);
+        }
+        from_half(reinterpret_cast<float2*>(w.tout), hr, ctx->g, ctx->st);
+    } else {
+        for (int k = 0; k < nsteps; ++k) {
+            dslash<T>(DS_MRDOT, w.vq, w.tout, U, w.tout, ctx->g, ctx->mass, ctx->prm.omega, 0, ctx->R, ctx->st);
+            mr_update<T>(w.tin, w.tout, w.vq, n, true, ctx->R, ctx->st);
+        }
     }
     CKL();
     TRY(download_fine<T>(ctx, w.tin, e));
@@ -889,6 +981,7 @@ int mg_set_links(mg_ctx* ctx, const double* U) {
     CKL();
     CK(cudaStreamSynchronize(ctx->st));
     ctx->has_links = true;
+    ctx->u16_valid = false;
     ctx->full.valid = false;   // D_c depends on the links
     return MG_OK;
 }
@@ -1064,9 +1157,50 @@ int mg_vcycle(mg_ctx* ctx, const double* r, double* z, int prec) {
     return prec != MG_FP64 ? hook_vcycle<float>(ctx, r, z) : hook_vcycle<double>(ctx, r, z);
 }
 
+// FP16-storage dslash for the timers: out = D in on the smoother's FP16 buffers
+static int time_dslash_h(mg_ctx* ctx, int reps, void* flush, size_t flush_bytes, double* ms_per_launch) {
+    TRY(ensure_work<float>(ctx));
+    TRY(ensure_fine16(ctx));
+    HalfSpinor a{ctx->h_r, ctx->h_sr}, b{ctx->h_q, ctx->h_sq};
+    to_half(a, reinterpret_cast<const float2*>(work<float>(ctx).tin), ctx->g, ctx->st);
+    for (int i = 0; i < 3; ++i) dslash_h_plain(b, a, ctx->U16, ctx->g, ctx->mass, ctx->st);
+    double total = 0;
+    if (!flush) CK(cudaEventRecord(ctx->ev0, ctx->st));
+    for (int i = 0; i < reps; ++i) {
+        if (flush) {
+            CK(cudaMemsetAsync(flush, i & 0xff, flush_bytes, ctx->st));
+            CK(cudaEventRecord(ctx->ev0, ctx->st));
+        }
+        dslash_h_plain((i & 1) ? a : b, (i & 1) ? ConstHalfSpinor(b) : ConstHalfSpinor(a), ctx->U16, ctx->g, ctx->mass,
+                       ctx->st);
+        if (flush) {
+            CK(cudaEventRecord(ctx->ev1, ctx->st));
+            CK(cudaEventSynchronize(ctx->ev1));
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+            total += ms;
+        }
+    }
+    if (!flush) {
+        CK(cudaEventRecord(ctx->ev1, ctx->st));
+        CK(cudaEventSynchronize(ctx->ev1));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+        total = ms;
+    }
+    CKL();
+    *ms_per_launch = total / reps;
+    return MG_OK;
+}
+
 int mg_time_dslash(mg_ctx* ctx, int prec, int reps, double* ms_per_launch, double* bytes_per_launch) {
     TRY(need_links(ctx));
     if (reps <= 0 || !ms_per_launch) return MG_ERR_INVALID_ARG;
+    if (prec == MG_FP16) {
+        // links 4 x 5 pair words + input and output 12 half2 + one FP32 scale each per site
+        if (bytes_per_launch) *bytes_per_launch = (double)ctx->g.V * (160 + 52 + 52);
+        return time_dslash_h(ctx, reps, nullptr, 0, ms_per_launch);
+    }
     size_t real = prec != MG_FP64 ? 4 : 8;
     // algorithmic minimum: 4 links x 18 reals + input 24 reals + output 24 reals per site
     if (bytes_per_launch) *bytes_per_launch = (double)ctx->g.V * (72 + 24 + 24) * real;
@@ -1096,6 +1230,10 @@ int mg_time_dslash_cold(mg_ctx* ctx, int prec, int reps, void* flush, size_t flu
                         double* bytes_per_launch) {
     TRY(need_links(ctx));
     if (reps <= 0 || !ms_per_launch || !flush || flush_bytes == 0) return MG_ERR_INVALID_ARG;
+    if (prec == MG_FP16) {
+        if (bytes_per_launch) *bytes_per_launch = (double)ctx->g.V * (160 + 52 + 52);
+        return time_dslash_h(ctx, reps, flush, flush_bytes, ms_per_launch);
+    }
     size_t real = prec != MG_FP64 ? 4 : 8;
     if (bytes_per_launch) *bytes_per_launch = (double)ctx->g.V * (72 + 24 + 24) * real;
     auto run = [&](auto tag) -> int {
@@ -1437,16 +1575,9 @@ int solve_batched_impl(mg_ctx* ctx, int nrhs, mg_solve_info* infos) {
                 PROF_BEGIN(MG_K_PROLONG);
                 prolong<float>(zk, L.P32, b.yB, L.nv, ctx->g, ctx->st, b.npad, r);
                 PROF_END(MG_K_PROLONG);
-                PROF_BEGIN(MG_K_DSLASH);
-                dslash<float>(DS_XMY, w.vr, zk, U, b.r32 + r * n, ctx->g, ctx->mass, 0.0, 0, Rr, ctx->st);
-                PROF_END(MG_K_DSLASH);
-                for (int s = 0; s < p.smoother_steps; ++s) {
-                    PROF_BEGIN(MG_K_DSLASH);
-                    dslash<float>(DS_MRDOT, w.vq, w.vr, U, w.vr, ctx->g, ctx->mass, p.omega, 0, Rr, ctx->st);
-                    PROF_END(MG_K_DSLASH);
-                    PROF_BEGIN(MG_K_KRYLOV);
-                    mr_update<float>(zk, w.vr, w.vq, n, s + 1 < p.smoother_steps, Rr, ctx->st);
-                    PROF_END(MG_K_KRYLOV);
+                {
+                    Counters scnt;
+                    TRY(smooth<float>(ctx, b.r32 + r * n, zk, Rr, scnt));
                 }
                 PROF_BEGIN(MG_K_DSLASH);
                 dslash<float>(DS_PLAIN, Pr + (size_t)kk[r] * n, zk, U, zk, ctx->g, ctx->mass, 0.0, 0, Rr, ctx->st);

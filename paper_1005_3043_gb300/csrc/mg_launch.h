@@ -132,6 +132,32 @@ template <typename T> struct CgnrArgs {
 template <typename T> cudaError_t cgnr_persistent(const CgnrArgs<T>& args, cudaStream_t st);
 void coarse_neighbour_table(int* nbr, const Geom& g, cudaStream_t st);
 
+// FP16 storage of fine spinors (kernels_half.cu): v[X][6][l] holds components
+// (2j, 2j+1) as two __half2 (value / s[X][l]); FP16 links U16[mu][X][5][l]
+struct HalfSpinor {
+    uint2* v;
+    float* s;
+};
+struct ConstHalfSpinor {
+    const uint2* v;
+    const float* s;
+    ConstHalfSpinor(const uint2* v_, const float* s_) : v(v_), s(s_) {}
+    ConstHalfSpinor(HalfSpinor h) : v(h.v), s(h.s) {}
+};
+void links_to_half(uint2* U16, const float2* U32, const Geom& g, cudaStream_t st);
+void to_half(HalfSpinor h, const float2* x, const Geom& g, cudaStream_t st);
+void from_half(float2* x, ConstHalfSpinor h, const Geom& g, cudaStream_t st);
+void dslash_h_plain(HalfSpinor out, ConstHalfSpinor in, const uint2* U16, const Geom& g, double mass, cudaStream_t st);
+// out = src - D in (in FP32)
+void dslash_h_xmy(HalfSpinor out, const float2* in, const uint2* U16, const float2* src, const Geom& g, double mass,
+                  cudaStream_t st);
+// out = D in, scal[S_MR_ALPHA..+1] = omega <out, in> / |out|^2 of the stored out
+void dslash_h_mrdot(HalfSpinor out, ConstHalfSpinor in, const uint2* U16, const Geom& g, double mass, double omega,
+                    const Reduce& R, cudaStream_t st);
+// e += alpha r; r -= alpha q when update_r (alpha from scal[S_MR_ALPHA])
+void mr_update_h(float2* e, HalfSpinor r, ConstHalfSpinor q, const Geom& g, bool update_r, const Reduce& R,
+                 cudaStream_t st);
+
 // Coarse CGLS with the operator on chip (kernels_cgls.cu).  The operator rows
 // of each aggregate are cut into units of `ru` rows, Au[X*H + h][d][b][a].
 struct CglsShape {

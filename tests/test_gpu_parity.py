@@ -295,3 +295,44 @@ def test_fp16_coarse_storage(c1):
         x, info = mg.solve(b)
     assert info["status"] == 0
     assert _true_rel(U, x, b, m, L) <= 1e-10
+
+
+def test_fp16_fine_storage_dslash_and_mr():
+    """MG_FP16 smoother storage: spinors in FP16 with one FP32 scale per site and
+    FP16 links.  The oracle error of a single application is at the FP16
+    rounding level (2^-11 relative per stored entry, a few entries per output);
+    the bound 4e-3 is reported, not a parity claim; MR steps reduce the residual
+    as in FP64 to the same precision."""
+    L = (8, 4, 4, 8)
+    U = rough_gauge(L, seed=4)
+    m, w = -0.3, 0.9
+    psi = synth.gaussian_spinor(L, 17)
+    ref = oracle.dslash(U, psi, m, L)
+    e = synth.gaussian_spinor(L, 1)
+    r = synth.gaussian_spinor(L, 2)
+    e_ref, r_ref = oracle.mr(U, e, r, m, L, 4, w)
+    with wmg.WilsonMG(L, make_params(2, (4, 4, 4, 4))) as mg:
+        mg.set_links(U)
+        mg.set_mass(m)
+        err = maxrel(mg.dslash(psi, wmg.MG_FP16), ref)
+        assert 1e-5 < err < 4e-3, err             # FP16-rounded, but close
+        e16, r16 = mg.mr(e, r, 4, wmg.MG_FP16)
+    assert maxrel(e16, e_ref) < 1e-2 and maxrel(r16, r_ref) < 1e-2
+    # the residual it returns is the residual of the e it returns (to FP16 storage)
+    r_true = r + oracle.dslash(U, e, m, L) - oracle.dslash(U, e16, m, L)
+    assert maxrel(r16, r_true) < 1e-2
+
+
+@pytest.mark.parametrize("smoother_fp16", [1, 2])
+def test_fp16_mode_solve_with_each_smoother_storage(c1, smoother_fp16):
+    """MG_FP16 solves with the smoother's spinors and links in FP16 (1) or FP32 (2)
+    both reach a true FP64 residual of 1e-10."""
+    L, B, nv, U, m = c1["L"], c1["B"], c1["nv"], c1["U"], c1["m"]
+    b = synth.gaussian_spinor(L, 7)
+    with wmg.WilsonMG(L, make_params(nv, B, prec_inner=wmg.MG_FP16, delta=1e-4, smoother_fp16=smoother_fp16)) as mg:
+        mg.set_links(U)
+        mg.set_mass(m)
+        mg.set_null_vectors(c1["Vs"])
+        x, info = mg.solve(b)
+    assert info["status"] == 0
+    assert _true_rel(U, x, b, m, L) <= 1e-10
