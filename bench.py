@@ -123,7 +123,7 @@ def mg_params(w, prec):
         p.block[i] = w.block[i]
     p.nvec = w.nvec
     p.setup_group = 4          # Sec. IV: 10 relaxations, then groups of 4 prototypes,
-    p.setup_iters = 5          # each refined by 5 truncated-MG iterations
+    p.setup_iters = w.extra.get("setup_iters", 5)   # each refined by 5 truncated-MG iterations
     p.setup_init_relax = 10
     p.gcr_restart = 16
     p.tol = 1e-10
@@ -368,29 +368,38 @@ def run_ours(args, w):
         }
         line.update(extra)
         if not args.no_baseline:
-            line["cpu_baseline"] = cpu_baseline(w, U, srcs, masses, V0, iters)
+            line["cpu_baseline"] = cpu_baseline(w, U, srcs, masses, V0, oracle_iters(w, iters),
+                                                mg_params(w, "fp64").setup_iters)
         print(json.dumps(line), flush=True)
     if dist:
         torch.distributed.destroy_process_group()
 
 
-def cpu_baseline(w, U, srcs, masses, V0, gpu_iters, budget_s=25.0):
-    """The FP64 CPU oracle on a bounded sample of the step: block orthonormalisation
-    and the Galerkin operator from the relaxed-free random prototypes, then outer
-    MG-GCR iterations at the heaviest mass until the budget is used; the oracle's
-    time per solve is its time per outer iteration times the outer-iteration count
-    the solve needs (taken from the GPU run of the same workload), and the step is
-    that for every mass plus the measured setup pieces."""
+def cpu_baseline(w, U, srcs, masses, V0, outer_iters, setup_iters, budget_s=25.0):
+    """The FP64 CPU oracle on a bounded sample of the step, scaled to whole solves.
+
+    Timed: one Wilson operator application, one block orthonormalisation and one
+    Galerkin build from the random prototypes, and outer MG-GCR iterations at the
+    heaviest mass until the budget is used.  Scaled: a solve costs its outer
+    iteration count times the time of one outer iteration (the counts are the
+    oracle's own, measured once per workload by tests/golden/make_oracle_iters.py;
+    the GPU's counts where none are stored); the setup costs 10 MR relaxations of
+    every prototype (two operator applications per step), Nv/4 groups x
+    setup_iters x 4 truncated-cycle iterations (one outer iteration each) and
+    1 + Nv/4 orthonormalisations and builds."""
     import oracle
     oracle.build()
     cores = os.cpu_count()
+    t0 = time.perf_counter()
+    oracle.dslash(U, srcs[0], masses[0], w.dims)
+    t_d = time.perf_counter() - t0
     t0 = time.perf_counter()
     P, st = oracle.block_orthonormalize(V0, w.dims, w.block)
     t_ortho = time.perf_counter() - t0
     t0 = time.perf_counter()
     A = oracle.coarse_build(U, P, masses[0], w.dims, w.block)
     t_build = time.perf_counter() - t0
-    remaining = max(budget_s - t_ortho - t_build, 2.0)
+    remaining = max(budget_s - t_ortho - t_build - t_d, 2.0)
     k = 1
     t_it = None
     while True:
@@ -402,14 +411,21 @@ def cpu_baseline(w, U, srcs, masses, V0, gpu_iters, budget_s=25.0):
         if dt * 2 > remaining or k >= 16:
             break
         k *= 2
-    # setup estimate: the practical setup does 1 + (Nv / group) orthonormalisations and builds
-    n_builds = 1 + w.nvec // 4
-    step_s = n_builds * (t_ortho + t_build) + t_it * sum(gpu_iters)
+    groups = w.nvec // 4
+    n_builds = 1 + groups
+    setup_s = 10 * w.nvec * 2 * t_d + groups * setup_iters * 4 * t_it + n_builds * (t_ortho + t_build)
+    step_s = setup_s + t_it * sum(outer_iters)
     return {"value": len(masses) / step_s, "unit": "solves/s", "cores": cores, "kind": "oracle",
-            "sample": (f"oracle (OpenMP, {cores} threads): block orthonormalisation {t_ortho:.1f} s, coarse build "
-                       f"{t_build:.1f} s, {k} outer MG-GCR iterations ({t_it:.2f} s each) on this workload; step "
-                       f"= {n_builds} x (orthonormalisation + build) + {sum(gpu_iters)} outer iterations "
-                       f"(the counts of the GPU solves); relaxation of the setup not included")}
+            "sample": (f"oracle (OpenMP, {cores} threads) timed on this workload: one operator application "
+                       f"{t_d:.2f} s, block orthonormalisation {t_ortho:.2f} s, Galerkin build {t_build:.2f} s, "
+                       f"{k} outer MG-GCR iterations ({t_it:.3f} s each); step = setup estimate {setup_s:.0f} s + "
+                       f"{sum(outer_iters)} outer iterations ({list(outer_iters)} per mass)")}
+
+
+def oracle_iters(w, fallback):
+    """Outer iterations per mass of the oracle on this workload (stored), else the fallback."""
+    it = w.extra.get("oracle_outer_iters")
+    return list(it) if it else list(fallback)
 
 
 def run_reference(args, w):
@@ -419,11 +435,12 @@ def run_reference(args, w):
     import oracle
     oracle.build()
     U, V0, srcs, masses, plaq = make_inputs(w)
-    iters = list(w.extra.get("outer_iters", [250] * len(masses)))
+    iters = oracle_iters(w, [250] * len(masses))
+    setup_iters = mg_params(w, "fp64").setup_iters
     t0 = time.perf_counter()
     cb = None
     for _ in range(max(1, args.steps)):
-        cb = cpu_baseline(w, U, srcs, masses, V0, iters, budget_s=20.0)
+        cb = cpu_baseline(w, U, srcs, masses, V0, iters, setup_iters, budget_s=20.0)
     dt = time.perf_counter() - t0
     line = {"metric": METRIC, "value": cb["value"], "unit": "solves/s", "n_gpus": 0, "steps": args.steps,
             "warmup": 0, "ms_per_step": 1e3 * dt / max(1, args.steps), "higher_is_better": True, "scaling": "weak",

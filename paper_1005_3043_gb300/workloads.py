@@ -7,7 +7,9 @@ Masses: D(m) = D(0) + m exactly, so m = target - Re(lambda_min(D(0))).  The
 Re(lambda_min(D(0))) values below were computed once per field with ARPACK
 (implicitly restarted Arnoldi, which='SR') on the FP64 Wilson operator by
 tests/golden/make_masses.py; the field is bitwise reproducible on x86-64 and
-aarch64, and its plaquette is stored to detect any difference.
+aarch64, and its plaquette is stored to detect any difference.  The oracle's
+outer MG-GCR iteration counts per mass (for scaling a timed sample of oracle
+iterations to whole solves) come from tests/golden/make_oracle_iters.py.
 """
 from __future__ import annotations
 
@@ -43,7 +45,10 @@ WILSON_8x8x8x8 = Workload(
     name="wilson_8x8x8x8_nv8_beta6",
     dims=(8, 8, 8, 8), block=(4, 4, 4, 4), nvec=8, seed=1001,
     re_lambda_min_m0=0.7985754005, plaquette=0.593627332231,
-    targets=(0.01,), setup_target=0.01)
+    targets=(0.01,), setup_target=0.01,
+    # the configuration's 3 setup sweeps; the oracle's outer iterations from
+    # tests/golden/make_oracle_iters.py
+    extra={"setup_iters": 3, "oracle_outer_iters": (140,)})
 
 # 16^3 x 32, Nv = 20, masses swept toward critical (log-spaced Re lambda_min)
 WILSON_16x16x16x32 = Workload(
