@@ -128,6 +128,8 @@ def mg_params(w, prec):
     p.gcr_restart = 16
     p.tol = 1e-10
     p.max_outer = 4000
+    p.smoother = w.extra.get("smoother", 0)                # 0: MR steps; 1: one GMRES(steps) application
+    p.smoother_steps = w.extra.get("smoother_steps", 4)
     p.prec_inner = {"fp32": wmg.MG_FP32, "fp16": wmg.MG_FP16, "fp64": wmg.MG_FP64}[prec]
     p.delta = 0.0 if prec == "fp64" else 1e-4
     return p
@@ -403,7 +405,8 @@ def cpu_baseline(w, U, srcs, masses, V0, outer_iters, setup_iters, budget_s=25.0
     k = 1
     t_it = None
     while True:
-        p = oracle.make_params(w.dims, w.block, nv=w.nvec, m=masses[0], tol=0.0, max_outer=k, gcr_restart=16)
+        p = oracle.make_params(w.dims, w.block, nv=w.nvec, m=masses[0], tol=0.0, max_outer=k, gcr_restart=16,
+                               smoother=w.extra.get("smoother", 0), mr_steps=w.extra.get("smoother_steps", 4))
         t1 = time.perf_counter()
         _, info = oracle.gcr_solve(p, U, P, A, srcs[0])
         dt = time.perf_counter() - t1

@@ -85,6 +85,9 @@ typedef struct {
                               shared memory, else as 1; 1 operator read from global memory into
                               registers every iteration; 2 operator streamed through a
                               shared-memory ring (tests); 3 shared memory only (tests) */
+    int smoother;          /* post-smoother: 0 (default) smoother_steps MR steps, each scaled by omega;
+                              1 one GMRES(smoother_steps) application scaled by omega (Sec. III-IV:
+                              GMRES(4)), smoother_steps <= 16, FP32/FP64 storage */
     int smoother_fp16;     /* MG_FP16 only, storage of the smoother's spinors and links: 0 (default)
                               FP16 when the FP32 smoother working set (links + 3 spinors, 576 B per
                               site) exceeds the device L2, else FP32; 1 always FP16; 2 never */
@@ -103,7 +106,7 @@ typedef struct {
 /* Fill p with the defaults: block 4^4, nvec 8, relax 10, iters 3, group 4,
  * smoother 4, omega 0.9, restart 16, tol 1e-10, coarse_tol 1e-3,
  * max_outer 1000, max_coarse 5000, delta 0, FP64, coarse_check 16, coarse_kernel 0,
- * smoother_fp16 0. */
+ * smoother 0 (MR), smoother_fp16 0. */
 int mg_default_params(mg_params* p);
 
 /* Create a context for an L0 x L1 x L2 x L3 lattice.  dims[mu] must be a

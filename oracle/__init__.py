@@ -57,7 +57,8 @@ class Params(ctypes.Structure):
                 ("tap", ctypes.c_int), ("m", ctypes.c_double), ("mr_steps", ctypes.c_int),
                 ("omega", ctypes.c_double), ("coarse_tol", ctypes.c_double),
                 ("coarse_maxit", ctypes.c_int), ("gcr_restart", ctypes.c_int),
-                ("tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("use_mg", ctypes.c_int)]
+                ("tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("use_mg", ctypes.c_int),
+                ("smoother", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -88,6 +89,7 @@ def _load():
             lib.or_coarse_apply.argtypes = [P, I, P, P, P]
             lib.or_coarse_apply_dag.argtypes = [P, I, P, P, P]
             lib.or_mr.argtypes = [P, I, P, D, I, D, P, P]
+            lib.or_gmres_smooth.argtypes = [P, I, P, D, I, D, P, P]
             lib.or_cgnr.argtypes = [P, I, P, P, P, D, I, P]
             lib.or_cgnr.restype = I
             lib.or_vcycle.argtypes = [P, P, P, P, P, P, P]
@@ -198,6 +200,13 @@ def mr(U, e, r, m: float, L, nsteps: int, omega: float, tap: int = 1):
     return e, r
 
 
+def gmres_smooth(U, e, r, m: float, L, k: int, omega: float, tap: int = 1):
+    """One GMRES(k) smoothing application: returns e + omega * argmin over K_k(D, r) of ||r - D d||."""
+    e, r = _c(e).copy(), _c(r)
+    _load().or_gmres_smooth(_p(_i4(L)), int(tap), _p(_c(U)), float(m), int(k), float(omega), _p(e), _p(r))
+    return e
+
+
 def cgnr(A, rc, Lc, tol: float, maxit: int):
     """Returns (y, iterations, final relative residual)."""
     A, rc = _c(A), _c(rc)
@@ -209,7 +218,7 @@ def cgnr(A, rc, Lc, tol: float, maxit: int):
 
 
 def make_params(L, B=(4, 4, 4, 4), nv=8, m=0.0, tap=1, mr_steps=4, omega=0.9, coarse_tol=1e-3,
-                coarse_maxit=10000, gcr_restart=16, tol=1e-10, max_outer=1000, use_mg=1) -> Params:
+                coarse_maxit=10000, gcr_restart=16, tol=1e-10, max_outer=1000, use_mg=1, smoother=0) -> Params:
     p = Params()
     for i in range(4):
         p.L[i] = int(L[i]); p.B[i] = int(B[i])
@@ -217,6 +226,7 @@ def make_params(L, B=(4, 4, 4, 4), nv=8, m=0.0, tap=1, mr_steps=4, omega=0.9, co
     p.mr_steps, p.omega = int(mr_steps), float(omega)
     p.coarse_tol, p.coarse_maxit = float(coarse_tol), int(coarse_maxit)
     p.gcr_restart, p.tol, p.max_outer, p.use_mg = int(gcr_restart), float(tol), int(max_outer), int(use_mg)
+    p.smoother = int(smoother)
     return p
 
 

@@ -466,6 +466,7 @@ typedef struct {
     double tol;          /* outer relative true residual */
     int max_outer;
     int use_mg;          /* 0: unpreconditioned GCR (M = I) */
+    int smoother;        /* 0: mr_steps MR steps; 1: one GMRES(mr_steps) application */
 } or_params;
 
 typedef struct {
@@ -528,6 +529,79 @@ static void mr_internal(const mg_t* g, int nsteps, cplx* e, cplx* r) {
         vaxpy(n, -alpha, q, r);
     }
     free(q);
+}
+
+/*
+ * GMRES(k) post-smoothing with under-relaxation (Sec. III: GMRES as the
+ * smoother with omega = 0.9; Sec. IV: the post-relaxation is one application
+ * of GMRES(4)).  With r = r_in - D e: Arnoldi on the Krylov space
+ * K_k(D, r), beta = ||r||, v_0 = r / beta, for j < k: w = D v_j,
+ * h_ij = <v_i, w> (i <= j), w -= sum_i h_ij v_i (one classical Gram-Schmidt
+ * pass), h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j}; then
+ * y = argmin || beta e_1 - Hbar y || (Givens rotations) and e += omega V_k y.
+ * A zero h_{j+1,j} ends the space at dimension j + 1 (exact solution in it).
+ */
+static void gmres_smooth(const mg_t* g, int k, cplx* e, const cplx* r) {
+    int64_t n = g->bk.V * 12;
+    double beta = sqrt(vnorm2(n, r));
+    if (!(beta > 0) || k <= 0) return;
+    cplx* V = (cplx*)malloc(sizeof(cplx) * n * (k + 1));
+    cplx* H = (cplx*)calloc((size_t)(k + 1) * k, sizeof(cplx));   /* H[i * k + j] */
+    for (int64_t i = 0; i < n; ++i) V[i] = r[i] / beta;
+    int dim = k;
+    for (int j = 0; j < k; ++j) {
+        cplx* w = V + (int64_t)(j + 1) * n;
+        D_apply(g, V + (int64_t)j * n, w);
+        for (int i = 0; i <= j; ++i) H[i * k + j] = vdot(n, V + (int64_t)i * n, w);
+        for (int i = 0; i <= j; ++i) vaxpy(n, -H[i * k + j], V + (int64_t)i * n, w);
+        double hn = sqrt(vnorm2(n, w));
+        H[(j + 1) * k + j] = hn;
+        if (!(hn > 0)) { dim = j + 1; break; }
+        for (int64_t i = 0; i < n; ++i) w[i] /= hn;
+    }
+    /* least squares by Givens rotations: R y = Q^dag beta e_1 */
+    cplx* g1 = (cplx*)calloc((size_t)dim + 1, sizeof(cplx));
+    g1[0] = beta;
+    for (int j = 0; j < dim; ++j) {
+        cplx a = H[j * k + j], b = H[(j + 1) * k + j];
+        double nrm = sqrt(creal(a) * creal(a) + cimag(a) * cimag(a) + creal(b) * creal(b) + cimag(b) * cimag(b));
+        if (!(nrm > 0)) continue;
+        cplx c = a / nrm, s = b / nrm;   /* [conj(c) conj(s); -s c] maps (a, b) to (nrm, 0) */
+        for (int jj = j; jj < dim; ++jj) {
+            cplx x1 = H[j * k + jj], x2 = H[(j + 1) * k + jj];
+            H[j * k + jj] = conj(c) * x1 + conj(s) * x2;
+            H[(j + 1) * k + jj] = -s * x1 + c * x2;
+        }
+        cplx t1 = g1[j], t2 = g1[j + 1];
+        g1[j] = conj(c) * t1 + conj(s) * t2;
+        g1[j + 1] = -s * t1 + c * t2;
+    }
+    cplx* y = (cplx*)calloc((size_t)dim, sizeof(cplx));
+    for (int i = dim - 1; i >= 0; --i) {
+        cplx acc = g1[i];
+        for (int jj = i + 1; jj < dim; ++jj) acc -= H[i * k + jj] * y[jj];
+        y[i] = acc / H[i * k + i];
+    }
+    for (int j = 0; j < dim; ++j) vaxpy(n, g->p->omega * y[j], V + (int64_t)j * n, e);
+    free(V); free(H); free(g1); free(y);
+}
+
+/* e += omega * argmin_{d in K_k(D, r)} ||r - D d|| (the GMRES(k) smoother on
+ * its own: e and r given, r = the residual of e; e is updated in place). */
+OR_API void or_gmres_smooth(const int* L, int tap, const double* Ur, double m, int k, double omega, double* er,
+                            const double* rr) {
+    or_params p;
+    memset(&p, 0, sizeof(p));
+    for (int i = 0; i < 4; ++i) p.L[i] = L[i];
+    p.tap = tap;
+    p.m = m;
+    p.omega = omega;
+    mg_t g;
+    memset(&g, 0, sizeof(g));
+    g.p = &p;
+    g.U = (const cplx*)Ur;
+    g.bk.V = vol(L);
+    gmres_smooth(&g, k, (cplx*)er, (const cplx*)rr);
 }
 
 /*
@@ -598,7 +672,10 @@ static void vcycle(const mg_t* g, const cplx* r_in, cplx* z) {
     or_prolong(p->L, p->B, p->nv, (const double*)g->P, (const double*)yc, (double*)z);
     D_apply(g, z, De);
     for (int64_t i = 0; i < n; ++i) r[i] = r_in[i] - De[i];
-    mr_internal(g, p->mr_steps, z, r);
+    if (p->smoother == 1)
+        gmres_smooth(g, p->mr_steps, z, r);
+    else
+        mr_internal(g, p->mr_steps, z, r);
     free(rc); free(yc); free(r); free(De);
 }
 

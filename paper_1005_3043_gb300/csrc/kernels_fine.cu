@@ -425,6 +425,104 @@ void gcr_xupdate(double2* x, const v2<T>* Z, size_t n, int k, const GcrCoef& y, 
     k_gcr_xupdate<T><<<stream_grid(n), kThreads, 0, st>>>(x, Z, n, k, y);
 }
 
+// ================================================================ GMRES(k) smoother
+// One application of GMRES(k) with under-relaxation (Sec. III-IV): Arnoldi
+// vectors basis[0..k] (basis[0] = r / beta), column j of the Hessenberg matrix
+// Hbar in the scalars: h_ij = scal[rslot(i, j+1)] (i <= j) from
+// k_gcr_multidot / k_gcr_orth_norm (one classical Gram-Schmidt pass), and
+// h_{j+1,j} = scal[rslot(j+1, j+1)] written when basis[j+1] is normalised.
+template <typename T> __global__ void k_gmres_normalize(v2<T>* basis, size_t n, int k, const double* __restrict__ in,
+                                                        double* __restrict__ out) {
+    const double nk = sqrt(in[S_GCR_PN2]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        out[rslot(k, k)] = nk;
+        out[rslot(k, k) + 1] = 0.0;
+    }
+    const T f = (T)(nk > 0 ? 1.0 / nk : 0.0);   // a zero vector stays zero (breakdown: exact in the space)
+    v2<T>* pk = basis + (size_t)k * n;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        st<T>(pk + i, f * ld<T>(pk + i));
+}
+// y = argmin || beta e_1 - Hbar y || by Givens rotations (one thread), then
+// scal[S_GCR_C + 2j] = omega y_j.  beta = scal[rslot(0, 0)] (the norm of r,
+// recorded when basis[0] was normalised).  The space ends at the first zero
+// h_{j+1,j}.
+constexpr int kGmresMax = 16;   // largest smoother Krylov dimension (mg_params check)
+__global__ void k_gmres_ls(double* scal, int k, double omega) {
+    // the small problem lives in shared memory (no per-thread stack frame)
+    __shared__ double hr[kGmresMax + 1][kGmresMax], hi[kGmresMax + 1][kGmresMax];
+    __shared__ double gr[kGmresMax + 1], gi[kGmresMax + 1], yr[kGmresMax], yi[kGmresMax];
+    if (blockIdx.x != 0 || threadIdx.x != 0 || k > kGmresMax) return;
+    int dim = k;
+    for (int j = 0; j < k; ++j) {
+        for (int i = 0; i <= j + 1; ++i) {
+            const int s = rslot(i, j + 1);
+            hr[i][j] = scal[s];
+            hi[i][j] = scal[s + 1];
+        }
+        if (dim == k && !(hr[j + 1][j] > 0)) dim = j + 1;
+    }
+    for (int i = 0; i <= k; ++i) { gr[i] = 0; gi[i] = 0; }
+    gr[0] = scal[rslot(0, 0)];
+    for (int j = 0; j < dim; ++j) {
+        const double ar = hr[j][j], ai = hi[j][j], br = hr[j + 1][j], bi = hi[j + 1][j];
+        const double nrm = sqrt(ar * ar + ai * ai + br * br + bi * bi);
+        if (!(nrm > 0)) continue;
+        const double cr = ar / nrm, ci = ai / nrm, sr = br / nrm, si = bi / nrm;
+        // [conj(c) conj(s); -s c] applied to rows j, j+1 of columns j.. and of g
+        for (int jj = j; jj < dim; ++jj) {
+            const double x1r = hr[j][jj], x1i = hi[j][jj], x2r = hr[j + 1][jj], x2i = hi[j + 1][jj];
+            hr[j][jj] = cr * x1r + ci * x1i + sr * x2r + si * x2i;
+            hi[j][jj] = cr * x1i - ci * x1r + sr * x2i - si * x2r;
+            hr[j + 1][jj] = -(sr * x1r - si * x1i) + (cr * x2r - ci * x2i);
+            hi[j + 1][jj] = -(sr * x1i + si * x1r) + (cr * x2i + ci * x2r);
+        }
+        const double t1r = gr[j], t1i = gi[j], t2r = gr[j + 1], t2i = gi[j + 1];
+        gr[j] = cr * t1r + ci * t1i + sr * t2r + si * t2i;
+        gi[j] = cr * t1i - ci * t1r + sr * t2i - si * t2r;
+        gr[j + 1] = -(sr * t1r - si * t1i) + (cr * t2r - ci * t2i);
+        gi[j + 1] = -(sr * t1i + si * t1r) + (cr * t2i + ci * t2r);
+    }
+    for (int i = dim - 1; i >= 0; --i) {
+        double ar = gr[i], ai = gi[i];
+        for (int jj = i + 1; jj < dim; ++jj) {
+            ar -= hr[i][jj] * yr[jj] - hi[i][jj] * yi[jj];
+            ai -= hr[i][jj] * yi[jj] + hi[i][jj] * yr[jj];
+        }
+        const double dr = hr[i][i], di = hi[i][i], dd = dr * dr + di * di;
+        yr[i] = dd > 0 ? (ar * dr + ai * di) / dd : 0.0;
+        yi[i] = dd > 0 ? (ai * dr - ar * di) / dd : 0.0;
+    }
+    for (int j = 0; j < k; ++j) {
+        scal[S_GCR_C + 2 * j] = j < dim ? omega * yr[j] : 0.0;
+        scal[S_GCR_C + 2 * j + 1] = j < dim ? omega * yi[j] : 0.0;
+    }
+}
+// z += sum_{j<k} c_j basis[j], c_j = scal[S_GCR_C + 2j]
+template <typename T>
+__global__ void k_multi_axpy(v2<T>* z, const v2<T>* __restrict__ basis, size_t n, int k, const double* __restrict__ scal) {
+    __shared__ double c[2 * K_MAX];
+    for (int j = threadIdx.x; j < 2 * k; j += blockDim.x) c[j] = scal[S_GCR_C + j];
+    __syncthreads();
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        cx<T> v = ld<T>(z + i);
+        for (int j = 0; j < k; ++j) cmad(v, cx<T>((T)c[2 * j], (T)c[2 * j + 1]), ld<T>(basis + (size_t)j * n + i));
+        st<T>(z + i, v);
+    }
+}
+template <typename T> void gmres_normalize(v2<T>* basis, size_t n, int k, const Reduce& R, cudaStream_t st) {
+    note_launch();
+    k_gmres_normalize<T><<<stream_grid(n), kThreads, 0, st>>>(basis, n, k, R.scal, R.scal);
+}
+void gmres_ls(const Reduce& R, int k, double omega, cudaStream_t st) {
+    note_launch();
+    k_gmres_ls<<<1, 1, 0, st>>>(R.scal, k, omega);
+}
+template <typename T> void multi_axpy(v2<T>* z, const v2<T>* basis, size_t n, int k, const Reduce& R, cudaStream_t st) {
+    note_launch();
+    k_multi_axpy<T><<<stream_grid(n), kThreads, 0, st>>>(z, basis, n, k, R.scal);
+}
+
 // ================================================================ instantiations
 #define INST(T)                                                                                                     \
     template void spinor_to_internal<T>(v2<T>*, const double2*, const Geom&, cudaStream_t);                         \
@@ -443,7 +541,9 @@ void gcr_xupdate(double2* x, const v2<T>* Z, size_t n, int k, const GcrCoef& y, 
     template void gcr_orth_norm<T>(v2<T>*, size_t, int, const Reduce&, cudaStream_t);                               \
     template void gcr_cdot<T>(const v2<T>*, const v2<T>*, size_t, int, const Reduce&, cudaStream_t);                \
     template void gcr_update<T>(v2<T>*, v2<T>*, size_t, int, const Reduce&, cudaStream_t);                          \
-    template void gcr_xupdate<T>(double2*, const v2<T>*, size_t, int, const GcrCoef&, cudaStream_t);
+    template void gcr_xupdate<T>(double2*, const v2<T>*, size_t, int, const GcrCoef&, cudaStream_t);          \
+    template void gmres_normalize<T>(v2<T>*, size_t, int, const Reduce&, cudaStream_t);                        \
+    template void multi_axpy<T>(v2<T>*, const v2<T>*, size_t, int, const Reduce&, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

@@ -87,6 +87,8 @@ template <typename T> struct Work {
     v2<T>* cq = nullptr;
     v2<T>* cr1 = nullptr;  // second buffers of the coarse CG
     v2<T>* cp1 = nullptr;
+    v2<T>* gm = nullptr;   // GMRES smoother basis, gm_k + 1 vectors
+    int gm_k = 0;
     int cnc = 0;           // coarse dof the coarse vectors are sized for
     bool ready = false;
 };
@@ -124,6 +126,7 @@ struct mg_ctx {
     int* cnbr = nullptr;             // coarse neighbour table [Vc][9]
     unsigned long long* xch = nullptr;   // exchange slots of the on-chip coarse CGLS
     unsigned int xch_epoch = 1;          // next free epoch
+    double* scal_s = nullptr;            // scalars of the GMRES smoother (its Hessenberg matrix)
     int coarse_kernel_used = MG_CK_NONE;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<void*> allocs;
@@ -484,6 +487,43 @@ int smooth(mg_ctx* ctx, const v2<T>* r, v2<T>* z, const Reduce& R, Counters& cnt
     Work<T>& w = work<T>(ctx);
     const size_t n = nfine(ctx);
     const int steps = ctx->prm.smoother_steps;
+    if (ctx->prm.smoother == 1 && steps > 0) {
+        // one GMRES(steps) application, under-relaxed by omega (Sec. III-IV):
+        // Arnoldi with one classical Gram-Schmidt pass per vector, the small
+        // least-squares problem on the device, z += omega V y
+        if (w.gm_k < steps) {
+            if (w.gm) { dfree(ctx, w.gm); w.gm = nullptr; w.gm_k = 0; }
+            TRY(dalloc(ctx, &w.gm, sizeof(v2<T>) * n * (size_t)(steps + 1)));
+            w.gm_k = steps;
+        }
+        Reduce Rs = R;
+        Rs.scal = ctx->scal_s;
+        const v2<T>* U = links<T>(ctx);
+        v2<T>* V = w.gm;
+        PROF_BEGIN(MG_K_DSLASH);
+        dslash<T>(DS_XMY, V, z, U, r, ctx->g, ctx->mass, 0.0, 0, Rs, ctx->st);
+        PROF_END(MG_K_DSLASH);
+        PROF_BEGIN(MG_K_KRYLOV);
+        norm2<T>(V, n, S_GCR_PN2, Rs, ctx->st);
+        gmres_normalize<T>(V, n, 0, Rs, ctx->st);
+        PROF_END(MG_K_KRYLOV);
+        for (int j = 0; j < steps; ++j) {
+            PROF_BEGIN(MG_K_DSLASH);
+            dslash<T>(DS_PLAIN, V + (size_t)(j + 1) * n, V + (size_t)j * n, U, V, ctx->g, ctx->mass, 0.0, 0, Rs, ctx->st);
+            PROF_END(MG_K_DSLASH);
+            PROF_BEGIN(MG_K_KRYLOV);
+            gcr_multidot<T>(V, n, j + 1, Rs, ctx->st);
+            gcr_orth_norm<T>(V, n, j + 1, Rs, ctx->st);
+            gmres_normalize<T>(V, n, j + 1, Rs, ctx->st);
+            PROF_END(MG_K_KRYLOV);
+        }
+        PROF_BEGIN(MG_K_KRYLOV);
+        gmres_ls(Rs, steps, ctx->prm.omega, ctx->st);
+        multi_axpy<T>(z, V, n, steps, Rs, ctx->st);
+        PROF_END(MG_K_KRYLOV);
+        cnt.matvecs += steps + 1;
+        return MG_OK;
+    }
     if (std::is_same<T, float>::value && smoother_fp16(ctx)) {
         TRY(ensure_fine16(ctx));
         HalfSpinor hr{ctx->h_r, ctx->h_sr}, hq{ctx->h_q, ctx->h_sq};
@@ -736,6 +776,8 @@ int check_params(const int dims[4], const mg_params* p, std::string& why) {
     if (p->prec_inner == MG_FP16 && p->nvec % 2 != 0) { why = "MG_FP16 needs an even nvec"; return MG_ERR_INVALID_ARG; }
     if (p->coarse_kernel < 0 || p->coarse_kernel > 3) { why = "coarse_kernel must be 0, 1, 2 or 3"; return MG_ERR_INVALID_ARG; }
     if (p->smoother_fp16 < 0 || p->smoother_fp16 > 2) { why = "smoother_fp16 must be 0, 1 or 2"; return MG_ERR_INVALID_ARG; }
+    if (p->smoother < 0 || p->smoother > 1) { why = "smoother must be 0 (MR) or 1 (GMRES)"; return MG_ERR_INVALID_ARG; }
+    if (p->smoother == 1 && p->smoother_steps > 16) { why = "GMRES smoother: smoother_steps <= 16"; return MG_ERR_INVALID_ARG; }
     return MG_OK;
 }
 
@@ -936,7 +978,8 @@ int mg_create(const int dims[4], int t_antiperiodic, const mg_params* p, void* s
         (rc = dalloc(ctx, &ctx->R.scal, sizeof(double) * S_COUNT)) || (rc = dalloc(ctx, &ctx->d_status, sizeof(int))) ||
         (rc = dalloc(ctx, &ctx->bar, sizeof(unsigned int) * 4)) ||
         (rc = dalloc(ctx, &ctx->cnbr, sizeof(int) * 9 * (size_t)g.Vc)) ||
-        (rc = dalloc(ctx, &ctx->xch, sizeof(unsigned long long) * kXchWords))) {
+        (rc = dalloc(ctx, &ctx->xch, sizeof(unsigned long long) * kXchWords)) ||
+        (rc = dalloc(ctx, &ctx->scal_s, sizeof(double) * S_COUNT))) {
         mg_destroy(ctx);
         return rc;
     }

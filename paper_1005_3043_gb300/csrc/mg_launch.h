@@ -64,6 +64,12 @@ template <typename T> void gcr_update(v2<T>* basis, v2<T>* r, size_t n, int k, c
 struct GcrCoef { double c[2 * K_MAX]; };
 template <typename T>
 void gcr_xupdate(double2* x, const v2<T>* Z, size_t n, int k, const GcrCoef& y, cudaStream_t st);
+// GMRES(k) smoother pieces: normalise basis[k] by sqrt(scal[S_GCR_PN2]) and record
+// it as h_{k,k-1}; solve the small least-squares problem (omega y -> S_GCR_C);
+// z += sum_j c_j basis[j]
+template <typename T> void gmres_normalize(v2<T>* basis, size_t n, int k, const Reduce& R, cudaStream_t st);
+void gmres_ls(const Reduce& R, int k, double omega, cudaStream_t st);
+template <typename T> void multi_axpy(v2<T>* z, const v2<T>* basis, size_t n, int k, const Reduce& R, cudaStream_t st);
 
 // ---------------------------------------------------------------- transfer / coarse
 // P64[X][s][i][6][l] from prototypes V[i][X][12][l]; *status = 1 on rank deficiency

@@ -22,13 +22,20 @@ from paper_1005_3043_gb300.workloads import WORKLOADS  # noqa: E402
 SETUP_ITERS = {"wilson_8x8x8x8_nv8_beta6": 3}   # the 8^4 configuration's 3 sweeps; otherwise Sec. IV's 5
 
 
+def smoother(w):
+    """(smoother, steps) of the workload: 0 = MR steps, 1 = one GMRES(steps)."""
+    return int(w.extra.get("smoother", 0)), int(w.extra.get("smoother_steps", 4))
+
+
 def main(name):
     w = WORKLOADS[name]
     oracle.build()
     U = synth.gauge_field(w.dims, beta=w.beta, sweeps=w.sweeps, n_or=w.n_or, seed=w.seed)
     V0 = synth.gaussian_vectors(w.dims, w.nvec, w.setup_seed)
     t0 = time.time()
-    po = oracle.make_params(w.dims, w.block, nv=w.nvec, m=w.setup_mass(), gcr_restart=16, tol=1e-10, max_outer=20000)
+    sm, steps = smoother(w)
+    po = oracle.make_params(w.dims, w.block, nv=w.nvec, m=w.setup_mass(), gcr_restart=16, tol=1e-10, max_outer=20000,
+                            smoother=sm, mr_steps=steps)
     Vs, P, A, st = oracle.setup(po, U, V0, init_relax=10, n_iter=SETUP_ITERS.get(name, 5), group_size=4)
     assert st == 0
     t_setup = time.time() - t0
@@ -36,7 +43,8 @@ def main(name):
     iters, rels = [], []
     for i, m in enumerate(w.masses()):
         b = synth.gaussian_spinor(w.dims, w.source_seed, stream=i)
-        po = oracle.make_params(w.dims, w.block, nv=w.nvec, m=m, gcr_restart=16, tol=1e-10, max_outer=20000)
+        po = oracle.make_params(w.dims, w.block, nv=w.nvec, m=m, gcr_restart=16, tol=1e-10, max_outer=20000,
+                                smoother=sm, mr_steps=steps)
         A_m = oracle.coarse_build(U, P, m, w.dims, w.block)
         t = time.time()
         x, info = oracle.gcr_solve(po, U, P, A_m, b)
@@ -47,7 +55,8 @@ def main(name):
     out = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"{name}_oracle_iters.txt")
     with open(out, "w") as f:
         f.write(f"# {name}: oracle setup ({SETUP_ITERS.get(name, 5)} refinement iterations per group of 4) "
-                f"at m = {w.setup_mass():.10f}, then one FP64 MG-GCR(16) solve per mass to 1e-10\n")
+                f"at m = {w.setup_mass():.10f}, then one FP64 MG-GCR(16) solve per mass to 1e-10; "
+                f"smoother {'GMRES(%d)' % steps if sm else '%d MR steps' % steps}\n")
         f.write(f"# masses {w.masses()}\n# true relative residuals {rels}\n# setup {t_setup:.0f} s\n")
         f.write("outer_iters " + " ".join(map(str, iters)) + "\n")
     print(open(out).read())

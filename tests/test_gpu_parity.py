@@ -336,3 +336,39 @@ def test_fp16_mode_solve_with_each_smoother_storage(c1, smoother_fp16):
         x, info = mg.solve(b)
     assert info["status"] == 0
     assert _true_rel(U, x, b, m, L) <= 1e-10
+
+
+@pytest.mark.parametrize("steps", [4, 8])
+def test_vcycle_parity_gmres_smoother(steps):
+    """V(0, GMRES(k)) cycle: one GMRES(k) post-smoothing application scaled by
+    omega (Sec. III-IV) against the oracle's, fixed coarse iterations."""
+    L, B, nv = (8, 8, 8, 8), (4, 4, 4, 4), 4
+    m = -0.2
+    U, V0, P, A = _level(L, B, nv, m=m)
+    r = synth.gaussian_spinor(L, 12)
+    po = oracle.make_params(L, B, nv=nv, m=m, coarse_tol=0.0, coarse_maxit=30, smoother=1, mr_steps=steps)
+    z_ref, _ = oracle.vcycle(po, U, P, A, r)
+    with wmg.WilsonMG(L, make_params(nv, B, coarse_tol=0.0, max_coarse=30, smoother=1, smoother_steps=steps)) as mg:
+        mg.set_links(U)
+        mg.set_mass(m)
+        mg.set_null_vectors(V0)
+        assert maxrel(mg.vcycle(r), z_ref) < 1e-10
+        assert maxrel(mg.vcycle(r, wmg.MG_FP32), z_ref) < 1e-4
+
+
+def test_solve_gmres_smoother_matches_oracle(c1):
+    """MG-GCR with the GMRES(8) smoother: FP64 iteration count within 2 of the
+    oracle's, the FP16-storage mode reaches the same 1e-10 true residual."""
+    L, B, nv, U, m = c1["L"], c1["B"], c1["nv"], c1["U"], c1["m"]
+    b = synth.gaussian_spinor(L, 7)
+    po = oracle.make_params(L, B, nv=nv, m=m, smoother=1, mr_steps=8)
+    x_ref, info_ref = oracle.gcr_solve(po, U, c1["P"], c1["A"], b)
+    for prec, delta in ((wmg.MG_FP64, 0.0), (wmg.MG_FP16, 1e-4)):
+        with wmg.WilsonMG(L, make_params(nv, B, prec_inner=prec, delta=delta, smoother=1, smoother_steps=8)) as mg:
+            mg.set_links(U)
+            mg.set_mass(m)
+            mg.set_null_vectors(c1["Vs"])
+            x, info = mg.solve(b)
+        assert info["status"] == 0
+        assert _true_rel(U, x, b, m, L) <= 1e-10
+        assert abs(info["outer_iters"] - info_ref["outer_iters"]) <= (2 if prec == wmg.MG_FP64 else 6)
