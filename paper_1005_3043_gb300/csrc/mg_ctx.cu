@@ -1563,7 +1563,6 @@ int batched_coarse_solve(mg_ctx* ctx, int nrhs, double tol, int maxit, std::vect
 int solve_batched_impl(mg_ctx* ctx, int nrhs, mg_solve_info* infos) {
     TRY(ensure_work<float>(ctx));
     BatchWork& b = ctx->bw;
-    Work<float>& w = ctx->wf;
     const mg_params& p = ctx->prm;
     const CoarseLevel& L = ctx->full;
     const size_t n = nfine(ctx);
