@@ -78,3 +78,27 @@ def test_batched_solve_matches_single_solves():
         assert res <= 1e-10, (i, res)
         # same method per source; the FP16 coarse operator changes the preconditioner only slightly
         assert abs(infos[i]["outer_iters"] - single[i]["outer_iters"]) <= max(3, 0.15 * single[i]["outer_iters"])
+
+
+def test_batched_solve_with_gmres_smoother():
+    """The lockstep batched solve with one GMRES(8) post-smoothing per cycle and
+    the FP16-storage mode: every source reaches 1e-10, iteration counts close to
+    the single-source solves."""
+    L, B, nv, U, m = c1_workload()
+    V0 = synth.gaussian_vectors(L, nv, 2001)
+    po = oracle.make_params(L, B, nv=nv, m=m, smoother=1, mr_steps=8)
+    Vs, P, A, st = oracle.setup(po, U, V0, init_relax=10, n_iter=3, group_size=4)
+    assert st == 0
+    nrhs = 4
+    b = np.stack([synth.gaussian_spinor(L, 7, stream=i) for i in range(nrhs - 1)] + [synth.point_source(L, 0, 1, 2)])
+    with wmg.WilsonMG(L, params(nv, B, prec_inner=wmg.MG_FP16, delta=1e-4, smoother=1, smoother_steps=8)) as mg:
+        mg.set_links(U)
+        mg.set_mass(m)
+        mg.set_null_vectors(Vs)
+        x, infos = mg.solve_batched(b)
+        single = [mg.solve(b[i])[1] for i in range(nrhs)]
+    for i in range(nrhs):
+        assert infos[i]["status"] == 0
+        res = np.linalg.norm(b[i] - oracle.dslash(U, x[i], m, L)) / np.linalg.norm(b[i])
+        assert res <= 1e-10, (i, res)
+        assert abs(infos[i]["outer_iters"] - single[i]["outer_iters"]) <= max(3, 0.2 * single[i]["outer_iters"])

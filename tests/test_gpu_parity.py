@@ -372,3 +372,23 @@ def test_solve_gmres_smoother_matches_oracle(c1):
         assert info["status"] == 0
         assert _true_rel(U, x, b, m, L) <= 1e-10
         assert abs(info["outer_iters"] - info_ref["outer_iters"]) <= (2 if prec == wmg.MG_FP64 else 6)
+
+
+def test_gmres_smoother_edge_cases():
+    """GMRES(1) is one MR step (same minimiser over span{r}); invalid smoother
+    parameters are rejected."""
+    L, B, nv = (8, 8, 8, 8), (4, 4, 4, 4), 4
+    m = -0.2
+    U, V0, P, A = _level(L, B, nv, m=m)
+    r = synth.gaussian_spinor(L, 12)
+    outs = []
+    for sm in (0, 1):
+        with wmg.WilsonMG(L, make_params(nv, B, coarse_tol=0.0, max_coarse=10, smoother=sm, smoother_steps=1)) as mg:
+            mg.set_links(U)
+            mg.set_mass(m)
+            mg.set_null_vectors(V0)
+            outs.append(mg.vcycle(r))
+    assert maxrel(outs[1], outs[0]) < 1e-11
+    for bad in ({"smoother": 2}, {"smoother": 1, "smoother_steps": 17}):
+        with pytest.raises(wmg.MGError):
+            wmg.WilsonMG(L, make_params(nv, B, **bad))
