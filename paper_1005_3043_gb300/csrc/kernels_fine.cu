@@ -84,6 +84,27 @@ template <typename Tin, typename Tout> void convert(v2<Tout>* out, const v2<Tin>
     k_convert<Tin, Tout><<<grid > 0 ? grid : 1, kThreads, 0, st>>>(out, in, n);
 }
 
+// FP32 links for the dslash: U4[mu][X][j 4][l] = (U[.][2j], U[.][2j+1]) as float4,
+// then U8[mu][X][l] = U[.][8] (36 float2 per site in one allocation)
+__global__ void k_links_pair(float2* __restrict__ out, const float2* __restrict__ U, Geom g) {
+    const long long n = 4LL * g.V;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long ms = i / g.Vb, l = i - ms * g.Vb;   // ms = mu * Vc + X
+        const float2* src = U + ms * 9 * g.Vb + l;
+        float4* u4 = reinterpret_cast<float4*>(out) + ms * 4 * g.Vb + l;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float2 a = src[(2 * j) * g.Vb], b = src[(2 * j + 1) * g.Vb];
+            u4[(size_t)j * g.Vb] = make_float4(a.x, a.y, b.x, b.y);
+        }
+        out[(size_t)32 * g.V + ms * g.Vb + l] = src[8 * g.Vb];
+    }
+}
+void links_pair(float2* out, const float2* U32, const Geom& g, cudaStream_t st) {
+    note_launch();
+    k_links_pair<<<(int)std::min<long long>((4LL * g.V + kThreads - 1) / kThreads, 152 * 16), kThreads, 0, st>>>(out, U32, g);
+}
+
 // ================================================================ Wilson operator
 template <typename T>
 __device__ __forceinline__ void load_spinor(cx<T> (&p)[4][3], const v2<T>* __restrict__ base, int Vb) {
@@ -105,7 +126,26 @@ __device__ __forceinline__ void hop(cx<T> (&acc)[4][3], const v2<T>* __restrict_
     cx<T> h[2][3];
     project<T, MU, FWD>(p, h);
     // link U^mu_x (forward) or U^mu_{x-mu} (backward)
-    const v2<T>* u = FWD ? U + ((size_t)MU * g.Vc + X) * 9 * g.Vb + l : U + ((size_t)MU * g.Vc + Xn) * 9 * g.Vb + ln;
+    const size_t ls = FWD ? ((size_t)MU * g.Vc + X) : ((size_t)MU * g.Vc + Xn);
+    const int lsite = FWD ? l : ln;
+    cx<T> m[9];
+    if constexpr (sizeof(T) == 4) {
+        // FP32 links in pairs: entries (2j, 2j+1) as one 16-byte word, j < 4, then entry 8
+        const float4* u4 = reinterpret_cast<const float4*>(U) + ls * 4 * g.Vb + lsite;
+        const float2* u8 = reinterpret_cast<const float2*>(U) + (size_t)32 * g.V + ls * g.Vb + lsite;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float4 q = __ldg(u4 + (size_t)j * g.Vb);
+            m[2 * j] = cx<T>(q.x, q.y);
+            m[2 * j + 1] = cx<T>(q.z, q.w);
+        }
+        const float2 q8 = __ldg(u8);
+        m[8] = cx<T>(q8.x, q8.y);
+    } else {
+        const v2<T>* u = U + ls * 9 * g.Vb + lsite;
+#pragma unroll
+        for (int e = 0; e < 9; ++e) m[e] = ldg<T>(u + e * g.Vb);
+    }
     cx<T> w[2][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -117,13 +157,11 @@ __device__ __forceinline__ void hop(cx<T> (&acc)[4][3], const v2<T>* __restrict_
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
             if (FWD) {
-                cx<T> uab = ldg<T>(u + (3 * a + b) * g.Vb);
-                cmad(w[0][a], uab, h[0][b]);
-                cmad(w[1][a], uab, h[1][b]);
+                cmad(w[0][a], m[3 * a + b], h[0][b]);
+                cmad(w[1][a], m[3 * a + b], h[1][b]);
             } else {
-                cx<T> uba = ldg<T>(u + (3 * b + a) * g.Vb);
-                cmadc(w[0][a], uba, h[0][b]);
-                cmadc(w[1][a], uba, h[1][b]);
+                cmadc(w[0][a], m[3 * b + a], h[0][b]);
+                cmadc(w[1][a], m[3 * b + a], h[1][b]);
             }
         }
     accumulate<T, MU, FWD>(acc, w, flip ? T(0.5) : T(-0.5));

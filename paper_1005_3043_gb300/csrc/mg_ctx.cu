@@ -105,6 +105,7 @@ struct mg_ctx {
     bool has_links = false;
     double2* U64 = nullptr;          // links [mu][X][9][Vb]
     float2* U32 = nullptr;
+    float2* U32p = nullptr;         // FP32 links in the dslash's paired layout
     double2* b64 = nullptr;          // FP64 fine vectors (internal layout)
     double2* x64 = nullptr;
     double2* r64 = nullptr;
@@ -217,7 +218,7 @@ template <typename T> Work<T>& work(mg_ctx* c);
 template <> Work<float>& work<float>(mg_ctx* c) { return c->wf; }
 template <> Work<double>& work<double>(mg_ctx* c) { return c->wd; }
 template <typename T> const v2<T>* links(const mg_ctx* c);
-template <> const v2<float>* links<float>(const mg_ctx* c) { return c->U32; }
+template <> const v2<float>* links<float>(const mg_ctx* c) { return c->U32p; }   // paired layout
 template <> const v2<double>* links<double>(const mg_ctx* c) { return c->U64; }
 template <typename T> const v2<T>* lvlP(const CoarseLevel& L);
 template <> const v2<float>* lvlP<float>(const CoarseLevel& L) { return L.P32; }
@@ -969,6 +970,7 @@ int mg_create(const int dims[4], int t_antiperiodic, const mg_params* p, void* s
     int rc = MG_OK;
     if ((rc = dalloc(ctx, &ctx->U64, sizeof(double2) * 36 * (size_t)g.V)) ||
         (rc = dalloc(ctx, &ctx->U32, sizeof(float2) * 36 * (size_t)g.V)) ||
+        (rc = dalloc(ctx, &ctx->U32p, sizeof(float2) * 36 * (size_t)g.V)) ||
         (rc = dalloc(ctx, &ctx->b64, sizeof(double2) * n)) || (rc = dalloc(ctx, &ctx->x64, sizeof(double2) * n)) ||
         (rc = dalloc(ctx, &ctx->r64, sizeof(double2) * n)) ||
         (rc = dalloc(ctx, &ctx->stage_a, sizeof(double2) * 36 * (size_t)g.V)) ||
@@ -1021,6 +1023,7 @@ int mg_set_links(mg_ctx* ctx, const double* U) {
     CK(cudaMemcpyAsync(ctx->stage_a, U, sizeof(double2) * 36 * (size_t)ctx->g.V, cudaMemcpyHostToDevice, ctx->st));
     links_to_internal<double>(ctx->U64, ctx->stage_a, ctx->g, ctx->st);
     convert<double, float>(ctx->U32, ctx->U64, 36 * (size_t)ctx->g.V, ctx->st);
+    links_pair(ctx->U32p, ctx->U32, ctx->g, ctx->st);
     CKL();
     CK(cudaStreamSynchronize(ctx->st));
     ctx->has_links = true;
@@ -1567,7 +1570,7 @@ int solve_batched_impl(mg_ctx* ctx, int nrhs, mg_solve_info* infos) {
     const CoarseLevel& L = ctx->full;
     const size_t n = nfine(ctx);
     const int K = b.K;
-    const v2<float>* U = ctx->U32;
+    const v2<float>* U = links<float>(ctx);
     std::vector<double> bnorm(nrhs), rnorm(nrhs), rcycle(nrhs), rel(nrhs, 1.0), coarse(nrhs, 0.0);
     std::vector<int> iters(nrhs, 0), restarts(nrhs, 0), status(nrhs, MG_ERR_NOT_CONVERGED), kk(nrhs, 0),
         active(nrhs, 1), cycle_end(nrhs, 0), mv(nrhs, 0);

@@ -151,6 +151,9 @@ struct ConstHalfSpinor {
     ConstHalfSpinor(HalfSpinor h) : v(h.v), s(h.s) {}
 };
 void links_to_half(uint2* U16, const float2* U32, const Geom& g, cudaStream_t st);
+// the FP32 links in the dslash's paired layout (36 float2 per site): the dslash<float>
+// launchers take this array, the coarse build and the FP16 copy the plain one
+void links_pair(float2* out, const float2* U32, const Geom& g, cudaStream_t st);
 void to_half(HalfSpinor h, const float2* x, const Geom& g, cudaStream_t st);
 void from_half(float2* x, ConstHalfSpinor h, const Geom& g, cudaStream_t st);
 void dslash_h_plain(HalfSpinor out, ConstHalfSpinor in, const uint2* U16, const Geom& g, double mass, cudaStream_t st);
