@@ -59,6 +59,7 @@ WILSON_16x16x16x32 = Workload(
     # one GMRES(12) post-smoothing application per cycle (the paper's smoother;
     # 12 vectors minimise the step time of this two-level cycle, measured over
     # 6..16: 2.38 s against 8.64 s for 4 MR steps)
-    extra={"smoother": 1, "smoother_steps": 12})
+    # the oracle's outer iterations from tests/golden/make_oracle_iters.py
+    extra={"smoother": 1, "smoother_steps": 12, "oracle_outer_iters": (25, 27, 29, 29, 31)})
 
 WORKLOADS = {w.name: w for w in (WILSON_8x8x8x8, WILSON_16x16x16x32)}
