@@ -173,6 +173,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_coarse_apply_tc(TcApplyArgs a
         for (int i = tid; i < nc * nw; i += kTcThreads) {
             int b = i / nw, n = i - b * nw;
             float2 v = xY[(size_t)b * npad + n];
+            if (a.colscale) {
+                const float sc = (float)a.colscale[n0 + n];
+                v.x *= sc;
+                v.y *= sc;
+            }
             if (a.dag && b >= nvh) { v.x = -v.x; v.y = -v.y; }
             __half hr = __float2half_rn(v.x), hi = __float2half_rn(v.y);
             __half lr = __float2half_rn(v.x - __half2float(hr)), li = __float2half_rn(v.y - __half2float(hi));
@@ -213,6 +218,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_coarse_apply_tc(TcApplyArgs a
     for (int c0 = 0; c0 < nw; c0 += 16) {
         float v[16];
         tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        if (a.colscale)
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] *= (float)(1.0 / a.colscale[n0 + c0 + j]);
         if (ok && valid_row) {
 #pragma unroll
             for (int j = 0; j < 16; ++j)
@@ -392,7 +400,14 @@ __global__ void k_bcol_norm(const float2* __restrict__ v, long long rows, int np
     col_partial(s, t, npad, shf, part);
 }
 // scale_n = ||rc_n||, done = (scale == 0 || n >= nrhs)
-__global__ void k_bcg_scale(BatchScal S, const float* part, int nparts, int npad, int nrhs, int maxit) {
+// power of two nearest sqrt(rows / s): entries of a column with |x|^2 = s then sit
+// near 1 in magnitude, far above the FP16 subnormal range, after scaling
+__device__ __forceinline__ double pow2_scale(double s, long long rows) {
+    if (!(s > 0)) return 1.0;
+    const double e = rint(0.5 * log2((double)rows / s));
+    return exp2(fmin(fmax(e, -120.0), 120.0));
+}
+__global__ void k_bcg_scale(BatchScal S, const float* part, int nparts, int npad, int nrhs, int maxit, long long rows) {
     double s = col_total(part, nparts, npad);
     if (threadIdx.x != 0) return;
     int n = blockIdx.x;
@@ -401,6 +416,7 @@ __global__ void k_bcg_scale(BatchScal S, const float* part, int nparts, int npad
     S.done[n] = (n >= nrhs || !(sc > 0) || maxit <= 0) ? 1.0 : 0.0;
     S.iters[n] = 0;
     S.r2[n] = S.done[n] != 0 ? 0.0 : 1.0;
+    S.csr[n] = pow2_scale(1.0, rows);   // r starts with unit norm
 }
 __global__ void k_bcg_start(float2* __restrict__ y, float2* __restrict__ r, const float2* __restrict__ rc,
                             long long total, int npad, BatchScal S) {
@@ -414,9 +430,12 @@ __global__ void k_bcg_start(float2* __restrict__ y, float2* __restrict__ r, cons
     }
 }
 // gamma = ||s||^2 (first direction)
-__global__ void k_bcg_gamma0(BatchScal S, const float* xpart, int nx, int npad) {
+__global__ void k_bcg_gamma0(BatchScal S, const float* xpart, int nx, int npad, long long rows) {
     double s = col_total(xpart, nx, npad);
-    if (threadIdx.x == 0) S.gamma[blockIdx.x] = s;
+    if (threadIdx.x == 0) {
+        S.gamma[blockIdx.x] = s;
+        S.csp[blockIdx.x] = pow2_scale(s, rows);   // p = s
+    }
 }
 // alpha = gamma / ||q||^2
 __global__ void k_bcg_alpha(BatchScal S, const float* xpart, int nx, int npad) {
@@ -448,22 +467,25 @@ __global__ void k_bcg_update1(float2* __restrict__ y, float2* __restrict__ r, co
     col_partial(s, t, npad, shf, part);
 }
 // ||r||^2, iteration count, stopping test; *active counts columns still running
-__global__ void k_bcg_check(BatchScal S, const float* part, int nparts, int npad, double tol2, int maxit, int* active) {
+__global__ void k_bcg_check(BatchScal S, const float* part, int nparts, int npad, double tol2, int maxit, int* active,
+                            long long rows) {
     double s = col_total(part, nparts, npad);
     int n = blockIdx.x;
     if (threadIdx.x != 0 || S.done[n] != 0) return;
     S.r2[n] = s;                         // relative to ||rc_n||^2 = 1 after scaling
+    S.csr[n] = pow2_scale(s, rows);
     S.iters[n] += 1;
     if (s <= tol2 || S.iters[n] >= maxit) S.done[n] = 1;
     else atomicAdd(active, 1);
 }
 // beta = ||s||^2 / gamma, gamma = ||s||^2
-__global__ void k_bcg_beta(BatchScal S, const float* xpart, int nx, int npad) {
+__global__ void k_bcg_beta(BatchScal S, const float* xpart, int nx, int npad, long long rows) {
     double s = col_total(xpart, nx, npad);
     int n = blockIdx.x;
     if (threadIdx.x != 0 || S.done[n] != 0) return;
     S.beta[n] = S.gamma[n] > 0 ? s / S.gamma[n] : 0.0;
     S.gamma[n] = s;
+    S.csp[n] = pow2_scale(s, rows);      // p = s + beta p is of the size of s or larger
 }
 __global__ void k_bcg_update2(float2* __restrict__ p, const float2* __restrict__ s, long long total, int npad,
                               BatchScal S, int first) {
@@ -502,18 +524,18 @@ void bcg_iteration(const BatchCg& c, cudaStream_t st) {
     const long long rows = (long long)c.g.Vc * c.nc, total = rows * c.npad;
     const int ct = col_threads(c.npad);
     const size_t cs = col_smem(c.npad);
-    TcApplyArgs ap{c.Aemb, c.p, c.q, c.nc, c.npad, c.nw, 0, c.g, c.xpart, c.err};
+    TcApplyArgs ap{c.Aemb, c.p, c.q, c.nc, c.npad, c.nw, 0, c.g, c.xpart, c.err, c.S.csp};
     coarse_apply_tc(ap, st);                                                               // q = D_c p
     note_launch();
     k_bcg_alpha<<<c.npad, 256, 0, st>>>(c.S, c.xpart, c.g.Vc, c.npad);
     note_launch();
     k_bcg_update1<<<kRowChunks, ct, cs, st>>>(c.y, c.r, c.p, c.q, rows, c.npad, c.S, c.rpart, c.active);
     note_launch();
-    k_bcg_check<<<c.npad, 256, 0, st>>>(c.S, c.rpart, kRowChunks, c.npad, c.tol2, c.maxit, c.active);
-    TcApplyArgs as{c.Aemb, c.r, c.s, c.nc, c.npad, c.nw, 1, c.g, c.xpart, c.err};
+    k_bcg_check<<<c.npad, 256, 0, st>>>(c.S, c.rpart, kRowChunks, c.npad, c.tol2, c.maxit, c.active, rows);
+    TcApplyArgs as{c.Aemb, c.r, c.s, c.nc, c.npad, c.nw, 1, c.g, c.xpart, c.err, c.S.csr};
     coarse_apply_tc(as, st);                                                               // s = D_c^dag r
     note_launch();
-    k_bcg_beta<<<c.npad, 256, 0, st>>>(c.S, c.xpart, c.g.Vc, c.npad);
+    k_bcg_beta<<<c.npad, 256, 0, st>>>(c.S, c.xpart, c.g.Vc, c.npad, rows);
     note_launch();
     k_bcg_update2<<<ew_grid(total), 256, 0, st>>>(c.p, c.s, total, c.npad, c.S, 0);
 }
@@ -524,13 +546,13 @@ void bcg_start(const BatchCg& c, cudaStream_t st) {
     note_launch();
     k_bcol_norm<<<kRowChunks, col_threads(c.npad), col_smem(c.npad), st>>>(c.rc, rows, c.npad, c.rpart);
     note_launch();
-    k_bcg_scale<<<c.npad, 256, 0, st>>>(c.S, c.rpart, kRowChunks, c.npad, c.nrhs, c.maxit);
+    k_bcg_scale<<<c.npad, 256, 0, st>>>(c.S, c.rpart, kRowChunks, c.npad, c.nrhs, c.maxit, rows);
     note_launch();
     k_bcg_start<<<ew_grid(total), 256, 0, st>>>(c.y, c.r, c.rc, total, c.npad, c.S);
-    TcApplyArgs as{c.Aemb, c.r, c.s, c.nc, c.npad, c.nw, 1, c.g, c.xpart, c.err};
+    TcApplyArgs as{c.Aemb, c.r, c.s, c.nc, c.npad, c.nw, 1, c.g, c.xpart, c.err, c.S.csr};
     coarse_apply_tc(as, st);
     note_launch();
-    k_bcg_gamma0<<<c.npad, 256, 0, st>>>(c.S, c.xpart, c.g.Vc, c.npad);
+    k_bcg_gamma0<<<c.npad, 256, 0, st>>>(c.S, c.xpart, c.g.Vc, c.npad, rows);
     note_launch();
     k_bcg_update2<<<ew_grid(total), 256, 0, st>>>(c.p, c.s, total, c.npad, c.S, 1);
 }

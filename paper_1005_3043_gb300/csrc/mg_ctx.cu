@@ -50,7 +50,7 @@ struct CoarseLevel {
 struct BatchWork {
     int npad = 0, nrhs_cap = 0, K = 0, nc = 0;
     float2 *rcB = nullptr, *yB = nullptr, *rB = nullptr, *sB = nullptr, *pB = nullptr, *qB = nullptr;
-    double* cgs = nullptr;          // 7 x npad per-RHS CG scalars
+    double* cgs = nullptr;          // 9 x npad per-RHS CG scalars
     float* xpart = nullptr;         // Vc x npad
     float* rpart = nullptr;         // 152 x npad
     int* flags = nullptr;           // [0] active columns, [1] error
@@ -1475,7 +1475,7 @@ int ensure_batch(mg_ctx* ctx, int nrhs) {
     TRY(dalloc(ctx, &b.sB, sizeof(float2) * pe));
     TRY(dalloc(ctx, &b.pB, sizeof(float2) * pe));
     TRY(dalloc(ctx, &b.qB, sizeof(float2) * pe));
-    TRY(dalloc(ctx, &b.cgs, sizeof(double) * 7 * npad));
+    TRY(dalloc(ctx, &b.cgs, sizeof(double) * 9 * npad));
     TRY(dalloc(ctx, &b.xpart, sizeof(float) * (size_t)ctx->g.Vc * npad));
     TRY(dalloc(ctx, &b.rpart, sizeof(float) * kBatchRowChunks * npad));
     TRY(dalloc(ctx, &b.flags, sizeof(int) * 4));
@@ -1508,6 +1508,7 @@ BatchCg batch_cg(mg_ctx* ctx, double tol, int maxit, int nrhs) {
     c.g = ctx->g;
     c.S.scale = b.cgs; c.S.done = b.cgs + b.npad; c.S.iters = b.cgs + 2 * b.npad; c.S.r2 = b.cgs + 3 * b.npad;
     c.S.gamma = b.cgs + 4 * b.npad; c.S.alpha = b.cgs + 5 * b.npad; c.S.beta = b.cgs + 6 * b.npad;
+    c.S.csp = b.cgs + 7 * b.npad; c.S.csr = b.cgs + 8 * b.npad;
     c.xpart = b.xpart; c.rpart = b.rpart; c.active = b.flags; c.err = b.flags + 1;
     return c;
 }

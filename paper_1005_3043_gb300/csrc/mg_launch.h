@@ -226,6 +226,8 @@ struct TcApplyArgs {
     Geom g;
     float* norms;   // optional per-aggregate column sums of |y|^2: [Vc][npad]
     int* err;       // set to 1 if a bounded wait gave up
+    const double* colscale;   // optional per-column power-of-two factor applied to x before the
+                              // FP16 hi/lo split (y is scaled back exactly); nullptr: 1
 };
 // y = D_c x (dag: sigma3 D_c sigma3 x) for the whole panel on tcgen05 tensor cores;
 // coarse_apply_tc_prepare(nc, npad) once per shape before launching (and before any capture)
@@ -249,6 +251,8 @@ struct BatchScal {   // per-RHS CG scalars, npad doubles each
     double* gamma;
     double* alpha;
     double* beta;
+    double* csp;     // power-of-two panel scales of p and r for the FP16 split (from |s|^2, |r|^2)
+    double* csr;
 };
 struct BatchCg {
     const __half* Aemb;

@@ -102,3 +102,31 @@ def test_batched_solve_with_gmres_smoother():
         res = np.linalg.norm(b[i] - oracle.dslash(U, x[i], m, L)) / np.linalg.norm(b[i])
         assert res <= 1e-10, (i, res)
         assert abs(infos[i]["outer_iters"] - single[i]["outer_iters"]) <= max(3, 0.2 * single[i]["outer_iters"])
+
+
+def test_batched_solve_deep_coarse_iterations_16x16x16x32():
+    """At the lightest 16^3x32 mass with the GMRES(12) setup the coarse CG runs
+    hundreds of iterations per cycle and its vectors shrink far below 1: the
+    tensor-core split of the panel into FP16 hi + lo must stay out of the FP16
+    subnormal range (per-column power-of-two scaling).  Batched and single solves
+    then take the same outer iterations and all reach 1e-10."""
+    from paper_1005_3043_gb300.workloads import WORKLOADS
+    w = WORKLOADS["wilson_16x16x16x32_nv20_beta6_5mass"]
+    U = synth.gauge_field(w.dims, beta=w.beta, sweeps=w.sweeps, n_or=w.n_or, seed=w.seed)
+    V0 = synth.gaussian_vectors(w.dims, w.nvec, w.setup_seed)
+    b = np.stack([synth.point_source(w.dims, 0, 0, 2), synth.gaussian_spinor(w.dims, w.source_seed, stream=102)])
+    m = w.masses()[-1]
+    p = params(w.nvec, w.block, prec_inner=wmg.MG_FP16, delta=1e-4, setup_group=4, setup_iters=5,
+               smoother=1, smoother_steps=12, max_outer=300)
+    with wmg.WilsonMG(w.dims, p) as mg:
+        mg.set_links(U)
+        mg.set_mass(w.setup_mass())
+        mg.setup(V0)
+        mg.set_mass(m)
+        x, infos = mg.solve_batched(b)
+        single = [mg.solve(b[i])[1] for i in range(len(b))]
+    for i in range(len(b)):
+        assert infos[i]["status"] == 0, infos[i]
+        res = np.linalg.norm(b[i] - oracle.dslash(U, x[i], m, w.dims)) / np.linalg.norm(b[i])
+        assert res <= 1e-10, (i, res)
+        assert abs(infos[i]["outer_iters"] - single[i]["outer_iters"]) <= 2
