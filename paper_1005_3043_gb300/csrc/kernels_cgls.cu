@@ -35,6 +35,7 @@
 namespace wmg {
 
 constexpr int kCglsThreads = 512;
+constexpr int kXchScratch = 2 * (32 + kXchMaxGrid + 1);   // floats for xch_allreduce<2>
 constexpr long long kCopyWaitLimit = 4000000LL;   // polls of a bulk-copy mbarrier before giving up
 
 // Four consecutive rows a..a+3 of one column of a unit, as complex FP32 pairs
@@ -402,8 +403,10 @@ template <bool H16, bool TM> struct CglsCta {
     }
 };
 
-template <bool H16, bool TM> __device__ void cgls_body(const CglsArgs& a, CglsCta<H16, TM>& c, float* shr) {
+template <bool H16, bool TM> __device__ void cgls_body(const CglsArgs& a, CglsCta<H16, TM>& c) {
     unsigned int e = a.epoch0;   // one epoch per exchange
+    // exchange scratch: its own kXchScratch floats after the staging buffer
+    float* shr = reinterpret_cast<float*>(c.xs + (size_t)a.sh.nx_max * c.K);
     float2* rbuf[2] = {a.r, a.r1};
     float2* pbuf[2] = {a.p, a.p1};
     // y = 0, r = rc on the own rows; |rc|^2
@@ -469,10 +472,9 @@ template <bool H16, bool TM> __device__ void cgls_body(const CglsArgs& a, CglsCt
 
 template <bool H16, bool TM> __global__ void __launch_bounds__(kCglsThreads, 1) k_cgls_onchip(CglsArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ float shr[33];
     CglsCta<H16, TM> c(a, smem_raw);
     c.start();
-    cgls_body<H16, TM>(a, c, shr);
+    cgls_body<H16, TM>(a, c);
     c.drain();   // no copy may still be writing shared memory, and no TMEM stays allocated, when the CTA exits
 }
 
@@ -566,7 +568,7 @@ bool cgls_shape(int nc, int Vc, bool h16, int mode, CglsShape* out) {
         s.stride = (int)(round_up(ub, 128) + (ru * esz) % 128);
         // one reduction buffer of (rows x row splits) <= 4T entries
         s.red_n = std::max(4 * T, s.nu_max * ru);
-        size_t off = round_up(256 + (size_t)s.red_n * 8 + (size_t)s.nx_max * 9 * nc * 8, 128);
+        size_t off = round_up(256 + (size_t)s.red_n * 8 + (size_t)s.nx_max * 9 * nc * 8 + kXchScratch * 4, 128);
         long long score;
         const int quads = s.nu_max * ru / 4;
         const int ks_min = quads <= T ? T / quads : 0;
@@ -577,7 +579,7 @@ bool cgls_shape(int nc, int Vc, bool h16, int mode, CglsShape* out) {
             s.nx_max = std::min(Vc, (s.nu_max - 1 + H - 1) / H + 1);
             s.resident = 0;
             s.red_n = std::max(4 * T, ru);   // two reduction buffers (consecutive waves)
-            off = round_up(256 + 2 * (size_t)s.red_n * 8 + (size_t)s.nx_max * 9 * nc * 8, 128);
+            off = round_up(256 + 2 * (size_t)s.red_n * 8 + (size_t)s.nx_max * 9 * nc * 8 + kXchScratch * 4, 128);
             if (off + 2 * (size_t)s.stride > budget) continue;
             s.groups = 2;
             s.wave = 1;

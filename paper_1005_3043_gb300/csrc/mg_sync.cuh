@@ -119,25 +119,51 @@ __device__ __forceinline__ bool xch_wait(const unsigned long long* slot, unsigne
 constexpr int kXchPad = 16;
 // v[j] (this thread's share) -> the grid-wide sums, identical in every CTA.
 // slots: [parity 2][value 2][G][kXchPad]; needs NV * G <= blockDim.x.
+// sc: shared scratch of at least NV * (32 + G + 1) floats, free during the call.
+// Three CTA barriers for any NV: warp partial sums -> thread 0 publishes;
+// polled values -> one warp per value sums them in CTA order.
 template <int NV>
-__device__ bool xch_allreduce(float (&v)[NV], unsigned long long* slots, unsigned int e, int* err, float* sh) {
+__device__ bool xch_allreduce(float (&v)[NV], unsigned long long* slots, unsigned int e, int* err, float* sc) {
     static_assert(NV >= 1 && NV <= 2, "one or two values per exchange");
-    const int G = gridDim.x, t = threadIdx.x;
+    const int G = gridDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
     unsigned long long* base = slots + (size_t)(e & 1) * 2 * G * kXchPad;
-    float cta[NV];
+    float* wsum = sc;                  // [NV][32] warp partials
+    float* gv = sc + NV * 32;          // [NV * G] polled CTA sums
+    float* res = gv + NV * G;          // [NV] grid sums
 #pragma unroll
-    for (int j = 0; j < NV; ++j) cta[j] = block_sum_t<float>(v[j], sh);
+    for (int j = 0; j < NV; ++j) {
+        const float w = warp_sum_t<float>(v[j]);
+        if (lane == 0) wsum[j * 32 + warp] = w;
+    }
+    __syncthreads();
     if (t == 0) {
+        float cta[NV];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            float a = 0.f;
+            for (int i = 0; i < nw; ++i) a += wsum[j * 32 + i];
+            cta[j] = a;
+        }
         __threadfence();
 #pragma unroll
         for (int j = 0; j < NV; ++j) xch_publish(base + ((size_t)j * G + blockIdx.x) * kXchPad, cta[j], e);
     }
     float got = 0.f;
     bool ok = true;
-    if (t < NV * G) ok = xch_wait(base + (size_t)t * kXchPad, e, err, got);
+    if (t < NV * G) {
+        ok = xch_wait(base + (size_t)t * kXchPad, e, err, got);
+        gv[t] = got;
+    }
     if (__syncthreads_or(!ok)) return false;
+    if (warp < NV) {
+        float a = 0.f;
+        for (int c = lane; c < G; c += 32) a += gv[warp * G + c];
+        a = warp_sum_t<float>(a);
+        if (lane == 0) res[warp] = a;
+    }
+    __syncthreads();
 #pragma unroll
-    for (int j = 0; j < NV; ++j) v[j] = block_sum_t<float>((t >= j * G && t < (j + 1) * G) ? got : 0.f, sh);
+    for (int j = 0; j < NV; ++j) v[j] = res[j];
     return true;
 }
 
