@@ -88,9 +88,10 @@ typedef struct {
     int smoother;          /* post-smoother: 0 (default) smoother_steps MR steps, each scaled by omega;
                               1 one GMRES(smoother_steps) application scaled by omega (Sec. III-IV:
                               GMRES(4)), smoother_steps <= 16, FP32/FP64 storage */
-    int smoother_fp16;     /* MG_FP16 only, storage of the smoother's spinors and links: 0 (default)
-                              FP16 when the FP32 smoother working set (links + 3 spinors, 576 B per
-                              site) exceeds the device L2, else FP32; 1 always FP16; 2 never */
+    int smoother_fp16;     /* MG_FP16 only, storage of the smoother's spinors and links (MR) or of its
+                              Arnoldi basis (GMRES): 0 (default) FP16 when the FP32 working set
+                              (MR: links + 3 spinors, 576 B per site; GMRES: k + 1 spinors, 96 B
+                              each) exceeds the device L2, else FP32; 1 always FP16; 2 never */
 } mg_params;
 
 typedef struct {

@@ -235,6 +235,108 @@ __global__ void k_links_to_half(uint2* __restrict__ U16, const float2* __restric
     }
 }
 
+// ---------------------------------------------------------------- GMRES basis in FP16 storage
+// Vector j of the basis: pairs B[j][X][6][l] and per-site scales S[j][X][l] (the
+// HalfSpinor layout); column j of the Hessenberg matrix in the scalars as in the
+// FP32 smoother (rslot).  Normalising a vector only rescales its site scales.
+namespace {
+__device__ __forceinline__ int rslot_h(int j, int k) { return S_GCR_R + 2 * (k * K_MAX + j); }
+}
+template <int NJ>
+__global__ void __launch_bounds__(kHalfThreads) k_h_multidot(const uint2* __restrict__ B, const float* __restrict__ S,
+                                                              Geom g, int k, Reduce R) {
+    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    float a[2 * NJ];
+#pragma unroll
+    for (int j = 0; j < 2 * NJ; ++j) a[j] = 0.f;
+    if (s < g.V) {
+        const int X = (int)(s / g.Vb), l = (int)(s - (long long)X * g.Vb);
+        const size_t self6 = (size_t)X * 6 * g.Vb + l, V6 = (size_t)6 * g.V;
+        cx<float> w[12];
+        ld_site_h(B + (size_t)k * V6 + self6, S[(size_t)k * g.V + s], g.Vb, w);
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            if (j < k) {
+                cx<float> v[12];
+                ld_site_h(B + (size_t)j * V6 + self6, S[(size_t)j * g.V + s], g.Vb, v);
+                cx<float> t(0.f, 0.f);
+#pragma unroll
+                for (int q = 0; q < 12; ++q) cmadc(t, v[q], w[q]);
+                a[2 * j] = t.r;
+                a[2 * j + 1] = t.i;
+            }
+        }
+    }
+    grid_reduce<2 * NJ, float>(a, R.partials, R.ticket, [&](double (&t)[2 * NJ]) {
+        for (int j = 0; j < k && j < NJ; ++j) {
+            R.scal[rslot_h(j, k)] = t[2 * j];
+            R.scal[rslot_h(j, k) + 1] = t[2 * j + 1];
+        }
+    });
+}
+// basis[k] -= sum_{j<k} h_jk basis[j] (h from the scalars), stored again in FP16
+// with new site scales; scal[S_GCR_PN2] = |basis[k]|^2 of the stored vector
+__global__ void __launch_bounds__(kHalfThreads) k_h_orth(uint2* __restrict__ B, float* __restrict__ S, Geom g, int k,
+                                                          Reduce R) {
+    __shared__ double beta[2 * K_MAX];
+    for (int j = threadIdx.x; j < 2 * k; j += blockDim.x) beta[j] = R.scal[S_GCR_R + 2 * k * K_MAX + j];
+    __syncthreads();
+    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    float a = 0.f;
+    if (s < g.V) {
+        const int X = (int)(s / g.Vb), l = (int)(s - (long long)X * g.Vb);
+        const size_t self6 = (size_t)X * 6 * g.Vb + l, V6 = (size_t)6 * g.V;
+        cx<float> w[12];
+        ld_site_h(B + (size_t)k * V6 + self6, S[(size_t)k * g.V + s], g.Vb, w);
+        for (int j = 0; j < k; ++j) {
+            cx<float> v[12];
+            ld_site_h(B + (size_t)j * V6 + self6, S[(size_t)j * g.V + s], g.Vb, v);
+            const cx<float> b((float)beta[2 * j], (float)beta[2 * j + 1]);
+#pragma unroll
+            for (int q = 0; q < 12; ++q) w[q] = w[q] - b * v[q];
+        }
+        store_site_h(B + (size_t)k * V6 + self6, S + (size_t)k * g.V + s, w, g.Vb,
+                     [&](int, cx<float> q) { a += norm2(q); });
+    }
+    float acc[1] = {a};
+    grid_reduce<1, float>(acc, R.partials, R.ticket, [&](double (&t)[1]) { R.scal[S_GCR_PN2] = t[0]; });
+}
+// normalise basis[k]: its site scales times 1 / sqrt(scal[S_GCR_PN2]); h_{k,k-1} recorded
+__global__ void k_h_normalize(float* __restrict__ Sk, long long n, int k, double* scal) {
+    const double nk = sqrt(scal[S_GCR_PN2]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        scal[rslot_h(k, k)] = nk;
+        scal[rslot_h(k, k) + 1] = 0.0;
+    }
+    const float f = (float)(nk > 0 ? 1.0 / nk : 0.0);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        Sk[i] *= f;
+}
+// z += sum_{j<k} c_j basis[j], c_j = scal[S_GCR_C + 2j]
+__global__ void __launch_bounds__(kHalfThreads) k_h_multi_axpy(float2* __restrict__ z, const uint2* __restrict__ B,
+                                                                const float* __restrict__ S, Geom g, int k,
+                                                                const double* __restrict__ scal) {
+    __shared__ float c[2 * K_MAX];
+    for (int j = threadIdx.x; j < 2 * k; j += blockDim.x) c[j] = (float)scal[S_GCR_C + j];
+    __syncthreads();
+    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (s >= g.V) return;
+    const int X = (int)(s / g.Vb), l = (int)(s - (long long)X * g.Vb);
+    const size_t self = (size_t)X * 12 * g.Vb + l, self6 = (size_t)X * 6 * g.Vb + l, V6 = (size_t)6 * g.V;
+    cx<float> acc[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) acc[q] = ld<float>(z + self + (size_t)q * g.Vb);
+    for (int j = 0; j < k; ++j) {
+        cx<float> v[12];
+        ld_site_h(B + (size_t)j * V6 + self6, S[(size_t)j * g.V + s], g.Vb, v);
+        const cx<float> cj(c[2 * j], c[2 * j + 1]);
+#pragma unroll
+        for (int q = 0; q < 12; ++q) cmad(acc[q], cj, v[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 12; ++q) st<float>(z + self + (size_t)q * g.Vb, acc[q]);
+}
+
 // ---------------------------------------------------------------- launchers
 void links_to_half(uint2* U16, const float2* U32, const Geom& g, cudaStream_t st) {
     const long long n = 4LL * g.Vc * 5 * g.Vb;
@@ -265,6 +367,25 @@ void dslash_h_mrdot(HalfSpinor out, ConstHalfSpinor in, const uint2* U16, const 
     note_launch();
     k_dslash_h<HMODE_MRDOT, true><<<half_grid(g.V), kHalfThreads, 0, st>>>(out.v, out.s, in.v, in.s, U16, nullptr, g,
                                                                           (float)(4.0 + mass), omega, R);
+}
+void h_multidot(const uint2* B, const float* S, const Geom& g, int k, const Reduce& R, cudaStream_t st) {
+    note_launch();
+    if (k <= 4) k_h_multidot<4><<<half_grid(g.V), kHalfThreads, 0, st>>>(B, S, g, k, R);
+    else if (k <= 8) k_h_multidot<8><<<half_grid(g.V), kHalfThreads, 0, st>>>(B, S, g, k, R);
+    else k_h_multidot<16><<<half_grid(g.V), kHalfThreads, 0, st>>>(B, S, g, k, R);
+}
+void h_orth(uint2* B, float* S, const Geom& g, int k, const Reduce& R, cudaStream_t st) {
+    note_launch();
+    k_h_orth<<<half_grid(g.V), kHalfThreads, 0, st>>>(B, S, g, k, R);
+}
+void h_normalize(float* S, const Geom& g, int k, const Reduce& R, cudaStream_t st) {
+    note_launch();
+    k_h_normalize<<<(int)std::min<long long>((g.V + 255) / 256, 152 * 8), 256, 0, st>>>(S + (size_t)k * g.V, g.V, k,
+                                                                                         R.scal);
+}
+void h_multi_axpy(float2* z, const uint2* B, const float* S, const Geom& g, int k, const Reduce& R, cudaStream_t st) {
+    note_launch();
+    k_h_multi_axpy<<<half_grid(g.V), kHalfThreads, 0, st>>>(z, B, S, g, k, R.scal);
 }
 void mr_update_h(float2* e, HalfSpinor r, ConstHalfSpinor q, const Geom& g, bool update_r, const Reduce& R,
                  cudaStream_t st) {

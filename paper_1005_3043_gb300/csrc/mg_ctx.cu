@@ -141,6 +141,9 @@ struct mg_ctx {
     uint2* U16 = nullptr;           // FP16 links (built on demand from U32)
     bool u16_valid = false;
     uint2 *h_r = nullptr, *h_q = nullptr;     // FP16 smoother vectors r, q (+ per-site scales)
+    uint2* h_basis = nullptr;                 // FP16 GMRES basis, h_bk + 1 vectors (+ site scales)
+    float* h_bscale = nullptr;
+    int h_bk = 0;
     float *h_sr = nullptr, *h_sq = nullptr;
 };
 
@@ -479,6 +482,19 @@ bool smoother_fp16(mg_ctx* ctx) {
     return (double)ctx->g.V * 576.0 > (double)l2;
 }
 
+// MG_FP16 with the GMRES smoother: whether its Arnoldi basis is stored in FP16.
+// Its Gram-Schmidt passes re-read the whole basis, so FP16 pays when the FP32
+// basis ((k + 1) x 96 B per site) would not stay in L2 (smoother_fp16 0), or
+// always (1), or never (2).
+bool gmres_fp16(mg_ctx* ctx, int k) {
+    if (!ctx->coarse16 || ctx->prm.smoother_fp16 == 2) return false;
+    if (ctx->prm.smoother_fp16 == 1) return true;
+    int dev = 0, l2 = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+    return (double)ctx->g.V * 96.0 * (k + 1) > (double)l2;
+}
+
 // Post-smoothing of the V(0,n) cycle (Sec. III): r_s = r - D z, then n MR steps
 // q = D r_s, alpha = omega <q,r_s>/<q,q>, z += alpha r_s, r_s -= alpha q.  In
 // MG_FP16 mode r_s and q are stored in FP16 with a per-site scale and the
@@ -488,6 +504,48 @@ int smooth(mg_ctx* ctx, const v2<T>* r, v2<T>* z, const Reduce& R, Counters& cnt
     Work<T>& w = work<T>(ctx);
     const size_t n = nfine(ctx);
     const int steps = ctx->prm.smoother_steps;
+    if (std::is_same<T, float>::value && ctx->prm.smoother == 1 && steps > 0 && gmres_fp16(ctx, steps)) {
+        // GMRES(steps) with the Arnoldi basis in FP16 storage (pairs + site scales): the
+        // same algorithm, the basis (steps + 1) x 52 B per site instead of 96 B
+        TRY(ensure_fine16(ctx));
+        const size_t V = (size_t)ctx->g.V;
+        if (ctx->h_bk < steps) {
+            if (ctx->h_basis) { dfree(ctx, ctx->h_basis); dfree(ctx, ctx->h_bscale); ctx->h_basis = nullptr; }
+            TRY(dalloc(ctx, &ctx->h_basis, sizeof(uint2) * 6 * V * (size_t)(steps + 1)));
+            TRY(dalloc(ctx, &ctx->h_bscale, sizeof(float) * V * (size_t)(steps + 1)));
+            ctx->h_bk = steps;
+        }
+        Reduce Rs = R;
+        Rs.scal = ctx->scal_s;
+        uint2* B = ctx->h_basis;
+        float* S = ctx->h_bscale;
+        float2* zf = reinterpret_cast<float2*>(z);
+        PROF_BEGIN(MG_K_DSLASH);
+        dslash_h_xmy(HalfSpinor{B, S}, zf, ctx->U16, reinterpret_cast<const float2*>(r), ctx->g, ctx->mass, ctx->st);
+        PROF_END(MG_K_DSLASH);
+        PROF_BEGIN(MG_K_KRYLOV);
+        h_orth(B, S, ctx->g, 0, Rs, ctx->st);        // no projection for k = 0: |v_0|^2
+        h_normalize(S, ctx->g, 0, Rs, ctx->st);
+        PROF_END(MG_K_KRYLOV);
+        for (int j = 0; j < steps; ++j) {
+            HalfSpinor out{B + (size_t)(j + 1) * 6 * V, S + (size_t)(j + 1) * V};
+            PROF_BEGIN(MG_K_DSLASH);
+            dslash_h_plain(out, ConstHalfSpinor(B + (size_t)j * 6 * V, S + (size_t)j * V), ctx->U16, ctx->g, ctx->mass,
+                           ctx->st);
+            PROF_END(MG_K_DSLASH);
+            PROF_BEGIN(MG_K_KRYLOV);
+            h_multidot(B, S, ctx->g, j + 1, Rs, ctx->st);
+            h_orth(B, S, ctx->g, j + 1, Rs, ctx->st);
+            h_normalize(S, ctx->g, j + 1, Rs, ctx->st);
+            PROF_END(MG_K_KRYLOV);
+        }
+        PROF_BEGIN(MG_K_KRYLOV);
+        gmres_ls(Rs, steps, ctx->prm.omega, ctx->st);
+        h_multi_axpy(zf, B, S, ctx->g, steps, Rs, ctx->st);
+        PROF_END(MG_K_KRYLOV);
+        cnt.matvecs += steps + 1;
+        return MG_OK;
+    }
     if (ctx->prm.smoother == 1 && steps > 0) {
         // one GMRES(steps) application, under-relaxed by omega (Sec. III-IV):
         // Arnoldi with one classical Gram-Schmidt pass per vector, the small

@@ -163,6 +163,14 @@ void dslash_h_xmy(HalfSpinor out, const float2* in, const uint2* U16, const floa
 // out = D in, scal[S_MR_ALPHA..+1] = omega <out, in> / |out|^2 of the stored out
 void dslash_h_mrdot(HalfSpinor out, ConstHalfSpinor in, const uint2* U16, const Geom& g, double mass, double omega,
                     const Reduce& R, cudaStream_t st);
+// GMRES basis in FP16 storage: B[j] / S[j] = vector j in the HalfSpinor layout
+// (6 V pair words, V site scales each); dots of basis[k] with basis[j < k] into the
+// Hessenberg scalars, Gram-Schmidt update of basis[k] (and its norm^2 into
+// S_GCR_PN2), normalisation by rescaling the site scales, z += sum c_j basis[j]
+void h_multidot(const uint2* B, const float* S, const Geom& g, int k, const Reduce& R, cudaStream_t st);
+void h_orth(uint2* B, float* S, const Geom& g, int k, const Reduce& R, cudaStream_t st);
+void h_normalize(float* S, const Geom& g, int k, const Reduce& R, cudaStream_t st);
+void h_multi_axpy(float2* z, const uint2* B, const float* S, const Geom& g, int k, const Reduce& R, cudaStream_t st);
 // e += alpha r; r -= alpha q when update_r (alpha from scal[S_MR_ALPHA])
 void mr_update_h(float2* e, HalfSpinor r, ConstHalfSpinor q, const Geom& g, bool update_r, const Reduce& R,
                  cudaStream_t st);

@@ -323,13 +323,17 @@ def test_fp16_fine_storage_dslash_and_mr():
     assert maxrel(r16, r_true) < 1e-2
 
 
+@pytest.mark.parametrize("smoother", [0, 1])
 @pytest.mark.parametrize("smoother_fp16", [1, 2])
-def test_fp16_mode_solve_with_each_smoother_storage(c1, smoother_fp16):
-    """MG_FP16 solves with the smoother's spinors and links in FP16 (1) or FP32 (2)
-    both reach a true FP64 residual of 1e-10."""
+def test_fp16_mode_solve_with_each_smoother_storage(c1, smoother_fp16, smoother):
+    """MG_FP16 solves with the smoother's storage in FP16 (1) or FP32 (2) — the MR
+    smoother's spinors and links, or the GMRES(8) smoother's Arnoldi basis — all
+    reach a true FP64 residual of 1e-10."""
     L, B, nv, U, m = c1["L"], c1["B"], c1["nv"], c1["U"], c1["m"]
     b = synth.gaussian_spinor(L, 7)
-    with wmg.WilsonMG(L, make_params(nv, B, prec_inner=wmg.MG_FP16, delta=1e-4, smoother_fp16=smoother_fp16)) as mg:
+    steps = 8 if smoother else 4
+    with wmg.WilsonMG(L, make_params(nv, B, prec_inner=wmg.MG_FP16, delta=1e-4, smoother_fp16=smoother_fp16,
+                                     smoother=smoother, smoother_steps=steps)) as mg:
         mg.set_links(U)
         mg.set_mass(m)
         mg.set_null_vectors(c1["Vs"])
