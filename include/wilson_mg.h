@@ -92,6 +92,10 @@ typedef struct {
                               Arnoldi basis (GMRES): 0 (default) FP16 when the FP32 working set
                               (MR: links + 3 spinors, 576 B per site; GMRES: k + 1 spinors, 96 B
                               each) exceeds the device L2, else FP32; 1 always FP16; 2 never */
+    int coarse_form;       /* iteration form of the on-chip coarse solve (coarse_kernel 0, 2, 3):
+                              0 (default) Chronopoulos-Gear form, one grid-wide exchange and one
+                              neighbour barrier per iteration; 1 textbook CGLS, two grid-wide
+                              exchanges per iteration.  Same iterates in exact arithmetic */
 } mg_params;
 
 typedef struct {
@@ -107,7 +111,7 @@ typedef struct {
 /* Fill p with the defaults: block 4^4, nvec 8, relax 10, iters 3, group 4,
  * smoother 4, omega 0.9, restart 16, tol 1e-10, coarse_tol 1e-3,
  * max_outer 1000, max_coarse 5000, delta 0, FP64, coarse_check 16, coarse_kernel 0,
- * smoother 0 (MR), smoother_fp16 0. */
+ * smoother 0 (MR), smoother_fp16 0, coarse_form 0. */
 int mg_default_params(mg_params* p);
 
 /* Create a context for an L0 x L1 x L2 x L3 lattice.  dims[mu] must be a

@@ -41,7 +41,8 @@ class MgParams(ctypes.Structure):
                 ("omega", ctypes.c_double), ("gcr_restart", ctypes.c_int), ("tol", ctypes.c_double),
                 ("coarse_tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("max_coarse", ctypes.c_int),
                 ("delta", ctypes.c_double), ("prec_inner", ctypes.c_int), ("coarse_check", ctypes.c_int),
-                ("coarse_kernel", ctypes.c_int), ("smoother", ctypes.c_int), ("smoother_fp16", ctypes.c_int)]
+                ("coarse_kernel", ctypes.c_int), ("smoother", ctypes.c_int), ("smoother_fp16", ctypes.c_int),
+                ("coarse_form", ctypes.c_int)]
 
 
 class MgSolveInfo(ctypes.Structure):

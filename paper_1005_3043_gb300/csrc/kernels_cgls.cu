@@ -35,7 +35,7 @@
 namespace wmg {
 
 constexpr int kCglsThreads = 512;
-constexpr int kXchScratch = 2 * (32 + kXchMaxGrid + 1);   // floats for xch_allreduce<2>
+constexpr int kXchScratch = kXchMaxNV * (32 + kXchMaxGrid + 1);   // floats for xch_allreduce<3>
 constexpr long long kCopyWaitLimit = 4000000LL;   // polls of a bulk-copy mbarrier before giving up
 
 // Four consecutive rows a..a+3 of one column of a unit, as complex FP32 pairs
@@ -87,8 +87,14 @@ struct CglsPhase {
     float2* out;
     float coef;            // beta (ST_P) or alpha (ST_R)
     bool first;
+    // EPI_CG (the second stencil of the one-exchange form): out = w = D_c^dag u is
+    // not stored; p = s + beta p, z = w + beta z, q = u + beta q, y += alpha p,
+    // r -= alpha q, s -= alpha z on the own rows (first: no beta terms)
+    float2 *cs, *cp, *cz, *cq, *cu, *cy, *cr;
+    float alpha, beta;
 };
 enum { ST_IN = 0, ST_P = 1, ST_R = 2 };
+enum { EPI_STORE = 0, EPI_CG = 1 };
 
 constexpr int kStageRegs = 4;   // staged operand entries per thread kept as precomputed offsets
 
@@ -271,13 +277,41 @@ template <bool H16, bool TM> struct CglsCta {
         return v;
     }
 
+    // output row o = X * nc + row of the stencil: EPI_STORE stores it (n0 += |out|^2);
+    // EPI_CG applies the one-exchange updates (n0 += |s'|^2, n1 += |r'|^2)
+    template <int EPI> __device__ __forceinline__ void emit(const CglsPhase& ph, size_t o, cx<float> w, float& n0,
+                                                            float& n1) {
+        if (EPI == EPI_STORE) {
+            st<float>(ph.out + o, w);
+            n0 += norm2(w);
+        } else {
+            const cx<float> s = ld<float>(ph.cs + o), u = ld<float>(ph.cu + o);
+            cx<float> p = s, z = w, q = u;
+            if (!ph.first) {
+                p = p + ph.beta * ld<float>(ph.cp + o);
+                z = z + ph.beta * ld<float>(ph.cz + o);
+                q = q + ph.beta * ld<float>(ph.cq + o);
+            }
+            const cx<float> sn = s - ph.alpha * z, rn = ld<float>(ph.cr + o) - ph.alpha * q;
+            st<float>(ph.cp + o, p);
+            st<float>(ph.cz + o, z);
+            st<float>(ph.cq + o, q);
+            st<float>(ph.cy + o, ld<float>(ph.cy + o) + ph.alpha * p);
+            st<float>(ph.cr + o, rn);
+            st<float>(ph.cs + o, sn);
+            n0 += norm2(sn);
+            n1 += norm2(rn);
+        }
+    }
+
     // One stencil application out = D_c (or D_c^dag) x on the CTA's rows, the
     // operand x formed while staging:
     //   ST_IN: x = in
     //   ST_P : x = s + beta p_old (first: s); own entries -> p_new
     //   ST_R : x = r_old - alpha q; own entries -> r_new, y += alpha p_new, n1 += |x|^2
     // n0 accumulates |out|^2 over the CTA's rows.
-    template <int STAGE, bool DAG> __device__ void phase(const CglsPhase& ph, float& n0, float& n1) {
+    template <int STAGE, bool DAG, int EPI = EPI_STORE>
+    __device__ void phase(const CglsPhase& ph, float& n0, float& n1) {
         const int T = blockDim.x;
         if (pre) {
             cx<float> v[kStageRegs];
@@ -342,8 +376,7 @@ template <bool H16, bool TM> struct CglsCta {
                 for (int ks = 1; ks < q_KS; ++ks) sum = sum + red[ks * rows + rr];
                 const int jj = rr / RU, ain = rr - jj * RU, u = u0 + jj, X = u / H, row = (u - X * H) * RU + ain;
                 if (DAG && row >= nvh) sum = cx<float>(-sum.r, -sum.i);
-                st<float>(ph.out + (size_t)X * nc + row, sum);
-                n0 += norm2(sum);
+                emit<EPI>(ph, (size_t)X * nc + row, sum, n0, n1);
             }
             return;
         }
@@ -395,8 +428,7 @@ template <bool H16, bool TM> struct CglsCta {
                 for (int ks = 1; ks < KS; ++ks) sum = sum + rb[ks * rows + r];
                 const int j = r / RU, ain = r - j * RU, u = u0 + j0 + j, X = u / H, row = (u - X * H) * RU + ain;
                 if (DAG && row >= nvh) sum = cx<float>(-sum.r, -sum.i);
-                st<float>(ph.out + (size_t)X * nc + row, sum);
-                n0 += norm2(sum);
+                emit<EPI>(ph, (size_t)X * nc + row, sum, n0, n1);
             }
             if (!resident) buf ^= 1;
         }
@@ -470,11 +502,112 @@ template <bool H16, bool TM> __device__ void cgls_body(const CglsArgs& a, CglsCt
     }
 }
 
+// The same CG on D_c^dag D_c in the Chronopoulos-Gear arrangement (same
+// iterates in exact arithmetic): with u = D_c s and w = D_c^dag u = D_c^dag D_c s,
+// both scalars of an iteration come from the first stencil,
+//   gamma = |s|^2,  delta = <w, s> = |u|^2,  beta = gamma/gamma_old,
+//   alpha = gamma / (delta - beta gamma / alpha_old)   (first: gamma/delta),
+// and the recurrences p = s + beta p, z = w + beta z (= D^dag D p),
+// q = u + beta q (= D p), y += alpha p, r -= alpha q, s -= alpha z follow the
+// second.  Per iteration: u = D_c s; one exchange of (|u|^2, |s|^2, |r|^2);
+// w = D_c^dag u with the updates in its epilogue; a barrier with the neighbour
+// CTAs only (the next stencil reads s on the CTA's aggregates and their
+// neighbours).  |r|^2 is that of the current r, so convergence is seen one
+// stencil later than in the textbook form, with the same iteration count.
+template <bool H16, bool TM> __device__ void cgls_body_cg(const CglsArgs& a, CglsCta<H16, TM>& c) {
+    __shared__ unsigned int nbmask[kXchMaxGrid / 32];
+    unsigned int ex = a.epoch0, en = a.epoch0;   // exchange and neighbour-flag epochs
+    float* shr = reinterpret_cast<float*>(c.xs + (size_t)a.sh.nx_max * c.K);
+    unsigned long long* flags = a.xch + kXchFlagOffset;
+    // the CTAs owning a unit of an aggregate this CTA stages (its own aggregates
+    // and their neighbours); the relation is symmetric
+    for (int i = threadIdx.x; i < kXchMaxGrid / 32; i += blockDim.x) nbmask[i] = 0u;
+    __syncthreads();
+    {
+        const long long NU = (long long)a.g.Vc * c.H, G = gridDim.x;
+        for (int i = threadIdx.x; i < c.nX * 9; i += blockDim.x) {
+            const int X = c.X0 + i / 9, d = i - (i / 9) * 9;
+            const long long Y = __ldg(a.nbr + (size_t)X * 9 + d);
+            const long long ua = Y * c.H, ub = Y * c.H + c.H - 1;
+            const int ca = (int)(((ua + 1) * G + NU - 1) / NU - 1), cb = (int)(((ub + 1) * G + NU - 1) / NU - 1);
+            for (int cc = ca; cc <= cb; ++cc)
+                if (cc != (int)blockIdx.x) atomicOr(&nbmask[cc >> 5], 1u << (cc & 31));
+        }
+    }
+    // y = 0, r = rc on the own rows; |rc|^2
+    float one[1] = {0.f};
+    for (int i = threadIdx.x; i < c.nu * c.RU; i += blockDim.x) {
+        const int j = i / c.RU, ain = i - j * c.RU, u = c.u0 + j, X = u / c.H;
+        const size_t o = (size_t)X * c.nc + (u - X * c.H) * c.RU + ain;
+        const float2 v = a.rc[o];
+        a.r[o] = v;
+        a.y[o] = make_float2(0.f, 0.f);
+        one[0] += v.x * v.x + v.y * v.y;
+    }
+    const float rpart0 = one[0];
+    if (!xch_allreduce<1>(one, a.xch, ex++, a.err, shr)) return;
+    const float rc2 = one[0];
+    int it = 0;
+    float r2 = rc2;
+    if (rc2 > 0.f && a.maxit > 0) {
+        float2 *s = a.s, *p = a.p, *q = a.q, *u = a.r1, *z = a.p1;
+        CglsPhase ph{};
+        float n0 = 0.f, n1 = 0.f;
+        // s = D_c^dag r, own |s|^2
+        ph.in = a.r;
+        ph.out = s;
+        c.template phase<ST_IN, true>(ph, n0, n1);
+        float gpart = n0, rpart = rpart0;
+        if (!neighbour_sync(flags, nbmask, en++, a.err)) return;
+        float gamma_old = 0.f, alpha_old = 0.f;
+        for (int i = 0;; ++i) {
+            ph = CglsPhase{};
+            ph.in = s;
+            ph.out = u;
+            n0 = 0.f; n1 = 0.f;
+            c.template phase<ST_IN, false>(ph, n0, n1);   // u = D_c s
+            float three[3] = {n0, gpart, rpart};
+            if (!xch_allreduce<3>(three, a.xch, ex++, a.err, shr)) return;
+            const float delta = three[0], gamma = three[1];
+            r2 = three[2];
+            it = i;
+            if ((i > 0 && r2 <= a.tol2 * rc2) || i >= a.maxit) break;
+            const float beta = i > 0 ? gamma / gamma_old : 0.f;
+            const float den = i > 0 ? delta - beta * gamma / alpha_old : delta;
+            if (!(gamma > 0.f) || !(den > 0.f)) break;
+            const float alpha = gamma / den;
+            ph = CglsPhase{};
+            ph.in = u;
+            ph.cs = s; ph.cp = p; ph.cz = z; ph.cq = q; ph.cu = u; ph.cy = a.y; ph.cr = a.r;
+            ph.alpha = alpha;
+            ph.beta = beta;
+            ph.first = (i == 0);
+            n0 = 0.f; n1 = 0.f;
+            c.template phase<ST_IN, true, EPI_CG>(ph, n0, n1);   // w = D_c^dag u and the updates
+            gpart = n0;
+            rpart = n1;
+            gamma_old = gamma;
+            alpha_old = alpha;
+            if (!neighbour_sync(flags, nbmask, en++, a.err)) return;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.scal[S_CG_ITERS] = (double)it;
+        a.scal[S_CG_R2] = (double)r2;
+        a.scal[S_CG_RC2] = (double)rc2;
+        a.scal[S_CG_DONE] = 1.0;
+        a.scal[S_CG_TOTAL] += (double)it;
+    }
+}
+
 template <bool H16, bool TM> __global__ void __launch_bounds__(kCglsThreads, 1) k_cgls_onchip(CglsArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     CglsCta<H16, TM> c(a, smem_raw);
     c.start();
-    cgls_body<H16, TM>(a, c);
+    if (a.form == CGLS_CG_ONE_EXCHANGE)
+        cgls_body_cg<H16, TM>(a, c);
+    else
+        cgls_body<H16, TM>(a, c);
     c.drain();   // no copy may still be writing shared memory, and no TMEM stays allocated, when the CTA exits
 }
 

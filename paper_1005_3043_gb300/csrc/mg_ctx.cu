@@ -406,6 +406,7 @@ int coarse_solve(mg_ctx* ctx, const CoarseLevel& L, const v2<T>* rc, v2<T>* y, d
         }
         c.xch = ctx->xch;
         c.epoch0 = ctx->xch_epoch;
+        c.form = ctx->prm.coarse_form == 1 ? CGLS_TEXTBOOK : CGLS_CG_ONE_EXCHANGE;
         ctx->xch_epoch += (unsigned int)reserve;
         CK(cudaMemsetAsync(ctx->bar, 0, sizeof(unsigned int) * 3, ctx->st));
         PROF_BEGIN(MG_K_COARSE_SOLVE);
@@ -835,6 +836,7 @@ int check_params(const int dims[4], const mg_params* p, std::string& why) {
     if (p->prec_inner == MG_FP16 && p->nvec % 2 != 0) { why = "MG_FP16 needs an even nvec"; return MG_ERR_INVALID_ARG; }
     if (p->coarse_kernel < 0 || p->coarse_kernel > 3) { why = "coarse_kernel must be 0, 1, 2 or 3"; return MG_ERR_INVALID_ARG; }
     if (p->smoother_fp16 < 0 || p->smoother_fp16 > 2) { why = "smoother_fp16 must be 0, 1 or 2"; return MG_ERR_INVALID_ARG; }
+    if (p->coarse_form < 0 || p->coarse_form > 1) { why = "coarse_form must be 0 or 1"; return MG_ERR_INVALID_ARG; }
     if (p->smoother < 0 || p->smoother > 1) { why = "smoother must be 0 (MR) or 1 (GMRES)"; return MG_ERR_INVALID_ARG; }
     if (p->smoother == 1 && p->smoother_steps > 16) { why = "GMRES smoother: smoother_steps <= 16"; return MG_ERR_INVALID_ARG; }
     return MG_OK;

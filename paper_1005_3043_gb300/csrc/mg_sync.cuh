@@ -117,16 +117,18 @@ __device__ __forceinline__ bool xch_wait(const unsigned long long* slot, unsigne
 // a hot spot (measured: 4.2 us from the last publish to the first CTA through,
 // 2.3 us with one slot per line).
 constexpr int kXchPad = 16;
+constexpr int kXchMaxNV = 3;
 // v[j] (this thread's share) -> the grid-wide sums, identical in every CTA.
-// slots: [parity 2][value 2][G][kXchPad]; needs NV * G <= blockDim.x.
+// slots: [parity 2][value kXchMaxNV][G][kXchPad]; the parity is that of e, so
+// consecutive calls must use consecutive epochs.
 // sc: shared scratch of at least NV * (32 + G + 1) floats, free during the call.
 // Three CTA barriers for any NV: warp partial sums -> thread 0 publishes;
 // polled values -> one warp per value sums them in CTA order.
 template <int NV>
 __device__ bool xch_allreduce(float (&v)[NV], unsigned long long* slots, unsigned int e, int* err, float* sc) {
-    static_assert(NV >= 1 && NV <= 2, "one or two values per exchange");
+    static_assert(NV >= 1 && NV <= kXchMaxNV, "one to three values per exchange");
     const int G = gridDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
-    unsigned long long* base = slots + (size_t)(e & 1) * 2 * G * kXchPad;
+    unsigned long long* base = slots + (size_t)(e & 1) * kXchMaxNV * G * kXchPad;
     float* wsum = sc;                  // [NV][32] warp partials
     float* gv = sc + NV * 32;          // [NV * G] polled CTA sums
     float* res = gv + NV * G;          // [NV] grid sums
@@ -148,11 +150,11 @@ __device__ bool xch_allreduce(float (&v)[NV], unsigned long long* slots, unsigne
 #pragma unroll
         for (int j = 0; j < NV; ++j) xch_publish(base + ((size_t)j * G + blockIdx.x) * kXchPad, cta[j], e);
     }
-    float got = 0.f;
     bool ok = true;
-    if (t < NV * G) {
-        ok = xch_wait(base + (size_t)t * kXchPad, e, err, got);
-        gv[t] = got;
+    for (int i = t; i < NV * G && ok; i += blockDim.x) {
+        float got = 0.f;
+        ok = xch_wait(base + (size_t)i * kXchPad, e, err, got);
+        gv[i] = got;
     }
     if (__syncthreads_or(!ok)) return false;
     if (warp < NV) {
@@ -165,6 +167,40 @@ __device__ bool xch_allreduce(float (&v)[NV], unsigned long long* slots, unsigne
 #pragma unroll
     for (int j = 0; j < NV; ++j) v[j] = res[j];
     return true;
+}
+
+// ---------------------------------------------------------------- neighbour flags
+// Point-to-point barrier with the CTAs whose data this CTA reads (and which read
+// its data): CTA c publishes epoch e in flags[c][0] after its writes, then waits
+// until every CTA in its mask carries an epoch >= e.  Epochs only increase, so
+// a neighbour that is already further on does not hold anyone up.
+__device__ __forceinline__ bool flag_wait(const unsigned long long* flag, unsigned int e, int* err) {
+    long long spins = 0;
+    for (;;) {
+        const unsigned int w = (unsigned int)xch_load(flag);
+        if ((int)(w - e) >= 0) return true;
+        if (*(volatile int*)err) return false;
+        if (++spins > kExchangeSpinLimit) {
+            atomicExch(err, 1);
+            return false;
+        }
+        if (spins > 32) __nanosleep(20);
+    }
+}
+// mask: shared bitmask over the grid's CTAs (bit c of word c / 32)
+__device__ __forceinline__ bool neighbour_sync(unsigned long long* flags, const unsigned int* mask, unsigned int e, int* err) {
+    const int G = gridDim.x, t = threadIdx.x;
+    __syncthreads();
+    if (t == 0) {
+        __threadfence();
+        asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(flags + (size_t)blockIdx.x * kXchPad),
+                     "l"((unsigned long long)e)
+                     : "memory");
+    }
+    bool ok = true;
+    for (int c = t; c < G && ok; c += blockDim.x)
+        if ((mask[c >> 5] >> (c & 31)) & 1u) ok = flag_wait(flags + (size_t)c * kXchPad, e, err);
+    return !__syncthreads_or(!ok);
 }
 
 }  // namespace wmg

@@ -3,7 +3,9 @@ and with the FP16-stored operator, for each coarse kernel: 0 the operator held
 on chip for the whole solve (tensor memory at these sizes), 1 the operator
 read from global memory into registers, 2 the operator streamed through a
 shared-memory ring with several waves per phase, 3 the operator resident in
-shared memory.  References are the FP64 oracle's CGLS on
+shared memory; the on-chip kernels (0, 2, 3) in both iteration forms, the
+Chronopoulos-Gear form with one grid-wide exchange per iteration (coarse_form
+0) and the textbook CGLS (coarse_form 1).  References are the FP64 oracle's CGLS on
 the oracle's own D_c (FP32) or on that D_c rounded to FP16 with one scale per
 (aggregate, direction) block, the storage rule of the FP16 mode."""
 import numpy as np
@@ -16,7 +18,8 @@ from tests._fields import c1_workload
 
 pytestmark = pytest.mark.gpu
 
-KERNELS = (0, 1, 2, 3)
+# (coarse_kernel, coarse_form); the register kernel has one form
+VARIANTS = [(0, 0), (0, 1), (1, 0), (2, 0), (2, 1), (3, 0), (3, 1)]
 # FP32 CG iterates against FP64 after k steps on this operator (condition
 # number ~14): near FP32 rounding for the first steps (1.7e-7 at k = 1 and 7
 # for a complex64 CGLS in numpy), then growing with the loss of conjugacy
@@ -89,7 +92,7 @@ def level_random():
     return dict(L=L, B=B, nv=nv, m=m, U=U, V0=V0, A=A, A16=quantise16(A), Lc=Lc, rc=rc)
 
 
-def _mg(lv, kernel, prec):
+def _mg(lv, kernel, prec, form=0):
     p = wmg.mg_default_params()
     for i in range(4):
         p.block[i] = lv["B"][i]
@@ -97,6 +100,7 @@ def _mg(lv, kernel, prec):
     p.setup_group = 4
     p.prec_inner = prec
     p.coarse_kernel = kernel
+    p.coarse_form = form
     mg = wmg.WilsonMG(lv["L"], p)
     mg.set_links(lv["U"])
     mg.set_mass(lv["m"])
@@ -104,9 +108,9 @@ def _mg(lv, kernel, prec):
     return mg
 
 
-@pytest.mark.parametrize("kernel", KERNELS)
-def test_fixed_iterations_match_oracle_fp32(level, kernel):
-    with _mg(level, kernel, wmg.MG_FP32) as mg:
+@pytest.mark.parametrize("kernel,form", VARIANTS)
+def test_fixed_iterations_match_oracle_fp32(level, kernel, form):
+    with _mg(level, kernel, wmg.MG_FP32, form) as mg:
         for k, tol in FIXED_K_TOL.items():
             y_ref, it_ref, _ = oracle.cgnr(level["A"], level["rc"], level["Lc"], 0.0, k)
             y, it, _ = mg.coarse_solve(level["rc"], 0.0, k, wmg.MG_FP32)
@@ -114,14 +118,14 @@ def test_fixed_iterations_match_oracle_fp32(level, kernel):
             assert maxrel(y, y_ref) < tol, (k, maxrel(y, y_ref))
 
 
-@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("kernel,form", VARIANTS)
 @pytest.mark.parametrize("prec", [wmg.MG_FP32, wmg.MG_FP16])
-def test_fixed_iterations_exact_fp16_rounding(level_random, kernel, prec):
+def test_fixed_iterations_exact_fp16_rounding(level_random, kernel, form, prec):
     """The FP16 operator against the oracle's CGLS on the same entries rounded to
     FP16 (well-conditioned D_c: a few steps reach FP32 rounding, so k <= 6)."""
     lv = level_random
     A = lv["A"] if prec == wmg.MG_FP32 else lv["A16"]
-    with _mg(lv, kernel, prec) as mg:
+    with _mg(lv, kernel, prec, form) as mg:
         for k in (1, 3, 6):
             y_ref, it_ref, _ = oracle.cgnr(A, lv["rc"], lv["Lc"], 0.0, k)
             y, it, _ = mg.coarse_solve(lv["rc"], 0.0, k, prec)
@@ -129,12 +133,12 @@ def test_fixed_iterations_exact_fp16_rounding(level_random, kernel, prec):
             assert maxrel(y, y_ref) < 1e-5, (k, maxrel(y, y_ref))
 
 
-@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("kernel,form", VARIANTS)
 @pytest.mark.parametrize("prec", [wmg.MG_FP32, wmg.MG_FP16])
-def test_converged_solve(level, kernel, prec):
+def test_converged_solve(level, kernel, form, prec):
     A = level["A"] if prec == wmg.MG_FP32 else level["A16"]
     y_ref, it_ref, rel_ref = oracle.cgnr(A, level["rc"], level["Lc"], 1e-3, 5000)
-    with _mg(level, kernel, prec) as mg:
+    with _mg(level, kernel, prec, form) as mg:
         y, it, rel = mg.coarse_solve(level["rc"], 1e-3, 5000, prec)
     assert rel <= 1e-3
     assert abs(it - it_ref) <= 2
@@ -143,22 +147,22 @@ def test_converged_solve(level, kernel, prec):
     assert true_rel <= 1.5e-3, true_rel
 
 
-@pytest.mark.parametrize("kernel", KERNELS)
-def test_zero_rhs_and_zero_iterations(level, kernel):
+@pytest.mark.parametrize("kernel,form", VARIANTS)
+def test_zero_rhs_and_zero_iterations(level, kernel, form):
     z = np.zeros_like(level["rc"])
-    with _mg(level, kernel, wmg.MG_FP32) as mg:
+    with _mg(level, kernel, wmg.MG_FP32, form) as mg:
         y, it, _ = mg.coarse_solve(z, 1e-3, 100, wmg.MG_FP32)
         assert it == 0 and not np.any(y)
         y, it, _ = mg.coarse_solve(level["rc"], 1e-3, 0, wmg.MG_FP32)
         assert it == 0 and not np.any(y)
 
 
-@pytest.mark.parametrize("kernel", KERNELS)
-def test_kernels_agree_in_a_full_solve(level, kernel):
+@pytest.mark.parametrize("kernel,form", VARIANTS)
+def test_kernels_agree_in_a_full_solve(level, kernel, form):
     """Whole MG-GCR solves with each coarse kernel reach 1e-10 in FP64."""
     L, m, U = level["L"], level["m"], level["U"]
     b = synth.gaussian_spinor(L, 7)
-    with _mg(level, kernel, wmg.MG_FP32) as mg:
+    with _mg(level, kernel, wmg.MG_FP32, form) as mg:
         x, info = mg.solve(b)
     assert info["status"] == 0
     r = b - oracle.dslash(U, x, m, L)
