@@ -93,9 +93,10 @@ typedef struct {
                               (MR: links + 3 spinors, 576 B per site; GMRES: k + 1 spinors, 96 B
                               each) exceeds the device L2, else FP32; 1 always FP16; 2 never */
     int coarse_form;       /* iteration form of the on-chip coarse solve (coarse_kernel 0, 2, 3):
-                              0 (default) Chronopoulos-Gear form, one grid-wide exchange and one
-                              neighbour barrier per iteration; 1 textbook CGLS, two grid-wide
-                              exchanges per iteration.  Same iterates in exact arithmetic */
+                              0 (default) Chronopoulos-Gear form, one grid-wide exchange per
+                              iteration, the vectors other SMs read carrying epoch tags instead
+                              of barriers; 1 textbook CGLS, two grid-wide exchanges per
+                              iteration.  Same iterates in exact arithmetic */
 } mg_params;
 
 typedef struct {

@@ -19,11 +19,14 @@
 // pre-multiplied by the FP16 block scales and with the sigma_3 sign flips of
 // D_c^dag = sigma_3 D_c sigma_3 applied.
 //
-// Iteration (textbook CGLS, two grid-wide exchanges of partial sums, which
+// Iteration, two forms with the same iterates in exact arithmetic.
+// Textbook CGLS (cgls_body: two grid-wide exchanges of partial sums, which
 // also serve as the grid barriers):
 //   q = D_c p,  alpha = gamma/|q|^2,  y += alpha p,  r -= alpha q,
 //   s = D_c^dag r,  gamma' = |s|^2,  beta = gamma'/gamma,  p = s + beta p
 // with the vector updates done while staging (p and r double-buffered).
+// Chronopoulos-Gear (cgls_body_tag, the default): one exchange per iteration,
+// the vectors read across CTAs carrying epoch tags instead of barriers.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -87,14 +90,20 @@ struct CglsPhase {
     float2* out;
     float coef;            // beta (ST_P) or alpha (ST_R)
     bool first;
-    // EPI_CG (the second stencil of the one-exchange form): out = w = D_c^dag u is
-    // not stored; p = s + beta p, z = w + beta z, q = u + beta q, y += alpha p,
-    // r -= alpha q, s -= alpha z on the own rows (first: no beta terms)
-    float2 *cs, *cp, *cz, *cq, *cu, *cy, *cr;
+    // epoch-tagged vectors (two 64-bit words per entry): ST_TAG stages tin at
+    // epoch etag; EPI_TAG stores out to tout at epoch etag_out; EPI_CG_TAG (the
+    // second stencil of the Chronopoulos-Gear form): out = w = D_c^dag u is not
+    // stored; p = s + beta p, z = w + beta z, q = u + beta q, y += alpha p,
+    // r -= alpha q, s -= alpha z on the own rows (first: no beta terms), with s
+    // and u in the tagged buffers ts, tu (s' stored at epoch etag_out)
+    float2 *cp, *cz, *cq, *cy, *cr;
     float alpha, beta;
+    const unsigned long long* tin;
+    unsigned long long *tout, *ts, *tu;
+    unsigned int etag, etag_out;
 };
-enum { ST_IN = 0, ST_P = 1, ST_R = 2 };
-enum { EPI_STORE = 0, EPI_CG = 1 };
+enum { ST_IN = 0, ST_P = 1, ST_R = 2, ST_TAG = 3 };
+enum { EPI_STORE = 0, EPI_TAG = 1, EPI_CG_TAG = 2 };
 
 constexpr int kStageRegs = 4;   // staged operand entries per thread kept as precomputed offsets
 
@@ -126,6 +135,7 @@ template <bool H16, bool TM> struct CglsCta {
     int st_o[kStageRegs];
     float st_s[kStageRegs];
     int st_f[kStageRegs];
+    bool sfail = false;   // a tagged staging wait gave up (error flag raised)
 
     __device__ CglsCta(const CglsArgs& args, unsigned char* sm) : a(args) {
         nc = a.nc; K = 9 * nc; nvh = nc >> 1; RU = a.sh.ru; H = nc / RU;
@@ -262,6 +272,10 @@ template <bool H16, bool TM> struct CglsCta {
         cx<float> v;
         if (STAGE == ST_IN) {
             v = ld<float>(ph.in + o);
+        } else if (STAGE == ST_TAG) {
+            float2 t;
+            if (!tag_wait(ph.tin + 2 * (size_t)o, ph.etag, a.err, t)) sfail = true;
+            v = cx<float>(t.x, t.y);
         } else if (STAGE == ST_P) {
             v = ld<float>(ph.s + o);
             if (!ph.first) v = v + ph.coef * ld<float>(ph.p_old + o);
@@ -277,15 +291,21 @@ template <bool H16, bool TM> struct CglsCta {
         return v;
     }
 
-    // output row o = X * nc + row of the stencil: EPI_STORE stores it (n0 += |out|^2);
-    // EPI_CG applies the one-exchange updates (n0 += |s'|^2, n1 += |r'|^2)
+    // output row o = X * nc + row of the stencil: EPI_STORE / EPI_TAG store it
+    // (n0 += |out|^2); EPI_CG_TAG applies the updates (n0 += |s'|^2, n1 += |r'|^2)
     template <int EPI> __device__ __forceinline__ void emit(const CglsPhase& ph, size_t o, cx<float> w, float& n0,
                                                             float& n1) {
         if (EPI == EPI_STORE) {
             st<float>(ph.out + o, w);
             n0 += norm2(w);
-        } else {
-            const cx<float> s = ld<float>(ph.cs + o), u = ld<float>(ph.cu + o);
+        } else if (EPI == EPI_TAG) {
+            tag_store(ph.tout + 2 * o, w.r, w.i, ph.etag_out);
+            n0 += norm2(w);
+        } else if (EPI == EPI_CG_TAG) {
+            float2 s2, u2;
+            tag_load(ph.ts + 2 * o, 0u, s2);   // own entries, written by this CTA
+            tag_load(ph.tu + 2 * o, 0u, u2);
+            const cx<float> s(s2.x, s2.y), u(u2.x, u2.y);
             cx<float> p = s, z = w, q = u;
             if (!ph.first) {
                 p = p + ph.beta * ld<float>(ph.cp + o);
@@ -298,7 +318,7 @@ template <bool H16, bool TM> struct CglsCta {
             st<float>(ph.cq + o, q);
             st<float>(ph.cy + o, ld<float>(ph.cy + o) + ph.alpha * p);
             st<float>(ph.cr + o, rn);
-            st<float>(ph.cs + o, sn);
+            tag_store(ph.ts + 2 * o, sn.r, sn.i, ph.etag_out);
             n0 += norm2(sn);
             n1 += norm2(rn);
         }
@@ -311,13 +331,40 @@ template <bool H16, bool TM> struct CglsCta {
     //   ST_R : x = r_old - alpha q; own entries -> r_new, y += alpha p_new, n1 += |x|^2
     // n0 accumulates |out|^2 over the CTA's rows.
     template <int STAGE, bool DAG, int EPI = EPI_STORE>
-    __device__ void phase(const CglsPhase& ph, float& n0, float& n1) {
+    __device__ bool phase(const CglsPhase& ph, float& n0, float& n1) {
         const int T = blockDim.x;
         if (pre) {
             cx<float> v[kStageRegs];
+            if (STAGE == ST_TAG) {
+                // all loads first, then re-poll only the entries not yet at epoch etag
+                unsigned int okm = 0;
 #pragma unroll
-            for (int q = 0; q < kStageRegs; ++q)
-                if (st_o[q] >= 0) v[q] = form<STAGE>(ph, st_o[q], (st_f[q] & 1) != 0, n1);
+                for (int q = 0; q < kStageRegs; ++q) {
+                    float2 t = make_float2(0.f, 0.f);
+                    if (st_o[q] < 0 || tag_load(ph.tin + 2 * (size_t)st_o[q], ph.etag, t)) okm |= 1u << q;
+                    v[q] = cx<float>(t.x, t.y);
+                }
+                long long spins = 0;
+                while (okm != (1u << kStageRegs) - 1u) {
+#pragma unroll
+                    for (int q = 0; q < kStageRegs; ++q)
+                        if (!((okm >> q) & 1u)) {
+                            float2 t;
+                            if (tag_load(ph.tin + 2 * (size_t)st_o[q], ph.etag, t)) {
+                                okm |= 1u << q;
+                                v[q] = cx<float>(t.x, t.y);
+                            }
+                        }
+                    if (okm == (1u << kStageRegs) - 1u) break;
+                    if (*(volatile int*)a.err) { sfail = true; break; }
+                    if (++spins > kExchangeSpinLimit) { atomicExch(a.err, 1); sfail = true; break; }
+                    if (spins > 32) __nanosleep(20);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < kStageRegs; ++q)
+                    if (st_o[q] >= 0) v[q] = form<STAGE>(ph, st_o[q], (st_f[q] & 1) != 0, n1);
+            }
 #pragma unroll
             for (int q = 0; q < kStageRegs; ++q)
                 if (st_o[q] >= 0) {
@@ -337,7 +384,7 @@ template <bool H16, bool TM> struct CglsCta {
                 xs[i] = w;
             }
         }
-        __syncthreads();
+        if (__syncthreads_or(sfail)) return false;
         const float2* xs2 = reinterpret_cast<const float2*>(xs);
         if (TM) {
             const int rows = nu * RU;
@@ -378,7 +425,7 @@ template <bool H16, bool TM> struct CglsCta {
                 if (DAG && row >= nvh) sum = cx<float>(-sum.r, -sum.i);
                 emit<EPI>(ph, (size_t)X * nc + row, sum, n0, n1);
             }
-            return;
+            return true;
         }
         for (int iw = 0; iw < NW; ++iw) {
             const int j0 = iw * W, n = min(W, nu - j0), rows = n * RU, quads = rows >> 2;
@@ -432,6 +479,7 @@ template <bool H16, bool TM> struct CglsCta {
             }
             if (!resident) buf ^= 1;
         }
+        return true;
     }
 };
 
@@ -510,30 +558,23 @@ template <bool H16, bool TM> __device__ void cgls_body(const CglsArgs& a, CglsCt
 // and the recurrences p = s + beta p, z = w + beta z (= D^dag D p),
 // q = u + beta q (= D p), y += alpha p, r -= alpha q, s -= alpha z follow the
 // second.  Per iteration: u = D_c s; one exchange of (|u|^2, |s|^2, |r|^2);
-// w = D_c^dag u with the updates in its epilogue; a barrier with the neighbour
-// CTAs only (the next stencil reads s on the CTA's aggregates and their
-// neighbours).  |r|^2 is that of the current r, so convergence is seen one
-// stencil later than in the textbook form, with the same iteration count.
-template <bool H16, bool TM> __device__ void cgls_body_cg(const CglsArgs& a, CglsCta<H16, TM>& c) {
-    __shared__ unsigned int nbmask[kXchMaxGrid / 32];
-    unsigned int ex = a.epoch0, en = a.epoch0;   // exchange and neighbour-flag epochs
+// w = D_c^dag u with the updates in its epilogue.  |r|^2 is that of the
+// current r, so convergence is seen one stencil later than in the textbook
+// form, with the same iteration count.
+// No barrier other than the exchange:
+// s and u, the two vectors other CTAs read, live in epoch-tagged buffers
+// (s_i and u_i carry epoch E + i), so a stencil's staging waits for exactly the
+// entries it reads and needs no flag or fence; the exchange of the partial
+// sums publishes with relaxed stores for the same reason.  A writer can never
+// be a whole iteration ahead of a reader of the same entry: it overwrites s
+// (u) only after the exchange (the next s staging) that needs the reader's
+// partial sums, published after the reader's staging.
+template <bool H16, bool TM> __device__ void cgls_body_tag(const CglsArgs& a, CglsCta<H16, TM>& c) {
+    unsigned int ex = a.epoch0;           // exchange epochs
+    const unsigned int E = a.epoch0;      // tag epoch of s_0 and u_0
     float* shr = reinterpret_cast<float*>(c.xs + (size_t)a.sh.nx_max * c.K);
-    unsigned long long* flags = a.xch + kXchFlagOffset;
-    // the CTAs owning a unit of an aggregate this CTA stages (its own aggregates
-    // and their neighbours); the relation is symmetric
-    for (int i = threadIdx.x; i < kXchMaxGrid / 32; i += blockDim.x) nbmask[i] = 0u;
-    __syncthreads();
-    {
-        const long long NU = (long long)a.g.Vc * c.H, G = gridDim.x;
-        for (int i = threadIdx.x; i < c.nX * 9; i += blockDim.x) {
-            const int X = c.X0 + i / 9, d = i - (i / 9) * 9;
-            const long long Y = __ldg(a.nbr + (size_t)X * 9 + d);
-            const long long ua = Y * c.H, ub = Y * c.H + c.H - 1;
-            const int ca = (int)(((ua + 1) * G + NU - 1) / NU - 1), cb = (int)(((ub + 1) * G + NU - 1) / NU - 1);
-            for (int cc = ca; cc <= cb; ++cc)
-                if (cc != (int)blockIdx.x) atomicOr(&nbmask[cc >> 5], 1u << (cc & 31));
-        }
-    }
+    unsigned long long* ts = a.tag;                                  // s: [Vc * nc][2]
+    unsigned long long* tu = a.tag + 2 * (size_t)a.g.Vc * a.nc;      // u
     // y = 0, r = rc on the own rows; |rc|^2
     float one[1] = {0.f};
     for (int i = threadIdx.x; i < c.nu * c.RU; i += blockDim.x) {
@@ -545,29 +586,30 @@ template <bool H16, bool TM> __device__ void cgls_body_cg(const CglsArgs& a, Cgl
         one[0] += v.x * v.x + v.y * v.y;
     }
     const float rpart0 = one[0];
-    if (!xch_allreduce<1>(one, a.xch, ex++, a.err, shr)) return;
+    if (!xch_allreduce<1, false>(one, a.xch, ex++, a.err, shr)) return;
     const float rc2 = one[0];
     int it = 0;
     float r2 = rc2;
     if (rc2 > 0.f && a.maxit > 0) {
-        float2 *s = a.s, *p = a.p, *q = a.q, *u = a.r1, *z = a.p1;
         CglsPhase ph{};
         float n0 = 0.f, n1 = 0.f;
-        // s = D_c^dag r, own |s|^2
-        ph.in = a.r;
-        ph.out = s;
-        c.template phase<ST_IN, true>(ph, n0, n1);
+        // s_0 = D_c^dag rc (rc is the launch's input: no tag needed), own |s_0|^2
+        ph.in = a.rc;
+        ph.tout = ts;
+        ph.etag_out = E;
+        if (!c.template phase<ST_IN, true, EPI_TAG>(ph, n0, n1)) return;
         float gpart = n0, rpart = rpart0;
-        if (!neighbour_sync(flags, nbmask, en++, a.err)) return;
         float gamma_old = 0.f, alpha_old = 0.f;
         for (int i = 0;; ++i) {
             ph = CglsPhase{};
-            ph.in = s;
-            ph.out = u;
+            ph.tin = ts;
+            ph.etag = E + (unsigned int)i;
+            ph.tout = tu;
+            ph.etag_out = E + (unsigned int)i;
             n0 = 0.f; n1 = 0.f;
-            c.template phase<ST_IN, false>(ph, n0, n1);   // u = D_c s
+            if (!c.template phase<ST_TAG, false, EPI_TAG>(ph, n0, n1)) return;   // u = D_c s
             float three[3] = {n0, gpart, rpart};
-            if (!xch_allreduce<3>(three, a.xch, ex++, a.err, shr)) return;
+            if (!xch_allreduce<3, false>(three, a.xch, ex++, a.err, shr)) return;
             const float delta = three[0], gamma = three[1];
             r2 = three[2];
             it = i;
@@ -577,18 +619,20 @@ template <bool H16, bool TM> __device__ void cgls_body_cg(const CglsArgs& a, Cgl
             if (!(gamma > 0.f) || !(den > 0.f)) break;
             const float alpha = gamma / den;
             ph = CglsPhase{};
-            ph.in = u;
-            ph.cs = s; ph.cp = p; ph.cz = z; ph.cq = q; ph.cu = u; ph.cy = a.y; ph.cr = a.r;
+            ph.tin = tu;
+            ph.etag = E + (unsigned int)i;
+            ph.ts = ts; ph.tu = tu;
+            ph.cp = a.p; ph.cz = a.p1; ph.cq = a.q; ph.cy = a.y; ph.cr = a.r;
+            ph.etag_out = E + (unsigned int)i + 1u;
             ph.alpha = alpha;
             ph.beta = beta;
             ph.first = (i == 0);
             n0 = 0.f; n1 = 0.f;
-            c.template phase<ST_IN, true, EPI_CG>(ph, n0, n1);   // w = D_c^dag u and the updates
+            if (!c.template phase<ST_TAG, true, EPI_CG_TAG>(ph, n0, n1)) return;   // w = D_c^dag u, updates
             gpart = n0;
             rpart = n1;
             gamma_old = gamma;
             alpha_old = alpha;
-            if (!neighbour_sync(flags, nbmask, en++, a.err)) return;
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -604,8 +648,8 @@ template <bool H16, bool TM> __global__ void __launch_bounds__(kCglsThreads, 1) 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     CglsCta<H16, TM> c(a, smem_raw);
     c.start();
-    if (a.form == CGLS_CG_ONE_EXCHANGE)
-        cgls_body_cg<H16, TM>(a, c);
+    if (a.form == CGLS_CG_TAGGED)
+        cgls_body_tag<H16, TM>(a, c);
     else
         cgls_body<H16, TM>(a, c);
     c.drain();   // no copy may still be writing shared memory, and no TMEM stays allocated, when the CTA exits
@@ -765,7 +809,8 @@ cudaError_t cgls_onchip(const CglsArgs& args, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         attr[h16][tm] = true;
     }
-    if (args.sh.smem > (size_t)lim.smem - 1024 || args.sh.grid <= 0 || args.sh.grid > lim.sms ||
+    if ((args.form == CGLS_CG_TAGGED && !args.tag) || args.sh.smem > (size_t)lim.smem - 1024 || args.sh.grid <= 0 ||
+        args.sh.grid > lim.sms ||
         args.sh.grid > kXchMaxGrid || 2 * args.sh.grid > kCglsThreads)
         return cudaErrorInvalidValue;
     int per = 0;

@@ -87,6 +87,7 @@ template <typename T> struct Work {
     v2<T>* cq = nullptr;
     v2<T>* cr1 = nullptr;  // second buffers of the coarse CG
     v2<T>* cp1 = nullptr;
+    unsigned long long* ctag = nullptr;   // epoch-tagged s and u of the on-chip coarse CG (T == float)
     v2<T>* gm = nullptr;   // GMRES smoother basis, gm_k + 1 vectors
     int gm_k = 0;
     int cnc = 0;           // coarse dof the coarse vectors are sized for
@@ -257,6 +258,11 @@ template <typename T> int ensure_work(mg_ctx* ctx) {
     TRY(dalloc(ctx, &w.cq, cb));
     TRY(dalloc(ctx, &w.cr1, cb));
     TRY(dalloc(ctx, &w.cp1, cb));
+    if (sizeof(T) == 4) {
+        const size_t tb = sizeof(unsigned long long) * 4 * (size_t)ctx->g.Vc * (nc > 0 ? nc : 2);
+        TRY(dalloc(ctx, &w.ctag, tb));
+        CK(cudaMemsetAsync(w.ctag, 0, tb, ctx->st));   // epoch 0 is never awaited
+    }
     w.cnc = nc;
     w.ready = true;
     return MG_OK;
@@ -402,11 +408,13 @@ int coarse_solve(mg_ctx* ctx, const CoarseLevel& L, const v2<T>* rc, v2<T>* y, d
         const unsigned long long reserve = 2ull * (unsigned long long)(maxit > 0 ? maxit : 0) + 4ull;
         if ((unsigned long long)ctx->xch_epoch + reserve >= 0xFFFFFFFFull) {   // 32-bit epochs would wrap
             CK(cudaMemsetAsync(ctx->xch, 0, sizeof(unsigned long long) * kXchWords, ctx->st));
+            CK(cudaMemsetAsync(w.ctag, 0, sizeof(unsigned long long) * 4 * (size_t)ctx->g.Vc * L.nc, ctx->st));
             ctx->xch_epoch = 1;
         }
         c.xch = ctx->xch;
         c.epoch0 = ctx->xch_epoch;
-        c.form = ctx->prm.coarse_form == 1 ? CGLS_TEXTBOOK : CGLS_CG_ONE_EXCHANGE;
+        c.form = ctx->prm.coarse_form == 1 ? CGLS_TEXTBOOK : CGLS_CG_TAGGED;
+        c.tag = (unsigned long long*)w.ctag;
         ctx->xch_epoch += (unsigned int)reserve;
         CK(cudaMemsetAsync(ctx->bar, 0, sizeof(unsigned int) * 3, ctx->st));
         PROF_BEGIN(MG_K_COARSE_SOLVE);

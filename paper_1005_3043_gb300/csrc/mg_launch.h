@@ -195,8 +195,8 @@ struct CglsShape {
 };
 enum { CGLS_AUTO = 0, CGLS_STREAM = 2, CGLS_SMEM = 3 };
 // iteration form of the on-chip CGLS: two grid-wide exchanges per iteration, or
-// the Chronopoulos-Gear form with one exchange and one neighbour-flag barrier
-enum { CGLS_TEXTBOOK = 0, CGLS_CG_ONE_EXCHANGE = 1 };
+// the Chronopoulos-Gear form with one exchange and epoch-tagged shared vectors
+enum { CGLS_TEXTBOOK = 0, CGLS_CG_TAGGED = 1 };
 struct CglsArgs {
     const void* Au;        // float2 or __half2 units
     const float* su;       // FP16 block scales [X][d]; nullptr selects the FP32 operator
@@ -207,17 +207,17 @@ struct CglsArgs {
     Geom g;
     float tol2;
     int maxit;
-    unsigned long long* xch;   // exchange slots and neighbour flags, kXchWords words
+    unsigned long long* xch;   // exchange slots, kXchWords words
     unsigned int epoch0;       // first epoch of this launch; 2 * maxit + 4 are reserved
-    int form;                  // CGLS_TEXTBOOK or CGLS_CG_ONE_EXCHANGE
+    int form;                  // CGLS_TEXTBOOK or CGLS_CG_TAGGED
+    unsigned long long* tag;   // CGLS_CG_TAGGED: epoch-tagged s and u, 4 * Vc * nc words
     double* scal;
     int* err;                  // error flag (zeroed before the launch)
     CglsShape sh;
 };
 constexpr int kXchMaxGrid = 256;
-// exchange slots [parity 2][value 3][grid][16], then one flag line per CTA [grid][16]
-constexpr size_t kXchFlagOffset = (size_t)2 * 3 * kXchMaxGrid * 16;
-constexpr size_t kXchWords = kXchFlagOffset + (size_t)kXchMaxGrid * 16;
+// exchange slots [parity 2][value 3][grid][16]
+constexpr size_t kXchWords = (size_t)2 * 3 * kXchMaxGrid * 16;
 bool cgls_shape(int nc, int Vc, bool h16, int mode, CglsShape* out);
 // Not for graph capture: every launch takes a fresh epoch range from the host.
 void coarse_pack_units(void* Au, float* su, const double2* A, int nc, int ru, int Vc, bool h16, cudaStream_t st);

@@ -90,6 +90,12 @@ __device__ __forceinline__ void xch_publish(unsigned long long* slot, float v, u
     const unsigned long long w = ((unsigned long long)e << 32) | __float_as_uint(v);
     asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(slot), "l"(w) : "memory");
 }
+// relaxed publish: for callers whose shared data carries its own epoch tags
+// (nothing else has to be visible when the value is)
+__device__ __forceinline__ void xch_publish_relaxed(unsigned long long* slot, float v, unsigned int e) {
+    const unsigned long long w = ((unsigned long long)e << 32) | __float_as_uint(v);
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(slot), "l"(w) : "memory");
+}
 __device__ __forceinline__ unsigned long long xch_load(const unsigned long long* slot) {
     unsigned long long w;
     asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(slot) : "memory");
@@ -124,7 +130,9 @@ constexpr int kXchMaxNV = 3;
 // sc: shared scratch of at least NV * (32 + G + 1) floats, free during the call.
 // Three CTA barriers for any NV: warp partial sums -> thread 0 publishes;
 // polled values -> one warp per value sums them in CTA order.
-template <int NV>
+// FENCE false: no fence before the publish (the caller's cross-CTA data is
+// epoch-tagged, so only the partial sums themselves must arrive).
+template <int NV, bool FENCE = true>
 __device__ bool xch_allreduce(float (&v)[NV], unsigned long long* slots, unsigned int e, int* err, float* sc) {
     static_assert(NV >= 1 && NV <= kXchMaxNV, "one to three values per exchange");
     const int G = gridDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
@@ -146,9 +154,14 @@ __device__ bool xch_allreduce(float (&v)[NV], unsigned long long* slots, unsigne
             for (int i = 0; i < nw; ++i) a += wsum[j * 32 + i];
             cta[j] = a;
         }
-        __threadfence();
+        if (FENCE) {
+            __threadfence();
 #pragma unroll
-        for (int j = 0; j < NV; ++j) xch_publish(base + ((size_t)j * G + blockIdx.x) * kXchPad, cta[j], e);
+            for (int j = 0; j < NV; ++j) xch_publish(base + ((size_t)j * G + blockIdx.x) * kXchPad, cta[j], e);
+        } else {
+#pragma unroll
+            for (int j = 0; j < NV; ++j) xch_publish_relaxed(base + ((size_t)j * G + blockIdx.x) * kXchPad, cta[j], e);
+        }
     }
     bool ok = true;
     for (int i = t; i < NV * G && ok; i += blockDim.x) {
@@ -169,16 +182,27 @@ __device__ bool xch_allreduce(float (&v)[NV], unsigned long long* slots, unsigne
     return true;
 }
 
-// ---------------------------------------------------------------- neighbour flags
-// Point-to-point barrier with the CTAs whose data this CTA reads (and which read
-// its data): CTA c publishes epoch e in flags[c][0] after its writes, then waits
-// until every CTA in its mask carries an epoch >= e.  Epochs only increase, so
-// a neighbour that is already further on does not hold anyone up.
-__device__ __forceinline__ bool flag_wait(const unsigned long long* flag, unsigned int e, int* err) {
+// ---------------------------------------------------------------- epoch-tagged vectors
+// A complex entry as two 64-bit words (epoch << 32 | float bits) for re and im.
+// Each word is written and read whole (single-copy atomic), so a reader that
+// sees the expected epoch in both words has the value of that epoch, with no
+// fence or flag between writer and reader.
+__device__ __forceinline__ void tag_store(unsigned long long* w, float re, float im, unsigned int e) {
+    const unsigned long long a = ((unsigned long long)e << 32) | __float_as_uint(re);
+    const unsigned long long b = ((unsigned long long)e << 32) | __float_as_uint(im);
+    asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(w), "l"(a), "l"(b) : "memory");
+}
+// one load; true when both words carry epoch e
+__device__ __forceinline__ bool tag_load(const unsigned long long* w, unsigned int e, float2& v) {
+    unsigned long long a, b;
+    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(w) : "memory");
+    v = make_float2(__uint_as_float((unsigned int)a), __uint_as_float((unsigned int)b));
+    return (unsigned int)(a >> 32) == e && (unsigned int)(b >> 32) == e;
+}
+// bounded wait for epoch e at w; false on timeout or a raised error flag
+__device__ __forceinline__ bool tag_wait(const unsigned long long* w, unsigned int e, int* err, float2& v) {
     long long spins = 0;
-    for (;;) {
-        const unsigned int w = (unsigned int)xch_load(flag);
-        if ((int)(w - e) >= 0) return true;
+    while (!tag_load(w, e, v)) {
         if (*(volatile int*)err) return false;
         if (++spins > kExchangeSpinLimit) {
             atomicExch(err, 1);
@@ -186,21 +210,7 @@ __device__ __forceinline__ bool flag_wait(const unsigned long long* flag, unsign
         }
         if (spins > 32) __nanosleep(20);
     }
-}
-// mask: shared bitmask over the grid's CTAs (bit c of word c / 32)
-__device__ __forceinline__ bool neighbour_sync(unsigned long long* flags, const unsigned int* mask, unsigned int e, int* err) {
-    const int G = gridDim.x, t = threadIdx.x;
-    __syncthreads();
-    if (t == 0) {
-        __threadfence();
-        asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(flags + (size_t)blockIdx.x * kXchPad),
-                     "l"((unsigned long long)e)
-                     : "memory");
-    }
-    bool ok = true;
-    for (int c = t; c < G && ok; c += blockDim.x)
-        if ((mask[c >> 5] >> (c & 31)) & 1u) ok = flag_wait(flags + (size_t)c * kXchPad, e, err);
-    return !__syncthreads_or(!ok);
+    return true;
 }
 
 }  // namespace wmg

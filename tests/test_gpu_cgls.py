@@ -4,8 +4,8 @@ on chip for the whole solve (tensor memory at these sizes), 1 the operator
 read from global memory into registers, 2 the operator streamed through a
 shared-memory ring with several waves per phase, 3 the operator resident in
 shared memory; the on-chip kernels (0, 2, 3) in both iteration forms, the
-Chronopoulos-Gear form with one grid-wide exchange per iteration (coarse_form
-0) and the textbook CGLS (coarse_form 1).  References are the FP64 oracle's CGLS on
+Chronopoulos-Gear form with one grid-wide exchange per iteration and
+epoch-tagged vectors (coarse_form 0) and the textbook CGLS (coarse_form 1).  References are the FP64 oracle's CGLS on
 the oracle's own D_c (FP32) or on that D_c rounded to FP16 with one scale per
 (aggregate, direction) block, the storage rule of the FP16 mode."""
 import numpy as np
