@@ -487,51 +487,68 @@ template <typename T> __global__ void k_gmres_normalize(v2<T>* basis, size_t n, 
 // h_{j+1,j}.
 constexpr int kGmresMax = 16;   // largest smoother Krylov dimension (mg_params check)
 __global__ void k_gmres_ls(double* scal, int k, double omega) {
-    // the small problem lives in shared memory (no per-thread stack frame)
-    __shared__ double hr[kGmresMax + 1][kGmresMax], hi[kGmresMax + 1][kGmresMax];
-    __shared__ double gr[kGmresMax + 1], gi[kGmresMax + 1], yr[kGmresMax], yi[kGmresMax];
-    if (blockIdx.x != 0 || threadIdx.x != 0 || k > kGmresMax) return;
-    int dim = k;
-    for (int j = 0; j < k; ++j) {
-        for (int i = 0; i <= j + 1; ++i) {
-            const int s = rslot(i, j + 1);
-            hr[i][j] = scal[s];
-            hi[i][j] = scal[s + 1];
+    // one warp: lane jj owns column jj of the Hessenberg matrix (lane kGmresMax
+    // the right-hand side g), so each Givens rotation is applied to all columns at
+    // once with the same arithmetic per column as a serial sweep; the back
+    // substitution runs in lane 0 in the usual order
+    __shared__ double hr[kGmresMax + 1][kGmresMax + 1], hi[kGmresMax + 1][kGmresMax + 1];
+    __shared__ double yr[kGmresMax], yi[kGmresMax];
+    __shared__ int s_dim;
+    const int lane = threadIdx.x;
+    if (blockIdx.x != 0 || lane >= 32 || k > kGmresMax) return;
+    // H[i][j] = scal[rslot(i, j + 1)], i <= j + 1; column kGmresMax holds g = beta e_0
+    for (int e = lane; e < (kGmresMax + 1) * (kGmresMax + 1); e += 32) {
+        const int i = e / (kGmresMax + 1), j = e - i * (kGmresMax + 1);
+        double vr = 0.0, vi = 0.0;
+        if (j < k && i <= j + 1) {
+            const int sl = rslot(i, j + 1);
+            vr = scal[sl];
+            vi = scal[sl + 1];
+        } else if (j == kGmresMax && i == 0) {
+            vr = scal[rslot(0, 0)];
         }
-        if (dim == k && !(hr[j + 1][j] > 0)) dim = j + 1;
+        hr[i][j] = vr;
+        hi[i][j] = vi;
     }
-    for (int i = 0; i <= k; ++i) { gr[i] = 0; gi[i] = 0; }
-    gr[0] = scal[rslot(0, 0)];
+    __syncwarp();
+    if (lane == 0) {
+        int dim = k;
+        for (int j = 0; j < k; ++j)
+            if (!(hr[j + 1][j] > 0)) { dim = j + 1; break; }
+        s_dim = dim;
+    }
+    __syncwarp();
+    const int dim = s_dim;
+    const int col = lane < dim ? lane : (lane == 31 ? kGmresMax : -1);   // lane 31 carries g
     for (int j = 0; j < dim; ++j) {
         const double ar = hr[j][j], ai = hi[j][j], br = hr[j + 1][j], bi = hi[j + 1][j];
+        __syncwarp();
         const double nrm = sqrt(ar * ar + ai * ai + br * br + bi * bi);
-        if (!(nrm > 0)) continue;
-        const double cr = ar / nrm, ci = ai / nrm, sr = br / nrm, si = bi / nrm;
-        // [conj(c) conj(s); -s c] applied to rows j, j+1 of columns j.. and of g
-        for (int jj = j; jj < dim; ++jj) {
-            const double x1r = hr[j][jj], x1i = hi[j][jj], x2r = hr[j + 1][jj], x2i = hi[j + 1][jj];
-            hr[j][jj] = cr * x1r + ci * x1i + sr * x2r + si * x2i;
-            hi[j][jj] = cr * x1i - ci * x1r + sr * x2i - si * x2r;
-            hr[j + 1][jj] = -(sr * x1r - si * x1i) + (cr * x2r - ci * x2i);
-            hi[j + 1][jj] = -(sr * x1i + si * x1r) + (cr * x2i + ci * x2r);
+        if (nrm > 0 && col >= 0 && (col >= j)) {
+            const double cr = ar / nrm, ci = ai / nrm, sr = br / nrm, si = bi / nrm;
+            // [conj(c) conj(s); -s c] applied to rows j, j+1
+            const double x1r = hr[j][col], x1i = hi[j][col], x2r = hr[j + 1][col], x2i = hi[j + 1][col];
+            hr[j][col] = cr * x1r + ci * x1i + sr * x2r + si * x2i;
+            hi[j][col] = cr * x1i - ci * x1r + sr * x2i - si * x2r;
+            hr[j + 1][col] = -(sr * x1r - si * x1i) + (cr * x2r - ci * x2i);
+            hi[j + 1][col] = -(sr * x1i + si * x1r) + (cr * x2i + ci * x2r);
         }
-        const double t1r = gr[j], t1i = gi[j], t2r = gr[j + 1], t2i = gi[j + 1];
-        gr[j] = cr * t1r + ci * t1i + sr * t2r + si * t2i;
-        gi[j] = cr * t1i - ci * t1r + sr * t2i - si * t2r;
-        gr[j + 1] = -(sr * t1r - si * t1i) + (cr * t2r - ci * t2i);
-        gi[j + 1] = -(sr * t1i + si * t1r) + (cr * t2i + ci * t2r);
+        __syncwarp();
     }
-    for (int i = dim - 1; i >= 0; --i) {
-        double ar = gr[i], ai = gi[i];
-        for (int jj = i + 1; jj < dim; ++jj) {
-            ar -= hr[i][jj] * yr[jj] - hi[i][jj] * yi[jj];
-            ai -= hr[i][jj] * yi[jj] + hi[i][jj] * yr[jj];
+    if (lane == 0) {
+        for (int i = dim - 1; i >= 0; --i) {
+            double ar = hr[i][kGmresMax], ai = hi[i][kGmresMax];
+            for (int jj = i + 1; jj < dim; ++jj) {
+                ar -= hr[i][jj] * yr[jj] - hi[i][jj] * yi[jj];
+                ai -= hr[i][jj] * yi[jj] + hi[i][jj] * yr[jj];
+            }
+            const double dr = hr[i][i], di = hi[i][i], dd = dr * dr + di * di;
+            yr[i] = dd > 0 ? (ar * dr + ai * di) / dd : 0.0;
+            yi[i] = dd > 0 ? (ai * dr - ar * di) / dd : 0.0;
         }
-        const double dr = hr[i][i], di = hi[i][i], dd = dr * dr + di * di;
-        yr[i] = dd > 0 ? (ar * dr + ai * di) / dd : 0.0;
-        yi[i] = dd > 0 ? (ai * dr - ar * di) / dd : 0.0;
     }
-    for (int j = 0; j < k; ++j) {
+    __syncwarp();
+    for (int j = lane; j < k; j += 32) {
         scal[S_GCR_C + 2 * j] = j < dim ? omega * yr[j] : 0.0;
         scal[S_GCR_C + 2 * j + 1] = j < dim ? omega * yi[j] : 0.0;
     }
@@ -554,7 +571,7 @@ template <typename T> void gmres_normalize(v2<T>* basis, size_t n, int k, const 
 }
 void gmres_ls(const Reduce& R, int k, double omega, cudaStream_t st) {
     note_launch();
-    k_gmres_ls<<<1, 1, 0, st>>>(R.scal, k, omega);
+    k_gmres_ls<<<1, 32, 0, st>>>(R.scal, k, omega);
 }
 template <typename T> void multi_axpy(v2<T>* z, const v2<T>* basis, size_t n, int k, const Reduce& R, cudaStream_t st) {
     note_launch();

@@ -28,6 +28,10 @@ __device__ __forceinline__ uint32_t c2h(float re, float im) {
     const __half2 q = __floats2half2_rn(re, im);
     return *reinterpret_cast<const uint32_t*>(&q);
 }
+// the factor 1 / |v| of a normalised basis vector, stored as a float in a
+// double scalar (nullptr: 1); its site scales times this factor are the
+// scales of the normalised vector
+__device__ __forceinline__ float inv_norm(const double* f) { return f ? (float)*f : 1.f; }
 // the 12 components of a site (6 pair words at stride Vb), times s
 __device__ __forceinline__ void ld_site_h(const uint2* p, float s, int Vb, cx<float> (&v)[12]) {
 #pragma unroll
@@ -63,16 +67,16 @@ __device__ __forceinline__ void store_site_h(uint2* h, float* s, const cx<float>
 // one hop on FP16 storage (input spinor IN16: FP16 pairs + scale, else FP32)
 template <int MU, bool FWD, bool IN16>
 __device__ __forceinline__ void hop_h(cx<float> (&acc)[4][3], const void* __restrict__ in, const float* __restrict__ sin,
-                                      const uint2* __restrict__ U, const Geom& g, int X, int l, const int (&lc)[4],
-                                      const int (&xc)[4]) {
+                                      float fin, const uint2* __restrict__ U, const Geom& g, int X, int l,
+                                      const int (&lc)[4], const int (&xc)[4]) {
     int Xn, ln;
     bool flip;
     neighbour(g, X, l, lc, xc, MU, FWD ? 1 : -1, Xn, ln, flip);
     cx<float> p[4][3];
     cx<float>(&pf)[12] = reinterpret_cast<cx<float>(&)[12]>(p);
     if (IN16) {
-        ld_site_h(reinterpret_cast<const uint2*>(in) + (size_t)Xn * 6 * g.Vb + ln, __ldg(sin + (size_t)Xn * g.Vb + ln),
-                  g.Vb, pf);
+        ld_site_h(reinterpret_cast<const uint2*>(in) + (size_t)Xn * 6 * g.Vb + ln,
+                  __ldg(sin + (size_t)Xn * g.Vb + ln) * fin, g.Vb, pf);
     } else {
         const float2* b = reinterpret_cast<const float2*>(in) + (size_t)Xn * 12 * g.Vb + ln;
 #pragma unroll
@@ -117,9 +121,10 @@ enum { HMODE_PLAIN = 0, HMODE_XMY = 1, HMODE_MRDOT = 2 };
 template <int MODE, bool IN16>
 __global__ void __launch_bounds__(kHalfThreads, MODE == HMODE_MRDOT ? 6 : 7)
     k_dslash_h(uint2* __restrict__ out, float* __restrict__ sout, const void* __restrict__ in,
-               const float* __restrict__ sin, const uint2* __restrict__ U, const float2* __restrict__ src, Geom g,
-               float diag, double omega, Reduce R) {
+               const float* __restrict__ sin, const double* __restrict__ fnorm, const uint2* __restrict__ U,
+               const float2* __restrict__ src, Geom g, float diag, double omega, Reduce R) {
     const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const float fin = IN16 ? inv_norm(fnorm) : 1.f;   // the input's site scales times fin
     float red[3] = {0.f, 0.f, 0.f};
     if (s < g.V) {
         const int X = (int)(s / g.Vb), l = (int)(s - (long long)X * g.Vb);
@@ -128,7 +133,7 @@ __global__ void __launch_bounds__(kHalfThreads, MODE == HMODE_MRDOT ? 6 : 7)
         coarse_coords(g, X, xc);
         const size_t self = (size_t)X * 12 * g.Vb + l;     // FP32 vectors
         const size_t self6 = (size_t)X * 6 * g.Vb + l;     // FP16 pair vectors
-        const float sself = IN16 ? __ldg(sin + (size_t)X * g.Vb + l) : 1.f;
+        const float sself = IN16 ? __ldg(sin + (size_t)X * g.Vb + l) * fin : 1.f;
         // the input at this site (re-read, cached, where the MR dots need it)
         auto self_in = [&](int k) -> cx<float> {
             if (IN16) {
@@ -142,14 +147,14 @@ __global__ void __launch_bounds__(kHalfThreads, MODE == HMODE_MRDOT ? 6 : 7)
         for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
             for (int c = 0; c < 3; ++c) acc[sp][c] = diag * self_in(3 * sp + c);
-        hop_h<0, true, IN16>(acc, in, sin, U, g, X, l, lc, xc);
-        hop_h<0, false, IN16>(acc, in, sin, U, g, X, l, lc, xc);
-        hop_h<1, true, IN16>(acc, in, sin, U, g, X, l, lc, xc);
-        hop_h<1, false, IN16>(acc, in, sin, U, g, X, l, lc, xc);
-        hop_h<2, true, IN16>(acc, in, sin, U, g, X, l, lc, xc);
-        hop_h<2, false, IN16>(acc, in, sin, U, g, X, l, lc, xc);
-        hop_h<3, true, IN16>(acc, in, sin, U, g, X, l, lc, xc);
-        hop_h<3, false, IN16>(acc, in, sin, U, g, X, l, lc, xc);
+        hop_h<0, true, IN16>(acc, in, sin, fin, U, g, X, l, lc, xc);
+        hop_h<0, false, IN16>(acc, in, sin, fin, U, g, X, l, lc, xc);
+        hop_h<1, true, IN16>(acc, in, sin, fin, U, g, X, l, lc, xc);
+        hop_h<1, false, IN16>(acc, in, sin, fin, U, g, X, l, lc, xc);
+        hop_h<2, true, IN16>(acc, in, sin, fin, U, g, X, l, lc, xc);
+        hop_h<2, false, IN16>(acc, in, sin, fin, U, g, X, l, lc, xc);
+        hop_h<3, true, IN16>(acc, in, sin, fin, U, g, X, l, lc, xc);
+        hop_h<3, false, IN16>(acc, in, sin, fin, U, g, X, l, lc, xc);
         cx<float>(&v)[12] = reinterpret_cast<cx<float>(&)[12]>(acc);   // component k = 3 spin + colour
         if (MODE == HMODE_XMY)
 #pragma unroll
@@ -245,6 +250,9 @@ __device__ __forceinline__ int rslot_h(int j, int k) { return S_GCR_R + 2 * (k *
 template <int NJ>
 __global__ void __launch_bounds__(kHalfThreads) k_h_multidot(const uint2* __restrict__ B, const float* __restrict__ S,
                                                               Geom g, int k, Reduce R) {
+    __shared__ float fac[K_MAX];   // basis j < k is normalised through its stored norm
+    for (int j = threadIdx.x; j < k && j < K_MAX; j += blockDim.x) fac[j] = inv_norm(R.scal + S_GMRES_F + j);
+    __syncthreads();
     const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     float a[2 * NJ];
 #pragma unroll
@@ -258,7 +266,7 @@ __global__ void __launch_bounds__(kHalfThreads) k_h_multidot(const uint2* __rest
         for (int j = 0; j < NJ; ++j) {
             if (j < k) {
                 cx<float> v[12];
-                ld_site_h(B + (size_t)j * V6 + self6, S[(size_t)j * g.V + s], g.Vb, v);
+                ld_site_h(B + (size_t)j * V6 + self6, S[(size_t)j * g.V + s] * fac[j], g.Vb, v);
                 cx<float> t(0.f, 0.f);
 #pragma unroll
                 for (int q = 0; q < 12; ++q) cmadc(t, v[q], w[q]);
@@ -275,11 +283,15 @@ __global__ void __launch_bounds__(kHalfThreads) k_h_multidot(const uint2* __rest
     });
 }
 // basis[k] -= sum_{j<k} h_jk basis[j] (h from the scalars), stored again in FP16
-// with new site scales; scal[S_GCR_PN2] = |basis[k]|^2 of the stored vector
+// with new site scales; h_{k,k-1} = |basis[k]| of the stored vector is recorded
+// and normalises it: its readers scale its site scales by the float 1 / |basis[k]|
+// (S_GMRES_F + k), the same float product a rescaling pass would have stored
 __global__ void __launch_bounds__(kHalfThreads) k_h_orth(uint2* __restrict__ B, float* __restrict__ S, Geom g, int k,
                                                           Reduce R) {
     __shared__ double beta[2 * K_MAX];
+    __shared__ float fac[K_MAX];
     for (int j = threadIdx.x; j < 2 * k; j += blockDim.x) beta[j] = R.scal[S_GCR_R + 2 * k * K_MAX + j];
+    for (int j = threadIdx.x; j < k && j < K_MAX; j += blockDim.x) fac[j] = inv_norm(R.scal + S_GMRES_F + j);
     __syncthreads();
     const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     float a = 0.f;
@@ -290,7 +302,7 @@ __global__ void __launch_bounds__(kHalfThreads) k_h_orth(uint2* __restrict__ B, 
         ld_site_h(B + (size_t)k * V6 + self6, S[(size_t)k * g.V + s], g.Vb, w);
         for (int j = 0; j < k; ++j) {
             cx<float> v[12];
-            ld_site_h(B + (size_t)j * V6 + self6, S[(size_t)j * g.V + s], g.Vb, v);
+            ld_site_h(B + (size_t)j * V6 + self6, S[(size_t)j * g.V + s] * fac[j], g.Vb, v);
             const cx<float> b((float)beta[2 * j], (float)beta[2 * j + 1]);
 #pragma unroll
             for (int q = 0; q < 12; ++q) w[q] = w[q] - b * v[q];
@@ -299,25 +311,21 @@ __global__ void __launch_bounds__(kHalfThreads) k_h_orth(uint2* __restrict__ B, 
                      [&](int, cx<float> q) { a += norm2(q); });
     }
     float acc[1] = {a};
-    grid_reduce<1, float>(acc, R.partials, R.ticket, [&](double (&t)[1]) { R.scal[S_GCR_PN2] = t[0]; });
-}
-// normalise basis[k]: its site scales times 1 / sqrt(scal[S_GCR_PN2]); h_{k,k-1} recorded
-__global__ void k_h_normalize(float* __restrict__ Sk, long long n, int k, double* scal) {
-    const double nk = sqrt(scal[S_GCR_PN2]);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        scal[rslot_h(k, k)] = nk;
-        scal[rslot_h(k, k) + 1] = 0.0;
-    }
-    const float f = (float)(nk > 0 ? 1.0 / nk : 0.0);
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        Sk[i] *= f;
+    grid_reduce<1, float>(acc, R.partials, R.ticket, [&](double (&t)[1]) {
+        const double nk = sqrt(t[0]);
+        R.scal[rslot_h(k, k)] = nk;
+        R.scal[rslot_h(k, k) + 1] = 0.0;
+        R.scal[S_GMRES_F + k] = (double)(float)(nk > 0 ? 1.0 / nk : 0.0);
+    });
 }
 // z += sum_{j<k} c_j basis[j], c_j = scal[S_GCR_C + 2j]
 __global__ void __launch_bounds__(kHalfThreads) k_h_multi_axpy(float2* __restrict__ z, const uint2* __restrict__ B,
                                                                 const float* __restrict__ S, Geom g, int k,
                                                                 const double* __restrict__ scal) {
     __shared__ float c[2 * K_MAX];
+    __shared__ float fac[K_MAX];
     for (int j = threadIdx.x; j < 2 * k; j += blockDim.x) c[j] = (float)scal[S_GCR_C + j];
+    for (int j = threadIdx.x; j < k && j < K_MAX; j += blockDim.x) fac[j] = inv_norm(scal + S_GMRES_F + j);
     __syncthreads();
     const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (s >= g.V) return;
@@ -328,7 +336,7 @@ __global__ void __launch_bounds__(kHalfThreads) k_h_multi_axpy(float2* __restric
     for (int q = 0; q < 12; ++q) acc[q] = ld<float>(z + self + (size_t)q * g.Vb);
     for (int j = 0; j < k; ++j) {
         cx<float> v[12];
-        ld_site_h(B + (size_t)j * V6 + self6, S[(size_t)j * g.V + s], g.Vb, v);
+        ld_site_h(B + (size_t)j * V6 + self6, S[(size_t)j * g.V + s] * fac[j], g.Vb, v);
         const cx<float> cj(c[2 * j], c[2 * j + 1]);
 #pragma unroll
         for (int q = 0; q < 12; ++q) cmad(acc[q], cj, v[q]);
@@ -351,22 +359,26 @@ void from_half(float2* x, ConstHalfSpinor h, const Geom& g, cudaStream_t st) {
     note_launch();
     k_from_half<<<half_grid(g.V), kHalfThreads, 0, st>>>(x, h.v, h.s, g);
 }
-void dslash_h_plain(HalfSpinor out, ConstHalfSpinor in, const uint2* U16, const Geom& g, double mass, cudaStream_t st) {
+void dslash_h_plain(HalfSpinor out, ConstHalfSpinor in, const uint2* U16, const Geom& g, double mass, cudaStream_t st,
+                    const double* in_norm) {
     note_launch();
-    k_dslash_h<HMODE_PLAIN, true><<<half_grid(g.V), kHalfThreads, 0, st>>>(out.v, out.s, in.v, in.s, U16, nullptr, g,
-                                                                          (float)(4.0 + mass), 0.0, Reduce{});
+    k_dslash_h<HMODE_PLAIN, true><<<half_grid(g.V), kHalfThreads, 0, st>>>(out.v, out.s, in.v, in.s, in_norm, U16,
+                                                                          nullptr, g, (float)(4.0 + mass), 0.0,
+                                                                          Reduce{});
 }
 void dslash_h_xmy(HalfSpinor out, const float2* in, const uint2* U16, const float2* src, const Geom& g, double mass,
                   cudaStream_t st) {
     note_launch();
-    k_dslash_h<HMODE_XMY, false><<<half_grid(g.V), kHalfThreads, 0, st>>>(out.v, out.s, in, nullptr, U16, src, g,
-                                                                          (float)(4.0 + mass), 0.0, Reduce{});
+    k_dslash_h<HMODE_XMY, false><<<half_grid(g.V), kHalfThreads, 0, st>>>(out.v, out.s, in, nullptr, nullptr, U16,
+                                                                          src, g, (float)(4.0 + mass), 0.0,
+                                                                          Reduce{});
 }
 void dslash_h_mrdot(HalfSpinor out, ConstHalfSpinor in, const uint2* U16, const Geom& g, double mass, double omega,
                     const Reduce& R, cudaStream_t st) {
     note_launch();
-    k_dslash_h<HMODE_MRDOT, true><<<half_grid(g.V), kHalfThreads, 0, st>>>(out.v, out.s, in.v, in.s, U16, nullptr, g,
-                                                                          (float)(4.0 + mass), omega, R);
+    k_dslash_h<HMODE_MRDOT, true><<<half_grid(g.V), kHalfThreads, 0, st>>>(out.v, out.s, in.v, in.s, nullptr, U16,
+                                                                          nullptr, g, (float)(4.0 + mass), omega,
+                                                                          R);
 }
 void h_multidot(const uint2* B, const float* S, const Geom& g, int k, const Reduce& R, cudaStream_t st) {
     note_launch();
@@ -377,11 +389,6 @@ void h_multidot(const uint2* B, const float* S, const Geom& g, int k, const Redu
 void h_orth(uint2* B, float* S, const Geom& g, int k, const Reduce& R, cudaStream_t st) {
     note_launch();
     k_h_orth<<<half_grid(g.V), kHalfThreads, 0, st>>>(B, S, g, k, R);
-}
-void h_normalize(float* S, const Geom& g, int k, const Reduce& R, cudaStream_t st) {
-    note_launch();
-    k_h_normalize<<<(int)std::min<long long>((g.V + 255) / 256, 152 * 8), 256, 0, st>>>(S + (size_t)k * g.V, g.V, k,
-                                                                                         R.scal);
 }
 void h_multi_axpy(float2* z, const uint2* B, const float* S, const Geom& g, int k, const Reduce& R, cudaStream_t st) {
     note_launch();

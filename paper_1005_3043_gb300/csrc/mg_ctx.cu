@@ -533,19 +533,19 @@ int smooth(mg_ctx* ctx, const v2<T>* r, v2<T>* z, const Reduce& R, Counters& cnt
         dslash_h_xmy(HalfSpinor{B, S}, zf, ctx->U16, reinterpret_cast<const float2*>(r), ctx->g, ctx->mass, ctx->st);
         PROF_END(MG_K_DSLASH);
         PROF_BEGIN(MG_K_KRYLOV);
-        h_orth(B, S, ctx->g, 0, Rs, ctx->st);        // no projection for k = 0: |v_0|^2
-        h_normalize(S, ctx->g, 0, Rs, ctx->st);
+        h_orth(B, S, ctx->g, 0, Rs, ctx->st);        // no projection for k = 0: |v_0|
         PROF_END(MG_K_KRYLOV);
         for (int j = 0; j < steps; ++j) {
+            // v_j is normalised by its norm h_{j,j-1} (|v_0| for j = 0): every reader
+            // of the basis scales its site scales by 1 / |v_j| from the scalars
             HalfSpinor out{B + (size_t)(j + 1) * 6 * V, S + (size_t)(j + 1) * V};
             PROF_BEGIN(MG_K_DSLASH);
             dslash_h_plain(out, ConstHalfSpinor(B + (size_t)j * 6 * V, S + (size_t)j * V), ctx->U16, ctx->g, ctx->mass,
-                           ctx->st);
+                           ctx->st, Rs.scal + S_GMRES_F + j);
             PROF_END(MG_K_DSLASH);
             PROF_BEGIN(MG_K_KRYLOV);
             h_multidot(B, S, ctx->g, j + 1, Rs, ctx->st);
             h_orth(B, S, ctx->g, j + 1, Rs, ctx->st);
-            h_normalize(S, ctx->g, j + 1, Rs, ctx->st);
             PROF_END(MG_K_KRYLOV);
         }
         PROF_BEGIN(MG_K_KRYLOV);

@@ -156,7 +156,10 @@ void links_to_half(uint2* U16, const float2* U32, const Geom& g, cudaStream_t st
 void links_pair(float2* out, const float2* U32, const Geom& g, cudaStream_t st);
 void to_half(HalfSpinor h, const float2* x, const Geom& g, cudaStream_t st);
 void from_half(float2* x, ConstHalfSpinor h, const Geom& g, cudaStream_t st);
-void dslash_h_plain(HalfSpinor out, ConstHalfSpinor in, const uint2* U16, const Geom& g, double mass, cudaStream_t st);
+// in_norm (device scalar, or nullptr): the input's site scales times the
+// float *in_norm (an Arnoldi vector normalised through its stored 1 / |v|)
+void dslash_h_plain(HalfSpinor out, ConstHalfSpinor in, const uint2* U16, const Geom& g, double mass, cudaStream_t st,
+                    const double* in_norm = nullptr);
 // out = src - D in (in FP32)
 void dslash_h_xmy(HalfSpinor out, const float2* in, const uint2* U16, const float2* src, const Geom& g, double mass,
                   cudaStream_t st);
@@ -169,7 +172,6 @@ void dslash_h_mrdot(HalfSpinor out, ConstHalfSpinor in, const uint2* U16, const 
 // S_GCR_PN2), normalisation by rescaling the site scales, z += sum c_j basis[j]
 void h_multidot(const uint2* B, const float* S, const Geom& g, int k, const Reduce& R, cudaStream_t st);
 void h_orth(uint2* B, float* S, const Geom& g, int k, const Reduce& R, cudaStream_t st);
-void h_normalize(float* S, const Geom& g, int k, const Reduce& R, cudaStream_t st);
 void h_multi_axpy(float2* z, const uint2* B, const float* S, const Geom& g, int k, const Reduce& R, cudaStream_t st);
 // e += alpha r; r -= alpha q when update_r (alpha from scal[S_MR_ALPHA])
 void mr_update_h(float2* e, HalfSpinor r, ConstHalfSpinor q, const Geom& g, bool update_r, const Reduce& R,
