@@ -1,5 +1,6 @@
 """The C-ABI library loads on a machine without a GPU and exports every entry
 point that include/wilson_mg.h declares (no compute calls here)."""
+import ctypes
 import os
 import re
 import subprocess
@@ -52,3 +53,22 @@ def test_host_only_calls(lib):
     assert p.nvec == 8 and tuple(p.block) == (4, 4, 4, 4) and p.omega == 0.9 and p.tol == 1e-10
     assert wmg.status_string(0) == "MG_OK"
     assert wmg.status_string(wmg.MG_ERR_NUMERIC) == "MG_ERR_NUMERIC"
+
+
+def test_params_struct_matches_header():
+    """The binding's MgParams has the header's mg_params fields, in order and
+    with the same C types (int / double / int[4])."""
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "wilson_mg.h")).read(), flags=re.S)
+    body = re.search(r"typedef\s+struct\s*\{(.*?)\}\s*mg_params\s*;", src, flags=re.S).group(1)
+    fields = []
+    for decl in body.split(";"):
+        m = re.match(r"\s*(int|double)\s+(\w+)\s*(\[\s*(\d+)\s*\])?\s*$", decl)
+        if m:
+            fields.append((m.group(2), m.group(1), int(m.group(4)) if m.group(4) else None))
+    assert fields, "no fields parsed"
+    ct = {"int": ctypes.c_int, "double": ctypes.c_double}
+    got = [(n, t) for n, t in wmg.MgParams._fields_]
+    assert [f[0] for f in fields] == [n for n, _ in got]
+    for (name, ctype, arr), (_, t) in zip(fields, got):
+        want = ct[ctype] * arr if arr else ct[ctype]
+        assert t == want or (arr and t._type_ is ct[ctype] and t._length_ == arr), name

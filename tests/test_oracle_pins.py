@@ -323,6 +323,53 @@ def test_cgnr_reaches_dense_solution():
     assert rel(Dc @ y3.ravel(), rc.ravel()) == pytest.approx(rel3, rel=1e-9)
 
 
+def _cg_one_reduction(Dc, b, maxit, tol):
+    """CG on Dc^dag Dc in the Chronopoulos-Gear arrangement (both scalars of an
+    iteration from u = Dc s: gamma = |s|^2, delta = |u|^2), written on the dense
+    operator; convergence is read from |r|^2 at the start of an iteration."""
+    y = np.zeros_like(b)
+    r = b.copy()
+    s = Dc.conj().T @ r
+    rc2 = np.vdot(b, b).real
+    p = z = q = None
+    gamma_old = alpha_old = 0.0
+    i = 0
+    while True:
+        u = Dc @ s
+        delta, gamma, r2 = np.vdot(u, u).real, np.vdot(s, s).real, np.vdot(r, r).real
+        if (i > 0 and r2 <= tol * tol * rc2) or i >= maxit:
+            return y, i
+        beta = gamma / gamma_old if i else 0.0
+        alpha = gamma / (delta - beta * gamma / alpha_old) if i else gamma / delta
+        w = Dc.conj().T @ u
+        p, z, q = (s, w, u) if i == 0 else (s + beta * p, w + beta * z, u + beta * q)
+        y, r, s = y + alpha * p, r - alpha * q, s - alpha * z
+        gamma_old, alpha_old = gamma, alpha
+        i += 1
+
+
+def test_one_reduction_cg_has_the_cgls_iterates():
+    """The coarse solve's CG on the normal equations (Sec. IV) in the arrangement
+    with one reduction per iteration produces the same iterates and the same
+    iteration count to 1e-3 as the oracle's textbook CGLS."""
+    L, B = (4, 4, 4, 4), (2, 2, 2, 2)
+    nv = 2
+    U, V0, P = _setup_small(L, B, nv=nv, seed=43)
+    A = oracle.coarse_build(U, P, 0.1, L, B)
+    Lc = oracle.coarse_dims(L, B)
+    nC = oracle.volume(Lc) * 2 * nv
+    Dc = dense_from_apply(lambda e: oracle.coarse_apply(A, e.reshape(-1, 2 * nv), Lc).ravel(), nC)
+    rc = synth.gaussian(nC, 3, 0).reshape(-1, 2 * nv)
+    for k in (1, 5, 12):
+        y_ref, it_ref, _ = oracle.cgnr(A, rc, Lc, 0.0, k)
+        y, it = _cg_one_reduction(Dc, rc.ravel(), k, 0.0)
+        assert it == it_ref == k
+        assert rel(y, y_ref.ravel()) < 1e-10, k
+    _, it3, _ = oracle.cgnr(A, rc, Lc, 1e-3, 5000)
+    _, it3b = _cg_one_reduction(Dc, rc.ravel(), 5000, 1e-3)
+    assert it3b == it3
+
+
 def test_gcr_without_preconditioner_equals_gmres():
     """GCR and GMRES minimise ||b - D x|| over the same Krylov space K_k(D, b)."""
     L = (2, 2, 2, 4)
