@@ -169,6 +169,10 @@ void prolong(v2<T>* e, const v2<T>* P, const v2<T>* yc, int nv, const Geom& g, c
 // X through its face in direction h go to A[X][1+h]; hops staying inside X go
 // to Aself[X][h] (summed later with the diagonal (4+m)).  FP64 throughout.
 constexpr int kBuildChunk = 8;
+// stride (complex entries) of one (site, column) spinor in the build's shared
+// memory: 13, not 12, so the lanes of a warp (consecutive columns) fall on
+// distinct banks in the product loop (12 put every fourth lane on one bank)
+constexpr int kWStride = 13;
 
 template <typename TC, int MU, bool FWD>
 __device__ __forceinline__ void hop_column(const cx<TC> (&p)[4][3], const v2<TC>* __restrict__ u, int Vb, TC coef,
@@ -237,7 +241,7 @@ __device__ void build_hop(double2* __restrict__ A, double2* __restrict__ Aself, 
     coarse_coords(g, X, xcX);
     for (int l0 = 0; l0 < g.Vb; l0 += kBuildChunk) {
         int cs = min(kBuildChunk, g.Vb - l0);
-        // W_b(x) for x in chunk, all columns b: Wsh[(xi*nc + b)*12 + k]
+        // W_b(x) for x in chunk, all columns b: Wsh[(xi*nc + b)*kWStride + k]
         for (int t = threadIdx.x; t < cs * nc; t += blockDim.x) {
             int xi = t / nc, b = t - xi * nc;
             int l = l0 + xi;
@@ -263,7 +267,7 @@ __device__ void build_hop(double2* __restrict__ A, double2* __restrict__ Aself, 
 #pragma unroll
             for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) st<TC>(Wsh + ((size_t)xi * nc + b) * 12 + 3 * sp + c, o[sp][c]);
+                for (int c = 0; c < 3; ++c) st<TC>(Wsh + ((size_t)xi * nc + b) * kWStride + 3 * sp + c, o[sp][c]);
         }
         // P_a(x) for x in chunk: Psh[(xi*nc + a)*6 + kk]
         for (int t = threadIdx.x; t < cs * nc * 6; t += blockDim.x) {
@@ -285,7 +289,7 @@ __device__ void build_hop(double2* __restrict__ A, double2* __restrict__ Aself, 
 #pragma unroll
                     for (int kk = 0; kk < 6; ++kk)
                         cmadc(t, ld<TC>(Psh + ((size_t)xi * nc + a) * 6 + kk),
-                              ld<TC>(Wsh + ((size_t)xi * nc + b) * 12 + 6 * sa + kk));
+                              ld<TC>(Wsh + ((size_t)xi * nc + b) * kWStride + 6 * sa + kk));
                     if (leaves[xi]) co = co + t;
                     else ci = ci + t;
                 }
@@ -313,7 +317,7 @@ __global__ void __launch_bounds__(256) k_coarse_hop(double2* A, double2* Aself, 
     extern __shared__ unsigned char smem_raw[];
     const int nc = 2 * nv;
     v2<TC>* Wsh = reinterpret_cast<v2<TC>*>(smem_raw);
-    v2<TC>* Psh = Wsh + (size_t)kBuildChunk * nc * 12;
+    v2<TC>* Psh = Wsh + (size_t)kBuildChunk * nc * kWStride;
     unsigned char* leaves = reinterpret_cast<unsigned char*>(Psh + (size_t)kBuildChunk * nc * 6);
     int X = blockIdx.x >> 3, h = blockIdx.x & 7;
     switch (h) {
@@ -344,7 +348,7 @@ template <typename TC>
 void coarse_build_t(double2* A, double2* Aself, const v2<TC>* P, const v2<TC>* U, int nv, double mass, const Geom& g,
                     cudaStream_t st) {
     int nc = 2 * nv;
-    size_t sm = sizeof(v2<TC>) * kBuildChunk * nc * 18 + kBuildChunk + 16;
+    size_t sm = sizeof(v2<TC>) * kBuildChunk * nc * (kWStride + 6) + kBuildChunk + 16;
     cudaFuncSetAttribute(k_coarse_hop<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     note_launch();
     k_coarse_hop<TC><<<g.Vc * 8, kThreads, sm, st>>>(A, Aself, P, U, nv, g);
