@@ -18,9 +18,17 @@ Parity status per function (what pins it; see the tests):
   mr                exact residual-decrease identity per step
   cgnr              reaches the dense LU solution; CGLS orthogonality
   gcr_solve         with M = I equals GMRES residuals; true residual <= tol
+  vcycle            coarse part Galerkin (P^dag (r - D z) = 0); smoothing half
+                    equal to the least-squares correction over K_k(D, r') of
+                    the coarse-corrected residual r' (numpy lstsq)
   setup             parity unpinned as a bit pattern (iterative, nonlinear);
-                    pinned by the invariants of its outputs and by the two-grid
-                    convergence factor against random prototypes
+                    pinned by the invariants of its outputs, by the two-grid
+                    convergence factor (refined < relaxed only < random
+                    prototypes) and by its truncated level (the refined group
+                    is outside range(P_t), every other prototype inside)
+  two_grid_factor   eq. 3 with an exact coarse solve: a start in range(P)
+                    is annihilated, the unsmoothed E_TG is a projection, the
+                    corrected residual is Galerkin-orthogonal to range(P)
 """
 from __future__ import annotations
 
@@ -97,6 +105,8 @@ def _load():
             lib.or_gcr_solve.restype = I
             lib.or_setup.argtypes = [P, P, P, I, I, I, P, P]
             lib.or_setup.restype = I
+            lib.or_setup_truncated_level.argtypes = [P, P, P, I, I, P, P, P]
+            lib.or_setup_truncated_level.restype = I
             _lib = lib
     return _lib
 
@@ -265,3 +275,63 @@ def setup(params: Params, U, V0, init_relax: int, n_iter: int, group_size: int =
     st = _load().or_setup(ctypes.byref(params), _p(U), _p(Vv), int(init_relax), int(n_iter),
                          int(group_size), _p(P), _p(A))
     return Vv, P, A, st
+
+
+def setup_truncated_level(params: Params, U, V, g0: int, group_size: int):
+    """The truncated level the group refinement of Sec. IV builds for group
+    g0 .. g0 + group_size - 1: (Vt, Pt, At, status) with Vt the prototypes
+    without the group, Pt their block orthonormalisation (eq. 4) and
+    At = Pt^dag D Pt.  The same C routine serves the setup itself."""
+    U, V = _c(U), _c(V)
+    nv = V.shape[0]
+    assert nv == params.nv
+    nt = nv - group_size
+    Lc = coarse_dims(list(params.L), list(params.B))
+    Vt = np.empty((nt,) + V.shape[1:], dtype=np.complex128)
+    Pt = np.empty_like(Vt)
+    At = np.empty((volume(Lc), 9, 2 * nt, 2 * nt), dtype=np.complex128)
+    st = _load().or_setup_truncated_level(ctypes.byref(params), _p(U), _p(V), int(g0), int(group_size), _p(Vt),
+                                          _p(Pt), _p(At))
+    return Vt, Pt, At, st
+
+
+def coarse_dense(A, Lc) -> np.ndarray:
+    """D_c as a dense (Vc nc) x (Vc nc) matrix, column by column from coarse_apply."""
+    A = _c(A)
+    nC = A.shape[0] * A.shape[-1]
+    M = np.empty((nC, nC), dtype=np.complex128)
+    for k in range(nC):
+        e = np.zeros(nC, dtype=np.complex128)
+        e[k] = 1.0
+        M[:, k] = coarse_apply(A, e.reshape(A.shape[0], A.shape[-1]), Lc).ravel()
+    return M
+
+
+def two_grid_factor(params: Params, U, P, A, e0, k: int):
+    """Two-grid convergence factor (||E_TG^k e0|| / ||e0||)^(1/k) of eq. 3,
+    E_TG = S (I - P (P^dag D P)^-1 P^dag D), with the coarse system solved
+    exactly (dense LU of D_c, numpy) and S the post-smoother of the cycle
+    (params.smoother: mr_steps MR steps, or one GMRES(mr_steps) application,
+    under-relaxed by params.omega).  The iteration is the two-grid method on
+    D x = 0 with x = e: coarse correction e <- e + P D_c^-1 P^dag (-D e), then
+    the smoother on (e, -D e).  Returns (factor, [||e_j|| for j = 0..k])."""
+    U, P, A = _c(U), _c(P), _c(A)
+    L, B = list(params.L), list(params.B)
+    m, tap = params.m, params.tap
+    Lc = coarse_dims(L, B)
+    from scipy.linalg import lu_factor, lu_solve
+    lu = lu_factor(coarse_dense(A, Lc))   # exact coarse solve (small coarse grids only)
+    e = _c(e0).copy()
+    norms = [float(np.linalg.norm(e))]
+    for _ in range(k):
+        r = -dslash(U, e, m, L, tap)
+        y = lu_solve(lu, restrict(P, r, L, B).ravel()).reshape(volume(Lc), -1)
+        e = e + prolong(P, y, L, B)
+        if params.mr_steps > 0:
+            r = -dslash(U, e, m, L, tap)
+            if params.smoother == 1:
+                e = gmres_smooth(U, e, r, m, L, params.mr_steps, params.omega, tap)
+            else:
+                e, _ = mr(U, e, r, m, L, params.mr_steps, params.omega, tap)
+        norms.append(float(np.linalg.norm(e)))
+    return (norms[-1] / norms[0]) ** (1.0 / k), norms

@@ -786,6 +786,29 @@ OR_API int or_gcr_solve(const or_params* p, const double* Ur, const double* Pr, 
  * prolongator and coarse operator.  n_iter = 0 (or group_size >= Nv) skips
  * step (iii).
  */
+/*
+ * The truncated level of the group refinement (Sec. IV: a group is removed
+ * from V and the multigrid method built from the remaining prototypes):
+ * Vt = V without prototypes g0 .. g0 + group_size - 1 (order kept),
+ * Pt = block-orthonormalised Vt (eq. 4), At = Pt^dag D Pt.  Vt, Pt hold
+ * nv - group_size fine vectors; At the coarse operator of that many.
+ */
+OR_API int or_setup_truncated_level(const or_params* p, const double* Ur, const double* Vr, int g0,
+                                    int group_size, double* Vtr, double* Ptr, double* Atr) {
+    int64_t n = vol(p->L) * 12;
+    int nv = p->nv, nt = nv - group_size;
+    if (group_size <= 0 || nt <= 0 || g0 < 0 || g0 + group_size > nv) return OR_ERR_ARG;
+    const cplx* V = (const cplx*)Vr;
+    cplx* Vt = (cplx*)Vtr;
+    int k = 0;
+    for (int i = 0; i < nv; ++i)
+        if (i < g0 || i >= g0 + group_size) memcpy(Vt + (int64_t)(k++) * n, V + (int64_t)i * n, sizeof(cplx) * n);
+    int st = or_block_orthonormalize(p->L, p->B, nt, Vtr, Ptr);
+    if (st != OR_OK) return st;
+    or_coarse_build(p->L, p->B, nt, p->tap, Ur, p->m, Ptr, Atr);
+    return OR_OK;
+}
+
 OR_API int or_setup(const or_params* p, const double* Ur, double* Vr, int init_relax, int n_iter,
                     int group_size, double* Pr, double* Ar) {
     blocking_t bk;
@@ -815,12 +838,8 @@ OR_API int or_setup(const or_params* p, const double* Ur, double* Vr, int init_r
         cplx* Pt = (cplx*)malloc(sizeof(cplx) * n * nt);
         cplx* At = (cplx*)malloc(sizeof(cplx) * bt.Vc * 9 * bt.nc * bt.nc);
         for (int g0 = 0; g0 < nv && st == OR_OK; g0 += group_size) {
-            int k = 0;
-            for (int i = 0; i < nv; ++i)
-                if (i < g0 || i >= g0 + group_size) memcpy(Vt + (int64_t)(k++) * n, V + (int64_t)i * n, sizeof(cplx) * n);
-            st = or_block_orthonormalize(p->L, p->B, nt, (const double*)Vt, (double*)Pt);
+            st = or_setup_truncated_level(p, Ur, Vr, g0, group_size, (double*)Vt, (double*)Pt, (double*)At);
             if (st != OR_OK) break;
-            or_coarse_build(p->L, p->B, nt, p->tap, Ur, p->m, (const double*)Pt, (double*)At);
             mg_t g;
             g.bk = bt; g.p = &pt; g.U = (const cplx*)Ur; g.P = Pt; g.A = At; g.info = NULL;
             for (int i = g0; i < g0 + group_size; ++i) {

@@ -501,3 +501,130 @@ def test_gmres_smoother_lowers_outer_iterations():
         assert info["status"] == 0 and info["true_rel_res"] <= 1e-10
         its[sm] = info["outer_iters"]
     assert its[1] < its[0], its
+
+
+# ---------------------------------------------------------------- eq. 3: two-grid convergence factor
+def _small_level(L=(4, 4, 4, 8), B=(2, 2, 2, 4), nv=4, seed=61, m=-0.2):
+    U = rough_gauge(L, sweeps=5)
+    V0 = synth.gaussian_vectors(L, nv, seed)
+    P, st = oracle.block_orthonormalize(V0, L, B)
+    assert st == 0
+    return L, B, nv, U, m, P, oracle.coarse_build(U, P, m, L, B)
+
+
+def test_two_grid_factor_coarse_correction_identities():
+    """Without smoothing, E_TG = I - P D_c^-1 P^dag D (eq. 3): it annihilates
+    range(P) (a start e0 = P y gives e1 = 0), it is a projection (E^2 = E, so
+    the norms stay at ||E e0|| after the first step), and the corrected error
+    has a Galerkin-orthogonal residual, P^dag D e1 = 0."""
+    L, B, nv, U, m, P, A = _small_level()
+    p0 = oracle.make_params(L, B, nv=nv, m=m, mr_steps=0)
+    Lc = oracle.coarse_dims(L, B)
+    y = synth.gaussian(oracle.volume(Lc) * 2 * nv, 62, 0).reshape(-1, 2 * nv)
+    e_in_P = oracle.prolong(P, y, L, B)
+    f, norms = oracle.two_grid_factor(p0, U, P, A, e_in_P, 1)
+    assert norms[1] < 1e-11 * norms[0]
+    e0 = synth.gaussian_spinor(L, 63)
+    f3, norms3 = oracle.two_grid_factor(p0, U, P, A, e0, 3)
+    assert 0 < norms3[1] < norms3[0]
+    assert abs(norms3[2] - norms3[1]) < 1e-10 * norms3[1] and abs(norms3[3] - norms3[1]) < 1e-10 * norms3[1]
+    # e1 by hand from the definition, then its restricted residual
+    _, n1 = oracle.two_grid_factor(p0, U, P, A, e0, 1)
+    r = -oracle.dslash(U, e0, m, L)
+    Dc = oracle.coarse_dense(A, Lc)
+    e1 = e0 + oracle.prolong(P, np.linalg.solve(Dc, oracle.restrict(P, r, L, B).ravel()).reshape(-1, 2 * nv), L, B)
+    assert abs(np.linalg.norm(e1) - n1[1]) < 1e-12 * n1[1]
+    assert np.linalg.norm(oracle.restrict(P, oracle.dslash(U, e1, m, L), L, B)) < 1e-11 * np.linalg.norm(r)
+
+
+def test_two_grid_factor_smoothing_contracts():
+    """With the post-smoother the two-grid method contracts (factor < 1) and the
+    smoother can only lower the error of the unsmoothed projection here."""
+    L, B, nv, U, m, P, A = _small_level()
+    e0 = synth.gaussian_spinor(L, 64)
+    f0, _ = oracle.two_grid_factor(oracle.make_params(L, B, nv=nv, m=m, mr_steps=0), U, P, A, e0, 4)
+    f4, _ = oracle.two_grid_factor(oracle.make_params(L, B, nv=nv, m=m, mr_steps=4), U, P, A, e0, 4)
+    fg, _ = oracle.two_grid_factor(oracle.make_params(L, B, nv=nv, m=m, mr_steps=4, smoother=1), U, P, A, e0, 4)
+    assert f4 < 1 and fg < 1 and f4 < f0 and fg < f0, (f0, f4, fg)
+
+
+def test_setup_truncated_level_removes_the_group():
+    """The refinement of Sec. IV removes the group being refined from V: the
+    truncated prolongator reproduces every remaining prototype (P_t P_t^dag v = v,
+    eq. 4) and none of the group's, in order."""
+    L, B, nv = (4, 4, 4, 8), (2, 2, 2, 4), 6
+    U = rough_gauge(L, sweeps=5)
+    V = synth.gaussian_vectors(L, nv, 71)
+    p = oracle.make_params(L, B, nv=nv, m=-0.2)
+    for g0 in (0, 2, 4):
+        Vt, Pt, At, st = oracle.setup_truncated_level(p, U, V, g0, 2)
+        assert st == 0 and Vt.shape[0] == nv - 2
+        kept = [i for i in range(nv) if not g0 <= i < g0 + 2]
+        assert all(np.array_equal(Vt[j], V[i]) for j, i in enumerate(kept))
+        for i in range(nv):
+            proj = oracle.prolong(Pt, oracle.restrict(Pt, V[i], L, B), L, B)
+            miss = np.linalg.norm(V[i] - proj) / np.linalg.norm(V[i])
+            if i in kept:
+                assert miss < 1e-12, (g0, i, miss)
+            else:
+                assert miss > 0.5, (g0, i, miss)   # a random vector mostly outside a 4 of 96 per block subspace
+        # the truncated coarse operator is the Galerkin product of the truncated P
+        assert np.abs(At - oracle.coarse_build(U, Pt, -0.2, L, B)).max() == 0
+
+
+@pytest.mark.slow
+def test_setup_lowers_the_two_grid_factor():
+    """Setup quality measured by eq. 3 on the 8^4 beta = 6.0 field at
+    Re(lambda_min) = 0.01 (exact coarse solve, the configuration's MR(4)
+    smoother, one random error): the asymptotic rate (||e_40|| / ||e_20||)^(1/20)
+    orders relaxed + group-refined prototypes < relaxed prototypes < the random
+    starts (0.945 < 0.957 < 0.970; the first iterations are a transient)."""
+    from tests._fields import c1_workload
+    L, B, nv, U, m = c1_workload()
+    V0 = synth.gaussian_vectors(L, nv, 2001)
+    p = oracle.make_params(L, B, nv=nv, m=m)
+    e0 = synth.gaussian_spinor(L, 2002)
+    def rate(P, A):
+        _, n = oracle.two_grid_factor(p, U, P, A, e0, 40)
+        return (n[40] / n[20]) ** (1 / 20)
+
+    Prand, _ = oracle.block_orthonormalize(V0, L, B)
+    f_rand = rate(Prand, oracle.coarse_build(U, Prand, m, L, B))
+    _, P0, A0, st0 = oracle.setup(p, U, V0, init_relax=10, n_iter=0, group_size=4)
+    _, P3, A3, st3 = oracle.setup(p, U, V0, init_relax=10, n_iter=3, group_size=4)
+    assert st0 == 0 and st3 == 0
+    f_relax, f_ref = rate(P0, A0), rate(P3, A3)
+    assert f_ref < f_relax < f_rand < 1, (f_ref, f_relax, f_rand)
+
+
+@pytest.mark.parametrize("smoother,k", [(1, 1), (1, 4), (0, 1)])
+def test_vcycle_smoothing_half(smoother, k):
+    """The post-smoothing half of the V(0, k) cycle (Sec. III-IV) acts on the
+    coarse-corrected residual r' = r - D P D_c^-1 P^dag r: with an exact coarse
+    solve, r - D z equals r' - omega D d with d the least-squares minimiser of
+    ||r' - D d|| over K_k(D, r') (numpy lstsq over the power basis).  GMRES(k)
+    and one MR step (k = 1) alike; a cycle smoothing r instead of r' fails."""
+    L, B, nv, U, m, P, A = _small_level()
+    Lc = oracle.coarse_dims(L, B)
+    omega = 0.9
+    p = oracle.make_params(L, B, nv=nv, m=m, mr_steps=k, smoother=smoother, omega=omega, coarse_tol=1e-15,
+                           coarse_maxit=50000)
+    r = synth.gaussian_spinor(L, 81)
+    z, _ = oracle.vcycle(p, U, P, A, r)
+    Dc = oracle.coarse_dense(A, Lc)
+    e0 = oracle.prolong(P, np.linalg.solve(Dc, oracle.restrict(P, r, L, B).ravel()).reshape(-1, 2 * nv), L, B)
+
+    def expected(res):
+        basis = [res]
+        for _ in range(k - 1):
+            basis.append(oracle.dslash(U, basis[-1], m, L))
+        DK = np.stack([oracle.dslash(U, b, m, L).ravel() for b in basis], axis=1)
+        c, *_ = np.linalg.lstsq(DK, res.ravel(), rcond=None)
+        return res - omega * (DK @ c).reshape(res.shape)
+
+    r1 = r - oracle.dslash(U, e0, m, L)
+    got = r - oracle.dslash(U, z, m, L)
+    want = expected(r1)
+    assert np.abs(got - want).max() < 1e-9 * np.abs(want).max()
+    wrong = r - oracle.dslash(U, e0, m, L) - (r - expected(r))   # smoothing r, not r'
+    assert np.abs(got - wrong).max() > 1e-3 * np.abs(want).max()
