@@ -99,63 +99,92 @@ typedef struct {
                               iteration.  Same iterates in exact arithmetic */
 } mg_params;
 
+/* Outcome of one solve (Sec. IV reports outer iterations and fine matvecs). */
 typedef struct {
-    int outer_iters;       /* preconditioner applications (the paper's outer GCR count) */
+    int outer_iters;       /* preconditioner applications (the paper's outer GCR count, Table I) */
     int coarse_iters;      /* total coarse-solver iterations */
-    int fine_matvecs;      /* fine D applications, all precisions */
+    int fine_matvecs;      /* fine D applications, all precisions (the work unit of Fig. 1) */
     int restarts;          /* true-residual recomputations */
     double true_rel_res;   /* ||b - D x|| / ||b|| in FP64 */
     double solve_ms;       /* device time of the solve (CUDA events) */
     int status;
+    double setup_ms;       /* device time of the context's last adaptive setup (0: none) */
+    double dslash_bytes;   /* algorithmic bytes of the fine D applications of this solve: per
+                              application and site the links, one input and one output spinor
+                              in that application's storage (FP64 960, FP32 480, FP16 248 B) */
 } mg_solve_info;
 
-/* Fill p with the defaults: block 4^4, nvec 8, relax 10, iters 3, group 4,
+/* Fill p with the defaults (Sec. III-IV parameters where the paper gives them):
+ * block 4^4, nvec 8, relax 10, iters 3, group 4,
  * smoother 4, omega 0.9, restart 16, tol 1e-10, coarse_tol 1e-3,
  * max_outer 1000, max_coarse 5000, delta 0, FP64, coarse_check 16, coarse_kernel 0,
  * smoother 0 (MR), smoother_fp16 0, coarse_form 0. */
 int mg_default_params(mg_params* p);
 
-/* Create a context for an L0 x L1 x L2 x L3 lattice.  dims[mu] must be a
- * multiple of p->block[mu].  stream is a cudaStream_t (NULL: legacy default).
+/* Create a context for the Wilson-Dirac system D(U) psi = b (eqs. 1-2) on an
+ * L0 x L1 x L2 x L3 lattice.  dims[mu] must be a multiple of p->block[mu]
+ * (geometric 4^4 aggregates, Sec. III).  stream is a cudaStream_t (NULL:
+ * legacy default); the device current at this call owns the context.
  * Allocates the device buffers of the fine level; the coarse level is
- * allocated by mg_set_null_vectors / mg_setup. */
+ * allocated by mg_set_null_vectors / mg_setup.  *out is NULL on error. */
 int mg_create(const int dims[4], int t_antiperiodic, const mg_params* p, void* stream, mg_ctx** out);
 
-/* Free every device buffer of the context.  Accepts NULL. */
+/* Free every device buffer of the context (synchronises its stream first).
+ * Accepts NULL. */
 void mg_destroy(mg_ctx* ctx);
 
-/* Copy SU(3) links (host, boundary layout, 4*V*9 complex) to the device. */
+/* Copy the SU(3) links U_x^mu of eq. 2 (host, boundary layout, 4*V*9
+ * complex) to the device.  Synchronous.  Invalidates the coarse level (D_c
+ * depends on U): run mg_setup or mg_set_null_vectors again. */
 int mg_set_links(mg_ctx* ctx, const double* U);
+
+/* As mg_set_links with U_dev in device memory (boundary layout, FP64, owned by
+ * the caller).  Stream-ordered, no host synchronisation: the conversion waits
+ * for the work already queued on `stream` (a cudaStream_t; NULL: legacy
+ * default) and later work on `stream` waits for the conversion, so the caller
+ * may overwrite or free U_dev after queuing it there. */
+int mg_set_links_device(mg_ctx* ctx, const double* U_dev, void* stream);
 
 /* Bare mass m of eq. (2).  After a setup the coarse operator is shifted in
  * place: D_c(m) = D_c(m0) + (m - m0) I, exact because P^dag P = I (eq. 4). */
 int mg_set_mass(mg_ctx* ctx, double m);
 
-/* Replace the solver parameters that do not change buffer sizes (tolerances,
- * smoother, restart <= the value at create, precision, ...). */
+/* Replace the solver parameters (Sec. III-IV) that do not change buffer sizes
+ * (tolerances, smoother, restart <= the value at create, precision, ...);
+ * nvec and block are fixed at create (MG_ERR_INVALID_ARG otherwise). */
 int mg_set_params(mg_ctx* ctx, const mg_params* p);
 
 /* Adaptive setup (Sec. II alpha-SA loop in the two-step form of Sec. IV) from
  * caller-provided random starts V0 (host, Nv fine vectors): relaxation, group
  * refinement with the truncated two-level method, block orthonormalisation
- * (eq. 4) and the Galerkin coarse operator D_c = P^dag D P. */
+ * (eq. 4) and the Galerkin coarse operator D_c = P^dag D P.  The starts are
+ * an argument, not a seed, so that any generator (and the CPU checker of the
+ * tests) can supply identical vectors; the paper only asks for random ones.
+ * Run at the lightest mass of interest (Sec. IV: the prototypes serve every
+ * heavier mass); info.setup_ms of later solves reports its device time. */
 int mg_setup(mg_ctx* ctx, const double* V0);
 
-/* As mg_setup with the random starts in device memory (boundary layout, FP64). */
+/* As mg_setup (Sec. II, IV) with the random starts in device memory
+ * (boundary layout, FP64, owned by the caller; read before the call returns). */
 int mg_setup_device(mg_ctx* ctx, const double* V0_dev);
 
 /* Use the given prototypes (host, nv == p->nvec fine vectors) as they are:
- * block-orthonormalise them (eq. 4) and build D_c = P^dag D P. */
+ * block-orthonormalise them (eq. 4) and build D_c = P^dag D P (Sec. III).
+ * MG_ERR_NUMERIC when an aggregate's prototypes are rank-deficient. */
 int mg_set_null_vectors(mg_ctx* ctx, const double* V, int nv);
 
-/* Read back the block-orthonormal prolongator columns (host, Nv fine
- * vectors: column (X, s, i) is vector i on the sites of X and spins of s). */
+/* Read back the block-orthonormal prolongator columns of eq. 4 (host, Nv
+ * fine vectors: column (X, s, i) is vector i on the sites of X and spins of
+ * s, chirality kept as in Sec. III). */
 int mg_get_prolongator(mg_ctx* ctx, double* P);
 
-/* Read back the current prototypes (host, Nv fine vectors). */
+/* Read back the current prototypes V (the near-null vectors of Sec. II;
+ * host, Nv fine vectors). */
 int mg_get_null_vectors(mg_ctx* ctx, double* V);
 
-/* Read back D_c in FP64 (host, boundary coarse-operator layout). */
+/* Read back the Galerkin coarse operator D_c = P^dag D P (Sec. III, nearest
+ * neighbour with 2Nv x 2Nv links) in FP64 (host, boundary coarse-operator
+ * layout). */
 int mg_get_coarse_op(mg_ctx* ctx, double* A);
 
 /* Solve D x = b by MG-preconditioned flexible GCR (Sec. III), x0 = 0.
@@ -163,26 +192,33 @@ int mg_get_coarse_op(mg_ctx* ctx, double* A);
  * last iterate when max_outer is reached. */
 int mg_solve(mg_ctx* ctx, const double* b, double* x, mg_solve_info* info);
 
-/* As mg_solve with b and x in device memory (boundary layout, FP64). */
+/* As mg_solve (Sec. III) with b and x in device memory (boundary layout,
+ * FP64, owned by the caller); synchronises the context stream. */
 int mg_solve_device(mg_ctx* ctx, const double* b_dev, double* x_dev, mg_solve_info* info);
 
-/* Solve D x_n = b_n for nrhs sources together (12 spin-colour point sources
- * plus Gaussian sources, say): flexible GCR in lockstep over the sources, each
+/* Solve D x_n = b_n (eq. 1) for nrhs sources together (12 spin-colour point
+ * sources plus Gaussian sources, say; the paper solves one point source at a
+ * time, Sec. IV): flexible GCR (Sec. III) in lockstep over the sources, each
  * with its own Krylov space and scalars, the fine-level steps per source and
  * the coarse solve of all sources as one batched CGNR on an RHS panel, its
  * stencil a dense contraction on the tensor cores (FP16 operator, FP16 hi+lo
  * panel, FP32 accumulation), its iterations replayed from a captured CUDA
  * graph.  b, x: nrhs consecutive host fine spinors; info: nrhs entries.
- * Needs prec_inner == MG_FP32 and 2*nvec a multiple of 16 (<= 128),
- * nrhs <= 256; with MG_FP64 the sources are solved one after another. */
+ * Needs prec_inner MG_FP32 or MG_FP16 (the smoother then follows the FP16
+ * storage rules of mg_params.smoother_fp16) and 2*nvec a multiple of 16
+ * (<= 128), nrhs <= 256; with MG_FP64 the sources are solved one after
+ * another. */
 int mg_solve_batched(mg_ctx* ctx, const double* b, double* x, int nrhs, mg_solve_info* info);
 
-/* As mg_solve_batched with b and x in device memory (boundary layout). */
+/* As mg_solve_batched with b and x in device memory (boundary layout, nrhs
+ * consecutive fine spinors, owned by the caller). */
 int mg_solve_batched_device(mg_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, mg_solve_info* info);
 
-/* Coarse stencil on nrhs coarse vectors at once: y_n = D_c x_n (dagger: D_c^dag).
- * x, y: nrhs consecutive host coarse vectors.  impl 0: tensor cores (FP16
- * operator, as in the batched solve); impl 1: SIMT with the FP64 operator. */
+/* Coarse stencil (Sec. III) on nrhs coarse vectors at once: y_n = D_c x_n
+ * (dagger: D_c^dag).  x, y: nrhs consecutive host coarse vectors, nrhs <= 256.
+ * impl 0: tensor cores (operator rounded to FP16 without scale, each source
+ * scaled to max |x| = 1 and split into FP16 hi + lo, FP32 accumulation; needs
+ * 2 nvec a multiple of 16 and <= 128); impl 1: SIMT with the FP64 operator. */
 int mg_apply_coarse_batched(mg_ctx* ctx, const double* x, double* y, int nrhs, int dagger, int impl);
 
 /* ---- single steps of the method (host buffers, FP64 at the boundary; the
@@ -192,22 +228,28 @@ int mg_apply_coarse_batched(mg_ctx* ctx, const double* x, double* y, int nrhs, i
  * FP16 links, out rounded likewise (the smoother's storage). */
 int mg_apply_dslash(mg_ctx* ctx, const double* in, double* out, int prec);
 
-/* r_c = P^dag r (eq. 8 with R = P^dag, chirality kept). */
+/* r_c = P^dag r: the restriction of the coarse-grid correction (eq. 5 with
+ * R = P^dag once the gamma5 factors cancel, chirality kept, Sec. III). */
 int mg_restrict(mg_ctx* ctx, const double* r, double* rc, int prec);
 
-/* e = P y_c. */
+/* e = P y_c: prolongation of a coarse vector (eq. 5, Sec. III). */
 int mg_prolong(mg_ctx* ctx, const double* yc, double* e, int prec);
 
-/* y = D_c x, or D_c^dag x = sigma3 D_c sigma3 x when dagger != 0. */
+/* y = D_c x, or D_c^dag x = sigma3 D_c sigma3 x when dagger != 0 (the coarse
+ * operator keeps gamma5-hermiticity as sigma3-hermiticity, Sec. III). */
 int mg_apply_coarse(mg_ctx* ctx, const double* x, double* y, int dagger, int prec);
 
-/* nsteps MR smoothing steps on (e, r): q = D r, alpha = omega <q,r>/<q,q>,
+/* nsteps MR smoothing steps (GMRES(1) restarts with under-relaxation omega,
+ * the smoother of Sec. III) on (e, r): q = D r, alpha = omega <q,r>/<q,q>,
  * e += alpha r, r -= alpha q.  e and r are read and overwritten.  MG_FP16:
  * r and q stored in FP16 with a per-site scale, FP16 links, e in FP32. */
 int mg_mr(mg_ctx* ctx, double* e, double* r, int nsteps, int prec);
 
 /* Coarse solve y = CGNR(D_c, rc) from y = 0 to ||rc - D_c y|| <= tol ||rc||
- * or maxit iterations (tol = 0: exactly maxit). */
+ * or maxit iterations (tol = 0: exactly maxit): CG on the normal equations,
+ * the coarsest-grid solver of Sec. IV.  rc, y: host coarse vectors; *iters
+ * and *final_rel (may be NULL) receive the iterations and the final relative
+ * coarse residual. */
 int mg_coarse_solve(mg_ctx* ctx, const double* rc, double* y, double tol, int maxit, int prec,
                     int* iters, double* final_rel);
 
@@ -229,27 +271,32 @@ int mg_coarse_solve(mg_ctx* ctx, const double* rc, double* y, double tol, int ma
  *     the arrival counter is cleared on every call, everything else is
  *     written before it is read.  Calls that overlap on the GPU (other
  *     streams, other host threads, other contexts on the same device) race.
- *   - Work runs on the context's stream; the call synchronises that stream. */
+ *   - Work runs on the context's stream; the call synchronises that stream.
+ *   - The context's device (current at mg_create) must be current, else
+ *     MG_ERR_INVALID_ARG. */
 int mg_coarse_solve_noalloc(mg_ctx* ctx, const double* rc_dev, double* y_dev, double tol, int maxit, int* iters,
                             double* final_rel);
 
-/* z = M r, one two-level V(0, smoother_steps) cycle. */
+/* z = M r, one two-level V(0, smoother_steps) cycle (Sec. II-III: coarse
+ * correction with R = P^dag, then post-smoothing; the preconditioner of the
+ * flexible GCR).  r, z: host fine spinors. */
 int mg_vcycle(mg_ctx* ctx, const double* r, double* z, int prec);
 
-/* Device-resident operator application for timing: out = D in on internal
+/* Device-resident application of eq. 2 for timing (a measurement hook, no
+ * counterpart in the paper): out = D in on internal
  * buffers of the context, `reps` launches, returns the mean kernel time in
  * ms (CUDA events on the context stream) and the bytes one launch must move
  * at minimum (algorithmic: links + input + output, each read/written once). */
 int mg_time_dslash(mg_ctx* ctx, int prec, int reps, double* ms_per_launch, double* bytes_per_launch);
 
-/* As mg_time_dslash, with the L2 cache flushed before every launch: the
+/* As mg_time_dslash (eq. 2), with the L2 cache flushed before every launch: the
  * caller's device buffer `flush` (flush_bytes, larger than the L2) is
  * overwritten on the context stream between launches, and only the dslash
  * launches are timed (one event pair each). */
 int mg_time_dslash_cold(mg_ctx* ctx, int prec, int reps, void* flush, size_t flush_bytes, double* ms_per_launch,
                         double* bytes_per_launch);
 
-/* Kernel classes for the launch timer below. */
+/* Kernel classes for the launch timer below (steps of Sec. II-IV). */
 enum mg_kernel_class {
     MG_K_DSLASH = 0,       /* fine Wilson operator, all variants and precisions */
     MG_K_COARSE_SOLVE = 1, /* persistent CGNR on D_c (whole coarse solve per launch) */
@@ -262,7 +309,8 @@ enum mg_kernel_class {
     MG_K_NCLASSES = 8
 };
 
-/* Launch timer: while enabled, every launch of a tracked kernel class is
+/* Launch timer (a measurement hook, no counterpart in the paper): while
+ * enabled, every launch of a tracked kernel class is
  * bracketed by CUDA events on the context stream (negligible device cost).
  * mg_profile_read synchronises the stream and returns, per class, the summed
  * device time (ms) and the launch count since the last read (then resets);
@@ -272,7 +320,8 @@ int mg_profile_enable(mg_ctx* ctx, int on);
 int mg_profile_read(mg_ctx* ctx, double* ms, int* launches, double* coarse_iters);
 
 /* Number of kernel launches this library has issued in the process so far
- * (all contexts); the difference over a region counts its launches. */
+ * (all contexts); the difference over a region counts its launches (a
+ * measurement hook, no counterpart in the paper). */
 long long mg_kernel_launches(void);
 
 /* Which coarse CGNR kernel the last coarse solve of this context ran (a
@@ -283,6 +332,21 @@ long long mg_kernel_launches(void);
 enum mg_coarse_kernel_id { MG_CK_NONE = -1, MG_CK_REGISTER = 0, MG_CK_SMEM = 1, MG_CK_STREAM = 2, MG_CK_TMEM = 3 };
 int mg_coarse_kernel(mg_ctx* ctx);
 
+/* Check of the library's bounded device waits (the paper has no counterpart;
+ * every spin-wait in these kernels gives up after a poll limit, raises the
+ * context's error flag and returns instead of hanging).  Runs one small kernel
+ * that drives one wait primitive into a configuration that cannot complete,
+ * with a poll limit of spin_limit (1 .. 1e7): kind 0 the epoch exchange of the
+ * on-chip coarse CG (one publishing CTA missing), 1 the counter grid barrier of
+ * the persistent CG (one arrival missing), 2 an mbarrier transaction that no
+ * copy completes, 3 an epoch-tagged vector entry never written.  Returns
+ * MG_ERR_TIMEOUT when the wait gave up as designed (the context stays usable),
+ * MG_OK if it unexpectedly completed, another status on a CUDA error. */
+int mg_check_wait_timeout(mg_ctx* ctx, int kind, long long spin_limit);
+
+/* Name of a status code; last error message of a context (NUL-terminated,
+ * owned by the library: valid until the next call on that context).  No
+ * counterpart in the paper. */
 const char* mg_status_string(int status);
 const char* mg_last_error(const mg_ctx* ctx);
 

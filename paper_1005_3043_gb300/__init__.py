@@ -48,7 +48,7 @@ class MgParams(ctypes.Structure):
 class MgSolveInfo(ctypes.Structure):
     _fields_ = [("outer_iters", ctypes.c_int), ("coarse_iters", ctypes.c_int), ("fine_matvecs", ctypes.c_int),
                 ("restarts", ctypes.c_int), ("true_rel_res", ctypes.c_double), ("solve_ms", ctypes.c_double),
-                ("status", ctypes.c_int)]
+                ("status", ctypes.c_int), ("setup_ms", ctypes.c_double), ("dslash_bytes", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -69,6 +69,7 @@ _SIGS = {
     "mg_create": ([_P, _I, _P, _P, _P], _I),
     "mg_destroy": ([_P], None),
     "mg_set_links": ([_P, _P], _I),
+    "mg_set_links_device": ([_P, _P, _P], _I),
     "mg_set_mass": ([_P, _D], _I),
     "mg_set_params": ([_P, _P], _I),
     "mg_setup": ([_P, _P], _I),
@@ -96,6 +97,7 @@ _SIGS = {
     "mg_profile_read": ([_P, _P, _P, _P], _I),
     "mg_kernel_launches": ([], ctypes.c_longlong),
     "mg_coarse_kernel": ([ctypes.c_void_p], ctypes.c_int),
+    "mg_check_wait_timeout": ([_P, _I, ctypes.c_longlong], _I),
     "mg_status_string": ([_I], ctypes.c_char_p),
     "mg_last_error": ([_P], ctypes.c_char_p),
 }
@@ -182,6 +184,11 @@ def mg_destroy(ctx) -> None:
 
 def mg_set_links(ctx, U) -> None:
     _check(load().mg_set_links(ctx, _ptr(_host(U))), ctx)
+
+
+def mg_set_links_device(ctx, U_dev, stream=None) -> None:
+    """Links from device memory (boundary layout, complex128), ordered on ``stream``."""
+    _check(load().mg_set_links_device(ctx, _dev_ptr(U_dev), _stream_ptr(stream)), ctx)
 
 
 def mg_set_mass(ctx, m: float) -> None:
@@ -359,6 +366,11 @@ def mg_coarse_kernel(ctx) -> int:
     return int(load().mg_coarse_kernel(ctx))
 
 
+def mg_check_wait_timeout(ctx, kind: int, spin_limit: int = 20000) -> int:
+    """Status of one bounded device wait driven to give up (MG_ERR_TIMEOUT expected)."""
+    return int(load().mg_check_wait_timeout(ctx, int(kind), int(spin_limit)))
+
+
 def mg_profile_enable(ctx, on: bool = True) -> None:
     _check(load().mg_profile_enable(ctx, int(bool(on))), ctx)
 
@@ -404,6 +416,9 @@ class WilsonMG:
 
     def set_links(self, U):
         mg_set_links(self.ctx, U)
+
+    def set_links_device(self, U_dev, stream=None):
+        mg_set_links_device(self.ctx, U_dev, stream)
 
     def set_mass(self, m):
         mg_set_mass(self.ctx, m)

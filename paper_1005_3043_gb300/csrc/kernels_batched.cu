@@ -14,6 +14,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "mg_launch.h"
@@ -112,13 +113,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_coarse_apply_tc(TcApplyArgs a
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * SA + 4 * SB);   // [0,1]: A landed, [2,3]: MMA done
     __shared__ uint32_t s_taddr;
     __shared__ int s_fail;
+    __shared__ int s_last_commit;     // stage * 2 + parity of the last MMA commit, -1: none
     __shared__ float s_nrm[4][256];
     const int X = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t ncols = tc_tmem_cols(nw);
     const uint32_t bytesA = (uint32_t)(K * K * 2);
 
+    // bulk copy issued by thread 0 and not yet seen complete: stage, parity
+    int copy_pending = -1, copy_parity = 0;
     if (tid == 0) {
         s_fail = 0;
+        s_last_commit = -1;
         for (int i = 0; i < 4; ++i) mbar_init(bar + i, 1);
         fence_mbar_init();
     }
@@ -150,6 +155,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_coarse_apply_tc(TcApplyArgs a
         if (tid == 0) {
             mbar_expect_tx(bar + s, bytesA);
             bulk_copy_g2s(As + (size_t)s * 128 * K, a.Aemb + ((size_t)X * 9 + d) * K * K, bytesA, bar + s);
+            copy_pending = s;
+            copy_parity = (d >> 1) & 1;
         }
         // B = x[X+d] as hi + lo FP16, rows = RHS n, K-major columns k = (re|im, b)
         const int Y = coarse_neighbour(a.g, X, d);
@@ -177,6 +184,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_coarse_apply_tc(TcApplyArgs a
             if (!mbar_wait(bar + s, (d >> 1) & 1, kTcWaitLimit)) {
                 s_fail = 1;
             } else {
+                copy_pending = -1;
                 tc_fence_after();
                 const uint32_t a0 = smem_u32(As + (size_t)s * 128 * K);
                 const uint32_t bh0 = smem_u32(bh), bl0 = smem_u32(bl);
@@ -186,13 +194,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_coarse_apply_tc(TcApplyArgs a
                     mma_f16(tmem, ad, smem_desc(bl0 + ks * 256, lbo, sbo), idesc, 1u);
                 }
                 mma_commit(bar + 2 + s);
+                s_last_commit = s * 2 + ((d >> 1) & 1);
             }
         }
     }
     __syncthreads();
-    // wait for the last commit (direction 8 on stage 0, its 5th use): covers every MMA issued
+    // Wait for the last commit (direction 8 on stage 0, its 5th use, when nothing
+    // failed): it covers every MMA this CTA issued.  After a failed wait the CTA
+    // still drains what it started -- the last MMAs and a bulk copy it has not
+    // seen land -- with bounded waits, so that no asynchronous write into its
+    // shared or tensor memory outlives it.
     bool ok = (s_fail == 0);
-    if (!mbar_wait(bar + 2, 0, kTcWaitLimit)) ok = false;
+    const int lc = s_last_commit;
+    if (lc >= 0 && !mbar_wait(bar + 2 + (lc >> 1), lc & 1, kTcWaitLimit)) ok = false;
+    if (tid == 0 && copy_pending >= 0 && !mbar_wait(bar + copy_pending, copy_parity, kTcWaitLimit)) ok = false;
     tc_fence_after();
     // epilogue: warp w owns TMEM lanes 32w..32w+31 = embedded rows m
     const int m = warp * 32 + lane;
@@ -263,11 +278,18 @@ cudaError_t coarse_apply_tc(const TcApplyArgs& args, cudaStream_t st) {
 
 // Chunk width for (nc, npad): every candidate (multiples of 16 dividing npad)
 // is timed with CUDA events on the given stream and the fastest is kept.
+// The cache is keyed by device as well and guarded for concurrent host threads.
 int coarse_apply_tc_tune(const TcApplyArgs& args, cudaStream_t st) {
-    struct Entry { int nc, npad, nw; };
+    struct Entry { int dev, nc, npad, nw; };
     static std::vector<Entry> cache;
-    for (const Entry& e : cache)
-        if (e.nc == args.nc && e.npad == args.npad) return e.nw;
+    static std::mutex mu;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        for (const Entry& e : cache)
+            if (e.dev == dev && e.nc == args.nc && e.npad == args.npad) return e.nw;
+    }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -288,7 +310,8 @@ int coarse_apply_tc_tune(const TcApplyArgs& args, cudaStream_t st) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cache.push_back({args.nc, args.npad, best});
+    std::lock_guard<std::mutex> lock(mu);
+    cache.push_back({dev, args.nc, args.npad, best});
     return best;
 }
 

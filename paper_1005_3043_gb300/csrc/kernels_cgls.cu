@@ -27,6 +27,7 @@
 // with the vector updates done while staging (p and r double-buffered).
 // Chronopoulos-Gear (cgls_body_tag, the default): one exchange per iteration,
 // the vectors read across CTAs carrying epoch tags instead of barriers.
+#include <atomic>
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -699,16 +700,24 @@ void coarse_pack_units(void* Au, float* su, const double2* A, int nc, int ru, in
 // ---------------------------------------------------------------- shape and launch
 namespace {
 struct DevLimits {
-    int sms = 0, smem = 0;
+    int sms = 0, smem = 0, dev = -1;
 };
+constexpr int kCglsDevs = 16;
+// SM count and opt-in shared memory of the current device, looked up once per
+// device (atomic slots: host threads calling at once see 0 or the final value)
 DevLimits dev_limits() {
-    static DevLimits cached[16];
+    static std::atomic<int> c_sms[kCglsDevs], c_smem[kCglsDevs];
+    DevLimits l;
     int dev = 0;
-    cudaGetDevice(&dev);
-    DevLimits& l = cached[dev & 15];
-    if (l.sms == 0) {
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kCglsDevs) return l;
+    l.dev = dev;
+    l.sms = c_sms[dev].load(std::memory_order_acquire);
+    l.smem = c_smem[dev].load(std::memory_order_acquire);
+    if (l.sms == 0 || l.smem == 0) {
         cudaDeviceGetAttribute(&l.sms, cudaDevAttrMultiProcessorCount, dev);
         cudaDeviceGetAttribute(&l.smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        c_smem[dev].store(l.smem, std::memory_order_release);
+        c_sms[dev].store(l.sms, std::memory_order_release);
     }
     return l;
 }
@@ -763,16 +772,20 @@ bool cgls_shape(int nc, int Vc, bool h16, int mode, CglsShape* out) {
             s.slots = 2;
             score = (long long)s.nu_max * ru;
         } else if (mode == CGLS_AUTO && chunks <= 4 && off <= budget) {
-            // the operator in tensor memory; shared memory padded past half an SM so
-            // that no second CTA (and no second TMEM allocation) shares the SM
+            // the operator in tensor memory; shared memory padded to the whole
+            // per-CTA budget, so that with the per-CTA reservation and the static
+            // shared memory it fills the SM: no other CTA -- a second one of this
+            // kernel, or a tensor-core stencil CTA launched from another stream or
+            // context -- can share the SM and hold TMEM columns this CTA's
+            // all-512-column allocation would wait for
             s.tm = 1;
             s.tm_chunks = chunks;
             s.resident = 1;
             s.slots = 0;
             s.wave = s.nu_max;
             s.groups = 1;
-            off = std::max(off, (size_t)lim.smem / 2 + 4096);
             if (off > budget) continue;
+            off = budget;
             score = (long long)s.nu_max * ru;
         } else if (off + (size_t)s.nu_max * s.stride <= budget) {
             s.resident = 1;
@@ -802,12 +815,13 @@ cudaError_t cgls_onchip(const CglsArgs& args, cudaStream_t st) {
     const void* fns[2][2] = {{(const void*)k_cgls_onchip<false, false>, (const void*)k_cgls_onchip<false, true>},
                              {(const void*)k_cgls_onchip<true, false>, (const void*)k_cgls_onchip<true, true>}};
     const void* fn = fns[h16][tm];
-    static bool attr[2][2] = {{false, false}, {false, false}};
+    static std::atomic<bool> attr[kCglsDevs][2][2];   // per device: the attribute is set on the current one
     const DevLimits lim = dev_limits();
-    if (!attr[h16][tm]) {
+    if (lim.dev < 0) return cudaErrorInvalidDevice;
+    if (!attr[lim.dev][h16][tm].load(std::memory_order_acquire)) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lim.smem - 1024);
         if (e != cudaSuccess) return e;
-        attr[h16][tm] = true;
+        attr[lim.dev][h16][tm].store(true, std::memory_order_release);
     }
     if ((args.form == CGLS_CG_TAGGED && !args.tag) || args.sh.smem > (size_t)lim.smem - 1024 || args.sh.grid <= 0 ||
         args.sh.grid > lim.sms ||
@@ -824,4 +838,48 @@ cudaError_t cgls_onchip(const CglsArgs& args, cudaStream_t st) {
     return cudaLaunchCooperativeKernel(fn, dim3(a.sh.grid), dim3(kCglsThreads), params, a.sh.smem, st);
 }
 
+}  // namespace wmg
+
+// ---------------------------------------------------------------- bounded-wait check
+namespace wmg {
+// Drives one of the library's device-side waits into a configuration that
+// cannot complete, with a short poll limit, so that a test can check that the
+// wait gives up, raises the error flag and returns (the kernel then exits
+// normally and the context stays usable).  Buffers (all zeroed by the caller):
+// words >= 2 * kXchMaxNV * (G + 1) * kXchPad 64-bit words; ctr >= 3 uints;
+// err 1 int.  kind 0: epoch exchange expecting G + 1 publishing CTAs (slot G is
+// never written); 1: counter barrier expecting G + 1 arrivals; 2: mbarrier
+// transaction of 16 bytes that no copy completes; 3: epoch-tagged entry never
+// stored with the awaited epoch.
+__global__ void k_wait_probe(int kind, unsigned long long* words, unsigned int* ctr, int* err, long long limit) {
+    __shared__ float sc[kXchMaxNV * (32 + 64 + 2)];
+    __shared__ __align__(8) uint64_t bar;
+    const int G = gridDim.x;
+    if (kind == 0) {
+        float v[1] = {1.f};
+        xch_allreduce<1>(v, words, 1u, err, sc, G + 1, limit);
+    } else if (kind == 1) {
+        grid_sync(ctr, ctr + 1, (unsigned int)G + 1u, err, limit);
+    } else if (kind == 2) {
+        if (threadIdx.x == 0) {
+            mbar_init(&bar, 1);
+            fence_mbar_init();
+            mbar_expect_tx(&bar, 16);
+            if (!mbar_wait(&bar, 0, limit)) atomicExch(err, 1);
+        }
+    } else if (kind == 3) {
+        if (threadIdx.x == 0) {
+            float2 v;
+            tag_wait(words, 5u, err, v, limit);
+        }
+    }
+}
+
+cudaError_t wait_probe(int kind, int G, unsigned long long* words, unsigned int* ctr, int* err, long long limit,
+                       cudaStream_t st) {
+    if (kind < 0 || kind > 3 || G < 1 || G > 64 || limit < 1) return cudaErrorInvalidValue;
+    note_launch();
+    k_wait_probe<<<G, 128, 0, st>>>(kind, words, ctr, err, limit);
+    return cudaGetLastError();
+}
 }  // namespace wmg

@@ -2,6 +2,7 @@
 // prototypes (eq. 4 with the chirality split), restriction r_c = P^dag r,
 // prolongation e = P y, the Galerkin coarse operator D_c = P^dag D P and its
 // nearest-neighbour application, and the CGNR (CGLS) coarse solve steps.
+#include <atomic>
 #include "mg_launch.h"
 #include "mg_sync.cuh"
 
@@ -850,19 +851,23 @@ template <typename T, bool H16> size_t cgnr_smem(int nc) {
 
 // co-resident CTAs for this nc, then the smallest balanced grid covering all aggregates
 template <typename T, bool H16> int cgnr_grid(int nc, int Vc) {
-    static int cached[2][128] = {};
+    // per device (SM count and occupancy may differ between devices); slots are
+    // atomic so host threads calling at once see either 0 or the final value
+    constexpr int kDevs = 16;
+    static std::atomic<int> cached[kDevs][2][128];
     int dev = 0;
-    cudaGetDevice(&dev);
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevs) return 0;
     int key = nc < 128 ? nc : 127;
-    int* slot = &cached[H16 ? 1 : 0][key];
-    if (*slot == 0) {
+    std::atomic<int>& slot = cached[dev][H16 ? 1 : 0][key];
+    int gmax = slot.load(std::memory_order_acquire);
+    if (gmax == 0) {
         int sms = 0, per = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         size_t sm = cgnr_smem<T, H16>(nc);   // < 48 KB: no attribute needed
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cgnr_persistent<T, H16>, cgnr_block_threads<T, H16>(nc), sm);
-        *slot = per * sms;
+        gmax = per * sms;
+        slot.store(gmax, std::memory_order_release);
     }
-    int gmax = *slot;
     if (gmax <= 0) return 0;
     int xpb = cgnr_xpb<T, H16>(nc);
     int batches = (Vc + xpb - 1) / xpb;               // CTA-sized pieces of work

@@ -117,6 +117,8 @@ struct mg_ctx {
     double2* protos_stage = nullptr; // boundary layout, nv vectors
     double2* Aself = nullptr;        // coarse-build scratch
     double2* cstage = nullptr;       // coarse staging (FP64)
+    int dev = 0;                     // device current at mg_create (owns every buffer and the stream)
+    double setup_ms = 0.0;           // device time of the last adaptive setup (CUDA events)
     CoarseLevel full, trunc;
     BatchWork bw;
     Work<float> wf;
@@ -270,6 +272,15 @@ template <typename T> int ensure_work(mg_ctx* ctx) {
 
 int ensure_level(mg_ctx* ctx, CoarseLevel& L, int nv) {
     if (L.cap < nv) {
+        // every buffer sized by the capacity goes, the derived ones (FP16 copy,
+        // tensor-core embedding) are rebuilt at the new size on demand
+        CK(cudaStreamSynchronize(ctx->st));
+        for (void* q : {(void*)L.P64, (void*)L.P32, (void*)L.A64, (void*)L.A32, (void*)L.Aemb, (void*)L.A16,
+                        (void*)L.s16})
+            dfree(ctx, q);
+        L.P64 = nullptr; L.P32 = nullptr; L.A64 = nullptr; L.A32 = nullptr;
+        L.Aemb = nullptr; L.A16 = nullptr; L.s16 = nullptr;
+        L.emb_valid = L.a16_valid = L.au_valid = L.valid = false;
         size_t np = (size_t)nv * nfine(ctx);
         size_t na = (size_t)ctx->g.Vc * 9 * (2 * nv) * (2 * nv);
         TRY(dalloc(ctx, &L.P64, sizeof(double2) * np));
@@ -454,9 +465,23 @@ int check_timeout(mg_ctx* ctx) {
 }
 
 // ---------------------------------------------------------------- V(0, n) cycle
+// Algorithmic bytes per lattice site of one fine operator application: the
+// links, one input and one output spinor, each read or written once, in the
+// application's storage precision (FP16: 4 x 9 complex link entries in FP16,
+// spinors as 12 complex FP16 plus one FP32 site scale).
+constexpr double kDslashBytesF64 = 960.0, kDslashBytesF32 = 480.0, kDslashBytesF16 = 144.0 + 2 * 52.0;
+template <typename T> constexpr double dslash_site_bytes() {
+    return sizeof(T) == 8 ? kDslashBytesF64 : kDslashBytesF32;
+}
+
 struct Counters {
     int coarse_iters = 0;
     int matvecs = 0;
+    double site_bytes = 0.0;   // sum over applications of the bytes per site
+    void fine(int k, double bytes_per_site) {
+        matvecs += k;
+        site_bytes += k * bytes_per_site;
+    }
 };
 
 // FP16 links and the FP16 smoother vectors (MG_FP16 mode), built on first use
@@ -552,7 +577,7 @@ int smooth(mg_ctx* ctx, const v2<T>* r, v2<T>* z, const Reduce& R, Counters& cnt
         gmres_ls(Rs, steps, ctx->prm.omega, ctx->st);
         h_multi_axpy(zf, B, S, ctx->g, steps, Rs, ctx->st);
         PROF_END(MG_K_KRYLOV);
-        cnt.matvecs += steps + 1;
+        cnt.fine(steps + 1, kDslashBytesF16);
         return MG_OK;
     }
     if (ctx->prm.smoother == 1 && steps > 0) {
@@ -589,7 +614,7 @@ int smooth(mg_ctx* ctx, const v2<T>* r, v2<T>* z, const Reduce& R, Counters& cnt
         gmres_ls(Rs, steps, ctx->prm.omega, ctx->st);
         multi_axpy<T>(z, V, n, steps, Rs, ctx->st);
         PROF_END(MG_K_KRYLOV);
-        cnt.matvecs += steps + 1;
+        cnt.fine(steps + 1, dslash_site_bytes<T>());
         return MG_OK;
     }
     if (std::is_same<T, float>::value && smoother_fp16(ctx)) {
@@ -599,7 +624,7 @@ int smooth(mg_ctx* ctx, const v2<T>* r, v2<T>* z, const Reduce& R, Counters& cnt
         PROF_BEGIN(MG_K_DSLASH);
         dslash_h_xmy(hr, zf, ctx->U16, reinterpret_cast<const float2*>(r), ctx->g, ctx->mass, ctx->st);
         PROF_END(MG_K_DSLASH);
-        cnt.matvecs += 1;
+        cnt.fine(1, kDslashBytesF16);
         for (int k = 0; k < steps; ++k) {
             PROF_BEGIN(MG_K_DSLASH);
             dslash_h_mrdot(hq, hr, ctx->U16, ctx->g, ctx->mass, ctx->prm.omega, R, ctx->st);
@@ -607,7 +632,7 @@ int smooth(mg_ctx* ctx, const v2<T>* r, v2<T>* z, const Reduce& R, Counters& cnt
             PROF_BEGIN(MG_K_KRYLOV);
             mr_update_h(zf, hr, hq, ctx->g, k + 1 < steps, R, ctx->st);
             PROF_END(MG_K_KRYLOV);
-            cnt.matvecs += 1;
+            cnt.fine(1, kDslashBytesF16);
         }
         return MG_OK;
     }
@@ -615,7 +640,7 @@ int smooth(mg_ctx* ctx, const v2<T>* r, v2<T>* z, const Reduce& R, Counters& cnt
     PROF_BEGIN(MG_K_DSLASH);
     dslash<T>(DS_XMY, w.vr, z, U, r, ctx->g, ctx->mass, 0.0, 0, R, ctx->st);
     PROF_END(MG_K_DSLASH);
-    cnt.matvecs += 1;
+    cnt.fine(1, dslash_site_bytes<T>());
     for (int k = 0; k < steps; ++k) {
         PROF_BEGIN(MG_K_DSLASH);
         dslash<T>(DS_MRDOT, w.vq, w.vr, U, w.vr, ctx->g, ctx->mass, ctx->prm.omega, 0, R, ctx->st);
@@ -623,7 +648,7 @@ int smooth(mg_ctx* ctx, const v2<T>* r, v2<T>* z, const Reduce& R, Counters& cnt
         PROF_BEGIN(MG_K_KRYLOV);
         mr_update<T>(z, w.vr, w.vq, n, k + 1 < steps, R, ctx->st);
         PROF_END(MG_K_KRYLOV);
-        cnt.matvecs += 1;
+        cnt.fine(1, dslash_site_bytes<T>());
     }
     return MG_OK;
 }
@@ -679,7 +704,7 @@ template <typename T> int gcr_solve(mg_ctx* ctx, mg_solve_info* info) {
             PROF_BEGIN(MG_K_DSLASH);
             dslash<T>(DS_PLAIN, w.Pk + (size_t)k * n, zk, U, zk, ctx->g, ctx->mass, 0.0, 0, ctx->R, ctx->st);
             PROF_END(MG_K_DSLASH);
-            cnt.matvecs += 1;
+            cnt.fine(1, dslash_site_bytes<T>());
             PROF_BEGIN(MG_K_KRYLOV);
             if (k > 0) {
                 gcr_multidot<T>(w.Pk, n, k, ctx->R, ctx->st);
@@ -727,7 +752,7 @@ template <typename T> int gcr_solve(mg_ctx* ctx, mg_solve_info* info) {
         dslash<double>(DS_XMY_NORM, ctx->r64, ctx->x64, ctx->U64, ctx->b64, ctx->g, ctx->mass, 0.0, S_NORM_B, ctx->R,
                        ctx->st);
         PROF_END(MG_K_TRUE_RESIDUAL);
-        cnt.matvecs += 1;
+        cnt.fine(1, kDslashBytesF64);
         CKL();
         TRY(read_scalars(ctx, S_NORM_B, 1));
         ++restarts;
@@ -750,6 +775,8 @@ template <typename T> int gcr_solve(mg_ctx* ctx, mg_solve_info* info) {
         info->restarts = restarts;
         info->true_rel_res = rel;
         info->solve_ms = ms;
+        info->setup_ms = ctx->setup_ms;
+        info->dslash_bytes = cnt.site_bytes * (double)ctx->g.V;
         info->status = status;
     }
     if (status == MG_ERR_NOT_CONVERGED) ctx->err = "max_outer reached";
@@ -1015,6 +1042,11 @@ int mg_create(const int dims[4], int t_antiperiodic, const mg_params* p, void* s
     std::string why;
     if (check_params(dims, p, why) != MG_OK) return MG_ERR_INVALID_ARG;
     mg_ctx* ctx = new mg_ctx();
+    if (cudaGetDevice(&ctx->dev) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return MG_ERR_CUDA;
+    }
     ctx->prm = *p;
     ctx->K = p->gcr_restart;
     ctx->st = (cudaStream_t)stream;
@@ -1086,17 +1118,44 @@ void mg_destroy(mg_ctx* ctx) {
     delete ctx;
 }
 
-int mg_set_links(mg_ctx* ctx, const double* U) {
-    if (!ctx || !U) return MG_ERR_INVALID_ARG;
-    CK(cudaMemcpyAsync(ctx->stage_a, U, sizeof(double2) * 36 * (size_t)ctx->g.V, cudaMemcpyHostToDevice, ctx->st));
-    links_to_internal<double>(ctx->U64, ctx->stage_a, ctx->g, ctx->st);
+namespace {
+// links (boundary layout, device memory) -> the internal FP64, FP32 and paired
+// FP32 copies, on the context stream; every level built on the old links is stale
+int load_links(mg_ctx* ctx, const double2* U_dev) {
+    links_to_internal<double>(ctx->U64, U_dev, ctx->g, ctx->st);
     convert<double, float>(ctx->U32, ctx->U64, 36 * (size_t)ctx->g.V, ctx->st);
     links_pair(ctx->U32p, ctx->U32, ctx->g, ctx->st);
     CKL();
-    CK(cudaStreamSynchronize(ctx->st));
     ctx->has_links = true;
     ctx->u16_valid = false;
     ctx->full.valid = false;   // D_c depends on the links
+    return MG_OK;
+}
+}  // namespace
+
+int mg_set_links(mg_ctx* ctx, const double* U) {
+    if (!ctx || !U) return MG_ERR_INVALID_ARG;
+    CK(cudaMemcpyAsync(ctx->stage_a, U, sizeof(double2) * 36 * (size_t)ctx->g.V, cudaMemcpyHostToDevice, ctx->st));
+    TRY(load_links(ctx, ctx->stage_a));
+    CK(cudaStreamSynchronize(ctx->st));
+    return MG_OK;
+}
+
+int mg_set_links_device(mg_ctx* ctx, const double* U_dev, void* stream) {
+    if (!ctx || !U_dev) return MG_ERR_INVALID_ARG;
+    cudaStream_t cs = (cudaStream_t)stream;
+    // the context stream waits for the caller's work that produced U_dev ...
+    if (cs != ctx->st) {
+        CK(cudaEventRecord(ctx->ev1, cs));
+        CK(cudaStreamWaitEvent(ctx->st, ctx->ev1, 0));
+    }
+    TRY(load_links(ctx, (const double2*)U_dev));
+    // ... and the caller's stream waits for the conversion, so that work the
+    // caller queues after this call may overwrite or free U_dev
+    if (cs != ctx->st) {
+        CK(cudaEventRecord(ctx->ev1, ctx->st));
+        CK(cudaStreamWaitEvent(cs, ctx->ev1, 0));
+    }
     return MG_OK;
 }
 
@@ -1128,18 +1187,34 @@ int mg_set_params(mg_ctx* ctx, const mg_params* p) {
     return MG_OK;
 }
 
+namespace {
+// the adaptive setup from the prototypes' random starts (already in ctx->protos,
+// internal layout), timed on the context stream from the event recorded in ev0
+int run_setup(mg_ctx* ctx) {
+    ctx->coarse16 = ctx->prm.prec_inner == MG_FP16;
+    int st = ctx->prm.prec_inner != MG_FP64 ? setup_impl<float>(ctx) : setup_impl<double>(ctx);
+    if (st != MG_OK) return st;
+    CK(cudaEventRecord(ctx->ev1, ctx->st));
+    CK(cudaEventSynchronize(ctx->ev1));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+    ctx->setup_ms = ms;
+    return MG_OK;
+}
+}  // namespace
+
 int mg_setup(mg_ctx* ctx, const double* V0) {
     TRY(need_links(ctx));
     if (!V0) return fail(ctx, MG_ERR_INVALID_ARG, "V0 is NULL");
     TRY(ensure_protos(ctx));
     int nv = ctx->prm.nvec;
     size_t n = nfine(ctx);
+    CK(cudaEventRecord(ctx->ev0, ctx->st));
     CK(cudaMemcpyAsync(ctx->protos_stage, V0, sizeof(double2) * n * nv, cudaMemcpyHostToDevice, ctx->st));
     for (int i = 0; i < nv; ++i)
         spinor_to_internal<double>(ctx->protos + (size_t)i * n, ctx->protos_stage + (size_t)i * n, ctx->g, ctx->st);
     CKL();
-    ctx->coarse16 = ctx->prm.prec_inner == MG_FP16;
-    return ctx->prm.prec_inner != MG_FP64 ? setup_impl<float>(ctx) : setup_impl<double>(ctx);
+    return run_setup(ctx);
 }
 
 int mg_setup_device(mg_ctx* ctx, const double* V0_dev) {
@@ -1147,11 +1222,11 @@ int mg_setup_device(mg_ctx* ctx, const double* V0_dev) {
     if (!V0_dev) return fail(ctx, MG_ERR_INVALID_ARG, "V0 is NULL");
     TRY(ensure_protos(ctx));
     size_t n = nfine(ctx);
+    CK(cudaEventRecord(ctx->ev0, ctx->st));
     for (int i = 0; i < ctx->prm.nvec; ++i)
         spinor_to_internal<double>(ctx->protos + (size_t)i * n, (const double2*)V0_dev + (size_t)i * n, ctx->g, ctx->st);
     CKL();
-    ctx->coarse16 = ctx->prm.prec_inner == MG_FP16;
-    return ctx->prm.prec_inner != MG_FP64 ? setup_impl<float>(ctx) : setup_impl<double>(ctx);
+    return run_setup(ctx);
 }
 
 int mg_set_null_vectors(mg_ctx* ctx, const double* V, int nv) {
@@ -1398,6 +1473,29 @@ int mg_profile_read(mg_ctx* ctx, double* ms, int* launches, double* coarse_iters
 }
 
 long long mg_kernel_launches(void) { return launch_counter().load(std::memory_order_relaxed); }
+
+int mg_check_wait_timeout(mg_ctx* ctx, int kind, long long spin_limit) {
+    if (!ctx) return MG_ERR_INVALID_ARG;
+    if (kind < 0 || kind > 3 || spin_limit < 1 || spin_limit > 10000000LL)
+        return fail(ctx, MG_ERR_INVALID_ARG, "kind must be 0..3 and spin_limit in 1..1e7");
+    const int G = 4;
+    const size_t words = (size_t)2 * 3 * (G + 1) * 16;   // two parities x three values x (G + 1) padded slots
+    unsigned long long* w = nullptr;
+    unsigned int* ctr = nullptr;
+    TRY(dalloc(ctx, &w, sizeof(unsigned long long) * words));
+    TRY(dalloc(ctx, &ctr, sizeof(unsigned int) * 4));   // [0] count, [1] generation, [2] error flag
+    int st = MG_OK;
+    CK(cudaMemsetAsync(w, 0, sizeof(unsigned long long) * words, ctx->st));
+    CK(cudaMemsetAsync(ctr, 0, sizeof(unsigned int) * 4, ctx->st));
+    CK(wait_probe(kind, G, w, ctr, (int*)(ctr + 2), spin_limit, ctx->st));
+    unsigned int flag = 0;
+    CK(cudaMemcpyAsync(&flag, ctr + 2, sizeof(flag), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    dfree(ctx, w);
+    dfree(ctx, ctr);
+    if (flag) st = fail(ctx, MG_ERR_TIMEOUT, "bounded wait gave up as expected (kind " + std::to_string(kind) + ")");
+    return st;
+}
 int mg_coarse_kernel(mg_ctx* ctx) { return ctx ? ctx->coarse_kernel_used : MG_CK_NONE; }
 
 const char* mg_status_string(int status) {
@@ -1438,6 +1536,10 @@ unsigned char* g_noalloc_addr[kMaxDevices] = {};
 int noalloc_scratch(mg_ctx* ctx, unsigned char** out) {
     int dev = 0;
     CK(cudaGetDevice(&dev));
+    if (dev != ctx->dev)
+        return fail(ctx, MG_ERR_INVALID_ARG,
+                    "the current device (" + std::to_string(dev) + ") is not the context's device (" +
+                        std::to_string(ctx->dev) + "): make the context's device current before this call");
     if (dev < 0 || dev >= kMaxDevices) return fail(ctx, MG_ERR_INVALID_ARG, "device ordinal out of range");
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
     if (!g_noalloc_addr[dev]) {
@@ -1643,6 +1745,7 @@ int solve_batched_impl(mg_ctx* ctx, int nrhs, mg_solve_info* infos) {
     std::vector<double> bnorm(nrhs), rnorm(nrhs), rcycle(nrhs), rel(nrhs, 1.0), coarse(nrhs, 0.0);
     std::vector<int> iters(nrhs, 0), restarts(nrhs, 0), status(nrhs, MG_ERR_NOT_CONVERGED), kk(nrhs, 0),
         active(nrhs, 1), cycle_end(nrhs, 0), mv(nrhs, 0);
+    std::vector<double> mvb(nrhs, 0.0);   // bytes per site of the fine operator applications
     auto RR = [&](int r) {
         Reduce R = ctx->R;
         R.scal = b.scal + (size_t)r * S_COUNT;
@@ -1689,11 +1792,14 @@ int solve_batched_impl(mg_ctx* ctx, int nrhs, mg_solve_info* infos) {
                 {
                     Counters scnt;
                     TRY(smooth<float>(ctx, b.r32 + r * n, zk, Rr, scnt));
+                    mv[r] += scnt.matvecs;
+                    mvb[r] += scnt.site_bytes;
                 }
                 PROF_BEGIN(MG_K_DSLASH);
                 dslash<float>(DS_PLAIN, Pr + (size_t)kk[r] * n, zk, U, zk, ctx->g, ctx->mass, 0.0, 0, Rr, ctx->st);
                 PROF_END(MG_K_DSLASH);
-                mv[r] += 2 + p.smoother_steps;
+                mv[r] += 1;
+                mvb[r] += kDslashBytesF32;
                 PROF_BEGIN(MG_K_KRYLOV);
                 if (kk[r] > 0) {
                     gcr_multidot<float>(Pr, n, kk[r], Rr, ctx->st);
@@ -1754,6 +1860,7 @@ int solve_batched_impl(mg_ctx* ctx, int nrhs, mg_solve_info* infos) {
             PROF_END(MG_K_TRUE_RESIDUAL);
             convert<double, float>(b.r32 + r * n, ctx->r64, n, ctx->st);
             mv[r] += 1;
+            mvb[r] += kDslashBytesF64;
             CKL();
         }
         CK(cudaMemcpyAsync(b.h_scal, b.scal, sizeof(double) * S_COUNT * nrhs, cudaMemcpyDeviceToHost, ctx->st));
@@ -1784,6 +1891,8 @@ int solve_batched_impl(mg_ctx* ctx, int nrhs, mg_solve_info* infos) {
             infos[r].restarts = restarts[r];
             infos[r].true_rel_res = rel[r];
             infos[r].solve_ms = ms;
+            infos[r].setup_ms = ctx->setup_ms;
+            infos[r].dslash_bytes = mvb[r] * (double)ctx->g.V;
             infos[r].status = status[r];
         }
         if (status[r] == MG_ERR_NUMERIC) worst = MG_ERR_NUMERIC;

@@ -224,6 +224,9 @@ bool cgls_shape(int nc, int Vc, bool h16, int mode, CglsShape* out);
 // Not for graph capture: every launch takes a fresh epoch range from the host.
 void coarse_pack_units(void* Au, float* su, const double2* A, int nc, int ru, int Vc, bool h16, cudaStream_t st);
 cudaError_t cgls_onchip(const CglsArgs& args, cudaStream_t st);
+// one bounded device wait driven into a configuration that cannot complete
+cudaError_t wait_probe(int kind, int G, unsigned long long* words, unsigned int* ctr, int* err, long long limit,
+                       cudaStream_t st);
 // FP16 coarse operator with a per-(X, d) block scale, for the FP16-storage mode
 void coarse_pack16(__half2* A16, float* s16, const double2* A, int nc, int Vc, cudaStream_t st);
 

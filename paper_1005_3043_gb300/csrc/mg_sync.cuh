@@ -14,7 +14,8 @@ namespace wmg {
 
 constexpr long long kBarrierSpinLimit = 40000000LL;   // a few seconds of polls
 
-__device__ __forceinline__ bool grid_sync(unsigned int* count, unsigned int* gen, unsigned int G, int* err) {
+__device__ __forceinline__ bool grid_sync(unsigned int* count, unsigned int* gen, unsigned int G, int* err,
+                                          long long limit = kBarrierSpinLimit) {
     __shared__ int s_fail;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -31,7 +32,7 @@ __device__ __forceinline__ bool grid_sync(unsigned int* count, unsigned int* gen
             long long spins = 0;
             while (*vgen == my) {
                 if (*verr) { s_fail = 1; break; }
-                if (++spins > kBarrierSpinLimit) { atomicExch(err, 1); s_fail = 1; break; }
+                if (++spins > limit) { atomicExch(err, 1); s_fail = 1; break; }
                 if (spins > 256) __nanosleep(32);
             }
         }
@@ -102,7 +103,8 @@ __device__ __forceinline__ unsigned long long xch_load(const unsigned long long*
     return w;
 }
 // bounded wait until *slot carries epoch e; false on timeout or a raised error flag
-__device__ __forceinline__ bool xch_wait(const unsigned long long* slot, unsigned int e, int* err, float& v) {
+__device__ __forceinline__ bool xch_wait(const unsigned long long* slot, unsigned int e, int* err, float& v,
+                                         long long limit = kExchangeSpinLimit) {
     long long spins = 0;
     for (;;) {
         const unsigned long long w = xch_load(slot);
@@ -111,7 +113,7 @@ __device__ __forceinline__ bool xch_wait(const unsigned long long* slot, unsigne
             return true;
         }
         if (*(volatile int*)err) return false;
-        if (++spins > kExchangeSpinLimit) {
+        if (++spins > limit) {
             atomicExch(err, 1);
             return false;
         }
@@ -132,10 +134,12 @@ constexpr int kXchMaxNV = 3;
 // polled values -> one warp per value sums them in CTA order.
 // FENCE false: no fence before the publish (the caller's cross-CTA data is
 // epoch-tagged, so only the partial sums themselves must arrive).
+// Gx: the number of CTAs that publish (0: gridDim.x); limit: polls per slot.
 template <int NV, bool FENCE = true>
-__device__ bool xch_allreduce(float (&v)[NV], unsigned long long* slots, unsigned int e, int* err, float* sc) {
+__device__ bool xch_allreduce(float (&v)[NV], unsigned long long* slots, unsigned int e, int* err, float* sc, int Gx = 0,
+                              long long limit = kExchangeSpinLimit) {
     static_assert(NV >= 1 && NV <= kXchMaxNV, "one to three values per exchange");
-    const int G = gridDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
+    const int G = Gx > 0 ? Gx : (int)gridDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
     unsigned long long* base = slots + (size_t)(e & 1) * kXchMaxNV * G * kXchPad;
     float* wsum = sc;                  // [NV][32] warp partials
     float* gv = sc + NV * 32;          // [NV * G] polled CTA sums
@@ -166,7 +170,7 @@ __device__ bool xch_allreduce(float (&v)[NV], unsigned long long* slots, unsigne
     bool ok = true;
     for (int i = t; i < NV * G && ok; i += blockDim.x) {
         float got = 0.f;
-        ok = xch_wait(base + (size_t)i * kXchPad, e, err, got);
+        ok = xch_wait(base + (size_t)i * kXchPad, e, err, got, limit);
         gv[i] = got;
     }
     if (__syncthreads_or(!ok)) return false;
@@ -200,11 +204,12 @@ __device__ __forceinline__ bool tag_load(const unsigned long long* w, unsigned i
     return (unsigned int)(a >> 32) == e && (unsigned int)(b >> 32) == e;
 }
 // bounded wait for epoch e at w; false on timeout or a raised error flag
-__device__ __forceinline__ bool tag_wait(const unsigned long long* w, unsigned int e, int* err, float2& v) {
+__device__ __forceinline__ bool tag_wait(const unsigned long long* w, unsigned int e, int* err, float2& v,
+                                         long long limit = kExchangeSpinLimit) {
     long long spins = 0;
     while (!tag_load(w, e, v)) {
         if (*(volatile int*)err) return false;
-        if (++spins > kExchangeSpinLimit) {
+        if (++spins > limit) {
             atomicExch(err, 1);
             return false;
         }

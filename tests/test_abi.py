@@ -55,11 +55,12 @@ def test_host_only_calls(lib):
     assert wmg.status_string(wmg.MG_ERR_NUMERIC) == "MG_ERR_NUMERIC"
 
 
-def test_params_struct_matches_header():
-    """The binding's MgParams has the header's mg_params fields, in order and
-    with the same C types (int / double / int[4])."""
+@pytest.mark.parametrize("cname,pytype", [("mg_params", wmg.MgParams), ("mg_solve_info", wmg.MgSolveInfo)])
+def test_struct_matches_header(cname, pytype):
+    """The binding's structs have the header's fields, in order and with the
+    same C types (int / double / int[4])."""
     src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "wilson_mg.h")).read(), flags=re.S)
-    body = re.search(r"typedef\s+struct\s*\{(.*?)\}\s*mg_params\s*;", src, flags=re.S).group(1)
+    body = re.search(r"typedef\s+struct\s*\{([^{}]*)\}\s*" + cname + r"\s*;", src).group(1)
     fields = []
     for decl in body.split(";"):
         m = re.match(r"\s*(int|double)\s+(\w+)\s*(\[\s*(\d+)\s*\])?\s*$", decl)
@@ -67,7 +68,7 @@ def test_params_struct_matches_header():
             fields.append((m.group(2), m.group(1), int(m.group(4)) if m.group(4) else None))
     assert fields, "no fields parsed"
     ct = {"int": ctypes.c_int, "double": ctypes.c_double}
-    got = [(n, t) for n, t in wmg.MgParams._fields_]
+    got = [(n, t) for n, t in pytype._fields_]
     assert [f[0] for f in fields] == [n for n, _ in got]
     for (name, ctype, arr), (_, t) in zip(fields, got):
         want = ct[ctype] * arr if arr else ct[ctype]
