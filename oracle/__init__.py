@@ -26,6 +26,11 @@ Parity status per function (what pins it; see the tests):
                     convergence factor (refined < relaxed only < random
                     prototypes) and by its truncated level (the refined group
                     is outside range(P_t), every other prototype inside)
+  eo_schur / eo_cg  red-black preconditioned CG (the comparison of Sec. IV):
+                    D applied to (x_e, H_oe x_e / (4+m)) is (Dhat x_e, 0);
+                    gamma5-hermiticity of Dhat; CG iterates equal the
+                    least-squares solution over the Krylov space (numpy
+                    lstsq); dense solve on a small lattice; true residual
   two_grid_factor   eq. 3 with an exact coarse solve: a start in range(P)
                     is annihilated, the unsmoothed E_TG is a projection, the
                     corrected residual is Galerkin-orthogonal to range(P)
@@ -107,6 +112,9 @@ def _load():
             lib.or_setup.restype = I
             lib.or_setup_truncated_level.argtypes = [P, P, P, I, I, P, P, P]
             lib.or_setup_truncated_level.restype = I
+            lib.or_eo_schur.argtypes = [P, I, P, D, I, P, P]
+            lib.or_eo_cg.argtypes = [P, I, P, D, P, P, D, I, P, P, P]
+            lib.or_eo_cg.restype = I
             _lib = lib
     return _lib
 
@@ -335,3 +343,30 @@ def two_grid_factor(params: Params, U, P, A, e0, k: int):
                 e, _ = mr(U, e, r, m, L, params.mr_steps, params.omega, tap)
         norms.append(float(np.linalg.norm(e)))
     return (norms[-1] / norms[0]) ** (1.0 / k), norms
+
+
+def parity_mask(L) -> np.ndarray:
+    """(V,) bool, True on the even sites ((x + y + z + t) mod 2 = 0)."""
+    c = np.indices(tuple(L)[::-1]).reshape(4, -1)[::-1]    # c[mu] per lexicographic site
+    return (c.sum(0) % 2) == 0
+
+
+def eo_schur(U, xe, m: float, L, dag: bool = False, tap: int = 1) -> np.ndarray:
+    """Dhat xe = (4+m) xe - H_eo H_oe xe / (4+m) on the even sites (dag:
+    gamma5 Dhat gamma5), the Schur complement of the red-black preconditioned
+    CG that Sec. IV compares against; xe read on the even sites."""
+    xe = _c(xe)
+    out = np.empty_like(xe)
+    _load().or_eo_schur(_p(_i4(L)), int(tap), _p(_c(U)), float(m), int(bool(dag)), _p(xe), _p(out))
+    return out
+
+
+def eo_cg(U, b, m: float, L, tol: float, maxit: int, tap: int = 1):
+    """Red-black preconditioned CG (CGLS on the even-site Schur complement) for
+    D x = b: returns (x, iterations, matvecs, true relative residual, status)."""
+    b = _c(b)
+    x = np.empty_like(b)
+    it, mv, rel = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0)
+    st = _load().or_eo_cg(_p(_i4(L)), int(tap), _p(_c(U)), float(m), _p(b), _p(x), float(tol), int(maxit),
+                          ctypes.byref(it), ctypes.byref(mv), ctypes.byref(rel))
+    return x, it.value, mv.value, rel.value, st

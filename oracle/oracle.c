@@ -861,3 +861,138 @@ OR_API int or_setup(const or_params* p, const double* Ur, double* Vr, int init_r
     free(r); free(z);
     return st;
 }
+
+/* ------------------------------------------------------------------ */
+/* Red-black (even-odd) preconditioned CG on the normal equations: the  */
+/* comparison solver of Sec. IV (Fig. 1 counts its Wilson matrix-vector */
+/* products, Fig. 2 its flops against MG-GCR).  The paper names it and  */
+/* uses it; the construction below is the standard one it refers to.    */
+/*                                                                     */
+/* With H the hopping part of eq. 2 (D = (4+m) I - H) and sites split   */
+/* by parity (x+y+z+t) mod 2, H couples only opposite parities on a     */
+/* lattice of even extents.  Eliminating the odd sites leaves the Schur */
+/* complement on the even sites                                          */
+/*     Dhat = (4+m) I - H_eo H_oe / (4+m),                               */
+/*     Dhat x_e = bhat,  bhat = b_e + H_eo b_o / (4+m),                  */
+/*     x_o = (b_o + H_oe x_e) / (4+m),                                   */
+/* and b - D x vanishes on the odd sites and equals bhat - Dhat x_e on   */
+/* the even ones.  Dhat^dag = gamma5 Dhat gamma5 (gamma5-hermiticity of  */
+/* D carries over, H_eo^dag = gamma5 H_oe gamma5).                       */
+/* ------------------------------------------------------------------ */
+static int site_parity(const int* L, int64_t s) {
+    int c[4];
+    coords(L, s, c);
+    return (c[0] + c[1] + c[2] + c[3]) & 1;
+}
+
+/* out = H in on the sites of parity p (zero on the others), in read on the
+ * sites of parity 1 - p.  H in = -D(m = -4) in (eq. 2 with 4 + m = 0). */
+static void hop_to_parity(const int* L, int tap, const double* U, int p, const cplx* in, cplx* out, cplx* tmp) {
+    int64_t V = vol(L);
+    for (int64_t s = 0; s < V; ++s)
+        for (int k = 0; k < 12; ++k) tmp[12 * s + k] = site_parity(L, s) == 1 - p ? in[12 * s + k] : 0;
+    or_dslash(L, tap, U, -4.0, (const double*)tmp, (double*)out);
+    for (int64_t s = 0; s < V; ++s)
+        for (int k = 0; k < 12; ++k) out[12 * s + k] = site_parity(L, s) == p ? -out[12 * s + k] : 0;
+}
+
+/* out = Dhat xe (even sites; xe read on the even sites), dag: gamma5 Dhat gamma5 */
+static void schur_apply(const int* L, int tap, const double* U, double m, int dag, const cplx* xe, cplx* out,
+                        cplx* t1, cplx* t2, cplx* t3) {
+    int64_t V = vol(L);
+    const double a = 4.0 + m;
+    const cplx* x = xe;
+    if (dag) {
+        or_gamma5(V, (const double*)xe, (double*)t3);
+        x = t3;
+    }
+    hop_to_parity(L, tap, U, 1, x, t1, t2);       /* t1 = H_oe x (odd sites) */
+    hop_to_parity(L, tap, U, 0, t1, out, t2);     /* out = H_eo H_oe x (even sites) */
+    for (int64_t s = 0; s < V; ++s)
+        for (int k = 0; k < 12; ++k)
+            out[12 * s + k] = site_parity(L, s) == 0 ? a * x[12 * s + k] - out[12 * s + k] / a : 0;
+    if (dag) or_gamma5(V, (const double*)out, (double*)out);
+}
+
+OR_API void or_eo_schur(const int* L, int tap, const double* U, double m, int dag, const double* xe, double* out) {
+    int64_t n = vol(L) * 12;
+    cplx* t = (cplx*)malloc(sizeof(cplx) * 3 * n);
+    schur_apply(L, tap, U, m, dag, (const cplx*)xe, (cplx*)out, t, t + n, t + 2 * n);
+    free(t);
+}
+
+/*
+ * Solve D x = b: CGLS on Dhat from x_e = 0 (r = bhat, s = Dhat^dag r, p = s;
+ * per iteration q = Dhat p, alpha = |s|^2 / |q|^2, x_e += alpha p,
+ * r -= alpha q, stop when |r| <= tol |b|, else s = Dhat^dag r,
+ * beta = |s_new|^2 / |s|^2, p = s + beta p), then x_o from x_e and the true
+ * residual |b - D x| / |b| with the full operator.  If the recursive residual
+ * has drifted above the true one's target, the solve restarts on the true
+ * residual (the correction is added to x).  iters counts CG iterations;
+ * matvecs counts applications of Dhat or Dhat^dag (each two half-lattice
+ * hops: one full-lattice hopping term) plus the full-lattice products of the
+ * source preparation, the odd-site reconstruction and the residual checks.
+ */
+OR_API int or_eo_cg(const int* L, int tap, const double* Ur, double m, const double* br, double* xr, double tol,
+                    int maxit, int* iters_out, int* matvecs_out, double* rel_out) {
+    int64_t V = vol(L), n = V * 12;
+    for (int mu = 0; mu < 4; ++mu)
+        if (L[mu] % 2) return OR_ERR_ARG;
+    const double a = 4.0 + m;
+    const cplx* b = (const cplx*)br;
+    cplx* x = (cplx*)xr;
+    cplx* w = (cplx*)malloc(sizeof(cplx) * n * 10);
+    cplx *bh = w, *xe = w + n, *r = w + 2 * n, *s = w + 3 * n, *p = w + 4 * n, *q = w + 5 * n, *res = w + 6 * n;
+    cplx *t1 = w + 7 * n, *t2 = w + 8 * n, *t3 = w + 9 * n;
+    double bnorm = sqrt(vnorm2(n, b));
+    int it = 0, mv = 0, st = OR_ERR_NOT_CONVERGED;
+    double rel = bnorm > 0 ? 1.0 : 0.0;
+    memset(x, 0, sizeof(cplx) * n);
+    memcpy(res, b, sizeof(cplx) * n);                 /* residual of the current x */
+    if (bnorm == 0) st = OR_OK;
+    while (st == OR_ERR_NOT_CONVERGED && it < maxit) {
+        /* bhat from the current residual (x = 0 at the start) */
+        hop_to_parity(L, tap, Ur, 0, res, t1, t2);    /* t1 = H_eo res_o */
+        for (int64_t i = 0; i < n; ++i) bh[i] = site_parity(L, i / 12) == 0 ? res[i] + t1[i] / a : 0;
+        mv += 1;
+        memset(xe, 0, sizeof(cplx) * n);
+        memcpy(r, bh, sizeof(cplx) * n);
+        schur_apply(L, tap, Ur, m, 1, r, s, t1, t2, t3);
+        mv += 1;
+        memcpy(p, s, sizeof(cplx) * n);
+        double gamma = vnorm2(n, s);
+        while (it < maxit && gamma > 0) {
+            schur_apply(L, tap, Ur, m, 0, p, q, t1, t2, t3);
+            mv += 1;
+            double qq = vnorm2(n, q);
+            if (!(qq > 0)) break;
+            double alpha = gamma / qq;
+            vaxpy(n, alpha, p, xe);
+            vaxpy(n, -alpha, q, r);
+            ++it;
+            if (sqrt(vnorm2(n, r)) <= tol * bnorm) break;
+            schur_apply(L, tap, Ur, m, 1, r, s, t1, t2, t3);
+            mv += 1;
+            double gnew = vnorm2(n, s);
+            double beta = gnew / gamma;
+            gamma = gnew;
+            for (int64_t i = 0; i < n; ++i) p[i] = s[i] + beta * p[i];
+        }
+        /* x_o = (res_o + H_oe x_e) / (4 + m); x += (x_e, x_o) */
+        hop_to_parity(L, tap, Ur, 1, xe, t1, t2);
+        mv += 1;
+        for (int64_t i = 0; i < n; ++i)
+            x[i] += site_parity(L, i / 12) == 0 ? xe[i] : (res[i] + t1[i]) / a;
+        or_dslash(L, tap, Ur, m, (const double*)x, (double*)t1);
+        mv += 1;
+        for (int64_t i = 0; i < n; ++i) res[i] = b[i] - t1[i];
+        rel = sqrt(vnorm2(n, res)) / bnorm;
+        if (!isfinite(rel)) { st = OR_ERR_NUMERIC; break; }
+        if (rel <= tol) st = OR_OK;
+    }
+    free(w);
+    if (iters_out) *iters_out = it;
+    if (matvecs_out) *matvecs_out = mv;
+    if (rel_out) *rel_out = rel;
+    return st;
+}

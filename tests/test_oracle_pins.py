@@ -628,3 +628,98 @@ def test_vcycle_smoothing_half(smoother, k):
     assert np.abs(got - want).max() < 1e-9 * np.abs(want).max()
     wrong = r - oracle.dslash(U, e0, m, L) - (r - expected(r))   # smoothing r, not r'
     assert np.abs(got - wrong).max() > 1e-3 * np.abs(want).max()
+
+
+# ---------------------------------------------------------------- red-black preconditioned CG (Sec. IV comparison)
+def _even_part(L, psi):
+    return psi * oracle.parity_mask(L)[:, None, None]
+
+
+def test_eo_schur_complement_eliminates_odd_sites():
+    """D applied to (x_e, x_o) with x_o = H_oe x_e / (4+m) is (Dhat x_e, 0):
+    checked with the full operator of eq. 2 (H = (4+m) - D, so H_oe x_e is the
+    odd part of (4+m) x_e - D x_e)."""
+    L = (4, 4, 2, 6)
+    U = rough_gauge(L, seed=17)
+    m = -0.3
+    xe = _even_part(L, synth.gaussian_spinor(L, 5))
+    odd = ~oracle.parity_mask(L)
+    Hx = (4 + m) * xe - oracle.dslash(U, xe, m, L)            # H x_e (its odd part)
+    x = xe + (Hx * odd[:, None, None]) / (4 + m)
+    Dx = oracle.dslash(U, x, m, L)
+    assert np.abs(Dx[odd]).max() < 1e-13 * np.abs(Dx).max()
+    Dh = oracle.eo_schur(U, xe, m, L)
+    assert np.abs(Dh[odd]).max() == 0
+    assert rel(Dh, _even_part(L, Dx)) < 1e-13
+
+
+def test_eo_schur_gamma5_hermitian():
+    L = (4, 2, 4, 4)
+    U = rough_gauge(L, seed=18)
+    m = -0.1
+    u = _even_part(L, synth.gaussian_spinor(L, 6))
+    v = _even_part(L, synth.gaussian_spinor(L, 7))
+    lhs = np.vdot(u, oracle.eo_schur(U, v, m, L))
+    rhs = np.vdot(oracle.eo_schur(U, u, m, L, dag=True), v)
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+    # dag is gamma5 Dhat gamma5
+    assert rel(oracle.eo_schur(U, u, m, L, dag=True), oracle.gamma5(oracle.eo_schur(U, oracle.gamma5(u), m, L))) < 1e-14
+
+
+@pytest.mark.parametrize("k", [1, 2, 4])
+def test_eo_cg_iterates_are_krylov_least_squares(k):
+    """CG on the normal equations minimises |bhat - Dhat x| over the Krylov space
+    K_k(Dhat^dag Dhat, Dhat^dag bhat): after k iterations the true residual
+    equals the least-squares one (numpy lstsq over the explicit power basis)."""
+    L = (4, 4, 2, 4)
+    U = rough_gauge(L, seed=19)
+    m = -0.2
+    b = synth.gaussian_spinor(L, 8)
+    x, it, mv, relres, st = oracle.eo_cg(U, b, m, L, 0.0, k)
+    assert it == k
+    odd = ~oracle.parity_mask(L)
+    bh = _even_part(L, b) + _even_part(L, (4 + m) * np.where(odd[:, None, None], b, 0)
+                                       - oracle.dslash(U, np.where(odd[:, None, None], b, 0), m, L)) / (4 + m)
+    ev = oracle.parity_mask(L)
+    K = [oracle.eo_schur(U, bh, m, L, dag=True)]
+    for _ in range(k - 1):
+        K.append(oracle.eo_schur(U, oracle.eo_schur(U, K[-1], m, L), m, L, dag=True))
+    DK = np.stack([oracle.eo_schur(U, v, m, L)[ev].ravel() for v in K], 1)
+    c, *_ = np.linalg.lstsq(DK, bh[ev].ravel(), rcond=None)
+    want = np.linalg.norm(bh[ev].ravel() - DK @ c)
+    got = np.linalg.norm(b - oracle.dslash(U, x, m, L))    # = |bhat - Dhat x_e| (odd part vanishes)
+    assert abs(got - want) < 1e-9 * want, (got, want)
+
+
+def test_eo_cg_solves_against_dense():
+    """To 1e-12 on a 2^3 x 4 lattice: the solution of the dense system (numpy
+    solve of D built column by column from eq. 2), in at most 2 x 192 iterations."""
+    L = (2, 2, 2, 4)
+    U = rough_gauge(L, seed=20)
+    m = -0.25
+    V = oracle.volume(L)
+    b = synth.gaussian_spinor(L, 9)
+    D = dense_from_apply(lambda e: oracle.dslash(U, e.reshape(V, 4, 3), m, L).ravel(), V * 12)
+    x_ref = np.linalg.solve(D, b.ravel()).reshape(b.shape)
+    x, it, mv, relres, st = oracle.eo_cg(U, b, m, L, 1e-12, 2000)
+    assert st == 0 and relres <= 1e-12 and it <= 2 * V * 6
+    assert rel(x, x_ref) < 1e-9
+    # one pass: Dhat and Dhat^dag per iteration (no Dhat^dag after the last),
+    # plus bhat, the first Dhat^dag r, the odd-site reconstruction and the check
+    assert mv == 2 * it + 3, (mv, it)
+
+
+def test_eo_cg_iterations_grow_toward_critical_mass():
+    """Critical slowing down of CG (the motivation of Sec. I and Fig. 1): on the
+    8^4 beta = 6.0 field the iteration count to 1e-10 rises as Re(lambda_min)
+    falls from 0.1 to 0.01, and every solve reaches the tolerance."""
+    from tests._fields import c1_workload, C1_RE_LAMBDA_MIN_M0
+    L, B, nv, U, m = c1_workload()
+    b = synth.gaussian_spinor(L, 7)
+    its = []
+    for target in (0.1, 0.03, 0.01):
+        x, it, mv, relres, st = oracle.eo_cg(U, b, target - C1_RE_LAMBDA_MIN_M0, L, 1e-10, 20000)
+        assert st == 0 and relres <= 1e-10
+        assert np.linalg.norm(b - oracle.dslash(U, x, target - C1_RE_LAMBDA_MIN_M0, L)) <= 1e-10 * np.linalg.norm(b)
+        its.append(it)
+    assert its[0] < its[1] < its[2], its
