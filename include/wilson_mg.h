@@ -214,6 +214,30 @@ int mg_solve_batched(mg_ctx* ctx, const double* b, double* x, int nrhs, mg_solve
  * consecutive fine spinors, owned by the caller). */
 int mg_solve_batched_device(mg_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, mg_solve_info* info);
 
+/* Red-black (even-odd) preconditioned CG, the solver Sec. IV compares MG-GCR
+ * against (Fig. 1: Wilson matrix-vector products, Fig. 2: flops): CG on the
+ * normal equations of the even-site Schur complement
+ * Dhat = (4+m) - H_eo H_oe / (4+m) of eq. 2 (D = (4+m) - H), the odd sites
+ * reconstructed as x_o = (b_o + H_oe x_e) / (4+m).  prec MG_FP32: the CG
+ * iterates in FP32; each time its own residual has fallen by 1e-4 the
+ * solution is accumulated in FP64, the residual recomputed in FP64 and the
+ * CG continued from it with its search direction kept (reliable update);
+ * MG_FP64: FP64 throughout.  Stops when ||b - D x|| <= tol ||b|| in
+ * FP64 or after maxit CG iterations (MG_ERR_NOT_CONVERGED, x the last
+ * iterate).  Needs even lattice extents.  Uses the context's links and mass,
+ * no setup.  info: outer_iters = CG iterations, restarts = defect-correction
+ * cycles, coarse_iters = 0, fine_matvecs = matrix products: one per Dhat or
+ * Dhat^dag (two half-lattice hops each) and, per cycle, one each for the
+ * right-hand side Dhat x_e = b_e + H_eo b_o / (4+m), the odd-site
+ * reconstruction and the FP64 residual; dslash_bytes counts every half-lattice
+ * hop (all 4V links, input and output half vectors).  b, x: host spinors. */
+int mg_solve_eo_cg(mg_ctx* ctx, const double* b, double* x, double tol, int maxit, int prec, mg_solve_info* info);
+
+/* As mg_solve_eo_cg with b and x in device memory (boundary layout, FP64,
+ * owned by the caller); synchronises the context stream. */
+int mg_solve_eo_cg_device(mg_ctx* ctx, const double* b_dev, double* x_dev, double tol, int maxit, int prec,
+                          mg_solve_info* info);
+
 /* Coarse stencil (Sec. III) on nrhs coarse vectors at once: y_n = D_c x_n
  * (dagger: D_c^dag).  x, y: nrhs consecutive host coarse vectors, nrhs <= 256.
  * impl 0: tensor cores (operator rounded to FP16 without scale, each source

@@ -83,6 +83,8 @@ _SIGS = {
     "mg_solve_batched": ([_P, _P, _P, _I, _P], _I),
     "mg_solve_batched_device": ([_P, _P, _P, _I, _P], _I),
     "mg_apply_coarse_batched": ([_P, _P, _P, _I, _I, _I], _I),
+    "mg_solve_eo_cg": ([_P, _P, _P, _D, _I, _I, _P], _I),
+    "mg_solve_eo_cg_device": ([_P, _P, _P, _D, _I, _I, _P], _I),
     "mg_apply_dslash": ([_P, _P, _P, _I], _I),
     "mg_restrict": ([_P, _P, _P, _I], _I),
     "mg_prolong": ([_P, _P, _P, _I], _I),
@@ -261,6 +263,23 @@ def mg_solve_batched_device(ctx, b_dev, x_dev, nrhs: int):
     _check(load().mg_solve_batched_device(ctx, _dev_ptr(b_dev), _dev_ptr(x_dev), int(nrhs), infos), ctx,
            allow=(MG_ERR_NOT_CONVERGED,))
     return [i.as_dict() for i in infos]
+
+
+def mg_solve_eo_cg(ctx, b, tol: float = 1e-10, maxit: int = 100000, prec: int = MG_FP32):
+    """Red-black preconditioned CG (host buffers): returns (x, info dict)."""
+    b = _host(b)
+    x = np.empty_like(b)
+    info = MgSolveInfo()
+    _check(load().mg_solve_eo_cg(ctx, _ptr(b), _ptr(x), float(tol), int(maxit), int(prec), ctypes.byref(info)), ctx,
+           allow=(MG_ERR_NOT_CONVERGED,))
+    return x, info.as_dict()
+
+
+def mg_solve_eo_cg_device(ctx, b_dev, x_dev, tol: float = 1e-10, maxit: int = 100000, prec: int = MG_FP32) -> dict:
+    info = MgSolveInfo()
+    _check(load().mg_solve_eo_cg_device(ctx, _dev_ptr(b_dev), _dev_ptr(x_dev), float(tol), int(maxit), int(prec),
+                                        ctypes.byref(info)), ctx, allow=(MG_ERR_NOT_CONVERGED,))
+    return info.as_dict()
 
 
 def mg_apply_coarse_batched(ctx, x, dagger: bool = False, impl: int = 0) -> np.ndarray:
@@ -456,6 +475,12 @@ class WilsonMG:
 
     def solve_batched_device(self, b_dev, x_dev, nrhs):
         return mg_solve_batched_device(self.ctx, b_dev, x_dev, nrhs)
+
+    def solve_eo_cg(self, b, tol=1e-10, maxit=100000, prec=MG_FP32):
+        return mg_solve_eo_cg(self.ctx, b, tol, maxit, prec)
+
+    def solve_eo_cg_device(self, b_dev, x_dev, tol=1e-10, maxit=100000, prec=MG_FP32):
+        return mg_solve_eo_cg_device(self.ctx, b_dev, x_dev, tol, maxit, prec)
 
     def coarse_batched(self, x, dagger=False, impl=0):
         return mg_apply_coarse_batched(self.ctx, x, dagger, impl)

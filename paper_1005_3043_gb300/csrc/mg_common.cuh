@@ -138,6 +138,7 @@ enum ScalarSlot {
     S_GCR_PN2 = 20,      // ||p_k||^2 after orthogonalisation
     S_GCR_R2 = 21,       // ||r||^2 after the update
     S_GMRES_F = 24,      // 17: 1 / ||v_k|| of the FP16 Arnoldi basis, rounded to float
+    S_EO = 42,           // 12: red-black CG (gamma x2, |q|^2, |r|^2, tol^2, done, iterations, residual norms)
     S_GCR_R = 64,        // R[j][k] complex, K_MAX x K_MAX (column k, row j): 2*K_MAX*K_MAX
     S_GCR_C = 64 + 2 * 32 * 32,   // c_k complex
     S_COUNT = 64 + 2 * 32 * 32 + 64

@@ -68,6 +68,17 @@ struct BatchWork {
     long long graph_key[6] = {0, 0, 0, 0, 0, 0};
 };
 
+// Workspace of the red-black preconditioned CG (checkerboard layout).
+struct EoWork {
+    EoGeom e{};
+    double2* U64 = nullptr;   // [p][mu][9][Vh]
+    float2* U32 = nullptr;    // paired FP32 links
+    bool links_valid = false;
+    double2 *b = nullptr, *x = nullptr, *res = nullptr, *t = nullptr;   // FP64 full vectors [p][12][Vh]
+    void *xe = nullptr, *r = nullptr, *s = nullptr, *p = nullptr, *q = nullptr, *t1 = nullptr;   // inner, [12][Vh]
+    int inner_bytes = 0;      // 8: FP32 inner vectors, 16: FP64
+};
+
 template <typename T> struct Work {
     v2<T>* r = nullptr;    // GCR residual (T == double: aliases the FP64 residual)
     v2<T>* Z = nullptr;    // K_restart preconditioned directions
@@ -121,6 +132,7 @@ struct mg_ctx {
     double setup_ms = 0.0;           // device time of the last adaptive setup (CUDA events)
     CoarseLevel full, trunc;
     BatchWork bw;
+    EoWork eo;
     Work<float> wf;
     Work<double> wd;
     Reduce R{};
@@ -1128,6 +1140,7 @@ int load_links(mg_ctx* ctx, const double2* U_dev) {
     CKL();
     ctx->has_links = true;
     ctx->u16_valid = false;
+    ctx->eo.links_valid = false;
     ctx->full.valid = false;   // D_c depends on the links
     return MG_OK;
 }
@@ -1594,6 +1607,211 @@ extern "C" int mg_coarse_solve_noalloc(mg_ctx* ctx, const double* rc_dev, double
     if (final_rel)
         *final_rel = ctx->h_scal[S_CG_RC2] > 0 ? std::sqrt(ctx->h_scal[S_CG_R2] / ctx->h_scal[S_CG_RC2]) : 0.0;
     return MG_OK;
+}
+
+// ======================================================================= red-black preconditioned CG
+// The comparison solver of Sec. IV: CG on the normal equations of the
+// even-site Schur complement Dhat = (4+m) - H_eo H_oe / (4+m), inner
+// iterations in T (FP32 or FP64) with the solution accumulated in FP64; each
+// cycle restarts the CG on the FP64 true residual (defect correction) until
+// ||b - D x|| <= tol ||b||.
+namespace {
+
+constexpr int kEoCheck = 16;   // CG iterations queued between host reads of the done flag
+constexpr double kEoInnerDelta = 1e-4;   // FP32 inner solve: residual reduction per cycle
+
+int ensure_eo(mg_ctx* ctx, int inner_bytes) {
+    EoWork& w = ctx->eo;
+    const Geom& g = ctx->g;
+    if (!w.U64) {
+        for (int mu = 0; mu < 4; ++mu)
+            if (g.L[mu] % 2) return fail(ctx, MG_ERR_INVALID_ARG, "red-black CG needs even lattice extents");
+        w.e.Lh0 = g.L[0] / 2;
+        for (int mu = 0; mu < 4; ++mu) w.e.L[mu] = g.L[mu];
+        w.e.Vh = g.V / 2;
+        w.e.tap = g.tap;
+        const size_t nf = (size_t)24 * w.e.Vh;
+        TRY(dalloc(ctx, &w.U64, sizeof(double2) * 36 * (size_t)g.V));
+        TRY(dalloc(ctx, &w.U32, sizeof(float2) * 36 * (size_t)g.V));
+        TRY(dalloc(ctx, &w.b, sizeof(double2) * nf));
+        TRY(dalloc(ctx, &w.x, sizeof(double2) * nf));
+        TRY(dalloc(ctx, &w.res, sizeof(double2) * nf));
+        TRY(dalloc(ctx, &w.t, sizeof(double2) * nf));
+    }
+    if (w.inner_bytes != inner_bytes) {
+        for (void* q : {w.xe, w.r, w.s, w.p, w.q, w.t1}) dfree(ctx, q);
+        const size_t nh = (size_t)12 * w.e.Vh * inner_bytes;
+        for (void** q : {&w.xe, &w.r, &w.s, &w.p, &w.q, &w.t1}) {
+            unsigned char* a = nullptr;
+            TRY(dalloc(ctx, &a, nh));
+            *q = a;
+        }
+        w.inner_bytes = inner_bytes;
+    }
+    if (!w.links_valid) {
+        eo_links_pack(w.U64, w.U32, ctx->U64, g, w.e, ctx->st);
+        CKL();
+        w.links_valid = true;
+    }
+    return MG_OK;
+}
+
+// b_dev, x_dev: boundary-layout FP64 device spinors
+template <typename T>
+int eo_cg_solve(mg_ctx* ctx, const double2* b_dev, double2* x_dev, double tol, int maxit, mg_solve_info* info) {
+    TRY(need_links(ctx));
+    if (!(tol > 0) || maxit < 0) return fail(ctx, MG_ERR_INVALID_ARG, "tol must be > 0 and maxit >= 0");
+    TRY(ensure_eo(ctx, (int)sizeof(v2<T>)));
+    EoWork& w = ctx->eo;
+    const EoGeom& e = w.e;
+    const Reduce& R = ctx->R;
+    const long long nh = 12 * e.Vh;
+    const double a = 4.0 + ctx->mass, ainv = 1.0 / a;
+    const void* Ui = sizeof(T) == 4 ? (const void*)w.U32 : (const void*)w.U64;
+    v2<T>*xe = (v2<T>*)w.xe, *r = (v2<T>*)w.r, *sv = (v2<T>*)w.s, *p = (v2<T>*)w.p, *q = (v2<T>*)w.q,
+         *t1 = (v2<T>*)w.t1;
+    double2 *be = w.b, *bo = w.b + nh, *xe64 = w.x, *xo64 = w.x + nh, *re = w.res, *ro = w.res + nh;
+    double2 *te = w.t, *to = w.t + nh;
+    enum { G0 = S_EO, G1 = S_EO + 1, Q2 = S_EO + 2, R2 = S_EO + 3, TOL2 = S_EO + 4, DONE = S_EO + 5, ITS = S_EO + 6,
+           RE2 = S_EO + 7, RO2 = S_EO + 8, B2 = S_EO + 9 };
+    long long half_hops = 0, products = 0;   // half-lattice hops (bytes); matrix products (the count of Fig. 1)
+    int iters = 0, cycles = 0, status = MG_ERR_NOT_CONVERGED;
+    CK(cudaEventRecord(ctx->ev0, ctx->st));
+    eo_spinor_pack<double>(w.b, b_dev, e, ctx->st);
+    zero<double>(w.x, 2 * nh, ctx->st);
+    CK(cudaMemcpyAsync(w.res, w.b, sizeof(double2) * 2 * nh, cudaMemcpyDeviceToDevice, ctx->st));
+    norm2<double>(w.b, 2 * nh, B2, R, ctx->st);
+    CKL();
+    TRY(read_scalars(ctx, B2, 1));
+    const double bnorm = std::sqrt(ctx->h_scal[B2]);
+    ctx->h_scal[ITS] = 0.0;
+    CK(cudaMemcpyAsync(R.scal + ITS, ctx->h_scal + ITS, sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+    double rel = bnorm > 0 ? 1.0 : 0.0, rnorm = bnorm;
+    if (!std::isfinite(bnorm)) return fail(ctx, MG_ERR_NUMERIC, "right-hand side is not finite");
+    if (bnorm == 0) status = MG_OK;
+    const double delta = sizeof(T) == 4 ? kEoInnerDelta : 0.0;
+    // Reliable updates: every cycle ends with the FP64 residual of the
+    // accumulated solution; the next cycle replaces the CG residual by it and
+    // keeps the search direction (p = D^dag r + beta p with beta from the new
+    // |D^dag r|^2), so the FP32 iterations continue one CG instead of
+    // restarting it.  jg is the global iteration index: gamma_j = |s_j|^2
+    // lives in slot G0 + (j & 1).
+    int jg = 0;
+    while (status == MG_ERR_NOT_CONVERGED && iters < maxit) {
+        // bhat = res_e + H_eo res_o / (4+m) -> the inner right-hand side r, x_e = 0
+        eo_hop<double>(EO_SRC, te, ro, re, nullptr, w.U64, e, 0, 1.0, 0.0, ainv, 0, DONE, R, ctx->st);
+        half_hops += 1;
+        convert<double, T>(r, te, nh, ctx->st);
+        zero<T>(xe, nh, ctx->st);
+        // the inner residual equals b - D x in exact arithmetic; a drift is
+        // caught by the FP64 residual at the end of the cycle
+        const double target = std::max(delta * rnorm, tol * bnorm);
+        ctx->h_scal[TOL2] = target * target;
+        ctx->h_scal[DONE] = 0.0;
+        CK(cudaMemcpyAsync(R.scal + TOL2, ctx->h_scal + TOL2, sizeof(double) * 2, cudaMemcpyHostToDevice, ctx->st));
+        // s = Dhat^dag r = (4+m) r - gamma5 H_eo H_oe gamma5 r / (4+m); gamma_jg = |s|^2
+        const int gj = (jg & 1) ? G1 : G0, gprev = (jg & 1) ? G0 : G1;
+        eo_hop<T>(EO_G5IN, t1, r, nullptr, nullptr, Ui, e, 1, 0.0, 0.0, 1.0, 0, DONE, R, ctx->st);
+        eo_hop<T>(EO_SELF | EO_NORM | EO_G5H, sv, t1, nullptr, r, Ui, e, 0, 0.0, a, -ainv, gj, DONE, R, ctx->st);
+        half_hops += 2;
+        if (jg == 0) CK(cudaMemcpyAsync(p, sv, sizeof(v2<T>) * nh, cudaMemcpyDeviceToDevice, ctx->st));
+        else eo_cg_update2<T>(p, sv, nh, gprev, gj, DONE, R, ctx->st);
+        CKL();
+        const int budget = maxit - iters;
+        int queued = 0, done_its = 0;
+        for (;;) {
+            const int n = std::min(kEoCheck, budget - queued);
+            for (int j = jg + queued; j < jg + queued + n; ++j) {
+                const int g_old = (j & 1) ? G1 : G0, g_new = (j & 1) ? G0 : G1;
+                EoCgSlots sl{g_old, Q2, R2, TOL2, DONE, ITS};
+                // q = Dhat p, |q|^2
+                eo_hop<T>(EO_SKIP, t1, p, nullptr, nullptr, Ui, e, 1, 0.0, 0.0, 1.0, 0, DONE, R, ctx->st);
+                eo_hop<T>(EO_SKIP | EO_SELF | EO_NORM, q, t1, nullptr, p, Ui, e, 0, 0.0, a, -ainv, Q2, DONE, R, ctx->st);
+                // x_e += alpha p, r -= alpha q, |r|^2, convergence
+                eo_cg_update1<T>(xe, r, p, q, nh, sl, j, R, ctx->st);
+                // s = Dhat^dag r, |s|^2 -> the new gamma; p = s + beta p
+                eo_hop<T>(EO_SKIP | EO_G5IN, t1, r, nullptr, nullptr, Ui, e, 1, 0.0, 0.0, 1.0, 0, DONE, R, ctx->st);
+                eo_hop<T>(EO_SKIP | EO_SELF | EO_NORM | EO_G5H, sv, t1, nullptr, r, Ui, e, 0, 0.0, a, -ainv, g_new, DONE,
+                          R, ctx->st);
+                eo_cg_update2<T>(p, sv, nh, g_old, g_new, DONE, R, ctx->st);
+            }
+            CKL();
+            queued += n;
+            TRY(read_scalars(ctx, DONE, 2));
+            done_its = (int)ctx->h_scal[ITS] - jg;
+            if (ctx->h_scal[DONE] != 0.0 || queued >= budget) break;
+        }
+        // the last iteration's D^dag r is skipped once the CG has stopped
+        const int skipped = done_its > 0 && ctx->h_scal[DONE] != 0.0 ? 1 : 0;
+        iters += done_its;
+        jg += done_its;
+        half_hops += 4LL * done_its - 2 * skipped;
+        // per cycle: bhat, Dhat^dag r_0, Dhat and Dhat^dag per iteration, x_o, the residual
+        products += 1 + 1 + 2LL * done_its - skipped + 1 + 1;
+        // x_e += x_e(inner); x_o += (res_o + H_oe x_e(inner)) / (4+m), in FP64
+        convert<T, double>(te, xe, nh, ctx->st);
+        axpy<double>(xe64, te, nh, 1.0, 0.0, ctx->st);
+        eo_hop<double>(EO_SRC | EO_ACC, xo64, te, ro, nullptr, w.U64, e, 1, ainv, 0.0, ainv, 0, DONE, R, ctx->st);
+        // the true residual b - D x in FP64 on both parities
+        eo_hop<double>(EO_SRC | EO_SELF | EO_NORM, re, xo64, be, xe64, w.U64, e, 0, 1.0, -a, 1.0, RE2, DONE, R, ctx->st);
+        eo_hop<double>(EO_SRC | EO_SELF | EO_NORM, ro, xe64, bo, xo64, w.U64, e, 1, 1.0, -a, 1.0, RO2, DONE, R, ctx->st);
+        half_hops += 3;
+        CKL();
+        TRY(read_scalars(ctx, RE2, 2));
+        ++cycles;
+        rnorm = std::sqrt(ctx->h_scal[RE2] + ctx->h_scal[RO2]);
+        rel = rnorm / bnorm;
+        if (!std::isfinite(rel)) { status = MG_ERR_NUMERIC; break; }
+        if (rel <= tol) status = MG_OK;
+        else if (done_its == 0) { status = MG_ERR_NUMERIC; break; }   // no progress possible
+    }
+    eo_spinor_unpack<double>(x_dev, w.x, e, ctx->st);
+    CKL();
+    CK(cudaEventRecord(ctx->ev1, ctx->st));
+    CK(cudaEventSynchronize(ctx->ev1));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+    if (info) {
+        info->outer_iters = iters;
+        info->coarse_iters = 0;
+        info->fine_matvecs = (int)products;
+        info->restarts = cycles;
+        info->true_rel_res = rel;
+        info->solve_ms = ms;
+        info->status = status;
+        info->setup_ms = 0.0;
+        // per half-lattice hop: all 4 V links once, the input and output half vectors
+        const double per_site = sizeof(T) == 4 ? (288.0 + 96.0) : (576.0 + 192.0);
+        info->dslash_bytes = (double)half_hops * per_site * (double)ctx->g.V;
+    }
+    if (status == MG_ERR_NOT_CONVERGED) ctx->err = "red-black CG: maxit reached";
+    if (status == MG_ERR_NUMERIC) ctx->err = "red-black CG: non-finite residual or no progress";
+    return status;
+}
+
+}  // namespace
+
+extern "C" int mg_solve_eo_cg_device(mg_ctx* ctx, const double* b_dev, double* x_dev, double tol, int maxit, int prec,
+                                     mg_solve_info* info) {
+    if (!ctx || !b_dev || !x_dev) return MG_ERR_INVALID_ARG;
+    if (prec != MG_FP64 && prec != MG_FP32) return fail(ctx, MG_ERR_INVALID_ARG, "prec must be MG_FP64 or MG_FP32");
+    int st = prec == MG_FP64 ? eo_cg_solve<double>(ctx, (const double2*)b_dev, (double2*)x_dev, tol, maxit, info)
+                             : eo_cg_solve<float>(ctx, (const double2*)b_dev, (double2*)x_dev, tol, maxit, info);
+    if (st == MG_OK || st == MG_ERR_NOT_CONVERGED) CK(cudaStreamSynchronize(ctx->st));
+    return st;
+}
+
+extern "C" int mg_solve_eo_cg(mg_ctx* ctx, const double* b, double* x, double tol, int maxit, int prec,
+                              mg_solve_info* info) {
+    if (!ctx || !b || !x) return MG_ERR_INVALID_ARG;
+    const size_t n = nfine(ctx);
+    CK(cudaMemcpyAsync(ctx->stage_a, b, sizeof(double2) * n, cudaMemcpyHostToDevice, ctx->st));
+    int st = mg_solve_eo_cg_device(ctx, (const double*)ctx->stage_a, (double*)ctx->stage_b, tol, maxit, prec, info);
+    if (st == MG_OK || st == MG_ERR_NOT_CONVERGED) {
+        CK(cudaMemcpyAsync(x, ctx->stage_b, sizeof(double2) * n, cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+    }
+    return st;
 }
 
 // ======================================================================= batched right-hand sides

@@ -224,6 +224,34 @@ bool cgls_shape(int nc, int Vc, bool h16, int mode, CglsShape* out);
 // Not for graph capture: every launch takes a fresh epoch range from the host.
 void coarse_pack_units(void* Au, float* su, const double2* A, int nc, int ru, int Vc, bool h16, cudaStream_t st);
 cudaError_t cgls_onchip(const CglsArgs& args, cudaStream_t st);
+// ---------------------------------------------------------------- red-black preconditioned CG
+// checkerboard geometry: Vh = V / 2 sites per parity, cb index = lex >> 1
+struct EoGeom {
+    int L[4];
+    int Lh0;        // L[0] / 2
+    long long Vh;
+    int tap;
+};
+// epilogue flags of the half-lattice hop
+enum EoFlags { EO_PLAIN = 0, EO_SRC = 1, EO_SELF = 2, EO_ACC = 4, EO_NORM = 8, EO_G5IN = 16, EO_G5H = 32, EO_SKIP = 64 };
+// device scalar slots of the CG
+struct EoCgSlots {
+    int gamma, q2, r2, tol2, done, iters;
+};
+template <typename T>
+void eo_hop(int flags, v2<T>* out, const v2<T>* in, const v2<T>* src, const v2<T>* self, const void* U,
+            const EoGeom& e, int p, double c_src, double c_self, double c_h, int slot, int done_slot, const Reduce& R,
+            cudaStream_t st);
+template <typename T>
+void eo_cg_update1(v2<T>* x, v2<T>* r, const v2<T>* p, const v2<T>* q, long long n, const EoCgSlots& s, int iter,
+                   const Reduce& R, cudaStream_t st);
+template <typename T>
+void eo_cg_update2(v2<T>* p, const v2<T>* sv, long long n, int gamma_old, int gamma_new, int done, const Reduce& R,
+                   cudaStream_t st);
+template <typename T> void eo_spinor_pack(v2<T>* out, const double2* in, const EoGeom& e, cudaStream_t st);
+template <typename T> void eo_spinor_unpack(double2* out, const v2<T>* in, const EoGeom& e, cudaStream_t st);
+void eo_links_pack(double2* U64, float2* U32, const double2* Uint, const Geom& g, const EoGeom& e, cudaStream_t st);
+
 // one bounded device wait driven into a configuration that cannot complete
 cudaError_t wait_probe(int kind, int G, unsigned long long* words, unsigned int* ctr, int* err, long long limit,
                        cudaStream_t st);
