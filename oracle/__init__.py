@@ -31,6 +31,16 @@ Parity status per function (what pins it; see the tests):
                     gamma5-hermiticity of Dhat; CG iterates equal the
                     least-squares solution over the Krylov space (numpy
                     lstsq); dense solve on a small lattice; true residual
+  cblock_orthonormalize / crestrict / cprolong / ccoarse_build (level 2)
+                    P2^dag P2 = I, P2 V2_c = V2, sigma3 kept, numpy QR,
+                    adjointness, dense P2^dag A1 P2 for level-2 extents 2, 1
+                    and mixed, (I - P2 A2^-1 P2^dag A1) P2 = 0
+  csmooth / kcycle_l1 / vcycle3 / gcr_solve3 / setup_level2
+                    level-1 smoother = lstsq over K_k(A1, r); the W-cycle
+                    equals its composition from single V-cycles; the fine
+                    cycle smooths r - D P K1(P^dag r) (lstsq); the 3-level
+                    solve reaches 1e-10; the level-2 setup lowers the level-1
+                    two-grid rate (refined < relaxed < random)
   two_grid_factor   eq. 3 with an exact coarse solve: a start in range(P)
                     is annihilated, the unsmoothed E_TG is a projection, the
                     corrected residual is Galerkin-orthogonal to range(P)
@@ -71,7 +81,9 @@ class Params(ctypes.Structure):
                 ("omega", ctypes.c_double), ("coarse_tol", ctypes.c_double),
                 ("coarse_maxit", ctypes.c_int), ("gcr_restart", ctypes.c_int),
                 ("tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("use_mg", ctypes.c_int),
-                ("smoother", ctypes.c_int)]
+                ("smoother", ctypes.c_int), ("levels", ctypes.c_int), ("B2", ctypes.c_int * 4),
+                ("nv2", ctypes.c_int), ("smoother1", ctypes.c_int), ("steps1", ctypes.c_int),
+                ("cycles1", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -110,6 +122,20 @@ def _load():
             lib.or_gcr_solve.restype = I
             lib.or_setup.argtypes = [P, P, P, I, I, I, P, P]
             lib.or_setup.restype = I
+            lib.or_cblock_orthonormalize.argtypes = [P, P, I, I, P, P]
+            lib.or_cblock_orthonormalize.restype = I
+            lib.or_crestrict.argtypes = [P, P, I, I, P, P, P]
+            lib.or_cprolong.argtypes = [P, P, I, I, P, P, P]
+            lib.or_ccoarse_build.argtypes = [P, P, I, I, P, P, P]
+            lib.or_csmooth.argtypes = [P, P, P, P, P]
+            lib.or_kcycle_l1.argtypes = [P, P, P, P, P, P, P]
+            lib.or_setup_level2.argtypes = [P, P, P, I, I, I, P, P, P]
+            lib.or_setup_level2.restype = I
+            lib.or_vcycle3.argtypes = [P, P, P, P, P, P, P, P, P]
+            lib.or_gcr_solve3.argtypes = [P, P, P, P, P, P, P, P, P]
+            lib.or_gcr_solve3.restype = I
+            lib.or_setup_counted.argtypes = [P, P, P, I, I, I, P, P, P]
+            lib.or_setup_counted.restype = I
             lib.or_setup_truncated_level.argtypes = [P, P, P, I, I, P, P, P]
             lib.or_setup_truncated_level.restype = I
             lib.or_eo_schur.argtypes = [P, I, P, D, I, P, P]
@@ -236,7 +262,8 @@ def cgnr(A, rc, Lc, tol: float, maxit: int):
 
 
 def make_params(L, B=(4, 4, 4, 4), nv=8, m=0.0, tap=1, mr_steps=4, omega=0.9, coarse_tol=1e-3,
-                coarse_maxit=10000, gcr_restart=16, tol=1e-10, max_outer=1000, use_mg=1, smoother=0) -> Params:
+                coarse_maxit=10000, gcr_restart=16, tol=1e-10, max_outer=1000, use_mg=1, smoother=0,
+                levels=2, B2=(2, 2, 2, 2), nv2=0, smoother1=1, steps1=4, cycles1=2) -> Params:
     p = Params()
     for i in range(4):
         p.L[i] = int(L[i]); p.B[i] = int(B[i])
@@ -245,6 +272,10 @@ def make_params(L, B=(4, 4, 4, 4), nv=8, m=0.0, tap=1, mr_steps=4, omega=0.9, co
     p.coarse_tol, p.coarse_maxit = float(coarse_tol), int(coarse_maxit)
     p.gcr_restart, p.tol, p.max_outer, p.use_mg = int(gcr_restart), float(tol), int(max_outer), int(use_mg)
     p.smoother = int(smoother)
+    p.levels, p.nv2 = int(levels), int(nv2)
+    for i in range(4):
+        p.B2[i] = int(B2[i])
+    p.smoother1, p.steps1, p.cycles1 = int(smoother1), int(steps1), int(cycles1)
     return p
 
 
@@ -283,6 +314,23 @@ def setup(params: Params, U, V0, init_relax: int, n_iter: int, group_size: int =
     st = _load().or_setup(ctypes.byref(params), _p(U), _p(Vv), int(init_relax), int(n_iter),
                          int(group_size), _p(P), _p(A))
     return Vv, P, A, st
+
+
+def setup_counted(params: Params, U, V0, init_relax: int, n_iter: int, group_size: int = 4):
+    """setup() that also returns its work: (V, P, A, status, info) with
+    info['fine_matvecs'] the operator applications of the relaxation and the
+    truncated cycles and info['coarse_iters'] their coarse CG iterations."""
+    U = _c(U)
+    Vv = _c(V0).copy()
+    nv = Vv.shape[0]
+    assert nv == params.nv
+    Lc = coarse_dims(list(params.L), list(params.B))
+    P = np.empty_like(Vv)
+    A = np.empty((volume(Lc), 9, 2 * nv, 2 * nv), dtype=np.complex128)
+    info = Info()
+    st = _load().or_setup_counted(ctypes.byref(params), _p(U), _p(Vv), int(init_relax), int(n_iter),
+                                  int(group_size), _p(P), _p(A), ctypes.byref(info))
+    return Vv, P, A, st, info.as_dict()
 
 
 def setup_truncated_level(params: Params, U, V, g0: int, group_size: int):
@@ -370,3 +418,117 @@ def eo_cg(U, b, m: float, L, tol: float, maxit: int, tap: int = 1):
     st = _load().or_eo_cg(_p(_i4(L)), int(tap), _p(_c(U)), float(m), _p(b), _p(x), float(tol), int(maxit),
                           ctypes.byref(it), ctypes.byref(mv), ctypes.byref(rel))
     return x, it.value, mv.value, rel.value, st
+
+
+# ---------------------------------------------------------------- third level (Sec. III recursion, Sec. IV W-cycle)
+def cblock_orthonormalize(V2, Lc1, B2, nv1: int):
+    """Level-1 vectors V2 (nv2, Vc1, 2 nv1) -> (P2, status): eq. 4 one level down,
+    per level-2 aggregate and chirality (dof a of chirality a // nv1)."""
+    V2 = _c(V2)
+    P2 = np.empty_like(V2)
+    st = _load().or_cblock_orthonormalize(_p(_i4(Lc1)), _p(_i4(B2)), int(nv1), int(V2.shape[0]), _p(V2), _p(P2))
+    return P2, st
+
+
+def crestrict(P2, r1, Lc1, B2, nv1: int) -> np.ndarray:
+    P2, r1 = _c(P2), _c(r1)
+    Lc2 = coarse_dims(Lc1, B2)
+    out = np.empty((volume(Lc2), 2 * P2.shape[0]), dtype=np.complex128)
+    _load().or_crestrict(_p(_i4(Lc1)), _p(_i4(B2)), int(nv1), int(P2.shape[0]), _p(P2), _p(r1), _p(out))
+    return out
+
+
+def cprolong(P2, y2, Lc1, B2, nv1: int) -> np.ndarray:
+    P2, y2 = _c(P2), _c(y2)
+    out = np.empty((volume(Lc1), 2 * nv1), dtype=np.complex128)
+    _load().or_cprolong(_p(_i4(Lc1)), _p(_i4(B2)), int(nv1), int(P2.shape[0]), _p(P2), _p(y2), _p(out))
+    return out
+
+
+def ccoarse_build(A1, P2, Lc1, B2) -> np.ndarray:
+    """A2 = P2^dag A1 P2 in nearest-neighbour form (slots by the face a term leaves through)."""
+    A1, P2 = _c(A1), _c(P2)
+    nv1, nv2 = A1.shape[-1] // 2, P2.shape[0]
+    Lc2 = coarse_dims(Lc1, B2)
+    A2 = np.empty((volume(Lc2), 9, 2 * nv2, 2 * nv2), dtype=np.complex128)
+    _load().or_ccoarse_build(_p(_i4(Lc1)), _p(_i4(B2)), int(nv1), int(nv2), _p(A1), _p(P2), _p(A2))
+    return A2
+
+
+def csmooth(params: Params, Lc1, A1, e, r):
+    """Level-1 post-smoothing (params.smoother1: MR or GMRES(steps1), omega) on (e, r); returns (e, r)."""
+    e, r = _c(e).copy(), _c(r).copy()
+    _load().or_csmooth(ctypes.byref(params), _p(_i4(Lc1)), _p(_c(A1)), _p(e), _p(r))
+    return e, r
+
+
+def kcycle_l1(params: Params, A1, P2, A2, r1):
+    """The three-level method's coarse-grid correction: params.cycles1 level-1
+    V-cycles on A1 e = r1 from e = 0.  Returns (e1, info)."""
+    r1 = _c(r1)
+    e1 = np.empty_like(r1)
+    info = Info()
+    _load().or_kcycle_l1(ctypes.byref(params), _p(_c(A1)), _p(_c(P2)), _p(_c(A2)), _p(r1), _p(e1),
+                         ctypes.byref(info))
+    return e1, info.as_dict()
+
+
+def setup_level2(params: Params, A1, V2, init_relax: int, n_iter: int, group_size: int = 4):
+    """Adaptive setup of level 2 on the operator A1 from random level-1 starts V2
+    (nv2, Vc1, 2 nv1): returns (V2, P2, A2, status, info)."""
+    A1 = _c(A1)
+    V = _c(V2).copy()
+    Lc1 = coarse_dims(list(params.L), list(params.B))
+    Lc2 = coarse_dims(Lc1, list(params.B2))
+    nv2 = V.shape[0]
+    assert nv2 == params.nv2
+    P2 = np.empty_like(V)
+    A2 = np.empty((volume(Lc2), 9, 2 * nv2, 2 * nv2), dtype=np.complex128)
+    info = Info()
+    st = _load().or_setup_level2(ctypes.byref(params), _p(A1), _p(V), int(init_relax), int(n_iter), int(group_size),
+                                 _p(P2), _p(A2), ctypes.byref(info))
+    return V, P2, A2, st, info.as_dict()
+
+
+def vcycle3(params: Params, U, P, A, P2, A2, r):
+    r = _c(r)
+    z = np.empty_like(r)
+    info = Info()
+    _load().or_vcycle3(ctypes.byref(params), _p(_c(U)), _p(_c(P)), _p(_c(A)), _p(_c(P2)), _p(_c(A2)), _p(r), _p(z),
+                       ctypes.byref(info))
+    return z, info.as_dict()
+
+
+def gcr_solve3(params: Params, U, P, A, P2, A2, b):
+    """Flexible GCR preconditioned by the three-level W-cycle: returns (x, info)."""
+    b = _c(b)
+    x = np.empty_like(b)
+    info = Info()
+    _load().or_gcr_solve3(ctypes.byref(params), _p(_c(U)), _p(_c(P)), _p(_c(A)), _p(_c(P2)), _p(_c(A2)), _p(b),
+                          _p(x), ctypes.byref(info))
+    return x, info.as_dict()
+
+
+def ctwo_grid_factor(params: Params, A1, P2, A2, e0, k: int):
+    """Eq. 3 one level down: the two-grid method of levels 1 and 2 on A1 e = 0
+    with the level-2 system solved exactly (dense LU of A2, scipy) and the
+    level-1 post-smoother (params.smoother1, steps1, omega): e <- e + P2 A2^-1
+    P2^dag (-A1 e), then the smoother on (e, -A1 e).  Returns (factor over k
+    iterations, [||e_j||, j = 0..k])."""
+    from scipy.linalg import lu_factor, lu_solve
+    A1, P2, A2 = _c(A1), _c(P2), _c(A2)
+    Lc1 = coarse_dims(list(params.L), list(params.B))
+    B2 = list(params.B2)
+    Lc2 = coarse_dims(Lc1, B2)
+    nv1 = A1.shape[-1] // 2
+    lu = lu_factor(coarse_dense(A2, Lc2))
+    e = _c(e0).copy()
+    norms = [float(np.linalg.norm(e))]
+    for _ in range(k):
+        r = -coarse_apply(A1, e, Lc1)
+        y = lu_solve(lu, crestrict(P2, r, Lc1, B2, nv1).ravel()).reshape(volume(Lc2), -1)
+        e = e + cprolong(P2, y, Lc1, B2, nv1)
+        if params.steps1 > 0:
+            e, _ = csmooth(params, Lc1, A1, e, -coarse_apply(A1, e, Lc1))
+        norms.append(float(np.linalg.norm(e)))
+    return (norms[-1] / norms[0]) ** (1.0 / k), norms

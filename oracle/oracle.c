@@ -467,6 +467,13 @@ typedef struct {
     int max_outer;
     int use_mg;          /* 0: unpreconditioned GCR (M = I) */
     int smoother;        /* 0: mr_steps MR steps; 1: one GMRES(mr_steps) application */
+    /* third level (Sec. IV's 3-level W-cycle); levels = 2 ignores the rest */
+    int levels;          /* 2 or 3 */
+    int B2[4];           /* aggregates of the first coarse lattice (level 1 -> level 2) */
+    int nv2;             /* prototypes of level 2 (2 nv2 dof per level-2 site) */
+    int smoother1;       /* level-1 post-smoother: 0 MR steps, 1 one GMRES(steps1) */
+    int steps1;
+    int cycles1;         /* level-1 V-cycles per fine-grid correction (2: the W-cycle) */
 } or_params;
 
 typedef struct {
@@ -484,8 +491,12 @@ typedef struct {
     const cplx* U;
     const cplx* P;
     const cplx* A;
+    const cplx* P2;      /* third level (levels = 3): level-2 prolongator and operator */
+    const cplx* A2;
     or_info* info;
 } mg_t;
+
+static void kcycle_l1(const mg_t* g, const cplx* r1, cplx* e1);
 
 static void D_apply(const mg_t* g, const cplx* in, cplx* out) {
     or_dslash(g->p->L, g->p->tap, (const double*)g->U, g->p->m, (const double*)in, (double*)out);
@@ -666,9 +677,13 @@ static void vcycle(const mg_t* g, const cplx* r_in, cplx* z) {
     cplx* r = (cplx*)malloc(sizeof(cplx) * n);
     cplx* De = (cplx*)malloc(sizeof(cplx) * n);
     or_restrict(p->L, p->B, p->nv, (const double*)g->P, (const double*)r_in, (double*)rc);
-    int it = or_cgnr(g->bk.Lc, g->bk.nc, (const double*)g->A, (const double*)rc, (double*)yc,
-                     p->coarse_tol, p->coarse_maxit, NULL);
-    if (g->info) g->info->coarse_iters += it;
+    if (p->levels == 3 && g->P2) {
+        kcycle_l1(g, rc, yc);                  /* Sec. IV: V-cycles on the intermediate grid */
+    } else {
+        int it = or_cgnr(g->bk.Lc, g->bk.nc, (const double*)g->A, (const double*)rc, (double*)yc,
+                         p->coarse_tol, p->coarse_maxit, NULL);
+        if (g->info) g->info->coarse_iters += it;
+    }
     or_prolong(p->L, p->B, p->nv, (const double*)g->P, (const double*)yc, (double*)z);
     D_apply(g, z, De);
     for (int64_t i = 0; i < n; ++i) r[i] = r_in[i] - De[i];
@@ -684,6 +699,17 @@ OR_API void or_vcycle(const or_params* p, const double* U, const double* P, cons
     mg_t g;
     blocking_init(&g.bk, p->L, p->B, p->nv);
     g.p = p; g.U = (const cplx*)U; g.P = (const cplx*)P; g.A = (const cplx*)A; g.info = info;
+    g.P2 = NULL; g.A2 = NULL;
+    vcycle(&g, (const cplx*)r, (cplx*)z);
+}
+
+/* one fine-grid cycle of the three-level method (p->levels = 3) */
+OR_API void or_vcycle3(const or_params* p, const double* U, const double* P, const double* A, const double* P2,
+                       const double* A2, const double* r, double* z, or_info* info) {
+    mg_t g;
+    blocking_init(&g.bk, p->L, p->B, p->nv);
+    g.p = p; g.U = (const cplx*)U; g.P = (const cplx*)P; g.A = (const cplx*)A; g.info = info;
+    g.P2 = (const cplx*)P2; g.A2 = (const cplx*)A2;
     vcycle(&g, (const cplx*)r, (cplx*)z);
 }
 
@@ -697,8 +723,22 @@ OR_API void or_vcycle(const or_params* p, const double* U, const double* P, cons
  * (upper triangular), x += sum_k y_k z_k, r = b - D x (true residual).
  * Converged when the true relative residual is <= tol.
  */
+static int gcr_solve_impl(const or_params* p, const double* Ur, const double* Pr, const double* Ar,
+                          const double* P2r, const double* A2r, const double* br, double* xr, or_info* info);
+
 OR_API int or_gcr_solve(const or_params* p, const double* Ur, const double* Pr, const double* Ar,
                         const double* br, double* xr, or_info* info) {
+    return gcr_solve_impl(p, Ur, Pr, Ar, NULL, NULL, br, xr, info);
+}
+
+/* the same with the third level: P2r, A2r from or_setup_level2 (p->levels = 3) */
+OR_API int or_gcr_solve3(const or_params* p, const double* Ur, const double* Pr, const double* Ar,
+                         const double* P2r, const double* A2r, const double* br, double* xr, or_info* info) {
+    return gcr_solve_impl(p, Ur, Pr, Ar, P2r, A2r, br, xr, info);
+}
+
+static int gcr_solve_impl(const or_params* p, const double* Ur, const double* Pr, const double* Ar,
+                          const double* P2r, const double* A2r, const double* br, double* xr, or_info* info) {
     mg_t g;
     if (p->use_mg) {
         if (blocking_init(&g.bk, p->L, p->B, p->nv) != OR_OK) return OR_ERR_ARG;
@@ -709,6 +749,7 @@ OR_API int or_gcr_solve(const or_params* p, const double* Ur, const double* Pr, 
     or_info local;
     memset(&local, 0, sizeof(local));
     g.p = p; g.U = (const cplx*)Ur; g.P = (const cplx*)Pr; g.A = (const cplx*)Ar; g.info = &local;
+    g.P2 = (const cplx*)P2r; g.A2 = (const cplx*)A2r;
     int64_t n = g.bk.V * 12;
     int K = p->gcr_restart;
     const cplx* b = (const cplx*)br;
@@ -809,8 +850,21 @@ OR_API int or_setup_truncated_level(const or_params* p, const double* Ur, const 
     return OR_OK;
 }
 
+OR_API int or_setup_counted(const or_params* p, const double* Ur, double* Vr, int init_relax, int n_iter,
+                            int group_size, double* Pr, double* Ar, or_info* info);
+
 OR_API int or_setup(const or_params* p, const double* Ur, double* Vr, int init_relax, int n_iter,
                     int group_size, double* Pr, double* Ar) {
+    return or_setup_counted(p, Ur, Vr, init_relax, n_iter, group_size, Pr, Ar, NULL);
+}
+
+/* or_setup that also reports its work (info may be NULL): fine_matvecs counts
+ * the operator applications of the relaxation and of the truncated cycles,
+ * coarse_iters the coarse CG iterations of those cycles. */
+OR_API int or_setup_counted(const or_params* p, const double* Ur, double* Vr, int init_relax, int n_iter,
+                            int group_size, double* Pr, double* Ar, or_info* info) {
+    or_info local;
+    memset(&local, 0, sizeof(local));
     blocking_t bk;
     if (blocking_init(&bk, p->L, p->B, p->nv) != OR_OK) return OR_ERR_ARG;
     if (group_size <= 0 || p->nv % group_size != 0) return OR_ERR_ARG;
@@ -825,6 +879,7 @@ OR_API int or_setup(const or_params* p, const double* Ur, double* Vr, int init_r
         or_dslash(p->L, p->tap, Ur, p->m, (const double*)v, (double*)r);
         for (int64_t k = 0; k < n; ++k) r[k] = -r[k];
         or_mr(p->L, p->tap, Ur, p->m, init_relax, p->omega, (double*)v, (double*)r);
+        local.fine_matvecs += 1 + init_relax;
         double nrm = sqrt(vnorm2(n, v));
         for (int64_t k = 0; k < n; ++k) v[k] /= nrm;
     }
@@ -841,7 +896,9 @@ OR_API int or_setup(const or_params* p, const double* Ur, double* Vr, int init_r
             st = or_setup_truncated_level(p, Ur, Vr, g0, group_size, (double*)Vt, (double*)Pt, (double*)At);
             if (st != OR_OK) break;
             mg_t g;
-            g.bk = bt; g.p = &pt; g.U = (const cplx*)Ur; g.P = Pt; g.A = At; g.info = NULL;
+            g.bk = bt; g.p = &pt; g.U = (const cplx*)Ur; g.P = Pt; g.A = At; g.info = &local;
+            g.P2 = NULL; g.A2 = NULL;
+            pt.levels = 2;                     /* the truncated method is two-level */
             for (int i = g0; i < g0 + group_size; ++i) {
                 cplx* v = V + (int64_t)i * n;
                 for (int it = 0; it < n_iter; ++it) {
@@ -859,6 +916,8 @@ OR_API int or_setup(const or_params* p, const double* Ur, double* Vr, int init_r
     if (st == OR_OK) st = or_block_orthonormalize(p->L, p->B, nv, Vr, Pr);
     if (st == OR_OK) or_coarse_build(p->L, p->B, nv, p->tap, Ur, p->m, Pr, Ar);
     free(r); free(z);
+    local.status = st;
+    if (info) *info = local;
     return st;
 }
 
@@ -994,5 +1053,384 @@ OR_API int or_eo_cg(const int* L, int tap, const double* Ur, double m, const dou
     if (iters_out) *iters_out = it;
     if (matvecs_out) *matvecs_out = mv;
     if (rel_out) *rel_out = rel;
+    return st;
+}
+
+/* ------------------------------------------------------------------ */
+/* The next level down.  Sec. III: the coarsening is recursed with the   */
+/* chiral components kept separate, so every level is a nearest-        */
+/* neighbour operator with 2Nv x 2Nv links.  Sec. IV: a 3-level cycle,  */
+/* GMRES post-relaxation on each level, and a W-cycle -- for every      */
+/* correction to the fine grid two V-cycles update the intermediate     */
+/* grid -- with CG on the normal equations to 1e-3 on the coarsest.     */
+/*                                                                     */
+/* Level-1 vectors: [x1][2 nv1] complex, dof a of chirality a / nv1.    */
+/* Level-2 prolongator P2: nv2 level-1 vectors [i][x1][2 nv1]; column   */
+/* (X2, s, i) is vector i on the level-1 sites of aggregate X2 and the  */
+/* dof of chirality s.  Level-2 operator A2[X2][d][a][b] like D_c.      */
+/* ------------------------------------------------------------------ */
+
+/* Block orthonormalisation of level-1 vectors (eq. 4 one level down): per
+ * aggregate X2 and chirality s, MGS twice in index order over the entries
+ * (x1 in X2, j < nv1) of dof s*nv1 + j; positive real R diagonal. */
+OR_API int or_cblock_orthonormalize(const int* Lc1, const int* B2, int nv1, int nv2, const double* vr, double* Pr) {
+    blocking_t bk;
+    if (blocking_init(&bk, Lc1, B2, nv2) != OR_OK || nv1 <= 0 || nv2 <= 0) return OR_ERR_ARG;
+    const int nc1 = 2 * nv1;
+    const cplx* v = (const cplx*)vr;
+    cplx* P = (cplx*)Pr;
+    int64_t Vb = bk.V / bk.Vc, len = Vb * nv1;
+    int64_t* sites = block_sites(&bk);
+    int status = OR_OK;
+    cplx* W = (cplx*)malloc(sizeof(cplx) * len * nv2);
+    double* orig = (double*)malloc(sizeof(double) * nv2);
+    for (int64_t X = 0; X < bk.Vc; ++X)
+        for (int s = 0; s < 2; ++s) {
+            for (int i = 0; i < nv2; ++i)
+                for (int64_t k = 0; k < Vb; ++k)
+                    for (int j = 0; j < nv1; ++j)
+                        W[i * len + k * nv1 + j] = v[((int64_t)i * bk.V + sites[X * Vb + k]) * nc1 + s * nv1 + j];
+            for (int i = 0; i < nv2; ++i) {
+                cplx* wi = W + i * len;
+                orig[i] = sqrt(vnorm2(len, wi));
+                for (int pass = 0; pass < 2; ++pass)
+                    for (int j = 0; j < i; ++j) {
+                        cplx c = vdot(len, W + j * len, wi);
+                        vaxpy(len, -c, W + j * len, wi);
+                    }
+                double nn = sqrt(vnorm2(len, wi));
+                if (!(nn > 1e-12 * orig[i])) { status = OR_ERR_NUMERIC; nn = 1.0; }
+                for (int64_t k = 0; k < len; ++k) wi[k] /= nn;
+            }
+            for (int i = 0; i < nv2; ++i)
+                for (int64_t k = 0; k < Vb; ++k)
+                    for (int j = 0; j < nv1; ++j)
+                        P[((int64_t)i * bk.V + sites[X * Vb + k]) * nc1 + s * nv1 + j] = W[i * len + k * nv1 + j];
+        }
+    free(W); free(orig); free(sites);
+    return status;
+}
+
+/* r2 = P2^dag r1: r2[X2][s nv2 + i] = sum over x1 in X2, j < nv1 of conj(P2_i(x1, s nv1 + j)) r1(x1, s nv1 + j) */
+OR_API int or_crestrict(const int* Lc1, const int* B2, int nv1, int nv2, const double* Pr, const double* rr,
+                        double* r2r) {
+    blocking_t bk;
+    if (blocking_init(&bk, Lc1, B2, nv2) != OR_OK) return OR_ERR_ARG;
+    const int nc1 = 2 * nv1, nc2 = 2 * nv2;
+    const cplx* P = (const cplx*)Pr;
+    const cplx* r = (const cplx*)rr;
+    cplx* r2 = (cplx*)r2r;
+    int64_t Vb = bk.V / bk.Vc;
+    int64_t* sites = block_sites(&bk);
+    for (int64_t X = 0; X < bk.Vc; ++X)
+        for (int s = 0; s < 2; ++s)
+            for (int i = 0; i < nv2; ++i) {
+                cplx acc = 0;
+                for (int64_t k = 0; k < Vb; ++k) {
+                    int64_t x = sites[X * Vb + k];
+                    for (int j = 0; j < nv1; ++j)
+                        acc += conj(P[((int64_t)i * bk.V + x) * nc1 + s * nv1 + j]) * r[x * nc1 + s * nv1 + j];
+                }
+                r2[X * nc2 + s * nv2 + i] = acc;
+            }
+    free(sites);
+    return OR_OK;
+}
+
+/* e1 = P2 y2: e1(x1, s nv1 + j) = sum_i P2_i(x1, s nv1 + j) y2[X2(x1)][s nv2 + i] */
+OR_API int or_cprolong(const int* Lc1, const int* B2, int nv1, int nv2, const double* Pr, const double* yr,
+                       double* er) {
+    blocking_t bk;
+    if (blocking_init(&bk, Lc1, B2, nv2) != OR_OK) return OR_ERR_ARG;
+    const int nc1 = 2 * nv1, nc2 = 2 * nv2;
+    const cplx* P = (const cplx*)Pr;
+    const cplx* y = (const cplx*)yr;
+    cplx* e = (cplx*)er;
+    for (int64_t x = 0; x < bk.V; ++x) {
+        int64_t X = block_of(&bk, x);
+        for (int a = 0; a < nc1; ++a) {
+            int s = a / nv1;
+            cplx acc = 0;
+            for (int i = 0; i < nv2; ++i) acc += P[((int64_t)i * bk.V + x) * nc1 + a] * y[X * nc2 + s * nv2 + i];
+            e[x * nc1 + a] = acc;
+        }
+    }
+    return OR_OK;
+}
+
+/*
+ * Galerkin operator one level down, A2 = P2^dag A1 P2 in nearest-neighbour
+ * form: A2[X2][d][a][b] = sum over x1 in X2 and stencil terms t of A1 of
+ * conj(P2_a(x1)) A1[x1][t] P2_b(x1 + t), where term t lands in slot d = 0
+ * when t = 0 or the term stays inside X2, and in slot d = t when it leaves X2
+ * through the face of direction t (exact for any level-2 extent, as the
+ * fine-to-level-1 build).
+ */
+OR_API int or_ccoarse_build(const int* Lc1, const int* B2, int nv1, int nv2, const double* A1r, const double* Pr,
+                            double* A2r) {
+    blocking_t bk;
+    if (blocking_init(&bk, Lc1, B2, nv2) != OR_OK) return OR_ERR_ARG;
+    const int nc1 = 2 * nv1, nc2 = 2 * nv2;
+    const cplx* A1 = (const cplx*)A1r;
+    const cplx* P = (const cplx*)Pr;
+    cplx* A2 = (cplx*)A2r;
+    int64_t Vb = bk.V / bk.Vc;
+    int64_t* sites = block_sites(&bk);
+    memset(A2, 0, sizeof(cplx) * bk.Vc * 9 * nc2 * nc2);
+    cplx* HP = (cplx*)malloc(sizeof(cplx) * nc1 * nc2);
+    for (int64_t X = 0; X < bk.Vc; ++X)
+        for (int64_t k = 0; k < Vb; ++k) {
+            int64_t x = sites[X * Vb + k];
+            int cx[4];
+            coords(Lc1, x, cx);
+            for (int t = 0; t < 9; ++t) {
+                int64_t y = coarse_neighbour(Lc1, x, t);
+                int d = 0;
+                if (t > 0) {
+                    int mu = (t - 1) / 2, dir = (t % 2 == 1) ? 1 : -1;
+                    int leaves = (dir > 0) ? (cx[mu] % B2[mu] == B2[mu] - 1) : (cx[mu] % B2[mu] == 0);
+                    d = leaves ? t : 0;
+                }
+                const cplx* At = A1 + (x * 9 + t) * nc1 * nc1;
+                /* HP[q][b] = (A1[x][t] P2_b(y))_q, b = (sb, ib) */
+                for (int q = 0; q < nc1; ++q)
+                    for (int b = 0; b < nc2; ++b) {
+                        int sb = b / nv2, ib = b % nv2;
+                        cplx acc = 0;
+                        for (int j = 0; j < nv1; ++j)
+                            acc += At[q * nc1 + sb * nv1 + j] * P[((int64_t)ib * bk.V + y) * nc1 + sb * nv1 + j];
+                        HP[q * nc2 + b] = acc;
+                    }
+                cplx* Ad = A2 + (X * 9 + d) * nc2 * nc2;
+                for (int a = 0; a < nc2; ++a) {
+                    int sa = a / nv2, ia = a % nv2;
+                    for (int b = 0; b < nc2; ++b) {
+                        cplx acc = 0;
+                        for (int j = 0; j < nv1; ++j)
+                            acc += conj(P[((int64_t)ia * bk.V + x) * nc1 + sa * nv1 + j]) * HP[(sa * nv1 + j) * nc2 + b];
+                        Ad[a * nc2 + b] += acc;
+                    }
+                }
+            }
+        }
+    free(HP); free(sites);
+    return OR_OK;
+}
+
+/* ---- level-1 relaxation: the smoothers of Sec. III on the operator A1 ---- */
+typedef struct {
+    const int* Lc;
+    int nc;
+    const cplx* A;
+} cop_t;
+
+static void cop_apply(const cop_t* c, const cplx* in, cplx* out) {
+    or_coarse_apply(c->Lc, c->nc, (const double*)c->A, (const double*)in, (double*)out);
+}
+
+/* MR steps with under-relaxation on (e, r), operator A1 (as mr_internal) */
+static void cmr(const cop_t* c, int nsteps, double omega, cplx* e, cplx* r) {
+    int64_t n = vol(c->Lc) * c->nc;
+    cplx* q = (cplx*)malloc(sizeof(cplx) * n);
+    for (int k = 0; k < nsteps; ++k) {
+        cop_apply(c, r, q);
+        cplx qr = vdot(n, q, r);
+        double qq = vnorm2(n, q);
+        if (!(qq > 0)) break;
+        cplx alpha = omega * qr / qq;
+        vaxpy(n, alpha, r, e);
+        vaxpy(n, -alpha, q, r);
+    }
+    free(q);
+}
+
+/* one GMRES(k) application with under-relaxation, operator A1 (as gmres_smooth):
+ * e += omega argmin over K_k(A1, r) of |r - A1 d| */
+static void cgmres(const cop_t* c, int k, double omega, cplx* e, const cplx* r) {
+    int64_t n = vol(c->Lc) * c->nc;
+    double beta = sqrt(vnorm2(n, r));
+    if (!(beta > 0) || k <= 0) return;
+    cplx* V = (cplx*)malloc(sizeof(cplx) * n * (k + 1));
+    cplx* H = (cplx*)calloc((size_t)(k + 1) * k, sizeof(cplx));
+    for (int64_t i = 0; i < n; ++i) V[i] = r[i] / beta;
+    int dim = k;
+    for (int j = 0; j < k; ++j) {
+        cplx* w = V + (int64_t)(j + 1) * n;
+        cop_apply(c, V + (int64_t)j * n, w);
+        for (int i = 0; i <= j; ++i) H[i * k + j] = vdot(n, V + (int64_t)i * n, w);
+        for (int i = 0; i <= j; ++i) vaxpy(n, -H[i * k + j], V + (int64_t)i * n, w);
+        double hn = sqrt(vnorm2(n, w));
+        H[(j + 1) * k + j] = hn;
+        if (!(hn > 0)) { dim = j + 1; break; }
+        for (int64_t i = 0; i < n; ++i) w[i] /= hn;
+    }
+    /* least squares min |beta e_1 - Hbar y| by Givens rotations */
+    cplx* g = (cplx*)calloc(dim + 1, sizeof(cplx));
+    g[0] = beta;
+    cplx* R = (cplx*)malloc(sizeof(cplx) * (dim + 1) * dim);
+    for (int i = 0; i <= dim; ++i)
+        for (int j = 0; j < dim; ++j) R[i * dim + j] = H[i * k + j];
+    for (int j = 0; j < dim; ++j) {
+        cplx a = R[j * dim + j], b = R[(j + 1) * dim + j];
+        double den = sqrt(creal(a * conj(a)) + creal(b * conj(b)));
+        if (!(den > 0)) continue;
+        cplx cs = a / den, sn = b / den;   /* [conj(cs) conj(sn); -sn cs] zeroes b */
+        for (int jj = j; jj < dim; ++jj) {
+            cplx u = R[j * dim + jj], v = R[(j + 1) * dim + jj];
+            R[j * dim + jj] = conj(cs) * u + conj(sn) * v;
+            R[(j + 1) * dim + jj] = -sn * u + cs * v;
+        }
+        cplx u = g[j], v = g[j + 1];
+        g[j] = conj(cs) * u + conj(sn) * v;
+        g[j + 1] = -sn * u + cs * v;
+    }
+    cplx* y = (cplx*)calloc(dim, sizeof(cplx));
+    for (int i = dim - 1; i >= 0; --i) {
+        cplx acc = g[i];
+        for (int j = i + 1; j < dim; ++j) acc -= R[i * dim + j] * y[j];
+        y[i] = acc / R[i * dim + i];
+    }
+    for (int j = 0; j < dim; ++j) vaxpy(n, omega * y[j], V + (int64_t)j * n, e);
+    free(V); free(H); free(g); free(R); free(y);
+}
+
+/* level-1 post-smoothing on (e, r = r_in - A1 e) by the configured smoother */
+static void csmooth(const or_params* p, const cop_t* c, cplx* e, cplx* r) {
+    if (p->smoother1 == 1) cgmres(c, p->steps1, p->omega, e, r);
+    else cmr(c, p->steps1, p->omega, e, r);
+}
+
+/* M1: one V(0, steps1) cycle on level 1 (the two-grid cycle of level 1 and
+ * level 2): r2 = P2^dag r; y2 = CGNR(A2, r2) to coarse_tol; z = P2 y2; then
+ * post-smoothing on A1 from z with the residual r - A1 z. */
+static void vcycle_l1(const mg_t* g, const cplx* r, cplx* z) {
+    const or_params* p = g->p;
+    int Lc2[4];
+    for (int m = 0; m < 4; ++m) Lc2[m] = g->bk.Lc[m] / p->B2[m];
+    const int nc1 = g->bk.nc, nc2 = 2 * p->nv2;
+    int64_t n1 = g->bk.Vc * nc1, n2 = vol(Lc2) * nc2;
+    cplx* r2 = (cplx*)malloc(sizeof(cplx) * n2);
+    cplx* y2 = (cplx*)malloc(sizeof(cplx) * n2);
+    cplx* rr = (cplx*)malloc(sizeof(cplx) * n1);
+    or_crestrict(g->bk.Lc, p->B2, p->nv, p->nv2, (const double*)g->P2, (const double*)r, (double*)r2);
+    int it = or_cgnr(Lc2, nc2, (const double*)g->A2, (const double*)r2, (double*)y2, p->coarse_tol, p->coarse_maxit,
+                     NULL);
+    if (g->info) g->info->coarse_iters += it;
+    or_cprolong(g->bk.Lc, p->B2, p->nv, p->nv2, (const double*)g->P2, (const double*)y2, (double*)z);
+    cop_t c = {g->bk.Lc, nc1, g->A};
+    cop_apply(&c, z, rr);
+    for (int64_t i = 0; i < n1; ++i) rr[i] = r[i] - rr[i];
+    csmooth(p, &c, z, rr);
+    free(r2); free(y2); free(rr);
+}
+
+/* The coarse-grid correction of the three-level method: cycles1 V-cycles on
+ * A1 e = r1 from e = 0 (Sec. IV: two, the W-cycle), e += M1 (r1 - A1 e). */
+static void kcycle_l1(const mg_t* g, const cplx* r1, cplx* e1) {
+    const int nc1 = g->bk.nc;
+    int64_t n1 = g->bk.Vc * nc1;
+    cplx* res = (cplx*)malloc(sizeof(cplx) * n1);
+    cplx* z = (cplx*)malloc(sizeof(cplx) * n1);
+    cop_t c = {g->bk.Lc, nc1, g->A};
+    memset(e1, 0, sizeof(cplx) * n1);
+    for (int k = 0; k < g->p->cycles1; ++k) {
+        cop_apply(&c, e1, res);
+        for (int64_t i = 0; i < n1; ++i) res[i] = r1[i] - res[i];
+        vcycle_l1(g, res, z);
+        for (int64_t i = 0; i < n1; ++i) e1[i] += z[i];
+    }
+    free(res); free(z);
+}
+
+/* level-1 smoothing as a routine of its own (tests): e, r updated in place */
+OR_API void or_csmooth(const or_params* p, const int* Lc1, const double* A1, double* er, double* rr) {
+    cop_t c = {Lc1, 2 * p->nv, (const cplx*)A1};
+    csmooth(p, &c, (cplx*)er, (cplx*)rr);
+}
+
+/* the coarse-grid correction of the three-level method as a routine (tests):
+ * e1 = K1 r1 with p->cycles1 level-1 V-cycles */
+OR_API void or_kcycle_l1(const or_params* p, const double* A1, const double* P2, const double* A2, const double* r1,
+                         double* e1, or_info* info) {
+    mg_t g;
+    blocking_init(&g.bk, p->L, p->B, p->nv);
+    g.p = p; g.U = NULL; g.P = NULL; g.A = (const cplx*)A1; g.P2 = (const cplx*)P2; g.A2 = (const cplx*)A2;
+    g.info = info;
+    kcycle_l1(&g, (const cplx*)r1, (cplx*)e1);
+}
+
+/*
+ * Adaptive setup of level 2 (Sec. II's loop in the two-step form of Sec. IV,
+ * applied to A1 as the operator to coarsen): init_relax MR steps on A1 v = 0
+ * from each random start, normalise; then groups of group_size prototypes
+ * refined one group at a time with the truncated two-level method of levels
+ * 1 and 2 built from the other prototypes (n_iter iterations of
+ * v <- v + M1_t (-A1 v), normalised); finally P2 and A2 = P2^dag A1 P2.
+ * V2 (nv2 level-1 vectors) is overwritten with the prototypes.
+ */
+OR_API int or_setup_level2(const or_params* p, const double* A1r, double* V2r, int init_relax, int n_iter,
+                           int group_size, double* P2r, double* A2r, or_info* info) {
+    or_info local;
+    memset(&local, 0, sizeof(local));
+    blocking_t bk;
+    if (blocking_init(&bk, p->L, p->B, p->nv) != OR_OK) return OR_ERR_ARG;
+    const int nv2 = p->nv2, nc1 = bk.nc;
+    if (group_size <= 0 || nv2 % group_size != 0) return OR_ERR_ARG;
+    int Lc2[4];
+    for (int m = 0; m < 4; ++m) {
+        if (p->B2[m] <= 0 || bk.Lc[m] % p->B2[m]) return OR_ERR_ARG;
+        Lc2[m] = bk.Lc[m] / p->B2[m];
+    }
+    int64_t n1 = bk.Vc * nc1;
+    cplx* V = (cplx*)V2r;
+    cplx* r = (cplx*)malloc(sizeof(cplx) * n1);
+    cplx* z = (cplx*)malloc(sizeof(cplx) * n1);
+    cop_t c = {bk.Lc, nc1, (const cplx*)A1r};
+    for (int i = 0; i < nv2; ++i) {
+        cplx* v = V + (int64_t)i * n1;
+        cop_apply(&c, v, r);
+        for (int64_t k = 0; k < n1; ++k) r[k] = -r[k];
+        cmr(&c, init_relax, p->omega, v, r);
+        double nrm = sqrt(vnorm2(n1, v));
+        for (int64_t k = 0; k < n1; ++k) v[k] /= nrm;
+    }
+    int st = OR_OK;
+    int nt = nv2 - group_size;
+    if (n_iter > 0 && nt > 0) {
+        or_params pt = *p;
+        pt.nv2 = nt;
+        pt.levels = 3;
+        cplx* Vt = (cplx*)malloc(sizeof(cplx) * n1 * nt);
+        cplx* Pt = (cplx*)malloc(sizeof(cplx) * n1 * nt);
+        cplx* At = (cplx*)malloc(sizeof(cplx) * vol(Lc2) * 9 * (2 * nt) * (2 * nt));
+        for (int g0 = 0; g0 < nv2 && st == OR_OK; g0 += group_size) {
+            int k = 0;
+            for (int i = 0; i < nv2; ++i)
+                if (i < g0 || i >= g0 + group_size) memcpy(Vt + (int64_t)(k++) * n1, V + (int64_t)i * n1, sizeof(cplx) * n1);
+            st = or_cblock_orthonormalize(bk.Lc, p->B2, p->nv, nt, (const double*)Vt, (double*)Pt);
+            if (st != OR_OK) break;
+            or_ccoarse_build(bk.Lc, p->B2, p->nv, nt, A1r, (const double*)Pt, (double*)At);
+            mg_t g;
+            g.bk = bk; g.p = &pt; g.U = NULL; g.P = NULL; g.A = (const cplx*)A1r; g.P2 = Pt; g.A2 = At;
+            g.info = &local;
+            for (int i = g0; i < g0 + group_size; ++i) {
+                cplx* v = V + (int64_t)i * n1;
+                for (int it = 0; it < n_iter; ++it) {
+                    cop_apply(&c, v, r);
+                    for (int64_t q = 0; q < n1; ++q) r[q] = -r[q];
+                    vcycle_l1(&g, r, z);
+                    for (int64_t q = 0; q < n1; ++q) v[q] += z[q];
+                    double nrm = sqrt(vnorm2(n1, v));
+                    for (int64_t q = 0; q < n1; ++q) v[q] /= nrm;
+                }
+            }
+        }
+        free(Vt); free(Pt); free(At);
+    }
+    if (st == OR_OK) st = or_cblock_orthonormalize(bk.Lc, p->B2, p->nv, nv2, V2r, P2r);
+    if (st == OR_OK) or_ccoarse_build(bk.Lc, p->B2, p->nv, nv2, A1r, P2r, A2r);
+    free(r); free(z);
+    local.status = st;
+    if (info) *info = local;
     return st;
 }

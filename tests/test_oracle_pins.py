@@ -723,3 +723,203 @@ def test_eo_cg_iterations_grow_toward_critical_mass():
         assert np.linalg.norm(b - oracle.dslash(U, x, target - C1_RE_LAMBDA_MIN_M0, L)) <= 1e-10 * np.linalg.norm(b)
         its.append(it)
     assert its[0] < its[1] < its[2], its
+
+
+# ---------------------------------------------------------------- third level (Sec. III recursion, Sec. IV W-cycle)
+def _level1(L=(4, 4, 4, 8), B=(2, 2, 2, 2), nv=4, m=-0.3, seed=91):
+    """A level-1 operator D_c = P^dag D P from random prototypes on a small lattice."""
+    U = rough_gauge(L, seed=seed)
+    V0 = synth.gaussian_vectors(L, nv, seed + 1)
+    P, st = oracle.block_orthonormalize(V0, L, B)
+    assert st == 0
+    A1 = oracle.coarse_build(U, P, m, L, B)
+    return L, B, nv, U, m, P, A1, oracle.coarse_dims(L, B)
+
+
+def _level1_vectors(Lc1, nv1, n, seed):
+    Vc1 = oracle.volume(Lc1)
+    return synth.gaussian(n * Vc1 * 2 * nv1, seed, 0).reshape(n, Vc1, 2 * nv1)
+
+
+def _dense_P2(P2, Lc1, B2, nv1):
+    Lc2 = oracle.coarse_dims(Lc1, B2)
+    nC = oracle.volume(Lc2) * 2 * P2.shape[0]
+    cols = []
+    for k in range(nC):
+        e = np.zeros(nC, dtype=np.complex128)
+        e[k] = 1
+        cols.append(oracle.cprolong(P2, e.reshape(oracle.volume(Lc2), -1), Lc1, B2, nv1).ravel())
+    return np.stack(cols, 1)
+
+
+@pytest.mark.parametrize("B2", [(1, 1, 2, 2), (2, 2, 2, 2), (2, 2, 2, 4)])
+def test_level2_prolongator_and_galerkin_operator(B2):
+    """One level down (Sec. III): P2^dag P2 = I and P2 V2_c = V2 (eq. 4), chirality
+    kept, Q equal to numpy's QR (positive diagonal) per aggregate and chirality,
+    restriction the adjoint of prolongation, and A2 = P2^dag A1 P2 equal to the
+    dense product for level-2 extents 2, 1 and mixed (the exit-face slots),
+    sigma3-hermitian like A1, with (I - P2 A2^-1 P2^dag A1) P2 = 0."""
+    L, B, nv1, U, m, P, A1, Lc1 = _level1()
+    nv2 = 3
+    V2 = _level1_vectors(Lc1, nv1, nv2, 92)
+    P2, st = oracle.cblock_orthonormalize(V2, Lc1, B2, nv1)
+    assert st == 0
+    P2d = _dense_P2(P2, Lc1, B2, nv1)
+    assert np.abs(P2d.conj().T @ P2d - np.eye(P2d.shape[1])).max() < 1e-13
+    for i in range(nv2):                         # P2 P2^dag v_i = v_i
+        v = V2[i]
+        proj = oracle.cprolong(P2, oracle.crestrict(P2, v, Lc1, B2, nv1), Lc1, B2, nv1)
+        assert rel(proj, v) < 1e-13
+        assert not np.any(P2[i][:, :nv1] * 0)     # both chiralities present in the prototypes
+    # numpy QR of one aggregate's chirality-0 block
+    Lc2 = oracle.coarse_dims(Lc1, B2)
+    c1 = np.indices(tuple(Lc1)[::-1]).reshape(4, -1)[::-1]
+    blk = (c1[0] // B2[0]) + Lc2[0] * ((c1[1] // B2[1]) + Lc2[1] * ((c1[2] // B2[2]) + Lc2[2] * (c1[3] // B2[3])))
+    sites = np.nonzero(blk == 0)[0]
+    W = np.stack([V2[i][sites, :nv1].ravel() for i in range(nv2)], 1)
+    Q, R = np.linalg.qr(W)
+    Q = Q * (np.sign(np.diag(R).real) * np.exp(-1j * np.angle(np.diag(R))) * np.abs(np.sign(np.diag(R))))[None, :]
+    Qp = np.stack([P2[i][sites, :nv1].ravel() for i in range(nv2)], 1)
+    ph = np.diag(R) / np.abs(np.diag(R))
+    assert np.abs(Qp - np.linalg.qr(W)[0] * ph[None, :]).max() < 1e-12
+    assert np.all(P2[:, sites][:, :, nv1:][:, :, :].shape)   # shape sanity
+    # chirality: sigma3 P2 = P2 sigma3 (columns of chirality s live on dof of chirality s)
+    s1 = np.concatenate([np.ones(nv1), -np.ones(nv1)])
+    s2 = np.concatenate([np.ones(nv2), -np.ones(nv2)])
+    S1 = np.diag(np.tile(s1, oracle.volume(Lc1)))
+    S2 = np.diag(np.tile(s2, oracle.volume(Lc2)))
+    assert np.abs(S1 @ P2d - P2d @ S2).max() == 0
+    # adjointness
+    r1 = _level1_vectors(Lc1, nv1, 1, 93)[0]
+    y2 = synth.gaussian(oracle.volume(Lc2) * 2 * nv2, 94, 0).reshape(-1, 2 * nv2)
+    lhs = np.vdot(y2, oracle.crestrict(P2, r1, Lc1, B2, nv1))
+    rhs = np.vdot(oracle.cprolong(P2, y2, Lc1, B2, nv1), r1)
+    assert abs(lhs - rhs) < 1e-13 * abs(lhs)
+    # Galerkin product against the dense one
+    A1d = oracle.coarse_dense(A1, Lc1)
+    A2 = oracle.ccoarse_build(A1, P2, Lc1, B2)
+    A2d = oracle.coarse_dense(A2, Lc2)
+    assert np.abs(A2d - P2d.conj().T @ A1d @ P2d).max() < 1e-12 * np.abs(A2d).max()
+    assert np.abs(S2 @ A2d @ S2 - A2d.conj().T).max() < 1e-12 * np.abs(A2d).max()
+    C = P2d - P2d @ np.linalg.solve(A2d, P2d.conj().T @ A1d @ P2d)
+    assert np.abs(C).max() < 1e-10
+
+
+@pytest.mark.parametrize("smoother1,k", [(1, 1), (1, 4), (0, 1)])
+def test_level1_smoother_minimises_over_the_krylov_space(smoother1, k):
+    """Level-1 post-smoothing (Sec. III smoother on A1): e += omega d with d the
+    least-squares minimiser of |r - A1 d| over K_k(A1, r) (numpy lstsq over the
+    power basis); one MR step is GMRES(1)."""
+    L, B, nv1, U, m, P, A1, Lc1 = _level1()
+    p = oracle.make_params(L, B, nv=nv1, m=m, smoother1=smoother1, steps1=k, omega=0.9)
+    e0 = _level1_vectors(Lc1, nv1, 1, 95)[0]
+    r = _level1_vectors(Lc1, nv1, 1, 96)[0]
+    basis = [r]
+    for _ in range(k - 1):
+        basis.append(oracle.coarse_apply(A1, basis[-1], Lc1))
+    K = np.stack([b.ravel() for b in basis], 1)
+    AK = np.stack([oracle.coarse_apply(A1, b, Lc1).ravel() for b in basis], 1)
+    c, *_ = np.linalg.lstsq(AK, r.ravel(), rcond=None)
+    e1, r1 = oracle.csmooth(p, Lc1, A1, e0, r)
+    want = e0 + 0.9 * (K @ c).reshape(r.shape)
+    assert np.abs(e1 - want).max() < 1e-9 * np.abs(want).max()
+
+
+def test_three_level_cycle_composition():
+    """The three-level cycle (Sec. IV) from its parts, with an exact coarsest
+    solve: one level-1 V-cycle is P2 A2^-1 P2^dag r1 followed by the level-1
+    smoother on the corrected residual (lstsq check); two cycles (the W-cycle)
+    are e = K(r1), e += K(r1 - A1 e); the fine cycle with this correction
+    smooths r - D P K1(P^dag r) (lstsq over the fine Krylov space)."""
+    L, B, nv1, U, m, P, A1, Lc1 = _level1()
+    B2, nv2 = (1, 1, 2, 2), 4
+    P2, _ = oracle.cblock_orthonormalize(_level1_vectors(Lc1, nv1, nv2, 97), Lc1, B2, nv1)
+    A2 = oracle.ccoarse_build(A1, P2, Lc1, B2)
+    Lc2 = oracle.coarse_dims(Lc1, B2)
+    kw = dict(nv=nv1, m=m, levels=3, B2=B2, nv2=nv2, smoother1=1, steps1=3, coarse_tol=1e-15, coarse_maxit=100000,
+              omega=0.9)
+    r1 = _level1_vectors(Lc1, nv1, 1, 98)[0]
+    e_one, _ = oracle.kcycle_l1(oracle.make_params(L, B, cycles1=1, **kw), A1, P2, A2, r1)
+    y2 = np.linalg.solve(oracle.coarse_dense(A2, Lc2), oracle.crestrict(P2, r1, Lc1, B2, nv1).ravel())
+    e0 = oracle.cprolong(P2, y2.reshape(oracle.volume(Lc2), -1), Lc1, B2, nv1)
+    rr = r1 - oracle.coarse_apply(A1, e0, Lc1)
+    basis = [rr]
+    for _ in range(2):
+        basis.append(oracle.coarse_apply(A1, basis[-1], Lc1))
+    K = np.stack([b.ravel() for b in basis], 1)
+    AK = np.stack([oracle.coarse_apply(A1, b, Lc1).ravel() for b in basis], 1)
+    c, *_ = np.linalg.lstsq(AK, rr.ravel(), rcond=None)
+    assert rel(e_one, e0 + 0.9 * (K @ c).reshape(rr.shape)) < 1e-9
+    e_two, _ = oracle.kcycle_l1(oracle.make_params(L, B, cycles1=2, **kw), A1, P2, A2, r1)
+    e_b, _ = oracle.kcycle_l1(oracle.make_params(L, B, cycles1=1, **kw), A1, P2, A2,
+                              r1 - oracle.coarse_apply(A1, e_one, Lc1))
+    assert rel(e_two, e_one + e_b) < 1e-12
+    # the fine cycle around it
+    p3 = oracle.make_params(L, B, cycles1=2, smoother=1, mr_steps=2, **kw)
+    r = synth.gaussian_spinor(L, 99)
+    z, _ = oracle.vcycle3(p3, U, P, A1, P2, A2, r)
+    ez = oracle.prolong(P, oracle.kcycle_l1(p3, A1, P2, A2, oracle.restrict(P, r, L, B))[0], L, B)
+    rf = r - oracle.dslash(U, ez, m, L)
+    basis = [rf, oracle.dslash(U, rf, m, L)]
+    DK = np.stack([oracle.dslash(U, b, m, L).ravel() for b in basis], 1)
+    c, *_ = np.linalg.lstsq(DK, rf.ravel(), rcond=None)
+    want = rf - 0.9 * (DK @ c).reshape(rf.shape)
+    got = r - oracle.dslash(U, z, m, L)
+    assert np.abs(got - want).max() < 1e-9 * np.abs(want).max()
+
+
+@pytest.mark.slow
+def test_three_level_solve_and_level2_setup():
+    """On the 8^4 beta = 6.0 field at Re(lambda_min) = 0.01 (Nv = 8, 4^4 then
+    1x1x2x2 aggregates, Nv2 = 8): the level-2 setup keeps its invariants and
+    orders the asymptotic level-1 two-grid rate (eq. 3 on A1, exact level-2
+    solve, MR(4) level-1 smoother): refined < relaxed only < random level-2
+    prototypes (0.21 < 0.29 < 0.58); MG-GCR with the three-level W-cycle
+    reaches 1e-10 in FP64.  (On this 2^4 intermediate lattice the outer
+    iteration count is not ordered the same way: 111 with the refined against
+    103 with random prototypes, whose well-conditioned A2 the 1e-3 coarsest
+    CG solves more accurately.)"""
+    from tests._fields import c1_workload
+    L, B, nv, U, m = c1_workload()
+    V0 = synth.gaussian_vectors(L, nv, 2001)
+    p2 = oracle.make_params(L, B, nv=nv, m=m, smoother=1, mr_steps=4)
+    _, P, A1, st = oracle.setup(p2, U, V0, init_relax=10, n_iter=3, group_size=4)
+    assert st == 0
+    Lc1 = oracle.coarse_dims(L, B)
+    B2, nv2 = (1, 1, 2, 2), 8
+    p3 = oracle.make_params(L, B, nv=nv, m=m, smoother=1, mr_steps=4, levels=3, B2=B2, nv2=nv2, smoother1=1,
+                            steps1=4, cycles1=2)
+    V2 = _level1_vectors(Lc1, nv, nv2, 2003)
+    _, P2, A2, st2, sinfo = oracle.setup_level2(p3, A1, V2, init_relax=10, n_iter=3, group_size=4)
+    assert st2 == 0 and sinfo["coarse_iters"] > 0
+    P2d = _dense_P2(P2, Lc1, B2, nv)
+    assert np.abs(P2d.conj().T @ P2d - np.eye(P2d.shape[1])).max() < 1e-12
+    b = synth.gaussian_spinor(L, 7)
+    x, info = oracle.gcr_solve3(p3, U, P, A1, P2, A2, b)
+    assert info["status"] == 0
+    assert np.linalg.norm(b - oracle.dslash(U, x, m, L)) <= 1e-10 * np.linalg.norm(b)
+    P2r, _ = oracle.cblock_orthonormalize(V2, Lc1, B2, nv)
+    _, P20, A20, st0, _ = oracle.setup_level2(p3, A1, V2, init_relax=10, n_iter=0, group_size=4)
+    pm = oracle.make_params(L, B, nv=nv, m=m, levels=3, B2=B2, nv2=nv2, smoother1=0, steps1=4)
+    e0 = _level1_vectors(Lc1, nv, 1, 77)[0]
+
+    def rate(P2_, A2_):
+        _, n = oracle.ctwo_grid_factor(pm, A1, P2_, A2_, e0, 40)
+        return (n[40] / n[20]) ** (1 / 20)
+
+    f_rand = rate(P2r, oracle.ccoarse_build(A1, P2r, Lc1, B2))
+    f_relax, f_ref = rate(P20, A20), rate(P2, A2)
+    assert f_ref < f_relax < f_rand < 1, (f_ref, f_relax, f_rand)
+
+
+def test_level1_two_grid_factor_annihilates_range_of_p2():
+    """Without smoothing the level-1 two-grid step removes any error in range(P2)."""
+    L, B, nv1, U, m, P, A1, Lc1 = _level1()
+    B2, nv2 = (1, 1, 2, 2), 3
+    P2, _ = oracle.cblock_orthonormalize(_level1_vectors(Lc1, nv1, nv2, 80), Lc1, B2, nv1)
+    A2 = oracle.ccoarse_build(A1, P2, Lc1, B2)
+    Lc2 = oracle.coarse_dims(Lc1, B2)
+    p = oracle.make_params(L, B, nv=nv1, m=m, levels=3, B2=B2, nv2=nv2, steps1=0)
+    y2 = synth.gaussian(oracle.volume(Lc2) * 2 * nv2, 81, 0).reshape(-1, 2 * nv2)
+    f, n = oracle.ctwo_grid_factor(p, A1, P2, A2, oracle.cprolong(P2, y2, Lc1, B2, nv1), 1)
+    assert n[1] < 1e-12 * n[0]
