@@ -97,6 +97,14 @@ typedef struct {
                               iteration, the vectors other SMs read carrying epoch tags instead
                               of barriers; 1 textbook CGLS, two grid-wide exchanges per
                               iteration.  Same iterates in exact arithmetic */
+    /* third level (Sec. IV: 3-level V(0,4) cycle with GMRES(4) post-relaxation on
+       each level and a W-cycle); levels = 2 ignores the rest */
+    int levels;            /* 2 (default) or 3 */
+    int block2[4];         /* level-2 aggregates on the level-1 lattice (default 2^4; Sec. IV's
+                              footnote: 2^3 x 4 on 24^3 x 64) */
+    int nvec2;             /* N_v of level 2 (default 32), 2 nvec2 dof per level-2 site */
+    int smoother_steps1;   /* level-1 post-smoothing: one GMRES(smoother_steps1) scaled by omega */
+    int cycles1;           /* level-1 V-cycles per fine-grid correction (Sec. IV: 2, the W-cycle) */
 } mg_params;
 
 /* Outcome of one solve (Sec. IV reports outer iterations and fine matvecs). */
@@ -118,7 +126,8 @@ typedef struct {
  * block 4^4, nvec 8, relax 10, iters 3, group 4,
  * smoother 4, omega 0.9, restart 16, tol 1e-10, coarse_tol 1e-3,
  * max_outer 1000, max_coarse 5000, delta 0, FP64, coarse_check 16, coarse_kernel 0,
- * smoother 0 (MR), smoother_fp16 0, coarse_form 0. */
+ * smoother 0 (MR), smoother_fp16 0, coarse_form 0, levels 2, block2 2^4,
+ * nvec2 32, smoother_steps1 4, cycles1 2. */
 int mg_default_params(mg_params* p);
 
 /* Create a context for the Wilson-Dirac system D(U) psi = b (eqs. 1-2) on an
@@ -177,6 +186,40 @@ int mg_set_null_vectors(mg_ctx* ctx, const double* V, int nv);
  * fine vectors: column (X, s, i) is vector i on the sites of X and spins of
  * s, chirality kept as in Sec. III). */
 int mg_get_prolongator(mg_ctx* ctx, double* P);
+
+/* ---- the third level (levels = 3) -----------------------------------------
+ * Level-1 vectors are coarse vectors (boundary coarse-vector layout [X1][2 Nv]).
+ * Sec. III recurses the coarsening with the chiral components kept separate:
+ * level-2 aggregates are block2 level-1 sites, level-2 dof (s, i) of chirality s.
+ * Level-2 vectors [X2][2 nvec2], X2 lexicographic over the level-2 lattice
+ * (level-1 extents / block2); the level-2 operator [X2][d 9][a][b] as D_c. */
+
+/* Adaptive setup of level 2 (the two-step setup of Sec. IV applied to D_c:
+ * setup_init_relax relaxation steps -- GMRES(1) applications, each equal to
+ * one MR step -- on D_c v = 0 from each start, then groups of setup_group
+ * prototypes refined by setup_iters iterations of the truncated two-level
+ * method of levels 1 and 2), then P2 = block-orthonormalised prototypes and
+ * A2 = P2^dag D_c P2.  V2: host, nvec2 random level-1 vectors.  Needs the
+ * level-1 setup (mg_setup or mg_set_null_vectors) first; runs at the current
+ * mass.  MG_ERR_NUMERIC on rank-deficient level-2 aggregates. */
+int mg_setup_level2(mg_ctx* ctx, const double* V2);
+
+/* Use the given level-1 vectors (host, nvec2) as level-2 prototypes as they
+ * are: block-orthonormalise them and build A2 = P2^dag D_c P2 (Sec. III). */
+int mg_set_level2_vectors(mg_ctx* ctx, const double* V2);
+
+/* Read back the level-2 prolongator as nvec2 level-1 vectors (column (X2, s, i)
+ * is vector i on the level-1 sites of X2 and dof of chirality s) and the
+ * level-2 operator in FP64 (host). */
+int mg_get_level2_prolongator(mg_ctx* ctx, double* P2);
+int mg_get_level2_op(mg_ctx* ctx, double* A2);
+
+/* e1 = the three-level method's coarse-grid correction of a level-1 residual
+ * r1 (Sec. IV): cycles1 level-1 V-cycles on D_c e1 = r1 from e1 = 0, each
+ * r2 = P2^dag r, level-2 CGNR to coarse_tol, e = P2 y2, one GMRES(smoother_
+ * steps1) post-smoothing on D_c.  r1, e1: host level-1 vectors; prec as the
+ * solve's inner precision. */
+int mg_kcycle(mg_ctx* ctx, const double* r1, double* e1, int prec);
 
 /* Read back the current prototypes V (the near-null vectors of Sec. II;
  * host, Nv fine vectors). */

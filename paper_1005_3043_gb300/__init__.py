@@ -42,7 +42,8 @@ class MgParams(ctypes.Structure):
                 ("coarse_tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("max_coarse", ctypes.c_int),
                 ("delta", ctypes.c_double), ("prec_inner", ctypes.c_int), ("coarse_check", ctypes.c_int),
                 ("coarse_kernel", ctypes.c_int), ("smoother", ctypes.c_int), ("smoother_fp16", ctypes.c_int),
-                ("coarse_form", ctypes.c_int)]
+                ("coarse_form", ctypes.c_int), ("levels", ctypes.c_int), ("block2", ctypes.c_int * 4),
+                ("nvec2", ctypes.c_int), ("smoother_steps1", ctypes.c_int), ("cycles1", ctypes.c_int)]
 
 
 class MgSolveInfo(ctypes.Structure):
@@ -77,6 +78,11 @@ _SIGS = {
     "mg_set_null_vectors": ([_P, _P, _I], _I),
     "mg_get_prolongator": ([_P, _P], _I),
     "mg_get_null_vectors": ([_P, _P], _I),
+    "mg_setup_level2": ([_P, _P], _I),
+    "mg_set_level2_vectors": ([_P, _P], _I),
+    "mg_get_level2_prolongator": ([_P, _P], _I),
+    "mg_get_level2_op": ([_P, _P], _I),
+    "mg_kcycle": ([_P, _P, _P, _I], _I),
     "mg_get_coarse_op": ([_P, _P], _I),
     "mg_solve": ([_P, _P, _P, _P], _I),
     "mg_solve_device": ([_P, _P, _P, _P], _I),
@@ -224,6 +230,33 @@ def mg_get_null_vectors(ctx, nv: int, V: int) -> np.ndarray:
     out = np.empty((nv, V, 4, 3), dtype=np.complex128)
     _check(load().mg_get_null_vectors(ctx, _ptr(out)), ctx)
     return out
+
+
+def mg_setup_level2(ctx, V2) -> None:
+    _check(load().mg_setup_level2(ctx, _ptr(_host(V2))), ctx)
+
+
+def mg_set_level2_vectors(ctx, V2) -> None:
+    _check(load().mg_set_level2_vectors(ctx, _ptr(_host(V2))), ctx)
+
+
+def mg_get_level2_prolongator(ctx, nv2: int, Vc1: int, nc1: int) -> np.ndarray:
+    out = np.empty((nv2, Vc1, nc1), dtype=np.complex128)
+    _check(load().mg_get_level2_prolongator(ctx, _ptr(out)), ctx)
+    return out
+
+
+def mg_get_level2_op(ctx, Vc2: int, nc2: int) -> np.ndarray:
+    out = np.empty((Vc2, 9, nc2, nc2), dtype=np.complex128)
+    _check(load().mg_get_level2_op(ctx, _ptr(out)), ctx)
+    return out
+
+
+def mg_kcycle(ctx, r1, prec: int = MG_FP64) -> np.ndarray:
+    r1 = _host(r1)
+    e1 = np.empty_like(r1)
+    _check(load().mg_kcycle(ctx, _ptr(r1), _ptr(e1), int(prec)), ctx)
+    return e1
 
 
 def mg_get_coarse_op(ctx, Vc: int, nc: int) -> np.ndarray:
@@ -454,6 +487,25 @@ class WilsonMG:
 
     def set_null_vectors(self, V):
         mg_set_null_vectors(self.ctx, V)
+
+    @property
+    def Vc2(self):
+        return int(np.prod([d // b // c for d, b, c in zip(self.dims, self.params.block, self.params.block2)]))
+
+    def setup_level2(self, V2):
+        mg_setup_level2(self.ctx, V2)
+
+    def set_level2_vectors(self, V2):
+        mg_set_level2_vectors(self.ctx, V2)
+
+    def level2_prolongator(self):
+        return mg_get_level2_prolongator(self.ctx, self.params.nvec2, self.Vc, self.nc)
+
+    def level2_op(self):
+        return mg_get_level2_op(self.ctx, self.Vc2, 2 * self.params.nvec2)
+
+    def kcycle(self, r1, prec=MG_FP64):
+        return mg_kcycle(self.ctx, r1, prec)
 
     def prolongator(self):
         return mg_get_prolongator(self.ctx, self.nv, self.V)

@@ -271,9 +271,13 @@ cudaError_t coarse_apply_tc_prepare(int nc, int npad) {
 cudaError_t coarse_apply_tc(const TcApplyArgs& args, cudaStream_t st) {
     TcApplyArgs a = args;
     if (a.nw <= 0) a.nw = a.npad;
+    TmemOrder order(st);
+    if (order.error() != cudaSuccess) return order.error();
     note_launch();
     k_coarse_apply_tc<<<dim3(a.g.Vc, a.npad / a.nw), kTcThreads, tc_launch_smem(a.nc, a.nw), st>>>(a);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return order.launched();
 }
 
 // Chunk width for (nc, npad): every candidate (multiples of 16 dividing npad)

@@ -79,6 +79,18 @@ struct EoWork {
     int inner_bytes = 0;      // 8: FP32 inner vectors, 16: FP64
 };
 
+// Work vectors of the three-level method on level 1 (sized for the level-1
+// lattice) and of its level-2 coarse solve.
+template <typename T> struct L1Work {
+    v2<T>*z = nullptr, *res = nullptr, *zero = nullptr, *sv = nullptr, *sz = nullptr;
+    v2<T>* gm = nullptr;     // level-1 GMRES basis, gm_k + 1 vectors
+    int gm_k = 0;
+    v2<T>*crc = nullptr, *cy = nullptr;                      // level-2 right-hand side and solution
+    v2<T>*cr = nullptr, *cr1 = nullptr, *cs = nullptr, *cp = nullptr, *cp1 = nullptr, *cq = nullptr;
+    unsigned long long* ctag = nullptr;
+    bool ready = false;
+};
+
 template <typename T> struct Work {
     v2<T>* r = nullptr;    // GCR residual (T == double: aliases the FP64 residual)
     v2<T>* Z = nullptr;    // K_restart preconditioned directions
@@ -133,6 +145,14 @@ struct mg_ctx {
     CoarseLevel full, trunc;
     BatchWork bw;
     EoWork eo;
+    // third level (levels == 3)
+    Geom g2{};                       // the level-1 lattice cut into level-2 aggregates
+    int* cnbr2 = nullptr;            // level-2 neighbour table
+    CoarseLevel full2, trunc2;       // P64/P32: level-2 prolongator panels; A64/A32: A2
+    double2* protos2 = nullptr;      // level-2 prototypes [nv2][Vc1][2 nv1] FP64
+    double2* protos2_t = nullptr;
+    L1Work<float> l1f;
+    L1Work<double> l1d;
     Work<float> wf;
     Work<double> wd;
     Reduce R{};
@@ -353,14 +373,14 @@ int build_level(mg_ctx* ctx, CoarseLevel& L, const double2* V, int nv) {
 }
 
 // ---------------------------------------------------------------- coarse solve
-int ensure_a16(mg_ctx* ctx, CoarseLevel& L) {
+int ensure_a16(mg_ctx* ctx, CoarseLevel& L, int Vc) {
     if (L.a16_valid) return MG_OK;
     if (L.nc % 4 != 0) return fail(ctx, MG_ERR_INVALID_ARG, "FP16 coarse storage needs an even nvec");
     if (!L.A16) {
-        TRY(dalloc(ctx, &L.A16, sizeof(__half2) * (size_t)ctx->g.Vc * 9 * (2 * L.cap) * (2 * L.cap)));
-        TRY(dalloc(ctx, &L.s16, sizeof(float) * (size_t)ctx->g.Vc * 9));
+        TRY(dalloc(ctx, &L.A16, sizeof(__half2) * (size_t)Vc * 9 * (2 * L.cap) * (2 * L.cap)));
+        TRY(dalloc(ctx, &L.s16, sizeof(float) * (size_t)Vc * 9));
     }
-    coarse_pack16(L.A16, L.s16, L.A64, L.nc, ctx->g.Vc, ctx->st);
+    coarse_pack16(L.A16, L.s16, L.A64, L.nc, Vc, ctx->st);
     CKL();
     L.a16_valid = true;
     return MG_OK;
@@ -368,22 +388,22 @@ int ensure_a16(mg_ctx* ctx, CoarseLevel& L) {
 
 // The operator in the unit layout of the on-chip CGLS kernel; false when no
 // shape fits this device (the register-streaming kernel is used instead).
-int ensure_units(mg_ctx* ctx, CoarseLevel& L, bool h16, int mode, bool* ok) {
+int ensure_units(mg_ctx* ctx, CoarseLevel& L, int Vc, bool h16, int mode, bool* ok) {
     *ok = false;
     if (L.au_valid && L.au_h16 == h16 && L.au_mode == mode) {
         *ok = true;
         return MG_OK;
     }
     CglsShape sh{};
-    if (!cgls_shape(L.nc, ctx->g.Vc, h16, mode, &sh)) return MG_OK;
-    const size_t bytes = (size_t)ctx->g.Vc * 9 * L.nc * L.nc * (h16 ? 4 : 8);
+    if (!cgls_shape(L.nc, Vc, h16, mode, &sh)) return MG_OK;
+    const size_t bytes = (size_t)Vc * 9 * L.nc * L.nc * (h16 ? 4 : 8);
     if (L.au_bytes < bytes) {
         if (L.Au) { dfree(ctx, L.Au); L.Au = nullptr; L.au_bytes = 0; }
         TRY(dalloc(ctx, &L.Au, bytes));
         L.au_bytes = bytes;
     }
-    if (h16 && !L.su) TRY(dalloc(ctx, &L.su, sizeof(float) * (size_t)ctx->g.Vc * 9));
-    coarse_pack_units(L.Au, h16 ? L.su : nullptr, L.A64, L.nc, sh.ru, ctx->g.Vc, h16, ctx->st);
+    if (h16 && !L.su) TRY(dalloc(ctx, &L.su, sizeof(float) * (size_t)Vc * 9));
+    coarse_pack_units(L.Au, h16 ? L.su : nullptr, L.A64, L.nc, sh.ru, Vc, h16, ctx->st);
     CKL();
     L.au_shape = sh;
     L.au_h16 = h16;
@@ -408,36 +428,51 @@ CgnrArgs<T> cgnr_args(const CoarseLevel& L, const Geom& g, const v2<T>* rc, v2<T
 // CGNR on D_c (one persistent cooperative launch).  With iters != nullptr the
 // call waits for the result; otherwise the count is only added to
 // scal[S_CG_TOTAL] and nothing synchronises.
-template <typename T>
-int coarse_solve(mg_ctx* ctx, const CoarseLevel& L, const v2<T>* rc, v2<T>* y, double tol, int maxit, int* iters) {
+int clear_epoch_tags(mg_ctx* ctx);
+
+// The coarsest-grid solve of one level: its geometry, neighbour table and CG
+// vectors (level 1 -- the two-level method -- or level 2 of the three-level one).
+template <typename T> struct CgSys {
+    Geom g;            // coarse lattice of the operator (Vc, Lc, xstride)
+    const int* nbr;    // its neighbour table [Vc][9]
+    v2<T>*cr, *cr1, *cs, *cp, *cp1, *cq;
+    unsigned long long* ctag;   // epoch-tagged vectors of the on-chip solver (T == float)
+};
+template <typename T> CgSys<T> level1_sys(mg_ctx* ctx) {
     Work<T>& w = work<T>(ctx);
-    CgnrArgs<T> a = cgnr_args<T>(L, ctx->g, rc, y, w.cr, w.cr1, w.cs, w.cp, w.cp1, w.cq, tol, maxit, ctx->R.partials,
-                                 ctx->bar, ctx->R.scal);
-    a.nbr = ctx->cnbr;
+    return CgSys<T>{ctx->g, ctx->cnbr, w.cr, w.cr1, w.cs, w.cp, w.cp1, w.cq, w.ctag};
+}
+
+template <typename T>
+int coarse_solve(mg_ctx* ctx, const CoarseLevel& L, const CgSys<T>& sys, const v2<T>* rc, v2<T>* y, double tol,
+                 int maxit, int* iters) {
+    CgnrArgs<T> a = cgnr_args<T>(L, sys.g, rc, y, sys.cr, sys.cr1, sys.cs, sys.cp, sys.cp1, sys.cq, tol, maxit,
+                                 ctx->R.partials, ctx->bar, ctx->R.scal);
+    a.nbr = sys.nbr;
     bool onchip = false;
     if (std::is_same<T, float>::value && ctx->prm.coarse_kernel != 1) {
         CoarseLevel& Lm = const_cast<CoarseLevel&>(L);
         const int mode = ctx->prm.coarse_kernel == 2 ? CGLS_STREAM : ctx->prm.coarse_kernel == 3 ? CGLS_SMEM : CGLS_AUTO;
-        TRY(ensure_units(ctx, Lm, ctx->coarse16, mode, &onchip));
+        TRY(ensure_units(ctx, Lm, sys.g.Vc, ctx->coarse16, mode, &onchip));
     }
     if (onchip) {
         CglsArgs c{};
-        c.Au = L.Au; c.su = ctx->coarse16 ? L.su : nullptr; c.nbr = ctx->cnbr;
+        c.Au = L.Au; c.su = ctx->coarse16 ? L.su : nullptr; c.nbr = sys.nbr;
         c.rc = (const float2*)a.rc; c.y = (float2*)a.y; c.r = (float2*)a.r; c.r1 = (float2*)a.r1;
         c.s = (float2*)a.s; c.p = (float2*)a.p; c.p1 = (float2*)a.p1; c.q = (float2*)a.q;
-        c.nc = L.nc; c.g = ctx->g; c.tol2 = (float)(tol * tol); c.maxit = maxit;
+        c.nc = L.nc; c.g = sys.g; c.tol2 = (float)(tol * tol); c.maxit = maxit;
         c.scal = ctx->R.scal; c.err = (int*)(ctx->bar + 2);
         c.sh = L.au_shape;
         const unsigned long long reserve = 2ull * (unsigned long long)(maxit > 0 ? maxit : 0) + 4ull;
         if ((unsigned long long)ctx->xch_epoch + reserve >= 0xFFFFFFFFull) {   // 32-bit epochs would wrap
             CK(cudaMemsetAsync(ctx->xch, 0, sizeof(unsigned long long) * kXchWords, ctx->st));
-            CK(cudaMemsetAsync(w.ctag, 0, sizeof(unsigned long long) * 4 * (size_t)ctx->g.Vc * L.nc, ctx->st));
+            TRY(clear_epoch_tags(ctx));
             ctx->xch_epoch = 1;
         }
         c.xch = ctx->xch;
         c.epoch0 = ctx->xch_epoch;
         c.form = ctx->prm.coarse_form == 1 ? CGLS_TEXTBOOK : CGLS_CG_TAGGED;
-        c.tag = (unsigned long long*)w.ctag;
+        c.tag = sys.ctag;
         ctx->xch_epoch += (unsigned int)reserve;
         CK(cudaMemsetAsync(ctx->bar, 0, sizeof(unsigned int) * 3, ctx->st));
         PROF_BEGIN(MG_K_COARSE_SOLVE);
@@ -446,7 +481,7 @@ int coarse_solve(mg_ctx* ctx, const CoarseLevel& L, const v2<T>* rc, v2<T>* y, d
         ctx->coarse_kernel_used = c.sh.tm ? MG_CK_TMEM : c.sh.resident ? MG_CK_SMEM : MG_CK_STREAM;
     } else if (std::is_same<T, float>::value && ctx->coarse16) {
         CoarseLevel& Lm = const_cast<CoarseLevel&>(L);
-        TRY(ensure_a16(ctx, Lm));
+        TRY(ensure_a16(ctx, Lm, sys.g.Vc));
         a.A16 = Lm.A16;
         a.s16 = Lm.s16;
     }
@@ -665,6 +700,220 @@ int smooth(mg_ctx* ctx, const v2<T>* r, v2<T>* z, const Reduce& R, Counters& cnt
     return MG_OK;
 }
 
+// ---------------------------------------------------------------- the third level (Sec. III recursion, Sec. IV W-cycle)
+template <typename T> L1Work<T>& l1work(mg_ctx* c);
+template <> L1Work<float>& l1work<float>(mg_ctx* c) { return c->l1f; }
+template <> L1Work<double>& l1work<double>(mg_ctx* c) { return c->l1d; }
+
+template <typename T> int ensure_l1work(mg_ctx* ctx) {
+    L1Work<T>& l = l1work<T>(ctx);
+    if (l.ready) return MG_OK;
+    const size_t n1 = (size_t)ctx->g.Vc * 2 * ctx->prm.nvec, n2 = (size_t)ctx->g2.Vc * 2 * ctx->prm.nvec2;
+    const size_t b1 = sizeof(v2<T>) * n1, b2 = sizeof(v2<T>) * n2;
+    TRY(dalloc(ctx, &l.z, b1));
+    TRY(dalloc(ctx, &l.res, b1));
+    TRY(dalloc(ctx, &l.zero, b1));
+    TRY(dalloc(ctx, &l.sv, b1));
+    TRY(dalloc(ctx, &l.sz, b1));
+    for (v2<T>** q : {&l.crc, &l.cy, &l.cr, &l.cr1, &l.cs, &l.cp, &l.cp1, &l.cq}) TRY(dalloc(ctx, q, b2));
+    zero<T>(l.zero, n1, ctx->st);
+    if (sizeof(T) == 4) {
+        const size_t tb = sizeof(unsigned long long) * 4 * n2;
+        TRY(dalloc(ctx, &l.ctag, tb));
+        CK(cudaMemsetAsync(l.ctag, 0, tb, ctx->st));   // epoch 0 is never awaited
+    }
+    l.ready = true;
+    return MG_OK;
+}
+template <typename T> CgSys<T> level2_sys(mg_ctx* ctx) {
+    L1Work<T>& l = l1work<T>(ctx);
+    return CgSys<T>{ctx->g2, ctx->cnbr2, l.cr, l.cr1, l.cs, l.cp, l.cp1, l.cq, l.ctag};
+}
+
+int clear_epoch_tags(mg_ctx* ctx) {
+    if (ctx->wf.ctag)
+        CK(cudaMemsetAsync(ctx->wf.ctag, 0, sizeof(unsigned long long) * 4 * (size_t)ctx->g.Vc * ctx->wf.cnc, ctx->st));
+    if (ctx->l1f.ctag)
+        CK(cudaMemsetAsync(ctx->l1f.ctag, 0, sizeof(unsigned long long) * 4 * (size_t)ctx->g2.Vc * 2 * ctx->prm.nvec2,
+                           ctx->st));
+    return MG_OK;
+}
+
+int ensure_level2(mg_ctx* ctx, CoarseLevel& L, int nv2) {
+    if (L.cap < nv2) {
+        CK(cudaStreamSynchronize(ctx->st));
+        for (void* q : {(void*)L.P64, (void*)L.P32, (void*)L.A64, (void*)L.A32, (void*)L.Aemb, (void*)L.A16,
+                        (void*)L.s16})
+            dfree(ctx, q);
+        L.P64 = nullptr; L.P32 = nullptr; L.A64 = nullptr; L.A32 = nullptr;
+        L.Aemb = nullptr; L.A16 = nullptr; L.s16 = nullptr;
+        L.emb_valid = L.a16_valid = L.au_valid = L.valid = false;
+        const size_t np = (size_t)nv2 * ctx->g.Vc * 2 * ctx->prm.nvec;
+        const size_t na = (size_t)ctx->g2.Vc * 9 * (2 * nv2) * (2 * nv2);
+        TRY(dalloc(ctx, &L.P64, sizeof(double2) * np));
+        TRY(dalloc(ctx, &L.P32, sizeof(float2) * np));
+        TRY(dalloc(ctx, &L.A64, sizeof(double2) * na));
+        TRY(dalloc(ctx, &L.A32, sizeof(float2) * na));
+        L.cap = nv2;
+    }
+    L.nv = nv2;
+    L.nc = 2 * nv2;
+    return MG_OK;
+}
+
+// P2 and A2 = P2^dag D_c P2 of a level-2 set from nv2 level-1 prototypes (FP64)
+int build_level2(mg_ctx* ctx, CoarseLevel& L, const double2* V2, int nv2) {
+    TRY(ensure_level2(ctx, L, nv2));
+    const int nv1 = ctx->prm.nvec;
+    CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->st));
+    PROF_BEGIN(MG_K_BLOCK_ORTHO);
+    block_orthonormalize_l2(L.P64, V2, nv1, nv2, ctx->g2, ctx->d_status, ctx->st);
+    PROF_END(MG_K_BLOCK_ORTHO);
+    CKL();
+    int status = 0;
+    CK(cudaMemcpyAsync(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    if (status) {
+        L.valid = false;
+        return fail(ctx, MG_ERR_NUMERIC, "level-2 block orthonormalisation: rank-deficient prototypes in an aggregate");
+    }
+    const size_t np = (size_t)nv2 * ctx->g.Vc * 2 * nv1, na = (size_t)ctx->g2.Vc * 9 * L.nc * L.nc;
+    convert<double, float>(L.P32, L.P64, np, ctx->st);
+    PROF_BEGIN(MG_K_COARSE_BUILD);
+    CK(coarse_build_l2(L.A64, L.P64, ctx->full.A64, nv1, nv2, ctx->g, ctx->g2, ctx->st));
+    PROF_END(MG_K_COARSE_BUILD);
+    convert<double, float>(L.A32, L.A64, na, ctx->st);
+    CKL();
+    L.mass = ctx->mass;
+    L.valid = true;
+    L.emb_valid = L.a16_valid = L.au_valid = false;
+    return MG_OK;
+}
+
+// Level-1 post-smoothing: one GMRES(k) application on D_c, scaled by omega
+// (Sec. III smoother one level down), on z with the residual r1 - D_c z.
+template <typename T> int smooth_l1(mg_ctx* ctx, const v2<T>* r1, v2<T>* z, int k) {
+    L1Work<T>& l = l1work<T>(ctx);
+    const size_t n1 = (size_t)ctx->g.Vc * ctx->full.nc;
+    if (l.gm_k < k) {
+        if (l.gm) { dfree(ctx, l.gm); l.gm = nullptr; l.gm_k = 0; }
+        TRY(dalloc(ctx, &l.gm, sizeof(v2<T>) * n1 * (size_t)(k + 1)));
+        l.gm_k = k;
+    }
+    Reduce Rs = ctx->R;
+    Rs.scal = ctx->scal_s;
+    const v2<T>* A1 = lvlA<T>(ctx->full);
+    v2<T>* V = l.gm;
+    PROF_BEGIN(MG_K_KRYLOV);
+    coarse_apply<T>(V, A1, z, ctx->full.nc, false, -1, ctx->g, Rs, ctx->st);   // v_0 = r1 - D_c z
+    scale<T>(V, n1, -1.0, ctx->st);
+    axpy<T>(V, r1, n1, 1.0, 0.0, ctx->st);
+    norm2<T>(V, n1, S_GCR_PN2, Rs, ctx->st);
+    gmres_normalize<T>(V, n1, 0, Rs, ctx->st);
+    for (int j = 0; j < k; ++j) {
+        coarse_apply<T>(V + (size_t)(j + 1) * n1, A1, V + (size_t)j * n1, ctx->full.nc, false, -1, ctx->g, Rs, ctx->st);
+        gcr_multidot<T>(V, n1, j + 1, Rs, ctx->st);
+        gcr_orth_norm<T>(V, n1, j + 1, Rs, ctx->st);
+        gmres_normalize<T>(V, n1, j + 1, Rs, ctx->st);
+    }
+    gmres_ls(Rs, k, ctx->prm.omega, ctx->st);
+    multi_axpy<T>(z, V, n1, k, Rs, ctx->st);
+    PROF_END(MG_K_KRYLOV);
+    CKL();
+    return MG_OK;
+}
+
+// M1: one V(0, k1) cycle of levels 1 and 2 on D_c z = r1 (z overwritten):
+// r2 = P2^dag r1, CGNR on A2 to coarse_tol, z = P2 y2, level-1 smoothing
+template <typename T> int vcycle_l1(mg_ctx* ctx, const CoarseLevel& L2, const v2<T>* r1, v2<T>* z) {
+    L1Work<T>& l = l1work<T>(ctx);
+    const int nv1 = ctx->prm.nvec;
+    PROF_BEGIN(MG_K_RESTRICT);
+    restrict_l2<T>(l.crc, lvlP<T>(L2), r1, nv1, L2.nv, ctx->g2, ctx->st);
+    PROF_END(MG_K_RESTRICT);
+    CKL();
+    TRY(coarse_solve<T>(ctx, L2, level2_sys<T>(ctx), l.crc, l.cy, ctx->prm.coarse_tol, ctx->prm.max_coarse, nullptr));
+    PROF_BEGIN(MG_K_PROLONG);
+    prolong_l2<T>(z, lvlP<T>(L2), l.cy, nv1, L2.nv, ctx->g2, ctx->st);
+    PROF_END(MG_K_PROLONG);
+    CKL();
+    return smooth_l1<T>(ctx, r1, z, ctx->prm.smoother_steps1);
+}
+
+// The three-level coarse-grid correction (Sec. IV): cycles1 V-cycles on
+// D_c e1 = r1 from e1 = 0, e1 += M1 (r1 - D_c e1)
+template <typename T> int kcycle(mg_ctx* ctx, const v2<T>* r1, v2<T>* e1) {
+    TRY(ensure_l1work<T>(ctx));
+    L1Work<T>& l = l1work<T>(ctx);
+    const size_t n1 = (size_t)ctx->g.Vc * ctx->full.nc;
+    const v2<T>* A1 = lvlA<T>(ctx->full);
+    for (int c = 0; c < ctx->prm.cycles1; ++c) {
+        if (c == 0) {
+            TRY(vcycle_l1<T>(ctx, ctx->full2, r1, e1));
+            continue;
+        }
+        PROF_BEGIN(MG_K_KRYLOV);
+        coarse_apply<T>(l.res, A1, e1, ctx->full.nc, false, -1, ctx->g, ctx->R, ctx->st);   // r1 - D_c e1
+        scale<T>(l.res, n1, -1.0, ctx->st);
+        axpy<T>(l.res, r1, n1, 1.0, 0.0, ctx->st);
+        PROF_END(MG_K_KRYLOV);
+        TRY(vcycle_l1<T>(ctx, ctx->full2, l.res, l.z));
+        PROF_BEGIN(MG_K_KRYLOV);
+        axpy<T>(e1, l.z, n1, 1.0, 0.0, ctx->st);
+        PROF_END(MG_K_KRYLOV);
+    }
+    CKL();
+    return MG_OK;
+}
+
+// Level-2 adaptive setup (Sec. IV's two-step setup applied to D_c), from the
+// random level-1 starts in ctx->protos2
+template <typename T> int setup_level2_impl(mg_ctx* ctx) {
+    TRY(ensure_l1work<T>(ctx));
+    L1Work<T>& l = l1work<T>(ctx);
+    const mg_params& p = ctx->prm;
+    const int nv2 = p.nvec2, gs = p.setup_group, nt = nv2 - gs;
+    const size_t n1 = (size_t)ctx->g.Vc * ctx->full.nc;
+    const v2<T>* A1 = lvlA<T>(ctx->full);
+    Reduce R = ctx->R;
+    // (ii) relaxation on D_c v = 0: setup_init_relax GMRES(1) steps (each one MR step)
+    for (int i = 0; i < nv2; ++i) {
+        double2* vi = ctx->protos2 + (size_t)i * n1;
+        convert<double, T>(l.sv, vi, n1, ctx->st);
+        for (int it = 0; it < p.setup_init_relax; ++it) TRY(smooth_l1<T>(ctx, l.zero, l.sv, 1));
+        norm2<T>(l.sv, n1, S_NORM_A, R, ctx->st);
+        normalize_dev<T>(l.sv, n1, S_NORM_A, R, ctx->st);
+        convert<T, double>(vi, l.sv, n1, ctx->st);
+    }
+    CKL();
+    // (iii) groups refined with the truncated two-level method of levels 1 and 2
+    if (p.setup_iters > 0 && nt > 0) {
+        for (int g0 = 0; g0 < nv2; g0 += gs) {
+            int k = 0;
+            for (int i = 0; i < nv2; ++i)
+                if (i < g0 || i >= g0 + gs)
+                    CK(cudaMemcpyAsync(ctx->protos2_t + (size_t)(k++) * n1, ctx->protos2 + (size_t)i * n1,
+                                       sizeof(double2) * n1, cudaMemcpyDeviceToDevice, ctx->st));
+            TRY(build_level2(ctx, ctx->trunc2, ctx->protos2_t, nt));
+            for (int i = g0; i < g0 + gs; ++i) {
+                double2* vi = ctx->protos2 + (size_t)i * n1;
+                convert<double, T>(l.sv, vi, n1, ctx->st);
+                for (int it = 0; it < p.setup_iters; ++it) {
+                    coarse_apply<T>(l.res, A1, l.sv, ctx->full.nc, false, -1, ctx->g, R, ctx->st);   // -D_c v
+                    scale<T>(l.res, n1, -1.0, ctx->st);
+                    TRY(vcycle_l1<T>(ctx, ctx->trunc2, l.res, l.sz));
+                    axpy<T>(l.sv, l.sz, n1, 1.0, 0.0, ctx->st);
+                    norm2<T>(l.sv, n1, S_NORM_A, R, ctx->st);
+                    normalize_dev<T>(l.sv, n1, S_NORM_A, R, ctx->st);
+                }
+                convert<T, double>(vi, l.sv, n1, ctx->st);
+            }
+        }
+    }
+    CKL();
+    return build_level2(ctx, ctx->full2, ctx->protos2, nv2);
+}
+
 template <typename T>
 int vcycle(mg_ctx* ctx, const CoarseLevel& L, const v2<T>* r, v2<T>* z, Counters& cnt) {
     Work<T>& w = work<T>(ctx);
@@ -674,7 +923,11 @@ int vcycle(mg_ctx* ctx, const CoarseLevel& L, const v2<T>* r, v2<T>* z, Counters
     restrict_<T>(w.crc, lvlP<T>(L), r, L.nv, ctx->g, ctx->st);
     PROF_END(MG_K_RESTRICT);
     CKL();
-    TRY(coarse_solve<T>(ctx, L, w.crc, w.cy, ctx->prm.coarse_tol, ctx->prm.max_coarse, nullptr));
+    if (ctx->prm.levels == 3 && &L == &ctx->full)
+        TRY(kcycle<T>(ctx, w.crc, w.cy));   // Sec. IV: V-cycles on the intermediate grid
+    else
+        TRY(coarse_solve<T>(ctx, L, level1_sys<T>(ctx), w.crc, w.cy, ctx->prm.coarse_tol, ctx->prm.max_coarse,
+                            nullptr));
     PROF_BEGIN(MG_K_PROLONG);
     prolong<T>(z, lvlP<T>(L), w.cy, L.nv, ctx->g, ctx->st);
     PROF_END(MG_K_PROLONG);
@@ -886,6 +1139,25 @@ int check_params(const int dims[4], const mg_params* p, std::string& why) {
     if (p->coarse_form < 0 || p->coarse_form > 1) { why = "coarse_form must be 0 or 1"; return MG_ERR_INVALID_ARG; }
     if (p->smoother < 0 || p->smoother > 1) { why = "smoother must be 0 (MR) or 1 (GMRES)"; return MG_ERR_INVALID_ARG; }
     if (p->smoother == 1 && p->smoother_steps > 16) { why = "GMRES smoother: smoother_steps <= 16"; return MG_ERR_INVALID_ARG; }
+    if (p->levels != 2 && p->levels != 3) { why = "levels must be 2 or 3"; return MG_ERR_INVALID_ARG; }
+    if (p->levels == 3) {
+        int vb2 = 1;
+        for (int m = 0; m < 4; ++m) {
+            const int lc = dims[m] / p->block[m];
+            if (p->block2[m] <= 0 || lc % p->block2[m] != 0) {
+                why = "level-1 extent must be a positive multiple of block2";
+                return MG_ERR_INVALID_ARG;
+            }
+            vb2 *= p->block2[m];
+        }
+        if (p->nvec2 <= 0 || p->nvec2 > 32) { why = "nvec2 must be in 1..32"; return MG_ERR_INVALID_ARG; }
+        if (vb2 * p->nvec < p->nvec2) { why = "a level-2 aggregate must hold at least nvec2 dof per chirality"; return MG_ERR_INVALID_ARG; }
+        if (p->nvec2 % p->setup_group != 0) { why = "setup_group must divide nvec2"; return MG_ERR_INVALID_ARG; }
+        if (p->prec_inner == MG_FP16 && p->nvec2 % 2 != 0) { why = "MG_FP16 needs an even nvec2"; return MG_ERR_INVALID_ARG; }
+        if (p->smoother_steps1 < 1 || p->smoother_steps1 > 16) { why = "smoother_steps1 must be in 1..16"; return MG_ERR_INVALID_ARG; }
+        if (p->cycles1 < 1 || p->cycles1 > 8) { why = "cycles1 must be in 1..8"; return MG_ERR_INVALID_ARG; }
+        if (!build_l2_supported(p->nvec, p->nvec2)) { why = "level-2 build does not support this nvec/nvec2"; return MG_ERR_INVALID_ARG; }
+    }
     return MG_OK;
 }
 
@@ -922,9 +1194,17 @@ int need_links(mg_ctx* ctx) {
     if (!ctx->has_links) return fail(ctx, MG_ERR_NOT_SETUP, "links not set");
     return MG_OK;
 }
+// level 1 (the coarse operator of the two-level method) is set up
 int need_level(mg_ctx* ctx) {
     TRY(need_links(ctx));
     if (!ctx->full.valid) return fail(ctx, MG_ERR_NOT_SETUP, "no coarse operator: call mg_setup or mg_set_null_vectors");
+    return MG_OK;
+}
+// every level of the configured cycle is set up (solves and cycles)
+int need_cycle(mg_ctx* ctx) {
+    TRY(need_level(ctx));
+    if (ctx->prm.levels == 3 && !ctx->full2.valid)
+        return fail(ctx, MG_ERR_NOT_SETUP, "levels = 3: call mg_setup_level2 or mg_set_level2_vectors");
     return MG_OK;
 }
 
@@ -1006,7 +1286,7 @@ int hook_coarse_solve(mg_ctx* ctx, const double* rc, double* y, double tol, int 
     size_t n = (size_t)ctx->g.Vc * ctx->full.nc;
     TRY(upload_coarse<T>(ctx, rc, w.crc, n));
     int it = 0;
-    TRY(coarse_solve<T>(ctx, ctx->full, w.crc, w.cy, tol, maxit, &it));
+    TRY(coarse_solve<T>(ctx, ctx->full, level1_sys<T>(ctx), w.crc, w.cy, tol, maxit, &it));
     TRY(read_scalars(ctx, S_CG_RC2, 2));
     if (iters) *iters = it;
     if (rel) *rel = ctx->h_scal[S_CG_RC2] > 0 ? std::sqrt(ctx->h_scal[S_CG_R2] / ctx->h_scal[S_CG_RC2]) : 0.0;
@@ -1032,6 +1312,11 @@ int mg_default_params(mg_params* p) {
     std::memset(p, 0, sizeof(*p));
     for (int m = 0; m < 4; ++m) p->block[m] = 4;
     p->nvec = 8;
+    p->levels = 2;
+    for (int m = 0; m < 4; ++m) p->block2[m] = 2;
+    p->nvec2 = 32;
+    p->smoother_steps1 = 4;
+    p->cycles1 = 2;
     p->setup_init_relax = 10;
     p->setup_iters = 3;
     p->setup_group = 4;
@@ -1078,6 +1363,24 @@ int mg_create(const int dims[4], int t_antiperiodic, const mg_params* p, void* s
     g.Vc = g.Lc[0] * g.Lc[1] * g.Lc[2] * g.Lc[3];
     g.V = (long long)g.Vb * g.Vc;
     g.tap = t_antiperiodic ? 1 : 0;
+    if (p->levels == 3) {   // the level-1 lattice cut into level-2 aggregates
+        Geom& h = ctx->g2;
+        for (int m = 0; m < 4; ++m) {
+            h.L[m] = g.Lc[m];
+            h.B[m] = p->block2[m];
+            h.Lc[m] = g.Lc[m] / p->block2[m];
+        }
+        h.lstride[0] = 1;
+        h.xstride[0] = 1;
+        for (int m = 1; m < 4; ++m) {
+            h.lstride[m] = h.lstride[m - 1] * h.B[m - 1];
+            h.xstride[m] = h.xstride[m - 1] * h.Lc[m - 1];
+        }
+        h.Vb = h.B[0] * h.B[1] * h.B[2] * h.B[3];
+        h.Vc = h.Lc[0] * h.Lc[1] * h.Lc[2] * h.Lc[3];
+        h.V = g.Vc;
+        h.tap = 0;   // the t boundary sign lives inside D_c
+    }
     size_t n = nfine(ctx);
     int rc = MG_OK;
     if ((rc = dalloc(ctx, &ctx->U64, sizeof(double2) * 36 * (size_t)g.V)) ||
@@ -1104,6 +1407,8 @@ int mg_create(const int dims[4], int t_antiperiodic, const mg_params* p, void* s
         cudaMemsetAsync(ctx->bar, 0, sizeof(unsigned int) * 4, ctx->st) != cudaSuccess ||
         cudaMemsetAsync(ctx->xch, 0, sizeof(unsigned long long) * kXchWords, ctx->st) != cudaSuccess ||
         (coarse_neighbour_table(ctx->cnbr, ctx->g, ctx->st), cudaGetLastError()) != cudaSuccess ||
+        (p->levels == 3 && (dalloc(ctx, &ctx->cnbr2, sizeof(int) * 9 * (size_t)ctx->g2.Vc) != MG_OK ||
+                            (coarse_neighbour_table(ctx->cnbr2, ctx->g2, ctx->st), cudaGetLastError()) != cudaSuccess)) ||
         cudaStreamSynchronize(ctx->st) != cudaSuccess) {
         cudaGetLastError();
         mg_destroy(ctx);
@@ -1183,6 +1488,14 @@ int mg_set_mass(mg_ctx* ctx, double m) {
         ctx->full.a16_valid = false;
         ctx->full.au_valid = false;
     }
+    if (ctx->full2.valid) {   // A2(m) = P2^dag D_c(m) P2 = A2(m0) + (m - m0) I, P2^dag P2 = I
+        CoarseLevel& L = ctx->full2;
+        coarse_shift_mass(L.A64, L.nc, m - L.mass, ctx->g2, ctx->st);
+        convert<double, float>(L.A32, L.A64, (size_t)ctx->g2.Vc * 9 * L.nc * L.nc, ctx->st);
+        CKL();
+        L.mass = m;
+        L.emb_valid = L.a16_valid = L.au_valid = false;
+    }
     ctx->mass = m;
     CK(cudaStreamSynchronize(ctx->st));
     return MG_OK;
@@ -1195,6 +1508,9 @@ int mg_set_params(mg_ctx* ctx, const mg_params* p) {
     for (int m = 0; m < 4; ++m)
         if (p->block[m] != ctx->prm.block[m]) return fail(ctx, MG_ERR_INVALID_ARG, "block size is fixed at create");
     if (p->nvec != ctx->prm.nvec) return fail(ctx, MG_ERR_INVALID_ARG, "nvec is fixed at create");
+    if (p->levels != ctx->prm.levels || p->nvec2 != ctx->prm.nvec2 ||
+        (p->levels == 3 && std::memcmp(p->block2, ctx->prm.block2, sizeof(p->block2)) != 0))
+        return fail(ctx, MG_ERR_INVALID_ARG, "levels, block2 and nvec2 are fixed at create");
     if (p->gcr_restart > ctx->K) return fail(ctx, MG_ERR_INVALID_ARG, "gcr_restart above the value at create");
     ctx->prm = *p;
     return MG_OK;
@@ -1254,6 +1570,101 @@ int mg_set_null_vectors(mg_ctx* ctx, const double* V, int nv) {
     return build_level(ctx, ctx->full, ctx->protos, nv);
 }
 
+// ---- the third level
+}  // extern "C"
+namespace {
+int need_three_levels(mg_ctx* ctx) {
+    if (ctx->prm.levels != 3) return fail(ctx, MG_ERR_INVALID_ARG, "the context was created with levels = 2");
+    TRY(need_links(ctx));
+    if (!ctx->full.valid) return fail(ctx, MG_ERR_NOT_SETUP, "no level-1 operator: run the fine setup first");
+    return MG_OK;
+}
+int upload_protos2(mg_ctx* ctx, const double* V2) {
+    const size_t n1 = (size_t)ctx->g.Vc * ctx->full.nc, nv2 = ctx->prm.nvec2;
+    if (!ctx->protos2) {
+        TRY(dalloc(ctx, &ctx->protos2, sizeof(double2) * n1 * nv2));
+        TRY(dalloc(ctx, &ctx->protos2_t, sizeof(double2) * n1 * nv2));
+    }
+    CK(cudaMemcpyAsync(ctx->protos2, V2, sizeof(double2) * n1 * nv2, cudaMemcpyHostToDevice, ctx->st));
+    return MG_OK;
+}
+template <typename T> int hook_kcycle(mg_ctx* ctx, const double* r1, double* e1) {
+    TRY(ensure_work<T>(ctx));
+    Work<T>& w = work<T>(ctx);
+    const size_t n1 = (size_t)ctx->g.Vc * ctx->full.nc;
+    CK(cudaMemcpyAsync(ctx->cstage, r1, sizeof(double2) * n1, cudaMemcpyHostToDevice, ctx->st));
+    convert<double, T>(w.crc, ctx->cstage, n1, ctx->st);
+    TRY(kcycle<T>(ctx, w.crc, w.cy));
+    convert<T, double>(ctx->cstage, w.cy, n1, ctx->st);
+    CKL();
+    CK(cudaMemcpyAsync(e1, ctx->cstage, sizeof(double2) * n1, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return check_timeout(ctx);
+}
+}  // namespace
+extern "C" {
+
+int mg_setup_level2(mg_ctx* ctx, const double* V2) {
+    if (!ctx || !V2) return MG_ERR_INVALID_ARG;
+    TRY(need_three_levels(ctx));
+    TRY(upload_protos2(ctx, V2));
+    ctx->coarse16 = ctx->prm.prec_inner == MG_FP16;
+    TRY(ctx->prm.prec_inner != MG_FP64 ? setup_level2_impl<float>(ctx) : setup_level2_impl<double>(ctx));
+    return check_timeout(ctx);
+}
+
+int mg_set_level2_vectors(mg_ctx* ctx, const double* V2) {
+    if (!ctx || !V2) return MG_ERR_INVALID_ARG;
+    TRY(need_three_levels(ctx));
+    TRY(upload_protos2(ctx, V2));
+    return build_level2(ctx, ctx->full2, ctx->protos2, ctx->prm.nvec2);
+}
+
+int mg_get_level2_prolongator(mg_ctx* ctx, double* P2) {
+    if (!ctx || !P2) return MG_ERR_INVALID_ARG;
+    if (!ctx->full2.valid) return fail(ctx, MG_ERR_NOT_SETUP, "no level-2 prolongator");
+    const CoarseLevel& L = ctx->full2;
+    const int nv1 = ctx->prm.nvec, nv2 = L.nv, nc1 = 2 * nv1, vb = ctx->g2.Vb, len = vb * nv1;
+    const size_t np = (size_t)nv2 * ctx->g.Vc * nc1;
+    std::vector<double2> panel(np);
+    CK(cudaMemcpyAsync(panel.data(), L.P64, sizeof(double2) * np, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    double2* out = reinterpret_cast<double2*>(P2);
+    for (int X2 = 0; X2 < ctx->g2.Vc; ++X2)
+        for (int sgn = 0; sgn < 2; ++sgn)
+            for (int i = 0; i < nv2; ++i)
+                for (int l2 = 0; l2 < vb; ++l2) {
+                    const long long X1 = lex_site(ctx->g2, X2, l2);
+                    for (int j = 0; j < nv1; ++j)
+                        out[((size_t)i * ctx->g.Vc + X1) * nc1 + sgn * nv1 + j] =
+                            panel[(((size_t)X2 * 2 + sgn) * nv2 + i) * len + (size_t)l2 * nv1 + j];
+                }
+    return MG_OK;
+}
+
+int mg_get_level2_op(mg_ctx* ctx, double* A2) {
+    if (!ctx || !A2) return MG_ERR_INVALID_ARG;
+    if (!ctx->full2.valid) return fail(ctx, MG_ERR_NOT_SETUP, "no level-2 operator");
+    const CoarseLevel& L = ctx->full2;
+    const size_t na = (size_t)ctx->g2.Vc * 9 * L.nc * L.nc;
+    double2* tmp = nullptr;
+    TRY(dalloc(ctx, &tmp, sizeof(double2) * na));
+    coarse_op_transpose(tmp, L.A64, L.nc, ctx->g2.Vc, ctx->st);
+    CKL();
+    CK(cudaMemcpyAsync(A2, tmp, sizeof(double2) * na, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    dfree(ctx, tmp);
+    return MG_OK;
+}
+
+int mg_kcycle(mg_ctx* ctx, const double* r1, double* e1, int prec) {
+    if (!ctx || !r1 || !e1) return MG_ERR_INVALID_ARG;
+    TRY(need_three_levels(ctx));
+    if (!ctx->full2.valid) return fail(ctx, MG_ERR_NOT_SETUP, "no level-2 operator");
+    ctx->coarse16 = prec == MG_FP16;
+    return prec != MG_FP64 ? hook_kcycle<float>(ctx, r1, e1) : hook_kcycle<double>(ctx, r1, e1);
+}
+
 int mg_get_prolongator(mg_ctx* ctx, double* P) {
     TRY(need_level(ctx));
     if (!P) return MG_ERR_INVALID_ARG;
@@ -1289,7 +1700,7 @@ int mg_get_coarse_op(mg_ctx* ctx, double* A) {
 }
 
 int mg_solve_device(mg_ctx* ctx, const double* b_dev, double* x_dev, mg_solve_info* info) {
-    TRY(need_level(ctx));
+    TRY(need_cycle(ctx));
     if (!b_dev || !x_dev) return fail(ctx, MG_ERR_INVALID_ARG, "null vector");
     spinor_to_internal<double>(ctx->b64, (const double2*)b_dev, ctx->g, ctx->st);
     CKL();
@@ -1303,7 +1714,7 @@ int mg_solve_device(mg_ctx* ctx, const double* b_dev, double* x_dev, mg_solve_in
 }
 
 int mg_solve(mg_ctx* ctx, const double* b, double* x, mg_solve_info* info) {
-    TRY(need_level(ctx));
+    TRY(need_cycle(ctx));
     if (!b || !x) return fail(ctx, MG_ERR_INVALID_ARG, "null vector");
     size_t n = nfine(ctx);
     CK(cudaMemcpyAsync(ctx->stage_a, b, sizeof(double2) * n, cudaMemcpyHostToDevice, ctx->st));
@@ -1353,7 +1764,7 @@ int mg_coarse_solve(mg_ctx* ctx, const double* rc, double* y, double tol, int ma
                            : hook_coarse_solve<double>(ctx, rc, y, tol, maxit, iters, final_rel);
 }
 int mg_vcycle(mg_ctx* ctx, const double* r, double* z, int prec) {
-    TRY(need_level(ctx));
+    TRY(need_cycle(ctx));
     if (!r || !z) return MG_ERR_INVALID_ARG;
     ctx->coarse16 = prec == MG_FP16;
     return prec != MG_FP64 ? hook_vcycle<float>(ctx, r, z) : hook_vcycle<double>(ctx, r, z);
@@ -2126,7 +2537,7 @@ int solve_batched_impl(mg_ctx* ctx, int nrhs, mg_solve_info* infos) {
 extern "C" {
 
 int mg_solve_batched_device(mg_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, mg_solve_info* infos) {
-    TRY(need_level(ctx));
+    TRY(need_cycle(ctx));
     if (!b_dev || !x_dev || nrhs <= 0) return fail(ctx, MG_ERR_INVALID_ARG, "null buffer or nrhs <= 0");
     size_t n = nfine(ctx);
     if (ctx->prm.prec_inner == MG_FP64) {   // FP64 inner precision: the sources one after another
@@ -2139,6 +2550,7 @@ int mg_solve_batched_device(mg_ctx* ctx, const double* b_dev, double* x_dev, int
         return worst;
     }
     if (nrhs > 256) return fail(ctx, MG_ERR_INVALID_ARG, "at most 256 sources per batch");
+    if (ctx->prm.levels != 2) return fail(ctx, MG_ERR_INVALID_ARG, "the batched solve runs the two-level cycle");
     if (!coarse_apply_tc_supported(ctx->full.nc, round16(nrhs)))
         return fail(ctx, MG_ERR_INVALID_ARG, "batched coarse stencil needs 2*nvec a multiple of 16 and <= 128");
     TRY(ensure_batch(ctx, nrhs));
@@ -2155,7 +2567,7 @@ int mg_solve_batched_device(mg_ctx* ctx, const double* b_dev, double* x_dev, int
 }
 
 int mg_solve_batched(mg_ctx* ctx, const double* b, double* x, int nrhs, mg_solve_info* infos) {
-    TRY(need_level(ctx));
+    TRY(need_cycle(ctx));
     if (!b || !x || nrhs <= 0) return fail(ctx, MG_ERR_INVALID_ARG, "null buffer or nrhs <= 0");
     size_t n = nfine(ctx);
     double2 *db = nullptr, *dx = nullptr;

@@ -1,5 +1,6 @@
 // Host-side launchers of the library's kernels (internal, not part of the C-ABI).
 #pragma once
+#include <mutex>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -252,6 +253,34 @@ template <typename T> void eo_spinor_pack(v2<T>* out, const double2* in, const E
 template <typename T> void eo_spinor_unpack(double2* out, const v2<T>* in, const EoGeom& e, cudaStream_t st);
 void eo_links_pack(double2* U64, float2* U32, const double2* Uint, const Geom& g, const EoGeom& e, cudaStream_t st);
 
+// ---------------------------------------------------------------- level 2 (three-level method)
+// g2: the level-1 lattice (L) cut into level-2 aggregates (B), Lc = level-2 lattice
+void block_orthonormalize_l2(double2* P2, const double2* V2, int nv1, int nv2, const Geom& g2, int* status,
+                             cudaStream_t st);
+template <typename T>
+void restrict_l2(v2<T>* r2, const v2<T>* P2, const v2<T>* r1, int nv1, int nv2, const Geom& g2, cudaStream_t st);
+template <typename T>
+void prolong_l2(v2<T>* e1, const v2<T>* P2, const v2<T>* y2, int nv1, int nv2, const Geom& g2, cudaStream_t st);
+bool build_l2_supported(int nv1, int nv2);
+cudaError_t coarse_build_l2(double2* A2, const double2* P2, const double2* A1, int nv1, int nv2, const Geom& g1,
+                            const Geom& g2, cudaStream_t st);
+
+// Orders this process's TMEM-kernel launches across streams: construct before
+// a launch (the stream then waits for the previous TMEM launch if that was on
+// another stream), call launched() right after it; held for the launch.
+class TmemOrder {
+  public:
+    explicit TmemOrder(cudaStream_t st);
+    cudaError_t error() const { return err_; }
+    cudaError_t launched();
+
+  private:
+    cudaStream_t st_;
+    std::lock_guard<std::mutex> lock_;
+    cudaError_t err_ = cudaSuccess;
+    bool skip_ = false;
+    int dev_ = 0;
+};
 // one bounded device wait driven into a configuration that cannot complete
 cudaError_t wait_probe(int kind, int G, unsigned long long* words, unsigned int* ctr, int* err, long long limit,
                        cudaStream_t st);

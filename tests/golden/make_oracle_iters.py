@@ -1,8 +1,11 @@
-"""Outer MG-GCR iteration counts of the FP64 oracle on a workload: the oracle's
-adaptive setup at the workload's setup mass, then one solve per mass of the
-sweep (the same inputs as the benchmark step).  The counts let the benchmark's
-CPU baseline time a bounded sample of oracle iterations and scale it to whole
-solves.  Calls only oracle/ and synth/.
+"""Work counts of the FP64 oracle on a workload: the oracle's adaptive setup at
+the workload's setup mass, then one solve per mass of the sweep (the same
+inputs as the benchmark step).  Recorded per solve: outer MG-GCR iterations,
+coarse CG iterations and fine operator applications; for the setup: its fine
+operator applications and coarse CG iterations (they depend on how good the
+prototypes become, which only the whole setup shows).  The benchmark's CPU
+baseline times the oracle's unit costs on the machine it runs on and scales
+them by these counts.  Calls only oracle/ and synth/.
 
 usage: python tests/golden/make_oracle_iters.py <workload name>
        -> tests/golden/<workload name>_oracle_iters.txt
@@ -36,11 +39,12 @@ def main(name):
     sm, steps = smoother(w)
     po = oracle.make_params(w.dims, w.block, nv=w.nvec, m=w.setup_mass(), gcr_restart=16, tol=1e-10, max_outer=20000,
                             smoother=sm, mr_steps=steps)
-    Vs, P, A, st = oracle.setup(po, U, V0, init_relax=10, n_iter=SETUP_ITERS.get(name, 5), group_size=4)
+    Vs, P, A, st, sinfo = oracle.setup_counted(po, U, V0, init_relax=10, n_iter=SETUP_ITERS.get(name, 5),
+                                               group_size=4)
     assert st == 0
     t_setup = time.time() - t0
     print(f"setup {t_setup:.0f} s", flush=True)
-    iters, rels = [], []
+    iters, rels, coarse, mvs = [], [], [], []
     for i, m in enumerate(w.masses()):
         b = synth.gaussian_spinor(w.dims, w.source_seed, stream=i)
         po = oracle.make_params(w.dims, w.block, nv=w.nvec, m=m, gcr_restart=16, tol=1e-10, max_outer=20000,
@@ -50,6 +54,8 @@ def main(name):
         x, info = oracle.gcr_solve(po, U, P, A_m, b)
         iters.append(int(info["outer_iters"]))
         rels.append(float(info["true_rel_res"]))
+        coarse.append(int(info["coarse_iters"]))
+        mvs.append(int(info["fine_matvecs"]))
         print(f"m {m:.10f}: {info['outer_iters']} outer iterations, true rel res {info['true_rel_res']:.3e}, "
               f"{time.time() - t:.0f} s", flush=True)
     out = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"{name}_oracle_iters.txt")
@@ -59,6 +65,9 @@ def main(name):
                 f"smoother {'GMRES(%d)' % steps if sm else '%d MR steps' % steps}\n")
         f.write(f"# masses {w.masses()}\n# true relative residuals {rels}\n# setup {t_setup:.0f} s\n")
         f.write("outer_iters " + " ".join(map(str, iters)) + "\n")
+        f.write("coarse_iters " + " ".join(map(str, coarse)) + "\n")
+        f.write("fine_matvecs " + " ".join(map(str, mvs)) + "\n")
+        f.write(f"setup_fine_matvecs {sinfo['fine_matvecs']}\nsetup_coarse_iters {sinfo['coarse_iters']}\n")
     print(open(out).read())
 
 
