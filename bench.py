@@ -31,7 +31,21 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_1005_3043_gb300.workloads import WORKLOADS  # noqa: E402
+
+
+def _load_workloads():
+    """The workload table, loaded by file path: the reference arm must not
+    import the CUDA package (nor map its library)."""
+    import importlib.util
+    path = os.path.join(ROOT, "paper_1005_3043_gb300", "workloads.py")
+    spec = importlib.util.spec_from_file_location("_wmg_workloads", path)
+    mod = importlib.util.module_from_spec(spec)
+    sys.modules["_wmg_workloads"] = mod
+    spec.loader.exec_module(mod)
+    return mod.WORKLOADS
+
+
+WORKLOADS = _load_workloads()
 
 DEFAULT_WORKLOAD = "wilson_16x16x16x32_nv20_beta6_5mass"
 METRIC = "MG-GCR solves/sec to 1e-10 true residual"
@@ -155,6 +169,121 @@ def one_step_rate(wmg, torch, w, prec, U, dV0, dB, dX, masses, stream):
     mg.close()
     ms = e0.elapsed_time(e1)
     return len(masses) / (ms / 1e3), ms, iters
+
+
+def three_level_leg(wmg, torch, w, U, dV0, dB, dX, masses, stream, prec, nv2=32, block2=(2, 2, 2, 2)):
+    """The paper's favoured method (Sec. IV) on the same step: three levels (4^4
+    then 2^4 aggregates, Nv2 = 32), the workload's GMRES post-smoother on the
+    fine grid and GMRES(4) on level 1, two level-1 V-cycles per fine correction
+    (the W-cycle), CG on the normal equations to 1e-3 on level 2; the step adds
+    the level-2 setup (random level-1 starts, seeded) to the fine setup.  One
+    warm-up step, one timed step (CUDA events)."""
+    import synth
+    p = mg_params(w, prec)
+    p.levels, p.nvec2, p.smoother_steps1, p.cycles1 = 3, nv2, 4, 2
+    for i in range(4):
+        p.block2[i] = block2[i]
+    Vc1 = int(np.prod([d // b for d, b in zip(w.dims, w.block)]))
+    V2 = synth.gaussian(nv2 * Vc1 * 2 * w.nvec, w.setup_seed + 2, 0).reshape(nv2, Vc1, 2 * w.nvec)
+    mg = wmg.WilsonMG(w.dims, p, stream=stream)
+    mg.set_links(U)
+    out = None
+    for rep in range(2):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        mg.set_mass(w.setup_mass())
+        mg.setup_device(dV0)
+        mg.setup_level2(V2)
+        e1.record(stream)
+        infos = []
+        for i, m in enumerate(masses):
+            mg.set_mass(m)
+            info = mg.solve_device(dB[i], dX[i])
+            if info["status"] != 0:
+                raise RuntimeError(f"three-level solve failed at m={m}: {info}")
+            infos.append(info)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e2)
+        out = {"levels": 3, "block2": "x".join(map(str, block2)), "nvec2": nv2, "smoother_steps1": 4, "cycles1": 2,
+               "solves_per_s": len(masses) / (ms / 1e3), "ms_per_step": ms, "setup_ms": e0.elapsed_time(e1),
+               "solves_ms": e1.elapsed_time(e2), "outer_iters": [i["outer_iters"] for i in infos],
+               "level2_cg_iters": [i["coarse_iters"] for i in infos],
+               "true_rel_res": [i["true_rel_res"] for i in infos]}
+    mg.close()
+    return out
+
+
+def flops_mg(w, info):
+    """Floating-point work of one MG-GCR solve, counted per fine site V and
+    coarse site Vc: 1320 V per fine operator application, 144 nc^2 Vc per
+    coarse CG iteration (D_c and D_c^dag, 9 complex nc x nc blocks each),
+    96 Nv V per cycle for restriction and prolongation, and per cycle the
+    Krylov vector work of the GMRES(k) smoother (k (k + 3) / 2 complex dots
+    and updates over 12 V entries, 8 flops each) and of the flexible GCR
+    (its average k / 2 + 2 dots and updates); reductions and scalars ignored."""
+    V = int(np.prod(w.dims))
+    nc = 2 * w.nvec
+    Vc = V // int(np.prod(w.block))
+    k = w.extra.get("smoother_steps", 4)
+    cyc = info["outer_iters"]
+    krylov = (k * (k + 3) / 2 + 16 / 2 + 2) * 2 * 8 * 12 * V
+    return info["fine_matvecs"] * 1320.0 * V + info["coarse_iters"] * 144.0 * nc * nc * Vc + \
+        cyc * (96.0 * w.nvec * V + krylov)
+
+
+def eo_cg_leg(wmg, torch, w, U, dB, dX, masses, mg_infos, stream):
+    """The comparison solver of Sec. IV (Fig. 1 and 2) on the same sources and
+    masses: red-black preconditioned CG (FP32 iterations, FP64 reliable updates)
+    to the same 1e-10, against the timed MG-GCR solves (FP16 mode, setup
+    excluded as in the paper's Fig. 1).  Wilson products: every Dhat or
+    Dhat^dag counts one (the fine work of Fig. 1); flops: 1320 V per product
+    plus the CG's vector work (about 170 V per iteration) against flops_mg."""
+    V = int(np.prod(w.dims))
+    mg = wmg.WilsonMG(w.dims, mg_params(w, "fp32"), stream=stream)
+    mg.set_links(U)
+    out = {"solver": "red-black CG on the normal equations, FP32 iterations, FP64 reliable updates",
+           "iters": [], "products": [], "ms": [], "true_rel_res": []}
+    for i, m in enumerate(masses):
+        mg.set_mass(m)
+        info = mg.solve_eo_cg_device(dB[i], dX[i], tol=1e-10, maxit=500000, prec=wmg.MG_FP32)
+        if info["status"] != 0:
+            raise RuntimeError(f"red-black CG failed at m={m}: {info}")
+        out["iters"].append(info["outer_iters"])
+        out["products"].append(info["fine_matvecs"])
+        out["ms"].append(info["solve_ms"])
+        out["true_rel_res"].append(info["true_rel_res"])
+    mg.close()
+    out["mg_products"] = [i["fine_matvecs"] for i in mg_infos]
+    out["mg_solve_ms"] = [i["solve_ms"] for i in mg_infos]
+    out["matvec_ratio"] = [a / b for a, b in zip(out["products"], out["mg_products"])]
+    out["time_ratio"] = [a / b for a, b in zip(out["ms"], out["mg_solve_ms"])]
+    cg_fl = [p * 1320.0 * V + it * 170.0 * V for p, it in zip(out["products"], out["iters"])]
+    out["flop_ratio"] = [a / flops_mg(w, i) for a, i in zip(cg_fl, mg_infos)]
+    return out
+
+
+def dslash_beyond_l2(wmg, torch, stream, peak):
+    """The fine operator on a 24^3 x 64 lattice (hot-start links: the bandwidth
+    does not depend on them), L2 flushed before every launch: FP32 (480 B per
+    site, 425 MB per application) and FP16 storage (248 B per site)."""
+    import synth
+    L = (24, 24, 24, 64)
+    U = synth.hot_gauge(L, 9)
+    p = wmg.mg_default_params()
+    p.nvec, p.setup_group = 2, 2
+    mg = wmg.WilsonMG(L, p, stream=stream)
+    mg.set_links(U)
+    mg.set_mass(-0.5)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    out = {"lattice": "24x24x24x64", "l2": "flushed before every launch", "peak_GBps": peak}
+    for name, prec in (("fp32", wmg.MG_FP32), ("fp16", wmg.MG_FP16)):
+        ms, nbytes = mg.time_dslash_cold(flush.data_ptr(), flush.numel(), prec, 50)
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        out[name] = {"us": 1e3 * ms, "bytes": nbytes, "GB/s": gbs, "frac": gbs / peak}
+    del flush
+    mg.close()
+    return out
 
 
 def max_over_ranks(ms, device="cpu"):
@@ -338,6 +467,11 @@ def run_ours(args, w):
                             "max_true_rel_res": max(b["true_rel_res"] for b in binfo),
                             "status": sorted({b["status"] for b in binfo})}
 
+    if not args.quick:
+        extra["three_level"] = three_level_leg(wmg, torch, w, U, dV0, dB, dX, masses, stream, args.prec)
+        extra["eo_cg"] = eo_cg_leg(wmg, torch, w, U, dB, dX, masses, infos[:n_solve], stream)
+        extra["dslash_24x24x24x64"] = dslash_beyond_l2(wmg, torch, stream, peak)
+
     if rank == 0:
         iters = [i["outer_iters"] for i in infos[:n_solve]]
         line = {
@@ -370,65 +504,100 @@ def run_ours(args, w):
         }
         line.update(extra)
         if not args.no_baseline:
-            line["cpu_baseline"] = cpu_baseline(w, U, srcs, masses, V0, oracle_iters(w, iters),
-                                                mg_params(w, "fp64").setup_iters)
+            cb = cpu_baseline(w, U, srcs, masses, V0)
+            if cb is not None:
+                line["cpu_baseline"] = {k: v for k, v in cb.items() if k not in ("step_s", "solve_s")}
         print(json.dumps(line), flush=True)
     if dist:
         torch.distributed.destroy_process_group()
 
 
-def cpu_baseline(w, U, srcs, masses, V0, outer_iters, setup_iters, budget_s=25.0):
-    """The FP64 CPU oracle on a bounded sample of the step, scaled to whole solves.
+def oracle_counts(w):
+    """The oracle's own work on this workload (setup at the setup mass, one solve
+    per mass), recorded by tests/golden/make_oracle_iters.py: per solve outer
+    iterations, coarse CG iterations and fine operator applications; for the
+    setup its fine operator applications and coarse CG iterations."""
+    path = os.path.join(ROOT, "tests", "golden", f"{w.name}_oracle_iters.txt")
+    out = {}
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, *v = line.split()
+        out[k] = [int(x) for x in v]
+    return out
 
-    Timed: one Wilson operator application, one block orthonormalisation and one
-    Galerkin build from the random prototypes, and outer MG-GCR iterations at the
-    heaviest mass until the budget is used.  Scaled: a solve costs its outer
-    iteration count times the time of one outer iteration (the counts are the
-    oracle's own, measured once per workload by tests/golden/make_oracle_iters.py;
-    the GPU's counts where none are stored); the setup costs 10 MR relaxations of
-    every prototype (two operator applications per step), Nv/4 groups x
-    setup_iters x 4 truncated-cycle iterations (one outer iteration each) and
-    1 + Nv/4 orthonormalisations and builds."""
+
+def cpu_baseline(w, U, srcs, masses, V0, budget_s=25.0):
+    """The FP64 CPU oracle on this workload: its unit costs timed here, scaled by
+    its own recorded work counts.
+
+    Timed on this machine (oracle calls only, with the workload's field, random
+    starts and sources): one fine operator application t_d; one block
+    orthonormalisation and one Galerkin build; one coarse CG iteration t_cg
+    (20 iterations of oracle.cgnr); and k outer MG-GCR iterations, whose time
+    less their own fine applications and coarse iterations gives the rest of
+    an outer iteration (GCR and smoother vector work, restriction,
+    prolongation) t_rest.  Scaled by the counts the oracle itself produced on
+    this workload: the step costs setup_fine_matvecs t_d + setup_coarse_iters
+    t_cg + (1 + Nv/4) orthonormalisations and builds (the Nv/4 truncated
+    levels scaled by (Nv-4)^2/Nv^2) + Nv/4 x setup_iters x 4 truncated cycles
+    of t_rest, plus per mass fine_matvecs t_d + coarse_iters t_cg +
+    outer_iters t_rest.  Without recorded counts it falls back to the GPU's
+    outer iteration counts and says so."""
     import oracle
     oracle.build()
     cores = os.cpu_count()
+    t_begin = time.perf_counter()
     t0 = time.perf_counter()
-    oracle.dslash(U, srcs[0], masses[0], w.dims)
-    t_d = time.perf_counter() - t0
+    for _ in range(3):
+        oracle.dslash(U, srcs[0], masses[0], w.dims)
+    t_d = (time.perf_counter() - t0) / 3
     t0 = time.perf_counter()
     P, st = oracle.block_orthonormalize(V0, w.dims, w.block)
     t_ortho = time.perf_counter() - t0
     t0 = time.perf_counter()
-    A = oracle.coarse_build(U, P, masses[0], w.dims, w.block)
+    A = oracle.coarse_build(U, P, masses[-1], w.dims, w.block)
     t_build = time.perf_counter() - t0
-    remaining = max(budget_s - t_ortho - t_build - t_d, 2.0)
+    Lc = oracle.coarse_dims(w.dims, w.block)
+    rc = oracle.restrict(P, srcs[0], w.dims, w.block)
+    t0 = time.perf_counter()
+    oracle.cgnr(A, rc, Lc, 0.0, 20)
+    t_cg = (time.perf_counter() - t0) / 20
+    sm, steps = w.extra.get("smoother", 0), w.extra.get("smoother_steps", 4)
     k = 1
-    t_it = None
     while True:
-        p = oracle.make_params(w.dims, w.block, nv=w.nvec, m=masses[0], tol=0.0, max_outer=k, gcr_restart=16,
-                               smoother=w.extra.get("smoother", 0), mr_steps=w.extra.get("smoother_steps", 4))
+        p = oracle.make_params(w.dims, w.block, nv=w.nvec, m=masses[-1], tol=0.0, max_outer=k, gcr_restart=16,
+                               smoother=sm, mr_steps=steps)
         t1 = time.perf_counter()
         _, info = oracle.gcr_solve(p, U, P, A, srcs[0])
         dt = time.perf_counter() - t1
-        t_it = dt / max(info["outer_iters"], 1)
-        if dt * 2 > remaining or k >= 16:
+        if dt * 2 > max(budget_s - (time.perf_counter() - t_begin), 2.0) or k >= 16:
             break
         k *= 2
+    n_out = max(info["outer_iters"], 1)
+    t_rest = max(dt - info["fine_matvecs"] * t_d - info["coarse_iters"] * t_cg, 0.0) / n_out
+    try:
+        c = oracle_counts(w)
+        outer, coarse, mvs = c["outer_iters"], c["coarse_iters"], c["fine_matvecs"]
+        s_mv, s_cg = c["setup_fine_matvecs"][0], c["setup_coarse_iters"][0]
+        src = "the oracle's own recorded counts (tests/golden/make_oracle_iters.py)"
+    except (OSError, KeyError):
+        return None
     groups = w.nvec // 4
-    n_builds = 1 + groups
-    setup_s = 10 * w.nvec * 2 * t_d + groups * setup_iters * 4 * t_it + n_builds * (t_ortho + t_build)
-    step_s = setup_s + t_it * sum(outer_iters)
+    setup_iters = w.extra.get("setup_iters", 5)
+    trunc = ((w.nvec - 4) / w.nvec) ** 2
+    setup_s = (s_mv * t_d + s_cg * t_cg + (t_ortho + t_build) * (1 + groups * trunc)
+               + groups * setup_iters * 4 * t_rest)
+    solve_s = [mvs[i] * t_d + coarse[i] * t_cg + outer[i] * t_rest for i in range(len(masses))]
+    step_s = setup_s + sum(solve_s)
     return {"value": len(masses) / step_s, "unit": "solves/s", "cores": cores, "kind": "oracle",
-            "sample": (f"oracle (OpenMP, {cores} threads) timed on this workload: one operator application "
-                       f"{t_d:.2f} s, block orthonormalisation {t_ortho:.2f} s, Galerkin build {t_build:.2f} s, "
-                       f"{k} outer MG-GCR iterations ({t_it:.3f} s each); step = setup estimate {setup_s:.0f} s + "
-                       f"{sum(outer_iters)} outer iterations ({list(outer_iters)} per mass)")}
-
-
-def oracle_iters(w, fallback):
-    """Outer iterations per mass of the oracle on this workload (stored), else the fallback."""
-    it = w.extra.get("oracle_outer_iters")
-    return list(it) if it else list(fallback)
+            "step_s": step_s, "setup_s": setup_s, "solve_s": solve_s,
+            "sample": (f"oracle (OpenMP, {cores} threads) unit costs timed here on this workload: operator "
+                       f"application {t_d:.3f} s, coarse CG iteration {t_cg * 1e3:.2f} ms, block "
+                       f"orthonormalisation {t_ortho:.2f} s, Galerkin build {t_build:.2f} s, rest of an outer "
+                       f"iteration {t_rest:.3f} s ({k} outer iterations timed); scaled by {src}: setup "
+                       f"{s_mv} applications + {s_cg} coarse iterations, solves {outer} outer / {coarse} coarse "
+                       f"iterations / {mvs} applications per mass")}
 
 
 def run_reference(args, w):
@@ -438,18 +607,20 @@ def run_reference(args, w):
     import oracle
     oracle.build()
     U, V0, srcs, masses, plaq = make_inputs(w)
-    iters = oracle_iters(w, [250] * len(masses))
-    setup_iters = mg_params(w, "fp64").setup_iters
-    t0 = time.perf_counter()
     cb = None
+    t0 = time.perf_counter()
     for _ in range(max(1, args.steps)):
-        cb = cpu_baseline(w, U, srcs, masses, V0, iters, setup_iters, budget_s=20.0)
-    dt = time.perf_counter() - t0
+        cb = cpu_baseline(w, U, srcs, masses, V0, budget_s=20.0)
+    sample_s = (time.perf_counter() - t0) / max(1, args.steps)
+    if cb is None:
+        print(json.dumps({"impl": "reference", "unavailable": f"no recorded oracle work counts for {w.name}"}))
+        return
     line = {"metric": METRIC, "value": cb["value"], "unit": "solves/s", "n_gpus": 0, "steps": args.steps,
-            "warmup": 0, "ms_per_step": 1e3 * dt / max(1, args.steps), "higher_is_better": True, "scaling": "weak",
+            "warmup": 0, "ms_per_step": 1e3 * cb["step_s"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": w.name, "lattice": "x".join(map(str, w.dims)), "nvec": w.nvec},
-            "cpu_baseline": cb,
+            "cpu_baseline": {k: v for k, v in cb.items() if k not in ("step_s", "solve_s")},
+            "sample_wall_s_per_step": sample_s,
             "e2e": {"value": cb["value"], "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

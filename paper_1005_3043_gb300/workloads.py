@@ -8,8 +8,8 @@ Re(lambda_min(D(0))) values below were computed once per field with ARPACK
 (implicitly restarted Arnoldi, which='SR') on the FP64 Wilson operator by
 tests/golden/make_masses.py; the field is bitwise reproducible on x86-64 and
 aarch64, and its plaquette is stored to detect any difference.  The oracle's
-outer MG-GCR iteration counts per mass (for scaling a timed sample of oracle
-iterations to whole solves) come from tests/golden/make_oracle_iters.py.
+own work counts on each workload (for the CPU baseline) are recorded by
+tests/golden/make_oracle_iters.py next to that script.
 """
 from __future__ import annotations
 
@@ -46,9 +46,8 @@ WILSON_8x8x8x8 = Workload(
     dims=(8, 8, 8, 8), block=(4, 4, 4, 4), nvec=8, seed=1001,
     re_lambda_min_m0=0.7985754005, plaquette=0.593627332231,
     targets=(0.01,), setup_target=0.01,
-    # the configuration's 3 setup sweeps; the oracle's outer iterations from
-    # tests/golden/make_oracle_iters.py
-    extra={"setup_iters": 3, "oracle_outer_iters": (140,)})
+    # the configuration's 3 setup sweeps
+    extra={"setup_iters": 3})
 
 # 16^3 x 32, Nv = 20, masses swept toward critical (log-spaced Re lambda_min)
 WILSON_16x16x16x32 = Workload(
@@ -59,7 +58,6 @@ WILSON_16x16x16x32 = Workload(
     # one GMRES(12) post-smoothing application per cycle (the paper's smoother;
     # 12 vectors minimise the step time of this two-level cycle, measured over
     # 6..16: 2.38 s against 8.64 s for 4 MR steps)
-    # the oracle's outer iterations from tests/golden/make_oracle_iters.py
-    extra={"smoother": 1, "smoother_steps": 12, "oracle_outer_iters": (25, 27, 29, 29, 31)})
+    extra={"smoother": 1, "smoother_steps": 12})
 
 WORKLOADS = {w.name: w for w in (WILSON_8x8x8x8, WILSON_16x16x16x32)}
