@@ -262,7 +262,7 @@ int mg_solve_batched_device(mg_ctx* ctx, const double* b_dev, double* x_dev, int
  * normal equations of the even-site Schur complement
  * Dhat = (4+m) - H_eo H_oe / (4+m) of eq. 2 (D = (4+m) - H), the odd sites
  * reconstructed as x_o = (b_o + H_oe x_e) / (4+m).  prec MG_FP32: the CG
- * iterates in FP32; each time its own residual has fallen by 1e-4 the
+ * iterates in FP32; each time its own residual has fallen by a factor 10 the
  * solution is accumulated in FP64, the residual recomputed in FP64 and the
  * CG continued from it with its search direction kept (reliable update);
  * MG_FP64: FP64 throughout.  Stops when ||b - D x|| <= tol ||b|| in

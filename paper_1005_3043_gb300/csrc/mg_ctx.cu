@@ -2029,7 +2029,7 @@ extern "C" int mg_coarse_solve_noalloc(mg_ctx* ctx, const double* rc_dev, double
 namespace {
 
 constexpr int kEoCheck = 16;   // CG iterations queued between host reads of the done flag
-constexpr double kEoInnerDelta = 1e-4;   // FP32 inner solve: residual reduction per cycle
+constexpr double kEoInnerDelta = 0.1;    // FP32 inner solve: residual reduction between reliable updates
 
 int ensure_eo(mg_ctx* ctx, int inner_bytes) {
     EoWork& w = ctx->eo;

@@ -62,7 +62,7 @@ def test_converged_solve_near_critical_8x8x8x8(prec):
     """The 8^4 beta = 6.0 field at Re(lambda_min) = 0.01: true residual <= 1e-10
     with the oracle's operator; FP64 iterations within 1 % (and 2) of the
     oracle's, mixed precision within 5 % (its FP32 CG replaces its residual
-    by the FP64 one every 1e-4 of reduction and keeps its direction)."""
+    by the FP64 one every factor 10 of reduction and keeps its direction)."""
     L, B, nv, U, m = c1_workload()
     b = synth.gaussian_spinor(L, 7)
     x_ref, it_ref, _, rel_ref, st_ref = oracle.eo_cg(U, b, m, L, 1e-10, 100000)
