@@ -139,7 +139,7 @@ def mg_params(w, prec):
     p.setup_group = 4          # Sec. IV: 10 relaxations, then groups of 4 prototypes,
     p.setup_iters = w.extra.get("setup_iters", 5)   # each refined by 5 truncated-MG iterations
     p.setup_init_relax = 10
-    p.gcr_restart = 16
+    p.gcr_restart = w.extra.get("gcr_restart", 16)
     p.tol = 1e-10
     p.max_outer = 4000
     p.smoother = w.extra.get("smoother", 0)                # 0: MR steps; 1: one GMRES(steps) application
@@ -169,6 +169,66 @@ def one_step_rate(wmg, torch, w, prec, U, dV0, dB, dX, masses, stream):
     mg.close()
     ms = e0.elapsed_time(e1)
     return len(masses) / (ms / 1e3), ms, iters
+
+
+def batched_leg(wmg, torch, stream, prec, name="wilson_24x24x24x64_nv24_beta6_76rhs", n_single=4):
+    """Many right-hand sides on the 24^3 x 64 workload (Nv = 24, 48 coarse dof):
+    12 spin-colour point sources at the origin + 64 Gaussian sources in one
+    batched solve (lockstep flexible GCR(8), the coarse solve of all sources
+    one CGLS on an RHS panel with the tensor-core stencil, its iterations
+    replayed from a CUDA graph), against n_single of the same sources solved
+    one at a time (the single-source path, on-chip or persistent coarse CG).
+    Setup once at the workload's mass; both timed with CUDA events."""
+    import synth
+    w = WORKLOADS[name]
+    U = synth.gauge_field(w.dims, beta=w.beta, sweeps=w.sweeps, n_or=w.n_or, seed=w.seed)
+    plaq = synth.plaquette(U, w.dims)
+    if abs(plaq - w.plaquette) > 1e-10:
+        raise RuntimeError(f"{name}: plaquette {plaq!r} differs from the recorded {w.plaquette!r}")
+    pts = [synth.point_source(w.dims, 0, sp, c) for sp in range(4) for c in range(3)]
+    gs = [synth.gaussian_spinor(w.dims, w.source_seed, stream=200 + i) for i in range(w.extra["gaussian_sources"])]
+    src = np.stack(pts + gs)
+    del pts, gs
+    V0 = synth.gaussian_vectors(w.dims, w.nvec, w.setup_seed)
+    mg = wmg.WilsonMG(w.dims, mg_params(w, prec), stream=stream)
+    mg.set_links(U)
+    mg.set_mass(w.setup_mass())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    mg.setup(V0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    setup_ms = e0.elapsed_time(e1)
+    dB = torch.from_numpy(src.view(np.float64)).cuda()
+    dX = torch.empty_like(dB)
+    del src
+    mg.solve_batched_device(dB[:2], dX[:2], 2)       # warm-up: workspace, graph capture, autotuner
+    e0.record(stream)
+    binfo = mg.solve_batched_device(dB, dX, dB.shape[0])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    bms = e0.elapsed_time(e1)
+    pick = list(range(n_single // 2)) + list(range(12, 12 + n_single - n_single // 2))
+    mg.solve_device(dB[0], dX[0])                   # warm-up of the single-source path
+    e0.record(stream)
+    sinfo = [mg.solve_device(dB[i], dX[i]) for i in pick]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sms = e0.elapsed_time(e1)
+    mg.close()
+    del dB, dX
+    n = len(binfo)
+    out = {"workload": name, "lattice": "x".join(map(str, w.dims)), "nvec": w.nvec, "mass": w.setup_mass(),
+           "plaquette": plaq, "sources": n, "gcr_restart": w.extra["gcr_restart"], "prec_inner": prec,
+           "setup_ms": setup_ms, "batched_ms": bms, "batched_solves_per_s": n / (bms / 1e3),
+           "batched_outer_iters": [b["outer_iters"] for b in binfo],
+           "batched_max_true_rel_res": max(b["true_rel_res"] for b in binfo),
+           "batched_status": sorted({b["status"] for b in binfo}),
+           "single_sources": pick, "single_ms": sms, "single_solves_per_s": len(pick) / (sms / 1e3),
+           "single_outer_iters": [i["outer_iters"] for i in sinfo],
+           "single_max_true_rel_res": max(i["true_rel_res"] for i in sinfo)}
+    out["batched_over_single"] = out["batched_solves_per_s"] / out["single_solves_per_s"]
+    return out
 
 
 def three_level_leg(wmg, torch, w, U, dV0, dB, dX, masses, stream, prec, nv2=32, block2=(2, 2, 2, 2)):
@@ -447,7 +507,7 @@ def run_ours(args, w):
         if "plain_fp64" in extra:
             extra["vs_plain_fp64"] = value / world / extra["plain_fp64"]["value"]
         bsrc = batch_sources(w)
-        mgb = wmg.WilsonMG(w.dims, mg_params(w, "fp32"), stream=stream)
+        mgb = wmg.WilsonMG(w.dims, mg_params(w, args.prec), stream=stream)
         mgb.set_links(U)
         mgb.set_mass(w.setup_mass())
         mgb.setup_device(dV0)
@@ -469,6 +529,7 @@ def run_ours(args, w):
 
     if not args.quick:
         extra["three_level"] = three_level_leg(wmg, torch, w, U, dV0, dB, dX, masses, stream, args.prec)
+        extra["batched_24x24x24x64"] = batched_leg(wmg, torch, stream, args.prec)
         extra["eo_cg"] = eo_cg_leg(wmg, torch, w, U, dB, dX, masses, infos[:n_solve], stream)
         extra["dslash_24x24x24x64"] = dslash_beyond_l2(wmg, torch, stream, peak)
 
