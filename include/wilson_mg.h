@@ -221,6 +221,38 @@ int mg_get_level2_op(mg_ctx* ctx, double* A2);
  * solve's inner precision. */
 int mg_kcycle(mg_ctx* ctx, const double* r1, double* e1, int prec);
 
+/* ---- the learned setup ------------------------------------------------------
+ * The paper has no network: this one stands in for the random-start
+ * relaxation that begins the Sec. IV setup (10 relaxation steps on each random
+ * vector, a polynomial in the hopping term of eq. 2).  A gauge-covariant
+ * parallel-transport convolution: four linear layers with 1, 8, 8, 8, 1
+ * channels, out[a](x) = sum_b sum_d W[a][b][d] (T_d in[b])(x) over the site
+ * (d = 0) and its eight neighbours (d = 1 + 2 mu: x + mu, 2 + 2 mu: x - mu),
+ * (T_{+mu} p)(x) = U_mu(x) p(x + mu), (T_{-mu} p)(x) = U_mu(x - mu)^dag
+ * p(x - mu), the antiperiodic sign across the t boundary, W[a][b][d] a 4x4
+ * complex spin matrix.  Weights: 20736 complex doubles, the layers in order,
+ * each [Cout][Cin][d 9][s 4][t 4] (out_s += W_st in_t).  Inputs eta: host
+ * random fine spinors (boundary layout); the outputs are its prototypes.
+ * Training target: the block projector P P^dag of the context's current level
+ * (the plain setup's, eq. 4); loss |(1 - P P^dag) v|^2 / |v|^2 averaged over
+ * the starts; gradient the Wirtinger 2 dLoss/d conj(W) in the weights' layout.
+ * FP32 kernels, FP64 gradient sums and weights. */
+int mg_nn_set_weights(mg_ctx* ctx, const double* W, int ncomplex);
+int mg_nn_get_weights(mg_ctx* ctx, double* W, int ncomplex);
+/* v_i = network(eta_i), i < n (host fine spinors). */
+int mg_nn_forward(mg_ctx* ctx, const double* eta, double* v, int n);
+/* loss (and, with grad != NULL, its gradient) over n starts; needs a level. */
+int mg_nn_loss_grad(mg_ctx* ctx, const double* eta, int n, double* loss, double* grad);
+/* steps Adam steps (learning rate lr, betas 0.9 / 0.999) on the current links
+ * and level, each over the n starts; the mean loss of the first and of the
+ * last step (each before its update) in *loss_first, *loss_last (may be NULL). */
+int mg_nn_train(mg_ctx* ctx, const double* eta, int n, int steps, double lr, double* loss_first, double* loss_last);
+/* The learned setup: prototypes v_i = network(eta_i), i < nvec, normalised,
+ * then (refine_iters > 0) the Sec. IV group refinement with refine_iters
+ * truncated-cycle iterations per prototype (no relaxation), then P and D_c
+ * (eq. 4, Sec. III).  info.setup_ms of later solves reports its device time. */
+int mg_setup_learned(mg_ctx* ctx, const double* eta, int refine_iters);
+
 /* Read back the current prototypes V (the near-null vectors of Sec. II;
  * host, Nv fine vectors). */
 int mg_get_null_vectors(mg_ctx* ctx, double* V);

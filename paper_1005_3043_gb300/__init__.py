@@ -79,6 +79,12 @@ _SIGS = {
     "mg_get_prolongator": ([_P, _P], _I),
     "mg_get_null_vectors": ([_P, _P], _I),
     "mg_setup_level2": ([_P, _P], _I),
+    "mg_nn_set_weights": ([_P, _P, _I], _I),
+    "mg_nn_get_weights": ([_P, _P, _I], _I),
+    "mg_nn_forward": ([_P, _P, _P, _I], _I),
+    "mg_nn_loss_grad": ([_P, _P, _I, _P, _P], _I),
+    "mg_nn_train": ([_P, _P, _I, _I, _D, _P, _P], _I),
+    "mg_setup_learned": ([_P, _P, _I], _I),
     "mg_set_level2_vectors": ([_P, _P], _I),
     "mg_get_level2_prolongator": ([_P, _P], _I),
     "mg_get_level2_op": ([_P, _P], _I),
@@ -230,6 +236,62 @@ def mg_get_null_vectors(ctx, nv: int, V: int) -> np.ndarray:
     out = np.empty((nv, V, 4, 3), dtype=np.complex128)
     _check(load().mg_get_null_vectors(ctx, _ptr(out)), ctx)
     return out
+
+
+NN_PARAMS = 20736   # complex weights of the learned setup's network (layers 1-8-8-8-1)
+NN_CHANNELS = (1, 8, 8, 8, 1)
+
+
+def nn_flatten(Ws) -> np.ndarray:
+    """Layer weight arrays [Cout, Cin, 9, 4, 4] -> the flat complex vector of the C-ABI."""
+    return np.concatenate([np.ascontiguousarray(W, dtype=np.complex128).ravel() for W in Ws])
+
+
+def nn_unflatten(w) -> list:
+    out, o = [], 0
+    for ci, co in zip(NN_CHANNELS[:-1], NN_CHANNELS[1:]):
+        n = co * ci * 144
+        out.append(np.asarray(w[o:o + n]).reshape(co, ci, 9, 4, 4))
+        o += n
+    return out
+
+
+def mg_nn_set_weights(ctx, Ws) -> None:
+    w = _host(nn_flatten(Ws) if isinstance(Ws, (list, tuple)) else Ws)
+    _check(load().mg_nn_set_weights(ctx, _ptr(w), int(w.size)), ctx)
+
+
+def mg_nn_get_weights(ctx) -> list:
+    w = np.empty(NN_PARAMS, dtype=np.complex128)
+    _check(load().mg_nn_get_weights(ctx, _ptr(w), NN_PARAMS), ctx)
+    return nn_unflatten(w)
+
+
+def mg_nn_forward(ctx, etas) -> np.ndarray:
+    e = _host(etas)
+    v = np.empty_like(e)
+    _check(load().mg_nn_forward(ctx, _ptr(e), _ptr(v), int(e.shape[0])), ctx)
+    return v
+
+
+def mg_nn_loss_grad(ctx, etas, grad: bool = True):
+    e = _host(etas)
+    loss = ctypes.c_double(0)
+    g = np.empty(NN_PARAMS, dtype=np.complex128) if grad else None
+    _check(load().mg_nn_loss_grad(ctx, _ptr(e), int(e.shape[0]), ctypes.byref(loss), _ptr(g) if grad else None), ctx)
+    return loss.value, (nn_unflatten(g) if grad else None)
+
+
+def mg_nn_train(ctx, etas, steps: int, lr: float):
+    e = _host(etas)
+    l0, l1 = ctypes.c_double(0), ctypes.c_double(0)
+    _check(load().mg_nn_train(ctx, _ptr(e), int(e.shape[0]), int(steps), float(lr), ctypes.byref(l0),
+                              ctypes.byref(l1)), ctx)
+    return l0.value, l1.value
+
+
+def mg_setup_learned(ctx, etas, refine_iters: int = 0) -> None:
+    _check(load().mg_setup_learned(ctx, _ptr(_host(etas)), int(refine_iters)), ctx)
 
 
 def mg_setup_level2(ctx, V2) -> None:
@@ -491,6 +553,24 @@ class WilsonMG:
     @property
     def Vc2(self):
         return int(np.prod([d // b // c for d, b, c in zip(self.dims, self.params.block, self.params.block2)]))
+
+    def nn_set_weights(self, Ws):
+        mg_nn_set_weights(self.ctx, Ws)
+
+    def nn_get_weights(self):
+        return mg_nn_get_weights(self.ctx)
+
+    def nn_forward(self, etas):
+        return mg_nn_forward(self.ctx, etas)
+
+    def nn_loss_grad(self, etas, grad=True):
+        return mg_nn_loss_grad(self.ctx, etas, grad)
+
+    def nn_train(self, etas, steps, lr):
+        return mg_nn_train(self.ctx, etas, steps, lr)
+
+    def setup_learned(self, etas, refine_iters=0):
+        mg_setup_learned(self.ctx, etas, refine_iters)
 
     def setup_level2(self, V2):
         mg_setup_level2(self.ctx, V2)

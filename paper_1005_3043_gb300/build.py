@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libwilson_mg.so")
 SOURCES = ["kernels_fine.cu", "kernels_half.cu", "kernels_coarse.cu", "kernels_batched.cu", "kernels_cgls.cu",
-           "kernels_eo.cu", "kernels_level2.cu", "mg_ctx.cu"]
+           "kernels_eo.cu", "kernels_level2.cu", "kernels_learn.cu", "mg_ctx.cu"]
 HEADERS = ["mg_common.cuh", "mg_launch.h", "mg_ptx.cuh", "mg_sync.cuh", "mg_wilson.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=default"]

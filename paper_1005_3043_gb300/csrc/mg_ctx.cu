@@ -79,6 +79,27 @@ struct EoWork {
     int inner_bytes = 0;      // 8: FP32 inner vectors, 16: FP64
 };
 
+// The learned setup's network: 4 parallel-transport layers, 1-8-8-8-1 channels.
+struct NnState {
+    static constexpr int kLayers = 4;
+    static constexpr int kCh[kLayers + 1] = {1, 8, 8, 8, 1};
+    float2* W[kLayers] = {};    // FP32 weights used by the kernels
+    float2* Wt[kLayers] = {};   // their adjoints (input-gradient pass)
+    double2* Wm = nullptr;      // FP64 master weights, all layers
+    double2 *G = nullptr, *m = nullptr, *v = nullptr;   // gradient and Adam moments
+    int off[kLayers + 1] = {};  // complex offsets of the layers in Wm / G
+    float2* act = nullptr;      // activations x0..x4: 26 fine vectors
+    float2* ga = nullptr;       // gradient of a layer's output (8 fine vectors)
+    float2* gb = nullptr;       // gradient of its input
+    float2* part = nullptr;     // weight-gradient partial sums
+    float2* r = nullptr;        // (1 - P P^dag) v
+    float2* cvec = nullptr;     // coarse temporary (cvec_nv prototypes)
+    int cvec_nv = 0;
+    int step = 0;
+    bool ready = false, weights = false;
+};
+constexpr int NnState::kCh[];
+
 // Work vectors of the three-level method on level 1 (sized for the level-1
 // lattice) and of its level-2 coarse solve.
 template <typename T> struct L1Work {
@@ -153,6 +174,7 @@ struct mg_ctx {
     double2* protos2_t = nullptr;
     L1Work<float> l1f;
     L1Work<double> l1d;
+    NnState nn;
     Work<float> wf;
     Work<double> wd;
     Reduce R{};
@@ -1570,6 +1592,222 @@ int mg_set_null_vectors(mg_ctx* ctx, const double* V, int nv) {
     return build_level(ctx, ctx->full, ctx->protos, nv);
 }
 
+// ---- the learned setup (gauge-covariant parallel-transport network)
+}  // extern "C"
+namespace {
+constexpr int kNnParams = 20736;   // complex weights: 1152 + 9216 + 9216 + 1152
+int ensure_nn(mg_ctx* ctx) {
+    NnState& q = ctx->nn;
+    if (q.ready) return MG_OK;
+    const size_t n = nfine(ctx);
+    int o = 0;
+    for (int k = 0; k < NnState::kLayers; ++k) {
+        q.off[k] = o;
+        const int c = NnState::kCh[k] * NnState::kCh[k + 1] * 144;
+        TRY(dalloc(ctx, &q.W[k], sizeof(float2) * c));
+        TRY(dalloc(ctx, &q.Wt[k], sizeof(float2) * c));
+        o += c;
+    }
+    q.off[NnState::kLayers] = o;
+    TRY(dalloc(ctx, &q.Wm, sizeof(double2) * o));
+    TRY(dalloc(ctx, &q.G, sizeof(double2) * o));
+    TRY(dalloc(ctx, &q.m, sizeof(double2) * o));
+    TRY(dalloc(ctx, &q.v, sizeof(double2) * o));
+    TRY(dalloc(ctx, &q.act, sizeof(float2) * n * 26));
+    TRY(dalloc(ctx, &q.ga, sizeof(float2) * n * 8));
+    TRY(dalloc(ctx, &q.gb, sizeof(float2) * n * 8));
+    TRY(dalloc(ctx, &q.part, sizeof(float2) * (size_t)nn_wgrad_blocks(ctx->g) * 576 * 16));
+    TRY(dalloc(ctx, &q.r, sizeof(float2) * n));
+    CK(cudaMemsetAsync(q.m, 0, sizeof(double2) * o, ctx->st));
+    CK(cudaMemsetAsync(q.v, 0, sizeof(double2) * o, ctx->st));
+    q.ready = true;
+    return MG_OK;
+}
+// FP32 weights and their adjoints from the FP64 master copy
+int nn_refresh(mg_ctx* ctx) {
+    NnState& q = ctx->nn;
+    for (int k = 0; k < NnState::kLayers; ++k) {
+        convert<double, float>(q.W[k], q.Wm + q.off[k], (size_t)(q.off[k + 1] - q.off[k]), ctx->st);
+        nn_adjoint_weights(q.Wt[k], q.W[k], NnState::kCh[k], NnState::kCh[k + 1], ctx->st);
+    }
+    CKL();
+    return MG_OK;
+}
+float2* nn_act(mg_ctx* ctx, int k) {   // activation k (channels kCh[k]) inside act
+    size_t c = 0;
+    for (int j = 0; j < k; ++j) c += NnState::kCh[j];
+    return ctx->nn.act + c * nfine(ctx);
+}
+// x0 = eta (internal FP32, in act), then x1..x4
+int nn_forward(mg_ctx* ctx) {
+    NnState& q = ctx->nn;
+    for (int k = 0; k < NnState::kLayers; ++k)
+        CK(nn_layer(nn_act(ctx, k + 1), nn_act(ctx, k), q.W[k], ctx->U32, ctx->g, NnState::kCh[k], NnState::kCh[k + 1],
+                    ctx->st));
+    return MG_OK;
+}
+// loss |(1 - P P^dag) v|^2 / |v|^2 of x4 into scal[S_NORM_B] / scal[S_NORM_A] and,
+// with grad, the gradient (scaled by gscale) added to G
+enum { NN_V2 = S_EO + 10, NN_R2 = S_EO + 11 };
+int nn_loss_grad(mg_ctx* ctx, bool grad, double gscale) {
+    NnState& q = ctx->nn;
+    const size_t n = nfine(ctx);
+    const CoarseLevel& L = ctx->full;
+    if (q.cvec_nv < L.nv) {   // sized by the current level (nvec may change with mg_set_params)
+        if (q.cvec) {
+            CK(cudaStreamSynchronize(ctx->st));
+            dfree(ctx, q.cvec);
+        }
+        TRY(dalloc(ctx, &q.cvec, sizeof(float2) * (size_t)ctx->g.Vc * 2 * L.nv));
+        q.cvec_nv = L.nv;
+    }
+    float2* v = reinterpret_cast<float2*>(nn_act(ctx, NnState::kLayers));
+    restrict_<float>((v2<float>*)q.cvec, L.P32, (const v2<float>*)v, L.nv, ctx->g, ctx->st);
+    prolong<float>((v2<float>*)q.r, L.P32, (const v2<float>*)q.cvec, L.nv, ctx->g, ctx->st);
+    scale<float>((v2<float>*)q.r, n, -1.0, ctx->st);
+    axpy<float>((v2<float>*)q.r, (const v2<float>*)v, n, 1.0, 0.0, ctx->st);
+    norm2<float>((const v2<float>*)v, n, NN_V2, ctx->R, ctx->st);
+    norm2<float>((const v2<float>*)q.r, n, NN_R2, ctx->R, ctx->st);
+    CKL();
+    if (!grad) return MG_OK;
+    nn_seed(q.ga, q.r, v, n, ctx->R.scal, NN_V2, NN_R2, ctx->st);
+    float2* gout = q.ga;
+    float2* gin = q.gb;
+    for (int k = NnState::kLayers - 1; k >= 0; --k) {
+        const int ci = NnState::kCh[k], co = NnState::kCh[k + 1];
+        CK(nn_wgrad(q.G + q.off[k], q.part, gout, nn_act(ctx, k), ctx->U32, ctx->g, ci, co, 2.0 * gscale, ctx->st));
+        if (k > 0) {
+            CK(nn_layer(gin, gout, q.Wt[k], ctx->U32, ctx->g, co, ci, ctx->st));
+            std::swap(gout, gin);
+        }
+    }
+    return MG_OK;
+}
+int nn_need(mg_ctx* ctx) {
+    TRY(need_links(ctx));
+    if (!ctx->nn.weights) return fail(ctx, MG_ERR_NOT_SETUP, "no network weights: call mg_nn_set_weights");
+    return MG_OK;
+}
+// n host random starts (boundary layout) -> x0 of start i in act
+int nn_upload_start(mg_ctx* ctx, const double* eta_host, int i) {
+    const size_t n = nfine(ctx);
+    CK(cudaMemcpyAsync(ctx->stage_a, eta_host + 2 * (size_t)i * n, sizeof(double2) * n, cudaMemcpyHostToDevice, ctx->st));
+    spinor_to_internal<float>((v2<float>*)nn_act(ctx, 0), ctx->stage_a, ctx->g, ctx->st);
+    CKL();
+    return MG_OK;
+}
+}  // namespace
+extern "C" {
+
+int mg_nn_set_weights(mg_ctx* ctx, const double* W, int ncomplex) {
+    if (!ctx || !W) return MG_ERR_INVALID_ARG;
+    if (ncomplex != kNnParams) return fail(ctx, MG_ERR_INVALID_ARG, "the network has 20736 complex weights");
+    TRY(ensure_nn(ctx));
+    CK(cudaMemcpyAsync(ctx->nn.Wm, W, sizeof(double2) * kNnParams, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemsetAsync(ctx->nn.m, 0, sizeof(double2) * kNnParams, ctx->st));
+    CK(cudaMemsetAsync(ctx->nn.v, 0, sizeof(double2) * kNnParams, ctx->st));
+    ctx->nn.step = 0;
+    TRY(nn_refresh(ctx));
+    CK(cudaStreamSynchronize(ctx->st));
+    ctx->nn.weights = true;
+    return MG_OK;
+}
+
+int mg_nn_get_weights(mg_ctx* ctx, double* W, int ncomplex) {
+    if (!ctx || !W) return MG_ERR_INVALID_ARG;
+    if (ncomplex != kNnParams) return fail(ctx, MG_ERR_INVALID_ARG, "the network has 20736 complex weights");
+    if (!ctx->nn.weights) return fail(ctx, MG_ERR_NOT_SETUP, "no network weights");
+    CK(cudaMemcpyAsync(W, ctx->nn.Wm, sizeof(double2) * kNnParams, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return MG_OK;
+}
+
+int mg_nn_forward(mg_ctx* ctx, const double* eta, double* v, int n) {
+    if (!ctx || !eta || !v || n <= 0) return MG_ERR_INVALID_ARG;
+    TRY(nn_need(ctx));
+    const size_t nf = nfine(ctx);
+    for (int i = 0; i < n; ++i) {
+        TRY(nn_upload_start(ctx, eta, i));
+        TRY(nn_forward(ctx));
+        spinor_from_internal<float>(ctx->stage_b, (const v2<float>*)nn_act(ctx, NnState::kLayers), ctx->g, ctx->st);
+        CKL();
+        CK(cudaMemcpyAsync(v + 2 * (size_t)i * nf, ctx->stage_b, sizeof(double2) * nf, cudaMemcpyDeviceToHost, ctx->st));
+    }
+    CK(cudaStreamSynchronize(ctx->st));
+    return MG_OK;
+}
+
+int mg_nn_loss_grad(mg_ctx* ctx, const double* eta, int n, double* loss, double* grad) {
+    if (!ctx || !eta || n <= 0) return MG_ERR_INVALID_ARG;
+    TRY(nn_need(ctx));
+    TRY(need_level(ctx));
+    CK(cudaMemsetAsync(ctx->nn.G, 0, sizeof(double2) * kNnParams, ctx->st));
+    double tot = 0;
+    for (int i = 0; i < n; ++i) {
+        TRY(nn_upload_start(ctx, eta, i));
+        TRY(nn_forward(ctx));
+        TRY(nn_loss_grad(ctx, grad != nullptr, 1.0 / n));
+        TRY(read_scalars(ctx, NN_V2, 2));
+        tot += ctx->h_scal[NN_R2] / ctx->h_scal[NN_V2];
+    }
+    if (loss) *loss = tot / n;
+    if (grad) {
+        CK(cudaMemcpyAsync(grad, ctx->nn.G, sizeof(double2) * kNnParams, cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+    }
+    return MG_OK;
+}
+
+int mg_nn_train(mg_ctx* ctx, const double* eta, int n, int steps, double lr, double* loss_first, double* loss_last) {
+    if (!ctx || !eta || n <= 0 || steps <= 0 || !(lr > 0)) return MG_ERR_INVALID_ARG;
+    TRY(nn_need(ctx));
+    TRY(need_level(ctx));
+    NnState& q = ctx->nn;
+    for (int it = 0; it < steps; ++it) {
+        double l = 0;
+        CK(cudaMemsetAsync(q.G, 0, sizeof(double2) * kNnParams, ctx->st));
+        for (int i = 0; i < n; ++i) {
+            TRY(nn_upload_start(ctx, eta, i));
+            TRY(nn_forward(ctx));
+            TRY(nn_loss_grad(ctx, true, 1.0 / n));
+            TRY(read_scalars(ctx, NN_V2, 2));
+            l += ctx->h_scal[NN_R2] / ctx->h_scal[NN_V2] / n;
+        }
+        q.step += 1;
+        nn_adam(nullptr, q.Wm, q.G, q.m, q.v, kNnParams, lr, 0.9, 0.999, 1e-8, q.step, ctx->st);   // Adam on the FP64 weights
+        TRY(nn_refresh(ctx));
+        if (it == 0 && loss_first) *loss_first = l;
+        if (loss_last) *loss_last = l;
+    }
+    CK(cudaStreamSynchronize(ctx->st));
+    return MG_OK;
+}
+
+int mg_setup_learned(mg_ctx* ctx, const double* eta, int refine_iters) {
+    if (!ctx || !eta || refine_iters < 0) return MG_ERR_INVALID_ARG;
+    TRY(nn_need(ctx));
+    TRY(ensure_protos(ctx));
+    const size_t n = nfine(ctx);
+    const int nv = ctx->prm.nvec;
+    CK(cudaEventRecord(ctx->ev0, ctx->st));
+    for (int i = 0; i < nv; ++i) {
+        TRY(nn_upload_start(ctx, eta, i));
+        TRY(nn_forward(ctx));
+        convert<float, double>(ctx->protos + (size_t)i * n, (const v2<float>*)nn_act(ctx, NnState::kLayers), n,
+                               ctx->st);
+        norm2<double>(ctx->protos + (size_t)i * n, n, S_NORM_A, ctx->R, ctx->st);
+        normalize_dev<double>(ctx->protos + (size_t)i * n, n, S_NORM_A, ctx->R, ctx->st);
+    }
+    CKL();
+    const int relax = ctx->prm.setup_init_relax, iters = ctx->prm.setup_iters;
+    ctx->prm.setup_init_relax = 0;
+    ctx->prm.setup_iters = refine_iters;
+    const int st = run_setup(ctx);
+    ctx->prm.setup_init_relax = relax;
+    ctx->prm.setup_iters = iters;
+    return st;
+}
+
 // ---- the third level
 }  // extern "C"
 namespace {
@@ -2375,6 +2613,7 @@ int solve_batched_impl(mg_ctx* ctx, int nrhs, mg_solve_info* infos) {
     std::vector<int> iters(nrhs, 0), restarts(nrhs, 0), status(nrhs, MG_ERR_NOT_CONVERGED), kk(nrhs, 0),
         active(nrhs, 1), cycle_end(nrhs, 0), mv(nrhs, 0);
     std::vector<double> mvb(nrhs, 0.0);   // bytes per site of the fine operator applications
+    std::string why;                      // the first numeric failure, for the error message
     auto RR = [&](int r) {
         Reduce R = ctx->R;
         R.scal = b.scal + (size_t)r * S_COUNT;
@@ -2449,7 +2688,14 @@ int solve_batched_impl(mg_ctx* ctx, int nrhs, mg_solve_info* infos) {
                 ++kk[r];
                 ++iters[r];
                 double pn = sc[S_GCR_PN2];
-                if (!(pn > 0) || !std::isfinite(pn)) { status[r] = MG_ERR_NUMERIC; active[r] = 0; continue; }
+                if (!(pn > 0) || !std::isfinite(pn)) {
+                    status[r] = MG_ERR_NUMERIC;
+                    active[r] = 0;
+                    if (why.empty())
+                        why = "source " + std::to_string(r) + ": GCR breakdown, |D z|^2 = " + std::to_string(pn) +
+                              " at outer iteration " + std::to_string(iters[r]);
+                    continue;
+                }
                 rnorm[r] = std::sqrt(sc[S_GCR_R2]);
                 if (rnorm[r] <= p.tol * bnorm[r] || (p.delta > 0 && rnorm[r] <= p.delta * rcycle[r]) || kk[r] >= K ||
                     iters[r] >= p.max_outer)
@@ -2502,7 +2748,13 @@ int solve_batched_impl(mg_ctx* ctx, int nrhs, mg_solve_info* infos) {
             kk[r] = 0;
             cycle_end[r] = 0;
             rcycle[r] = rnorm[r];
-            if (!std::isfinite(rel[r])) { status[r] = MG_ERR_NUMERIC; active[r] = 0; }
+            if (!std::isfinite(rel[r])) {
+                status[r] = MG_ERR_NUMERIC;
+                active[r] = 0;
+                if (why.empty())
+                    why = "source " + std::to_string(r) + ": non-finite true residual after outer iteration " +
+                          std::to_string(iters[r]);
+            }
             else if (rel[r] <= p.tol) { status[r] = MG_OK; active[r] = 0; }
             else if (iters[r] >= p.max_outer) { status[r] = MG_ERR_NOT_CONVERGED; active[r] = 0; }
         }
@@ -2527,7 +2779,7 @@ int solve_batched_impl(mg_ctx* ctx, int nrhs, mg_solve_info* infos) {
         if (status[r] == MG_ERR_NUMERIC) worst = MG_ERR_NUMERIC;
         else if (status[r] == MG_ERR_NOT_CONVERGED && worst == MG_OK) worst = MG_ERR_NOT_CONVERGED;
     }
-    if (worst == MG_ERR_NUMERIC) ctx->err = "non-finite residual or GCR breakdown in a batched source";
+    if (worst == MG_ERR_NUMERIC) ctx->err = "batched solve: " + why;
     if (worst == MG_ERR_NOT_CONVERGED) ctx->err = "max_outer reached for a batched source";
     return worst;
 }

@@ -194,6 +194,7 @@ struct CglsShape {
     int red_n;       // complex entries per reduction buffer
     int tm;          // 1: the operator in tensor memory (all 512 columns of the SM)
     int tm_chunks;   // 32-column TMEM chunks per thread
+    int own_off;     // byte offset of the own-row vectors of the tagged form in shared memory (0: global)
     size_t smem;     // dynamic shared memory per CTA
 };
 enum { CGLS_AUTO = 0, CGLS_STREAM = 2, CGLS_SMEM = 3 };
@@ -264,6 +265,18 @@ void prolong_l2(v2<T>* e1, const v2<T>* P2, const v2<T>* y2, int nv1, int nv2, c
 bool build_l2_supported(int nv1, int nv2);
 cudaError_t coarse_build_l2(double2* A2, const double2* P2, const double2* A1, int nv1, int nv2, const Geom& g1,
                             const Geom& g2, cudaStream_t st);
+
+// ---------------------------------------------------------------- learned setup (parallel-transport network)
+cudaError_t nn_layer(float2* out, const float2* in, const float2* W, const float2* U, const Geom& g, int cin, int cout,
+                     cudaStream_t st);
+int nn_wgrad_blocks(const Geom& g);
+cudaError_t nn_wgrad(double2* G, float2* part, const float2* gout, const float2* in, const float2* U, const Geom& g,
+                     int cin, int cout, double scale, cudaStream_t st);
+void nn_seed(float2* gout, const float2* r, const float2* v, size_t n, const double* scal, int vslot, int rslot,
+             cudaStream_t st);
+void nn_adam(float2* W, double2* Wm, const double2* G, double2* m, double2* v, int n, double lr, double b1, double b2,
+             double eps, int t, cudaStream_t st);
+void nn_adjoint_weights(float2* Wt, const float2* W, int cin, int cout, cudaStream_t st);
 
 // Orders this process's TMEM-kernel launches across streams: construct before
 // a launch (the stream then waits for the previous TMEM launch if that was on
