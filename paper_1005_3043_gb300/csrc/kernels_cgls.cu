@@ -103,9 +103,17 @@ struct CglsPhase {
     const unsigned long long* tin;
     unsigned long long *tout, *ts, *tu;
     unsigned int etag, etag_out;
+    int own_out;   // EPI_TAG with own-row vectors in shared memory: the one (OV_S, OV_U) that keeps out
+    bool stop;   // set by phase when its pre-emit step declined the epilogue
 };
 enum { ST_IN = 0, ST_P = 1, ST_R = 2, ST_TAG = 3 };
+// pre-emit step of a phase: runs (collectively) between the stencil's products
+// and its epilogue; 1 = emit, 0 = stop without emitting, -1 = failure
+struct NoPre {
+    __device__ int operator()() const { return 1; }
+};
 enum { EPI_STORE = 0, EPI_TAG = 1, EPI_CG_TAG = 2 };
+enum { OV_P = 0, OV_Z = 1, OV_Q = 2, OV_Y = 3, OV_R = 4, OV_S = 5, OV_U = 6, OV_COUNT = 7 };
 
 constexpr int kStageRegs = 4;   // staged operand entries per thread kept as precomputed offsets
 
@@ -122,6 +130,10 @@ template <bool H16, bool TM> struct CglsCta {
     cx<float>* red;
     cx<float>* xs;
     unsigned char* slots;
+    // own-row vectors of the tagged form in shared memory (nullptr: in global
+    // memory): [OV_* 7][own row], own row = the index of the row among the CTA's
+    cx<float>* ov = nullptr;
+    int ov_n = 0;
     int buf = 0;
     long long gw_next = 0;     // next wave to consume (all threads)
     long long gw_issued = 0;   // next wave to copy (thread 0)
@@ -155,6 +167,10 @@ template <bool H16, bool TM> struct CglsCta {
         red = reinterpret_cast<cx<float>*>(sm + 256);
         xs = red + (resident ? 1 : 2) * a.sh.red_n;
         slots = sm + a.sh.slot_off;
+        if (a.sh.own_off > 0 && a.form == CGLS_CG_TAGGED) {
+            ov = reinterpret_cast<cx<float>*>(sm + a.sh.own_off);
+            ov_n = a.sh.nu_max * RU;
+        }
         pre = nX * K <= kStageRegs * (int)blockDim.x;
         if (pre) {
 #pragma unroll
@@ -293,33 +309,66 @@ template <bool H16, bool TM> struct CglsCta {
         return v;
     }
 
-    // output row o = X * nc + row of the stencil: EPI_STORE / EPI_TAG store it
-    // (n0 += |out|^2); EPI_CG_TAG applies the updates (n0 += |s'|^2, n1 += |r'|^2)
-    template <int EPI> __device__ __forceinline__ void emit(const CglsPhase& ph, size_t o, cx<float> w, float& n0,
+    // output row o = X * nc + row of the stencil (own row j of the CTA): EPI_STORE /
+    // EPI_TAG store it (n0 += |out|^2); EPI_CG_TAG applies the updates
+    // (n0 += |s'|^2, n1 += |r'|^2), on the own-row vectors in shared memory when
+    // the shape has room for them
+    template <int EPI> __device__ __forceinline__ void emit(const CglsPhase& ph, size_t o, int j, cx<float> w, float& n0,
                                                             float& n1) {
         if (EPI == EPI_STORE) {
             st<float>(ph.out + o, w);
             n0 += norm2(w);
         } else if (EPI == EPI_TAG) {
             tag_store(ph.tout + 2 * o, w.r, w.i, ph.etag_out);
+            if (ov) ov[ph.own_out * ov_n + j] = w;
             n0 += norm2(w);
         } else if (EPI == EPI_CG_TAG) {
-            float2 s2, u2;
-            tag_load(ph.ts + 2 * o, 0u, s2);   // own entries, written by this CTA
-            tag_load(ph.tu + 2 * o, 0u, u2);
-            const cx<float> s(s2.x, s2.y), u(u2.x, u2.y);
+            cx<float> s, u, p0, z0, q0, y0, r0;
+            if (ov) {
+                s = ov[OV_S * ov_n + j];
+                u = ov[OV_U * ov_n + j];
+                y0 = ov[OV_Y * ov_n + j];
+                r0 = ov[OV_R * ov_n + j];
+                if (!ph.first) {
+                    p0 = ov[OV_P * ov_n + j];
+                    z0 = ov[OV_Z * ov_n + j];
+                    q0 = ov[OV_Q * ov_n + j];
+                }
+            } else {
+                float2 s2, u2;
+                tag_load(ph.ts + 2 * o, 0u, s2);   // own entries, written by this CTA
+                tag_load(ph.tu + 2 * o, 0u, u2);
+                s = cx<float>(s2.x, s2.y);
+                u = cx<float>(u2.x, u2.y);
+                y0 = ld<float>(ph.cy + o);
+                r0 = ld<float>(ph.cr + o);
+                if (!ph.first) {
+                    p0 = ld<float>(ph.cp + o);
+                    z0 = ld<float>(ph.cz + o);
+                    q0 = ld<float>(ph.cq + o);
+                }
+            }
             cx<float> p = s, z = w, q = u;
             if (!ph.first) {
-                p = p + ph.beta * ld<float>(ph.cp + o);
-                z = z + ph.beta * ld<float>(ph.cz + o);
-                q = q + ph.beta * ld<float>(ph.cq + o);
+                p = p + ph.beta * p0;
+                z = z + ph.beta * z0;
+                q = q + ph.beta * q0;
             }
-            const cx<float> sn = s - ph.alpha * z, rn = ld<float>(ph.cr + o) - ph.alpha * q;
-            st<float>(ph.cp + o, p);
-            st<float>(ph.cz + o, z);
-            st<float>(ph.cq + o, q);
-            st<float>(ph.cy + o, ld<float>(ph.cy + o) + ph.alpha * p);
-            st<float>(ph.cr + o, rn);
+            const cx<float> sn = s - ph.alpha * z, rn = r0 - ph.alpha * q, yn = y0 + ph.alpha * p;
+            if (ov) {
+                ov[OV_P * ov_n + j] = p;
+                ov[OV_Z * ov_n + j] = z;
+                ov[OV_Q * ov_n + j] = q;
+                ov[OV_Y * ov_n + j] = yn;
+                ov[OV_R * ov_n + j] = rn;
+                ov[OV_S * ov_n + j] = sn;
+            } else {
+                st<float>(ph.cp + o, p);
+                st<float>(ph.cz + o, z);
+                st<float>(ph.cq + o, q);
+                st<float>(ph.cy + o, yn);
+                st<float>(ph.cr + o, rn);
+            }
             tag_store(ph.ts + 2 * o, sn.r, sn.i, ph.etag_out);
             n0 += norm2(sn);
             n1 += norm2(rn);
@@ -331,9 +380,12 @@ template <bool H16, bool TM> struct CglsCta {
     //   ST_IN: x = in
     //   ST_P : x = s + beta p_old (first: s); own entries -> p_new
     //   ST_R : x = r_old - alpha q; own entries -> r_new, y += alpha p_new, n1 += |x|^2
-    // n0 accumulates |out|^2 over the CTA's rows.
-    template <int STAGE, bool DAG, int EPI = EPI_STORE>
-    __device__ bool phase(const CglsPhase& ph, float& n0, float& n1) {
+    // n0 accumulates |out|^2 over the CTA's rows.  pre_emit() runs after the
+    // products and before the first output row is emitted (see NoPre); false
+    // on a failed wait.
+    template <int STAGE, bool DAG, int EPI = EPI_STORE, typename Pre = NoPre>
+    __device__ bool phase(CglsPhase& ph, float& n0, float& n1, Pre&& pre_emit = Pre()) {
+        ph.stop = false;
         const int T = blockDim.x;
         if (pre) {
             cx<float> v[kStageRegs];
@@ -420,12 +472,18 @@ template <bool H16, bool TM> struct CglsCta {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) red[q_ks * rows + r + q] = cx<float>(P[q].x - P[q].y, Q[q].x + Q[q].y);
             __syncthreads();
+            const int go = pre_emit();
+            if (go < 0) return false;
+            if (go == 0) {
+                ph.stop = true;
+                return true;
+            }
             for (int rr = threadIdx.x; rr < rows; rr += T) {
                 cx<float> sum = red[rr];
                 for (int ks = 1; ks < q_KS; ++ks) sum = sum + red[ks * rows + rr];
                 const int jj = rr / RU, ain = rr - jj * RU, u = u0 + jj, X = u / H, row = (u - X * H) * RU + ain;
                 if (DAG && row >= nvh) sum = cx<float>(-sum.r, -sum.i);
-                emit<EPI>(ph, (size_t)X * nc + row, sum, n0, n1);
+                emit<EPI>(ph, (size_t)X * nc + row, rr, sum, n0, n1);
             }
             return true;
         }
@@ -472,12 +530,20 @@ template <bool H16, bool TM> struct CglsCta {
                     ++gw_issued;
                 }
             }
+            if (iw == 0) {
+                const int go = pre_emit();
+                if (go < 0) return false;
+                if (go == 0) {
+                    ph.stop = true;
+                    return true;
+                }
+            }
             for (int r = threadIdx.x; r < rows; r += T) {
                 cx<float> sum = rb[r];
                 for (int ks = 1; ks < KS; ++ks) sum = sum + rb[ks * rows + r];
                 const int j = r / RU, ain = r - j * RU, u = u0 + j0 + j, X = u / H, row = (u - X * H) * RU + ain;
                 if (DAG && row >= nvh) sum = cx<float>(-sum.r, -sum.i);
-                emit<EPI>(ph, (size_t)X * nc + row, sum, n0, n1);
+                emit<EPI>(ph, (size_t)X * nc + row, j0 * RU + r, sum, n0, n1);
             }
             if (!resident) buf ^= 1;
         }
@@ -583,8 +649,13 @@ template <bool H16, bool TM> __device__ void cgls_body_tag(const CglsArgs& a, Cg
         const int j = i / c.RU, ain = i - j * c.RU, u = c.u0 + j, X = u / c.H;
         const size_t o = (size_t)X * c.nc + (u - X * c.H) * c.RU + ain;
         const float2 v = a.rc[o];
-        a.r[o] = v;
-        a.y[o] = make_float2(0.f, 0.f);
+        if (c.ov) {
+            c.ov[OV_R * c.ov_n + i] = cx<float>(v.x, v.y);
+            c.ov[OV_Y * c.ov_n + i] = cx<float>(0.f, 0.f);
+        } else {
+            a.r[o] = v;
+            a.y[o] = make_float2(0.f, 0.f);
+        }
         one[0] += v.x * v.x + v.y * v.y;
     }
     const float rpart0 = one[0];
@@ -599,6 +670,7 @@ template <bool H16, bool TM> __device__ void cgls_body_tag(const CglsArgs& a, Cg
         ph.in = a.rc;
         ph.tout = ts;
         ph.etag_out = E;
+        ph.own_out = OV_S;
         if (!c.template phase<ST_IN, true, EPI_TAG>(ph, n0, n1)) return;
         float gpart = n0, rpart = rpart0;
         float gamma_old = 0.f, alpha_old = 0.f;
@@ -608,33 +680,55 @@ template <bool H16, bool TM> __device__ void cgls_body_tag(const CglsArgs& a, Cg
             ph.etag = E + (unsigned int)i;
             ph.tout = tu;
             ph.etag_out = E + (unsigned int)i;
+            ph.own_out = OV_U;
             n0 = 0.f; n1 = 0.f;
             if (!c.template phase<ST_TAG, false, EPI_TAG>(ph, n0, n1)) return;   // u = D_c s
+            // publish (|u|^2, |s|^2, |r|^2) now and collect the sums only after the
+            // products of the second stencil, which do not depend on them: the
+            // exchange's latency hides behind w = D_c^dag u
             float three[3] = {n0, gpart, rpart};
-            if (!xch_allreduce<3, false>(three, a.xch, ex++, a.err, shr)) return;
-            const float delta = three[0], gamma = three[1];
-            r2 = three[2];
-            it = i;
-            if ((i > 0 && r2 <= a.tol2 * rc2) || i >= a.maxit) break;
-            const float beta = i > 0 ? gamma / gamma_old : 0.f;
-            const float den = i > 0 ? delta - beta * gamma / alpha_old : delta;
-            if (!(gamma > 0.f) || !(den > 0.f)) break;
-            const float alpha = gamma / den;
+            const unsigned int ex_i = ex++;
+            xch_post<3, false>(three, a.xch, ex_i, shr);
+            float gamma = 0.f, alpha = 0.f;
             ph = CglsPhase{};
             ph.tin = tu;
             ph.etag = E + (unsigned int)i;
             ph.ts = ts; ph.tu = tu;
             ph.cp = a.p; ph.cz = a.p1; ph.cq = a.q; ph.cy = a.y; ph.cr = a.r;
             ph.etag_out = E + (unsigned int)i + 1u;
-            ph.alpha = alpha;
-            ph.beta = beta;
             ph.first = (i == 0);
+            auto pre = [&]() -> int {
+                if (!xch_collect<3>(three, a.xch, ex_i, a.err, shr)) return -1;
+                const float delta = three[0];
+                gamma = three[1];
+                r2 = three[2];
+                it = i;
+                if ((i > 0 && r2 <= a.tol2 * rc2) || i >= a.maxit) return 0;
+                const float beta = i > 0 ? gamma / gamma_old : 0.f;
+                const float den = i > 0 ? delta - beta * gamma / alpha_old : delta;
+                if (!(gamma > 0.f) || !(den > 0.f)) return 0;
+                alpha = gamma / den;
+                ph.alpha = alpha;
+                ph.beta = beta;
+                return 1;
+            };
             n0 = 0.f; n1 = 0.f;
-            if (!c.template phase<ST_TAG, true, EPI_CG_TAG>(ph, n0, n1)) return;   // w = D_c^dag u, updates
+            if (!c.template phase<ST_TAG, true, EPI_CG_TAG>(ph, n0, n1, pre)) return;   // w = D_c^dag u, updates
+            if (ph.stop) break;
             gpart = n0;
             rpart = n1;
             gamma_old = gamma;
             alpha_old = alpha;
+        }
+    }
+    if (c.ov) {   // the solution (and residual) of the own rows back to global memory
+        __syncthreads();
+        for (int i = threadIdx.x; i < c.nu * c.RU; i += blockDim.x) {
+            const int j = i / c.RU, ain = i - j * c.RU, u = c.u0 + j, X = u / c.H;
+            const size_t o = (size_t)X * c.nc + (u - X * c.H) * c.RU + ain;
+            const cx<float> y = c.ov[OV_Y * c.ov_n + i], r = c.ov[OV_R * c.ov_n + i];
+            a.y[o] = make_float2(y.r, y.i);
+            a.r[o] = make_float2(r.r, r.i);
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -786,7 +880,9 @@ bool cgls_shape(int nc, int Vc, bool h16, int mode, CglsShape* out) {
             s.slots = 0;
             s.wave = s.nu_max;
             s.groups = 1;
-            off = std::max(off, (size_t)lim.smem / 2 + 4096);
+            // the own-row vectors of the tagged form after the exchange scratch
+            s.own_off = (int)off;
+            off = std::max(off + (size_t)OV_COUNT * s.nu_max * ru * 8, (size_t)lim.smem / 2 + 4096);
             if (off > budget) continue;
             score = (long long)s.nu_max * ru;
         } else if (off + (size_t)s.nu_max * s.stride <= budget) {

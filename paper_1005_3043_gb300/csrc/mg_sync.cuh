@@ -135,15 +135,16 @@ constexpr int kXchMaxNV = 3;
 // FENCE false: no fence before the publish (the caller's cross-CTA data is
 // epoch-tagged, so only the partial sums themselves must arrive).
 // Gx: the number of CTAs that publish (0: gridDim.x); limit: polls per slot.
+// The exchange in two halves, so that a caller can do independent work between
+// publishing its share and collecting the sums: xch_post (warp partial sums,
+// one CTA barrier, thread 0 publishes) and xch_collect (poll, sum; two CTA
+// barriers).  The scratch sc must stay untouched from xch_post to xch_collect.
 template <int NV, bool FENCE = true>
-__device__ bool xch_allreduce(float (&v)[NV], unsigned long long* slots, unsigned int e, int* err, float* sc, int Gx = 0,
-                              long long limit = kExchangeSpinLimit) {
+__device__ void xch_post(const float (&v)[NV], unsigned long long* slots, unsigned int e, float* sc, int Gx = 0) {
     static_assert(NV >= 1 && NV <= kXchMaxNV, "one to three values per exchange");
     const int G = Gx > 0 ? Gx : (int)gridDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
     unsigned long long* base = slots + (size_t)(e & 1) * kXchMaxNV * G * kXchPad;
     float* wsum = sc;                  // [NV][32] warp partials
-    float* gv = sc + NV * 32;          // [NV * G] polled CTA sums
-    float* res = gv + NV * G;          // [NV] grid sums
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
         const float w = warp_sum_t<float>(v[j]);
@@ -167,6 +168,14 @@ __device__ bool xch_allreduce(float (&v)[NV], unsigned long long* slots, unsigne
             for (int j = 0; j < NV; ++j) xch_publish_relaxed(base + ((size_t)j * G + blockIdx.x) * kXchPad, cta[j], e);
         }
     }
+}
+template <int NV>
+__device__ bool xch_collect(float (&v)[NV], const unsigned long long* slots, unsigned int e, int* err, float* sc,
+                            int Gx = 0, long long limit = kExchangeSpinLimit) {
+    const int G = Gx > 0 ? Gx : (int)gridDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const unsigned long long* base = slots + (size_t)(e & 1) * kXchMaxNV * G * kXchPad;
+    float* gv = sc + NV * 32;          // [NV * G] polled CTA sums
+    float* res = gv + NV * G;          // [NV] grid sums
     bool ok = true;
     for (int i = t; i < NV * G && ok; i += blockDim.x) {
         float got = 0.f;
@@ -184,6 +193,21 @@ __device__ bool xch_allreduce(float (&v)[NV], unsigned long long* slots, unsigne
 #pragma unroll
     for (int j = 0; j < NV; ++j) v[j] = res[j];
     return true;
+}
+// v[j] (this thread's share) -> the grid-wide sums, identical in every CTA.
+// slots: [parity 2][value kXchMaxNV][G][kXchPad]; the parity is that of e, so
+// consecutive calls must use consecutive epochs.
+// sc: shared scratch of at least NV * (32 + G + 1) floats, free during the call.
+// Three CTA barriers for any NV: warp partial sums -> thread 0 publishes;
+// polled values -> one warp per value sums them in CTA order.
+// FENCE false: no fence before the publish (the caller's cross-CTA data is
+// epoch-tagged, so only the partial sums themselves must arrive).
+// Gx: the number of CTAs that publish (0: gridDim.x); limit: polls per slot.
+template <int NV, bool FENCE = true>
+__device__ bool xch_allreduce(float (&v)[NV], unsigned long long* slots, unsigned int e, int* err, float* sc, int Gx = 0,
+                              long long limit = kExchangeSpinLimit) {
+    xch_post<NV, FENCE>(v, slots, e, sc, Gx);
+    return xch_collect<NV>(v, slots, e, err, sc, Gx, limit);
 }
 
 // ---------------------------------------------------------------- epoch-tagged vectors
