@@ -248,9 +248,11 @@ int mg_nn_loss_grad(mg_ctx* ctx, const double* eta, int n, double* loss, double*
  * last step (each before its update) in *loss_first, *loss_last (may be NULL). */
 int mg_nn_train(mg_ctx* ctx, const double* eta, int n, int steps, double lr, double* loss_first, double* loss_last);
 /* The learned setup: prototypes v_i = network(eta_i), i < nvec, normalised,
- * then (refine_iters > 0) the Sec. IV group refinement with refine_iters
- * truncated-cycle iterations per prototype (no relaxation), then P and D_c
- * (eq. 4, Sec. III).  info.setup_ms of later solves reports its device time. */
+ * in place of the random starts of the Sec. IV setup; then, as in mg_setup,
+ * params.setup_init_relax relaxation steps (0 skips them) and the group
+ * refinement, here with refine_iters truncated-cycle iterations per prototype
+ * (0 skips it), then P and D_c (eq. 4, Sec. III).  info.setup_ms of later
+ * solves reports its device time. */
 int mg_setup_learned(mg_ctx* ctx, const double* eta, int refine_iters);
 
 /* Read back the current prototypes V (the near-null vectors of Sec. II;
@@ -387,6 +389,17 @@ int mg_vcycle(mg_ctx* ctx, const double* r, double* z, int prec);
  * ms (CUDA events on the context stream) and the bytes one launch must move
  * at minimum (algorithmic: links + input + output, each read/written once). */
 int mg_time_dslash(mg_ctx* ctx, int prec, int reps, double* ms_per_launch, double* bytes_per_launch);
+
+/* Latency floor of the on-chip coarse CGNR (measurement hook; the paper has no
+ * counterpart).  On the current level-1 operator and the solver's own launch
+ * shape, times `rounds` rounds of (a) the two epoch-tagged stencils of one
+ * Chronopoulos-Gear iteration without its exchange and (b) its three-value
+ * grid exchange alone, each in one cooperative launch (CUDA events on the
+ * context's stream, launch overhead included once).  *us_stencils and
+ * *us_exchange: microseconds per round.  Needs MG_FP32 or MG_FP16 inner
+ * precision and an on-chip shape (MG_ERR_INVALID_ARG otherwise); overwrites
+ * the coarse CG work vectors.  MG_ERR_TIMEOUT if a bounded wait gave up. */
+int mg_time_coarse_floor(mg_ctx* ctx, int rounds, double* us_stencils, double* us_exchange);
 
 /* As mg_time_dslash (eq. 2), with the L2 cache flushed before every launch: the
  * caller's device buffer `flush` (flush_bytes, larger than the L2) is

@@ -106,6 +106,7 @@ _SIGS = {
     "mg_coarse_solve_noalloc": ([_P, _P, _P, _D, _I, _P, _P], _I),
     "mg_vcycle": ([_P, _P, _P, _I], _I),
     "mg_time_dslash": ([_P, _I, _I, _P, _P], _I),
+    "mg_time_coarse_floor": ([_P, _I, _P, _P], _I),
     "mg_time_dslash_cold": ([_P, _I, _I, _P, ctypes.c_size_t, _P, _P], _I),
     "mg_profile_enable": ([_P, _I], _I),
     "mg_profile_read": ([_P, _P, _P, _P], _I),
@@ -453,6 +454,14 @@ def mg_time_dslash(ctx, prec: int = MG_FP32, reps: int = 50):
     return ms.value, nbytes.value
 
 
+def mg_time_coarse_floor(ctx, rounds: int = 200):
+    """(us per round of the two tagged coarse stencils alone, us per exchange alone)."""
+    a = ctypes.c_double(0)
+    b = ctypes.c_double(0)
+    _check(load().mg_time_coarse_floor(ctx, int(rounds), ctypes.byref(a), ctypes.byref(b)), ctx)
+    return a.value, b.value
+
+
 def mg_time_dslash_cold(ctx, flush_ptr: int, flush_bytes: int, prec: int = MG_FP32, reps: int = 20):
     """Mean dslash time with the L2 flushed (a device buffer of flush_bytes overwritten) before each launch."""
     ms = ctypes.c_double(0)
@@ -646,6 +655,9 @@ class WilsonMG:
 
     def time_dslash(self, prec=MG_FP32, reps=50):
         return mg_time_dslash(self.ctx, prec, reps)
+
+    def time_coarse_floor(self, rounds=200):
+        return mg_time_coarse_floor(self.ctx, rounds)
 
     def time_dslash_cold(self, flush_ptr: int, flush_bytes: int, prec=MG_FP32, reps=20):
         return mg_time_dslash_cold(self.ctx, flush_ptr, flush_bytes, prec, reps)

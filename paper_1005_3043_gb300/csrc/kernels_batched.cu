@@ -522,7 +522,7 @@ __global__ void k_bcg_unscale(float2* __restrict__ y, long long total, int npad,
 
 static inline int ew_grid(long long total) {
     long long b = (total + 255) / 256;
-    if (b > 152 * 8) b = 152 * 8;
+    if (b > 8LL * device_sm_count()) b = 8LL * device_sm_count();
     return (int)(b > 0 ? b : 1);
 }
 static inline int col_threads(int npad) {
@@ -581,7 +581,7 @@ void bcg_finish(const BatchCg& c, cudaStream_t st) {
 namespace wmg {
 static inline int ew_grid2(long long total) {
     long long b = (total + 255) / 256;
-    if (b > 152 * 8) b = 152 * 8;
+    if (b > 8LL * device_sm_count()) b = 8LL * device_sm_count();
     return (int)(b > 0 ? b : 1);
 }
 // columns n < nrhs of a panel from nrhs stacked coarse vectors in[n][row] (FP64), other columns zero

@@ -167,7 +167,7 @@ template <bool H16, bool TM> struct CglsCta {
         red = reinterpret_cast<cx<float>*>(sm + 256);
         xs = red + (resident ? 1 : 2) * a.sh.red_n;
         slots = sm + a.sh.slot_off;
-        if (a.sh.own_off > 0 && a.form == CGLS_CG_TAGGED) {
+        if (a.sh.own_off > 0 && (a.form == CGLS_CG_TAGGED || a.form == CGLS_PROBE_STENCILS)) {
             ov = reinterpret_cast<cx<float>*>(sm + a.sh.own_off);
             ov_n = a.sh.nu_max * RU;
         }
@@ -740,12 +740,50 @@ template <bool H16, bool TM> __device__ void cgls_body_tag(const CglsArgs& a, Cg
     }
 }
 
+// Latency probes (see CGLS_PROBE_*): maxit rounds of the tagged form's two
+// stencils (u = D_c s, s' = D_c^dag u, tagged staging and emission, values
+// unnormalised and unused) or of its three-value exchange.  Same epochs and
+// reader/writer ordering as the solver: a CTA rewrites s (u) only after staging
+// the neighbour entries of u (s) that the neighbour writes after reading it.
+template <bool H16, bool TM> __device__ void cgls_probe(const CglsArgs& a, CglsCta<H16, TM>& c) {
+    float* shr = reinterpret_cast<float*>(c.xs + (size_t)a.sh.nx_max * c.K);
+    const unsigned int E = a.epoch0;
+    if (a.form == CGLS_PROBE_EXCHANGE) {
+        for (int i = 0; i < a.maxit; ++i) {
+            float three[3] = {1.f, 1.f, 1.f};
+            if (!xch_allreduce<3, false>(three, a.xch, E + (unsigned int)i, a.err, shr)) return;
+        }
+        return;
+    }
+    unsigned long long* ts = a.tag;
+    unsigned long long* tu = a.tag + 2 * (size_t)a.g.Vc * a.nc;
+    CglsPhase ph{};
+    float n0 = 0.f, n1 = 0.f;
+    ph.in = a.rc;
+    ph.tout = ts;
+    ph.etag_out = E;
+    ph.own_out = OV_S;
+    if (!c.template phase<ST_IN, true, EPI_TAG>(ph, n0, n1)) return;
+    for (int i = 0; i < a.maxit; ++i) {
+        ph = CglsPhase{};
+        ph.tin = ts; ph.etag = E + (unsigned int)i;
+        ph.tout = tu; ph.etag_out = E + (unsigned int)i; ph.own_out = OV_U;
+        if (!c.template phase<ST_TAG, false, EPI_TAG>(ph, n0, n1)) return;
+        ph = CglsPhase{};
+        ph.tin = tu; ph.etag = E + (unsigned int)i;
+        ph.tout = ts; ph.etag_out = E + (unsigned int)i + 1u; ph.own_out = OV_S;
+        if (!c.template phase<ST_TAG, true, EPI_TAG>(ph, n0, n1)) return;
+    }
+}
+
 template <bool H16, bool TM> __global__ void __launch_bounds__(kCglsThreads, 1) k_cgls_onchip(CglsArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     CglsCta<H16, TM> c(a, smem_raw);
     c.start();
     if (a.form == CGLS_CG_TAGGED)
         cgls_body_tag<H16, TM>(a, c);
+    else if (a.form == CGLS_PROBE_STENCILS || a.form == CGLS_PROBE_EXCHANGE)
+        cgls_probe<H16, TM>(a, c);
     else
         cgls_body<H16, TM>(a, c);
     c.drain();   // no copy may still be writing shared memory, and no TMEM stays allocated, when the CTA exits
@@ -921,7 +959,7 @@ cudaError_t cgls_onchip(const CglsArgs& args, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         attr[lim.dev][h16][tm].store(true, std::memory_order_release);
     }
-    if ((args.form == CGLS_CG_TAGGED && !args.tag) || args.sh.smem > (size_t)lim.smem - 1024 || args.sh.grid <= 0 ||
+    if (((args.form == CGLS_CG_TAGGED || args.form == CGLS_PROBE_STENCILS) && !args.tag) || args.sh.smem > (size_t)lim.smem - 1024 || args.sh.grid <= 0 ||
         args.sh.grid > lim.sms ||
         args.sh.grid > kXchMaxGrid || 2 * args.sh.grid > kCglsThreads)
         return cudaErrorInvalidValue;

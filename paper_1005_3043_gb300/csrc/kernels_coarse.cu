@@ -429,14 +429,14 @@ __global__ void __launch_bounds__(256) k_coarse_apply(v2<T>* __restrict__ y, con
         red[0] = (double)norm2(acc);
     }
     if (FIN == 1) {
-        grid_reduce<1>(red, R.partials, R.ticket, [&](double (&t)[1]) { R.scal[slot] = t[0]; });
+        grid_reduce<1>(red, R.partials, R.ticket, R.partial_bytes, [&](double (&t)[1]) { R.scal[slot] = t[0]; });
     } else if (FIN == 2) {
-        grid_reduce<1>(red, R.partials, R.ticket, [&](double (&t)[1]) {
+        grid_reduce<1>(red, R.partials, R.ticket, R.partial_bytes, [&](double (&t)[1]) {
             if (t[0] > 0) R.scal[S_CG_ALPHA] = R.scal[S_CG_GAMMA] / t[0];
             else { R.scal[S_CG_ALPHA] = 0.0; R.scal[S_CG_DONE] = 1.0; }
         });
     } else if (FIN == 3) {
-        grid_reduce<1>(red, R.partials, R.ticket, [&](double (&t)[1]) {
+        grid_reduce<1>(red, R.partials, R.ticket, R.partial_bytes, [&](double (&t)[1]) {
             double gam = R.scal[S_CG_GAMMA];
             R.scal[S_CG_BETA] = gam > 0 ? t[0] / gam : 0.0;
             R.scal[S_CG_GAMMA] = t[0];
@@ -471,7 +471,7 @@ __global__ void k_cg_start(v2<T>* __restrict__ y, v2<T>* __restrict__ r, const v
         a += v.x * v.x + v.y * v.y;
     }
     double acc[1] = {(double)a};
-    grid_reduce<1>(acc, R.partials, R.ticket, [&](double (&t)[1]) {
+    grid_reduce<1>(acc, R.partials, R.ticket, R.partial_bytes, [&](double (&t)[1]) {
         R.scal[S_CG_RC2] = t[0];
         R.scal[S_CG_R2] = t[0];
         R.scal[S_CG_TOL2] = tol * tol;
@@ -498,7 +498,7 @@ __global__ void k_cg_update1(v2<T>* __restrict__ y, v2<T>* __restrict__ r, const
         a += norm2(v);
     }
     double acc[1] = {(double)a};
-    grid_reduce<1>(acc, R.partials, R.ticket, [&](double (&t)[1]) {
+    grid_reduce<1>(acc, R.partials, R.ticket, R.partial_bytes, [&](double (&t)[1]) {
         double it = R.scal[S_CG_ITERS] + 1.0;
         R.scal[S_CG_ITERS] = it;
         R.scal[S_CG_R2] = t[0];

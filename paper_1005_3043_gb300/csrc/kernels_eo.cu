@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(kEoThreads) k_eo_hop(v2<T>* __restrict__ out, 
     }
     if (F & EO_NORM) {
         T v1[1] = {nrm};
-        grid_reduce<1, T>(v1, R.partials, R.ticket, [&](double (&t)[1]) { R.scal[slot] = t[0]; });
+        grid_reduce<1, T>(v1, R.partials, R.ticket, R.partial_bytes, [&](double (&t)[1]) { R.scal[slot] = t[0]; });
     }
 }
 
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(kEoThreads) k_eo_cg_update1(v2<T>* __restrict_
         acc += norm2(rv);
     }
     T v1[1] = {acc};
-    grid_reduce<1, T>(v1, R.partials, R.ticket, [&](double (&t)[1]) {
+    grid_reduce<1, T>(v1, R.partials, R.ticket, R.partial_bytes, [&](double (&t)[1]) {
         R.scal[s.r2] = t[0];
         R.scal[s.iters] = (double)(iter + 1);
         if (t[0] <= R.scal[s.tol2] || !(qq > 0)) R.scal[s.done] = 1.0;

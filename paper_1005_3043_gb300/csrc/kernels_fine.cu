@@ -1,5 +1,7 @@
 // Fine-grid kernels: boundary/internal layout conversion, the Wilson-Dirac
 // operator of eq. (2) with spin projection, and BLAS-1 / GCR kernels.
+#include <atomic>
+
 #include "mg_launch.h"
 #include "mg_wilson.cuh"
 
@@ -79,7 +81,7 @@ template <typename T> void links_to_internal(v2<T>* out, const double2* in, cons
     k_links_to_internal<T><<<grid_for(g.V), kThreads, 0, st>>>(out, in, g);
 }
 template <typename Tin, typename Tout> void convert(v2<Tout>* out, const v2<Tin>* in, size_t n, cudaStream_t st) {
-    int grid = (int)std::min<size_t>((n + kThreads - 1) / kThreads, 152 * 16);
+    int grid = (int)std::min<size_t>((n + kThreads - 1) / kThreads, (size_t)device_sm_count() * 16);
     note_launch();
     k_convert<Tin, Tout><<<grid > 0 ? grid : 1, kThreads, 0, st>>>(out, in, n);
 }
@@ -102,7 +104,7 @@ __global__ void k_links_pair(float2* __restrict__ out, const float2* __restrict_
 }
 void links_pair(float2* out, const float2* U32, const Geom& g, cudaStream_t st) {
     note_launch();
-    k_links_pair<<<(int)std::min<long long>((4LL * g.V + kThreads - 1) / kThreads, 152 * 16), kThreads, 0, st>>>(out, U32, g);
+    k_links_pair<<<(int)std::min<long long>((4LL * g.V + kThreads - 1) / kThreads, 16LL * device_sm_count()), kThreads, 0, st>>>(out, U32, g);
 }
 
 // ================================================================ Wilson operator
@@ -167,17 +169,34 @@ __device__ __forceinline__ void hop(cx<T> (&acc)[4][3], const v2<T>* __restrict_
     accumulate<T, MU, FWD>(acc, w, flip ? T(0.5) : T(-0.5));
 }
 
-// CTA shape of the dslash: FP32 128 threads with 7 CTAs per SM (72 registers), so
-// one thread per site of a 16^3x32 lattice fits one wave of the 152 SMs (256
-// threads x 3 CTAs left a 12% second wave: measured 18.3 -> 14.4 us warm, 28.2 ->
-// 22.7 us with L2 flushed); FP64 256 x 2.
-template <typename T> struct DslashShape { static constexpr int threads = 128, blocks = 7; };
-template <> struct DslashShape<double> { static constexpr int threads = 256, blocks = 2; };
+// SM count of the current device, looked up once per device (atomic slots)
+int device_sm_count() {
+    static std::atomic<int> cache[16];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) return 152;
+    int n = cache[dev].load(std::memory_order_acquire);
+    if (n == 0) {
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+        cache[dev].store(n, std::memory_order_release);
+    }
+    return n;
+}
 
-template <typename T, int MODE>
-__global__ void __launch_bounds__(DslashShape<T>::threads, DslashShape<T>::blocks) k_dslash(v2<T>* __restrict__ out, const v2<T>* __restrict__ in,
-                                                const v2<T>* __restrict__ U, const v2<T>* __restrict__ src,
-                                                Geom g, T diag, double omega, int slot, Reduce R) {
+// CTA shape of the dslash.  FP32: 128 threads; with 7 CTAs per SM (72
+// registers) one thread per site of a 16^3x32 lattice fits one wave of the 152
+// SMs (256 threads x 3 CTAs left a 12% second wave: 18.3 -> 14.4 us warm, 28.2
+// -> 22.7 us with L2 flushed).  Lattices of several waves take 5 CTAs per SM
+// (up to 102 registers: more of each thread's neighbour loads in flight):
+// measured on 24^3x64, 99.8 -> 92.2 us with L2 flushed, 93.9 -> 85.8 us back to
+// back; 6 gave the same, 8 (64 registers, spills) 111 us.  FP64: 256 x 2.
+template <typename T, int MINB> struct DslashShape { static constexpr int threads = 128, blocks = MINB; };
+template <int MINB> struct DslashShape<double, MINB> { static constexpr int threads = 256, blocks = 2; };
+constexpr int kDslashOneWave = 7, kDslashMultiWave = 5;
+
+template <typename T, int MODE, int MINB>
+__global__ void __launch_bounds__(DslashShape<T, MINB>::threads, DslashShape<T, MINB>::blocks)
+    k_dslash(v2<T>* __restrict__ out, const v2<T>* __restrict__ in, const v2<T>* __restrict__ U,
+             const v2<T>* __restrict__ src, Geom g, T diag, double omega, int slot, Reduce R) {
     long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     T red[3] = {0, 0, 0};   // per-site partial sums in T, promoted once for the grid reduction
     if (s < g.V) {
@@ -220,10 +239,10 @@ __global__ void __launch_bounds__(DslashShape<T>::threads, DslashShape<T>::block
     }
     if (MODE == DS_XMY_NORM) {
         T v1[1] = {red[0]};
-        grid_reduce<1, T>(v1, R.partials, R.ticket, [&](double (&t)[1]) { R.scal[slot] = t[0]; });
+        grid_reduce<1, T>(v1, R.partials, R.ticket, R.partial_bytes, [&](double (&t)[1]) { R.scal[slot] = t[0]; });
     } else if (MODE == DS_MRDOT) {
         T v3[3] = {red[0], red[1], red[2]};
-        grid_reduce<3, T>(v3, R.partials, R.ticket, [&](double (&t)[3]) {
+        grid_reduce<3, T>(v3, R.partials, R.ticket, R.partial_bytes, [&](double (&t)[3]) {
             double f = t[2] > 0 ? omega / t[2] : 0.0;
             R.scal[S_MR_ALPHA] = f * t[0];
             R.scal[S_MR_ALPHA + 1] = f * t[1];
@@ -231,21 +250,31 @@ __global__ void __launch_bounds__(DslashShape<T>::threads, DslashShape<T>::block
     }
 }
 
+template <typename T, int MINB>
+static void dslash_launch(int mode, v2<T>* out, const v2<T>* in, const v2<T>* U, const v2<T>* src, const Geom& g,
+                          T diag, double omega, int slot, const Reduce& R, cudaStream_t st) {
+    constexpr int thr = DslashShape<T, MINB>::threads;
+    const int grid = grid_for(g.V, thr);
+    note_launch();
+    switch (mode) {
+        case DS_PLAIN: k_dslash<T, DS_PLAIN, MINB><<<grid, thr, 0, st>>>(out, in, U, src, g, diag, omega, slot, R); break;
+        case DS_XMY: k_dslash<T, DS_XMY, MINB><<<grid, thr, 0, st>>>(out, in, U, src, g, diag, omega, slot, R); break;
+        case DS_XMY_NORM:
+            k_dslash<T, DS_XMY_NORM, MINB><<<grid, thr, 0, st>>>(out, in, U, src, g, diag, omega, slot, R);
+            break;
+        case DS_MRDOT: k_dslash<T, DS_MRDOT, MINB><<<grid, thr, 0, st>>>(out, in, U, src, g, diag, omega, slot, R); break;
+    }
+}
+
 template <typename T>
 void dslash(int mode, v2<T>* out, const v2<T>* in, const v2<T>* U, const v2<T>* src, const Geom& g, double mass,
             double omega, int slot, const Reduce& R, cudaStream_t st) {
-    constexpr int thr = DslashShape<T>::threads;
-    int grid = grid_for(g.V, thr);
-    T diag = (T)(4.0 + mass);
-    switch (mode) {
-        case DS_PLAIN: { note_launch(); k_dslash<T, DS_PLAIN><<<grid, thr, 0, st>>>(out, in, U, src, g, diag, omega, slot, R); } break;
-        case DS_XMY: { note_launch(); k_dslash<T, DS_XMY><<<grid, thr, 0, st>>>(out, in, U, src, g, diag, omega, slot, R); } break;
-        case DS_XMY_NORM:
-            note_launch();
-            k_dslash<T, DS_XMY_NORM><<<grid, thr, 0, st>>>(out, in, U, src, g, diag, omega, slot, R);
-            break;
-        case DS_MRDOT: { note_launch(); k_dslash<T, DS_MRDOT><<<grid, thr, 0, st>>>(out, in, U, src, g, diag, omega, slot, R); } break;
-    }
+    const T diag = (T)(4.0 + mass);
+    const long long one_wave = (long long)device_sm_count() * kDslashOneWave * DslashShape<T, kDslashOneWave>::threads;
+    if (sizeof(T) == 8 || g.V <= one_wave)
+        dslash_launch<T, kDslashOneWave>(mode, out, in, U, src, g, diag, omega, slot, R, st);
+    else
+        dslash_launch<T, kDslashMultiWave>(mode, out, in, U, src, g, diag, omega, slot, R, st);
 }
 
 // ================================================================ BLAS-1
@@ -260,7 +289,7 @@ template <typename T> __global__ void k_norm2(const v2<T>* __restrict__ x, size_
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         a += norm2(ld<T>(x + i));
     T acc[1] = {a};
-    grid_reduce<1, T>(acc, R.partials, R.ticket, [&](double (&t)[1]) { R.scal[slot] = t[0]; });
+    grid_reduce<1, T>(acc, R.partials, R.ticket, R.partial_bytes, [&](double (&t)[1]) { R.scal[slot] = t[0]; });
 }
 template <typename T>
 __global__ void k_dot(const v2<T>* __restrict__ x, const v2<T>* __restrict__ y, size_t n, int slot, Reduce R) {
@@ -268,7 +297,7 @@ __global__ void k_dot(const v2<T>* __restrict__ x, const v2<T>* __restrict__ y, 
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         cmadc(a, ld<T>(x + i), ld<T>(y + i));
     T acc[2] = {a.r, a.i};
-    grid_reduce<2, T>(acc, R.partials, R.ticket, [&](double (&t)[2]) {
+    grid_reduce<2, T>(acc, R.partials, R.ticket, R.partial_bytes, [&](double (&t)[2]) {
         R.scal[slot] = t[0];
         R.scal[slot + 1] = t[1];
     });
@@ -308,7 +337,7 @@ template <typename T> __global__ void k_normalize(v2<T>* x, size_t n, const doub
 
 static inline int stream_grid(size_t n) {
     size_t b = (n + kThreads - 1) / kThreads;
-    if (b > 152 * 16) b = 152 * 16;
+    if (b > 16LL * device_sm_count()) b = 16LL * device_sm_count();
     return (int)(b > 0 ? b : 1);
 }
 
@@ -364,7 +393,7 @@ __global__ void k_gcr_multidot(const v2<T>* __restrict__ basis, size_t n, int k,
             }
         }
     }
-    grid_reduce<2 * NJ, T>(a, R.partials, R.ticket, [&](double (&t)[2 * NJ]) {
+    grid_reduce<2 * NJ, T>(a, R.partials, R.ticket, R.partial_bytes, [&](double (&t)[2 * NJ]) {
         for (int j = 0; j < k && j < NJ; ++j) {
             R.scal[rslot(j, k)] = t[2 * j];
             R.scal[rslot(j, k) + 1] = t[2 * j + 1];
@@ -389,7 +418,7 @@ __global__ void k_gcr_orth_norm(v2<T>* basis, size_t n, int k, Reduce R) {
         a += norm2(v);
     }
     T acc[1] = {a};
-    grid_reduce<1, T>(acc, R.partials, R.ticket, [&](double (&t)[1]) { R.scal[S_GCR_PN2] = t[0]; });
+    grid_reduce<1, T>(acc, R.partials, R.ticket, R.partial_bytes, [&](double (&t)[1]) { R.scal[S_GCR_PN2] = t[0]; });
 }
 template <typename T>
 __global__ void k_gcr_cdot(const v2<T>* __restrict__ basis, const v2<T>* __restrict__ r, size_t n, int k, Reduce R) {
@@ -398,7 +427,7 @@ __global__ void k_gcr_cdot(const v2<T>* __restrict__ basis, const v2<T>* __restr
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         cmadc(a, ld<T>(pk + i), ld<T>(r + i));
     T acc[2] = {a.r, a.i};
-    grid_reduce<2, T>(acc, R.partials, R.ticket, [&](double (&t)[2]) {
+    grid_reduce<2, T>(acc, R.partials, R.ticket, R.partial_bytes, [&](double (&t)[2]) {
         double nk = sqrt(R.scal[S_GCR_PN2]);
         R.scal[rslot(k, k)] = nk;
         R.scal[rslot(k, k) + 1] = 0.0;
@@ -422,7 +451,7 @@ __global__ void k_gcr_update(v2<T>* basis, v2<T>* r, size_t n, int k, Reduce R) 
         a += norm2(v);
     }
     T acc[1] = {a};
-    grid_reduce<1, T>(acc, R.partials, R.ticket, [&](double (&t)[1]) { R.scal[S_GCR_R2] = t[0]; });
+    grid_reduce<1, T>(acc, R.partials, R.ticket, R.partial_bytes, [&](double (&t)[1]) { R.scal[S_GCR_R2] = t[0]; });
 }
 template <typename T>
 __global__ void k_gcr_xupdate(double2* x, const v2<T>* __restrict__ Z, size_t n, int k, GcrCoef y) {

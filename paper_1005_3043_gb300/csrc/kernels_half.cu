@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kHalfThreads, MODE == HMODE_MRDOT ? 6 : 7)
     }
     if (MODE == HMODE_MRDOT) {
         float v3[3] = {red[0], red[1], red[2]};
-        grid_reduce<3, float>(v3, R.partials, R.ticket, [&](double (&t)[3]) {
+        grid_reduce<3, float>(v3, R.partials, R.ticket, R.partial_bytes, [&](double (&t)[3]) {
             const double f = t[2] > 0 ? omega / t[2] : 0.0;
             R.scal[S_MR_ALPHA] = f * t[0];
             R.scal[S_MR_ALPHA + 1] = f * t[1];
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(kHalfThreads) k_h_multidot(const uint2* __rest
             }
         }
     }
-    grid_reduce<2 * NJ, float>(a, R.partials, R.ticket, [&](double (&t)[2 * NJ]) {
+    grid_reduce<2 * NJ, float>(a, R.partials, R.ticket, R.partial_bytes, [&](double (&t)[2 * NJ]) {
         for (int j = 0; j < k && j < NJ; ++j) {
             R.scal[rslot_h(j, k)] = t[2 * j];
             R.scal[rslot_h(j, k) + 1] = t[2 * j + 1];
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(kHalfThreads) k_h_orth(uint2* __restrict__ B, 
                      [&](int, cx<float> q) { a += norm2(q); });
     }
     float acc[1] = {a};
-    grid_reduce<1, float>(acc, R.partials, R.ticket, [&](double (&t)[1]) {
+    grid_reduce<1, float>(acc, R.partials, R.ticket, R.partial_bytes, [&](double (&t)[1]) {
         const double nk = sqrt(t[0]);
         R.scal[rslot_h(k, k)] = nk;
         R.scal[rslot_h(k, k) + 1] = 0.0;
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(kHalfThreads) k_h_multi_axpy(float2* __restric
 void links_to_half(uint2* U16, const float2* U32, const Geom& g, cudaStream_t st) {
     const long long n = 4LL * g.Vc * 5 * g.Vb;
     note_launch();
-    k_links_to_half<<<(int)std::min<long long>((n + 255) / 256, 152 * 16), 256, 0, st>>>(U16, U32, g);
+    k_links_to_half<<<(int)std::min<long long>((n + 255) / 256, 16LL * device_sm_count()), 256, 0, st>>>(U16, U32, g);
 }
 void to_half(HalfSpinor h, const float2* x, const Geom& g, cudaStream_t st) {
     note_launch();
@@ -382,6 +382,8 @@ void dslash_h_mrdot(HalfSpinor out, ConstHalfSpinor in, const uint2* U16, const 
 }
 void h_multidot(const uint2* B, const float* S, const Geom& g, int k, const Reduce& R, cudaStream_t st) {
     note_launch();
+    // one block per 128 sites, 2 NJ <= 32 float partial sums each: the context
+    // sizes the reduction buffer for V / 128 such blocks (reduce_partial_bytes)
     if (k <= 4) k_h_multidot<4><<<half_grid(g.V), kHalfThreads, 0, st>>>(B, S, g, k, R);
     else if (k <= 8) k_h_multidot<8><<<half_grid(g.V), kHalfThreads, 0, st>>>(B, S, g, k, R);
     else k_h_multidot<16><<<half_grid(g.V), kHalfThreads, 0, st>>>(B, S, g, k, R);

@@ -265,7 +265,7 @@ cudaError_t nn_wgrad(double2* G, float2* part, const float2* gout, const float2*
 void nn_seed(float2* gout, const float2* r, const float2* v, size_t n, const double* scal, int vslot, int rslot,
              cudaStream_t st) {
     note_launch();
-    k_nn_seed<<<(int)std::min<size_t>((n + 255) / 256, 152 * 16), 256, 0, st>>>(gout, r, v, n, scal, vslot, rslot);
+    k_nn_seed<<<(int)std::min<size_t>((n + 255) / 256, (size_t)device_sm_count() * 16), 256, 0, st>>>(gout, r, v, n, scal, vslot, rslot);
 }
 void nn_adam(float2* W, double2* Wm, const double2* G, double2* m, double2* v, int n, double lr, double b1, double b2,
              double eps, int t, cudaStream_t st) {

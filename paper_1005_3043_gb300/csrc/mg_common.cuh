@@ -200,14 +200,30 @@ __device__ __forceinline__ void block_reduce_acc(TA (&v)[N], TA (*sh)[32]) {
     }
 }
 
+// Smallest partial-sum buffer of the grid reductions (Reduce::partials); a
+// context sizes its own for its lattice (reduce_partial_bytes).
+constexpr int kMaxReduceBlocks = 1216;   // 152 SMs x 8
+constexpr size_t kReducePartialsBytes = (size_t)kMaxReduceBlocks * 64 * sizeof(double);
+
 // Single-pass deterministic grid reduction: every block writes its partial
 // sums, the last block to arrive adds them in block order and calls
 // fin(total) on thread 0 (totals promoted to double).  TA is the accumulation
 // type inside blocks (float for the FP32 path: the FP64 pipe of this part is
-// narrow).  `partials` needs gridDim.x * N doubles, `ticket` one zeroed
-// counter (reset to 0 by the last block).
+// narrow).  `partials` holds `cap` bytes, `ticket` is one zeroed counter (reset
+// to 0 by the last block).  A grid whose partials would not fit writes
+// nothing and reports NaN totals (a launcher bug made visible, not memory
+// written out of bounds).
 template <int N, typename TA = double, typename Fin>
-__device__ __forceinline__ void grid_reduce(TA (&v)[N], double* partials, unsigned int* ticket, Fin fin) {
+__device__ __forceinline__ void grid_reduce(TA (&v)[N], double* partials, unsigned int* ticket, size_t cap, Fin fin) {
+    if ((size_t)gridDim.x * N * sizeof(TA) > cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            double t[N];
+#pragma unroll
+            for (int k = 0; k < N; ++k) t[k] = __longlong_as_double(0x7ff8000000000000LL);
+            fin(t);
+        }
+        return;
+    }
     __shared__ TA sh[N][32];
     __shared__ bool is_last;
     block_reduce_acc<N, TA>(v, sh);

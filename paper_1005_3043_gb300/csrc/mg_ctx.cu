@@ -52,7 +52,7 @@ struct BatchWork {
     float2 *rcB = nullptr, *yB = nullptr, *rB = nullptr, *sB = nullptr, *pB = nullptr, *qB = nullptr;
     double* cgs = nullptr;          // 9 x npad per-RHS CG scalars
     float* xpart = nullptr;         // Vc x npad
-    float* rpart = nullptr;         // 152 x npad
+    float* rpart = nullptr;         // kBatchRowChunks x npad
     int* flags = nullptr;           // [0] active columns, [1] error
     int* h_flags = nullptr;         // pinned
     double* h_iters = nullptr;      // pinned, npad
@@ -1412,7 +1412,7 @@ int mg_create(const int dims[4], int t_antiperiodic, const mg_params* p, void* s
         (rc = dalloc(ctx, &ctx->r64, sizeof(double2) * n)) ||
         (rc = dalloc(ctx, &ctx->stage_a, sizeof(double2) * 36 * (size_t)g.V)) ||
         (rc = dalloc(ctx, &ctx->stage_b, sizeof(double2) * n)) ||
-        (rc = dalloc(ctx, &ctx->R.partials, sizeof(double) * kMaxReduceBlocks * 64)) ||
+        (rc = dalloc(ctx, &ctx->R.partials, reduce_partial_bytes(g.V))) ||
         (rc = dalloc(ctx, &ctx->R.ticket, sizeof(unsigned int) * 4)) ||
         (rc = dalloc(ctx, &ctx->R.scal, sizeof(double) * S_COUNT)) || (rc = dalloc(ctx, &ctx->d_status, sizeof(int))) ||
         (rc = dalloc(ctx, &ctx->bar, sizeof(unsigned int) * 4)) ||
@@ -1422,6 +1422,7 @@ int mg_create(const int dims[4], int t_antiperiodic, const mg_params* p, void* s
         mg_destroy(ctx);
         return rc;
     }
+    ctx->R.partial_bytes = reduce_partial_bytes(g.V);
     if (cudaMallocHost(&ctx->h_scal, sizeof(double) * S_COUNT) != cudaSuccess ||
         cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess ||
         cudaMemsetAsync(ctx->R.ticket, 0, sizeof(unsigned int) * 4, ctx->st) != cudaSuccess ||
@@ -1799,11 +1800,9 @@ int mg_setup_learned(mg_ctx* ctx, const double* eta, int refine_iters) {
         normalize_dev<double>(ctx->protos + (size_t)i * n, n, S_NORM_A, ctx->R, ctx->st);
     }
     CKL();
-    const int relax = ctx->prm.setup_init_relax, iters = ctx->prm.setup_iters;
-    ctx->prm.setup_init_relax = 0;
+    const int iters = ctx->prm.setup_iters;
     ctx->prm.setup_iters = refine_iters;
     const int st = run_setup(ctx);
-    ctx->prm.setup_init_relax = relax;
     ctx->prm.setup_iters = iters;
     return st;
 }
@@ -2075,6 +2074,52 @@ int mg_time_dslash(mg_ctx* ctx, int prec, int reps, double* ms_per_launch, doubl
     return prec != MG_FP64 ? run(float{}) : run(double{});
 }
 
+int mg_time_coarse_floor(mg_ctx* ctx, int rounds, double* us_stencils, double* us_exchange) {
+    TRY(need_level(ctx));
+    if (rounds <= 0 || !us_stencils || !us_exchange) return MG_ERR_INVALID_ARG;
+    if (ctx->prm.prec_inner == MG_FP64 || ctx->prm.coarse_kernel == 1)
+        return fail(ctx, MG_ERR_INVALID_ARG, "the latency probes run the on-chip coarse solver (FP32 or FP16 inner precision)");
+    TRY(ensure_work<float>(ctx));
+    CoarseLevel& L = ctx->full;
+    const CgSys<float> sys = level1_sys<float>(ctx);
+    const int mode = ctx->prm.coarse_kernel == 2 ? CGLS_STREAM : ctx->prm.coarse_kernel == 3 ? CGLS_SMEM : CGLS_AUTO;
+    bool onchip = false;
+    TRY(ensure_units(ctx, L, sys.g.Vc, ctx->coarse16, mode, &onchip));
+    if (!onchip) return fail(ctx, MG_ERR_INVALID_ARG, "no on-chip shape for this coarse level");
+    double* outs[2] = {us_stencils, us_exchange};
+    const int forms[2] = {CGLS_PROBE_STENCILS, CGLS_PROBE_EXCHANGE};
+    for (int f = 0; f < 2; ++f) {
+        CglsArgs c{};
+        c.Au = L.Au; c.su = ctx->coarse16 ? L.su : nullptr; c.nbr = sys.nbr;
+        c.rc = (const float2*)sys.cr; c.y = (float2*)sys.cp; c.r = (float2*)sys.cr1; c.r1 = (float2*)sys.cr1;
+        c.s = (float2*)sys.cs; c.p = (float2*)sys.cp; c.p1 = (float2*)sys.cp1; c.q = (float2*)sys.cq;
+        c.nc = L.nc; c.g = sys.g; c.tol2 = 0.f; c.maxit = rounds;
+        c.scal = ctx->scal_s; c.err = (int*)(ctx->bar + 2);
+        c.sh = L.au_shape;
+        const unsigned long long reserve = 2ull * (unsigned long long)rounds + 4ull;
+        if ((unsigned long long)ctx->xch_epoch + reserve >= 0xFFFFFFFFull) {
+            CK(cudaMemsetAsync(ctx->xch, 0, sizeof(unsigned long long) * kXchWords, ctx->st));
+            TRY(clear_epoch_tags(ctx));
+            ctx->xch_epoch = 1;
+        }
+        c.xch = ctx->xch;
+        c.epoch0 = ctx->xch_epoch;
+        c.form = forms[f];
+        c.tag = sys.ctag;
+        ctx->xch_epoch += (unsigned int)reserve;
+        CK(cudaMemsetAsync(ctx->bar, 0, sizeof(unsigned int) * 3, ctx->st));
+        CK(cudaEventRecord(ctx->ev0, ctx->st));
+        CK(cgls_onchip(c, ctx->st));
+        CK(cudaEventRecord(ctx->ev1, ctx->st));
+        CK(cudaEventSynchronize(ctx->ev1));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+        TRY(check_timeout(ctx));
+        *outs[f] = 1e3 * (double)ms / rounds;
+    }
+    return MG_OK;
+}
+
 int mg_time_dslash_cold(mg_ctx* ctx, int prec, int reps, void* flush, size_t flush_bytes, double* ms_per_launch,
                         double* bytes_per_launch) {
     TRY(need_links(ctx));
@@ -2239,6 +2284,7 @@ extern "C" int mg_coarse_solve_noalloc(mg_ctx* ctx, const double* rc_dev, double
     R.partials = (double*)(base + 6 * kNoAllocVecBytes);
     R.scal = (double*)(base + 6 * kNoAllocVecBytes + kNoAllocPartialsBytes);
     R.ticket = (unsigned int*)(base + 6 * kNoAllocVecBytes + kNoAllocPartialsBytes + kNoAllocScalBytes);
+    R.partial_bytes = kNoAllocPartialsBytes;
     // the barrier counters and the error flag must start at zero; everything
     // else is written before it is read
     unsigned int* bar = R.ticket;

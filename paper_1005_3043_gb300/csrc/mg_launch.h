@@ -12,16 +12,24 @@ namespace wmg {
 
 // Count of kernel launches issued by this library (all contexts, all threads).
 std::atomic<long long>& launch_counter();
+// SM count of the current device (looked up once per device)
+int device_sm_count();
 inline void note_launch() { launch_counter().fetch_add(1, std::memory_order_relaxed); }
 
 // Scratch used by the single-pass grid reductions: per-block partial sums and
 // an arrival counter that the last block resets to zero.
 struct Reduce {
-    double* partials;      // >= kMaxReduceBlocks * 64 doubles
+    double* partials;      // partial_bytes bytes (at least kReducePartialsBytes)
     unsigned int* ticket;  // one zeroed counter
     double* scal;          // device scalars, S_COUNT doubles (ScalarSlot)
+    size_t partial_bytes;  // capacity of partials
 };
-constexpr int kMaxReduceBlocks = 1216;   // 152 SMs x 8
+// partial-sum buffer for a lattice of V sites: the widest per-block reduction of
+// the per-site kernels (32 floats per 128 sites) or kReducePartialsBytes
+inline size_t reduce_partial_bytes(long long V) {
+    const size_t per_site = (size_t)((V + 127) / 128) * 32 * sizeof(float);
+    return per_site > kReducePartialsBytes ? per_site : kReducePartialsBytes;
+}
 
 // ---------------------------------------------------------------- layout conversion
 template <typename T> void spinor_to_internal(v2<T>* out, const double2* in_lex, const Geom& g, cudaStream_t st);
@@ -201,6 +209,10 @@ enum { CGLS_AUTO = 0, CGLS_STREAM = 2, CGLS_SMEM = 3 };
 // iteration form of the on-chip CGLS: two grid-wide exchanges per iteration, or
 // the Chronopoulos-Gear form with one exchange and epoch-tagged shared vectors
 enum { CGLS_TEXTBOOK = 0, CGLS_CG_TAGGED = 1 };
+// latency probes on the same launch shape (maxit rounds, no arithmetic
+// dependence on the results): the two tagged stencils of one Chronopoulos-Gear
+// iteration without its exchange, or its exchange alone
+enum { CGLS_PROBE_STENCILS = 2, CGLS_PROBE_EXCHANGE = 3 };
 struct CglsArgs {
     const void* Au;        // float2 or __half2 units
     const float* su;       // FP16 block scales [X][d]; nullptr selects the FP32 operator
@@ -356,11 +368,11 @@ struct BatchCg {
     Geom g;
     BatchScal S;
     float* xpart;    // [Vc][npad]
-    float* rpart;    // [152][npad]
+    float* rpart;    // [kBatchRowChunks][npad]
     int* active;     // columns still iterating after the last check
     int* err;
 };
-constexpr int kBatchRowChunks = 152;
+constexpr int kBatchRowChunks = 152;   // row chunks of the batched CG's column sums (a buffer capacity)
 void bcg_start(const BatchCg& c, cudaStream_t st);
 void bcg_iteration(const BatchCg& c, cudaStream_t st);
 void bcg_finish(const BatchCg& c, cudaStream_t st);
