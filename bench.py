@@ -292,6 +292,41 @@ def flops_mg(w, info):
         cyc * (96.0 * w.nvec * V + krylov)
 
 
+def learned_leg(wmg, torch, w, U, V0, src, stream, prec):
+    """The learned setup against the plain one on this workload's field (the
+    start of the chain the network's training ensemble was drawn from, 10
+    sweeps before its first member): per setup its device time, the outer
+    iterations and time of one solve at the lightest mass, and the two-grid
+    rate (MR(4) smoother, coarse solve to 1e-5).  Variants: the plain Sec. IV
+    schedule (10 relaxations, 5 refinement iterations), the network's
+    prototypes with 2 refinement iterations, and with 10 relaxations + 2."""
+    from paper_1005_3043_gb300 import learned_setup as ls
+    if not os.path.exists(ls.WEIGHTS):
+        return {"unavailable": "no trained weights"}
+    base = mg_params(w, prec)
+    mg = wmg.WilsonMG(w.dims, base, stream=stream)
+    mg.set_links(U)
+    mg.nn_set_weights(wmg.nn_unflatten(np.load(ls.WEIGHTS)))
+    eta = ls.starts(w, w.nvec, 9200)
+    out = {"field": "the benchmark field (not a training member)", "mass": w.masses()[-1]}
+    for name, learned, relax, iters in (("plain", False, 10, 5), ("learned_r2", True, 0, 2),
+                                        ("learned_relax_r2", True, 10, 2)):
+        p = wmg.MgParams.from_buffer_copy(base)
+        p.setup_init_relax, p.setup_iters = relax, iters
+        mg.set_params(p)
+        mg.set_mass(w.setup_mass())
+        if learned:
+            mg.setup_learned(eta, refine_iters=iters)
+        else:
+            mg.setup(V0)
+        mg.set_mass(w.masses()[-1])
+        x, info = mg.solve(src)
+        out[name] = {"setup_ms": info["setup_ms"], "outer_iters": info["outer_iters"], "solve_ms": info["solve_ms"],
+                     "true_rel_res": info["true_rel_res"], "two_grid_rate": ls.two_grid_rate(wmg, mg, w)}
+    mg.close()
+    return out
+
+
 def eo_cg_leg(wmg, torch, w, U, dB, dX, masses, mg_infos, stream):
     """The comparison solver of Sec. IV (Fig. 1 and 2) on the same sources and
     masses: red-black preconditioned CG (FP32 iterations, FP64 reliable updates)
@@ -325,8 +360,10 @@ def eo_cg_leg(wmg, torch, w, U, dB, dX, masses, mg_infos, stream):
 
 def dslash_beyond_l2(wmg, torch, stream, peak):
     """The fine operator on a 24^3 x 64 lattice (hot-start links: the bandwidth
-    does not depend on them), L2 flushed before every launch: FP32 (480 B per
-    site, 425 MB per application) and FP16 storage (248 B per site)."""
+    does not depend on them): FP32 (480 B per site, 425 MB per application) and
+    FP16 storage (264 B per site), timed with the L2 flushed (a 512 MB buffer
+    written) before every launch and back to back (the 425 MB working set is
+    3.3x the L2, so back-to-back launches also read it from HBM)."""
     import synth
     L = (24, 24, 24, 64)
     U = synth.hot_gauge(L, 9)
@@ -336,11 +373,14 @@ def dslash_beyond_l2(wmg, torch, stream, peak):
     mg.set_links(U)
     mg.set_mass(-0.5)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
-    out = {"lattice": "24x24x24x64", "l2": "flushed before every launch", "peak_GBps": peak}
+    out = {"lattice": "24x24x24x64", "l2": "flushed before every launch; b2b_*: inputs larger than L2, back to back",
+           "peak_GBps": peak}
     for name, prec in (("fp32", wmg.MG_FP32), ("fp16", wmg.MG_FP16)):
         ms, nbytes = mg.time_dslash_cold(flush.data_ptr(), flush.numel(), prec, 50)
-        gbs = nbytes / (ms * 1e-3) / 1e9
-        out[name] = {"us": 1e3 * ms, "bytes": nbytes, "GB/s": gbs, "frac": gbs / peak}
+        ms2, _ = mg.time_dslash(prec, 200)
+        gbs, gbs2 = nbytes / (ms * 1e-3) / 1e9, nbytes / (ms2 * 1e-3) / 1e9
+        out[name] = {"us": 1e3 * ms, "bytes": nbytes, "GB/s": gbs, "frac": gbs / peak,
+                     "b2b_us": 1e3 * ms2, "b2b_GB/s": gbs2, "b2b_frac": gbs2 / peak}
     del flush
     mg.close()
     return out
@@ -493,6 +533,22 @@ def run_ours(args, w):
     ms_dc, _ = mg.time_dslash_cold(flush.data_ptr(), flush.numel(), ds_prec, 50)
     del flush
     coarse_kernel = wmg.COARSE_KERNELS.get(mg.coarse_kernel(), "unknown")
+    latency = None
+    if dom == "coarse_solve" and args.prec != "fp64" and coarse_iters > 0:
+        # the on-chip coarse CG's floor: its two tagged stencils alone and its
+        # exchange alone, on the same operator and launch shape
+        try:
+            us_st, us_x = mg.time_coarse_floor(500)
+        except wmg.MGError as e:   # no on-chip shape for this operator: no floor to report
+            us_st = us_x = None
+            latency = {"unavailable": str(e)}
+    if latency is None and dom == "coarse_solve" and args.prec != "fp64" and coarse_iters > 0:
+        us_it = dom_ms * 1e3 / coarse_iters
+        latency = {"us_per_cg_iteration": us_it, "us_two_stencils_only": us_st, "us_exchange_only": us_x,
+                   "floor_frac": us_st / us_it,
+                   "note": "operator resident on chip: the iteration is bound by the latency of its two "
+                           "stencils (tagged neighbour staging, products, emission); the exchange overlaps "
+                           "the second stencil; floor_frac = stencils-only time / time per CG iteration"}
     mg.close()
 
     # the other precision modes of the same step, and a batch of sources
@@ -531,6 +587,8 @@ def run_ours(args, w):
         extra["three_level"] = three_level_leg(wmg, torch, w, U, dV0, dB, dX, masses, stream, args.prec)
         extra["batched_24x24x24x64"] = batched_leg(wmg, torch, stream, args.prec)
         extra["eo_cg"] = eo_cg_leg(wmg, torch, w, U, dB, dX, masses, infos[:n_solve], stream)
+        if w.name == "wilson_16x16x16x32_nv20_beta6_5mass":
+            extra["learned_setup"] = learned_leg(wmg, torch, w, U, V0, srcs[-1], stream, args.prec)
         extra["dslash_24x24x24x64"] = dslash_beyond_l2(wmg, torch, stream, peak)
 
     if rank == 0:
@@ -554,7 +612,8 @@ def run_ours(args, w):
                          "kernel": {"coarse_solve": coarse_kernel, "dslash": "k_dslash",
                                     "true_residual": "k_dslash<double>"}.get(dom, dom),
                          "launches": dom_n, "avg_launch_ms": dom_ms / max(dom_n, 1), "work": unit_desc,
-                         "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
+                         "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                         "latency_floor": latency},
             "kernel_ms": {k: round(v[0], 3) for k, v in prof.items()},
             "dslash_alone": {"ms": ms_dc, "GB/s": bytes_ds / (ms_dc * 1e-3) / 1e9,
                              "frac": bytes_ds / (ms_dc * 1e-3) / 1e9 / peak, "l2": "flushed before every launch",

@@ -128,7 +128,13 @@ def two_grid_rate(wmg, mg, w, iters=16, seed=9300):
 
 
 def evaluate(n_train=32, n_eval=16, refine=(0, 1, 2), weights=WEIGHTS, with_rate=True, log=print):
-    """Plain against learned setup on held-out members n_train .. n_train + n_eval - 1."""
+    """Setups compared on held-out members n_train .. n_train + n_eval - 1 at the
+    lightest mass: "plain" (random starts, 10 relaxations, 5 refinement
+    iterations: the Sec. IV schedule), "plain_r{r}" (random starts, 10
+    relaxations, r iterations), "learned_r{r}" (network prototypes, no
+    relaxation, r iterations) and "learned_relax_r{r}" (network prototypes,
+    10 relaxations, r iterations).  Per setup: its device time, the outer
+    iterations and time of one solve, and the two-grid rate."""
     import torch
     import paper_1005_3043_gb300 as wmg
     import synth
@@ -141,26 +147,33 @@ def evaluate(n_train=32, n_eval=16, refine=(0, 1, 2), weights=WEIGHTS, with_rate
     b = synth.gaussian_spinor(w.dims, w.source_seed, stream=0)
     m = w.masses()[-1]
     st = torch.cuda.current_stream()
-    mg = wmg.WilsonMG(w.dims, make_params(wmg, w), stream=st)
+    base = make_params(wmg, w)
+    mg = wmg.WilsonMG(w.dims, base, stream=st)
     mg.nn_set_weights(wmg.nn_unflatten(np.load(weights)))
+    variants = [("plain", False, 10, 5)] + [(f"plain_r{r}", False, 10, r) for r in refine] + \
+               [(f"learned_r{r}", True, 0, r) for r in refine] + [(f"learned_relax_r{r}", True, 10, r) for r in refine]
     rows = []
     for k, U in ensemble(w, n_train + n_eval):
         if k < n_train:
             continue
         mg.set_links(U)
         row = {"member": k}
-        for name, r in [("plain", None)] + [(f"learned_refine{j}", j) for j in refine]:
+        for name, learned, relax, iters in variants:
+            p = wmg.MgParams.from_buffer_copy(base)
+            p.setup_init_relax, p.setup_iters = relax, iters
+            mg.set_params(p)
             mg.set_mass(w.setup_mass())
-            if r is None:
-                mg.setup(V0)
+            if learned:
+                mg.setup_learned(eta, refine_iters=iters)
             else:
-                mg.setup_learned(eta, refine_iters=r)
+                mg.setup(V0)
             mg.set_mass(m)
             x, info = mg.solve(b)
             row[name] = {"setup_ms": info["setup_ms"], "outer_iters": info["outer_iters"], "status": info["status"],
                          "solve_ms": info["solve_ms"], "true_rel_res": info["true_rel_res"]}
             if with_rate:
                 row[name]["two_grid_rate"] = two_grid_rate(wmg, mg, w)
+        mg.set_params(base)
         rows.append(row)
         log(json.dumps(row))
     mg.close()
