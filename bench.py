@@ -150,9 +150,13 @@ def mg_params(w, prec):
 
 
 def one_step_rate(wmg, torch, w, prec, U, dV0, dB, dX, masses, stream):
-    """solves/s of one step (setup + one solve per mass) in another precision mode"""
+    """solves/s of one step (setup + one solve per mass) in another precision
+    mode, with the launch timer on as in the headline step; also the coarse
+    CGNR's time per CG iteration in this mode"""
     mg = wmg.WilsonMG(w.dims, mg_params(w, prec), stream=stream)
     mg.set_links(U)
+    mg.profile_read()
+    mg.profile_enable(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     mg.set_mass(w.setup_mass())
@@ -166,9 +170,14 @@ def one_step_rate(wmg, torch, w, prec, U, dV0, dB, dX, masses, stream):
         iters.append(info["outer_iters"])
     e1.record(stream)
     torch.cuda.synchronize()
+    prof, coarse_iters = mg.profile_read()
+    mg.profile_enable(False)
+    kernel = wmg.COARSE_KERNELS.get(mg.coarse_kernel(), "unknown")
     mg.close()
     ms = e0.elapsed_time(e1)
-    return len(masses) / (ms / 1e3), ms, iters
+    coarse = {"kernel": kernel, "cg_iterations": coarse_iters,
+              "us_per_cg_iteration": 1e3 * prof["coarse_solve"][0] / coarse_iters if coarse_iters else None}
+    return len(masses) / (ms / 1e3), ms, iters, coarse
 
 
 def batched_leg(wmg, torch, stream, prec, name="wilson_24x24x24x64_nv24_beta6_76rhs", n_single=4):
@@ -208,6 +217,8 @@ def batched_leg(wmg, torch, stream, prec, name="wilson_24x24x24x64_nv24_beta6_76
     e1.record(stream)
     torch.cuda.synchronize()
     bms = e0.elapsed_time(e1)
+    # the tensor-core coarse stencil alone on a panel of this many columns
+    tc_ms, tc_bytes, tc_flops = mg.time_coarse_batched(dB.shape[0], 20)
     pick = list(range(n_single // 2)) + list(range(12, 12 + n_single - n_single // 2))
     mg.solve_device(dB[0], dX[0])                   # warm-up of the single-source path
     e0.record(stream)
@@ -228,7 +239,39 @@ def batched_leg(wmg, torch, stream, prec, name="wilson_24x24x24x64_nv24_beta6_76
            "single_outer_iters": [i["outer_iters"] for i in sinfo],
            "single_max_true_rel_res": max(i["true_rel_res"] for i in sinfo)}
     out["batched_over_single"] = out["batched_solves_per_s"] / out["single_solves_per_s"]
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm, bf16 = peaks.get("hbm_gbs", 6800.0), peaks.get("bf16_tflops", 1900.0)
+    out["tc_stencil"] = {"kernel": "k_coarse_apply_tc", "columns": n, "us": 1e3 * tc_ms,
+                         "bytes": tc_bytes, "GB/s": tc_bytes / (tc_ms * 1e-3) / 1e9,
+                         "hbm_frac": tc_bytes / (tc_ms * 1e-3) / 1e9 / hbm,
+                         "useful_TFLOP/s": tc_flops / (tc_ms * 1e-3) / 1e12,
+                         "tensor_frac": tc_flops / (tc_ms * 1e-3) / 1e12 / bf16,
+                         "note": "bound by streaming the FP16 embedded operator (9 x (2Nv x 2)^2 halves per aggregate, "
+                                 "larger than L2); useful flops exclude the padding of M to 128 and the hi/lo "
+                                 "split; peaks of MEASURED_PEAKS.json (HBM copy, bf16 burst)"}
     return out
+
+
+def coarse_tc_probe(nrhs=64, reps=20):
+    """One small case of the tensor-core batched coarse stencil for a profiler:
+    the 16^3 x 32 level after its setup, a panel of nrhs columns."""
+    import torch
+    import paper_1005_3043_gb300 as wmg
+    wmg.load()
+    w = WORKLOADS["wilson_16x16x16x32_nv20_beta6_5mass"]
+    U, V0, srcs, masses, plaq = make_inputs(w)
+    mg = wmg.WilsonMG(w.dims, mg_params(w, "fp16"), stream=torch.cuda.current_stream())
+    mg.set_links(U)
+    mg.set_mass(w.setup_mass())
+    mg.setup(V0)
+    ms, nb, fl = mg.time_coarse_batched(nrhs, reps)
+    mg.close()
+    print(json.dumps({"kernel": "k_coarse_apply_tc", "workload": w.name, "columns": nrhs, "us": 1e3 * ms,
+                      "GB/s": nb / (ms * 1e-3) / 1e9, "useful_TFLOP/s": fl / (ms * 1e-3) / 1e12}), flush=True)
 
 
 def three_level_leg(wmg, torch, w, U, dV0, dB, dX, masses, stream, prec, nv2=32, block2=(2, 2, 2, 2)):
@@ -292,38 +335,47 @@ def flops_mg(w, info):
         cyc * (96.0 * w.nvec * V + krylov)
 
 
-def learned_leg(wmg, torch, w, U, V0, src, stream, prec):
-    """The learned setup against the plain one on this workload's field (the
-    start of the chain the network's training ensemble was drawn from, 10
-    sweeps before its first member): per setup its device time, the outer
-    iterations and time of one solve at the lightest mass, and the two-grid
-    rate (MR(4) smoother, coarse solve to 1e-5).  Variants: the plain Sec. IV
-    schedule (10 relaxations, 5 refinement iterations), the network's
-    prototypes with 2 refinement iterations, and with 10 relaxations + 2."""
+def learned_leg(wmg, torch, w, U, V0, src, stream, prec, members=(32, 33)):
+    """The learned setup against the plain one on held-out fields of the
+    network's ensemble (members 32 and 33 of the chain started from this
+    workload's field; the network trained on members 0-31): per setup its
+    device time, the outer iterations and time of one solve at the lightest
+    mass, and the two-grid rate (MR(4) smoother, coarse solve to 1e-5).
+    Variants: the plain Sec. IV schedule (10 relaxations, 5 refinement
+    iterations), plain with 2 iterations, and the network's prototypes with 10
+    relaxations + 2 iterations and with 2 iterations alone."""
     from paper_1005_3043_gb300 import learned_setup as ls
     if not os.path.exists(ls.WEIGHTS):
         return {"unavailable": "no trained weights"}
     base = mg_params(w, prec)
     mg = wmg.WilsonMG(w.dims, base, stream=stream)
-    mg.set_links(U)
     mg.nn_set_weights(wmg.nn_unflatten(np.load(ls.WEIGHTS)))
     eta = ls.starts(w, w.nvec, 9200)
-    out = {"field": "the benchmark field (not a training member)", "mass": w.masses()[-1]}
-    for name, learned, relax, iters in (("plain", False, 10, 5), ("learned_r2", True, 0, 2),
-                                        ("learned_relax_r2", True, 10, 2)):
-        p = wmg.MgParams.from_buffer_copy(base)
-        p.setup_init_relax, p.setup_iters = relax, iters
-        mg.set_params(p)
-        mg.set_mass(w.setup_mass())
-        if learned:
-            mg.setup_learned(eta, refine_iters=iters)
-        else:
-            mg.setup(V0)
-        mg.set_mass(w.masses()[-1])
-        x, info = mg.solve(src)
-        out[name] = {"setup_ms": info["setup_ms"], "outer_iters": info["outer_iters"], "solve_ms": info["solve_ms"],
-                     "true_rel_res": info["true_rel_res"], "two_grid_rate": ls.two_grid_rate(wmg, mg, w)}
+    variants = (("plain", False, 10, 5), ("plain_r2", False, 10, 2), ("learned_relax_r2", True, 10, 2),
+                ("learned_r2", True, 0, 2))
+    out = {"fields": "held-out members %s of the training ensemble" % (list(members),), "mass": w.masses()[-1]}
+    rows = {}
+    for k, Uk in ls.ensemble(w, max(members) + 1):
+        if k not in members:
+            continue
+        mg.set_links(Uk)
+        for name, learned, relax, iters in variants:
+            p = wmg.MgParams.from_buffer_copy(base)
+            p.setup_init_relax, p.setup_iters = relax, iters
+            mg.set_params(p)
+            mg.set_mass(w.setup_mass())
+            if learned:
+                mg.setup_learned(eta, refine_iters=iters)
+            else:
+                mg.setup(V0)
+            mg.set_mass(w.masses()[-1])
+            x, info = mg.solve(src)
+            rows.setdefault(name, []).append(
+                {"member": k, "setup_ms": info["setup_ms"], "outer_iters": info["outer_iters"],
+                 "solve_ms": info["solve_ms"], "true_rel_res": info["true_rel_res"],
+                 "two_grid_rate": ls.two_grid_rate(wmg, mg, w)})
     mg.close()
+    out.update(rows)
     return out
 
 
@@ -558,8 +610,8 @@ def run_ours(args, w):
         for mode in ("fp64", "fp32", "fp16"):
             if mode == args.prec:
                 continue
-            r, msm, itm = one_step_rate(wmg, torch, w, mode, U, dV0, dB, dX, masses, stream)
-            extra[names[mode]] = {"value": r, "ms_per_step": msm, "outer_iters": itm}
+            r, msm, itm, cg = one_step_rate(wmg, torch, w, mode, U, dV0, dB, dX, masses, stream)
+            extra[names[mode]] = {"value": r, "ms_per_step": msm, "outer_iters": itm, "coarse": cg}
         if "plain_fp64" in extra:
             extra["vs_plain_fp64"] = value / world / extra["plain_fp64"]["value"]
         bsrc = batch_sources(w)

@@ -315,6 +315,16 @@ int mg_solve_eo_cg(mg_ctx* ctx, const double* b, double* x, double tol, int maxi
 int mg_solve_eo_cg_device(mg_ctx* ctx, const double* b_dev, double* x_dev, double tol, int maxit, int prec,
                           mg_solve_info* info);
 
+/* Timing of the tensor-core batched coarse stencil (measurement hook, no
+ * counterpart in the paper): `reps` launches of y = D_c x on a device panel of
+ * nrhs columns (the chunk width from the autotuner), CUDA events on the
+ * context stream; *ms_per_launch, and per launch the algorithmic bytes (the
+ * FP16 embedded operator once, the FP32 panel read and written once) and the
+ * useful flops (8 per complex multiply-add of D_c x_n).  Allocates and frees
+ * two panels.  Same shape limits as mg_apply_coarse_batched with impl 0. */
+int mg_time_coarse_batched(mg_ctx* ctx, int nrhs, int reps, double* ms_per_launch, double* bytes_per_launch,
+                           double* flops_per_launch);
+
 /* Coarse stencil (Sec. III) on nrhs coarse vectors at once: y_n = D_c x_n
  * (dagger: D_c^dag).  x, y: nrhs consecutive host coarse vectors, nrhs <= 256.
  * impl 0: tensor cores (operator rounded to FP16 without scale, each source

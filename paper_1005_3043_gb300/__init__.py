@@ -107,6 +107,7 @@ _SIGS = {
     "mg_vcycle": ([_P, _P, _P, _I], _I),
     "mg_time_dslash": ([_P, _I, _I, _P, _P], _I),
     "mg_time_coarse_floor": ([_P, _I, _P, _P], _I),
+    "mg_time_coarse_batched": ([_P, _I, _I, _P, _P, _P], _I),
     "mg_time_dslash_cold": ([_P, _I, _I, _P, ctypes.c_size_t, _P, _P], _I),
     "mg_profile_enable": ([_P, _I], _I),
     "mg_profile_read": ([_P, _P, _P, _P], _I),
@@ -462,6 +463,14 @@ def mg_time_coarse_floor(ctx, rounds: int = 200):
     return a.value, b.value
 
 
+def mg_time_coarse_batched(ctx, nrhs: int, reps: int = 20):
+    """(ms per launch, algorithmic bytes, useful flops) of the tensor-core batched coarse stencil."""
+    ms, nb, fl = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
+    _check(load().mg_time_coarse_batched(ctx, int(nrhs), int(reps), ctypes.byref(ms), ctypes.byref(nb),
+                                         ctypes.byref(fl)), ctx)
+    return ms.value, nb.value, fl.value
+
+
 def mg_time_dslash_cold(ctx, flush_ptr: int, flush_bytes: int, prec: int = MG_FP32, reps: int = 20):
     """Mean dslash time with the L2 flushed (a device buffer of flush_bytes overwritten) before each launch."""
     ms = ctypes.c_double(0)
@@ -658,6 +667,9 @@ class WilsonMG:
 
     def time_coarse_floor(self, rounds=200):
         return mg_time_coarse_floor(self.ctx, rounds)
+
+    def time_coarse_batched(self, nrhs, reps=20):
+        return mg_time_coarse_batched(self.ctx, nrhs, reps)
 
     def time_dslash_cold(self, flush_ptr: int, flush_bytes: int, prec=MG_FP32, reps=20):
         return mg_time_dslash_cold(self.ctx, flush_ptr, flush_bytes, prec, reps)

@@ -85,6 +85,7 @@ void coarse_embed(__half* Aemb, const double2* A, int nc, int Vc, cudaStream_t s
 
 // ---------------------------------------------------------------- tensor-core batched stencil
 constexpr int kTcThreads = 128;
+constexpr int kTcMaxStages = 3;   // pipeline depth when it fits shared memory, else 2
 constexpr long long kTcWaitLimit = 20000000LL;
 
 __host__ __device__ inline int tc_tmem_cols(int npad) {
@@ -92,47 +93,85 @@ __host__ __device__ inline int tc_tmem_cols(int npad) {
     while (c < npad) c <<= 1;
     return c;
 }
-__host__ __device__ inline size_t tc_smem_bytes(int nc, int npad) {
-    size_t K = 2 * nc;
-    size_t SA = 128 * K * 2, SB = (size_t)npad * K * 2;
-    return 2 * SA + 4 * SB + 64;
+// one pipeline stage: the (padded) 128-row A tile, the hi and lo B tiles
+__host__ __device__ inline size_t tc_stage_bytes(int nc, int nw) {
+    const size_t K = 2 * nc;
+    return 128 * K * 2 + 2 * (size_t)nw * K * 2;
+}
+constexpr size_t kTcStaticSmem = 256;   // barriers, TMEM address, flag
+__host__ __device__ inline int tc_stages(int nc, int nw) {
+    return kTcMaxStages * tc_stage_bytes(nc, nw) + kTcStaticSmem <= 227 * 1024 ? kTcMaxStages : 2;
+}
+__host__ __device__ inline size_t tc_smem_bytes(int nc, int nw) { return tc_stages(nc, nw) * tc_stage_bytes(nc, nw); }
+
+// The operand panel as FP16 hi + lo tiles in the tensor-core shared-memory
+// layout, one tile pair per (aggregate Y, column chunk c):
+//   bt[((Y * nch + c) * 2 + {0 hi, 1 lo}) * nw * K + core_off(n, k, K)],
+// k = b (real part) or nc + b (imaginary part) of x[Y][b][c * nw + n], with the
+// column scale and, for the adjoint, the sigma3 sign of rows b >= nc/2 applied.
+// One thread per (Y, c, n, 8-column group of k): two 16-byte stores.
+__global__ void k_tc_split(__half* __restrict__ bt, const float2* __restrict__ x, int nc, int npad, int nw, int dag,
+                           const double* __restrict__ colscale, long long total) {
+    const int K = 2 * nc, kg8 = K >> 3, nch = npad / nw, nvh = nc >> 1;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int kg = (int)(i % kg8);
+        long long t = i / kg8;
+        const int n = (int)(t % nw);
+        t /= nw;
+        const int c = (int)(t % nch);
+        const long long Y = t / nch;
+        const int col = c * nw + n;
+        const float sc = colscale ? (float)colscale[col] : 1.f;
+        __align__(16) __half hi[8], lo[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int k = kg * 8 + e, b = k < nc ? k : k - nc;
+            const float2 v = x[((size_t)Y * nc + b) * npad + col];
+            float f = (k < nc ? v.x : v.y) * sc;
+            if (dag && b >= nvh) f = -f;
+            const __half h = __float2half_rn(f);
+            hi[e] = h;
+            lo[e] = __float2half_rn(f - __half2float(h));
+        }
+        __half* base = bt + ((size_t)(Y * nch + c) * 2) * nw * K + core_off(n, kg * 8, K);
+        *reinterpret_cast<uint4*>(base) = *reinterpret_cast<const uint4*>(hi);
+        *reinterpret_cast<uint4*>(base + (size_t)nw * K) = *reinterpret_cast<const uint4*>(lo);
+    }
 }
 
-// One CTA per (aggregate X, column chunk of width nw).  Pipeline over the 9
-// directions d with two stages:
-// the bulk-copy engine brings A_emb[X][d], the CTA writes the hi/lo split of
-// x[X+d] (sigma3 applied for the adjoint), one thread issues the MMAs into the
-// TMEM accumulator (128 lanes = embedded rows, npad columns = RHS).
+// One CTA per (aggregate X, column chunk of width nw).  Thread 0 runs a
+// pipeline of 3 (or, where shared memory is short, 2) stages over the 9
+// directions d: the bulk-copy engine brings
+// A_emb[X][d] and the hi/lo tiles of x[X+d] (split beforehand by k_tc_split)
+// into a stage, thread 0 issues the MMAs (hi and lo per K step) into the TMEM
+// accumulator (128 lanes = embedded rows, nw columns = right-hand sides) and
+// commits them to the stage's "empty" barrier; a stage is refilled once its
+// MMAs are done.  Then the four warps read the accumulator back.
 __global__ void __launch_bounds__(kTcThreads, 1) k_coarse_apply_tc(TcApplyArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    const int nc = a.nc, npad = a.npad, nw = a.nw, n0 = blockIdx.y * nw, K = 2 * nc, nvh = nc / 2;
-    const size_t SA = (size_t)128 * K * 2, SB = (size_t)nw * K * 2;
-    __half* As = reinterpret_cast<__half*>(smem);
-    __half* Bh = reinterpret_cast<__half*>(smem + 2 * SA);
-    __half* Bl = reinterpret_cast<__half*>(smem + 2 * SA + 2 * SB);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * SA + 4 * SB);   // [0,1]: A landed, [2,3]: MMA done
+    // grid (column chunks, aggregates): the chunks of one aggregate run side by
+    // side and share its operator tiles through L2
+    const int nc = a.nc, npad = a.npad, nw = a.nw, chunk = blockIdx.x, n0 = chunk * nw, K = 2 * nc, nvh = nc / 2;
+    const int nch = npad / nw, S = tc_stages(nc, nw);
+    const size_t SA = (size_t)128 * K * 2, SB = (size_t)nw * K * 2, SS = SA + 2 * SB;
+    __shared__ __align__(8) uint64_t bar[2 * kTcMaxStages];   // [0, S): stage full, [S, 2S): stage empty
     __shared__ uint32_t s_taddr;
-    __shared__ int s_fail;
-    __shared__ int s_last_commit;     // stage * 2 + parity of the last MMA commit, -1: none
-    __shared__ float s_nrm[4][256];
-    const int X = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    __shared__ int s_ok;
+    const int X = blockIdx.y, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t ncols = tc_tmem_cols(nw);
-    const uint32_t bytesA = (uint32_t)(K * K * 2);
+    const uint32_t bytesA = (uint32_t)(K * K * 2), bytesB = (uint32_t)SB;
 
-    // bulk copy issued by thread 0 and not yet seen complete: stage, parity
-    int copy_pending = -1, copy_parity = 0;
     if (tid == 0) {
-        s_fail = 0;
-        s_last_commit = -1;
-        for (int i = 0; i < 4; ++i) mbar_init(bar + i, 1);
+        for (int i = 0; i < 2 * S; ++i) mbar_init(bar + i, 1);
         fence_mbar_init();
     }
-    // zero the padding rows (2nc..127) of both A stages once
-    {
-        const int pad0 = (K >> 3) * (K >> 3) * 64;   // first half of row group 2nc/8
-        for (int st = 0; st < 2; ++st)
-            for (int i = pad0 + tid; i < 128 * K; i += kTcThreads) As[st * 128 * K + i] = __float2half(0.f);
+    // zero the padding rows (2nc..127) of every stage's A tile once
+    for (int st = 0; st < S; ++st) {
+        __half* As = reinterpret_cast<__half*>(smem + st * SS);
+        for (int i = K * K + tid; i < 128 * K; i += kTcThreads) As[i] = __float2half(0.f);
     }
+    fence_proxy_async();   // the zeros are read by the MMAs (async proxy)
     if (warp == 0) {
         tmem_alloc(&s_taddr, ncols);
         tmem_relinquish();
@@ -141,107 +180,89 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_coarse_apply_tc(TcApplyArgs a
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_taddr;
-    const uint32_t idesc = idesc_f16(128, nw);
-    const uint32_t lbo = 128, sbo = (uint32_t)(K >> 3) * 128;
 
-    for (int d = 0; d < 9; ++d) {
-        const int s = d & 1;
-        if (d >= 2) {
-            // the MMAs that read stage s (direction d-2) must be done before it is rewritten
-            if (!mbar_wait(bar + 2 + s, ((d - 2) >> 1) & 1, kTcWaitLimit)) s_fail = 1;
-        }
-        __syncthreads();
-        if (s_fail) break;
-        if (tid == 0) {
-            mbar_expect_tx(bar + s, bytesA);
-            bulk_copy_g2s(As + (size_t)s * 128 * K, a.Aemb + ((size_t)X * 9 + d) * K * K, bytesA, bar + s);
-            copy_pending = s;
-            copy_parity = (d >> 1) & 1;
-        }
-        // B = x[X+d] as hi + lo FP16, rows = RHS n, K-major columns k = (re|im, b)
-        const int Y = coarse_neighbour(a.g, X, d);
-        const float2* xY = a.x + (size_t)Y * nc * npad + n0;
-        __half* bh = Bh + (size_t)s * nw * K;
-        __half* bl = Bl + (size_t)s * nw * K;
-        for (int i = tid; i < nc * nw; i += kTcThreads) {
-            int b = i / nw, n = i - b * nw;
-            float2 v = xY[(size_t)b * npad + n];
-            if (a.colscale) {
-                const float sc = (float)a.colscale[n0 + n];
-                v.x *= sc;
-                v.y *= sc;
+    if (tid == 0) {
+        const uint32_t idesc = idesc_f16(128, nw);
+        const uint32_t lbo = 128, sbo = (uint32_t)(K >> 3) * 128;
+        // stage bookkeeping for the drain: parity of the copy in flight per stage (-1: none)
+        int pending[kTcMaxStages];
+        for (int st = 0; st < kTcMaxStages; ++st) pending[st] = -1;
+        auto issue = [&](int d, int st) {
+            unsigned char* base = smem + st * SS;
+            const int Y = coarse_neighbour(a.g, X, d);
+            mbar_expect_tx(bar + st, bytesA + 2 * bytesB);
+            bulk_copy_g2s(base, a.Aemb + ((size_t)X * 9 + d) * K * K, bytesA, bar + st);
+            const __half* bsrc = a.bt + ((size_t)(Y * nch + chunk) * 2) * nw * K;
+            bulk_copy_g2s(base + SA, bsrc, bytesB, bar + st);
+            bulk_copy_g2s(base + SA + SB, bsrc + (size_t)nw * K, bytesB, bar + st);
+            pending[st] = (d / S) & 1;
+        };
+        bool ok = true;
+        int last = -1;   // stage * 2 + parity of the last commit
+        for (int d = 0; d < S && d < 9; ++d) issue(d, d);
+        for (int d = 0; d < 9 && ok; ++d) {
+            // refill the stage the previous direction's MMAs used, once they are done
+            const int dp = d - 1;
+            if (dp >= 0 && dp + S < 9) {
+                const int sp = dp % S;
+                if (!mbar_wait(bar + S + sp, (uint32_t)((dp / S) & 1), kTcWaitLimit)) { ok = false; break; }
+                issue(dp + S, sp);
             }
-            if (a.dag && b >= nvh) { v.x = -v.x; v.y = -v.y; }
-            __half hr = __float2half_rn(v.x), hi = __float2half_rn(v.y);
-            __half lr = __float2half_rn(v.x - __half2float(hr)), li = __float2half_rn(v.y - __half2float(hi));
-            int ore = core_off(n, b, K), oim = core_off(n, b + nc, K);
-            bh[ore] = hr; bl[ore] = lr;
-            bh[oim] = hi; bl[oim] = li;
-        }
-        fence_proxy_async();
-        __syncthreads();
-        if (tid == 0) {
-            if (!mbar_wait(bar + s, (d >> 1) & 1, kTcWaitLimit)) {
-                s_fail = 1;
-            } else {
-                copy_pending = -1;
-                tc_fence_after();
-                const uint32_t a0 = smem_u32(As + (size_t)s * 128 * K);
-                const uint32_t bh0 = smem_u32(bh), bl0 = smem_u32(bl);
-                for (int ks = 0; ks < (K >> 4); ++ks) {
-                    uint64_t ad = smem_desc(a0 + ks * 256, lbo, sbo);
-                    mma_f16(tmem, ad, smem_desc(bh0 + ks * 256, lbo, sbo), idesc, (d > 0 || ks > 0) ? 1u : 0u);
-                    mma_f16(tmem, ad, smem_desc(bl0 + ks * 256, lbo, sbo), idesc, 1u);
-                }
-                mma_commit(bar + 2 + s);
-                s_last_commit = s * 2 + ((d >> 1) & 1);
+            const int s = d % S;
+            if (!mbar_wait(bar + s, (uint32_t)((d / S) & 1), kTcWaitLimit)) { ok = false; break; }
+            pending[s] = -1;
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(smem + s * SS), bh0 = a0 + (uint32_t)SA, bl0 = bh0 + (uint32_t)SB;
+            for (int ks = 0; ks < (K >> 4); ++ks) {
+                const uint64_t ad = smem_desc(a0 + ks * 256, lbo, sbo);
+                mma_f16(tmem, ad, smem_desc(bh0 + ks * 256, lbo, sbo), idesc, (d > 0 || ks > 0) ? 1u : 0u);
+                mma_f16(tmem, ad, smem_desc(bl0 + ks * 256, lbo, sbo), idesc, 1u);
             }
+            mma_commit(bar + S + s);
+            last = s * 2 + ((d / S) & 1);
         }
+        // drain: the last commit covers every MMA issued; then every copy still in flight
+        if (last >= 0 && !mbar_wait(bar + S + (last >> 1), (uint32_t)(last & 1), kTcWaitLimit)) ok = false;
+        for (int st = 0; st < S; ++st)
+            if (pending[st] >= 0 && !mbar_wait(bar + st, (uint32_t)pending[st], kTcWaitLimit)) ok = false;
+        s_ok = ok ? 1 : 0;
     }
     __syncthreads();
-    // Wait for the last commit (direction 8 on stage 0, its 5th use, when nothing
-    // failed): it covers every MMA this CTA issued.  After a failed wait the CTA
-    // still drains what it started -- the last MMAs and a bulk copy it has not
-    // seen land -- with bounded waits, so that no asynchronous write into its
-    // shared or tensor memory outlives it.
-    bool ok = (s_fail == 0);
-    const int lc = s_last_commit;
-    if (lc >= 0 && !mbar_wait(bar + 2 + (lc >> 1), lc & 1, kTcWaitLimit)) ok = false;
-    if (tid == 0 && copy_pending >= 0 && !mbar_wait(bar + copy_pending, copy_parity, kTcWaitLimit)) ok = false;
+    const bool ok = s_ok != 0;
     tc_fence_after();
-    // epilogue: warp w owns TMEM lanes 32w..32w+31 = embedded rows m
+    // epilogue: warp w reads TMEM lanes 32w..32w+31 (embedded rows m) into a
+    // row-major tile in the (now idle) stage memory, T[m][n] (stride nw + 1);
+    // then rows a (real part) and nc + a (imaginary part) leave as one complex
+    // column-contiguous row of y, coalesced over the right-hand sides n
+    float* T = reinterpret_cast<float*>(smem);
+    const int ts = nw + 1;
     const int m = warp * 32 + lane;
-    const bool valid_row = m < K;
-    const int arow = m % nc;
-    const bool im = m >= nc;
-    const float sgn = (a.dag && arow >= nvh) ? -1.f : 1.f;
-    float* yf = reinterpret_cast<float*>(a.y);
     for (int c0 = 0; c0 < nw; c0 += 16) {
         float v[16];
         tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-        if (a.colscale)
-#pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] *= (float)(1.0 / a.colscale[n0 + c0 + j]);
-        if (ok && valid_row) {
+        if (m < K)
 #pragma unroll
             for (int j = 0; j < 16; ++j)
-                yf[(((size_t)X * nc + arow) * npad + n0 + c0 + j) * 2 + (im ? 1 : 0)] = sgn * v[j];
-        }
-        if (a.norms) {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                float q = (ok && valid_row) ? v[j] * v[j] : 0.f;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
-                if (lane == 0) s_nrm[warp][c0 + j] = q;
-            }
-        }
+                T[m * ts + c0 + j] = a.colscale ? v[j] * (float)(1.0 / a.colscale[n0 + c0 + j]) : v[j];
     }
     tc_fence_before();
     __syncthreads();
-    if (a.norms)
-        for (int n = tid; n < nw; n += kTcThreads)
-            a.norms[(size_t)X * npad + n0 + n] = s_nrm[0][n] + s_nrm[1][n] + s_nrm[2][n] + s_nrm[3][n];
+    if (ok) {
+        float2* y = a.y;
+        for (int i = tid; i < nc * nw; i += kTcThreads) {
+            const int ar = i / nw, n = i - ar * nw;
+            const float sg = (a.dag && ar >= nvh) ? -1.f : 1.f;
+            y[((size_t)X * nc + ar) * npad + n0 + n] = make_float2(sg * T[ar * ts + n], sg * T[(nc + ar) * ts + n]);
+        }
+        if (a.norms)
+            for (int n = tid; n < nw; n += kTcThreads) {
+                float q = 0.f;
+                for (int r = 0; r < K; ++r) q += T[r * ts + n] * T[r * ts + n];
+                a.norms[(size_t)X * npad + n0 + n] = q;
+            }
+    } else if (a.norms) {
+        for (int n = tid; n < nw; n += kTcThreads) a.norms[(size_t)X * npad + n0 + n] = 0.f;
+    }
     if (!ok && tid == 0) atomicExch(a.err, 1);
     if (warp == 0) tmem_dealloc(tmem, ncols);
 }
@@ -257,7 +278,7 @@ static size_t tc_launch_smem(int nc, int nw) {
 }
 bool coarse_apply_tc_supported(int nc, int npad) {
     return npad % 16 == 0 && npad >= 16 && npad <= 256 && (2 * nc) % 16 == 0 && 2 * nc <= 128 &&
-           tc_launch_smem(nc, npad) + 4224 <= 227 * 1024;
+           tc_launch_smem(nc, npad) + kTcStaticSmem <= 227 * 1024;
 }
 // attribute for the largest chunk width used with this nc (every nw <= npad fits)
 cudaError_t coarse_apply_tc_prepare(int nc, int npad) {
@@ -271,10 +292,15 @@ cudaError_t coarse_apply_tc_prepare(int nc, int npad) {
 cudaError_t coarse_apply_tc(const TcApplyArgs& args, cudaStream_t st) {
     TcApplyArgs a = args;
     if (a.nw <= 0) a.nw = a.npad;
+    if (!a.bt || a.g.Vc > 65535) return cudaErrorInvalidValue;   // aggregates index grid.y
+    const long long total = (long long)a.g.Vc * a.npad * (2 * a.nc / 8);
+    note_launch();
+    k_tc_split<<<(int)std::min<long long>((total + 255) / 256, 16LL * device_sm_count()), 256, 0, st>>>(
+        a.bt, a.x, a.nc, a.npad, a.nw, a.dag, a.colscale, total);
     TmemOrder order(st);
     if (order.error() != cudaSuccess) return order.error();
     note_launch();
-    k_coarse_apply_tc<<<dim3(a.g.Vc, a.npad / a.nw), kTcThreads, tc_launch_smem(a.nc, a.nw), st>>>(a);
+    k_coarse_apply_tc<<<dim3(a.npad / a.nw, a.g.Vc), kTcThreads, tc_launch_smem(a.nc, a.nw), st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return order.launched();
@@ -537,7 +563,7 @@ void bcg_iteration(const BatchCg& c, cudaStream_t st) {
     const long long rows = (long long)c.g.Vc * c.nc, total = rows * c.npad;
     const int ct = col_threads(c.npad);
     const size_t cs = col_smem(c.npad);
-    TcApplyArgs ap{c.Aemb, c.p, c.q, c.nc, c.npad, c.nw, 0, c.g, c.xpart, c.err, c.S.csp};
+    TcApplyArgs ap{c.Aemb, c.p, c.q, c.nc, c.npad, c.nw, 0, c.g, c.xpart, c.err, c.S.csp, c.bt};
     coarse_apply_tc(ap, st);                                                               // q = D_c p
     note_launch();
     k_bcg_alpha<<<c.npad, 256, 0, st>>>(c.S, c.xpart, c.g.Vc, c.npad);
@@ -545,7 +571,7 @@ void bcg_iteration(const BatchCg& c, cudaStream_t st) {
     k_bcg_update1<<<kRowChunks, ct, cs, st>>>(c.y, c.r, c.p, c.q, rows, c.npad, c.S, c.rpart, c.active);
     note_launch();
     k_bcg_check<<<c.npad, 256, 0, st>>>(c.S, c.rpart, kRowChunks, c.npad, c.tol2, c.maxit, c.active, rows);
-    TcApplyArgs as{c.Aemb, c.r, c.s, c.nc, c.npad, c.nw, 1, c.g, c.xpart, c.err, c.S.csr};
+    TcApplyArgs as{c.Aemb, c.r, c.s, c.nc, c.npad, c.nw, 1, c.g, c.xpart, c.err, c.S.csr, c.bt};
     coarse_apply_tc(as, st);                                                               // s = D_c^dag r
     note_launch();
     k_bcg_beta<<<c.npad, 256, 0, st>>>(c.S, c.xpart, c.g.Vc, c.npad, rows);
@@ -562,7 +588,7 @@ void bcg_start(const BatchCg& c, cudaStream_t st) {
     k_bcg_scale<<<c.npad, 256, 0, st>>>(c.S, c.rpart, kRowChunks, c.npad, c.nrhs, c.maxit, rows);
     note_launch();
     k_bcg_start<<<ew_grid(total), 256, 0, st>>>(c.y, c.r, c.rc, total, c.npad, c.S);
-    TcApplyArgs as{c.Aemb, c.r, c.s, c.nc, c.npad, c.nw, 1, c.g, c.xpart, c.err, c.S.csr};
+    TcApplyArgs as{c.Aemb, c.r, c.s, c.nc, c.npad, c.nw, 1, c.g, c.xpart, c.err, c.S.csr, c.bt};
     coarse_apply_tc(as, st);
     note_launch();
     k_bcg_gamma0<<<c.npad, 256, 0, st>>>(c.S, c.xpart, c.g.Vc, c.npad, rows);

@@ -51,6 +51,7 @@ struct BatchWork {
     int npad = 0, nrhs_cap = 0, K = 0, nc = 0;
     float2 *rcB = nullptr, *yB = nullptr, *rB = nullptr, *sB = nullptr, *pB = nullptr, *qB = nullptr;
     double* cgs = nullptr;          // 9 x npad per-RHS CG scalars
+    __half* bt = nullptr;           // split operand tiles of the tensor-core stencil
     float* xpart = nullptr;         // Vc x npad
     float* rpart = nullptr;         // kBatchRowChunks x npad
     int* flags = nullptr;           // [0] active columns, [1] error
@@ -2540,6 +2541,7 @@ int ensure_batch(mg_ctx* ctx, int nrhs) {
     if (b.npad || b.nrhs_cap) {   // grow: release the smaller workspace first
         CK(cudaStreamSynchronize(ctx->st));
         for (void* q : {(void*)b.rcB, (void*)b.yB, (void*)b.rB, (void*)b.sB, (void*)b.pB, (void*)b.qB, (void*)b.cgs,
+                        (void*)b.bt,
                         (void*)b.xpart, (void*)b.rpart, (void*)b.flags, (void*)b.r32, (void*)b.Z, (void*)b.Pk,
                         (void*)b.x64, (void*)b.b64, (void*)b.scal})
             dfree(ctx, q);
@@ -2559,6 +2561,7 @@ int ensure_batch(mg_ctx* ctx, int nrhs) {
     TRY(dalloc(ctx, &b.pB, sizeof(float2) * pe));
     TRY(dalloc(ctx, &b.qB, sizeof(float2) * pe));
     TRY(dalloc(ctx, &b.cgs, sizeof(double) * 9 * npad));
+    TRY(dalloc(ctx, &b.bt, tc_split_bytes(nc, npad, ctx->g.Vc)));
     TRY(dalloc(ctx, &b.xpart, sizeof(float) * (size_t)ctx->g.Vc * npad));
     TRY(dalloc(ctx, &b.rpart, sizeof(float) * kBatchRowChunks * npad));
     TRY(dalloc(ctx, &b.flags, sizeof(int) * 4));
@@ -2585,6 +2588,7 @@ BatchCg batch_cg(mg_ctx* ctx, double tol, int maxit, int nrhs) {
     BatchWork& b = ctx->bw;
     BatchCg c;
     c.Aemb = ctx->full.Aemb;
+    c.bt = b.bt;
     c.y = b.yB; c.r = b.rB; c.s = b.sB; c.p = b.pB; c.q = b.qB; c.rc = b.rcB;
     c.nc = ctx->full.nc; c.npad = b.npad; c.nw = b.npad; c.nrhs = nrhs; c.maxit = maxit;
     c.tol2 = tol * tol;
@@ -2604,7 +2608,7 @@ int batched_coarse_solve(mg_ctx* ctx, int nrhs, double tol, int maxit, std::vect
     CK(coarse_apply_tc_prepare(ctx->full.nc, b.npad));
     BatchCg c = batch_cg(ctx, tol, maxit, nrhs);
     {   // tile width from the autotuner (timed on the panel buffers once per shape)
-        TcApplyArgs t{c.Aemb, c.p, c.q, c.nc, c.npad, 0, 0, c.g, nullptr, c.err};
+        TcApplyArgs t{c.Aemb, c.p, c.q, c.nc, c.npad, 0, 0, c.g, nullptr, c.err, nullptr, c.bt};
         c.nw = coarse_apply_tc_tune(t, ctx->st);
         CKL();
     }
@@ -2886,6 +2890,59 @@ int mg_solve_batched(mg_ctx* ctx, const double* b, double* x, int nrhs, mg_solve
     return st;
 }
 
+int mg_time_coarse_batched(mg_ctx* ctx, int nrhs, int reps, double* ms_per_launch, double* bytes_per_launch,
+                           double* flops_per_launch) {
+    TRY(need_level(ctx));
+    if (nrhs <= 0 || nrhs > 256 || reps <= 0 || !ms_per_launch) return MG_ERR_INVALID_ARG;
+    CoarseLevel& L = ctx->full;
+    const int npad = round16(nrhs);
+    if (!coarse_apply_tc_supported(L.nc, npad)) return fail(ctx, MG_ERR_INVALID_ARG, "unsupported shape");
+    const size_t npanel = (size_t)ctx->g.Vc * L.nc * npad;
+    float2 *pa = nullptr, *pb = nullptr;
+    int* err = nullptr;
+    __half* bt = nullptr;
+    TRY(dalloc(ctx, &pa, sizeof(float2) * npanel));
+    TRY(dalloc(ctx, &pb, sizeof(float2) * npanel));
+    TRY(dalloc(ctx, &err, sizeof(int) * 4));
+    TRY(dalloc(ctx, &bt, tc_split_bytes(L.nc, npad, ctx->g.Vc)));
+    auto release = [&]() {
+        for (void* q : {(void*)pa, (void*)pb, (void*)err, (void*)bt}) {
+            for (size_t i = 0; i < ctx->allocs.size(); ++i)
+                if (ctx->allocs[i] == q) { ctx->allocs.erase(ctx->allocs.begin() + i); break; }
+            cudaFree(q);
+        }
+    };
+    int st = MG_OK;
+    do {
+        if ((st = ensure_embedding(ctx, L)) != MG_OK) break;
+        if (cudaMemsetAsync(err, 0, sizeof(int) * 4, ctx->st) != cudaSuccess ||
+            cudaMemsetAsync(pb, 0, sizeof(float2) * npanel, ctx->st) != cudaSuccess ||
+            coarse_apply_tc_prepare(L.nc, npad) != cudaSuccess) { st = fail(ctx, MG_ERR_CUDA, "probe setup"); break; }
+        // a zero panel (the values do not change the work or its timing)
+        panel_pack(pa, nullptr, (long long)ctx->g.Vc * L.nc, 0, npad, ctx->st);
+        TcApplyArgs a{L.Aemb, pa, pb, L.nc, npad, 0, 0, ctx->g, nullptr, err, nullptr, bt};
+        a.nw = coarse_apply_tc_tune(a, ctx->st);
+        for (int i = 0; i < 2; ++i) coarse_apply_tc(a, ctx->st);
+        cudaEventRecord(ctx->ev0, ctx->st);
+        for (int i = 0; i < reps; ++i) coarse_apply_tc(a, ctx->st);
+        cudaEventRecord(ctx->ev1, ctx->st);
+        if (cudaEventSynchronize(ctx->ev1) != cudaSuccess) { st = fail(ctx, MG_ERR_CUDA, "probe launch"); break; }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+        int h_err = 0;
+        cudaMemcpy(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost);
+        if (h_err) { st = fail(ctx, MG_ERR_TIMEOUT, "batched coarse stencil: a bounded wait gave up"); break; }
+        *ms_per_launch = (double)ms / reps;
+        const double K = 2.0 * L.nc;
+        // algorithmic: the FP16 embedded operator once, the FP32 panel read once and written once
+        if (bytes_per_launch) *bytes_per_launch = (double)ctx->g.Vc * 9 * K * K * 2 + 2.0 * npanel * sizeof(float2);
+        // useful work: 9 complex nc x nc blocks times nrhs columns per aggregate (8 real flops per complex MAC)
+        if (flops_per_launch) *flops_per_launch = 8.0 * 9 * L.nc * (double)L.nc * ctx->g.Vc * nrhs;
+    } while (false);
+    release();
+    return st;
+}
+
 int mg_apply_coarse_batched(mg_ctx* ctx, const double* x, double* y, int nrhs, int dagger, int impl) {
     TRY(need_level(ctx));
     if (!x || !y || nrhs <= 0 || nrhs > 256) return fail(ctx, MG_ERR_INVALID_ARG, "bad buffers or nrhs");
@@ -2917,11 +2974,14 @@ int mg_apply_coarse_batched(mg_ctx* ctx, const double* x, double* y, int nrhs, i
         tmp.push_back(pb);
         TRY(dalloc(ctx, &p64a, sizeof(int) * 4));   // error flag
         tmp.push_back(p64a);
+        __half* bt = nullptr;
+        TRY(dalloc(ctx, &bt, tc_split_bytes(L.nc, npad, ctx->g.Vc)));
+        tmp.push_back(bt);
         CK(cudaMemsetAsync(p64a, 0, sizeof(int) * 4, ctx->st));
         TRY(ensure_embedding(ctx, ctx->full));
         panel_pack(pa, hin, rows, nrhs, npad, ctx->st);
         CK(coarse_apply_tc_prepare(L.nc, npad));
-        TcApplyArgs a{L.Aemb, pa, pb, L.nc, npad, 0, dagger ? 1 : 0, ctx->g, nullptr, (int*)p64a};
+        TcApplyArgs a{L.Aemb, pa, pb, L.nc, npad, 0, dagger ? 1 : 0, ctx->g, nullptr, (int*)p64a, nullptr, bt};
         a.nw = coarse_apply_tc_tune(a, ctx->st);
         CK(coarse_apply_tc(a, ctx->st));
         panel_unpack(hout, pb, rows, nrhs, npad, ctx->st);

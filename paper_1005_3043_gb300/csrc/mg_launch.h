@@ -329,7 +329,10 @@ struct TcApplyArgs {
     int* err;       // set to 1 if a bounded wait gave up
     const double* colscale;   // optional per-column power-of-two factor applied to x before the
                               // FP16 hi/lo split (y is scaled back exactly); nullptr: 1
+    __half* bt;     // scratch for the split operand panel: tc_split_bytes(nc, npad) bytes
 };
+// bytes of the FP16 hi/lo operand tiles of one panel (any chunk width)
+inline size_t tc_split_bytes(int nc, int npad, long long Vc) { return (size_t)Vc * npad * (2 * nc) * 2 * sizeof(__half); }
 // y = D_c x (dag: sigma3 D_c sigma3 x) for the whole panel on tcgen05 tensor cores;
 // coarse_apply_tc_prepare(nc, npad) once per shape before launching (and before any capture)
 bool coarse_apply_tc_supported(int nc, int npad);
@@ -338,7 +341,7 @@ cudaError_t coarse_apply_tc(const TcApplyArgs& args, cudaStream_t st);
 // autotuner: fastest chunk width for args' (nc, npad), timed once and cached
 int coarse_apply_tc_tune(const TcApplyArgs& args, cudaStream_t st);
 // kernels launched by one bcg_iteration
-constexpr int kBcgKernelsPerIteration = 8;
+constexpr int kBcgKernelsPerIteration = 10;   // two stencils of two launches each + six
 // SIMT reference of the same contraction with the FP64 operator
 template <typename T>
 void coarse_apply_batched_simt(v2<T>* y, const double2* A, const v2<T>* x, int nc, int npad, bool dag, const Geom& g,
@@ -357,6 +360,7 @@ struct BatchScal {   // per-RHS CG scalars, npad doubles each
 };
 struct BatchCg {
     const __half* Aemb;
+    __half* bt;      // split operand tiles of the stencil (scratch)
     float2* y;
     float2* r;
     float2* s;
