@@ -78,4 +78,17 @@ WILSON_24x24x24x64 = Workload(
     extra={"mass": -0.79, "smoother": 1, "smoother_steps": 12, "gcr_restart": 8, "point_sources": 12,
            "gaussian_sources": 64})
 
-WORKLOADS = {w.name: w for w in (WILSON_8x8x8x8, WILSON_16x16x16x32, WILSON_24x24x24x64)}
+# 32^3 x 96, three levels (4^4 then 2^4 aggregates, Nv = 24 then 32): the
+# largest configuration, run as a parity case (a point source solved to 1e-10,
+# its residual recomputed with the oracle's operator).  Same field recipe and
+# uncalibrated bare mass as 24^3 x 64 (computing Re lambda_min(D(0)) at this
+# volume is beyond the host's eigensolver budget).
+WILSON_32x32x32x96 = Workload(
+    name="wilson_32x32x32x96_nv24_nv32_3level",
+    dims=(32, 32, 32, 96), block=(4, 4, 4, 4), nvec=24, seed=4001, sweeps=40,
+    re_lambda_min_m0=float("nan"), plaquette=0.593614315773,
+    targets=(), setup_target=float("nan"),
+    extra={"mass": -0.79, "smoother": 1, "smoother_steps": 12, "gcr_restart": 8, "levels": 3,
+           "block2": (2, 2, 2, 2), "nvec2": 32, "point_sources": 12})
+
+WORKLOADS = {w.name: w for w in (WILSON_8x8x8x8, WILSON_16x16x16x32, WILSON_24x24x24x64, WILSON_32x32x32x96)}
