@@ -18,11 +18,14 @@ static inline int reduce_grid(size_t n) {
 
 // ================================================================ block orthonormalisation
 // One CTA per (aggregate X, chirality s).  Column i of the panel is prototype i
-// restricted to X and to the spins of s (6*Vb complex).  Modified Gram-Schmidt
-// applied twice in index order, then normalisation: the Q factor with a
-// positive real R-diagonal.  Each thread keeps its elements of the current
-// column in registers; earlier columns are re-read from the output.
-constexpr int kOrthoMaxPerThread = 8;
+// restricted to X and to the spins of s (6*Vb complex).  Gram-Schmidt applied
+// twice in index order with all projections of a pass at once (classical form:
+// c = Q_<i^dag w, w -= Q_<i c), then normalisation: the unique Q factor with a
+// positive real R-diagonal, the same as modified Gram-Schmidt twice up to
+// rounding.  The column being orthogonalised sits in shared memory; warp w
+// forms the projections on columns w, w + 8, ... with warp shuffles, so a
+// pass costs three CTA barriers instead of one block reduction per column.
+constexpr int kOrthoMaxNv = 64;   // nvec <= 25 (parameter check)
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
     double a[1] = {v};
@@ -34,73 +37,62 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     __syncthreads();
     return r;
 }
-__device__ __forceinline__ cx<double> block_sum2(cx<double> v, double* sh) {
-    double a[2] = {v.r, v.i};
-    block_reduce<2>(a, (double (*)[32])sh);
-    __syncthreads();
-    if (threadIdx.x == 0) { sh[64] = a[0]; sh[65] = a[1]; }
-    __syncthreads();
-    cx<double> r(sh[64], sh[65]);
-    __syncthreads();
-    return r;
-}
 
 __global__ void __launch_bounds__(256) k_block_ortho(double2* __restrict__ P, const double2* __restrict__ Vin, int nv,
                                                      Geom g, int* status) {
+    extern __shared__ double2 wsh[];            // the column being orthogonalised, 6 * Vb entries
     __shared__ double sh[2 * 32 + 2];
-    int X = blockIdx.x >> 1, s = blockIdx.x & 1;
-    int len = 6 * g.Vb;
-    size_t vstride = (size_t)g.Vc * 12 * g.Vb;       // one prototype
+    __shared__ double2 cj[kOrthoMaxNv];        // projections of the current pass
+    const int X = blockIdx.x >> 1, s = blockIdx.x & 1;
+    const int len = 6 * g.Vb, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const size_t vstride = (size_t)g.Vc * 12 * g.Vb;       // one prototype
     double2* panel = P + ((size_t)X * 2 + s) * nv * len;
-    cx<double> w[kOrthoMaxPerThread];
     for (int i = 0; i < nv; ++i) {
         const double2* vi = Vin + (size_t)i * vstride + ((size_t)X * 12 + 6 * s) * g.Vb;   // k = 6s..6s+5 contiguous
         double n0 = 0;
-#pragma unroll
-        for (int q = 0; q < kOrthoMaxPerThread; ++q) {
-            int e = threadIdx.x + q * blockDim.x;
-            w[q] = e < len ? ld<double>(vi + e) : cx<double>(0, 0);
-            n0 += norm2(w[q]);
+        for (int e = threadIdx.x; e < len; e += blockDim.x) {
+            const double2 v = vi[e];
+            wsh[e] = v;
+            n0 += v.x * v.x + v.y * v.y;
         }
-        n0 = block_sum(n0, sh);
-        for (int pass = 0; pass < 2; ++pass)
-            for (int j = 0; j < i; ++j) {
+        n0 = block_sum(n0, sh);   // its barriers also publish wsh
+        for (int pass = 0; pass < 2 && i > 0; ++pass) {
+            // c_j = <q_j, w>, j < i: one warp per column, lanes over the entries
+            for (int j = warp; j < i; j += nw) {
                 const double2* qj = panel + (size_t)j * len;
                 cx<double> c(0, 0);
-#pragma unroll
-                for (int q = 0; q < kOrthoMaxPerThread; ++q) {
-                    int e = threadIdx.x + q * blockDim.x;
-                    if (e < len) cmadc(c, ld<double>(qj + e), w[q]);
-                }
-                c = block_sum2(c, sh);
-#pragma unroll
-                for (int q = 0; q < kOrthoMaxPerThread; ++q) {
-                    int e = threadIdx.x + q * blockDim.x;
-                    if (e < len) w[q] = w[q] - c * ld<double>(qj + e);
-                }
+                for (int e = lane; e < len; e += 32) cmadc(c, ld<double>(qj + e), ld<double>(wsh + e));
+                c.r = warp_sum(c.r);
+                c.i = warp_sum(c.i);
+                if (lane == 0) cj[j] = make_double2(c.r, c.i);
             }
+            __syncthreads();
+            // w -= sum_j c_j q_j
+            for (int e = threadIdx.x; e < len; e += blockDim.x) {
+                cx<double> w = ld<double>(wsh + e);
+                for (int j = 0; j < i; ++j) w = w - cx<double>(cj[j].x, cj[j].y) * ld<double>(panel + (size_t)j * len + e);
+                st<double>(wsh + e, w);
+            }
+            __syncthreads();
+        }
         double n = 0;
-#pragma unroll
-        for (int q = 0; q < kOrthoMaxPerThread; ++q) n += norm2(w[q]);
+        for (int e = threadIdx.x; e < len; e += blockDim.x) n += norm2(ld<double>(wsh + e));
         n = sqrt(block_sum(n, sh));
         if (!(n > 1e-12 * sqrt(n0))) {
             if (threadIdx.x == 0) atomicExch(status, 1);
             n = 1.0;
         }
-        double f = 1.0 / n;
+        const double f = 1.0 / n;
         double2* qi = panel + (size_t)i * len;
-#pragma unroll
-        for (int q = 0; q < kOrthoMaxPerThread; ++q) {
-            int e = threadIdx.x + q * blockDim.x;
-            if (e < len) st<double>(qi + e, f * w[q]);
-        }
+        for (int e = threadIdx.x; e < len; e += blockDim.x) st<double>(qi + e, f * ld<double>(wsh + e));
         __syncthreads();   // column i visible to the block before it is re-read
     }
 }
 
 void block_orthonormalize(double2* P, const double2* V, int nv, const Geom& g, int* d_status, cudaStream_t st) {
+    const size_t sm = sizeof(double2) * 6 * g.Vb;   // <= 32.7 KB: blocks hold at most 341 sites (parameter check)
     note_launch();
-    k_block_ortho<<<2 * g.Vc, kThreads, 0, st>>>(P, V, nv, g, d_status);
+    k_block_ortho<<<2 * g.Vc, kThreads, sm, st>>>(P, V, nv, g, d_status);
 }
 
 // ================================================================ restriction / prolongation

@@ -60,24 +60,33 @@ __global__ void __launch_bounds__(kL2Threads) k_block_ortho_l2(double2* __restri
             panel[(size_t)i * len + k] = V2[((size_t)i * g2.V + X1) * nc1 + s * nv1 + j];
         }
     __syncthreads();
+    // Gram-Schmidt twice in index order, all projections of a pass at once
+    // (classical form; the unique Q with positive real R-diagonal, as modified
+    // Gram-Schmidt twice up to rounding): warp w forms c_j for j = w, w + nw, ...
+    __shared__ double2 cj[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int i = 0; i < nv2; ++i) {
         double2* wi = panel + (size_t)i * len;
         double n0 = 0;
         for (int k = threadIdx.x; k < len; k += blockDim.x) n0 += wi[k].x * wi[k].x + wi[k].y * wi[k].y;
         const double orig = sqrt(cta_sum2(cx<double>(n0, 0), sh).r);
-        for (int pass = 0; pass < 2; ++pass)
-            for (int j = 0; j < i; ++j) {
+        for (int pass = 0; pass < 2 && i > 0; ++pass) {
+            for (int j = warp; j < i; j += nw) {
                 const double2* qj = panel + (size_t)j * len;
                 cx<double> c(0, 0);
-                for (int k = threadIdx.x; k < len; k += blockDim.x) cmadc(c, ld<double>(qj + k), ld<double>(wi + k));
-                c = cta_sum2(c, sh);
-                for (int k = threadIdx.x; k < len; k += blockDim.x) {
-                    cx<double> w = ld<double>(wi + k);
-                    cx<double> q = ld<double>(qj + k);
-                    st<double>(wi + k, w - c * q);
-                }
-                __syncthreads();
+                for (int k = lane; k < len; k += 32) cmadc(c, ld<double>(qj + k), ld<double>(wi + k));
+                c.r = warp_sum(c.r);
+                c.i = warp_sum(c.i);
+                if (lane == 0) cj[j] = make_double2(c.r, c.i);
             }
+            __syncthreads();
+            for (int k = threadIdx.x; k < len; k += blockDim.x) {
+                cx<double> w = ld<double>(wi + k);
+                for (int j = 0; j < i; ++j) w = w - cx<double>(cj[j].x, cj[j].y) * ld<double>(panel + (size_t)j * len + k);
+                st<double>(wi + k, w);
+            }
+            __syncthreads();
+        }
         double n1 = 0;
         for (int k = threadIdx.x; k < len; k += blockDim.x) n1 += wi[k].x * wi[k].x + wi[k].y * wi[k].y;
         double nrm = sqrt(cta_sum2(cx<double>(n1, 0), sh).r);
