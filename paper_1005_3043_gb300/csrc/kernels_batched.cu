@@ -102,7 +102,7 @@ constexpr size_t kTcStaticSmem = 256;   // barriers, TMEM address, flag
 __host__ __device__ inline int tc_stages(int nc, int nw) {
     return kTcMaxStages * tc_stage_bytes(nc, nw) + kTcStaticSmem <= 227 * 1024 ? kTcMaxStages : 2;
 }
-__host__ __device__ inline size_t tc_smem_bytes(int nc, int nw) { return tc_stages(nc, nw) * tc_stage_bytes(nc, nw); }
+__host__ __device__ inline int tc_stages_of(const TcApplyArgs& a) { return a.stages > 0 ? a.stages : tc_stages(a.nc, a.nw); }
 
 // The operand panel as FP16 hi + lo tiles in the tensor-core shared-memory
 // layout, one tile pair per (aggregate Y, column chunk c):
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_coarse_apply_tc(TcApplyArgs a
     // grid (column chunks, aggregates): the chunks of one aggregate run side by
     // side and share its operator tiles through L2
     const int nc = a.nc, npad = a.npad, nw = a.nw, chunk = blockIdx.x, n0 = chunk * nw, K = 2 * nc, nvh = nc / 2;
-    const int nch = npad / nw, S = tc_stages(nc, nw);
+    const int nch = npad / nw, S = tc_stages_of(a);
     const size_t SA = (size_t)128 * K * 2, SB = (size_t)nw * K * 2, SS = SA + 2 * SB;
     __shared__ __align__(8) uint64_t bar[2 * kTcMaxStages];   // [0, S): stage full, [S, 2S): stage empty
     __shared__ uint32_t s_taddr;
@@ -267,24 +267,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_coarse_apply_tc(TcApplyArgs a
     if (warp == 0) tmem_dealloc(tmem, ncols);
 }
 
-// Dynamic shared memory of one CTA: the two pipeline stages, padded so that at
+// Dynamic shared memory of one CTA: its pipeline stages, padded so that at
 // most 512 / ncols CTAs fit on an SM (their TMEM allocations never exceed the
 // 512 columns of an SM, so no allocation waits).
-static size_t tc_launch_smem(int nc, int nw) {
-    size_t sm = tc_smem_bytes(nc, nw);
+static size_t tc_launch_smem(int nc, int nw, int stages) {
+    size_t sm = (size_t)stages * tc_stage_bytes(nc, nw);
     size_t per_sm = 228 * 1024, cap = 512 / tc_tmem_cols(nw);
     size_t min_sm = per_sm / (cap + 1) + 1024;
     return sm > min_sm ? sm : min_sm;
 }
 bool coarse_apply_tc_supported(int nc, int npad) {
     return npad % 16 == 0 && npad >= 16 && npad <= 256 && (2 * nc) % 16 == 0 && 2 * nc <= 128 &&
-           tc_launch_smem(nc, npad) + kTcStaticSmem <= 227 * 1024;
+           tc_launch_smem(nc, npad, 2) + kTcStaticSmem <= 227 * 1024;
 }
 // attribute for the largest chunk width used with this nc (every nw <= npad fits)
 cudaError_t coarse_apply_tc_prepare(int nc, int npad) {
     if (!coarse_apply_tc_supported(nc, npad)) return cudaErrorInvalidValue;
     size_t mx = 0;
-    for (int nw = 16; nw <= npad; nw += 16) mx = std::max(mx, tc_launch_smem(nc, nw));
+    for (int nw = 16; nw <= npad; nw += 16) mx = std::max(mx, tc_launch_smem(nc, nw, tc_stages(nc, nw)));
     return cudaFuncSetAttribute(k_coarse_apply_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
 }
 // launch only (coarse_apply_tc_prepare must have been called for this shape);
@@ -300,17 +300,20 @@ cudaError_t coarse_apply_tc(const TcApplyArgs& args, cudaStream_t st) {
     TmemOrder order(st);
     if (order.error() != cudaSuccess) return order.error();
     note_launch();
-    k_coarse_apply_tc<<<dim3(a.npad / a.nw, a.g.Vc), kTcThreads, tc_launch_smem(a.nc, a.nw), st>>>(a);
+    if (a.stages != 0 && (a.stages < 2 || a.stages > tc_stages(a.nc, a.nw))) return cudaErrorInvalidValue;
+    k_coarse_apply_tc<<<dim3(a.npad / a.nw, a.g.Vc), kTcThreads, tc_launch_smem(a.nc, a.nw, tc_stages_of(a)), st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return order.launched();
 }
 
-// Chunk width for (nc, npad): every candidate (multiples of 16 dividing npad)
-// is timed with CUDA events on the given stream and the fastest is kept.
-// The cache is keyed by device as well and guarded for concurrent host threads.
-int coarse_apply_tc_tune(const TcApplyArgs& args, cudaStream_t st) {
-    struct Entry { int dev, nc, npad, nw; };
+// Chunk width and pipeline depth for (nc, npad): every candidate (multiples of
+// 16 dividing npad; 2 or 3 stages where 3 fit -- 2 can leave room for a second
+// CTA on the SM) is timed with CUDA events on the given stream and the fastest
+// is kept.  The cache is keyed by device as well and guarded for concurrent
+// host threads.
+int coarse_apply_tc_tune(const TcApplyArgs& args, cudaStream_t st, int* stages) {
+    struct Entry { int dev, nc, npad, nw, stages; };
     static std::vector<Entry> cache;
     static std::mutex mu;
     int dev = 0;
@@ -318,17 +321,22 @@ int coarse_apply_tc_tune(const TcApplyArgs& args, cudaStream_t st) {
     {
         std::lock_guard<std::mutex> lock(mu);
         for (const Entry& e : cache)
-            if (e.dev == dev && e.nc == args.nc && e.npad == args.npad) return e.nw;
+            if (e.dev == dev && e.nc == args.nc && e.npad == args.npad) {
+                if (stages) *stages = e.stages;
+                return e.nw;
+            }
     }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    int best = args.npad;
+    int best = args.npad, best_s = tc_stages(args.nc, args.npad);
     float best_ms = 1e30f;
-    for (int nw = 16; nw <= args.npad; nw += 16) {
-        if (args.npad % nw) continue;
+    for (int cand = 0; cand < 2 * 16; ++cand) {
+        const int nw = 16 * (cand / 2 + 1), S = 2 + cand % 2;
+        if (nw > args.npad || args.npad % nw || S > tc_stages(args.nc, nw)) continue;
         TcApplyArgs a = args;
         a.nw = nw;
+        a.stages = S;
         coarse_apply_tc(a, st);   // warm-up
         cudaEventRecord(e0, st);
         for (int r = 0; r < 5; ++r) coarse_apply_tc(a, st);
@@ -336,12 +344,13 @@ int coarse_apply_tc_tune(const TcApplyArgs& args, cudaStream_t st) {
         cudaEventSynchronize(e1);
         float ms = 0;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best_ms) { best_ms = ms; best = nw; }
+        if (ms < best_ms) { best_ms = ms; best = nw; best_s = S; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     std::lock_guard<std::mutex> lock(mu);
-    cache.push_back({dev, args.nc, args.npad, best});
+    cache.push_back({dev, args.nc, args.npad, best, best_s});
+    if (stages) *stages = best_s;
     return best;
 }
 
@@ -563,7 +572,7 @@ void bcg_iteration(const BatchCg& c, cudaStream_t st) {
     const long long rows = (long long)c.g.Vc * c.nc, total = rows * c.npad;
     const int ct = col_threads(c.npad);
     const size_t cs = col_smem(c.npad);
-    TcApplyArgs ap{c.Aemb, c.p, c.q, c.nc, c.npad, c.nw, 0, c.g, c.xpart, c.err, c.S.csp, c.bt};
+    TcApplyArgs ap{c.Aemb, c.p, c.q, c.nc, c.npad, c.nw, 0, c.g, c.xpart, c.err, c.S.csp, c.bt, c.stages};
     coarse_apply_tc(ap, st);                                                               // q = D_c p
     note_launch();
     k_bcg_alpha<<<c.npad, 256, 0, st>>>(c.S, c.xpart, c.g.Vc, c.npad);
@@ -571,7 +580,7 @@ void bcg_iteration(const BatchCg& c, cudaStream_t st) {
     k_bcg_update1<<<kRowChunks, ct, cs, st>>>(c.y, c.r, c.p, c.q, rows, c.npad, c.S, c.rpart, c.active);
     note_launch();
     k_bcg_check<<<c.npad, 256, 0, st>>>(c.S, c.rpart, kRowChunks, c.npad, c.tol2, c.maxit, c.active, rows);
-    TcApplyArgs as{c.Aemb, c.r, c.s, c.nc, c.npad, c.nw, 1, c.g, c.xpart, c.err, c.S.csr, c.bt};
+    TcApplyArgs as{c.Aemb, c.r, c.s, c.nc, c.npad, c.nw, 1, c.g, c.xpart, c.err, c.S.csr, c.bt, c.stages};
     coarse_apply_tc(as, st);                                                               // s = D_c^dag r
     note_launch();
     k_bcg_beta<<<c.npad, 256, 0, st>>>(c.S, c.xpart, c.g.Vc, c.npad, rows);
@@ -588,7 +597,7 @@ void bcg_start(const BatchCg& c, cudaStream_t st) {
     k_bcg_scale<<<c.npad, 256, 0, st>>>(c.S, c.rpart, kRowChunks, c.npad, c.nrhs, c.maxit, rows);
     note_launch();
     k_bcg_start<<<ew_grid(total), 256, 0, st>>>(c.y, c.r, c.rc, total, c.npad, c.S);
-    TcApplyArgs as{c.Aemb, c.r, c.s, c.nc, c.npad, c.nw, 1, c.g, c.xpart, c.err, c.S.csr, c.bt};
+    TcApplyArgs as{c.Aemb, c.r, c.s, c.nc, c.npad, c.nw, 1, c.g, c.xpart, c.err, c.S.csr, c.bt, c.stages};
     coarse_apply_tc(as, st);
     note_launch();
     k_bcg_gamma0<<<c.npad, 256, 0, st>>>(c.S, c.xpart, c.g.Vc, c.npad, rows);

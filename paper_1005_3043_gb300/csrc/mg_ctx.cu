@@ -2589,6 +2589,7 @@ BatchCg batch_cg(mg_ctx* ctx, double tol, int maxit, int nrhs) {
     BatchCg c;
     c.Aemb = ctx->full.Aemb;
     c.bt = b.bt;
+    c.stages = 0;
     c.y = b.yB; c.r = b.rB; c.s = b.sB; c.p = b.pB; c.q = b.qB; c.rc = b.rcB;
     c.nc = ctx->full.nc; c.npad = b.npad; c.nw = b.npad; c.nrhs = nrhs; c.maxit = maxit;
     c.tol2 = tol * tol;
@@ -2608,13 +2609,14 @@ int batched_coarse_solve(mg_ctx* ctx, int nrhs, double tol, int maxit, std::vect
     CK(coarse_apply_tc_prepare(ctx->full.nc, b.npad));
     BatchCg c = batch_cg(ctx, tol, maxit, nrhs);
     {   // tile width from the autotuner (timed on the panel buffers once per shape)
-        TcApplyArgs t{c.Aemb, c.p, c.q, c.nc, c.npad, 0, 0, c.g, nullptr, c.err, nullptr, c.bt};
-        c.nw = coarse_apply_tc_tune(t, ctx->st);
+        TcApplyArgs t{c.Aemb, c.p, c.q, c.nc, c.npad, 0, 0, c.g, nullptr, c.err, nullptr, c.bt, 0};
+        c.nw = coarse_apply_tc_tune(t, ctx->st, &c.stages);
         CKL();
     }
     long long tolbits = 0;
     std::memcpy(&tolbits, &c.tol2, sizeof(tolbits));
-    long long key[6] = {(long long)(size_t)c.Aemb, b.npad, nrhs, maxit, tolbits, ctx->full.nc * 1024 + c.nw};
+    long long key[6] = {(long long)(size_t)c.Aemb, b.npad, nrhs, maxit, tolbits,
+                        (ctx->full.nc * 1024 + c.nw) * 4 + c.stages};
     if (!b.graph || std::memcmp(key, b.graph_key, sizeof(key)) != 0) {
         if (b.graph) { cudaGraphExecDestroy(b.graph); b.graph = nullptr; }
         cudaGraph_t gr;
@@ -2920,8 +2922,8 @@ int mg_time_coarse_batched(mg_ctx* ctx, int nrhs, int reps, double* ms_per_launc
             coarse_apply_tc_prepare(L.nc, npad) != cudaSuccess) { st = fail(ctx, MG_ERR_CUDA, "probe setup"); break; }
         // a zero panel (the values do not change the work or its timing)
         panel_pack(pa, nullptr, (long long)ctx->g.Vc * L.nc, 0, npad, ctx->st);
-        TcApplyArgs a{L.Aemb, pa, pb, L.nc, npad, 0, 0, ctx->g, nullptr, err, nullptr, bt};
-        a.nw = coarse_apply_tc_tune(a, ctx->st);
+        TcApplyArgs a{L.Aemb, pa, pb, L.nc, npad, 0, 0, ctx->g, nullptr, err, nullptr, bt, 0};
+        a.nw = coarse_apply_tc_tune(a, ctx->st, &a.stages);
         for (int i = 0; i < 2; ++i) coarse_apply_tc(a, ctx->st);
         cudaEventRecord(ctx->ev0, ctx->st);
         for (int i = 0; i < reps; ++i) coarse_apply_tc(a, ctx->st);
@@ -2981,8 +2983,8 @@ int mg_apply_coarse_batched(mg_ctx* ctx, const double* x, double* y, int nrhs, i
         TRY(ensure_embedding(ctx, ctx->full));
         panel_pack(pa, hin, rows, nrhs, npad, ctx->st);
         CK(coarse_apply_tc_prepare(L.nc, npad));
-        TcApplyArgs a{L.Aemb, pa, pb, L.nc, npad, 0, dagger ? 1 : 0, ctx->g, nullptr, (int*)p64a, nullptr, bt};
-        a.nw = coarse_apply_tc_tune(a, ctx->st);
+        TcApplyArgs a{L.Aemb, pa, pb, L.nc, npad, 0, dagger ? 1 : 0, ctx->g, nullptr, (int*)p64a, nullptr, bt, 0};
+        a.nw = coarse_apply_tc_tune(a, ctx->st, &a.stages);
         CK(coarse_apply_tc(a, ctx->st));
         panel_unpack(hout, pb, rows, nrhs, npad, ctx->st);
         int err = 0;

@@ -330,6 +330,7 @@ struct TcApplyArgs {
     const double* colscale;   // optional per-column power-of-two factor applied to x before the
                               // FP16 hi/lo split (y is scaled back exactly); nullptr: 1
     __half* bt;     // scratch for the split operand panel: tc_split_bytes(nc, npad) bytes
+    int stages;     // pipeline stages per CTA (2 or 3; 0: as many as fit, up to 3)
 };
 // bytes of the FP16 hi/lo operand tiles of one panel (any chunk width)
 inline size_t tc_split_bytes(int nc, int npad, long long Vc) { return (size_t)Vc * npad * (2 * nc) * 2 * sizeof(__half); }
@@ -338,8 +339,9 @@ inline size_t tc_split_bytes(int nc, int npad, long long Vc) { return (size_t)Vc
 bool coarse_apply_tc_supported(int nc, int npad);
 cudaError_t coarse_apply_tc_prepare(int nc, int npad);
 cudaError_t coarse_apply_tc(const TcApplyArgs& args, cudaStream_t st);
-// autotuner: fastest chunk width for args' (nc, npad), timed once and cached
-int coarse_apply_tc_tune(const TcApplyArgs& args, cudaStream_t st);
+// autotuner: fastest chunk width (returned) and pipeline depth (*stages) for
+// args' (nc, npad), timed once and cached
+int coarse_apply_tc_tune(const TcApplyArgs& args, cudaStream_t st, int* stages);
 // kernels launched by one bcg_iteration
 constexpr int kBcgKernelsPerIteration = 10;   // two stencils of two launches each + six
 // SIMT reference of the same contraction with the FP64 operator
@@ -361,6 +363,7 @@ struct BatchScal {   // per-RHS CG scalars, npad doubles each
 struct BatchCg {
     const __half* Aemb;
     __half* bt;      // split operand tiles of the stencil (scratch)
+    int stages;      // pipeline depth of the stencil (from the autotuner)
     float2* y;
     float2* r;
     float2* s;
