@@ -62,64 +62,100 @@ __device__ __forceinline__ void nn_transport(cx<float> (&t)[4][3], const float2*
         }
 }
 
-// acc[s][c] += sum_t w[s][t] t[t][c]
-__device__ __forceinline__ void nn_spin(cx<float> (&acc)[4][3], const float2* w, const cx<float> (&t)[4][3]) {
-#pragma unroll
-    for (int s = 0; s < 4; ++s)
-#pragma unroll
-        for (int tt = 0; tt < 4; ++tt) {
-            const float2 ww = w[4 * s + tt];
-            const cx<float> wv(ww.x, ww.y);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) cmad(acc[s][c], wv, t[tt][c]);
-        }
-}
-
-template <int D>
-__device__ __forceinline__ void nn_direction(cx<float> (&acc)[4][3], const float2* __restrict__ in, const float2* sW,
-                                             const float2* __restrict__ U, const Geom& g, int X, int l,
-                                             const int (&lc)[4], const int (&xc)[4], int cin, size_t chan) {
-    for (int b = 0; b < cin; ++b) {
-        cx<float> t[4][3];
-        nn_transport<D>(t, in + (size_t)b * chan, U, g, X, l, lc, xc);
-        nn_spin(acc, sW + ((size_t)b * 9 + D) * 16, t);
-    }
-}
-
-// out[a] for a = blockIdx.y, one thread per site; the CTA's weights in shared memory
+// Four threads per site, one per spin s (lanes 4i .. 4i+3 of a warp share a
+// site).  For every input channel b and direction d, thread s transports its
+// own spin row of in[b] (3 colours: 3 loads, one link, 9 complex multiply-adds),
+// the four rows are exchanged by warp shuffles, and the thread adds
+// W[a][b][d][s][t] (T_d in[b])[t] for every output channel a into its
+// registers: each transport is formed once instead of once per output channel.
+// The layer's weights sit in shared memory (W[a][b][d][s][t], cout * cin * 144
+// complex).
+constexpr int kNnMaxCout = 8;
 __global__ void __launch_bounds__(kNnThreads) k_nn_layer(float2* __restrict__ out, const float2* __restrict__ in,
                                                          const float2* __restrict__ W, const float2* __restrict__ U,
-                                                         Geom g, int cin) {
-    extern __shared__ float2 sW[];   // W[a][b][d][16] for this a: cin * 9 * 16
-    const int a = blockIdx.y;
-    for (int i = threadIdx.x; i < cin * 144; i += blockDim.x) sW[i] = W[(size_t)a * cin * 144 + i];
+                                                         Geom g, int cin, int cout) {
+    extern __shared__ float2 sW[];
+    for (int i = threadIdx.x; i < cout * cin * 144; i += blockDim.x) sW[i] = W[i];
     __syncthreads();
-    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (s >= g.V) return;
+    const int lane = threadIdx.x & 31, sp = lane & 3, gbase = lane & ~3;
+    const long long site = blockIdx.x * (long long)(blockDim.x >> 2) + (threadIdx.x >> 2);
+    const bool live = site < g.V;
+    const long long s = live ? site : g.V - 1;   // idle lanes shadow the last site (for the shuffles)
     const int X = (int)(s / g.Vb), l = (int)(s - (long long)X * g.Vb);
     int lc[4], xc[4];
     local_coords(g, l, lc);
     coarse_coords(g, X, xc);
     const size_t chan = (size_t)g.V * 12;
-    cx<float> acc[4][3];
+    cx<float> acc[kNnMaxCout][3];
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+    for (int a = 0; a < kNnMaxCout; ++a)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) acc[q][c] = cx<float>(0, 0);
-    nn_direction<0>(acc, in, sW, U, g, X, l, lc, xc, cin, chan);
-    nn_direction<1>(acc, in, sW, U, g, X, l, lc, xc, cin, chan);
-    nn_direction<2>(acc, in, sW, U, g, X, l, lc, xc, cin, chan);
-    nn_direction<3>(acc, in, sW, U, g, X, l, lc, xc, cin, chan);
-    nn_direction<4>(acc, in, sW, U, g, X, l, lc, xc, cin, chan);
-    nn_direction<5>(acc, in, sW, U, g, X, l, lc, xc, cin, chan);
-    nn_direction<6>(acc, in, sW, U, g, X, l, lc, xc, cin, chan);
-    nn_direction<7>(acc, in, sW, U, g, X, l, lc, xc, cin, chan);
-    nn_direction<8>(acc, in, sW, U, g, X, l, lc, xc, cin, chan);
-    float2* o = out + (size_t)a * chan + (size_t)X * 12 * g.Vb + l;
+        for (int c = 0; c < 3; ++c) acc[a][c] = cx<float>(0, 0);
+    for (int b = 0; b < cin; ++b) {
+        const float2* inb = in + (size_t)b * chan;
+#pragma unroll 1
+        for (int d = 0; d < 9; ++d) {
+            int Xn = X, ln = l;
+            bool flip = false;
+            if (d > 0) neighbour(g, X, l, lc, xc, (d - 1) >> 1, (d & 1) ? 1 : -1, Xn, ln, flip);
+            cx<float> p[3];
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+            for (int c = 0; c < 3; ++c) p[c] = ldg<float>(inb + ((size_t)Xn * 12 + 3 * sp + c) * g.Vb + ln);
+            cx<float> t[3];
+            if (d == 0) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) st<float>(o + (3 * q + c) * g.Vb, acc[q][c]);
+                for (int c = 0; c < 3; ++c) t[c] = p[c];
+            } else {
+                const int mu = (d - 1) >> 1;
+                const bool fwd = (d & 1) != 0;
+                const size_t ls = fwd ? ((size_t)mu * g.Vc + X) : ((size_t)mu * g.Vc + Xn);
+                const float2* u = U + ls * 9 * g.Vb + (fwd ? l : ln);
+                cx<float> m[9];
+#pragma unroll
+                for (int e = 0; e < 9; ++e) m[e] = ldg<float>(u + (size_t)e * g.Vb);
+                const float sg = flip ? -1.f : 1.f;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    cx<float> q(0, 0);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        if (fwd) cmad(q, m[3 * a + c], p[c]);
+                        else cmadc(q, m[3 * c + a], p[c]);
+                    }
+                    t[a] = sg * q;
+                }
+            }
+            // the four spin rows of the transported vector, from the site's four lanes
+            cx<float> tt[4][3];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    tt[r][c].r = __shfl_sync(0xffffffffu, t[c].r, gbase + r);
+                    tt[r][c].i = __shfl_sync(0xffffffffu, t[c].i, gbase + r);
+                }
+            const float2* wb = sW + ((size_t)b * 9 + d) * 16 + 4 * sp;   // W[a][b][d][sp][.] at + a * cin * 144
+#pragma unroll
+            for (int a = 0; a < kNnMaxCout; ++a) {
+                if (a >= cout) break;
+                const float2* w = wb + (size_t)a * cin * 144;
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const cx<float> wv(w[r].x, w[r].y);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) cmad(acc[a][c], wv, tt[r][c]);
+                }
+            }
+        }
+    }
+    if (!live) return;
+#pragma unroll
+    for (int a = 0; a < kNnMaxCout; ++a) {
+        if (a >= cout) break;
+        float2* o = out + (size_t)a * chan + ((size_t)X * 12 + 3 * sp) * g.Vb + l;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) st<float>(o + (size_t)c * g.Vb, acc[a][c]);
+    }
 }
 
 // ---------------------------------------------------------------- weight gradient
@@ -239,13 +275,15 @@ __global__ void k_nn_adjoint_weights(float2* __restrict__ Wt, const float2* __re
 // ---------------------------------------------------------------- launchers
 cudaError_t nn_layer(float2* out, const float2* in, const float2* W, const float2* U, const Geom& g, int cin, int cout,
                      cudaStream_t st) {
-    const size_t sm = sizeof(float2) * (size_t)cin * 144;
+    if (cout > kNnMaxCout) return cudaErrorInvalidValue;
+    const size_t sm = sizeof(float2) * (size_t)cout * cin * 144;
     if (sm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_nn_layer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
+    const int sites_per_cta = kNnThreads / 4;
     note_launch();
-    k_nn_layer<<<dim3((unsigned)((g.V + kNnThreads - 1) / kNnThreads), cout), kNnThreads, sm, st>>>(out, in, W, U, g, cin);
+    k_nn_layer<<<(unsigned)((g.V + sites_per_cta - 1) / sites_per_cta), kNnThreads, sm, st>>>(out, in, W, U, g, cin, cout);
     return cudaGetLastError();
 }
 int nn_wgrad_blocks(const Geom& g) {

@@ -379,7 +379,7 @@ struct BatchCg {
     int* active;     // columns still iterating after the last check
     int* err;
 };
-constexpr int kBatchRowChunks = 152;   // row chunks of the batched CG's column sums (a buffer capacity)
+constexpr int kBatchRowChunks = 1216;   // row chunks of the batched CG's column sums (8 per SM: enough warps to stream the panel)
 void bcg_start(const BatchCg& c, cudaStream_t st);
 void bcg_iteration(const BatchCg& c, cudaStream_t st);
 void bcg_finish(const BatchCg& c, cudaStream_t st);
