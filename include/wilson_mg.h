@@ -81,10 +81,12 @@ typedef struct {
     int prec_inner;        /* MG_FP64, MG_FP32 or MG_FP16: smoother, dslash, transfers, coarse solve, Krylov basis */
     int coarse_check;      /* coarse iterations between convergence checks read by the host */
     int coarse_kernel;     /* FP32/FP16 coarse solve: 0 (default) operator held on chip for the
-                              whole solve, in tensor memory when each SM's share fits, else in
-                              shared memory, else as 1; 1 operator read from global memory into
-                              registers every iteration; 2 operator streamed through a
-                              shared-memory ring (tests); 3 shared memory only (tests) */
+                              whole solve, in tensor memory when each SM's share fits (FP16: its
+                              products on the tensor cores when each SM holds at most 140 rows),
+                              else in shared memory, else as 1; 1 operator read from global
+                              memory into registers every iteration; 2 operator streamed through
+                              a shared-memory ring (tests); 3 shared memory only (tests); 4 tensor
+                              memory with the products on the CUDA cores (tests) */
     int smoother;          /* post-smoother: 0 (default) smoother_steps MR steps, each scaled by omega;
                               1 one GMRES(smoother_steps) application scaled by omega (Sec. III-IV:
                               GMRES(4)), smoother_steps <= 16, FP32/FP64 storage */
@@ -92,7 +94,7 @@ typedef struct {
                               Arnoldi basis (GMRES): 0 (default) FP16 when the FP32 working set
                               (MR: links + 3 spinors, 576 B per site; GMRES: k + 1 spinors, 96 B
                               each) exceeds the device L2, else FP32; 1 always FP16; 2 never */
-    int coarse_form;       /* iteration form of the on-chip coarse solve (coarse_kernel 0, 2, 3):
+    int coarse_form;       /* iteration form of the on-chip coarse solve (coarse_kernel 0, 2, 3, 4):
                               0 (default) Chronopoulos-Gear form, one grid-wide exchange per
                               iteration, the vectors other SMs read carrying epoch tags instead
                               of barriers; 1 textbook CGLS, two grid-wide exchanges per
@@ -450,8 +452,12 @@ long long mg_kernel_launches(void);
  * diagnostic; no counterpart in the paper): MG_CK_REGISTER operator read from
  * global memory every iteration, MG_CK_SMEM operator resident in shared
  * memory, MG_CK_STREAM operator streamed through a shared-memory ring,
- * MG_CK_TMEM operator resident in tensor memory; MG_CK_NONE before any. */
-enum mg_coarse_kernel_id { MG_CK_NONE = -1, MG_CK_REGISTER = 0, MG_CK_SMEM = 1, MG_CK_STREAM = 2, MG_CK_TMEM = 3 };
+ * MG_CK_TMEM operator resident in tensor memory, products on the CUDA cores,
+ * MG_CK_TMEM_MMA operator resident in tensor memory, products on the tensor
+ * cores; MG_CK_NONE before any. */
+enum mg_coarse_kernel_id {
+    MG_CK_NONE = -1, MG_CK_REGISTER = 0, MG_CK_SMEM = 1, MG_CK_STREAM = 2, MG_CK_TMEM = 3, MG_CK_TMEM_MMA = 4
+};
 int mg_coarse_kernel(mg_ctx* ctx);
 
 /* Check of the library's bounded device waits (the paper has no counterpart;

@@ -491,7 +491,8 @@ def mg_kernel_launches() -> int:
 COARSE_KERNELS = {-1: "none", 0: "k_cgnr_persistent (operator from global memory)",
                   1: "k_cgls_onchip (operator resident in shared memory)",
                   2: "k_cgls_onchip (operator streamed through shared memory)",
-                  3: "k_cgls_onchip (operator resident in tensor memory)"}
+                  3: "k_cgls_onchip (operator resident in tensor memory, products on the CUDA cores)",
+                  4: "k_cgls_onchip (operator resident in tensor memory, products on the tensor cores)"}
 
 
 def mg_coarse_kernel(ctx) -> int:

@@ -22,37 +22,6 @@
 
 namespace wmg {
 
-// ---------------------------------------------------------------- tensor-memory and MMA helpers
-// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16, one CTA
-__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                        uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-// Shared-memory matrix descriptor, no swizzle, K-major "core matrix" layout:
-// 8 rows x 16 bytes per core matrix; lbo = byte distance between core
-// matrices adjacent in K, sbo = between core matrices adjacent in M/N.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr >> 4) & 0x3FFF);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-    d |= (uint64_t)1 << 46;   // descriptor version for this architecture
-    return d;                 // base offset 0, layout type 0 (no swizzle)
-}
-// instruction descriptor: D FP32, A/B FP16, both K-major, M x N
-__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
-    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
 // half offset of element (row r, k) in a K-major core-matrix tile with K columns
 __host__ __device__ __forceinline__ int core_off(int r, int k, int K) {
     return (((r >> 3) * (K >> 3) + (k >> 3)) << 6) + ((r & 7) << 3) + (k & 7);

@@ -117,7 +117,56 @@ enum { OV_P = 0, OV_Z = 1, OV_Q = 2, OV_Y = 3, OV_R = 4, OV_S = 5, OV_U = 6, OV_
 
 constexpr int kStageRegs = 4;   // staged operand entries per thread kept as precomputed offsets
 
-template <bool H16, bool TM> struct CglsCta {
+// Tensor-core products (TM == 2, FP16 operator): the first kMmaRows rows of a
+// CTA are one MMA tile, row r in TMEM lane r, column k holding the FP16 complex
+// entry k = d nc + b (low half Re, high half Im: the K-major A operand with
+// K = 2 * 9nc real elements).  B (kMmaN x 2K, K-major core matrices in shared
+// memory) holds per aggregate xl of the CTA four rows: the staged operand x as
+// FP16 hi + lo parts (x = hi + lo to ~22 bits, after a per-aggregate power-of-
+// two scale), laid out so that row 4xl (Re) pairs (Re a, Im a) with (Re x, -Im x)
+// and row 4xl+1 (Im) with (Im x, Re x); rows 4xl+2, 4xl+3 the same for lo.  So
+// D[r][4xl + {0,1,2,3}] summed in pairs is Re, Im of (D_c x)_r.  Rows beyond the
+// tile (at most kMmaRemWarps) are summed on the CUDA cores, one warp each.
+constexpr int kMmaRows = 128;
+constexpr int kMmaN = 32;
+constexpr int kMmaAgg = kMmaN / 4;
+constexpr int kMmaRemWarps = kCglsThreads / 32 - 4;
+// B tile: core matrices adjacent in N 128 bytes apart, adjacent in K one
+// group of kMmaN / 8 core matrices plus 16 bytes apart (so that the 16-byte
+// stores of 8 consecutive K groups by 8 lanes hit distinct banks)
+constexpr int kMmaLbo = (kMmaN / 8) * 128 + 16;
+constexpr int kMmaMaxAcc = 4;   // accumulators the K steps alternate over (TMEM columns permitting)
+// the per-accumulator row partials of the epilogue live in the reduction buffer
+static_assert(kMmaMaxAcc * kMmaRows * 16 <= 4 * kCglsThreads * 8, "reduction buffer too small for the partials");
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+// exponent es with max * 2^es in [2^13, 2^14), max given by its float bits (>= 0)
+__device__ __forceinline__ int agg_exp(int bits) {
+    if (bits <= 0) return 0;
+    const int es = 13 - (((bits >> 23) & 0xff) - 127);
+    return min(max(es, -126), 126);
+}
+// One chain of MMAs (K = 16 each) of a tile product: n steps, the first at A
+// column `at` and B descriptor `bd`, the next ones astep columns and bstep
+// descriptor units (16 bytes; the shared-memory window keeps the address field
+// below 2^14) further, all accumulating into d.  The issuing thread's loop is
+// the critical path, so it only adds constants.
+__device__ __forceinline__ void issue_chain(uint32_t d, uint32_t at, uint64_t bd, int n, uint32_t astep,
+                                            uint64_t bstep) {
+    constexpr uint32_t idesc = idesc_f16(kMmaRows, kMmaN);
+    mma_f16_ts(d, at, bd, idesc, 0u);
+#pragma unroll 4
+    for (int i = 1; i < n; ++i) {
+        at += astep;
+        bd += bstep;
+        mma_f16_ts(d, at, bd, idesc, 1u);
+    }
+}
+__device__ __forceinline__ uint32_t half_pair(__half lo, __half hi) {
+    __half2 h = __halves2half2(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+template <bool H16, int TM> struct CglsCta {
     using OT = typename UnitOp<H16>::type;
     // words of one row quad of one column: FP16 4 x half2, FP32 4 x float2
     static constexpr int kWpq = H16 ? 4 : 8;
@@ -139,7 +188,8 @@ template <bool H16, bool TM> struct CglsCta {
     long long gw_issued = 0;   // next wave to copy (thread 0)
     bool loaded = false;       // resident copy issued
     // staging entries of this thread (when nX * K <= kStageRegs * blockDim.x):
-    // global offset Y*nc + b, FP16 block scale, flags (1: own entry, 2: b >= nc/2)
+    // global offset Y*nc + b, FP16 block scale, flags (1: own entry, 2: b >= nc/2,
+    // bits 2..: the entry's aggregate among the CTA's)
     bool pre = false;
     // TMEM-resident operator (TM): this thread's quad qd and column split ks
     // (k = ks, ks + KS, ...), its TMEM lane/column base and the CTA-wide chunk count
@@ -150,6 +200,22 @@ template <bool H16, bool TM> struct CglsCta {
     float st_s[kStageRegs];
     int st_f[kStageRegs];
     bool sfail = false;   // a tagged staging wait gave up (error flag raised)
+    // tensor-core products (TM == 2): B tile, rows beyond the MMA tile, the
+    // per-aggregate maxima of the staged operand ([2][kMmaAgg] float bits,
+    // alternating between phases), commits issued, a commit not seen complete
+    unsigned char* bt = nullptr;
+    uint32_t* rop = nullptr;
+    int* amax = nullptr;
+    int mph = 0;
+    uint32_t mma_n = 0;
+    bool mma_out = false;
+    int rows_m = 0, rem = 0, nacc = 1;
+    uint32_t dcol = 0;
+    // per-thread row constants (TM == 2): the row this thread emits (-1: none),
+    // its output offset X nc + row, sign rule and aggregate; the aggregate of
+    // the row whose accumulator columns it reads (-1: none)
+    int e_row = -1, e_o = 0, e_xl = 0, p_xl = -1;
+    bool e_neg = false;
 
     __device__ CglsCta(const CglsArgs& args, unsigned char* sm) : a(args) {
         nc = a.nc; K = 9 * nc; nvh = nc >> 1; RU = a.sh.ru; H = nc / RU;
@@ -171,6 +237,28 @@ template <bool H16, bool TM> struct CglsCta {
             ov = reinterpret_cast<cx<float>*>(sm + a.sh.own_off);
             ov_n = a.sh.nu_max * RU;
         }
+        if (TM == 2) {
+            bt = sm + a.sh.bt_off;
+            rop = reinterpret_cast<uint32_t*>(sm + a.sh.rop_off);
+            amax = reinterpret_cast<int*>(sm + 64);
+            rows_m = min(nu * RU, kMmaRows);
+            rem = nu * RU - rows_m;
+            dcol = (uint32_t)(32 * ((K + 31) / 32));
+            nacc = a.sh.mma_acc;
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+            if (warp < 4 && (int)threadIdx.x < rows_m)
+                e_row = threadIdx.x;
+            else if (warp >= 4 && warp - 4 < rem)
+                e_row = kMmaRows + warp - 4;   // whole warp sums it; lane 0 emits
+            if (e_row >= 0) {
+                const int jj = e_row / RU, ain = e_row - jj * RU, u = u0 + jj, X = u / H, row = (u - X * H) * RU + ain;
+                e_o = X * nc + row;
+                e_neg = row >= nvh;
+                e_xl = X - X0;
+            }
+            const int rq = 32 * (warp & 3) + lane;
+            if (rq < rows_m) p_xl = (u0 + rq / RU) / H - X0;
+        }
         pre = nX * K <= kStageRegs * (int)blockDim.x;
         if (pre) {
 #pragma unroll
@@ -183,7 +271,7 @@ template <bool H16, bool TM> struct CglsCta {
                     const int xl = i / K, kk = i - xl * K, d = kk / nc, b = kk - d * nc, X = X0 + xl;
                     st_o[q] = __ldg(a.nbr + (size_t)X * 9 + d) * nc + b;
                     if (H16) st_s[q] = __ldg(a.su + (size_t)X * 9 + d);
-                    st_f[q] = ((d == 0 && owned(X, b)) ? 1 : 0) | (b >= nvh ? 2 : 0);
+                    st_f[q] = ((d == 0 && owned(X, b)) ? 1 : 0) | (b >= nvh ? 2 : 0) | (xl << 2);
                 }
             }
         }
@@ -234,11 +322,52 @@ template <bool H16, bool TM> struct CglsCta {
             tmem_alloc(&s_taddr, 512);
             tmem_relinquish();
         }
+        if (TM == 2) {
+            if (threadIdx.x == 0) {
+                mbar_init(mbar, nacc);   // MMA completion: one commit per issuing thread
+                fence_mbar_init();
+            }
+            if (threadIdx.x < 2 * kMmaAgg) amax[threadIdx.x] = 0;
+        }
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
         const uint32_t base = s_taddr;
         tm_base = base;
+        if constexpr (TM == 2) {
+            // row r of the CTA in lane r (warps w and w + 4k share lanes 32 (w % 4)..,
+            // and split the 32-column chunks); zeros past K and in lanes >= rows_m
+            const int lane = threadIdx.x & 31, r = 32 * (warp & 3) + lane;
+            const uint32_t* src = nullptr;
+            if (r < rows_m) {
+                const int j = r / RU, ain = r - j * RU;
+                src = reinterpret_cast<const uint32_t*>(reinterpret_cast<const unsigned char*>(a.Au) +
+                                                        (size_t)(u0 + j) * unit_bytes()) + ain;
+            }
+            const int nch = (K + 31) / 32;
+            for (int c = warp >> 2; c < nch; c += T / 128) {
+                uint32_t w[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const int k = 32 * c + i;
+                    w[i] = (src && k < K) ? __ldg(src + (size_t)k * RU) : 0u;
+                }
+                tmem_st32(base + ((uint32_t)(32 * (warp & 3)) << 16) + 32 * c, w);
+            }
+            // rows beyond the MMA tile: rop[rr][k] in shared memory
+            for (int i = threadIdx.x; i < rem * K; i += T) {
+                const int rr = i / K, k = i - rr * K, r2 = kMmaRows + rr, j = r2 / RU, ain = r2 - j * RU;
+                rop[i] = __ldg(reinterpret_cast<const uint32_t*>(reinterpret_cast<const unsigned char*>(a.Au) +
+                                                                 (size_t)(u0 + j) * unit_bytes()) +
+                               (size_t)k * RU + ain);
+            }
+            tmem_wait_st();
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            loaded = true;
+            return;
+        }
         q_quads = (nu * RU) >> 2;
         q_KS = max(1, T / q_quads);
         q_act = (int)threadIdx.x < q_quads * q_KS;
@@ -270,6 +399,9 @@ template <bool H16, bool TM> struct CglsCta {
     // TM: release the tensor memory
     __device__ void drain() {
         if (TM) {
+            // a commit whose completion a phase gave up on: wait (bounded) once more
+            // before the columns are released
+            if (TM == 2 && mma_out && threadIdx.x == 0) mbar_wait(mbar, (mma_n - 1) & 1u, kCopyWaitLimit);
             tc_fence_before();
             __syncthreads();
             tc_fence_after();
@@ -375,6 +507,161 @@ template <bool H16, bool TM> struct CglsCta {
         }
     }
 
+    // TM == 2 staging: the thread's entries (the coalesced mapping of the other
+    // shapes) signed and block-scaled into xs, each aggregate's maximum |x|
+    // through a warp reduction and one shared atomic per aggregate and warp;
+    // after a barrier thread t forms B from entries 4t..4t+3 (one aggregate xl,
+    // one 8-element K group): x * 2^es split into FP16 hi + lo in its 16-byte
+    // slots of the four B rows of xl.  Collective; ends with the async-proxy
+    // fence (the caller's barrier then orders the tile before the MMAs).
+    template <bool DAG> __device__ __forceinline__ void stage_mma(const cx<float> (&v)[kStageRegs]) {
+        const int T = blockDim.x;
+        int* am = amax + kMmaAgg * mph;
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int q = 0; q < kStageRegs; ++q) {
+            int xl = -1;
+            int bits = 0;
+            if (st_o[q] >= 0) {
+                cx<float> w = v[q];
+                if (DAG && (st_f[q] & 2)) w = cx<float>(-w.r, -w.i);
+                if (H16) w = st_s[q] * w;
+                xs[threadIdx.x + q * T] = w;
+                xl = st_f[q] >> 2;
+                bits = __float_as_int(fmaxf(fabsf(w.r), fabsf(w.i)));
+            }
+            // the warp's 32 consecutive entries span at most two aggregates (K >= 32;
+            // inactive entries, xl = -1, only at the end): one reduction each
+            const int x0 = __shfl_sync(0xffffffffu, xl, 0), x1 = __shfl_sync(0xffffffffu, xl, 31);
+            const int m0 = __reduce_max_sync(0xffffffffu, xl == x0 ? bits : 0);
+            if (lane == 0 && x0 >= 0) atomicMax(am + x0, m0);
+            if (x1 != x0) {
+                const int m1 = __reduce_max_sync(0xffffffffu, xl == x0 ? 0 : bits);
+                if (lane == 31 && x1 >= 0) atomicMax(am + x1, m1);
+            }
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < kMmaAgg) amax[kMmaAgg * (mph ^ 1) + threadIdx.x] = 0;   // next phase's maxima
+        const int i0 = kStageRegs * (int)threadIdx.x;
+        if (i0 < nX * K) {
+            const int xl = i0 / K;
+            const float sc = pow2f(agg_exp(am[xl]));
+            const float4* x4 = reinterpret_cast<const float4*>(xs + i0);
+            const float4 xa = x4[0], xb = x4[1];
+            const float re[4] = {xa.x * sc, xa.z * sc, xb.x * sc, xb.z * sc};
+            const float im[4] = {xa.y * sc, xa.w * sc, xb.y * sc, xb.w * sc};
+            uint32_t rh[kStageRegs], ih[kStageRegs], rl[kStageRegs], il[kStageRegs];
+#pragma unroll
+            for (int q = 0; q < kStageRegs; ++q) {
+                const __half reh = __float2half_rn(re[q]), imh = __float2half_rn(im[q]);
+                const __half rel = __float2half_rn(re[q] - __half2float(reh));
+                const __half iml = __float2half_rn(im[q] - __half2float(imh));
+                rh[q] = half_pair(reh, __hneg(imh));
+                ih[q] = half_pair(imh, reh);
+                rl[q] = half_pair(rel, __hneg(iml));
+                il[q] = half_pair(iml, rel);
+            }
+            unsigned char* dst = bt + (size_t)((i0 - xl * K) >> 2) * kMmaLbo + 64 * xl;
+            *reinterpret_cast<uint4*>(dst) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
+            *reinterpret_cast<uint4*>(dst + 16) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
+            *reinterpret_cast<uint4*>(dst + 32) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
+            *reinterpret_cast<uint4*>(dst + 48) = make_uint4(il[0], il[1], il[2], il[3]);
+        }
+        fence_proxy_async();
+        mph ^= 1;
+    }
+
+    // TM == 2 products and epilogue (after the staging barrier): thread 0 issues
+    // the 9nc/8 MMAs of the tile and commits them to the mbarrier; meanwhile
+    // warps 4.. sum the rows beyond the tile; every thread waits for the commit;
+    // warps 0-3 read their lanes' 32 accumulator columns and keep the four of
+    // their row's aggregate; pre_emit; one emitting thread per row.
+    template <bool DAG, int EPI, typename Pre>
+    __device__ bool mma_phase(CglsPhase& ph, float& n0, float& n1, Pre& pre_emit) {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if (lane == 0 && warp < nacc) {
+            // K steps k8 = warp, warp + nacc, ... into accumulator `warp`: nacc
+            // independent chains issued by nacc threads, each committing once
+            constexpr uint64_t kStep = (2 * kMmaLbo) >> 4;
+            tc_fence_after();
+            const uint64_t bd = smem_desc(smem_u32(bt), kMmaLbo, 128) + kStep * (uint64_t)warp;
+            issue_chain(tm_base + dcol + kMmaN * warp, tm_base + 8 * warp, bd, (K / 8 - warp + nacc - 1) / nacc,
+                        8u * nacc, kStep * (uint64_t)nacc);
+            mma_commit(mbar);
+        }
+        const int* am = amax + kMmaAgg * (mph ^ 1);   // this phase's maxima
+        cx<float> ysum(0.f, 0.f);
+        if (warp >= 4 && e_row >= 0) {
+            const float2* xv = reinterpret_cast<const float2*>(xs) + (size_t)e_xl * K;
+            const __half2* ar = reinterpret_cast<const __half2*>(rop) + (size_t)(warp - 4) * K;
+            float yr = 0.f, yi = 0.f;
+            for (int k = lane; k < K; k += 32) {
+                const float2 av = __half22float2(ar[k]), x = xv[k];
+                yr = fmaf(av.x, x.x, fmaf(-av.y, x.y, yr));
+                yi = fmaf(av.x, x.y, fmaf(av.y, x.x, yi));
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                yr += __shfl_xor_sync(0xffffffffu, yr, o);
+                yi += __shfl_xor_sync(0xffffffffu, yi, o);
+            }
+            ysum = cx<float>(yr, yi);
+        }
+        const bool got = mbar_wait(mbar, mma_n & 1u, kCopyWaitLimit);
+        ++mma_n;
+        tc_fence_after();
+        // accumulator j of lane quadrant w % 4 read by warp w = 4 j + quadrant (the
+        // four warps of a quadrant load in parallel); its row's four columns
+        // into part[j][row] (the reduction buffer, unused by this path)
+        float4* part = reinterpret_cast<float4*>(red);
+        if ((warp >> 2) < nacc) {
+            const int rq = 32 * (warp & 3) + lane;
+            uint32_t d[32];
+            tmem_ld32(tm_base + ((uint32_t)(32 * (warp & 3)) << 16) + dcol + kMmaN * (warp >> 2), d);
+            if (p_xl >= 0) {
+                // columns 4 p_xl .. 4 p_xl + 3 by a select tree on the bits of p_xl
+                // (constant register indices only)
+                uint32_t h[16], g[8], f[4];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) h[i] = (p_xl & 4) ? d[16 + i] : d[i];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) g[i] = (p_xl & 2) ? h[8 + i] : h[i];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) f[i] = (p_xl & 1) ? g[4 + i] : g[i];
+                part[(warp >> 2) * kMmaRows + rq] = make_float4(__uint_as_float(f[0]), __uint_as_float(f[1]),
+                                                                __uint_as_float(f[2]), __uint_as_float(f[3]));
+            }
+        }
+        tc_fence_before();
+        const int r = threadIdx.x;
+        if (__syncthreads_or(!got)) {
+            if (threadIdx.x == 0) atomicExch(a.err, 3);
+            mma_out = true;
+            return false;
+        }
+        const int go = pre_emit();
+        if (go < 0) return false;
+        if (go == 0) {
+            ph.stop = true;
+            return true;
+        }
+        if (e_row >= 0 && (warp < 4 || lane == 0)) {
+            cx<float> sum = ysum;
+            if (warp < 4) {
+                float4 c = part[r];
+                for (int j = 1; j < nacc; ++j) {
+                    const float4 e = part[j * kMmaRows + r];
+                    c.x += e.x; c.y += e.y; c.z += e.z; c.w += e.w;
+                }
+                const float inv = pow2f(-agg_exp(am[e_xl]));
+                sum = cx<float>((c.x + c.z) * inv, (c.y + c.w) * inv);
+            }
+            if (DAG && e_neg) sum = cx<float>(-sum.r, -sum.i);
+            emit<EPI>(ph, (size_t)e_o, e_row, sum, n0, n1);
+        }
+        return true;
+    }
+
     // One stencil application out = D_c (or D_c^dag) x on the CTA's rows, the
     // operand x formed while staging:
     //   ST_IN: x = in
@@ -419,14 +706,18 @@ template <bool H16, bool TM> struct CglsCta {
                 for (int q = 0; q < kStageRegs; ++q)
                     if (st_o[q] >= 0) v[q] = form<STAGE>(ph, st_o[q], (st_f[q] & 1) != 0, n1);
             }
+            if constexpr (TM == 2) {
+                stage_mma<DAG>(v);
+            } else {
 #pragma unroll
-            for (int q = 0; q < kStageRegs; ++q)
-                if (st_o[q] >= 0) {
-                    cx<float> w = v[q];
-                    if (DAG && (st_f[q] & 2)) w = cx<float>(-w.r, -w.i);
-                    if (H16) w = st_s[q] * w;
-                    xs[threadIdx.x + q * T] = w;
-                }
+                for (int q = 0; q < kStageRegs; ++q)
+                    if (st_o[q] >= 0) {
+                        cx<float> w = v[q];
+                        if (DAG && (st_f[q] & 2)) w = cx<float>(-w.r, -w.i);
+                        if (H16) w = st_s[q] * w;
+                        xs[threadIdx.x + q * T] = w;
+                    }
+            }
         } else {
             for (int i = threadIdx.x; i < nX * K; i += T) {
                 const int xl = i / K, kk = i - xl * K, d = kk / nc, b = kk - d * nc;
@@ -439,8 +730,9 @@ template <bool H16, bool TM> struct CglsCta {
             }
         }
         if (__syncthreads_or(sfail)) return false;
+        if constexpr (TM == 2) return mma_phase<DAG, EPI>(ph, n0, n1, pre_emit);
         const float2* xs2 = reinterpret_cast<const float2*>(xs);
-        if (TM) {
+        if constexpr (TM != 0) {
             const int rows = nu * RU;
             const int r = 4 * q_qd, j = r / RU;
             const float2* xv = xs2 + (size_t)((u0 + j) / H - X0) * K;
@@ -486,7 +778,7 @@ template <bool H16, bool TM> struct CglsCta {
                 emit<EPI>(ph, (size_t)X * nc + row, rr, sum, n0, n1);
             }
             return true;
-        }
+        } else {
         for (int iw = 0; iw < NW; ++iw) {
             const int j0 = iw * W, n = min(W, nu - j0), rows = n * RU, quads = rows >> 2;
             const int grp = resident ? 0 : (int)(gw_next % NG);
@@ -548,10 +840,11 @@ template <bool H16, bool TM> struct CglsCta {
             if (!resident) buf ^= 1;
         }
         return true;
+        }
     }
 };
 
-template <bool H16, bool TM> __device__ void cgls_body(const CglsArgs& a, CglsCta<H16, TM>& c) {
+template <bool H16, int TM> __device__ void cgls_body(const CglsArgs& a, CglsCta<H16, TM>& c) {
     unsigned int e = a.epoch0;   // one epoch per exchange
     // exchange scratch: its own kXchScratch floats after the staging buffer
     float* shr = reinterpret_cast<float*>(c.xs + (size_t)a.sh.nx_max * c.K);
@@ -637,7 +930,7 @@ template <bool H16, bool TM> __device__ void cgls_body(const CglsArgs& a, CglsCt
 // be a whole iteration ahead of a reader of the same entry: it overwrites s
 // (u) only after the exchange (the next s staging) that needs the reader's
 // partial sums, published after the reader's staging.
-template <bool H16, bool TM> __device__ void cgls_body_tag(const CglsArgs& a, CglsCta<H16, TM>& c) {
+template <bool H16, int TM> __device__ void cgls_body_tag(const CglsArgs& a, CglsCta<H16, TM>& c) {
     unsigned int ex = a.epoch0;           // exchange epochs
     const unsigned int E = a.epoch0;      // tag epoch of s_0 and u_0
     float* shr = reinterpret_cast<float*>(c.xs + (size_t)a.sh.nx_max * c.K);
@@ -745,7 +1038,7 @@ template <bool H16, bool TM> __device__ void cgls_body_tag(const CglsArgs& a, Cg
 // unnormalised and unused) or of its three-value exchange.  Same epochs and
 // reader/writer ordering as the solver: a CTA rewrites s (u) only after staging
 // the neighbour entries of u (s) that the neighbour writes after reading it.
-template <bool H16, bool TM> __device__ void cgls_probe(const CglsArgs& a, CglsCta<H16, TM>& c) {
+template <bool H16, int TM> __device__ void cgls_probe(const CglsArgs& a, CglsCta<H16, TM>& c) {
     float* shr = reinterpret_cast<float*>(c.xs + (size_t)a.sh.nx_max * c.K);
     const unsigned int E = a.epoch0;
     if (a.form == CGLS_PROBE_EXCHANGE) {
@@ -776,7 +1069,7 @@ template <bool H16, bool TM> __device__ void cgls_probe(const CglsArgs& a, CglsC
     }
 }
 
-template <bool H16, bool TM> __global__ void __launch_bounds__(kCglsThreads, 1) k_cgls_onchip(CglsArgs a) {
+template <bool H16, int TM> __global__ void __launch_bounds__(kCglsThreads, 1) k_cgls_onchip(CglsArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     CglsCta<H16, TM> c(a, smem_raw);
     c.start();
@@ -855,6 +1148,22 @@ DevLimits dev_limits() {
     return l;
 }
 size_t round_up(size_t x, size_t m) { return (x + m - 1) / m * m; }
+// tensor-core shape (tm 2): sets own_off, bt_off, mma_lbo, rop_off, rem_max
+// from the end `off` of the common regions and returns the padded total
+size_t mma_smem(size_t off, CglsShape& s, int K, int smem_optin) {
+    const int rows = s.nu_max * s.ru;
+    s.own_off = (int)off;
+    off = round_up(off + (size_t)OV_COUNT * rows * 8, 128);
+    s.bt_off = (int)off;
+    s.mma_lbo = kMmaLbo;
+    off += (size_t)(K / 4) * kMmaLbo;
+    off = round_up(off, 16);
+    s.rop_off = (int)off;
+    s.rem_max = std::max(0, rows - kMmaRows);
+    s.mma_acc = std::min(kMmaMaxAcc, (512 - 32 * ((K + 31) / 32)) / kMmaN);
+    off += (size_t)s.rem_max * K * 4;
+    return std::max(off, (size_t)smem_optin / 2 + 4096);
+}
 }  // namespace
 
 // Pick the rows per unit RU (a divisor of nc, a multiple of 4, with RU * element
@@ -904,7 +1213,19 @@ bool cgls_shape(int nc, int Vc, bool h16, int mode, CglsShape* out) {
             s.wave = 1;
             s.slots = 2;
             score = (long long)s.nu_max * ru;
-        } else if (mode == CGLS_AUTO && chunks <= 4 && off <= budget) {
+        } else if (mode == CGLS_AUTO && h16 && K % 8 == 0 && K <= 480 && s.nx_max <= kMmaAgg &&
+                   s.nx_max * K <= kStageRegs * T && s.nu_max * ru - kMmaRows <= kMmaRemWarps &&
+                   mma_smem(off, s, K, lim.smem) <= budget) {
+            // the operator in tensor memory, products on the tensor cores (same
+            // padding past half an SM as below)
+            s.tm = 2;
+            s.resident = 1;
+            s.slots = 0;
+            s.wave = s.nu_max;
+            s.groups = 1;
+            off = mma_smem(off, s, K, lim.smem);
+            score = (long long)s.nu_max * ru;
+        } else if ((mode == CGLS_AUTO || mode == CGLS_TMEM_CORES) && chunks <= 4 && off <= budget) {
             // the operator in tensor memory; shared memory padded past half an SM
             // so that no second CTA of this kernel (and no second all-column TMEM
             // allocation) shares the SM.  Padding to the whole SM would also keep
@@ -922,8 +1243,8 @@ bool cgls_shape(int nc, int Vc, bool h16, int mode, CglsShape* out) {
             s.own_off = (int)off;
             off = std::max(off + (size_t)OV_COUNT * s.nu_max * ru * 8, (size_t)lim.smem / 2 + 4096);
             if (off > budget) continue;
-            score = (long long)s.nu_max * ru;
-        } else if (off + (size_t)s.nu_max * s.stride <= budget) {
+            score = (long long)s.nu_max * ru + (mode == CGLS_AUTO ? (1LL << 38) : 0);   // tensor-core shapes first
+        } else if (mode != CGLS_TMEM_CORES && off + (size_t)s.nu_max * s.stride <= budget) {
             s.resident = 1;
             s.slots = s.nu_max;
             s.wave = s.nu_max;
@@ -948,16 +1269,19 @@ bool cgls_shape(int nc, int Vc, bool h16, int mode, CglsShape* out) {
 
 cudaError_t cgls_onchip(const CglsArgs& args, cudaStream_t st) {
     const bool h16 = args.su != nullptr, tm = args.sh.tm != 0;
-    const void* fns[2][2] = {{(const void*)k_cgls_onchip<false, false>, (const void*)k_cgls_onchip<false, true>},
-                             {(const void*)k_cgls_onchip<true, false>, (const void*)k_cgls_onchip<true, true>}};
-    const void* fn = fns[h16][tm];
-    static std::atomic<bool> attr[kCglsDevs][2][2];   // per device: the attribute is set on the current one
+    const int tmk = args.sh.tm;
+    if (tmk < 0 || tmk > 2 || (tmk == 2 && !h16)) return cudaErrorInvalidValue;
+    const void* fns[2][3] = {{(const void*)k_cgls_onchip<false, 0>, (const void*)k_cgls_onchip<false, 1>, nullptr},
+                             {(const void*)k_cgls_onchip<true, 0>, (const void*)k_cgls_onchip<true, 1>,
+                              (const void*)k_cgls_onchip<true, 2>}};
+    const void* fn = fns[h16][tmk];
+    static std::atomic<bool> attr[kCglsDevs][2][3];   // per device: the attribute is set on the current one
     const DevLimits lim = dev_limits();
     if (lim.dev < 0) return cudaErrorInvalidDevice;
-    if (!attr[lim.dev][h16][tm].load(std::memory_order_acquire)) {
+    if (!attr[lim.dev][h16][tmk].load(std::memory_order_acquire)) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lim.smem - 1024);
         if (e != cudaSuccess) return e;
-        attr[lim.dev][h16][tm].store(true, std::memory_order_release);
+        attr[lim.dev][h16][tmk].store(true, std::memory_order_release);
     }
     if (((args.form == CGLS_CG_TAGGED || args.form == CGLS_PROBE_STENCILS) && !args.tag) || args.sh.smem > (size_t)lim.smem - 1024 || args.sh.grid <= 0 ||
         args.sh.grid > lim.sms ||

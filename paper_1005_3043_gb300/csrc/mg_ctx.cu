@@ -409,6 +409,12 @@ int ensure_a16(mg_ctx* ctx, CoarseLevel& L, int Vc) {
     return MG_OK;
 }
 
+// shape mode of the on-chip CGLS for MgParams.coarse_kernel (0, 2, 3, 4)
+int cgls_mode(int coarse_kernel) {
+    return coarse_kernel == 2 ? CGLS_STREAM : coarse_kernel == 3 ? CGLS_SMEM : coarse_kernel == 4 ? CGLS_TMEM_CORES
+                                                                                                    : CGLS_AUTO;
+}
+
 // The operator in the unit layout of the on-chip CGLS kernel; false when no
 // shape fits this device (the register-streaming kernel is used instead).
 int ensure_units(mg_ctx* ctx, CoarseLevel& L, int Vc, bool h16, int mode, bool* ok) {
@@ -475,7 +481,7 @@ int coarse_solve(mg_ctx* ctx, const CoarseLevel& L, const CgSys<T>& sys, const v
     bool onchip = false;
     if (std::is_same<T, float>::value && ctx->prm.coarse_kernel != 1) {
         CoarseLevel& Lm = const_cast<CoarseLevel&>(L);
-        const int mode = ctx->prm.coarse_kernel == 2 ? CGLS_STREAM : ctx->prm.coarse_kernel == 3 ? CGLS_SMEM : CGLS_AUTO;
+        const int mode = cgls_mode(ctx->prm.coarse_kernel);
         TRY(ensure_units(ctx, Lm, sys.g.Vc, ctx->coarse16, mode, &onchip));
     }
     if (onchip) {
@@ -501,7 +507,7 @@ int coarse_solve(mg_ctx* ctx, const CoarseLevel& L, const CgSys<T>& sys, const v
         PROF_BEGIN(MG_K_COARSE_SOLVE);
         CK(cgls_onchip(c, ctx->st));
         PROF_END(MG_K_COARSE_SOLVE);
-        ctx->coarse_kernel_used = c.sh.tm ? MG_CK_TMEM : c.sh.resident ? MG_CK_SMEM : MG_CK_STREAM;
+        ctx->coarse_kernel_used = c.sh.tm == 2 ? MG_CK_TMEM_MMA : c.sh.tm ? MG_CK_TMEM : c.sh.resident ? MG_CK_SMEM : MG_CK_STREAM;
     } else if (std::is_same<T, float>::value && ctx->coarse16) {
         CoarseLevel& Lm = const_cast<CoarseLevel&>(L);
         TRY(ensure_a16(ctx, Lm, sys.g.Vc));
@@ -1157,7 +1163,7 @@ int check_params(const int dims[4], const mg_params* p, std::string& why) {
         return MG_ERR_INVALID_ARG;
     }
     if (p->prec_inner == MG_FP16 && p->nvec % 2 != 0) { why = "MG_FP16 needs an even nvec"; return MG_ERR_INVALID_ARG; }
-    if (p->coarse_kernel < 0 || p->coarse_kernel > 3) { why = "coarse_kernel must be 0, 1, 2 or 3"; return MG_ERR_INVALID_ARG; }
+    if (p->coarse_kernel < 0 || p->coarse_kernel > 4) { why = "coarse_kernel must be 0, 1, 2, 3 or 4"; return MG_ERR_INVALID_ARG; }
     if (p->smoother_fp16 < 0 || p->smoother_fp16 > 2) { why = "smoother_fp16 must be 0, 1 or 2"; return MG_ERR_INVALID_ARG; }
     if (p->coarse_form < 0 || p->coarse_form > 1) { why = "coarse_form must be 0 or 1"; return MG_ERR_INVALID_ARG; }
     if (p->smoother < 0 || p->smoother > 1) { why = "smoother must be 0 (MR) or 1 (GMRES)"; return MG_ERR_INVALID_ARG; }
@@ -2083,7 +2089,7 @@ int mg_time_coarse_floor(mg_ctx* ctx, int rounds, double* us_stencils, double* u
     TRY(ensure_work<float>(ctx));
     CoarseLevel& L = ctx->full;
     const CgSys<float> sys = level1_sys<float>(ctx);
-    const int mode = ctx->prm.coarse_kernel == 2 ? CGLS_STREAM : ctx->prm.coarse_kernel == 3 ? CGLS_SMEM : CGLS_AUTO;
+    const int mode = cgls_mode(ctx->prm.coarse_kernel);
     bool onchip = false;
     TRY(ensure_units(ctx, L, sys.g.Vc, ctx->coarse16, mode, &onchip));
     if (!onchip) return fail(ctx, MG_ERR_INVALID_ARG, "no on-chip shape for this coarse level");

@@ -200,12 +200,18 @@ struct CglsShape {
     int stride;      // bytes between slots
     int slot_off;    // byte offset of slot 0 in dynamic shared memory
     int red_n;       // complex entries per reduction buffer
-    int tm;          // 1: the operator in tensor memory (all 512 columns of the SM)
-    int tm_chunks;   // 32-column TMEM chunks per thread
+    int tm;          // the operator in tensor memory (all 512 columns of the SM): 1 products on the
+                     // CUDA cores, 2 products on the tensor cores (tcgen05.mma, A from TMEM)
+    int tm_chunks;   // 32-column TMEM chunks per thread (tm 1)
     int own_off;     // byte offset of the own-row vectors of the tagged form in shared memory (0: global)
+    int bt_off;      // tm 2: byte offset of the FP16 hi/lo operand tile (MMA B) in shared memory
+    int mma_lbo;     // tm 2: its byte distance between core matrices adjacent in K
+    int rop_off;     // tm 2: byte offset of the rows beyond the 128 MMA rows (FP16 operator, shared memory)
+    int rem_max;     // tm 2: those rows of the busiest CTA
+    int mma_acc;     // tm 2: accumulators (32 TMEM columns each) the K steps alternate over
     size_t smem;     // dynamic shared memory per CTA
 };
-enum { CGLS_AUTO = 0, CGLS_STREAM = 2, CGLS_SMEM = 3 };
+enum { CGLS_AUTO = 0, CGLS_STREAM = 2, CGLS_SMEM = 3, CGLS_TMEM_CORES = 4 };
 // iteration form of the on-chip CGLS: two grid-wide exchanges per iteration, or
 // the Chronopoulos-Gear form with one exchange and epoch-tagged shared vectors
 enum { CGLS_TEXTBOOK = 0, CGLS_CG_TAGGED = 1 };

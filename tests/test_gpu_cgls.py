@@ -18,8 +18,11 @@ from tests._fields import c1_workload
 
 pytestmark = pytest.mark.gpu
 
-# (coarse_kernel, coarse_form); the register kernel has one form
-VARIANTS = [(0, 0), (0, 1), (1, 0), (2, 0), (2, 1), (3, 0), (3, 1)]
+# (coarse_kernel, coarse_form); the register kernel has one form; 0 picks the
+# tensor-memory operator with tensor-core products for the FP16 operator at
+# this size, 4 the tensor-memory operator with CUDA-core products
+TMEM_KERNEL_RUN = {0: 4, 4: 3}   # coarse_kernel -> MG_CK_* id run with the FP16 operator
+VARIANTS = [(0, 0), (0, 1), (1, 0), (2, 0), (2, 1), (3, 0), (3, 1), (4, 0), (4, 1)]
 # FP32 CG iterates against FP64 after k steps on this operator (condition
 # number ~14): near FP32 rounding for the first steps (1.7e-7 at k = 1 and 7
 # for a complex64 CGLS in numpy), then growing with the loss of conjugacy
@@ -131,6 +134,8 @@ def test_fixed_iterations_exact_fp16_rounding(level_random, kernel, form, prec):
             y, it, _ = mg.coarse_solve(lv["rc"], 0.0, k, prec)
             assert it == it_ref == k
             assert maxrel(y, y_ref) < 1e-5, (k, maxrel(y, y_ref))
+            if prec == wmg.MG_FP16 and kernel in TMEM_KERNEL_RUN:
+                assert mg.coarse_kernel() == TMEM_KERNEL_RUN[kernel], wmg.COARSE_KERNELS[mg.coarse_kernel()]
 
 
 @pytest.mark.parametrize("kernel,form", VARIANTS)

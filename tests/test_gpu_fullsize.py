@@ -63,14 +63,14 @@ def c2():
                 A16_relax=quantise16(A_relax))
 
 
-def _mg(c, V, form, shift=0.0):
+def _mg(c, V, form, shift=0.0, kernel=0):
     p = wmg.mg_default_params()
     for i in range(4):
         p.block[i] = c["B"][i]
     p.nvec = c["nv"]
     p.setup_group = 4
     p.prec_inner = wmg.MG_FP64        # D_c built in FP64 from the prototypes
-    p.coarse_kernel = 0
+    p.coarse_kernel = kernel
     p.coarse_form = form
     mg = wmg.WilsonMG(c["L"], p)
     mg.set_links(c["U"])
@@ -84,19 +84,26 @@ def _mg(c, V, form, shift=0.0):
 FIXED_K_TOL = {1: 1e-5, 6: 1e-5, 25: 1e-4}
 
 
+# coarse_kernel -> MG_CK_* id at this size: 0 (default) the tensor-memory
+# operator with tensor-core products, 4 with CUDA-core products
+TMEM_KERNELS = {0: 4, 4: 3}
+
+
+@pytest.mark.parametrize("kernel", [0, 4])
 @pytest.mark.parametrize("form", [0, 1])
-def test_fixed_iterations_16x16x16x32_tmem(c2, form):
-    with _mg(c2, c2["V_rand"], form) as mg:
+def test_fixed_iterations_16x16x16x32_tmem(c2, form, kernel):
+    with _mg(c2, c2["V_rand"], form, kernel=kernel) as mg:
         for k, tol in FIXED_K_TOL.items():
             y_ref, it_ref, _ = oracle.cgnr(c2["A16_rand"], c2["rc"], c2["Lc"], 0.0, k)
             y, it, _ = mg.coarse_solve(c2["rc"], 0.0, k, wmg.MG_FP16)
-            assert mg.coarse_kernel() == 3, wmg.COARSE_KERNELS[mg.coarse_kernel()]
+            assert mg.coarse_kernel() == TMEM_KERNELS[kernel], wmg.COARSE_KERNELS[mg.coarse_kernel()]
             assert it == it_ref == k
             assert maxrel(y, y_ref) < tol, (k, maxrel(y, y_ref))
 
 
+@pytest.mark.parametrize("kernel", [0, 4])
 @pytest.mark.parametrize("form", [0, 1])
-def test_converged_solve_16x16x16x32_tmem(c2, form):
+def test_converged_solve_16x16x16x32_tmem(c2, form, kernel):
     """On the relaxed-prototype D_c at the shifted mass: iterates after 6, 25
     and 100 steps (a complex64 numpy CGLS on these entries stays within 5e-7
     of the FP64 one up to k = 100), then the solve to 1e-3 with an iteration
@@ -106,13 +113,13 @@ def test_converged_solve_16x16x16x32_tmem(c2, form):
     A16 = c2["A16_relax"]
     y_ref, it_ref, _ = oracle.cgnr(A16, c2["rc"], c2["Lc"], 1e-3, 20000)
     assert it_ref > 300, it_ref           # deep enough to exercise many exchanges
-    with _mg(c2, c2["V_relax"], form, SHIFT) as mg:
+    with _mg(c2, c2["V_relax"], form, SHIFT, kernel) as mg:
         for k, tol in ((6, 1e-5), (25, 1e-5), (100, 1e-4)):
             y_k, _, _ = oracle.cgnr(A16, c2["rc"], c2["Lc"], 0.0, k)
             y, it, _ = mg.coarse_solve(c2["rc"], 0.0, k, wmg.MG_FP16)
             assert it == k and maxrel(y, y_k) < tol, (k, maxrel(y, y_k))
         y, it, rel = mg.coarse_solve(c2["rc"], 1e-3, 20000, wmg.MG_FP16)
-        assert mg.coarse_kernel() == 3
+        assert mg.coarse_kernel() == TMEM_KERNELS[kernel]
     assert rel <= 1e-3
     assert abs(it - it_ref) <= max(2, 0.02 * it_ref), (it, it_ref)
     true_rel = np.linalg.norm(c2["rc"] - oracle.coarse_apply(A16, y, c2["Lc"])) / np.linalg.norm(c2["rc"])
