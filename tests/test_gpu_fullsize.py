@@ -1,7 +1,9 @@
 """Coarse CGNR parity at the 16^3 x 32 shapes the benchmark runs (4^4 aggregates,
 Nv = 20: Vc = 512 coarse sites, nc = 40 dof per site), on the default on-chip
-kernel with the FP16 operator in tensor memory (three 32-column TMEM chunks per
-thread, every one of the 152 CTAs owning units), in both iteration forms,
+kernel with the FP16 operator in tensor memory (products on the tensor cores:
+128 rows per CTA in one MMA tile, the 8 rows past it on the CUDA cores, every
+one of the 152 CTAs owning units) and on the CUDA-core form (three 32-column
+TMEM chunks per thread), in both iteration forms,
 against the oracle's CGLS (Sec. IV: CG on the normal equations of the
 coarsest operator) on the oracle's own D_c rounded by the FP16 storage rule.
 
@@ -124,3 +126,22 @@ def test_converged_solve_16x16x16x32_tmem(c2, form, kernel):
     assert abs(it - it_ref) <= max(2, 0.02 * it_ref), (it, it_ref)
     true_rel = np.linalg.norm(c2["rc"] - oracle.coarse_apply(A16, y, c2["Lc"])) / np.linalg.norm(c2["rc"])
     assert true_rel <= 1.5e-3, true_rel
+
+
+@pytest.mark.parametrize("kernel", [0, 4])
+def test_scale_invariance_16x16x16x32_tmem(c2, kernel):
+    """CGLS is linear in its right-hand side: y(lam rc) = lam y(rc) with the same
+    iterates.  The tensor-core form rescales each aggregate's operand by a power
+    of two before its FP16 hi/lo split, so right-hand sides far outside the FP16
+    range (lam = 2^-40, 2^40; |lam rc|^2 stays inside the FP32 range of the CG
+    scalars) give the same iterates as lam = 1, scaled by lam (powers of two:
+    exactly); a zero right-hand side gives y = 0 in zero iterations."""
+    with _mg(c2, c2["V_rand"], 0, kernel=kernel) as mg:
+        y1, it1, _ = mg.coarse_solve(c2["rc"], 0.0, 6, wmg.MG_FP16)
+        for lam in (2.0 ** -40, 2.0 ** 40):
+            y, it, _ = mg.coarse_solve(lam * c2["rc"], 0.0, 6, wmg.MG_FP16)
+            assert it == it1 == 6
+            assert maxrel(y / lam, y1) < 1e-6, (lam, maxrel(y / lam, y1))
+        y0, it0, _ = mg.coarse_solve(np.zeros_like(c2["rc"]), 1e-3, 100, wmg.MG_FP16)
+        assert it0 == 0 and not np.any(y0)
+        assert mg.coarse_kernel() == TMEM_KERNELS[kernel]
