@@ -926,10 +926,12 @@ template <bool H16, int TM> __device__ void cgls_body(const CglsArgs& a, CglsCta
 // s and u, the two vectors other CTAs read, live in epoch-tagged buffers
 // (s_i and u_i carry epoch E + i), so a stencil's staging waits for exactly the
 // entries it reads and needs no flag or fence; the exchange of the partial
-// sums publishes with relaxed stores for the same reason.  A writer can never
-// be a whole iteration ahead of a reader of the same entry: it overwrites s
-// (u) only after the exchange (the next s staging) that needs the reader's
-// partial sums, published after the reader's staging.
+// sums (xch_post_packed / xch_collect_packed: a CTA's three sums in one line)
+// publishes and polls with relaxed accesses for the same reason.  A writer can
+// never be a whole iteration ahead of a reader of the same entry: it overwrites
+// s (u) only after the exchange (the next s staging) that needs the reader's
+// partial sums, published after the reader's staging; the partial sums depend
+// on the staged values and the overwriting values on the collected sums.
 template <bool H16, int TM> __device__ void cgls_body_tag(const CglsArgs& a, CglsCta<H16, TM>& c) {
     unsigned int ex = a.epoch0;           // exchange epochs
     const unsigned int E = a.epoch0;      // tag epoch of s_0 and u_0
@@ -952,7 +954,8 @@ template <bool H16, int TM> __device__ void cgls_body_tag(const CglsArgs& a, Cgl
         one[0] += v.x * v.x + v.y * v.y;
     }
     const float rpart0 = one[0];
-    if (!xch_allreduce<1, false>(one, a.xch, ex++, a.err, shr)) return;
+    xch_post_packed<1>(one, a.xch, ex, shr);
+    if (!xch_collect_packed<1>(one, a.xch, ex++, a.err, shr)) return;
     const float rc2 = one[0];
     int it = 0;
     float r2 = rc2;
@@ -981,7 +984,7 @@ template <bool H16, int TM> __device__ void cgls_body_tag(const CglsArgs& a, Cgl
             // exchange's latency hides behind w = D_c^dag u
             float three[3] = {n0, gpart, rpart};
             const unsigned int ex_i = ex++;
-            xch_post<3, false>(three, a.xch, ex_i, shr);
+            xch_post_packed<3>(three, a.xch, ex_i, shr);
             float gamma = 0.f, alpha = 0.f;
             ph = CglsPhase{};
             ph.tin = tu;
@@ -991,7 +994,7 @@ template <bool H16, int TM> __device__ void cgls_body_tag(const CglsArgs& a, Cgl
             ph.etag_out = E + (unsigned int)i + 1u;
             ph.first = (i == 0);
             auto pre = [&]() -> int {
-                if (!xch_collect<3>(three, a.xch, ex_i, a.err, shr)) return -1;
+                if (!xch_collect_packed<3>(three, a.xch, ex_i, a.err, shr)) return -1;
                 const float delta = three[0];
                 gamma = three[1];
                 r2 = three[2];
@@ -1044,7 +1047,8 @@ template <bool H16, int TM> __device__ void cgls_probe(const CglsArgs& a, CglsCt
     if (a.form == CGLS_PROBE_EXCHANGE) {
         for (int i = 0; i < a.maxit; ++i) {
             float three[3] = {1.f, 1.f, 1.f};
-            if (!xch_allreduce<3, false>(three, a.xch, E + (unsigned int)i, a.err, shr)) return;
+            xch_post_packed<3>(three, a.xch, E + (unsigned int)i, shr);
+            if (!xch_collect_packed<3>(three, a.xch, E + (unsigned int)i, a.err, shr)) return;
         }
         return;
     }

@@ -194,6 +194,91 @@ __device__ bool xch_collect(float (&v)[NV], const unsigned long long* slots, uns
     for (int j = 0; j < NV; ++j) v[j] = res[j];
     return true;
 }
+// Packed form for callers whose cross-CTA data carries its own epoch tags (so
+// the exchange orders nothing but its own values): a CTA's NV partial sums sit
+// in one 128-byte line, words 0..NV-1 each (epoch << 32 | value), stored and
+// polled with relaxed GPU-scope accesses, one polling thread per CTA line.
+// slots: [parity 2][G][kXchPad] (inside the unpacked layout's footprint);
+// epochs consecutive as for xch_post.  Every word is single-copy atomic, and
+// the reader re-polls until all NV words carry the epoch.
+__device__ __forceinline__ void xch_store_words(unsigned long long* line, const unsigned long long* w, int n) {
+    if (n >= 2)
+        asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(line), "l"(w[0]), "l"(w[1]) : "memory");
+    else
+        asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(line), "l"(w[0]) : "memory");
+    if (n == 3) asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(line + 2), "l"(w[2]) : "memory");
+}
+template <int NV>
+__device__ void xch_post_packed(const float (&v)[NV], unsigned long long* slots, unsigned int e, float* sc) {
+    static_assert(NV >= 1 && NV <= kXchMaxNV, "one to three values per exchange");
+    const int G = (int)gridDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
+    unsigned long long* line = slots + ((size_t)(e & 1) * G + blockIdx.x) * kXchPad;
+    float* wsum = sc;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        const float w = warp_sum_t<float>(v[j]);
+        if (lane == 0) wsum[j * 32 + warp] = w;
+    }
+    __syncthreads();
+    if (t == 0) {
+        unsigned long long w[NV];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            float a = 0.f;
+            for (int i = 0; i < nw; ++i) a += wsum[j * 32 + i];
+            w[j] = ((unsigned long long)e << 32) | __float_as_uint(a);
+        }
+        xch_store_words(line, w, NV);
+    }
+}
+template <int NV>
+__device__ bool xch_collect_packed(float (&v)[NV], const unsigned long long* slots, unsigned int e, int* err, float* sc,
+                                   long long limit = kExchangeSpinLimit) {
+    const int G = (int)gridDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const unsigned long long* base = slots + (size_t)(e & 1) * G * kXchPad;
+    float* gv = sc + NV * 32;          // [NV][G] polled CTA sums
+    float* res = gv + NV * G;          // [NV] grid sums
+    bool ok = true;
+    for (int c = t; c < G && ok; c += blockDim.x) {
+        const unsigned long long* line = base + (size_t)c * kXchPad;
+        long long spins = 0;
+        for (;;) {
+            unsigned long long w[3] = {0ull, 0ull, 0ull};
+            if (NV >= 2)
+                asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(w[0]), "=l"(w[1]) : "l"(line) : "memory");
+            else
+                asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(w[0]) : "l"(line) : "memory");
+            if (NV == 3) asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(w[2]) : "l"(line + 2) : "memory");
+            bool all = true;
+#pragma unroll
+            for (int j = 0; j < NV; ++j) all = all && (unsigned int)(w[j] >> 32) == e;
+            if (all) {
+#pragma unroll
+                for (int j = 0; j < NV; ++j) gv[j * G + c] = __uint_as_float((unsigned int)w[j]);
+                break;
+            }
+            if (*(volatile int*)err) { ok = false; break; }
+            if (++spins > limit) {
+                atomicExch(err, 1);
+                ok = false;
+                break;
+            }
+            if (spins > 32) __nanosleep(20);
+        }
+    }
+    if (__syncthreads_or(!ok)) return false;
+    if (warp < NV) {
+        float a = 0.f;
+        for (int c = lane; c < G; c += 32) a += gv[warp * G + c];
+        a = warp_sum_t<float>(a);
+        if (lane == 0) res[warp] = a;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < NV; ++j) v[j] = res[j];
+    return true;
+}
+
 // v[j] (this thread's share) -> the grid-wide sums, identical in every CTA.
 // slots: [parity 2][value kXchMaxNV][G][kXchPad]; the parity is that of e, so
 // consecutive calls must use consecutive epochs.
