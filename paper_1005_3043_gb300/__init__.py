@@ -329,10 +329,17 @@ def mg_get_coarse_op(ctx, Vc: int, nc: int) -> np.ndarray:
     return out
 
 
-def mg_solve(ctx, b):
-    """Host solve: returns (x, info dict).  NOT_CONVERGED is reported in info."""
+def mg_solve(ctx, b, out=None):
+    """Host solve: returns (x, info dict).  NOT_CONVERGED is reported in info.
+    ``out``: an optional contiguous complex128 host array of b's size (e.g. a
+    view of pinned memory) that receives x."""
     b = _host(b)
-    x = np.empty_like(b)
+    if out is None:
+        x = np.empty_like(b)
+    else:
+        x = out
+        if not isinstance(x, np.ndarray) or x.dtype != np.complex128 or not x.flags.c_contiguous or x.size != b.size:
+            raise ValueError("out must be a contiguous complex128 array of the source's size")
     info = MgSolveInfo()
     _check(load().mg_solve(ctx, _ptr(b), _ptr(x), ctypes.byref(info)), ctx, allow=(MG_ERR_NOT_CONVERGED,))
     return x, info.as_dict()
@@ -615,8 +622,8 @@ class WilsonMG:
     def coarse_op(self):
         return mg_get_coarse_op(self.ctx, self.Vc, self.nc)
 
-    def solve(self, b):
-        return mg_solve(self.ctx, b)
+    def solve(self, b, out=None):
+        return mg_solve(self.ctx, b, out)
 
     def solve_device(self, b_dev, x_dev):
         return mg_solve_device(self.ctx, b_dev, x_dev)
