@@ -442,6 +442,10 @@ enum mg_kernel_class {
  * the coarse CG iterations run since the last read (profiling on or off). */
 int mg_profile_enable(mg_ctx* ctx, int on);
 int mg_profile_read(mg_ctx* ctx, double* ms, int* launches, double* coarse_iters);
+/* Kernel classes the launch timer tracks while enabled: bit c of mask selects
+ * class c (MG_K_*); default all.  Tracking one class keeps the event records
+ * off the others' launches.  MG_ERR_INVALID_ARG for a mask with no class. */
+int mg_profile_classes(mg_ctx* ctx, unsigned int mask);
 
 /* Number of kernel launches this library has issued in the process so far
  * (all contexts); the difference over a region counts its launches (a

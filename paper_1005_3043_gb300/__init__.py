@@ -111,6 +111,7 @@ _SIGS = {
     "mg_time_dslash_cold": ([_P, _I, _I, _P, ctypes.c_size_t, _P, _P], _I),
     "mg_profile_enable": ([_P, _I], _I),
     "mg_profile_read": ([_P, _P, _P, _P], _I),
+    "mg_profile_classes": ([_P, ctypes.c_uint], _I),
     "mg_kernel_launches": ([], ctypes.c_longlong),
     "mg_coarse_kernel": ([ctypes.c_void_p], ctypes.c_int),
     "mg_check_wait_timeout": ([_P, _I, ctypes.c_longlong], _I),
@@ -515,6 +516,14 @@ def mg_profile_enable(ctx, on: bool = True) -> None:
     _check(load().mg_profile_enable(ctx, int(bool(on))), ctx)
 
 
+def mg_profile_classes(ctx, classes) -> None:
+    """Track only the given kernel classes (names of KERNEL_CLASSES) while profiling."""
+    mask = 0
+    for c in classes:
+        mask |= 1 << KERNEL_CLASSES.index(c)
+    _check(load().mg_profile_classes(ctx, mask), ctx)
+
+
 def mg_profile_read(ctx):
     """({class: (total ms, launches)}, coarse CG iterations) since the last read."""
     n = len(KERNEL_CLASSES)
@@ -669,6 +678,9 @@ class WilsonMG:
 
     def profile_read(self):
         return mg_profile_read(self.ctx)
+
+    def profile_classes(self, classes):
+        mg_profile_classes(self.ctx, classes)
 
     def time_dslash(self, prec=MG_FP32, reps=50):
         return mg_time_dslash(self.ctx, prec, reps)

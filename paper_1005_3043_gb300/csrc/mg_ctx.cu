@@ -191,6 +191,7 @@ struct mg_ctx {
     std::vector<void*> allocs;
     // launch timer
     bool prof = false;
+    unsigned int prof_mask = 0xFFu;   // classes the launch timer tracks
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
     std::vector<int> ev_class;      // class of each (start, stop) pair
@@ -262,7 +263,7 @@ int read_scalars(mg_ctx* ctx, int first, int count) {
 
 // launch timer: a (start, stop) event pair around tracked launches
 int prof_mark(mg_ctx* ctx, int cls, bool start) {
-    if (!ctx->prof) return MG_OK;
+    if (!ctx->prof || !((ctx->prof_mask >> cls) & 1u)) return MG_OK;
     if (ctx->ev_used == ctx->ev_pool.size()) {
         cudaEvent_t e;
         CK(cudaEventCreate(&e));
@@ -2166,6 +2167,14 @@ int mg_time_dslash_cold(mg_ctx* ctx, int prec, int reps, void* flush, size_t flu
 int mg_profile_enable(mg_ctx* ctx, int on) {
     if (!ctx) return MG_ERR_INVALID_ARG;
     ctx->prof = on != 0;
+    return MG_OK;
+}
+
+int mg_profile_classes(mg_ctx* ctx, unsigned int mask) {
+    if (!ctx) return MG_ERR_INVALID_ARG;
+    if (!(mask & ((1u << MG_K_NCLASSES) - 1u))) return fail(ctx, MG_ERR_INVALID_ARG, "the mask selects no kernel class");
+    if (!ctx->ev_class.empty()) return fail(ctx, MG_ERR_INVALID_ARG, "read the launch timer before changing its classes");
+    ctx->prof_mask = mask;
     return MG_OK;
 }
 

@@ -221,6 +221,33 @@ def test_solve_into_caller_buffer(c1):
     assert np.abs(x2 - x).max() <= 1e-13 * np.abs(x).max()
 
 
+def test_launch_timer_classes(c1):
+    """The launch timer tracks the selected kernel classes only; the selection
+    cannot change while recorded launches are unread, and an empty one is refused."""
+    L, B, nv, U, m = c1["L"], c1["B"], c1["nv"], c1["U"], c1["m"]
+    b = synth.gaussian_spinor(L, 7)
+    with wmg.WilsonMG(L, make_params(nv, B, prec_inner=wmg.MG_FP32, delta=1e-4)) as mg:
+        mg.set_links(U)
+        mg.set_mass(m)
+        mg.set_null_vectors(c1["Vs"])
+        mg.profile_classes(["coarse_solve"])
+        mg.profile_enable(True)
+        mg.solve(b)
+        with pytest.raises(RuntimeError):
+            mg.profile_classes(["dslash"])          # unread launches pending
+        one, iters = mg.profile_read()
+        assert one["coarse_solve"][1] > 0 and iters > 0
+        assert all(v == (0.0, 0) for k, v in one.items() if k != "coarse_solve")
+        mg.profile_classes(wmg.KERNEL_CLASSES)
+        mg.solve(b)
+        every, _ = mg.profile_read()
+        mg.profile_enable(False)
+        assert every["coarse_solve"][1] == one["coarse_solve"][1]
+        assert every["dslash"][1] > 0 and every["krylov"][1] > 0
+        with pytest.raises(RuntimeError):
+            mg.profile_classes([])
+
+
 def test_solve_fp32_inner_reaches_fp64_residual(c1):
     L, B, nv, U, m = c1["L"], c1["B"], c1["nv"], c1["U"], c1["m"]
     b = synth.gaussian_spinor(L, 7)
