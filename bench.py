@@ -586,7 +586,7 @@ def run_ours(args, w):
     # DRAM bytes per launch of the dominant kernel from one ncu capture of this
     # command (dram__bytes_read.sum + dram__bytes_write.sum); known only for the
     # kernel and workload that were captured
-    traffic = {("wilson_16x16x16x32_nv20_beta6_5mass", "fp16", "coarse_solve"): 30.28e6 + 0.12e6}.get(
+    traffic = {("wilson_16x16x16x32_nv20_beta6_5mass", "fp16", "coarse_solve"): 30.16e6 + 0.09e6}.get(
         (w.name, args.prec, dom))
     peaks = {}
     try:
