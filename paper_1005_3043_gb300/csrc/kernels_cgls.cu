@@ -17,7 +17,12 @@
 // the grid barrier.  The stencil operand (the CG vector on the CTA's
 // aggregates and their 8 neighbours) is staged in shared memory per phase,
 // pre-multiplied by the FP16 block scales and with the sigma_3 sign flips of
-// D_c^dag = sigma_3 D_c sigma_3 applied.
+// D_c^dag = sigma_3 D_c sigma_3 applied.  In tensor memory (TM = 1, 2) the
+// CTA takes all 512 columns of its SM and the operator is written there once
+// per launch: TM = 1 keeps it as each thread's share of rows and columns and
+// forms the products with packed FP32 FMAs; TM = 2 (FP16 operator) keeps the
+// CTA's first 128 rows as the A operand of tcgen05.mma and forms the stencil
+// as one MMA tile per phase (see kMmaRows).
 //
 // Iteration, two forms with the same iterates in exact arithmetic.
 // Textbook CGLS (cgls_body: two grid-wide exchanges of partial sums, which
