@@ -576,11 +576,12 @@ template <bool H16, int TM> struct CglsCta {
         mph ^= 1;
     }
 
-    // TM == 2 products and epilogue (after the staging barrier): thread 0 issues
-    // the 9nc/8 MMAs of the tile and commits them to the mbarrier; meanwhile
-    // warps 4.. sum the rows beyond the tile; every thread waits for the commit;
-    // warps 0-3 read their lanes' 32 accumulator columns and keep the four of
-    // their row's aggregate; pre_emit; one emitting thread per row.
+    // TM == 2 products and epilogue (after the staging barrier): lane 0 of warps
+    // 0 .. nacc-1 issue the 9nc/8 MMAs of the tile as nacc chains into nacc
+    // accumulators and commit them to the mbarrier; meanwhile warps 4.. sum the
+    // rows beyond the tile; every thread waits for the commits; warp 4j + q
+    // reads accumulator j on lane quadrant q and keeps its row's four columns
+    // in part[j][row]; pre_emit; one emitting thread per row sums the partials.
     template <bool DAG, int EPI, typename Pre>
     __device__ bool mma_phase(CglsPhase& ph, float& n0, float& n1, Pre& pre_emit) {
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
